@@ -1,0 +1,307 @@
+#!/usr/bin/env python3
+"""Throughput of the hybrid LB step (stress history integral + D2Q9 stream-collide) on one GB300.
+
+Workload: the 1024 x 512 D2Q9 channel with L = 1024 retained history points per node (B = 8 blocks of
+C = 128), FP32, synthetic initial density noise 1e-6 (seed 2).  A step is one full hybrid step of every
+node.  Metric: node-history updates per second (one retained history point of one node processed in
+one step); MLUPS of the full step is reported beside it.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+--impl ours (default): the CUDA library through its C ABI.  Timed region: K steps bracketed by a
+barrier and a device synchronisation, CUDA events on the launching stream, max over ranks.  The
+history state (17 GB) is far larger than L2, so no flush is needed between steps.
+--impl reference: the FP64 CPU oracle (tests' reference implementation) on the host cores, on a
+bounded sample of the same workload (2 of the 1024 columns, all 512 rows, full history).
+With N > 1 (torchrun) every rank runs an independent replica (the method does not shard across
+GPUs here): value = all ranks' updates / slowest rank's time.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "node-history updates/s"
+UNIT = "node-history updates/s"
+BYTES_PER_UPDATE = 48        # FP32 D2Q9: read X (16 B) + write X (16 B) + read kappa (16 B) per point
+FALLBACK_HBM_GBS = 6800.0
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=300)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    return ap.parse_args()
+
+
+def dist_env():
+    return int(os.environ.get("RANK", "0")), int(os.environ.get("WORLD_SIZE", "1")), int(os.environ.get("LOCAL_RANK", "0"))
+
+
+def peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        with open(p) as f:
+            d = json.load(f)
+        return float(d["hbm_gbs"]), "measured"
+    return FALLBACK_HBM_GBS, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons, sampled every 100 ms while the timed region runs."""
+    Q = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.hw_slowdown,"
+         "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+         "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.index = index
+        self.proc = None
+        self.path = None
+
+    def __enter__(self):
+        fd, self.path = tempfile.mkstemp(suffix=".csv")
+        os.close(fd)
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.Q}",
+                                          "--format=csv,noheader,nounits", "-lms", "100"],
+                                         stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+        time.sleep(0.3)
+        return self
+
+    def __exit__(self, *a):
+        if self.proc is not None:
+            time.sleep(0.2)
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except Exception:
+                self.proc.kill()
+
+    def summary(self):
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        sm, mx, reasons = [], [], set()
+        try:
+            for line in open(self.path):
+                f = [x.strip() for x in line.split(",")]
+                if len(f) < 7:
+                    continue
+                try:
+                    sm.append(float(f[0]))
+                    mx.append(float(f[1]))
+                except ValueError:
+                    continue
+                for name, v in zip(names, f[3:7]):
+                    if v.lower() == "active":
+                        reasons.add(name)
+        finally:
+            os.unlink(self.path)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"], "samples": 0}
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx), "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def points_per_step(C: int, B: int, t0: int, K: int, L) -> list:
+    """Retained history points (including the one created) of steps t0 .. t0+K-1 (same at every node)."""
+    return [len(L.lbve_schedule(C, B, t)[0]) for t in range(t0, t0 + K)]
+
+
+def kernel_hash() -> str:
+    h = hashlib.sha256()
+    for f in ("lbve_kernels.cuh", "lbve_sched.cuh"):
+        with open(os.path.join(ROOT, "paper_1504_06123_gb300", "csrc", f), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()[:16]
+
+
+def recorded_traffic():
+    """DRAM bytes per history launch from the committed ncu summary, if it was taken on these kernels."""
+    p = os.path.join(ROOT, "profiles", "history_channel_1024x512_L1024.md")
+    if not os.path.exists(p):
+        return None
+    kh, traffic = None, None
+    for line in open(p):
+        if line.startswith("kernel_source_sha256_16:"):
+            kh = line.split(":", 1)[1].strip()
+        if line.startswith("dram_bytes_per_launch:"):
+            traffic = float(line.split(":", 1)[1].strip())
+    return traffic if kh == kernel_hash() else None
+
+
+def oracle_sample(steps: int | None = None, budget_s: float = 12.0, warmup: int = 1):
+    """The FP64 oracle on 2 columns x 512 rows of the benchmark channel with its full history: `warmup`
+    untimed steps, then `steps` timed ones (or as many as fit in budget_s)."""
+    import oracle
+    from paper_1504_06123_gb300 import configs, inputs
+    w = configs.plain_channel_large()
+    nx = 2
+    rho = inputs.initial_density(w.N, w.noise, w.seed).reshape(w.ny, w.nx)[:, :nx].ravel()
+    ch = oracle.Channel(oracle.D2Q9, nx, w.ny, tau_lb=w.tau_lb, G_inf=w.G_inf, tau=w.tau, gamma_c=w.gamma_c,
+                        g=(w.g, 0, 0), C=w.C, B=w.B, rho_init=rho)
+    t0 = time.perf_counter()
+    ch.step(max(1, warmup))
+    one = (time.perf_counter() - t0) / max(1, warmup)
+    t_start = ch.t
+    n = steps if steps is not None else max(2, int(budget_s / max(one, 1e-6)))
+    t0 = time.perf_counter()
+    ch.step(n)
+    dt = time.perf_counter() - t0
+    pts = [len(oracle.schedule(w.C, w.B, t)[0]) for t in range(t_start, t_start + n)]
+    upd = nx * w.ny * sum(pts)
+    ch.close()
+    sample = f"{nx} of {w.nx} columns x {w.ny} rows, L = {w.L}, steps {t_start}..{t_start + n - 1} ({dt:.1f} s)"
+    return upd / dt, sample, n, dt, upd
+
+
+def run_reference(args, rank, world):
+    if rank != 0:
+        return
+    # each step: one oracle step of the sample (about 0.1 s on one core)
+    val, sample, n, dt, upd = oracle_sample(steps=args.steps, warmup=args.warmup)
+    line = {
+        "metric": METRIC, "value": val, "unit": UNIT, "n_gpus": args.gpus, "steps": n, "warmup": args.warmup,
+        "ms_per_step": 1e3 * dt / n, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": "f64", "data": "synthetic", "impl": "reference",
+        "config": {"workload": "channel_1024x512_L1024", "sample": sample},
+        "cpu_baseline": {"value": val, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": sample},
+        "e2e": {"value": val, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+        "gpu_launches": 0,
+    }
+    print(json.dumps(line), flush=True)
+
+
+def run_ours(args, rank, world, local_rank):
+    import numpy as np
+    import torch
+    import torch.distributed as dist
+
+    from paper_1504_06123_gb300 import configs
+    from paper_1504_06123_gb300 import lbve as L
+
+    torch.cuda.set_device(local_rank)
+    if world > 1:
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local_rank))
+
+    def barrier():
+        if world > 1:
+            dist.barrier()
+
+    def max_over_ranks(x: float) -> float:
+        if world == 1:
+            return x
+        t = torch.tensor([x], dtype=torch.float64, device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        return float(t.item())
+
+    w = configs.plain_channel_large()
+    stream = torch.cuda.current_stream()
+    ch = L.Channel(w.desc(), w.rho_init())
+    K, W = args.steps, args.warmup
+    ch.step(W, stream)
+    torch.cuda.synchronize()
+    pts = points_per_step(w.C, w.B, W, K, L)
+    updates_rank = w.N * sum(pts)
+    mem_points = [p - 1 for p in pts]           # the new point of each step is not read from memory
+
+    L.lbve_profile(ch.h, True)
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    with ClockSampler(local_rank) as clk:
+        barrier()
+        torch.cuda.synchronize()
+        ev0.record(stream)
+        ch.step(K, stream)
+        ev1.record(stream)
+        torch.cuda.synchronize()
+        barrier()
+    ms = ev0.elapsed_time(ev1)
+    kms, launches = L.lbve_profile_read(ch.h)
+    L.lbve_profile(ch.h, False)
+    ms_max = max_over_ranks(ms)
+    value = updates_rank * world / (ms_max / 1e3)
+    mlups = w.N * K * world / (ms_max / 1e3) / 1e6
+
+    # roofline of the dominant kernel (the history sweep), from its own events
+    hist_ms = kms[1] / max(launches[1], 1)
+    alg_bytes = BYTES_PER_UPDATE * w.N * (sum(mem_points) / len(mem_points))
+    peak, peak_kind = peaks()
+    achieved = alg_bytes / (hist_ms / 1e3) / 1e9
+    traffic = recorded_traffic()
+
+    # end to end through the C ABI: every step sets the force (host scalars), advances one step and
+    # reads u and sigma back into pinned host memory
+    e2e = None
+    if not args.no_e2e:
+        mask = L.LBVE_FIELD_U | L.LBVE_FIELD_SIGMA
+        cnt = L.lbve_fields_count(ch.h, mask)
+        host = torch.empty(cnt, dtype=torch.float64, pin_memory=True)
+        Ke = max(10, K // 4)
+        pts_e = points_per_step(w.C, w.B, W + K, Ke, L)
+        barrier()
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        for _ in range(Ke):
+            L.lbve_set_force(ch.h, (w.g, 0.0, 0.0))
+            L.lbve_step(ch.h, 1, stream)
+            L.load().lbve_fields(ch.h, mask, host.data_ptr(), 0, int(stream.cuda_stream) or None)
+        torch.cuda.synchronize()
+        dt = max_over_ranks(time.perf_counter() - t0)
+        e2e = {"value": w.N * sum(pts_e) * world / dt, "unit": UNIT, "h2d_bytes_per_step": 24,
+               "d2h_bytes_per_step": 8 * cnt, "steps": Ke}
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        val, sample, *_ = oracle_sample()
+        cpu = {"value": val, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": sample}
+
+    if rank == 0:
+        line = {
+            "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": K, "warmup": W,
+            "ms_per_step": ms_max / K, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": "f32", "data": "synthetic",
+            "config": {"workload": "channel_1024x512_L1024", "lattice": "D2Q9", "nodes": w.N, "history_points": w.L,
+                       "blocks_B": w.B, "block_C": w.C, "tau_lb": w.tau_lb, "G_inf": w.G_inf, "tau": w.tau,
+                       "gamma_c": w.gamma_c, "g": w.g, "parallelism": f"replicas{world}",
+                       "l2": "no flush: history state 17.2 GB >> 129 MB L2"},
+            "mlups": mlups,
+            "kernel_ms_per_launch": {"moments": kms[0] / max(launches[0], 1), "history": hist_ms,
+                                     "collide_stream": kms[2] / max(launches[2], 1)},
+            "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                         "frac": achieved / peak, "traffic": traffic, "peak_kind": peak_kind,
+                         "kernel": "k_history", "algorithmic_bytes_per_launch": alg_bytes},
+            "clocks": clk.summary(),
+            "gpu_launches": int(sum(launches)),
+            "e2e": e2e,
+            "cpu_baseline": cpu,
+        }
+        print(json.dumps(line), flush=True)
+    ch.close()
+    if world > 1:
+        dist.destroy_process_group()
+
+
+def main():
+    args = parse()
+    rank, world, local_rank = dist_env()
+    if args.impl == "reference":
+        run_reference(args, rank, world)
+    else:
+        run_ours(args, rank, world, local_rank)
+
+
+if __name__ == "__main__":
+    main()

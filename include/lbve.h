@@ -1,0 +1,163 @@
+/*
+ * lbve.h -- C ABI of the GB300 (sm_103a) hybrid lattice-Boltzmann library for the integral nonlinear
+ * Maxwell fluid of Papenkort & Voigtmann, "Lattice Boltzmann simulations of a viscoelastic
+ * shear-thinning fluid" (arXiv:1504.06123).
+ *
+ * Every function is extern "C", takes plain pointers and sizes, returns an int status (LBVE_OK = 0 or
+ * a negative LBVE_E* code) and never lets a C++ exception cross it.  Device work is enqueued on the
+ * CUDA stream passed as `void* stream` (NULL = the legacy default stream); calls that return data
+ * to host memory synchronise that stream first.  A handle is not thread-safe: use one handle per host
+ * thread.
+ *
+ * Conventions (all arrays):
+ *   - lattice units dt = dx = 1;
+ *   - node index n = x + nx*(y + ny*z), x fastest; x is periodic; walls (half-way bounce-back) at
+ *     y = -1/2 and ny-1/2, and, for a D3Q19 duct, at z = -1/2 and nz-1/2;
+ *   - kappa[a][b] = d v_a / d x_b (kappa = (grad v)^T, Sec. I), d*d components, row-major;
+ *   - sigma (symmetric) components: 2D xx, yy, xy; 3D xx, yy, zz, xy, xz, yz.
+ */
+#ifndef LBVE_H
+#define LBVE_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ---- status codes ---------------------------------------------------------------------------- */
+#define LBVE_OK           0
+#define LBVE_EINVAL      -1  /* an argument is out of range; nothing was changed */
+#define LBVE_ENOMEM      -2  /* device memory could not be allocated */
+#define LBVE_ECUDA       -3  /* a CUDA call or kernel launch failed (see lbve_last_cuda_error) */
+#define LBVE_ENONFINITE  -4  /* a NaN or Inf appeared in the state */
+#define LBVE_ESTATE      -6  /* the call does not fit the handle's state */
+#define LBVE_ENOSUPPORT  -7  /* a valid combination this build does not implement */
+
+/* ---- enumerations ---------------------------------------------------------------------------- */
+#define LBVE_D2Q9   9    /* planar channel, Sec. III velocity set */
+#define LBVE_D3Q19 19    /* square duct ("the extension to 3D is straightforward", Sec. III) */
+
+#define LBVE_F32 0       /* populations / history stored in float */
+#define LBVE_F64 1       /* populations / history stored in double */
+#define LBVE_BF16 2      /* history stored as bfloat16 deviations (precision variant) */
+
+#define LBVE_TRACE_FULL 0 /* Eq. (bodyforce) with the density source d_t(delta rho) as written */
+#define LBVE_TRACE_NONE 1 /* both d_t(delta rho) terms dropped, rho = sum n (channel simplification) */
+
+#define LBVE_FIELD_RHO   1u  /* [N]        hydrodynamic density of Eq. (hydrofields) */
+#define LBVE_FIELD_U     2u  /* [d][N]     velocity u = (sum c n + f/2)/rho */
+#define LBVE_FIELD_SIGMA 4u  /* [nsig][N]  sigma_struc of Eq. (gitt) */
+#define LBVE_FIELD_KAPPA 8u  /* [d*d][N]   velocity gradient of the last step */
+#define LBVE_FIELD_N1   16u  /* [N]        first normal-stress difference sigma_xx - sigma_yy */
+
+/* ---- channel description (problem statement of Sec. III/IV) ----------------------------------- */
+typedef struct {
+    int32_t lattice;          /* LBVE_D2Q9 (nz must be 1) or LBVE_D3Q19 */
+    int32_t nx, ny, nz;       /* fluid nodes; ny >= 2 (walled); a duct needs nz >= 2 */
+    int32_t wall_z;           /* D3Q19: 1 = walls in z as well (square duct), 0 = z periodic */
+    double  tau_lb;           /* BGK relaxation time (> 1/2); eta_N = rho0 c_s^2 (tau_lb - 1/2) */
+    double  rho0;             /* reference density (populations are stored as n_i - w_i rho0) */
+    double  G_inf;            /* plateau modulus G_inf of Eq. (nlmax) (>= 0) */
+    double  tau;              /* structural relaxation time tau of Eq. (nlmax), in steps (> 0) */
+    double  gamma_c;          /* strain scale gamma_c of Eq. (nlmax) (> 0; +INFINITY = UCM limit) */
+    double  g[3];             /* body force per unit mass; force density f = rho0 g (Sec. IV driving) */
+    int32_t hist_C;           /* points per history block C (Sec. III; the paper uses 128), >= 4 */
+    int32_t hist_B;           /* number of blocks B, 1..16; B*C points span about C (2^B - 1) steps */
+    int32_t hist_storage;     /* LBVE_F32 | LBVE_F64 (| LBVE_BF16 where supported) */
+    int32_t pop_precision;    /* LBVE_F32 | LBVE_F64 (must equal hist_storage for F32/F64) */
+    int32_t trace_coupling;   /* LBVE_TRACE_FULL | LBVE_TRACE_NONE */
+} lbve_channel_desc;
+
+typedef struct lbve lbve_t;   /* opaque; owns every device buffer of one channel */
+
+/*
+ * Create a channel on the current CUDA device: fluid at rest, n_i = w_i rho_init(n) (rho0 where
+ * rho_init is NULL; otherwise a host array of N doubles, copied), every history point at rest
+ * (E = 1, kappa = 0).  The history grid of Sec. III starts full, so the first steps already run the
+ * block merges.  Device memory: 2 Q N populations, (d^2 + d^2) (B C + ... ) N history words and a few
+ * fields; sizes in lbve_memory_bytes.  *out is NULL on failure.
+ * Errors: EINVAL (bad sizes or parameters, including a shear-wave speed sqrt(G_inf/rho0) > 0.5 that
+ * the explicit stress coupling cannot carry), ENOMEM, ECUDA, ENOSUPPORT.
+ */
+int lbve_create(const lbve_channel_desc* desc, const double* rho_init, lbve_t** out);
+
+/* Free every device buffer of the handle (synchronises the device).  NULL is ignored. */
+void lbve_destroy(lbve_t* h);
+
+/* Replace the body force (startup / cessation, Sec. IV); takes effect at the next step. */
+int lbve_set_force(lbve_t* h, const double g[3]);
+
+/* Replace G_inf, tau, gamma_c of Eq. (nlmax); takes effect at the next step. */
+int lbve_set_params(lbve_t* h, double G_inf, double tau, double gamma_c);
+
+/*
+ * Advance n_steps >= 0 full hybrid steps (Sec. III): moments -> kappa by finite differences -> stress
+ * history (advance E, insert/merge per the quasi-logarithmic grid, -d_t'B, modulus of Eq. (nlmax),
+ * trapezoidal sum of Eq. (gitt)) -> trace split, density source, BGK collision with the forcing of
+ * Eq. (bodyforce) -> streaming with bounce-back.  Asynchronous on `stream`.
+ */
+int lbve_step(lbve_t* h, int64_t n_steps, void* stream);
+
+/* Number of completed steps (host-side counter; no synchronisation). */
+int lbve_get_time(const lbve_t* h, int64_t* t);
+
+/*
+ * Write the fields selected by field_mask (LBVE_FIELD_*) of the last completed step as doubles into
+ * dst, one block per field in increasing bit order, each block component-major ([comp][N]).
+ * dst_is_device = 1: dst is device memory (stream-ordered, asynchronous); 0: host memory (the call
+ * synchronises `stream`).  The caller owns dst; its size must be lbve_fields_count(h, mask) doubles.
+ * Returns ENONFINITE (after copying) when a copied value is NaN or Inf and dst is host memory (a
+ * device-side flag set by the copy kernel).
+ */
+int lbve_fields(lbve_t* h, uint32_t field_mask, double* dst, int32_t dst_is_device, void* stream);
+
+/* Number of doubles lbve_fields writes for field_mask. */
+int lbve_fields_count(const lbve_t* h, uint32_t field_mask, size_t* count);
+
+/*
+ * Test hook for the stress history alone (steps of Sec. III on a prescribed gradient): advance every
+ * node's history by one step with kappa(t) taken from kappa_dev (device, [d*d][N] doubles) instead of
+ * the finite differences of the flow, and write sigma_struc(t) to sigma_dev (device, [nsig][N]
+ * doubles).  Uses and advances the same history and step counter as lbve_step.  Asynchronous.
+ */
+int lbve_history_apply(lbve_t* h, const double* kappa_dev, double* sigma_dev, void* stream);
+
+/*
+ * Mass bookkeeping of the density source (Sec. III): *sum_n = total of all populations, *sum_drho =
+ * total of delta rho(t-1) = -tr sigma(t-1)/(d c_s^2).  With LBVE_TRACE_FULL their difference is
+ * conserved by the scheme.  Synchronises `stream`.
+ */
+int lbve_mass(lbve_t* h, double* sum_n, double* sum_drho, void* stream);
+
+/*
+ * The retained history points after step t >= 0 for blocks of C points and B blocks (identical at
+ * every node): their creation times t' newest first and trapezoidal weights.  tp_out and w_out must
+ * hold B*C entries; *n_out receives the count.  Pure host function (no device, no handle).
+ */
+int lbve_schedule(int32_t C, int32_t B, int64_t t, int64_t* tp_out, double* w_out, int32_t* n_out);
+
+/* Device bytes held by the handle (populations, history, fields). */
+int lbve_memory_bytes(const lbve_t* h, size_t* bytes);
+
+/*
+ * Kernel timing for benchmarks: with enable = 1, every later lbve_step records a CUDA event pair on
+ * its stream around each of its launches (moments, history, collide-stream).  lbve_profile_read waits
+ * for the last event, returns the summed device milliseconds and launch counts per kernel in that
+ * order (ms_out[3], launches_out[3]) and clears the record.  enable = 0 stops recording.
+ */
+int lbve_profile(lbve_t* h, int32_t enable);
+int lbve_profile_read(lbve_t* h, double ms_out[3], int64_t launches_out[3]);
+
+/* Static description of a status code. */
+const char* lbve_strerror(int status);
+
+/* Text of the last CUDA error seen by this library in the calling thread ("" if none). */
+const char* lbve_last_cuda_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* LBVE_H */

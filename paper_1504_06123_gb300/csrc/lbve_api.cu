@@ -1,0 +1,547 @@
+// lbve_api.cu -- runtime and C ABI (include/lbve.h) of the hybrid LB library.
+//
+// The handle owns every device buffer of one channel; allocation happens once in lbve_create, after
+// which lbve_step only enqueues kernels on the caller's stream.  The step counter lives in device
+// memory, so a step is a fixed sequence of launches that never needs host state.
+#include <cuda_runtime.h>
+
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <algorithm>
+#include <new>
+#include <utility>
+#include <vector>
+
+#include "../../include/lbve.h"
+#include "lbve_kernels.cuh"
+
+using namespace lbk;
+
+namespace {
+
+thread_local char g_cuda_err[256] = "";
+
+int cuda_fail(cudaError_t e, const char* what) {
+    std::snprintf(g_cuda_err, sizeof g_cuda_err, "%s: %s", what, cudaGetErrorString(e));
+    return e == cudaErrorMemoryAllocation ? LBVE_ENOMEM : LBVE_ECUDA;
+}
+
+#define LBVE_CUDA(call)                                \
+    do {                                               \
+        cudaError_t e_ = (call);                       \
+        if (e_ != cudaSuccess) return cuda_fail(e_, #call); \
+    } while (0)
+
+}  // namespace
+
+struct lbve {
+    lbve_channel_desc d;
+    int D, Q, NS, N, L;
+    long long Npad;
+    int dbl;                   // 1: populations and history in double
+    size_t esz;                // element size
+    void* pops[2] = {nullptr, nullptr};
+    int cur = 0;
+    void* u_raw = nullptr;
+    void* u = nullptr;
+    void* rho = nullptr;
+    void* sigma = nullptr;
+    void* kappa = nullptr;
+    void* tr_prev = nullptr;
+    void* X = nullptr;
+    void* K = nullptr;
+    long long* t_dev = nullptr;
+    double* red = nullptr;     // reduction scratch (2 doubles)
+    double* stage = nullptr;   // lbve_fields staging for host destinations
+    size_t stage_n = 0;
+    int64_t t_host = 0;
+    size_t bytes = 0;
+    int* flag = nullptr;       // non-finite flag of lbve_fields
+    // kernel timing (lbve_profile): event pairs recorded around each launch of lbve_step
+    int profiling = 0;
+    std::vector<cudaEvent_t> ev_pool;
+    size_t ev_used = 0;
+    std::vector<int> ev_kind;  // kernel id of each recorded pair
+};
+
+namespace {
+
+void free_all(lbve* h) {
+    void* ptrs[] = {h->pops[0], h->pops[1], h->u_raw, h->u, h->rho, h->sigma, h->kappa, h->tr_prev,
+                    h->X, h->K, h->t_dev, h->red, h->stage, h->flag};
+    for (void* p : ptrs)
+        if (p) cudaFree(p);
+    for (cudaEvent_t e : h->ev_pool) cudaEventDestroy(e);
+    h->ev_pool.clear();
+}
+
+// Kernel timing: mark(h, s, kind, true) before a launch and mark(h, s, kind, false) after it.
+enum { KIND_MOMENTS = 0, KIND_HISTORY = 1, KIND_COLLIDE = 2, KIND_COUNT = 3 };
+
+int prof_mark(lbve* h, cudaStream_t s, int kind, bool start) {
+    if (!h->profiling) return LBVE_OK;
+    if (h->ev_used == h->ev_pool.size()) {
+        cudaEvent_t e;
+        LBVE_CUDA(cudaEventCreate(&e));
+        h->ev_pool.push_back(e);
+    }
+    LBVE_CUDA(cudaEventRecord(h->ev_pool[h->ev_used++], s));
+    if (start) h->ev_kind.push_back(kind);
+    return LBVE_OK;
+}
+
+int alloc(lbve* h, void** p, size_t bytes) {
+    cudaError_t e = cudaMalloc(p, bytes);
+    if (e != cudaSuccess) {
+        *p = nullptr;
+        return cuda_fail(e, "cudaMalloc");
+    }
+    h->bytes += bytes;
+    return LBVE_OK;
+}
+
+Geom geom_of(const lbve* h) {
+    Geom g;
+    g.nx = h->d.nx;
+    g.ny = h->d.ny;
+    g.nz = h->d.nz;
+    g.wall_z = h->d.lattice == LBVE_D3Q19 ? h->d.wall_z : 0;
+    g.N = h->N;
+    g.Npad = h->Npad;
+    return g;
+}
+
+template <typename real>
+Phys<real> phys_of(const lbve* h) {
+    Phys<real> p;
+    p.rho0 = (real)h->d.rho0;
+    p.tau_lb = (real)h->d.tau_lb;
+    for (int a = 0; a < 3; ++a) p.f[a] = (real)(h->d.rho0 * h->d.g[a]);
+    p.G_inf = (real)h->d.G_inf;
+    p.inv_tau = (real)(1.0 / h->d.tau);
+    p.inv_gc = std::isinf(h->d.gamma_c) ? (real)0 : (real)(1.0 / h->d.gamma_c);
+    p.trace_full = h->d.trace_coupling == LBVE_TRACE_FULL;
+    return p;
+}
+
+int check_desc(const lbve_channel_desc* d) {
+    if (!d) return LBVE_EINVAL;
+    if (d->lattice != LBVE_D2Q9 && d->lattice != LBVE_D3Q19) return LBVE_EINVAL;
+    if (d->nx < 1 || d->ny < 2 || d->nz < 1) return LBVE_EINVAL;
+    if (d->lattice == LBVE_D2Q9 && d->nz != 1) return LBVE_EINVAL;
+    if (d->lattice == LBVE_D3Q19 && d->wall_z && d->nz < 2) return LBVE_EINVAL;
+    if ((long long)d->nx * d->ny * d->nz > (1ll << 30)) return LBVE_EINVAL;
+    if (!(d->tau_lb > 0.5) || !(d->rho0 > 0) || !(d->G_inf >= 0) || !(d->tau > 0) || !(d->gamma_c > 0))
+        return LBVE_EINVAL;
+    if (!std::isfinite(d->tau_lb) || !std::isfinite(d->rho0) || !std::isfinite(d->G_inf) || !std::isfinite(d->tau))
+        return LBVE_EINVAL;
+    for (int a = 0; a < 3; ++a)
+        if (!std::isfinite(d->g[a])) return LBVE_EINVAL;
+    // explicit stress coupling: shear-wave speed sqrt(G_inf/rho0) well below the lattice speed
+    if (std::sqrt(d->G_inf / d->rho0) > 0.5) return LBVE_EINVAL;
+    if (d->hist_C < 4 || d->hist_B < 1 || d->hist_B > LBVE_MAXB) return LBVE_EINVAL;
+    if ((long long)d->hist_C * d->hist_B > 4096) return LBVE_EINVAL;
+    if (d->trace_coupling != LBVE_TRACE_FULL && d->trace_coupling != LBVE_TRACE_NONE) return LBVE_EINVAL;
+    if (d->pop_precision != LBVE_F32 && d->pop_precision != LBVE_F64) return LBVE_EINVAL;
+    if (d->hist_storage != LBVE_F32 && d->hist_storage != LBVE_F64 && d->hist_storage != LBVE_BF16)
+        return LBVE_EINVAL;
+    if (d->hist_storage != d->pop_precision) return LBVE_ENOSUPPORT;
+    return LBVE_OK;
+}
+
+// Slot groups per CTA for the history sweep: enough CTAs to fill the GPU, the rest of the threads
+// split each node's points.
+int pick_groups(int N) {
+    const int sms = 152;
+    int G = 1;
+    while (G < 8 && (long long)((N + (256 / G) - 1) / (256 / G)) < 2ll * sms) G *= 2;
+    return G;
+}
+
+template <int D, typename real, int G>
+int launch_history_g(lbve* h, const HistArgs<real>& a, cudaStream_t s) {
+    const Geom g = geom_of(h);
+    const Phys<real> p = phys_of<real>(h);
+    constexpr int NODES = 256 / G;
+    const size_t smem = history_smem_bytes<D, real, G>(h->L);
+    if (smem > 48 * 1024)
+        LBVE_CUDA(cudaFuncSetAttribute(k_history<D, real, G>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    const int grid = (h->N + NODES - 1) / NODES;
+    k_history<D, real, G><<<grid, 256, smem, s>>>(a, g, p);
+    LBVE_CUDA(cudaGetLastError());
+    return LBVE_OK;
+}
+
+template <int D, typename real>
+int launch_history(lbve* h, const double* kappa_in, double* sigma_dbl, cudaStream_t s) {
+    HistArgs<real> a;
+    a.X = (real*)h->X;
+    a.K = (real*)h->K;
+    a.u_raw = (const real*)h->u_raw;
+    a.kappa_in = kappa_in;
+    a.kappa = (real*)h->kappa;
+    a.sigma = (real*)h->sigma;
+    a.sigma_dbl = sigma_dbl;
+    a.t_dev = h->t_dev;
+    a.B = h->d.hist_B;
+    a.C = h->d.hist_C;
+    switch (pick_groups(h->N)) {
+        case 1: return launch_history_g<D, real, 1>(h, a, s);
+        case 2: return launch_history_g<D, real, 2>(h, a, s);
+        case 4: return launch_history_g<D, real, 4>(h, a, s);
+        default: return launch_history_g<D, real, 8>(h, a, s);
+    }
+}
+
+__global__ void k_advance_t(long long* t) { *t += 1; }
+
+template <int Q, typename real>
+int step_impl(lbve* h, int64_t n, cudaStream_t s) {
+    constexpr int D = Lattice<Q>::D;
+    const Geom g = geom_of(h);
+    const Phys<real> p = phys_of<real>(h);
+    const int grid = (h->N + 255) / 256;
+    for (int64_t i = 0; i < n; ++i) {
+        const real* din = (const real*)h->pops[h->cur];
+        real* dout = (real*)h->pops[h->cur ^ 1];
+        int rc;
+        if ((rc = prof_mark(h, s, KIND_MOMENTS, true))) return rc;
+        k_moments<Q, real><<<grid, 256, 0, s>>>(din, (real*)h->u_raw, g, p);
+        LBVE_CUDA(cudaGetLastError());
+        if ((rc = prof_mark(h, s, KIND_MOMENTS, false))) return rc;
+        if ((rc = prof_mark(h, s, KIND_HISTORY, true))) return rc;
+        rc = launch_history<D, real>(h, nullptr, nullptr, s);
+        if (rc) return rc;
+        if ((rc = prof_mark(h, s, KIND_HISTORY, false))) return rc;
+        CollArgs<real> c;
+        c.dn_in = din;
+        c.dn_out = dout;
+        c.sigma = (const real*)h->sigma;
+        c.tr_prev = (real*)h->tr_prev;
+        c.rho = (real*)h->rho;
+        c.u = (real*)h->u;
+        c.t_dev = h->t_dev;
+        if ((rc = prof_mark(h, s, KIND_COLLIDE, true))) return rc;
+        k_collide_stream<Q, real><<<grid, 256, 0, s>>>(c, g, p);
+        LBVE_CUDA(cudaGetLastError());
+        if ((rc = prof_mark(h, s, KIND_COLLIDE, false))) return rc;
+        h->cur ^= 1;
+        h->t_host += 1;
+    }
+    return LBVE_OK;
+}
+
+// Fluid at rest: n_q = w_q rho_init(n) (deviation w_q (rho_init - rho0)), rho field = rho_init.
+template <typename real>
+__global__ void k_init(real* dn, real* rho, long long Npad, int N, int Q, const double* rho_init, double rho0,
+                       const double* w) {
+    const int n = blockIdx.x * blockDim.x + threadIdx.x;
+    if (n >= N) return;
+    const double r = rho_init ? rho_init[n] : rho0;
+    for (int q = 0; q < Q; ++q) dn[q * Npad + n] = (real)(w[q] * (r - rho0));
+    rho[n] = (real)r;
+}
+
+template <typename real>
+int init_state(lbve* h, const double* rho_init_host) {
+    double w[19];
+    for (int q = 0; q < h->Q; ++q) w[q] = h->Q == 9 ? Lattice<9>::w(q) : Lattice<19>::w(q);
+    double* tmp = nullptr;   // [Q] weights then [N] initial densities
+    const size_t n_tmp = h->Q + (rho_init_host ? (size_t)h->N : 0);
+    LBVE_CUDA(cudaMalloc(&tmp, sizeof(double) * n_tmp));
+    cudaError_t e = cudaMemcpy(tmp, w, sizeof(double) * h->Q, cudaMemcpyHostToDevice);
+    if (e == cudaSuccess && rho_init_host)
+        e = cudaMemcpy(tmp + h->Q, rho_init_host, sizeof(double) * h->N, cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) {
+        k_init<real><<<(h->N + 255) / 256, 256>>>((real*)h->pops[0], (real*)h->rho, h->Npad, h->N, h->Q,
+                                                  rho_init_host ? tmp + h->Q : nullptr, h->d.rho0, tmp);
+        e = cudaGetLastError();
+    }
+    if (e == cudaSuccess) e = cudaDeviceSynchronize();
+    cudaFree(tmp);
+    if (e != cudaSuccess) return cuda_fail(e, "initial state");
+    return LBVE_OK;
+}
+
+template <typename real>
+int fields_impl(lbve* h, uint32_t mask, double* dst, cudaStream_t s) {
+    const long long Np = h->Npad;
+    const int N = h->N;
+    size_t off = 0;
+    auto gather = [&](const void* src, int ncomp) -> int {
+        const long long tot = (long long)ncomp * N;
+        if (tot > 0) {
+            k_gather<real><<<(int)((tot + 255) / 256), 256, 0, s>>>((const real*)src, Np, ncomp, N, dst + off,
+                                                                      h->flag);
+            LBVE_CUDA(cudaGetLastError());
+        }
+        off += (size_t)tot;
+        return LBVE_OK;
+    };
+    int rc;
+    if (mask & LBVE_FIELD_RHO) if ((rc = gather(h->rho, 1))) return rc;
+    if (mask & LBVE_FIELD_U) if ((rc = gather(h->u, h->D))) return rc;
+    if (mask & LBVE_FIELD_SIGMA) if ((rc = gather(h->sigma, h->NS))) return rc;
+    if (mask & LBVE_FIELD_KAPPA) if ((rc = gather(h->kappa, h->D * h->D))) return rc;
+    if (mask & LBVE_FIELD_N1) {
+        if (N > 0) {
+            k_n1<real><<<(N + 255) / 256, 256, 0, s>>>((const real*)h->sigma, Np, N, dst + off, h->flag);
+            LBVE_CUDA(cudaGetLastError());
+        }
+        off += N;
+    }
+    return LBVE_OK;
+}
+
+size_t fields_count(const lbve* h, uint32_t mask) {
+    size_t c = 0;
+    if (mask & LBVE_FIELD_RHO) c += 1;
+    if (mask & LBVE_FIELD_U) c += h->D;
+    if (mask & LBVE_FIELD_SIGMA) c += h->NS;
+    if (mask & LBVE_FIELD_KAPPA) c += (size_t)h->D * h->D;
+    if (mask & LBVE_FIELD_N1) c += 1;
+    return c * (size_t)h->N;
+}
+
+template <typename real>
+int mass_impl(lbve* h, double* sum_n, double* sum_drho, cudaStream_t s) {
+    LBVE_CUDA(cudaMemsetAsync(h->red, 0, 2 * sizeof(double), s));
+    const int grid = 4 * 152;
+    k_sum<real><<<grid, 256, 0, s>>>((const real*)h->pops[h->cur], h->Npad, h->Q, h->N, 1.0, h->red);
+    LBVE_CUDA(cudaGetLastError());
+    // delta rho(t-1) = -tr sigma(t-1) / (d cs^2) = -3 tr / d
+    k_sum<real><<<grid, 256, 0, s>>>((const real*)h->tr_prev, h->Npad, 1, h->N, -3.0 / h->D, h->red + 1);
+    LBVE_CUDA(cudaGetLastError());
+    double r[2];
+    LBVE_CUDA(cudaMemcpyAsync(r, h->red, sizeof r, cudaMemcpyDeviceToHost, s));
+    LBVE_CUDA(cudaStreamSynchronize(s));
+    *sum_n = r[0] + h->d.rho0 * (double)h->N;   // populations are stored as n - w rho0
+    *sum_drho = r[1];
+    return LBVE_OK;
+}
+
+}  // namespace
+
+// =================================================================================================
+// C ABI
+// =================================================================================================
+extern "C" {
+
+int lbve_create(const lbve_channel_desc* desc, const double* rho_init, lbve_t** out) {
+    if (!out) return LBVE_EINVAL;
+    *out = nullptr;
+    int rc = check_desc(desc);
+    if (rc) return rc;
+    if (rho_init) {
+        const long long N = (long long)desc->nx * desc->ny * desc->nz;
+        for (long long i = 0; i < N; ++i)
+            if (!std::isfinite(rho_init[i]) || !(rho_init[i] > 0)) return LBVE_EINVAL;
+    }
+    lbve* h = new (std::nothrow) lbve();
+    if (!h) return LBVE_ENOMEM;
+    h->d = *desc;
+    h->D = desc->lattice == LBVE_D2Q9 ? 2 : 3;
+    h->Q = desc->lattice;
+    h->NS = h->D == 2 ? 3 : 6;
+    h->N = desc->nx * desc->ny * desc->nz;
+    h->L = desc->hist_C * desc->hist_B;
+    h->Npad = ((long long)h->N + 127) / 128 * 128;
+    h->dbl = desc->pop_precision == LBVE_F64;
+    h->esz = h->dbl ? 8 : 4;
+    const long long Np = h->Npad;
+    const int DD = h->D * h->D;
+    if ((rc = alloc(h, &h->pops[0], h->esz * h->Q * Np)) || (rc = alloc(h, &h->pops[1], h->esz * h->Q * Np)) ||
+        (rc = alloc(h, &h->u_raw, h->esz * h->D * Np)) || (rc = alloc(h, &h->u, h->esz * h->D * Np)) ||
+        (rc = alloc(h, &h->rho, h->esz * Np)) || (rc = alloc(h, &h->sigma, h->esz * h->NS * Np)) ||
+        (rc = alloc(h, &h->kappa, h->esz * DD * Np)) || (rc = alloc(h, &h->tr_prev, h->esz * Np)) ||
+        (rc = alloc(h, &h->X, h->esz * (size_t)h->L * DD * Np)) ||
+        (rc = alloc(h, &h->K, h->esz * (size_t)h->L * DD * Np)) ||
+        (rc = alloc(h, (void**)&h->t_dev, sizeof(long long))) || (rc = alloc(h, (void**)&h->red, 2 * sizeof(double))) ||
+        (rc = alloc(h, (void**)&h->flag, sizeof(int)))) {
+        free_all(h);
+        delete h;
+        return rc;
+    }
+    // zero every buffer: rest state, empty history (E = 1 <=> X = 0, kappa = 0), t = 0
+    void* zero_bufs[] = {h->pops[0], h->pops[1], h->u_raw, h->u, h->sigma, h->kappa, h->tr_prev, h->X, h->K,
+                         h->t_dev, h->flag};
+    size_t zero_sizes[] = {h->esz * h->Q * Np, h->esz * h->Q * Np, h->esz * h->D * Np, h->esz * h->D * Np,
+                           h->esz * h->NS * Np, h->esz * DD * Np, h->esz * Np, h->esz * (size_t)h->L * DD * Np,
+                           h->esz * (size_t)h->L * DD * Np, sizeof(long long), sizeof(int)};
+    for (int i = 0; i < 11; ++i) {
+        cudaError_t e = cudaMemset(zero_bufs[i], 0, zero_sizes[i]);
+        if (e != cudaSuccess) {
+            rc = cuda_fail(e, "cudaMemset");
+            free_all(h);
+            delete h;
+            return rc;
+        }
+    }
+    rc = h->dbl ? init_state<double>(h, rho_init) : init_state<float>(h, rho_init);
+    if (rc) {
+        free_all(h);
+        delete h;
+        return rc;
+    }
+    *out = h;
+    return LBVE_OK;
+}
+
+void lbve_destroy(lbve_t* h) {
+    if (!h) return;
+    cudaDeviceSynchronize();
+    free_all(h);
+    delete h;
+}
+
+int lbve_set_force(lbve_t* h, const double g[3]) {
+    if (!h || !g) return LBVE_EINVAL;
+    for (int a = 0; a < 3; ++a)
+        if (!std::isfinite(g[a])) return LBVE_EINVAL;
+    for (int a = 0; a < 3; ++a) h->d.g[a] = g[a];
+    return LBVE_OK;
+}
+
+int lbve_set_params(lbve_t* h, double G_inf, double tau, double gamma_c) {
+    if (!h) return LBVE_EINVAL;
+    lbve_channel_desc d = h->d;
+    d.G_inf = G_inf;
+    d.tau = tau;
+    d.gamma_c = gamma_c;
+    int rc = check_desc(&d);
+    if (rc) return rc;
+    h->d = d;
+    return LBVE_OK;
+}
+
+int lbve_step(lbve_t* h, int64_t n_steps, void* stream) {
+    if (!h || n_steps < 0) return LBVE_EINVAL;
+    cudaStream_t s = (cudaStream_t)stream;
+    if (h->Q == 9) return h->dbl ? step_impl<9, double>(h, n_steps, s) : step_impl<9, float>(h, n_steps, s);
+    return h->dbl ? step_impl<19, double>(h, n_steps, s) : step_impl<19, float>(h, n_steps, s);
+}
+
+int lbve_get_time(const lbve_t* h, int64_t* t) {
+    if (!h || !t) return LBVE_EINVAL;
+    *t = h->t_host;
+    return LBVE_OK;
+}
+
+int lbve_fields_count(const lbve_t* h, uint32_t mask, size_t* count) {
+    if (!h || !count || (mask & ~31u)) return LBVE_EINVAL;
+    *count = fields_count(h, mask);
+    return LBVE_OK;
+}
+
+int lbve_fields(lbve_t* h, uint32_t mask, double* dst, int32_t dst_is_device, void* stream) {
+    if (!h || !dst || (mask & ~31u)) return LBVE_EINVAL;
+    cudaStream_t s = (cudaStream_t)stream;
+    const size_t cnt = fields_count(h, mask);
+    if (dst_is_device) return h->dbl ? fields_impl<double>(h, mask, dst, s) : fields_impl<float>(h, mask, dst, s);
+    if (h->stage_n < cnt) {
+        if (h->stage) cudaFree(h->stage);
+        h->stage = nullptr;
+        h->stage_n = 0;
+        LBVE_CUDA(cudaMalloc(&h->stage, sizeof(double) * (cnt > 0 ? cnt : 1)));
+        h->stage_n = cnt;
+    }
+    LBVE_CUDA(cudaMemsetAsync(h->flag, 0, sizeof(int), s));
+    int rc = h->dbl ? fields_impl<double>(h, mask, h->stage, s) : fields_impl<float>(h, mask, h->stage, s);
+    if (rc) return rc;
+    int flag = 0;
+    LBVE_CUDA(cudaMemcpyAsync(dst, h->stage, sizeof(double) * cnt, cudaMemcpyDeviceToHost, s));
+    LBVE_CUDA(cudaMemcpyAsync(&flag, h->flag, sizeof(int), cudaMemcpyDeviceToHost, s));
+    LBVE_CUDA(cudaStreamSynchronize(s));
+    return flag ? LBVE_ENONFINITE : LBVE_OK;
+}
+
+int lbve_history_apply(lbve_t* h, const double* kappa_dev, double* sigma_dev, void* stream) {
+    if (!h || !kappa_dev || !sigma_dev) return LBVE_EINVAL;
+    cudaStream_t s = (cudaStream_t)stream;
+    int rc;
+    if (h->D == 2) rc = h->dbl ? launch_history<2, double>(h, kappa_dev, sigma_dev, s)
+                               : launch_history<2, float>(h, kappa_dev, sigma_dev, s);
+    else rc = h->dbl ? launch_history<3, double>(h, kappa_dev, sigma_dev, s)
+                     : launch_history<3, float>(h, kappa_dev, sigma_dev, s);
+    if (rc) return rc;
+    k_advance_t<<<1, 1, 0, s>>>(h->t_dev);
+    LBVE_CUDA(cudaGetLastError());
+    h->t_host += 1;
+    return LBVE_OK;
+}
+
+int lbve_mass(lbve_t* h, double* sum_n, double* sum_drho, void* stream) {
+    if (!h || !sum_n || !sum_drho) return LBVE_EINVAL;
+    cudaStream_t s = (cudaStream_t)stream;
+    return h->dbl ? mass_impl<double>(h, sum_n, sum_drho, s) : mass_impl<float>(h, sum_n, sum_drho, s);
+}
+
+int lbve_schedule(int32_t C, int32_t B, int64_t t, int64_t* tp_out, double* w_out, int32_t* n_out) {
+    if (C < 4 || B < 1 || B > LBVE_MAXB || t < 0 || !tp_out || !w_out || !n_out) return LBVE_EINVAL;
+    // the same per-slot roles the history kernel evaluates, plus the point created at step t
+    BlockStep bs[LBVE_MAXB];
+    sched_step(B, C, (long long)t, bs);
+    std::vector<std::pair<long long, double>> pts;
+    pts.reserve((size_t)B * C);
+    pts.emplace_back(0, 0.5);
+    for (int bb = 0; bb < B; ++bb)
+        for (int j = 0; j < C; ++j) {
+            int age, part;
+            const float w = sched_slot_role(bs, C, bb, j, &age, &part);
+            if (w != 0.0f) pts.emplace_back(age, (double)w);
+        }
+    std::sort(pts.begin(), pts.end());
+    for (size_t k = 0; k < pts.size(); ++k) {
+        tp_out[k] = t - pts[k].first;
+        w_out[k] = pts[k].second;
+    }
+    *n_out = (int32_t)pts.size();
+    return LBVE_OK;
+}
+
+int lbve_memory_bytes(const lbve_t* h, size_t* bytes) {
+    if (!h || !bytes) return LBVE_EINVAL;
+    *bytes = h->bytes;
+    return LBVE_OK;
+}
+
+const char* lbve_strerror(int status) {
+    switch (status) {
+        case LBVE_OK: return "ok";
+        case LBVE_EINVAL: return "invalid argument";
+        case LBVE_ENOMEM: return "out of device memory";
+        case LBVE_ECUDA: return "CUDA error";
+        case LBVE_ENONFINITE: return "non-finite value in the state";
+        case LBVE_ESTATE: return "call does not fit the handle's state";
+        case LBVE_ENOSUPPORT: return "combination not supported by this build";
+        default: return "unknown status";
+    }
+}
+
+const char* lbve_last_cuda_error(void) { return g_cuda_err; }
+
+int lbve_profile(lbve_t* h, int32_t enable) {
+    if (!h) return LBVE_EINVAL;
+    h->profiling = enable ? 1 : 0;
+    h->ev_used = 0;
+    h->ev_kind.clear();
+    return LBVE_OK;
+}
+
+int lbve_profile_read(lbve_t* h, double ms_out[3], int64_t launches_out[3]) {
+    if (!h || !ms_out || !launches_out) return LBVE_EINVAL;
+    for (int k = 0; k < KIND_COUNT; ++k) { ms_out[k] = 0.0; launches_out[k] = 0; }
+    if (h->ev_used > 0) LBVE_CUDA(cudaEventSynchronize(h->ev_pool[h->ev_used - 1]));
+    for (size_t i = 0; i < h->ev_kind.size(); ++i) {
+        float ms = 0.0f;
+        LBVE_CUDA(cudaEventElapsedTime(&ms, h->ev_pool[2 * i], h->ev_pool[2 * i + 1]));
+        ms_out[h->ev_kind[i]] += ms;
+        launches_out[h->ev_kind[i]] += 1;
+    }
+    h->ev_used = 0;
+    h->ev_kind.clear();
+    return LBVE_OK;
+}
+
+}  // extern "C"

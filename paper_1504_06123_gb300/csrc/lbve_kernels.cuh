@@ -1,0 +1,567 @@
+// lbve_kernels.cuh -- sm_103a kernels of one hybrid LB step (Sec. III of arXiv:1504.06123).
+//
+// Per step, three launches on one stream:
+//   k_moments        : u_raw = (sum c n + f/2) / sum n                                (Eq. hydrofields)
+//   k_history        : kappa(t) by finite differences; every retained history point advances
+//                      E <- exp(kappa(t-1)) E, forms -d_t'B = E kappa E^T + (.)^T and the modulus of
+//                      Eq. (nlmax), and the trapezoidal sum of Eq. (gitt) gives sigma_struc(t); then
+//                      the block merges of the quasi-logarithmic grid and the new point.  This is the
+//                      O(nodes x points) part and the only one that matters for bandwidth.
+//   k_collide_stream : trace split, density source, BGK collision with the forcing of Eq. (bodyforce),
+//                      push streaming with half-way bounce-back.
+//
+// Layouts (device, structure of arrays, every plane padded to Npad nodes):
+//   populations  d_n[q][Npad]            stored as n_q - w_q rho0 (deviation form keeps FP32 exact
+//                                        enough for velocities of 1e-5)
+//   history      X[slot][c][Npad]        X = E - 1 of each retained point (c < d*d, row-major)
+//                K[slot][c][Npad]        kappa of each retained point
+//   fields       u_raw[d][Npad], kappa[d*d][Npad], sigma[nsig][Npad], tr_prev[Npad], rho[Npad], u[d][Npad]
+// slot = bb*C + ring index, bb = 0 (coarsest block) .. B-1 (finest).
+#pragma once
+#include <cuda_runtime.h>
+#include <math.h>
+#include <stdint.h>
+
+#include "lbve_sched.cuh"
+
+namespace lbk {
+
+// ------------------------------------------------------------------------------------------------
+// Velocity sets (Sec. III for D2Q9; standard D3Q19 for the duct).  cs^2 = 1/3.
+// ------------------------------------------------------------------------------------------------
+template <int Q> struct Lattice;
+
+template <> struct Lattice<9> {
+    static constexpr int D = 2;
+    __host__ __device__ static constexpr int cx(int q) { return q == 1 || q == 5 || q == 8 ? 1 : (q == 3 || q == 6 || q == 7 ? -1 : 0); }
+    __host__ __device__ static constexpr int cy(int q) { return q == 2 || q == 5 || q == 6 ? 1 : (q == 4 || q == 7 || q == 8 ? -1 : 0); }
+    __host__ __device__ static constexpr int cz(int) { return 0; }
+    __host__ __device__ static constexpr double w(int q) { return q == 0 ? 4.0 / 9.0 : (q <= 4 ? 1.0 / 9.0 : 1.0 / 36.0); }
+    __host__ __device__ static constexpr int opp(int q) { return q == 0 ? 0 : (q <= 4 ? ((q + 1) % 4) + 1 : ((q - 5 + 2) % 4) + 5); }
+};
+
+// D3Q19: 0 rest; 1..6 faces +x,-x,+y,-y,+z,-z; 7..18 edges.
+template <> struct Lattice<19> {
+    static constexpr int D = 3;
+    __host__ __device__ static constexpr int c(int q, int a) {
+        // faces
+        return q == 0 ? 0
+             : q <= 6 ? (((q - 1) / 2) == a ? (((q - 1) & 1) ? -1 : 1) : 0)
+             : edge(q - 7, a);
+    }
+    // edges: for axis pairs (x,y), (x,z), (y,z), signs (+,+), (+,-), (-,+), (-,-)
+    __host__ __device__ static constexpr int edge(int e, int a) {
+        return (pair_a(e / 4) == a) ? ((e & 2) ? -1 : 1) : ((pair_b(e / 4) == a) ? ((e & 1) ? -1 : 1) : 0);
+    }
+    __host__ __device__ static constexpr int pair_a(int p) { return p == 2 ? 1 : 0; }
+    __host__ __device__ static constexpr int pair_b(int p) { return p == 0 ? 1 : 2; }
+    __host__ __device__ static constexpr int cx(int q) { return c(q, 0); }
+    __host__ __device__ static constexpr int cy(int q) { return c(q, 1); }
+    __host__ __device__ static constexpr int cz(int q) { return c(q, 2); }
+    __host__ __device__ static constexpr double w(int q) { return q == 0 ? 1.0 / 3.0 : (q <= 6 ? 1.0 / 18.0 : 1.0 / 36.0); }
+    __host__ __device__ static constexpr int opp(int q) {
+        return q == 0 ? 0 : (q <= 6 ? (((q - 1) ^ 1) + 1) : (((q - 7) ^ 3) + 7));
+    }
+};
+
+// ------------------------------------------------------------------------------------------------
+// Geometry and parameters shared by the kernels
+// ------------------------------------------------------------------------------------------------
+struct Geom {
+    int nx, ny, nz;   // nodes per axis
+    int wall_z;       // walls at z = -1/2, nz - 1/2
+    int N;            // nx*ny*nz
+    long long Npad;   // plane stride (multiple of 128)
+};
+
+template <typename real> struct Phys {
+    real rho0, tau_lb;
+    real f[3];        // force density rho0 g
+    real G_inf, inv_tau, inv_gc;
+    int trace_full;
+};
+
+__device__ __forceinline__ void node_xyz(const Geom& g, int n, int& x, int& y, int& z) {
+    x = n % g.nx;
+    const int r = n / g.nx;
+    y = r % g.ny;
+    z = r / g.ny;
+}
+
+// ------------------------------------------------------------------------------------------------
+// K1: raw moments -> u_raw
+// ------------------------------------------------------------------------------------------------
+template <int Q, typename real>
+__global__ void __launch_bounds__(256) k_moments(const real* __restrict__ dn, real* __restrict__ u_raw, Geom g,
+                                                 Phys<real> p) {
+    using L = Lattice<Q>;
+    constexpr int D = L::D;
+    const int n = blockIdx.x * blockDim.x + threadIdx.x;
+    if (n >= g.N) return;
+    real drho = 0, j[3] = {0, 0, 0};
+#pragma unroll
+    for (int q = 0; q < Q; ++q) {
+        const real v = dn[(long long)q * g.Npad + n];
+        drho += v;
+        if (L::cx(q)) j[0] += L::cx(q) * v;
+        if (L::cy(q)) j[1] += L::cy(q) * v;
+        if (D == 3 && L::cz(q)) j[2] += L::cz(q) * v;
+    }
+    const real inv = real(1) / (p.rho0 + drho);
+#pragma unroll
+    for (int a = 0; a < D; ++a) u_raw[(long long)a * g.Npad + n] = (j[a] + real(0.5) * p.f[a]) * inv;
+}
+
+// ------------------------------------------------------------------------------------------------
+// kappa(t) by second-order finite differences of u_raw (Sec. III): central in the bulk and on
+// periodic axes; at a wall-adjacent node the derivative of the parabola through the no-slip wall
+// half a node away and the two nearest nodes: low wall u0 + u1/3, high wall -(u0 + u_{-1}/3).
+// ------------------------------------------------------------------------------------------------
+template <typename real>
+__device__ __forceinline__ real d_axis(real um, real u0, real up, int i, int n, bool periodic) {
+    if (periodic) return real(0.5) * (up - um);
+    if (i == 0) return u0 + up * real(1.0 / 3.0);
+    if (i == n - 1) return -(u0 + um * real(1.0 / 3.0));
+    return real(0.5) * (up - um);
+}
+
+template <int D, typename real>
+__device__ __forceinline__ void kappa_fd(const real* __restrict__ u, const Geom& g, int n, real* kap) {
+    int x, y, z;
+    node_xyz(g, n, x, y, z);
+    const int xm = (x == 0 ? g.nx - 1 : x - 1), xp = (x == g.nx - 1 ? 0 : x + 1);
+    const int ym = (y == 0 ? y : y - 1), yp = (y == g.ny - 1 ? y : y + 1);
+    const int nxm = xm + g.nx * (y + g.ny * z), nxp = xp + g.nx * (y + g.ny * z);
+    const int nym = x + g.nx * (ym + g.ny * z), nyp = x + g.nx * (yp + g.ny * z);
+#pragma unroll
+    for (int a = 0; a < D; ++a) {
+        const real* ua = u + (long long)a * g.Npad;
+        const real u0 = ua[n];
+        kap[a * D + 0] = d_axis(ua[nxm], u0, ua[nxp], x, g.nx, true);
+        kap[a * D + 1] = d_axis(ua[nym], u0, ua[nyp], y, g.ny, false);
+    }
+    if (D == 3) {
+        int zm, zp;
+        if (g.wall_z) { zm = (z == 0 ? z : z - 1); zp = (z == g.nz - 1 ? z : z + 1); }
+        else { zm = (z == 0 ? g.nz - 1 : z - 1); zp = (z == g.nz - 1 ? 0 : z + 1); }
+        const int nzm = x + g.nx * (y + g.ny * zm), nzp = x + g.nx * (y + g.ny * zp);
+#pragma unroll
+        for (int a = 0; a < D; ++a) {
+            const real* ua = u + (long long)a * g.Npad;
+            kap[a * D + (D - 1)] = d_axis(ua[nzm], ua[n], ua[nzp], z, g.nz, !g.wall_z);
+        }
+    }
+}
+
+// ------------------------------------------------------------------------------------------------
+// Small matrix algebra in registers
+// ------------------------------------------------------------------------------------------------
+// A = exp(K) - 1 by the Taylor series in Horner form, truncated after K^4/4! (float: |K| <= 1e-2
+// leaves < 1e-12) or K^8/8! (double).
+template <int D, typename real>
+__device__ __forceinline__ void expm1_mat(const real* K, real* A) {
+    constexpr int DD = D * D;
+    constexpr int ORDER = sizeof(real) == 4 ? 4 : 8;
+    real P[DD];
+#pragma unroll
+    for (int i = 0; i < DD; ++i) P[i] = K[i] * real(1.0 / ORDER);   // K/ORDER
+#pragma unroll
+    for (int m = ORDER - 1; m >= 1; --m) {
+        // P <- K (1 + P) / m
+        real T[DD];
+#pragma unroll
+        for (int r = 0; r < D; ++r)
+#pragma unroll
+            for (int c = 0; c < D; ++c) {
+                real s = K[r * D + c];
+#pragma unroll
+                for (int k = 0; k < D; ++k) s += K[r * D + k] * P[k * D + c];
+                T[r * D + c] = s * real(1.0 / m);
+            }
+#pragma unroll
+        for (int i = 0; i < DD; ++i) P[i] = T[i];
+    }
+#pragma unroll
+    for (int i = 0; i < DD; ++i) A[i] = P[i];
+}
+
+// One history point: advance X <- X + A + A X, then the integrand w g (E kap E^T + (E kap E^T)^T)
+// accumulated into acc (nsig packed components).
+template <int D, typename real>
+__device__ __forceinline__ void point_update(real* X, const real* A, const real* kap, real age, real w,
+                                             real inv_tau, real inv_gc, real* acc) {
+    constexpr int DD = D * D;
+    real Xn[DD];
+#pragma unroll
+    for (int r = 0; r < D; ++r)
+#pragma unroll
+        for (int c = 0; c < D; ++c) {
+            real s = X[r * D + c] + A[r * D + c];
+#pragma unroll
+            for (int k = 0; k < D; ++k) s += A[r * D + k] * X[k * D + c];
+            Xn[r * D + c] = s;
+        }
+#pragma unroll
+    for (int i = 0; i < DD; ++i) X[i] = Xn[i];
+    // M = E kap E^T with E = 1 + X
+    real EK[DD];
+#pragma unroll
+    for (int r = 0; r < D; ++r)
+#pragma unroll
+        for (int c = 0; c < D; ++c) {
+            real s = kap[r * D + c];
+#pragma unroll
+            for (int k = 0; k < D; ++k) s += X[r * D + k] * kap[k * D + c];
+            EK[r * D + c] = s;
+        }
+    real M[DD];
+#pragma unroll
+    for (int r = 0; r < D; ++r)
+#pragma unroll
+        for (int c = 0; c < D; ++c) {
+            real s = EK[r * D + c];
+#pragma unroll
+            for (int k = 0; k < D; ++k) s += EK[r * D + k] * X[c * D + k];
+            M[r * D + c] = s;
+        }
+    // local shear rate of the point: gammadot^2 = (1/2) tr D^2, D = kap + kap^T
+    real trD2 = 0;
+#pragma unroll
+    for (int r = 0; r < D; ++r)
+#pragma unroll
+        for (int c = 0; c < D; ++c) {
+            const real Drc = kap[r * D + c] + kap[c * D + r];
+            trD2 += Drc * Drc;
+        }
+    const real gd = sqrt(real(0.5) * trD2);
+    const real gw = w * exp(-age * (inv_tau + gd * inv_gc));
+    if (D == 2) {
+        acc[0] += gw * (M[0] + M[0]);
+        acc[1] += gw * (M[3] + M[3]);
+        acc[2] += gw * (M[1] + M[2]);
+    } else {
+        acc[0] += gw * (M[0] + M[0]);
+        acc[1] += gw * (M[4] + M[4]);
+        acc[2] += gw * (M[8] + M[8]);
+        acc[3] += gw * (M[1] + M[3]);
+        acc[4] += gw * (M[2] + M[6]);
+        acc[5] += gw * (M[5] + M[7]);
+    }
+}
+
+// ------------------------------------------------------------------------------------------------
+// K2: the stress history integral
+// ------------------------------------------------------------------------------------------------
+template <typename real> struct HistArgs {
+    real* __restrict__ X;             // [L][DD][Npad]
+    real* __restrict__ K;             // [L][DD][Npad]
+    const real* __restrict__ u_raw;   // [D][Npad]  (flow path)
+    const double* __restrict__ kappa_in;  // [DD][N] prescribed gradient (test hook) or nullptr
+    real* __restrict__ kappa;         // [DD][Npad] kappa(t) out
+    real* __restrict__ sigma;         // [NS][Npad] sigma_struc(t) out
+    double* __restrict__ sigma_dbl;   // [NS][N] optional copy in double (test hook) or nullptr
+    const long long* t_dev;           // step index t
+    int B, C;
+};
+
+// Byte offset of the reduction buffer in the history kernel's shared memory (16-byte aligned).
+__host__ __device__ inline size_t history_red_offset(int L) {
+    const size_t o = (size_t)L * 12 + sizeof(BlockStep) * LBVE_MAXB;
+    return (o + 15) & ~(size_t)15;
+}
+
+template <int D, typename real, int G>
+__host__ __device__ inline size_t history_smem_bytes(int L) {
+    constexpr int NS = D == 2 ? 3 : 6;
+    return history_red_offset(L) + sizeof(real) * (size_t)(G > 1 ? G - 1 : 0) * NS * (256 / G);
+}
+
+// Threads of a CTA: NODES consecutive nodes x G slot groups; group gi handles slots gi, gi+G, ...
+// Shared memory: per slot age (float), weight (float), partner (int) + the per-block state +
+// the cross-group reduction buffer.
+template <int D, typename real, int G>
+__global__ void __launch_bounds__(256) k_history(HistArgs<real> a, Geom g, Phys<real> p) {
+    constexpr int DD = D * D;
+    constexpr int NS = D == 2 ? 3 : 6;
+    constexpr int NODES = 256 / G;
+    const int L = a.B * a.C;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    float* s_age = reinterpret_cast<float*>(smem_raw);
+    float* s_w = s_age + L;
+    int* s_part = reinterpret_cast<int*>(s_w + L);
+    BlockStep* s_bs = reinterpret_cast<BlockStep*>(s_part + L);
+    real* s_red = reinterpret_cast<real*>(smem_raw + history_red_offset(L));   // [G-1][NS][NODES]
+
+    const long long t = *a.t_dev;
+    if (threadIdx.x == 0) sched_step(a.B, a.C, t, s_bs);
+    __syncthreads();
+    for (int l = threadIdx.x; l < L; l += blockDim.x) {
+        int age, part;
+        const float w = sched_slot_role(s_bs, a.C, l / a.C, l % a.C, &age, &part);
+        s_age[l] = (float)age;
+        s_w[l] = w;
+        s_part[l] = part;
+    }
+    __syncthreads();
+
+    const int ln = threadIdx.x % NODES;
+    const int gi = threadIdx.x / NODES;
+    const int n = blockIdx.x * NODES + ln;
+    const long long Np = g.Npad;
+    const bool live = n < g.N;
+
+    real acc[NS];
+#pragma unroll
+    for (int i = 0; i < NS; ++i) acc[i] = 0;
+
+    if (live) {
+        // A = exp(kappa(t-1)) - 1; kappa(t-1) is the kappa of the point created last step, held at the
+        // newest slot of the finest block (a rest point, kappa = 0, before the first step).
+        real A[DD];
+        {
+            const long long s_last = (long long)(a.B - 1) * a.C + s_bs[a.B - 1].head_prev;
+            real kp[DD];
+#pragma unroll
+            for (int c = 0; c < DD; ++c) kp[c] = a.K[(s_last * DD + c) * Np + n];
+            expm1_mat<D>(kp, A);
+        }
+        for (int l = gi; l < L; l += G) {
+            const float w = s_w[l];
+            if (w == 0.0f) continue;
+            real X[DD], kap[DD];
+            real* Xp = a.X + (long long)l * DD * Np + n;
+            const real* Kp = a.K + (long long)l * DD * Np + n;
+#pragma unroll
+            for (int c = 0; c < DD; ++c) { X[c] = Xp[c * Np]; kap[c] = Kp[c * Np]; }
+            const int part = s_part[l];
+            if (part >= 0) {   // older half of a merge: kappa averaged with the newer half
+                const real* K2 = a.K + (long long)part * DD * Np + n;
+#pragma unroll
+                for (int c = 0; c < DD; ++c) kap[c] = real(0.5) * (kap[c] + K2[c * Np]);
+            }
+            point_update<D>(X, A, kap, (real)s_age[l], (real)w, p.inv_tau, p.inv_gc, acc);
+#pragma unroll
+            for (int c = 0; c < DD; ++c) Xp[c * Np] = X[c];
+        }
+    }
+    // reduce the slot groups of each node into group 0
+    if (G > 1) {
+        if (gi > 0) {
+#pragma unroll
+            for (int i = 0; i < NS; ++i) s_red[((gi - 1) * NS + i) * NODES + ln] = acc[i];
+        }
+    }
+    __syncthreads();   // also orders every X write of the sweep before the merges below
+    if (gi != 0 || !live) return;
+    if (G > 1) {
+        for (int j = 1; j < G; ++j)
+#pragma unroll
+            for (int i = 0; i < NS; ++i) acc[i] += s_red[((j - 1) * NS + i) * NODES + ln];
+    }
+    // the point created now: age 0, E = 1, weight 1/2, modulus G_inf
+    real kt[DD];
+    if (a.kappa_in) {
+#pragma unroll
+        for (int c = 0; c < DD; ++c) kt[c] = (real)a.kappa_in[(long long)c * g.N + n];
+    } else {
+        kappa_fd<D>(a.u_raw, g, n, kt);
+    }
+    if (D == 2) {
+        acc[0] += real(0.5) * (kt[0] + kt[0]);
+        acc[1] += real(0.5) * (kt[3] + kt[3]);
+        acc[2] += real(0.5) * (kt[1] + kt[2]);
+    } else {
+        acc[0] += real(0.5) * (kt[0] + kt[0]);
+        acc[1] += real(0.5) * (kt[4] + kt[4]);
+        acc[2] += real(0.5) * (kt[8] + kt[8]);
+        acc[3] += real(0.5) * (kt[1] + kt[3]);
+        acc[4] += real(0.5) * (kt[2] + kt[6]);
+        acc[5] += real(0.5) * (kt[5] + kt[7]);
+    }
+#pragma unroll
+    for (int i = 0; i < NS; ++i) {
+        const real s = p.G_inf * acc[i];
+        a.sigma[i * Np + n] = s;
+        if (a.sigma_dbl) a.sigma_dbl[(long long)i * g.N + n] = (double)s;
+    }
+#pragma unroll
+    for (int c = 0; c < DD; ++c) a.kappa[c * Np + n] = kt[c];
+
+    // block merges, coarsest first, so that every ring slot is read before it is overwritten
+    for (int bb = 1; bb < a.B; ++bb) {
+        const BlockStep& b = s_bs[bb];
+        if (!b.evict) continue;
+        int o1 = b.head_prev - (a.C - 1); if (o1 < 0) o1 += a.C;
+        int o2 = b.head_prev - (a.C - 2); if (o2 < 0) o2 += a.C;
+        const long long src1 = (long long)bb * a.C + o1, src2 = (long long)bb * a.C + o2;
+        const long long dst = (long long)(bb - 1) * a.C + s_bs[bb - 1].head_new;
+#pragma unroll
+        for (int c = 0; c < DD; ++c) {
+            a.X[(dst * DD + c) * Np + n] = a.X[(src1 * DD + c) * Np + n];
+            a.K[(dst * DD + c) * Np + n] = real(0.5) * (a.K[(src1 * DD + c) * Np + n] + a.K[(src2 * DD + c) * Np + n]);
+        }
+    }
+    // the new point enters the finest block
+    {
+        const long long dst = (long long)(a.B - 1) * a.C + s_bs[a.B - 1].head_new;
+#pragma unroll
+        for (int c = 0; c < DD; ++c) {
+            a.X[(dst * DD + c) * Np + n] = real(0);
+            a.K[(dst * DD + c) * Np + n] = kt[c];
+        }
+    }
+}
+
+// ------------------------------------------------------------------------------------------------
+// K3: collision with the non-Newtonian forcing and push streaming
+// ------------------------------------------------------------------------------------------------
+template <typename real> struct CollArgs {
+    const real* __restrict__ dn_in;   // [Q][Npad]
+    real* __restrict__ dn_out;        // [Q][Npad]
+    const real* __restrict__ sigma;   // [NS][Npad]
+    real* __restrict__ tr_prev;       // [Npad]
+    real* __restrict__ rho;           // [Npad]
+    real* __restrict__ u;             // [D][Npad]
+    long long* t_dev;                 // advanced by one thread after the step
+};
+
+template <int Q, typename real>
+__global__ void __launch_bounds__(256) k_collide_stream(CollArgs<real> a, Geom g, Phys<real> p) {
+    using L = Lattice<Q>;
+    constexpr int D = L::D;
+    const int n = blockIdx.x * blockDim.x + threadIdx.x;
+    if (n == 0) *a.t_dev += 1;   // no kernel of this step reads t after k_history
+    if (n >= g.N) return;
+    const long long Np = g.Npad;
+    const real cs2 = real(1.0 / 3.0);
+    real dn[Q];
+    real drho_raw = 0, j[3] = {0, 0, 0};
+#pragma unroll
+    for (int q = 0; q < Q; ++q) {
+        dn[q] = a.dn_in[q * Np + n];
+        drho_raw += dn[q];
+        if (L::cx(q)) j[0] += L::cx(q) * dn[q];
+        if (L::cy(q)) j[1] += L::cy(q) * dn[q];
+        if (D == 3 && L::cz(q)) j[2] += L::cz(q) * dn[q];
+    }
+    // stress: traceless part and density source (Sec. III, trace split)
+    real S[3][3];
+    if (D == 2) {
+        S[0][0] = a.sigma[0 * Np + n]; S[1][1] = a.sigma[1 * Np + n];
+        S[0][1] = S[1][0] = a.sigma[2 * Np + n];
+    } else {
+        S[0][0] = a.sigma[0 * Np + n]; S[1][1] = a.sigma[1 * Np + n]; S[2][2] = a.sigma[2 * Np + n];
+        S[0][1] = S[1][0] = a.sigma[3 * Np + n];
+        S[0][2] = S[2][0] = a.sigma[4 * Np + n];
+        S[1][2] = S[2][1] = a.sigma[5 * Np + n];
+    }
+    real tr = 0;
+#pragma unroll
+    for (int c = 0; c < D; ++c) tr += S[c][c];
+    real ddr = 0;
+    if (p.trace_full) ddr = -(tr - a.tr_prev[n]) / (real(D) * cs2);
+    const real drho = drho_raw + real(0.5) * ddr;        // rho - rho0
+    const real rho = p.rho0 + drho;
+    real u[3];
+#pragma unroll
+    for (int c = 0; c < D; ++c) u[c] = (j[c] + real(0.5) * p.f[c]) / rho;
+#pragma unroll
+    for (int c = 0; c < D; ++c) S[c][c] -= tr / real(D);
+    real uu = 0;
+#pragma unroll
+    for (int c = 0; c < D; ++c) uu += u[c] * u[c];
+    const real omega = real(1) / p.tau_lb;
+    const real fpre = real(1) - real(0.5) * omega;
+    const real inv2cs4 = real(4.5);   // 1/(2 cs^4)
+    // X_ab = -ddr u_a u_b + u_b f_a + u_a f_b  (second-order forcing term of Eq. bodyforce)
+    real Xf[3][3];
+#pragma unroll
+    for (int r = 0; r < D; ++r)
+#pragma unroll
+        for (int c = 0; c < D; ++c) Xf[r][c] = -ddr * u[r] * u[c] + u[c] * p.f[r] + u[r] * p.f[c];
+    real trX = 0;
+#pragma unroll
+    for (int c = 0; c < D; ++c) trX += Xf[c][c];
+
+    int x, y, z;
+    node_xyz(g, n, x, y, z);
+#pragma unroll
+    for (int q = 0; q < Q; ++q) {
+        const int cq[3] = {L::cx(q), L::cy(q), L::cz(q)};
+        real cu = 0, cf = 0, cSc = 0, cXc = 0;
+#pragma unroll
+        for (int r = 0; r < D; ++r) {
+            cu += cq[r] * u[r];
+            cf += cq[r] * p.f[r];
+#pragma unroll
+            for (int c = 0; c < D; ++c) {
+                if (cq[r] && cq[c]) {
+                    cSc += cq[r] * cq[c] * S[r][c];
+                    cXc += cq[r] * cq[c] * Xf[r][c];
+                }
+            }
+        }
+        const real wq = (real)L::w(q);
+        // deviation of the equilibrium from w rho0: w (rho - rho0) + w rho (c.u/cs2 + ((c.u)^2 - cs2 u.u)/(2 cs4))
+        const real dneq = wq * (drho + rho * (cu * real(3) + (cu * cu - cs2 * uu) * inv2cs4));
+        // Eq. (bodyforce); (cc - cs2 1):S = cSc (S traceless), (cc - cs2 1):X = cXc - cs2 tr X
+        const real Fq = wq * (-inv2cs4 * omega * cSc +
+                              fpre * (ddr + cf * real(3) + inv2cs4 * (cXc - cs2 * trX)));
+        const real post = dn[q] - omega * (dn[q] - dneq) + Fq;
+        // push with half-way bounce-back
+        int xd = x + cq[0];
+        xd = xd < 0 ? g.nx - 1 : (xd >= g.nx ? 0 : xd);
+        const int yd = y + cq[1];
+        bool wall = yd < 0 || yd >= g.ny;
+        int zd = z + cq[2];
+        if (D == 3) {
+            if (g.wall_z) wall = wall || zd < 0 || zd >= g.nz;
+            else zd = zd < 0 ? g.nz - 1 : (zd >= g.nz ? 0 : zd);
+        }
+        if (wall) a.dn_out[L::opp(q) * Np + n] = post;
+        else a.dn_out[q * Np + (xd + g.nx * (yd + g.ny * zd))] = post;
+    }
+    a.rho[n] = rho;
+#pragma unroll
+    for (int c = 0; c < D; ++c) a.u[c * Np + n] = u[c];
+    a.tr_prev[n] = p.trace_full ? tr : real(0);
+}
+
+// ------------------------------------------------------------------------------------------------
+// Field gather (lbve_fields) and reductions (lbve_mass)
+// ------------------------------------------------------------------------------------------------
+template <typename real>
+__global__ void k_gather(const real* __restrict__ src, long long Npad, int ncomp, int N, double* __restrict__ dst,
+                         int* nonfinite) {
+    const long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    if (i >= (long long)ncomp * N) return;
+    const int c = (int)(i / N), n = (int)(i % N);
+    const double v = (double)src[c * Npad + n];
+    dst[i] = v;
+    if (!isfinite(v)) atomicOr(nonfinite, 1);
+}
+
+template <typename real>
+__global__ void k_n1(const real* __restrict__ sigma, long long Npad, int N, double* __restrict__ dst,
+                     int* nonfinite) {
+    const int n = blockIdx.x * blockDim.x + threadIdx.x;
+    if (n >= N) return;
+    const double v = (double)sigma[n] - (double)sigma[Npad + n];
+    dst[n] = v;
+    if (!isfinite(v)) atomicOr(nonfinite, 1);
+}
+
+template <typename real>
+__global__ void k_sum(const real* __restrict__ src, long long Npad, int ncomp, int N, double scale,
+                      double* __restrict__ out) {
+    double s = 0;
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < (long long)ncomp * N;
+         i += (long long)gridDim.x * blockDim.x) {
+        const int c = (int)(i / N), n = (int)(i % N);
+        s += (double)src[c * Npad + n];
+    }
+    for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+    if ((threadIdx.x & 31) == 0) atomicAdd(out, s * scale);
+}
+
+}  // namespace lbk

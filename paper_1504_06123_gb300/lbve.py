@@ -1,0 +1,286 @@
+"""ctypes binding of the C ABI in ``include/lbve.h`` -- argument marshalling only.
+
+Every step of the method runs in the CUDA library ``_build/liblbve.so``; this module converts Python
+values to the C structures and raises :class:`LbveError` on a non-zero status.  Function names are the
+C names.  Device pointers may be passed as ints or as torch CUDA tensors (their ``data_ptr()``);
+streams as ints, ``torch.cuda.Stream`` objects or ``None`` (the current torch stream when torch is
+initialised on CUDA, else the legacy default stream).
+"""
+from __future__ import annotations
+
+import ctypes as C
+import math
+import os
+import threading
+
+import numpy as np
+
+from . import build as _build
+
+LBVE_OK, LBVE_EINVAL, LBVE_ENOMEM, LBVE_ECUDA, LBVE_ENONFINITE, LBVE_ESTATE, LBVE_ENOSUPPORT = 0, -1, -2, -3, -4, -6, -7
+LBVE_D2Q9, LBVE_D3Q19 = 9, 19
+LBVE_F32, LBVE_F64, LBVE_BF16 = 0, 1, 2
+LBVE_TRACE_FULL, LBVE_TRACE_NONE = 0, 1
+LBVE_FIELD_RHO, LBVE_FIELD_U, LBVE_FIELD_SIGMA, LBVE_FIELD_KAPPA, LBVE_FIELD_N1 = 1, 2, 4, 8, 16
+
+# Every entry point declared in include/lbve.h (checked by the tests against the header).
+EXPORTS = [
+    "lbve_create", "lbve_destroy", "lbve_set_force", "lbve_set_params", "lbve_step", "lbve_get_time",
+    "lbve_fields", "lbve_fields_count", "lbve_history_apply", "lbve_mass", "lbve_schedule",
+    "lbve_memory_bytes", "lbve_strerror", "lbve_last_cuda_error", "lbve_profile", "lbve_profile_read",
+]
+
+
+class lbve_channel_desc(C.Structure):
+    _fields_ = [
+        ("lattice", C.c_int32), ("nx", C.c_int32), ("ny", C.c_int32), ("nz", C.c_int32), ("wall_z", C.c_int32),
+        ("tau_lb", C.c_double), ("rho0", C.c_double), ("G_inf", C.c_double), ("tau", C.c_double),
+        ("gamma_c", C.c_double), ("g", C.c_double * 3), ("hist_C", C.c_int32), ("hist_B", C.c_int32),
+        ("hist_storage", C.c_int32), ("pop_precision", C.c_int32), ("trace_coupling", C.c_int32),
+    ]
+
+
+class LbveError(RuntimeError):
+    def __init__(self, status: int, where: str, lib=None):
+        msg = f"{where}: {lbve_strerror(status) if lib is not None else status} ({status})"
+        if status == LBVE_ECUDA and lib is not None:
+            msg += " -- " + lib.lbve_last_cuda_error().decode()
+        super().__init__(msg)
+        self.status = status
+
+
+_lock = threading.Lock()
+_lib = None
+
+
+def load(path: str | None = None):
+    """Load liblbve.so (building it first if it is missing or stale).  Raises if that fails."""
+    global _lib
+    with _lock:
+        if _lib is not None:
+            return _lib
+        p = path or _build.build()
+        if not os.path.exists(p):
+            raise RuntimeError(f"CUDA library not found at {p}; run paper_1504_06123_gb300.build.build()")
+        lib = C.CDLL(p)
+        vp, dp, i32, i64 = C.c_void_p, C.POINTER(C.c_double), C.c_int32, C.c_int64
+        lib.lbve_create.argtypes = [C.POINTER(lbve_channel_desc), dp, C.POINTER(vp)]
+        lib.lbve_destroy.argtypes = [vp]
+        lib.lbve_destroy.restype = None
+        lib.lbve_set_force.argtypes = [vp, dp]
+        lib.lbve_set_params.argtypes = [vp, C.c_double, C.c_double, C.c_double]
+        lib.lbve_step.argtypes = [vp, i64, vp]
+        lib.lbve_get_time.argtypes = [vp, C.POINTER(i64)]
+        lib.lbve_fields.argtypes = [vp, C.c_uint32, vp, i32, vp]
+        lib.lbve_fields_count.argtypes = [vp, C.c_uint32, C.POINTER(C.c_size_t)]
+        lib.lbve_history_apply.argtypes = [vp, vp, vp, vp]
+        lib.lbve_mass.argtypes = [vp, dp, dp, vp]
+        lib.lbve_schedule.argtypes = [i32, i32, i64, C.POINTER(i64), dp, C.POINTER(i32)]
+        lib.lbve_memory_bytes.argtypes = [vp, C.POINTER(C.c_size_t)]
+        lib.lbve_strerror.argtypes = [C.c_int]
+        lib.lbve_strerror.restype = C.c_char_p
+        lib.lbve_profile.argtypes = [vp, i32]
+        lib.lbve_profile_read.argtypes = [vp, dp, C.POINTER(i64)]
+        lib.lbve_last_cuda_error.argtypes = []
+        lib.lbve_last_cuda_error.restype = C.c_char_p
+        for name in EXPORTS:       # fail loudly if the library lacks an entry point of the header
+            getattr(lib, name)
+        _lib = lib
+        return lib
+
+
+def _check(rc: int, where: str):
+    if rc != LBVE_OK:
+        raise LbveError(rc, where, _lib)
+
+
+def _ptr(x) -> int | None:
+    if x is None:
+        return None
+    if isinstance(x, int):
+        return x
+    if hasattr(x, "data_ptr"):
+        return int(x.data_ptr())
+    raise TypeError(f"expected a device pointer or a tensor, got {type(x)}")
+
+
+def _stream(s) -> int | None:
+    if s is None:
+        try:
+            import torch
+            if torch.cuda.is_available() and torch.cuda.is_initialized():
+                return int(torch.cuda.current_stream().cuda_stream) or None
+        except Exception:
+            pass
+        return None
+    if isinstance(s, int):
+        return s or None
+    return int(s.cuda_stream) or None
+
+
+# ---- C ABI, one function each ------------------------------------------------------------------
+def lbve_strerror(status: int) -> str:
+    return load().lbve_strerror(int(status)).decode()
+
+
+def lbve_create(desc: lbve_channel_desc, rho_init: np.ndarray | None = None) -> int:
+    lib = load()
+    h = C.c_void_p()
+    ri = None
+    if rho_init is not None:
+        ri = np.ascontiguousarray(rho_init, dtype=np.float64).ravel()
+    rc = lib.lbve_create(C.byref(desc), ri.ctypes.data_as(C.POINTER(C.c_double)) if ri is not None else None,
+                         C.byref(h))
+    _check(rc, "lbve_create")
+    return h.value
+
+
+def lbve_destroy(h: int) -> None:
+    load().lbve_destroy(h)
+
+
+def lbve_set_force(h: int, g) -> None:
+    gg = (C.c_double * 3)(*[float(v) for v in g])
+    _check(load().lbve_set_force(h, gg), "lbve_set_force")
+
+
+def lbve_set_params(h: int, G_inf: float, tau: float, gamma_c: float) -> None:
+    _check(load().lbve_set_params(h, G_inf, tau, gamma_c), "lbve_set_params")
+
+
+def lbve_step(h: int, n_steps: int, stream=None) -> None:
+    _check(load().lbve_step(h, int(n_steps), _stream(stream)), "lbve_step")
+
+
+def lbve_get_time(h: int) -> int:
+    t = C.c_int64()
+    _check(load().lbve_get_time(h, C.byref(t)), "lbve_get_time")
+    return t.value
+
+
+def lbve_fields_count(h: int, mask: int) -> int:
+    n = C.c_size_t()
+    _check(load().lbve_fields_count(h, mask, C.byref(n)), "lbve_fields_count")
+    return n.value
+
+
+def lbve_fields(h: int, mask: int, dst=None, stream=None):
+    """Fields of the last step.  dst None: returns a new numpy array (host copy, synchronising);
+    dst a device tensor / pointer: asynchronous device write, returns dst."""
+    lib = load()
+    if dst is None:
+        out = np.empty(lbve_fields_count(h, mask), dtype=np.float64)
+        rc = lib.lbve_fields(h, mask, out.ctypes.data, 0, _stream(stream))
+        _check(rc, "lbve_fields")
+        return out
+    rc = lib.lbve_fields(h, mask, _ptr(dst), 1, _stream(stream))
+    _check(rc, "lbve_fields")
+    return dst
+
+
+def lbve_history_apply(h: int, kappa_dev, sigma_dev, stream=None) -> None:
+    _check(load().lbve_history_apply(h, _ptr(kappa_dev), _ptr(sigma_dev), _stream(stream)), "lbve_history_apply")
+
+
+def lbve_mass(h: int, stream=None):
+    a, b = C.c_double(), C.c_double()
+    _check(load().lbve_mass(h, C.byref(a), C.byref(b), _stream(stream)), "lbve_mass")
+    return a.value, b.value
+
+
+def lbve_schedule(C_: int, B: int, t: int):
+    """Host-only: (t' newest first, trapezoidal weights) of the retained history points after step t."""
+    tp = np.zeros(C_ * B, dtype=np.int64)
+    w = np.zeros(C_ * B)
+    n = C.c_int32()
+    rc = load().lbve_schedule(C_, B, t, tp.ctypes.data_as(C.POINTER(C.c_int64)),
+                              w.ctypes.data_as(C.POINTER(C.c_double)), C.byref(n))
+    _check(rc, "lbve_schedule")
+    return tp[: n.value].copy(), w[: n.value].copy()
+
+
+def lbve_memory_bytes(h: int) -> int:
+    n = C.c_size_t()
+    _check(load().lbve_memory_bytes(h, C.byref(n)), "lbve_memory_bytes")
+    return n.value
+
+
+def lbve_profile(h: int, enable: bool) -> None:
+    _check(load().lbve_profile(h, int(bool(enable))), "lbve_profile")
+
+
+def lbve_profile_read(h: int):
+    """(ms[3], launches[3]) summed over the recorded lbve_step launches: moments, history, collide-stream."""
+    ms = (C.c_double * 3)()
+    n = (C.c_int64 * 3)()
+    _check(load().lbve_profile_read(h, ms, n), "lbve_profile_read")
+    return list(ms), list(n)
+
+
+# ---- convenience wrapper ---------------------------------------------------------------------------
+def make_desc(lattice=LBVE_D2Q9, nx=4, ny=32, nz=1, *, tau_lb=0.9, rho0=1.0, G_inf=0.01, tau=200.0,
+              gamma_c=0.1, g=(0.0, 0.0, 0.0), C=128, B=1, precision=LBVE_F32, hist_storage=None,
+              trace_coupling=LBVE_TRACE_FULL, wall_z=1) -> lbve_channel_desc:
+    d = lbve_channel_desc()
+    d.lattice, d.nx, d.ny, d.nz, d.wall_z = lattice, nx, ny, nz, wall_z
+    d.tau_lb, d.rho0, d.G_inf, d.tau = tau_lb, rho0, G_inf, tau
+    d.gamma_c = math.inf if gamma_c is None else gamma_c
+    d.g[0], d.g[1], d.g[2] = [float(v) for v in g]
+    d.hist_C, d.hist_B = C, B
+    d.pop_precision = precision
+    d.hist_storage = precision if hist_storage is None else hist_storage
+    d.trace_coupling = trace_coupling
+    return d
+
+
+class Channel:
+    """Owns one lbve handle.  fields() returns host arrays in the oracle's [node][component] layout."""
+
+    def __init__(self, desc: lbve_channel_desc, rho_init=None):
+        self.desc = desc
+        self.d = 2 if desc.lattice == LBVE_D2Q9 else 3
+        self.N = desc.nx * desc.ny * desc.nz
+        self.h = lbve_create(desc, rho_init)
+
+    def close(self):
+        if getattr(self, "h", None):
+            lbve_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    @property
+    def t(self) -> int:
+        return lbve_get_time(self.h)
+
+    def step(self, n: int = 1, stream=None):
+        lbve_step(self.h, n, stream)
+
+    def set_force(self, g):
+        lbve_set_force(self.h, g)
+
+    def set_params(self, G_inf, tau, gamma_c):
+        lbve_set_params(self.h, G_inf, tau, gamma_c)
+
+    def fields(self, stream=None) -> dict:
+        d, N = self.d, self.N
+        ns = 3 if d == 2 else 6
+        mask = LBVE_FIELD_RHO | LBVE_FIELD_U | LBVE_FIELD_SIGMA | LBVE_FIELD_KAPPA | LBVE_FIELD_N1
+        a = lbve_fields(self.h, mask, None, stream)
+        o = 0
+        rho = a[o:o + N]; o += N
+        u = a[o:o + d * N].reshape(d, N).T.copy(); o += d * N
+        sig = a[o:o + ns * N].reshape(ns, N).T.copy(); o += ns * N
+        kap = a[o:o + d * d * N].reshape(d * d, N).T.reshape(N, d, d).copy(); o += d * d * N
+        n1 = a[o:o + N]
+        return {"rho": rho.copy(), "u": u, "sigma": sig, "kappa": kap, "n1": n1.copy()}
+
+    def mass(self, stream=None):
+        return lbve_mass(self.h, stream)
+
+    def memory_bytes(self) -> int:
+        return lbve_memory_bytes(self.h)

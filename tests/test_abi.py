@@ -1,0 +1,85 @@
+"""The C-ABI library on the CPU: it builds, loads, exports every entry point of include/lbve.h, validates
+arguments before touching a GPU, and its history grid (the kernel's per-slot roles, run on the host) is
+bit-identical to the oracle's merge simulation (Sec. III quasi-logarithmic layout)."""
+import math
+import os
+import re
+
+import numpy as np
+import pytest
+
+import oracle
+from paper_1504_06123_gb300 import lbve as L
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def header_functions():
+    text = open(os.path.join(ROOT, "include", "lbve.h")).read()
+    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+    return sorted(set(re.findall(r"\b(lbve_[a-z_0-9]+)\s*\(", text)))
+
+
+def test_library_exports_every_header_function():
+    lib = L.load()
+    names = header_functions()
+    assert len(names) >= 10
+    for n in names:
+        assert hasattr(lib, n), n
+    assert sorted(L.EXPORTS) == names
+
+
+def test_strerror():
+    assert L.lbve_strerror(0) == "ok"
+    assert "invalid" in L.lbve_strerror(L.LBVE_EINVAL)
+    assert L.lbve_strerror(12345) == "unknown status"
+
+
+@pytest.mark.parametrize("bad", [
+    dict(tau_lb=0.5), dict(ny=1), dict(nx=0), dict(C=3), dict(B=0), dict(B=17), dict(tau=0.0),
+    dict(G_inf=-1.0), dict(gamma_c=0.0), dict(G_inf=0.3), dict(nz=2), dict(C=4096, B=2),
+])
+def test_create_rejects_bad_descriptions(bad):
+    kw = dict(lattice=L.LBVE_D2Q9, nx=4, ny=8, tau_lb=0.9, G_inf=0.01, tau=100.0, gamma_c=0.1, C=8, B=2)
+    kw.update(bad)
+    d = L.make_desc(**kw)
+    with pytest.raises(L.LbveError) as e:
+        L.lbve_create(d)
+    assert e.value.status == L.LBVE_EINVAL
+
+
+def test_create_rejects_nonfinite_density():
+    d = L.make_desc(nx=2, ny=4, C=8, B=1)
+    rho = np.ones(8)
+    rho[3] = np.nan
+    with pytest.raises(L.LbveError) as e:
+        L.lbve_create(d, rho)
+    assert e.value.status == L.LBVE_EINVAL
+
+
+@pytest.mark.parametrize("C,B", [(4, 1), (4, 2), (4, 3), (6, 4), (8, 5), (128, 8), (256, 1), (64, 4), (5, 3),
+                                 (128, 4), (7, 16)])
+def test_schedule_bit_exact_vs_oracle(C, B):
+    ts = list(range(0, 80)) + [127, 128, 129, 255, 1023, 1024, 4097, 32767, 32768, 100000]
+    for t in ts:
+        tp, w = L.lbve_schedule(C, B, t)
+        otp, ow = oracle.schedule(C, B, t)
+        assert np.array_equal(tp, otp), (C, B, t)
+        assert np.array_equal(w, ow), (C, B, t)
+
+
+def test_schedule_rejects_bad_args():
+    with pytest.raises(L.LbveError):
+        L.lbve_schedule(3, 2, 0)
+    with pytest.raises(L.LbveError):
+        L.lbve_schedule(8, 2, -1)
+
+
+def test_no_cpu_fallback_without_gpu():
+    torch = pytest.importorskip("torch")
+    if torch.cuda.is_available():
+        pytest.skip("a GPU is present")
+    d = L.make_desc(nx=2, ny=4, C=8, B=1)
+    with pytest.raises(L.LbveError) as e:
+        L.lbve_create(d)
+    assert e.value.status in (L.LBVE_ECUDA, L.LBVE_ENOMEM)

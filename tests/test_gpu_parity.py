@@ -1,0 +1,198 @@
+"""GPU parity: the CUDA path (through the C ABI) against the FP64 oracle, element by element.
+
+Tolerances (normwise max-relative per field component, max|x - x_ref| / max|x_ref|):
+  FP32 path   <= 1e-5  (the stated bar for the plain FP32 form)
+  FP64 path   <= 1e-11 (rounding of 1e4 steps of double arithmetic on populations of order 0.1)
+Integer/structural results (x-invariance, history grid) are compared exactly.
+"""
+import math
+
+import numpy as np
+import pytest
+
+import oracle
+from paper_1504_06123_gb300 import configs, inputs
+from paper_1504_06123_gb300 import lbve as L
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+TOL = {L.LBVE_F32: 1e-5, L.LBVE_F64: 1e-11}
+
+
+def rel_err(x, ref):
+    x = np.asarray(x, dtype=np.float64).reshape(len(ref), -1)
+    ref = np.asarray(ref, dtype=np.float64).reshape(len(ref), -1)
+    out = []
+    for c in range(ref.shape[1]):
+        den = np.max(np.abs(ref[:, c]))
+        num = np.max(np.abs(x[:, c] - ref[:, c]))
+        out.append(0.0 if den == 0 and num == 0 else (num / den if den > 0 else math.inf))
+    return max(out)
+
+
+def compare(gpu: dict, orc: dict, tol: float, what: str):
+    for key in ("u", "sigma", "kappa", "n1"):
+        e = rel_err(gpu[key], orc[key])
+        assert e <= tol, f"{what}: {key} normwise error {e:.3e} > {tol:.1e}"
+    drho = rel_err(gpu["rho"] - 1.0, orc["rho"] - 1.0) if np.max(np.abs(orc["rho"] - 1.0)) > 1e-9 else 0.0
+    assert drho <= max(tol, 1e-4 if tol > 1e-8 else tol), f"{what}: rho error {drho:.3e}"
+
+
+# ---------------------------------------------------------------------------------------------
+# The history integral alone (Sec. III steps on a prescribed gradient): lbve_history_apply
+# ---------------------------------------------------------------------------------------------
+@pytest.mark.parametrize("prec", [L.LBVE_F32, L.LBVE_F64])
+@pytest.mark.parametrize("lattice,nx,ny,nz,C,B", [
+    (L.LBVE_D2Q9, 7, 115, 1, 16, 4),      # 805 nodes: several tiles + ragged tail
+    (L.LBVE_D2Q9, 1, 9, 1, 8, 1),         # uniform ring, tiny
+    (L.LBVE_D2Q9, 33, 64, 1, 5, 3),       # odd C
+    (L.LBVE_D3Q19, 3, 7, 11, 8, 3),       # 231 nodes, 3x3 tensors
+])
+def test_history_apply_vs_oracle(prec, lattice, nx, ny, nz, C, B):
+    d = 2 if lattice == L.LBVE_D2Q9 else 3
+    N = nx * ny * nz
+    T = 150
+    G, tau, gc = 0.02, 40.0, 0.1
+    kseq = inputs.kappa_sequence(T, N, d, 2e-3, seed=11, shear=1e-3)
+    ref = oracle.history_run(kseq, C, B, G, tau, gc)
+    ch = L.Channel(L.make_desc(lattice, nx, ny, nz, G_inf=G, tau=tau, gamma_c=gc, C=C, B=B, precision=prec))
+    ns = 3 if d == 2 else 6
+    kap_dev = torch.empty((d * d, N), dtype=torch.float64, device="cuda")
+    sig_dev = torch.empty((ns, N), dtype=torch.float64, device="cuda")
+    tol = TOL[prec]
+    for t in range(T):
+        kap_dev.copy_(torch.from_numpy(kseq[t].reshape(N, d * d).T.copy()))
+        L.lbve_history_apply(ch.h, kap_dev, sig_dev)
+        if t % 7 == 0 or t == T - 1:
+            got = sig_dev.cpu().numpy().T
+            e = rel_err(got, ref[t])
+            assert e <= tol, f"step {t}: sigma error {e:.3e}"
+    assert ch.t == T
+    ch.close()
+
+
+# ---------------------------------------------------------------------------------------------
+# Full hybrid step: startup and cessation in the small channel (plain FP32 and FP64)
+# ---------------------------------------------------------------------------------------------
+@pytest.mark.parametrize("prec", [L.LBVE_F32, L.LBVE_F64])
+@pytest.mark.parametrize("C,B", [(256, 1), (64, 4)])
+def test_small_channel_startup_cessation(prec, C, B):
+    w = configs.plain_channel_small()
+    orc = oracle.Channel(oracle.D2Q9, w.nx, w.ny, tau_lb=w.tau_lb, G_inf=w.G_inf, tau=w.tau, gamma_c=w.gamma_c,
+                         g=(w.g, 0, 0), C=C, B=B)
+    ch = L.Channel(w.desc(C=C, B=B, precision=prec))
+    checkpoints = [1, 2, 10, 100, 700, w.steps, w.steps + 1, w.steps + 300, w.steps + w.off_steps]
+    t = 0
+    for cp in checkpoints:
+        ch.step(cp - t)
+        orc.step(cp - t)
+        t = cp
+        compare(ch.fields(), orc.fields(), TOL[prec], f"C={C} B={B} step {t}")
+        if t == w.steps:          # cessation: the driving force is switched off
+            ch.set_force((0, 0, 0))
+            orc.set_force((0, 0, 0))
+    ch.close()
+
+
+# ---------------------------------------------------------------------------------------------
+# Edge cases: ragged and degenerate sizes, both trace couplings, UCM and Newtonian limits, density
+# noise, the D3Q19 duct and a periodic-z 3D box
+# ---------------------------------------------------------------------------------------------
+@pytest.mark.parametrize("case", [
+    dict(lattice=L.LBVE_D2Q9, nx=1, ny=2, C=4, B=2, G_inf=0.01, tau=20.0, gamma_c=0.1, g=1e-5),
+    dict(lattice=L.LBVE_D2Q9, nx=3, ny=7, C=6, B=3, G_inf=0.02, tau=15.0, gamma_c=math.inf, g=2e-5),
+    dict(lattice=L.LBVE_D2Q9, nx=5, ny=9, C=8, B=2, G_inf=0.0, tau=15.0, gamma_c=0.1, g=2e-5),
+    dict(lattice=L.LBVE_D2Q9, nx=6, ny=10, C=8, B=2, G_inf=0.01, tau=30.0, gamma_c=0.2, g=1e-5,
+         trace_coupling=L.LBVE_TRACE_NONE),
+    dict(lattice=L.LBVE_D2Q9, nx=9, ny=13, C=8, B=3, G_inf=0.01, tau=30.0, gamma_c=0.2, g=1e-5, noise=1e-4),
+    dict(lattice=L.LBVE_D3Q19, nx=3, ny=6, nz=5, C=8, B=2, G_inf=0.01, tau=25.0, gamma_c=0.1, g=2e-5),
+    dict(lattice=L.LBVE_D3Q19, nx=2, ny=5, nz=4, C=4, B=3, G_inf=0.01, tau=25.0, gamma_c=0.1, g=2e-5,
+         wall_z=0, noise=1e-4),
+])
+@pytest.mark.parametrize("prec", [L.LBVE_F32, L.LBVE_F64])
+def test_edge_cases_vs_oracle(case, prec):
+    c = dict(case)
+    noise = c.pop("noise", 0.0)
+    lattice = c.pop("lattice")
+    nz = c.pop("nz", 1)
+    wall_z = c.pop("wall_z", 1)
+    tc = c.pop("trace_coupling", L.LBVE_TRACE_FULL)
+    g = c.pop("g")
+    N = c["nx"] * c["ny"] * nz
+    rho = inputs.initial_density(N, noise, seed=7)
+    orc = oracle.Channel(lattice, c["nx"], c["ny"], nz, tau_lb=0.9, G_inf=c["G_inf"], tau=c["tau"],
+                         gamma_c=c["gamma_c"], g=(g, 0, 0), C=c["C"], B=c["B"], wall_z=bool(wall_z),
+                         trace_full=(tc == L.LBVE_TRACE_FULL), rho_init=rho)
+    desc = L.make_desc(lattice, c["nx"], c["ny"], nz, tau_lb=0.9, G_inf=c["G_inf"], tau=c["tau"],
+                       gamma_c=c["gamma_c"], g=(g, 0, 0), C=c["C"], B=c["B"], precision=prec,
+                       trace_coupling=tc, wall_z=wall_z)
+    ch = L.Channel(desc, rho)
+    for n in (1, 5, 60, 200):
+        ch.step(n)
+        orc.step(n)
+        compare(ch.fields(), orc.fields(), TOL[prec], f"{case} t={ch.t}")
+    ch.close()
+
+
+def test_zero_steps_and_initial_fields():
+    ch = L.Channel(L.make_desc(nx=3, ny=5, C=8, B=2))
+    ch.step(0)
+    f = ch.fields()
+    assert ch.t == 0
+    assert np.all(f["rho"] == 1.0) and np.all(f["u"] == 0) and np.all(f["sigma"] == 0)
+    ch.close()
+
+
+# ---------------------------------------------------------------------------------------------
+# Invariants on the GPU: x-invariance (bitwise), mass bookkeeping of the density source
+# ---------------------------------------------------------------------------------------------
+def test_translation_invariance_bitwise():
+    ch = L.Channel(L.make_desc(nx=37, ny=24, G_inf=0.01, tau=50.0, gamma_c=0.1, g=(1e-5, 0, 0), C=16, B=3))
+    ch.step(150)
+    f = ch.fields()
+    u = f["u"].reshape(24, 37, 2)
+    s = f["sigma"].reshape(24, 37, 3)
+    for x in range(1, 37):
+        assert np.array_equal(u[:, x], u[:, 0])
+        assert np.array_equal(s[:, x], s[:, 0])
+    ch.close()
+
+
+@pytest.mark.parametrize("prec,tol", [(L.LBVE_F64, 1e-13), (L.LBVE_F32, 2e-6)])
+def test_mass_invariant(prec, tol):
+    rho = inputs.initial_density(8 * 12, 1e-3, seed=3)
+    ch = L.Channel(L.make_desc(nx=8, ny=12, G_inf=0.01, tau=30.0, gamma_c=0.1, g=(1e-4, 0, 0), C=8, B=3,
+                               precision=prec), rho)
+    ch.step(1)
+    sn, sd = ch.mass()
+    m0 = sn - sd
+    for _ in range(10):
+        ch.step(17)
+        sn, sd = ch.mass()
+        assert abs((sn - sd) - m0) <= tol * m0
+    ch.close()
+
+
+# ---------------------------------------------------------------------------------------------
+# Full size, in the launch configuration the benchmark times: the 1024 x 512 channel with L = 1024
+# (17 GB of history).  Without density noise every column must equal the oracle's single column.
+# ---------------------------------------------------------------------------------------------
+def test_large_channel_columns_vs_oracle():
+    w = configs.plain_channel_large()
+    steps = 40
+    ch = L.Channel(w.desc())
+    orc = oracle.Channel(oracle.D2Q9, 1, w.ny, tau_lb=w.tau_lb, G_inf=w.G_inf, tau=w.tau, gamma_c=w.gamma_c,
+                         g=(w.g, 0, 0), C=w.C, B=w.B)
+    ch.step(steps)
+    orc.step(steps)
+    f = ch.fields()
+    o = orc.fields()
+    for key in ("u", "sigma", "kappa"):
+        g = f[key].reshape(w.ny, w.nx, -1)
+        ref = o[key].reshape(w.ny, -1)
+        err = max(rel_err(g[:, x], ref) for x in range(0, w.nx, 97))
+        assert err <= TOL[L.LBVE_F32], f"{key}: {err:.3e}"
+        # every column bitwise identical to the first (no noise: the flow is x-invariant)
+        assert np.array_equal(g, np.broadcast_to(g[:, :1], g.shape))
+    ch.close()

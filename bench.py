@@ -45,6 +45,8 @@ def parse():
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--nx", type=int, default=None,
+                    help="narrower channel (same rows, same history) for profiler captures; not a bench line")
     return ap.parse_args()
 
 
@@ -209,6 +211,8 @@ def run_ours(args, rank, world, local_rank):
         return float(t.item())
 
     w = configs.plain_channel_large()
+    if args.nx:
+        w.nx = args.nx
     stream = torch.cuda.current_stream()
     ch = L.Channel(w.desc(), w.rho_init())
     K, W = args.steps, args.warmup
@@ -273,7 +277,8 @@ def run_ours(args, rank, world, local_rank):
             "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": K, "warmup": W,
             "ms_per_step": ms_max / K, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
             "dtype": "f32", "data": "synthetic",
-            "config": {"workload": "channel_1024x512_L1024", "lattice": "D2Q9", "nodes": w.N, "history_points": w.L,
+            "config": {"workload": f"channel_{w.nx}x{w.ny}_L{w.L}", "lattice": "D2Q9", "nodes": w.N, "history_points": w.L,
+                       "precision": "history (E-1, kappa) f32 storage and arithmetic; populations f64",
                        "blocks_B": w.B, "block_C": w.C, "tau_lb": w.tau_lb, "G_inf": w.G_inf, "tau": w.tau,
                        "gamma_c": w.gamma_c, "g": w.g, "parallelism": f"replicas{world}",
                        "l2": "no flush: history state 17.2 GB >> 129 MB L2"},

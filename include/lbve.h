@@ -65,8 +65,10 @@ typedef struct {
     double  g[3];             /* body force per unit mass; force density f = rho0 g (Sec. IV driving) */
     int32_t hist_C;           /* points per history block C (Sec. III; the paper uses 128), >= 4 */
     int32_t hist_B;           /* number of blocks B, 1..16; B*C points span about C (2^B - 1) steps */
-    int32_t hist_storage;     /* LBVE_F32 | LBVE_F64 (| LBVE_BF16 where supported) */
-    int32_t pop_precision;    /* LBVE_F32 | LBVE_F64 (must equal hist_storage for F32/F64) */
+    int32_t hist_storage;     /* LBVE_F32 | LBVE_F64: storage and arithmetic of the history (| LBVE_BF16
+                                 where supported) */
+    int32_t pop_precision;    /* LBVE_F32 | LBVE_F64: storage and collision arithmetic of the populations
+                                 (independent of hist_storage; node fields are always double) */
     int32_t trace_coupling;   /* LBVE_TRACE_FULL | LBVE_TRACE_NONE */
 } lbve_channel_desc;
 

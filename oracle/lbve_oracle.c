@@ -14,6 +14,9 @@
  * algorithms.)
  *
  * Conventions
+ *   Populations are kept as deviations dn_i = n_i - w_i rho0 from the rest state.  This is an exact
+ *   re-parametrisation of the collide-stream rule (both are linear in n), chosen so that FP64 resolves
+ *   velocities of 1e-6 to 1e-16 relative instead of to the ~1e-10 left by rounding populations of 0.4.
  *   kappa[a][b] = d v_a / d x_b  (kappa = (grad v)^T, Sec. I), stored row-major, d*d entries.
  *   sigma components: 2D xx, yy, xy; 3D xx, yy, zz, xy, xz, yz.
  *   Node index: x fastest, then y, then z.  Node j of a walled axis sits at j, walls at -1/2 and
@@ -362,7 +365,7 @@ typedef struct {
     int c[ORC_MAXQ][3];
     double w[ORC_MAXQ];
     int opp[ORC_MAXQ];
-    double* n;               /* [N][Q] populations after streaming, time t */
+    double* n;               /* [N][Q] population deviations n - w rho0 after streaming, time t */
     double* n_next;
     double* rho_raw;         /* [N] */
     double* j;               /* [N][3] sum c n + f/2 */
@@ -452,7 +455,7 @@ orc_channel* orc_create(int lattice, int nx, int ny, int nz, int wall_z, double 
     ch->wts = (double*)malloc(sizeof(double) * (size_t)B * C);
     for (int64_t k = 0; k < N; ++k) {
         const double r = rho_init ? rho_init[k] : rho0;
-        for (int i = 0; i < Q; ++i) ch->n[k * Q + i] = ch->w[i] * r;
+        for (int i = 0; i < Q; ++i) ch->n[k * Q + i] = ch->w[i] * (r - rho0);
         ch->rho[k] = r;
     }
     return ch;
@@ -530,17 +533,18 @@ static void compute_kappa(const orc_channel* ch, const double* u, double* kappa)
             }
 }
 
-/* Equilibrium (second order in u), Sec. III: w_i rho (1 + c.u/cs2 + (c_a c_b - cs2 delta_ab) u_a u_b/(2 cs2^2)) */
-static double n_eq(const orc_channel* ch, int i, double rho, const double* u) {
+/* Equilibrium (second order in u), Sec. III: w_i rho (1 + c.u/cs2 + (c_a c_b - cs2 delta_ab) u_a u_b/(2 cs2^2)),
+ * returned as the deviation from w_i rho0 (drho = rho - rho0), written so that no O(1) terms cancel. */
+static double n_eq_dev(const orc_channel* ch, int i, double drho, double rho, const double* u) {
     const double cs2 = 1.0 / 3.0;
     double cu = 0.0, uu = 0.0;
     for (int a = 0; a < ch->d; ++a) { cu += ch->c[i][a] * u[a]; uu += u[a] * u[a]; }
-    return ch->w[i] * rho * (1.0 + cu / cs2 + (cu * cu - cs2 * uu) / (2.0 * cs2 * cs2));
+    return ch->w[i] * (drho + rho * (cu / cs2 + (cu * cu - cs2 * uu) / (2.0 * cs2 * cs2)));
 }
 
 /*
- * Collision of one node (Sec. III): populations n (time t, after streaming), sigma_struc(t) (nsig
- * packed), tr sigma(t-1).  Trace split, density source, fields of Eq. (hydrofields), BGK relaxation to
+ * Collision of one node (Sec. III): population deviations n - w rho0 (time t, after streaming),
+ * sigma_struc(t) (nsig packed), tr sigma(t-1).  Trace split, density source, fields of Eq. (hydrofields), BGK relaxation to
  * the second-order equilibrium and the forcing term of Eq. (bodyforce).  Writes post[Q], the
  * hydrodynamic rho and u, and tr sigma(t).
  */
@@ -549,9 +553,9 @@ static void collide_node(const orc_channel* ch, const double* n, const double* s
     const int d = ch->d, Q = ch->Q;
     const double cs2 = 1.0 / 3.0;
     const double f[3] = {ch->rho0 * ch->g[0], ch->rho0 * ch->g[1], ch->rho0 * ch->g[2]};
-    double rho_raw = 0.0, j[3] = {0, 0, 0};
+    double drho_raw = 0.0, j[3] = {0, 0, 0};
     for (int i = 0; i < Q; ++i) {
-        rho_raw += n[i];
+        drho_raw += n[i];
         for (int a = 0; a < 3; ++a) j[a] += ch->c[i][a] * n[i];
     }
     for (int a = 0; a < 3; ++a) j[a] += 0.5 * f[a];
@@ -566,14 +570,15 @@ static void collide_node(const orc_channel* ch, const double* n, const double* s
     for (int a = 0; a < d; ++a) tr += S[a][a];
     double dt_drho = 0.0;
     if (ch->trace_full) dt_drho = -(tr - tr_prev) / ((double)d * cs2);
-    const double rho = rho_raw + 0.5 * dt_drho;
+    const double drho = drho_raw + 0.5 * dt_drho;     /* rho - rho0 */
+    const double rho = ch->rho0 + drho;
     double u[3] = {0, 0, 0};
     for (int a = 0; a < d; ++a) u[a] = j[a] / rho;
     double Sb[3][3];   /* traceless part */
     for (int a = 0; a < d; ++a)
         for (int b = 0; b < d; ++b) Sb[a][b] = S[a][b] - ((a == b) ? tr / d : 0.0);
     for (int i = 0; i < Q; ++i) {
-        const double neq = n_eq(ch, i, rho, u);
+        const double neq = n_eq_dev(ch, i, drho, rho, u);
         /* Eq. (bodyforce) */
         double stress = 0.0, guo2 = 0.0, cf = 0.0;
         for (int a = 0; a < d; ++a) {
@@ -600,14 +605,16 @@ static void channel_step(orc_channel* ch) {
     const int64_t N = nodes_of(ch);
     const double f[3] = {ch->rho0 * ch->g[0], ch->rho0 * ch->g[1], ch->rho0 * ch->g[2]};
 
-    /* 1. raw moments: rho_raw = sum n, j = sum c n + f/2, u_raw = j / rho_raw */
+    /* 1. raw moments: rho_raw = sum n, j = sum c n + f/2, u_raw = j / rho_raw
+     *    (sum w rho0 = rho0 and sum c w rho0 = 0 for the stored deviations) */
     for (int64_t k = 0; k < N; ++k) {
-        double r = 0.0, jj[3] = {0, 0, 0};
+        double dr = 0.0, jj[3] = {0, 0, 0};
         for (int i = 0; i < Q; ++i) {
             const double ni = ch->n[k * Q + i];
-            r += ni;
+            dr += ni;
             for (int a = 0; a < 3; ++a) jj[a] += ch->c[i][a] * ni;
         }
+        const double r = ch->rho0 + dr;
         ch->rho_raw[k] = r;
         for (int a = 0; a < 3; ++a) {
             ch->j[k * 3 + a] = jj[a] + 0.5 * f[a];
@@ -673,7 +680,9 @@ void orc_fields(const orc_channel* ch, double* rho, double* u, double* sigma, do
 
 /* Populations [N][Q] after the last streaming (time t). */
 void orc_populations(const orc_channel* ch, double* out) {
-    memcpy(out, ch->n, sizeof(double) * (size_t)nodes_of(ch) * ch->Q);
+    const int64_t N = nodes_of(ch);
+    for (int64_t k = 0; k < N; ++k)
+        for (int i = 0; i < ch->Q; ++i) out[k * ch->Q + i] = ch->w[i] * ch->rho0 + ch->n[k * ch->Q + i];
 }
 
 /*
@@ -685,7 +694,7 @@ void orc_mass(const orc_channel* ch, double* sum_n, double* sum_drho_prev) {
     double s = 0.0, r = 0.0;
     for (int64_t k = 0; k < N * ch->Q; ++k) s += ch->n[k];
     for (int64_t k = 0; k < N; ++k) r += -ch->tr_prev[k] / ((double)ch->d / 3.0);
-    *sum_n = s;
+    *sum_n = s + ch->rho0 * (double)N;   /* sum of w rho0 over the lattice is rho0 per node */
     *sum_drho_prev = r;
 }
 
@@ -703,9 +712,12 @@ void orc_kappa_of(const orc_channel* ch, const double* u, double* kappa_out) {
 /* exp of a d x d matrix (test access). */
 void orc_expm(int d, const double* K, double* out) { expm_d(d, K, out); }
 
-/* Collision of one node with the channel's parameters (test access to Eq. (bodyforce)). */
+/* Collision of one node with the channel's parameters (test access to Eq. (bodyforce)): full
+ * populations n in, full post-collision populations out. */
 void orc_collide(const orc_channel* ch, const double* n, const double* sigma, double tr_prev, double* post,
                  double* rho, double* u) {
-    double tr;
-    collide_node(ch, n, sigma, tr_prev, post, rho, u, &tr);
+    double tr, dn[ORC_MAXQ];
+    for (int i = 0; i < ch->Q; ++i) dn[i] = n[i] - ch->w[i] * ch->rho0;
+    collide_node(ch, dn, sigma, tr_prev, post, rho, u, &tr);
+    for (int i = 0; i < ch->Q; ++i) post[i] += ch->w[i] * ch->rho0;
 }

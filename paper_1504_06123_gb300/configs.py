@@ -52,8 +52,10 @@ class Workload:
     off_steps: int = 0                  # cessation steps with g = 0 after `steps`
     noise: float = 0.0
     seed: int = 0
-    precision: int = L.LBVE_F32
-    hist_storage: int | None = None
+    # plain FP32 form: the history (nearly all of the traffic) in FP32; the O(N) populations in FP64,
+    # because FP32 populations alone leave ~1e-5 relative error in decaying flows (cessation)
+    precision: int = L.LBVE_F64
+    hist_storage: int | None = L.LBVE_F32
     extra: dict = field(default_factory=dict)
 
     @property

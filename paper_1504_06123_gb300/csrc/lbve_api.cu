@@ -39,8 +39,9 @@ struct lbve {
     lbve_channel_desc d;
     int D, Q, NS, N, L;
     long long Npad;
-    int dbl;                   // 1: populations and history in double
-    size_t esz;                // element size
+    int pop_dbl;               // 1: populations stored in double
+    int hist_dbl;              // 1: history stored (and advanced) in double
+    size_t pesz, hesz;         // element sizes of populations and history
     void* pops[2] = {nullptr, nullptr};
     int cur = 0;
     void* u_raw = nullptr;
@@ -112,15 +113,14 @@ Geom geom_of(const lbve* h) {
     return g;
 }
 
-template <typename real>
-Phys<real> phys_of(const lbve* h) {
-    Phys<real> p;
-    p.rho0 = (real)h->d.rho0;
-    p.tau_lb = (real)h->d.tau_lb;
-    for (int a = 0; a < 3; ++a) p.f[a] = (real)(h->d.rho0 * h->d.g[a]);
-    p.G_inf = (real)h->d.G_inf;
-    p.inv_tau = (real)(1.0 / h->d.tau);
-    p.inv_gc = std::isinf(h->d.gamma_c) ? (real)0 : (real)(1.0 / h->d.gamma_c);
+Phys phys_of(const lbve* h) {
+    Phys p;
+    p.rho0 = h->d.rho0;
+    p.tau_lb = h->d.tau_lb;
+    for (int a = 0; a < 3; ++a) p.f[a] = h->d.rho0 * h->d.g[a];
+    p.G_inf = h->d.G_inf;
+    p.inv_tau = 1.0 / h->d.tau;
+    p.inv_gc = std::isinf(h->d.gamma_c) ? 0.0 : 1.0 / h->d.gamma_c;
     p.trace_full = h->d.trace_coupling == LBVE_TRACE_FULL;
     return p;
 }
@@ -146,7 +146,7 @@ int check_desc(const lbve_channel_desc* d) {
     if (d->pop_precision != LBVE_F32 && d->pop_precision != LBVE_F64) return LBVE_EINVAL;
     if (d->hist_storage != LBVE_F32 && d->hist_storage != LBVE_F64 && d->hist_storage != LBVE_BF16)
         return LBVE_EINVAL;
-    if (d->hist_storage != d->pop_precision) return LBVE_ENOSUPPORT;
+    if (d->hist_storage == LBVE_BF16) return LBVE_ENOSUPPORT;
     return LBVE_OK;
 }
 
@@ -162,7 +162,7 @@ int pick_groups(int N) {
 template <int D, typename real, int G>
 int launch_history_g(lbve* h, const HistArgs<real>& a, cudaStream_t s) {
     const Geom g = geom_of(h);
-    const Phys<real> p = phys_of<real>(h);
+    const Phys p = phys_of(h);
     constexpr int NODES = 256 / G;
     const size_t smem = history_smem_bytes<D, real, G>(h->L);
     if (smem > 48 * 1024)
@@ -178,10 +178,10 @@ int launch_history(lbve* h, const double* kappa_in, double* sigma_dbl, cudaStrea
     HistArgs<real> a;
     a.X = (real*)h->X;
     a.K = (real*)h->K;
-    a.u_raw = (const real*)h->u_raw;
+    a.u_raw = (const double*)h->u_raw;
     a.kappa_in = kappa_in;
-    a.kappa = (real*)h->kappa;
-    a.sigma = (real*)h->sigma;
+    a.kappa = (double*)h->kappa;
+    a.sigma = (double*)h->sigma;
     a.sigma_dbl = sigma_dbl;
     a.t_dev = h->t_dev;
     a.B = h->d.hist_B;
@@ -196,34 +196,35 @@ int launch_history(lbve* h, const double* kappa_in, double* sigma_dbl, cudaStrea
 
 __global__ void k_advance_t(long long* t) { *t += 1; }
 
-template <int Q, typename real>
+// P: population storage type, R: history type, T: collision arithmetic type.
+template <int Q, typename P, typename R, typename T>
 int step_impl(lbve* h, int64_t n, cudaStream_t s) {
     constexpr int D = Lattice<Q>::D;
     const Geom g = geom_of(h);
-    const Phys<real> p = phys_of<real>(h);
+    const Phys p = phys_of(h);
     const int grid = (h->N + 255) / 256;
     for (int64_t i = 0; i < n; ++i) {
-        const real* din = (const real*)h->pops[h->cur];
-        real* dout = (real*)h->pops[h->cur ^ 1];
+        const P* din = (const P*)h->pops[h->cur];
+        P* dout = (P*)h->pops[h->cur ^ 1];
         int rc;
         if ((rc = prof_mark(h, s, KIND_MOMENTS, true))) return rc;
-        k_moments<Q, real><<<grid, 256, 0, s>>>(din, (real*)h->u_raw, g, p);
+        k_moments<Q, P><<<grid, 256, 0, s>>>(din, (double*)h->u_raw, g, p);
         LBVE_CUDA(cudaGetLastError());
         if ((rc = prof_mark(h, s, KIND_MOMENTS, false))) return rc;
         if ((rc = prof_mark(h, s, KIND_HISTORY, true))) return rc;
-        rc = launch_history<D, real>(h, nullptr, nullptr, s);
+        rc = launch_history<D, R>(h, nullptr, nullptr, s);
         if (rc) return rc;
         if ((rc = prof_mark(h, s, KIND_HISTORY, false))) return rc;
-        CollArgs<real> c;
+        CollArgs<P> c;
         c.dn_in = din;
         c.dn_out = dout;
-        c.sigma = (const real*)h->sigma;
-        c.tr_prev = (real*)h->tr_prev;
-        c.rho = (real*)h->rho;
-        c.u = (real*)h->u;
+        c.sigma = (const double*)h->sigma;
+        c.tr_prev = (double*)h->tr_prev;
+        c.rho = (double*)h->rho;
+        c.u = (double*)h->u;
         c.t_dev = h->t_dev;
         if ((rc = prof_mark(h, s, KIND_COLLIDE, true))) return rc;
-        k_collide_stream<Q, real><<<grid, 256, 0, s>>>(c, g, p);
+        k_collide_stream<Q, P, T><<<grid, 256, 0, s>>>(c, g, p);
         LBVE_CUDA(cudaGetLastError());
         if ((rc = prof_mark(h, s, KIND_COLLIDE, false))) return rc;
         h->cur ^= 1;
@@ -232,15 +233,15 @@ int step_impl(lbve* h, int64_t n, cudaStream_t s) {
     return LBVE_OK;
 }
 
-// Fluid at rest: n_q = w_q rho_init(n) (deviation w_q (rho_init - rho0)), rho field = rho_init.
-template <typename real>
-__global__ void k_init(real* dn, real* rho, long long Npad, int N, int Q, const double* rho_init, double rho0,
+// Fluid at rest: n_q = w_q rho_init(n) (deviation w_q (rho_init - rho0)), density field rho_init - rho0.
+template <typename P>
+__global__ void k_init(P* dn, double* rho, long long Npad, int N, int Q, const double* rho_init, double rho0,
                        const double* w) {
     const int n = blockIdx.x * blockDim.x + threadIdx.x;
     if (n >= N) return;
     const double r = rho_init ? rho_init[n] : rho0;
-    for (int q = 0; q < Q; ++q) dn[q * Npad + n] = (real)(w[q] * (r - rho0));
-    rho[n] = (real)r;
+    for (int q = 0; q < Q; ++q) dn[q * Npad + n] = (P)(w[q] * (r - rho0));
+    rho[n] = r - rho0;
 }
 
 template <typename real>
@@ -254,7 +255,7 @@ int init_state(lbve* h, const double* rho_init_host) {
     if (e == cudaSuccess && rho_init_host)
         e = cudaMemcpy(tmp + h->Q, rho_init_host, sizeof(double) * h->N, cudaMemcpyHostToDevice);
     if (e == cudaSuccess) {
-        k_init<real><<<(h->N + 255) / 256, 256>>>((real*)h->pops[0], (real*)h->rho, h->Npad, h->N, h->Q,
+        k_init<real><<<(h->N + 255) / 256, 256>>>((real*)h->pops[0], (double*)h->rho, h->Npad, h->N, h->Q,
                                                   rho_init_host ? tmp + h->Q : nullptr, h->d.rho0, tmp);
         e = cudaGetLastError();
     }
@@ -264,26 +265,26 @@ int init_state(lbve* h, const double* rho_init_host) {
     return LBVE_OK;
 }
 
-template <typename real>
 int fields_impl(lbve* h, uint32_t mask, double* dst, cudaStream_t s) {
+    using real = double;   // node fields are kept in double
     const long long Np = h->Npad;
     const int N = h->N;
     size_t off = 0;
-    auto gather = [&](const void* src, int ncomp) -> int {
+    auto gather = [&](const void* src, int ncomp, double offset) -> int {
         const long long tot = (long long)ncomp * N;
         if (tot > 0) {
-            k_gather<real><<<(int)((tot + 255) / 256), 256, 0, s>>>((const real*)src, Np, ncomp, N, dst + off,
-                                                                      h->flag);
+            k_gather<real><<<(int)((tot + 255) / 256), 256, 0, s>>>((const real*)src, Np, ncomp, N, offset,
+                                                                      dst + off, h->flag);
             LBVE_CUDA(cudaGetLastError());
         }
         off += (size_t)tot;
         return LBVE_OK;
     };
     int rc;
-    if (mask & LBVE_FIELD_RHO) if ((rc = gather(h->rho, 1))) return rc;
-    if (mask & LBVE_FIELD_U) if ((rc = gather(h->u, h->D))) return rc;
-    if (mask & LBVE_FIELD_SIGMA) if ((rc = gather(h->sigma, h->NS))) return rc;
-    if (mask & LBVE_FIELD_KAPPA) if ((rc = gather(h->kappa, h->D * h->D))) return rc;
+    if (mask & LBVE_FIELD_RHO) if ((rc = gather(h->rho, 1, h->d.rho0))) return rc;   // stored as rho - rho0
+    if (mask & LBVE_FIELD_U) if ((rc = gather(h->u, h->D, 0.0))) return rc;
+    if (mask & LBVE_FIELD_SIGMA) if ((rc = gather(h->sigma, h->NS, 0.0))) return rc;
+    if (mask & LBVE_FIELD_KAPPA) if ((rc = gather(h->kappa, h->D * h->D, 0.0))) return rc;
     if (mask & LBVE_FIELD_N1) {
         if (N > 0) {
             k_n1<real><<<(N + 255) / 256, 256, 0, s>>>((const real*)h->sigma, Np, N, dst + off, h->flag);
@@ -304,14 +305,14 @@ size_t fields_count(const lbve* h, uint32_t mask) {
     return c * (size_t)h->N;
 }
 
-template <typename real>
+template <typename P>
 int mass_impl(lbve* h, double* sum_n, double* sum_drho, cudaStream_t s) {
     LBVE_CUDA(cudaMemsetAsync(h->red, 0, 2 * sizeof(double), s));
     const int grid = 4 * 152;
-    k_sum<real><<<grid, 256, 0, s>>>((const real*)h->pops[h->cur], h->Npad, h->Q, h->N, 1.0, h->red);
+    k_sum<P><<<grid, 256, 0, s>>>((const P*)h->pops[h->cur], h->Npad, h->Q, h->N, 1.0, h->red);
     LBVE_CUDA(cudaGetLastError());
     // delta rho(t-1) = -tr sigma(t-1) / (d cs^2) = -3 tr / d
-    k_sum<real><<<grid, 256, 0, s>>>((const real*)h->tr_prev, h->Npad, 1, h->N, -3.0 / h->D, h->red + 1);
+    k_sum<double><<<grid, 256, 0, s>>>((const double*)h->tr_prev, h->Npad, 1, h->N, -3.0 / h->D, h->red + 1);
     LBVE_CUDA(cudaGetLastError());
     double r[2];
     LBVE_CUDA(cudaMemcpyAsync(r, h->red, sizeof r, cudaMemcpyDeviceToHost, s));
@@ -347,16 +348,19 @@ int lbve_create(const lbve_channel_desc* desc, const double* rho_init, lbve_t** 
     h->N = desc->nx * desc->ny * desc->nz;
     h->L = desc->hist_C * desc->hist_B;
     h->Npad = ((long long)h->N + 127) / 128 * 128;
-    h->dbl = desc->pop_precision == LBVE_F64;
-    h->esz = h->dbl ? 8 : 4;
+    h->pop_dbl = desc->pop_precision == LBVE_F64;
+    h->hist_dbl = desc->hist_storage == LBVE_F64;
+    h->pesz = h->pop_dbl ? 8 : 4;
+    h->hesz = h->hist_dbl ? 8 : 4;
     const long long Np = h->Npad;
     const int DD = h->D * h->D;
-    if ((rc = alloc(h, &h->pops[0], h->esz * h->Q * Np)) || (rc = alloc(h, &h->pops[1], h->esz * h->Q * Np)) ||
-        (rc = alloc(h, &h->u_raw, h->esz * h->D * Np)) || (rc = alloc(h, &h->u, h->esz * h->D * Np)) ||
-        (rc = alloc(h, &h->rho, h->esz * Np)) || (rc = alloc(h, &h->sigma, h->esz * h->NS * Np)) ||
-        (rc = alloc(h, &h->kappa, h->esz * DD * Np)) || (rc = alloc(h, &h->tr_prev, h->esz * Np)) ||
-        (rc = alloc(h, &h->X, h->esz * (size_t)h->L * DD * Np)) ||
-        (rc = alloc(h, &h->K, h->esz * (size_t)h->L * DD * Np)) ||
+    const size_t fe = sizeof(double);
+    if ((rc = alloc(h, &h->pops[0], h->pesz * h->Q * Np)) || (rc = alloc(h, &h->pops[1], h->pesz * h->Q * Np)) ||
+        (rc = alloc(h, &h->u_raw, fe * h->D * Np)) || (rc = alloc(h, &h->u, fe * h->D * Np)) ||
+        (rc = alloc(h, &h->rho, fe * Np)) || (rc = alloc(h, &h->sigma, fe * h->NS * Np)) ||
+        (rc = alloc(h, &h->kappa, fe * DD * Np)) || (rc = alloc(h, &h->tr_prev, fe * Np)) ||
+        (rc = alloc(h, &h->X, h->hesz * (size_t)h->L * DD * Np)) ||
+        (rc = alloc(h, &h->K, h->hesz * (size_t)h->L * DD * Np)) ||
         (rc = alloc(h, (void**)&h->t_dev, sizeof(long long))) || (rc = alloc(h, (void**)&h->red, 2 * sizeof(double))) ||
         (rc = alloc(h, (void**)&h->flag, sizeof(int)))) {
         free_all(h);
@@ -366,9 +370,9 @@ int lbve_create(const lbve_channel_desc* desc, const double* rho_init, lbve_t** 
     // zero every buffer: rest state, empty history (E = 1 <=> X = 0, kappa = 0), t = 0
     void* zero_bufs[] = {h->pops[0], h->pops[1], h->u_raw, h->u, h->sigma, h->kappa, h->tr_prev, h->X, h->K,
                          h->t_dev, h->flag};
-    size_t zero_sizes[] = {h->esz * h->Q * Np, h->esz * h->Q * Np, h->esz * h->D * Np, h->esz * h->D * Np,
-                           h->esz * h->NS * Np, h->esz * DD * Np, h->esz * Np, h->esz * (size_t)h->L * DD * Np,
-                           h->esz * (size_t)h->L * DD * Np, sizeof(long long), sizeof(int)};
+    size_t zero_sizes[] = {h->pesz * h->Q * Np, h->pesz * h->Q * Np, fe * h->D * Np, fe * h->D * Np,
+                           fe * h->NS * Np, fe * DD * Np, fe * Np, h->hesz * (size_t)h->L * DD * Np,
+                           h->hesz * (size_t)h->L * DD * Np, sizeof(long long), sizeof(int)};
     for (int i = 0; i < 11; ++i) {
         cudaError_t e = cudaMemset(zero_bufs[i], 0, zero_sizes[i]);
         if (e != cudaSuccess) {
@@ -378,7 +382,7 @@ int lbve_create(const lbve_channel_desc* desc, const double* rho_init, lbve_t** 
             return rc;
         }
     }
-    rc = h->dbl ? init_state<double>(h, rho_init) : init_state<float>(h, rho_init);
+    rc = h->pop_dbl ? init_state<double>(h, rho_init) : init_state<float>(h, rho_init);
     if (rc) {
         free_all(h);
         delete h;
@@ -418,8 +422,21 @@ int lbve_set_params(lbve_t* h, double G_inf, double tau, double gamma_c) {
 int lbve_step(lbve_t* h, int64_t n_steps, void* stream) {
     if (!h || n_steps < 0) return LBVE_EINVAL;
     cudaStream_t s = (cudaStream_t)stream;
-    if (h->Q == 9) return h->dbl ? step_impl<9, double>(h, n_steps, s) : step_impl<9, float>(h, n_steps, s);
-    return h->dbl ? step_impl<19, double>(h, n_steps, s) : step_impl<19, float>(h, n_steps, s);
+    const int combo = (h->pop_dbl ? 2 : 0) | (h->hist_dbl ? 1 : 0);
+    if (h->Q == 9) {
+        switch (combo) {
+            case 0: return step_impl<9, float, float, float>(h, n_steps, s);
+            case 1: return step_impl<9, float, double, float>(h, n_steps, s);
+            case 2: return step_impl<9, double, float, double>(h, n_steps, s);
+            default: return step_impl<9, double, double, double>(h, n_steps, s);
+        }
+    }
+    switch (combo) {
+        case 0: return step_impl<19, float, float, float>(h, n_steps, s);
+        case 1: return step_impl<19, float, double, float>(h, n_steps, s);
+        case 2: return step_impl<19, double, float, double>(h, n_steps, s);
+        default: return step_impl<19, double, double, double>(h, n_steps, s);
+    }
 }
 
 int lbve_get_time(const lbve_t* h, int64_t* t) {
@@ -438,7 +455,7 @@ int lbve_fields(lbve_t* h, uint32_t mask, double* dst, int32_t dst_is_device, vo
     if (!h || !dst || (mask & ~31u)) return LBVE_EINVAL;
     cudaStream_t s = (cudaStream_t)stream;
     const size_t cnt = fields_count(h, mask);
-    if (dst_is_device) return h->dbl ? fields_impl<double>(h, mask, dst, s) : fields_impl<float>(h, mask, dst, s);
+    if (dst_is_device) return fields_impl(h, mask, dst, s);
     if (h->stage_n < cnt) {
         if (h->stage) cudaFree(h->stage);
         h->stage = nullptr;
@@ -447,7 +464,7 @@ int lbve_fields(lbve_t* h, uint32_t mask, double* dst, int32_t dst_is_device, vo
         h->stage_n = cnt;
     }
     LBVE_CUDA(cudaMemsetAsync(h->flag, 0, sizeof(int), s));
-    int rc = h->dbl ? fields_impl<double>(h, mask, h->stage, s) : fields_impl<float>(h, mask, h->stage, s);
+    int rc = fields_impl(h, mask, h->stage, s);
     if (rc) return rc;
     int flag = 0;
     LBVE_CUDA(cudaMemcpyAsync(dst, h->stage, sizeof(double) * cnt, cudaMemcpyDeviceToHost, s));
@@ -460,10 +477,10 @@ int lbve_history_apply(lbve_t* h, const double* kappa_dev, double* sigma_dev, vo
     if (!h || !kappa_dev || !sigma_dev) return LBVE_EINVAL;
     cudaStream_t s = (cudaStream_t)stream;
     int rc;
-    if (h->D == 2) rc = h->dbl ? launch_history<2, double>(h, kappa_dev, sigma_dev, s)
-                               : launch_history<2, float>(h, kappa_dev, sigma_dev, s);
-    else rc = h->dbl ? launch_history<3, double>(h, kappa_dev, sigma_dev, s)
-                     : launch_history<3, float>(h, kappa_dev, sigma_dev, s);
+    if (h->D == 2) rc = h->hist_dbl ? launch_history<2, double>(h, kappa_dev, sigma_dev, s)
+                                    : launch_history<2, float>(h, kappa_dev, sigma_dev, s);
+    else rc = h->hist_dbl ? launch_history<3, double>(h, kappa_dev, sigma_dev, s)
+                          : launch_history<3, float>(h, kappa_dev, sigma_dev, s);
     if (rc) return rc;
     k_advance_t<<<1, 1, 0, s>>>(h->t_dev);
     LBVE_CUDA(cudaGetLastError());
@@ -474,7 +491,7 @@ int lbve_history_apply(lbve_t* h, const double* kappa_dev, double* sigma_dev, vo
 int lbve_mass(lbve_t* h, double* sum_n, double* sum_drho, void* stream) {
     if (!h || !sum_n || !sum_drho) return LBVE_EINVAL;
     cudaStream_t s = (cudaStream_t)stream;
-    return h->dbl ? mass_impl<double>(h, sum_n, sum_drho, s) : mass_impl<float>(h, sum_n, sum_drho, s);
+    return h->pop_dbl ? mass_impl<double>(h, sum_n, sum_drho, s) : mass_impl<float>(h, sum_n, sum_drho, s);
 }
 
 int lbve_schedule(int32_t C, int32_t B, int64_t t, int64_t* tp_out, double* w_out, int32_t* n_out) {

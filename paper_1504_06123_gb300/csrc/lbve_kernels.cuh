@@ -11,11 +11,14 @@
 //                      push streaming with half-way bounce-back.
 //
 // Layouts (device, structure of arrays, every plane padded to Npad nodes):
-//   populations  d_n[q][Npad]            stored as n_q - w_q rho0 (deviation form keeps FP32 exact
+//   populations  d_n[q][Npad]   type P   stored as n_q - w_q rho0 (deviation form keeps FP32 exact
 //                                        enough for velocities of 1e-5)
-//   history      X[slot][c][Npad]        X = E - 1 of each retained point (c < d*d, row-major)
-//                K[slot][c][Npad]        kappa of each retained point
-//   fields       u_raw[d][Npad], kappa[d*d][Npad], sigma[nsig][Npad], tr_prev[Npad], rho[Npad], u[d][Npad]
+//   history      X[slot][c][Npad] type R X = E - 1 of each retained point (c < d*d, row-major)
+//                K[slot][c][Npad] type R kappa of each retained point
+//   node fields  (double; O(N) words, negligible traffic next to the history)
+//                u_raw[d][Npad], kappa[d*d][Npad], sigma[nsig][Npad], tr_prev[Npad], drho[Npad] (rho - rho0),
+//                u[d][Npad]
+// P (population storage) and R (history storage and arithmetic) are float or double independently.
 // slot = bb*C + ring index, bb = 0 (coarsest block) .. B-1 (finest).
 #pragma once
 #include <cuda_runtime.h>
@@ -74,10 +77,10 @@ struct Geom {
     long long Npad;   // plane stride (multiple of 128)
 };
 
-template <typename real> struct Phys {
-    real rho0, tau_lb;
-    real f[3];        // force density rho0 g
-    real G_inf, inv_tau, inv_gc;
+struct Phys {
+    double rho0, tau_lb;
+    double f[3];      // force density rho0 g
+    double G_inf, inv_tau, inv_gc;
     int trace_full;
 };
 
@@ -91,25 +94,26 @@ __device__ __forceinline__ void node_xyz(const Geom& g, int n, int& x, int& y, i
 // ------------------------------------------------------------------------------------------------
 // K1: raw moments -> u_raw
 // ------------------------------------------------------------------------------------------------
-template <int Q, typename real>
-__global__ void __launch_bounds__(256) k_moments(const real* __restrict__ dn, real* __restrict__ u_raw, Geom g,
-                                                 Phys<real> p) {
+// Moments are summed in double: exact for float populations up to the last bit of the result.
+template <int Q, typename P>
+__global__ void __launch_bounds__(256) k_moments(const P* __restrict__ dn, double* __restrict__ u_raw, Geom g,
+                                                 Phys p) {
     using L = Lattice<Q>;
     constexpr int D = L::D;
     const int n = blockIdx.x * blockDim.x + threadIdx.x;
     if (n >= g.N) return;
-    real drho = 0, j[3] = {0, 0, 0};
+    double drho = 0, j[3] = {0, 0, 0};
 #pragma unroll
     for (int q = 0; q < Q; ++q) {
-        const real v = dn[(long long)q * g.Npad + n];
+        const double v = (double)dn[(long long)q * g.Npad + n];
         drho += v;
         if (L::cx(q)) j[0] += L::cx(q) * v;
         if (L::cy(q)) j[1] += L::cy(q) * v;
         if (D == 3 && L::cz(q)) j[2] += L::cz(q) * v;
     }
-    const real inv = real(1) / (p.rho0 + drho);
+    const double inv = 1.0 / (p.rho0 + drho);
 #pragma unroll
-    for (int a = 0; a < D; ++a) u_raw[(long long)a * g.Npad + n] = (j[a] + real(0.5) * p.f[a]) * inv;
+    for (int a = 0; a < D; ++a) u_raw[(long long)a * g.Npad + n] = (j[a] + 0.5 * p.f[a]) * inv;
 }
 
 // ------------------------------------------------------------------------------------------------
@@ -255,11 +259,11 @@ __device__ __forceinline__ void point_update(real* X, const real* A, const real*
 template <typename real> struct HistArgs {
     real* __restrict__ X;             // [L][DD][Npad]
     real* __restrict__ K;             // [L][DD][Npad]
-    const real* __restrict__ u_raw;   // [D][Npad]  (flow path)
+    const double* __restrict__ u_raw; // [D][Npad]  (flow path)
     const double* __restrict__ kappa_in;  // [DD][N] prescribed gradient (test hook) or nullptr
-    real* __restrict__ kappa;         // [DD][Npad] kappa(t) out
-    real* __restrict__ sigma;         // [NS][Npad] sigma_struc(t) out
-    double* __restrict__ sigma_dbl;   // [NS][N] optional copy in double (test hook) or nullptr
+    double* __restrict__ kappa;       // [DD][Npad] kappa(t) out
+    double* __restrict__ sigma;       // [NS][Npad] sigma_struc(t) out
+    double* __restrict__ sigma_dbl;   // [NS][N] optional copy (test hook) or nullptr
     const long long* t_dev;           // step index t
     int B, C;
 };
@@ -280,7 +284,7 @@ __host__ __device__ inline size_t history_smem_bytes(int L) {
 // Shared memory: per slot age (float), weight (float), partner (int) + the per-block state +
 // the cross-group reduction buffer.
 template <int D, typename real, int G>
-__global__ void __launch_bounds__(256) k_history(HistArgs<real> a, Geom g, Phys<real> p) {
+__global__ void __launch_bounds__(256) k_history(HistArgs<real> a, Geom g, Phys p) {
     constexpr int DD = D * D;
     constexpr int NS = D == 2 ? 3 : 6;
     constexpr int NODES = 256 / G;
@@ -313,6 +317,7 @@ __global__ void __launch_bounds__(256) k_history(HistArgs<real> a, Geom g, Phys<
     real acc[NS];
 #pragma unroll
     for (int i = 0; i < NS; ++i) acc[i] = 0;
+    const real inv_tau = (real)p.inv_tau, inv_gc = (real)p.inv_gc;
 
     if (live) {
         // A = exp(kappa(t-1)) - 1; kappa(t-1) is the kappa of the point created last step, held at the
@@ -339,7 +344,7 @@ __global__ void __launch_bounds__(256) k_history(HistArgs<real> a, Geom g, Phys<
 #pragma unroll
                 for (int c = 0; c < DD; ++c) kap[c] = real(0.5) * (kap[c] + K2[c * Np]);
             }
-            point_update<D>(X, A, kap, (real)s_age[l], (real)w, p.inv_tau, p.inv_gc, acc);
+            point_update<D>(X, A, kap, (real)s_age[l], (real)w, inv_tau, inv_gc, acc);
 #pragma unroll
             for (int c = 0; c < DD; ++c) Xp[c * Np] = X[c];
         }
@@ -359,13 +364,16 @@ __global__ void __launch_bounds__(256) k_history(HistArgs<real> a, Geom g, Phys<
             for (int i = 0; i < NS; ++i) acc[i] += s_red[((j - 1) * NS + i) * NODES + ln];
     }
     // the point created now: age 0, E = 1, weight 1/2, modulus G_inf
-    real kt[DD];
+    double ktd[DD];
     if (a.kappa_in) {
 #pragma unroll
-        for (int c = 0; c < DD; ++c) kt[c] = (real)a.kappa_in[(long long)c * g.N + n];
+        for (int c = 0; c < DD; ++c) ktd[c] = a.kappa_in[(long long)c * g.N + n];
     } else {
-        kappa_fd<D>(a.u_raw, g, n, kt);
+        kappa_fd<D>(a.u_raw, g, n, ktd);
     }
+    real kt[DD];
+#pragma unroll
+    for (int c = 0; c < DD; ++c) kt[c] = (real)ktd[c];
     if (D == 2) {
         acc[0] += real(0.5) * (kt[0] + kt[0]);
         acc[1] += real(0.5) * (kt[3] + kt[3]);
@@ -380,12 +388,12 @@ __global__ void __launch_bounds__(256) k_history(HistArgs<real> a, Geom g, Phys<
     }
 #pragma unroll
     for (int i = 0; i < NS; ++i) {
-        const real s = p.G_inf * acc[i];
+        const double s = p.G_inf * (double)acc[i];
         a.sigma[i * Np + n] = s;
-        if (a.sigma_dbl) a.sigma_dbl[(long long)i * g.N + n] = (double)s;
+        if (a.sigma_dbl) a.sigma_dbl[(long long)i * g.N + n] = s;
     }
 #pragma unroll
-    for (int c = 0; c < DD; ++c) a.kappa[c * Np + n] = kt[c];
+    for (int c = 0; c < DD; ++c) a.kappa[c * Np + n] = ktd[c];
 
     // block merges, coarsest first, so that every ring slot is read before it is overwritten
     for (int bb = 1; bb < a.B; ++bb) {
@@ -415,71 +423,77 @@ __global__ void __launch_bounds__(256) k_history(HistArgs<real> a, Geom g, Phys<
 // ------------------------------------------------------------------------------------------------
 // K3: collision with the non-Newtonian forcing and push streaming
 // ------------------------------------------------------------------------------------------------
-template <typename real> struct CollArgs {
-    const real* __restrict__ dn_in;   // [Q][Npad]
-    real* __restrict__ dn_out;        // [Q][Npad]
-    const real* __restrict__ sigma;   // [NS][Npad]
-    real* __restrict__ tr_prev;       // [Npad]
-    real* __restrict__ rho;           // [Npad]
-    real* __restrict__ u;             // [D][Npad]
-    long long* t_dev;                 // advanced by one thread after the step
+template <typename P> struct CollArgs {
+    const P* __restrict__ dn_in;        // [Q][Npad]
+    P* __restrict__ dn_out;             // [Q][Npad]
+    const double* __restrict__ sigma;   // [NS][Npad]
+    double* __restrict__ tr_prev;       // [Npad]
+    double* __restrict__ rho;           // [Npad] rho - rho0
+    double* __restrict__ u;             // [D][Npad]
+    long long* t_dev;                   // advanced by one thread after the step
 };
 
-template <int Q, typename real>
-__global__ void __launch_bounds__(256) k_collide_stream(CollArgs<real> a, Geom g, Phys<real> p) {
+// T: arithmetic type of the collision (double for double populations; float or double for float).
+template <int Q, typename P, typename T>
+__global__ void __launch_bounds__(256) k_collide_stream(CollArgs<P> a, Geom g, Phys p) {
     using L = Lattice<Q>;
     constexpr int D = L::D;
     const int n = blockIdx.x * blockDim.x + threadIdx.x;
     if (n == 0) *a.t_dev += 1;   // no kernel of this step reads t after k_history
     if (n >= g.N) return;
     const long long Np = g.Npad;
-    const real cs2 = real(1.0 / 3.0);
-    real dn[Q];
-    real drho_raw = 0, j[3] = {0, 0, 0};
+    const T cs2 = T(1.0 / 3.0);
+    T dn[Q];
+    double drho_raw = 0, jd[3] = {0, 0, 0};
 #pragma unroll
     for (int q = 0; q < Q; ++q) {
-        dn[q] = a.dn_in[q * Np + n];
-        drho_raw += dn[q];
-        if (L::cx(q)) j[0] += L::cx(q) * dn[q];
-        if (L::cy(q)) j[1] += L::cy(q) * dn[q];
-        if (D == 3 && L::cz(q)) j[2] += L::cz(q) * dn[q];
+        const P v = a.dn_in[q * Np + n];
+        dn[q] = (T)v;
+        drho_raw += (double)v;
+        if (L::cx(q)) jd[0] += L::cx(q) * (double)v;
+        if (L::cy(q)) jd[1] += L::cy(q) * (double)v;
+        if (D == 3 && L::cz(q)) jd[2] += L::cz(q) * (double)v;
     }
     // stress: traceless part and density source (Sec. III, trace split)
-    real S[3][3];
+    T S[3][3];
+    double trd = 0;
     if (D == 2) {
-        S[0][0] = a.sigma[0 * Np + n]; S[1][1] = a.sigma[1 * Np + n];
-        S[0][1] = S[1][0] = a.sigma[2 * Np + n];
+        S[0][0] = (T)a.sigma[0 * Np + n]; S[1][1] = (T)a.sigma[1 * Np + n];
+        S[0][1] = S[1][0] = (T)a.sigma[2 * Np + n];
+        trd = a.sigma[0 * Np + n] + a.sigma[1 * Np + n];
     } else {
-        S[0][0] = a.sigma[0 * Np + n]; S[1][1] = a.sigma[1 * Np + n]; S[2][2] = a.sigma[2 * Np + n];
-        S[0][1] = S[1][0] = a.sigma[3 * Np + n];
-        S[0][2] = S[2][0] = a.sigma[4 * Np + n];
-        S[1][2] = S[2][1] = a.sigma[5 * Np + n];
+        S[0][0] = (T)a.sigma[0 * Np + n]; S[1][1] = (T)a.sigma[1 * Np + n]; S[2][2] = (T)a.sigma[2 * Np + n];
+        S[0][1] = S[1][0] = (T)a.sigma[3 * Np + n];
+        S[0][2] = S[2][0] = (T)a.sigma[4 * Np + n];
+        S[1][2] = S[2][1] = (T)a.sigma[5 * Np + n];
+        trd = a.sigma[0 * Np + n] + a.sigma[1 * Np + n] + a.sigma[2 * Np + n];
     }
-    real tr = 0;
+    double ddr_d = 0;
+    if (p.trace_full) ddr_d = -(trd - a.tr_prev[n]) * (3.0 / D);   // -(tr - tr_prev)/(d cs^2)
+    const double drho_d = drho_raw + 0.5 * ddr_d;                  // rho - rho0
+    const double rho_d = p.rho0 + drho_d;
+    double ud[3] = {0, 0, 0};
 #pragma unroll
-    for (int c = 0; c < D; ++c) tr += S[c][c];
-    real ddr = 0;
-    if (p.trace_full) ddr = -(tr - a.tr_prev[n]) / (real(D) * cs2);
-    const real drho = drho_raw + real(0.5) * ddr;        // rho - rho0
-    const real rho = p.rho0 + drho;
-    real u[3];
+    for (int c = 0; c < D; ++c) ud[c] = (jd[c] + 0.5 * p.f[c]) / rho_d;
+    const T tr = (T)trd, ddr = (T)ddr_d, drho = (T)drho_d, rho = (T)rho_d;
+    T u[3], f[3];
 #pragma unroll
-    for (int c = 0; c < D; ++c) u[c] = (j[c] + real(0.5) * p.f[c]) / rho;
+    for (int c = 0; c < 3; ++c) { u[c] = (T)ud[c]; f[c] = (T)p.f[c]; }
 #pragma unroll
-    for (int c = 0; c < D; ++c) S[c][c] -= tr / real(D);
-    real uu = 0;
+    for (int c = 0; c < D; ++c) S[c][c] -= tr / T(D);
+    T uu = 0;
 #pragma unroll
     for (int c = 0; c < D; ++c) uu += u[c] * u[c];
-    const real omega = real(1) / p.tau_lb;
-    const real fpre = real(1) - real(0.5) * omega;
-    const real inv2cs4 = real(4.5);   // 1/(2 cs^4)
+    const T omega = T(1.0 / p.tau_lb);
+    const T fpre = T(1) - T(0.5) * omega;
+    const T inv2cs4 = T(4.5);   // 1/(2 cs^4)
     // X_ab = -ddr u_a u_b + u_b f_a + u_a f_b  (second-order forcing term of Eq. bodyforce)
-    real Xf[3][3];
+    T Xf[3][3];
 #pragma unroll
     for (int r = 0; r < D; ++r)
 #pragma unroll
-        for (int c = 0; c < D; ++c) Xf[r][c] = -ddr * u[r] * u[c] + u[c] * p.f[r] + u[r] * p.f[c];
-    real trX = 0;
+        for (int c = 0; c < D; ++c) Xf[r][c] = -ddr * u[r] * u[c] + u[c] * f[r] + u[r] * f[c];
+    T trX = 0;
 #pragma unroll
     for (int c = 0; c < D; ++c) trX += Xf[c][c];
 
@@ -488,11 +502,11 @@ __global__ void __launch_bounds__(256) k_collide_stream(CollArgs<real> a, Geom g
 #pragma unroll
     for (int q = 0; q < Q; ++q) {
         const int cq[3] = {L::cx(q), L::cy(q), L::cz(q)};
-        real cu = 0, cf = 0, cSc = 0, cXc = 0;
+        T cu = 0, cf = 0, cSc = 0, cXc = 0;
 #pragma unroll
         for (int r = 0; r < D; ++r) {
             cu += cq[r] * u[r];
-            cf += cq[r] * p.f[r];
+            cf += cq[r] * f[r];
 #pragma unroll
             for (int c = 0; c < D; ++c) {
                 if (cq[r] && cq[c]) {
@@ -501,13 +515,12 @@ __global__ void __launch_bounds__(256) k_collide_stream(CollArgs<real> a, Geom g
                 }
             }
         }
-        const real wq = (real)L::w(q);
+        const T wq = (T)L::w(q);
         // deviation of the equilibrium from w rho0: w (rho - rho0) + w rho (c.u/cs2 + ((c.u)^2 - cs2 u.u)/(2 cs4))
-        const real dneq = wq * (drho + rho * (cu * real(3) + (cu * cu - cs2 * uu) * inv2cs4));
+        const T dneq = wq * (drho + rho * (cu * T(3) + (cu * cu - cs2 * uu) * inv2cs4));
         // Eq. (bodyforce); (cc - cs2 1):S = cSc (S traceless), (cc - cs2 1):X = cXc - cs2 tr X
-        const real Fq = wq * (-inv2cs4 * omega * cSc +
-                              fpre * (ddr + cf * real(3) + inv2cs4 * (cXc - cs2 * trX)));
-        const real post = dn[q] - omega * (dn[q] - dneq) + Fq;
+        const T Fq = wq * (-inv2cs4 * omega * cSc + fpre * (ddr + cf * T(3) + inv2cs4 * (cXc - cs2 * trX)));
+        const P post = (P)(dn[q] - omega * (dn[q] - dneq) + Fq);
         // push with half-way bounce-back
         int xd = x + cq[0];
         xd = xd < 0 ? g.nx - 1 : (xd >= g.nx ? 0 : xd);
@@ -521,22 +534,22 @@ __global__ void __launch_bounds__(256) k_collide_stream(CollArgs<real> a, Geom g
         if (wall) a.dn_out[L::opp(q) * Np + n] = post;
         else a.dn_out[q * Np + (xd + g.nx * (yd + g.ny * zd))] = post;
     }
-    a.rho[n] = rho;
+    a.rho[n] = drho_d;
 #pragma unroll
-    for (int c = 0; c < D; ++c) a.u[c * Np + n] = u[c];
-    a.tr_prev[n] = p.trace_full ? tr : real(0);
+    for (int c = 0; c < D; ++c) a.u[c * Np + n] = ud[c];
+    a.tr_prev[n] = p.trace_full ? trd : 0.0;
 }
 
 // ------------------------------------------------------------------------------------------------
 // Field gather (lbve_fields) and reductions (lbve_mass)
 // ------------------------------------------------------------------------------------------------
 template <typename real>
-__global__ void k_gather(const real* __restrict__ src, long long Npad, int ncomp, int N, double* __restrict__ dst,
-                         int* nonfinite) {
+__global__ void k_gather(const real* __restrict__ src, long long Npad, int ncomp, int N, double offset,
+                         double* __restrict__ dst, int* nonfinite) {
     const long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x;
     if (i >= (long long)ncomp * N) return;
     const int c = (int)(i / N), n = (int)(i % N);
-    const double v = (double)src[c * Npad + n];
+    const double v = (double)src[c * Npad + n] + offset;
     dst[i] = v;
     if (!isfinite(v)) atomicOr(nonfinite, 1);
 }

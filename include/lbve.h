@@ -34,6 +34,7 @@ extern "C" {
 #define LBVE_ENONFINITE  -4  /* a NaN or Inf appeared in the state */
 #define LBVE_ESTATE      -6  /* the call does not fit the handle's state */
 #define LBVE_ENOSUPPORT  -7  /* a valid combination this build does not implement */
+#define LBVE_ETOOBIG     -8  /* request larger than the fixed device buffer of lbve_fields_host_fixed */
 
 /* ---- enumerations ---------------------------------------------------------------------------- */
 #define LBVE_D2Q9   9    /* planar channel, Sec. III velocity set */
@@ -151,6 +152,28 @@ int lbve_memory_bytes(const lbve_t* h, size_t* bytes);
  */
 int lbve_profile(lbve_t* h, int32_t enable);
 int lbve_profile_read(lbve_t* h, double ms_out[3], int64_t launches_out[3]);
+
+/*
+ * lbve_fields with a host destination, for callers that must not allocate device memory once their set-up
+ * is done.  (The paper has no counterpart: this is a library service.)  lbve_fields stages a host copy in
+ * a device buffer that it allocates on first use and keeps; some callers cannot allow that allocation:
+ * an application that has handed the whole GPU to a memory pool of its own, a service that runs with a
+ * fixed device-memory budget, or a time-stepping loop in which an allocation (and the device-wide
+ * synchronisation it implies) is not acceptable.  This variant allocates nothing: it stages through one
+ * fixed device array of LBVE_FIXED_STAGING_DOUBLES doubles (16 MiB) that every GPU which loads the library
+ * holds until the process exits.
+ *
+ * Same fields, layout and synchronisation as lbve_fields with dst_is_device = 0: dst is host memory of
+ * lbve_fields_count(h, mask) doubles, owned by the caller; `stream` is synchronised before return.
+ * Returns LBVE_ETOOBIG (nothing copied) when that count exceeds LBVE_FIXED_STAGING_DOUBLES, ENONFINITE
+ * (after copying) when a copied value is NaN or Inf, EINVAL for bad arguments.
+ * The first call on a device looks up the array's device address (once per device, on the current
+ * device); make that first call before any stream capture.  All calls on a device share the one array,
+ * so calls that overlap on the GPU (other streams, other host threads) race with each other: serialise
+ * them.  The non-finite flag kept in the array is cleared at the start of every call.
+ */
+#define LBVE_FIXED_STAGING_DOUBLES (1u << 21)
+int lbve_fields_host_fixed(lbve_t* h, uint32_t field_mask, double* dst_host, void* stream);
 
 /* Static description of a status code. */
 const char* lbve_strerror(int status);

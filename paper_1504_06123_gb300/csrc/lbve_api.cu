@@ -9,6 +9,7 @@
 #include <cstdio>
 #include <cstring>
 #include <algorithm>
+#include <mutex>
 #include <new>
 #include <utility>
 #include <vector>
@@ -532,6 +533,7 @@ const char* lbve_strerror(int status) {
         case LBVE_ENONFINITE: return "non-finite value in the state";
         case LBVE_ESTATE: return "call does not fit the handle's state";
         case LBVE_ENOSUPPORT: return "combination not supported by this build";
+        case LBVE_ETOOBIG: return "request exceeds the fixed staging buffer of lbve_fields_host_fixed";
         default: return "unknown status";
     }
 }
@@ -562,3 +564,79 @@ int lbve_profile_read(lbve_t* h, double ms_out[3], int64_t launches_out[3]) {
 }
 
 }  // extern "C"
+
+// =================================================================================================
+// lbve_fields_host_fixed: the host-destination field copy without any device allocation.
+// The staging lives in one fixed file-scope device array; its last 32 doubles (256 bytes) hold the
+// non-finite flag.  In host code the array's name is only a host-side stand-in, so the device address is
+// looked up once per device with cudaGetSymbolAddress and passed to the kernels.
+// =================================================================================================
+static __device__ __align__(256) double g_fixed_staging[LBVE_FIXED_STAGING_DOUBLES + 32];
+
+namespace {
+
+constexpr int kMaxDevices = 64;
+std::mutex g_fixed_mu;
+double* g_fixed_ptr[kMaxDevices] = {nullptr};
+
+// Device address of the fixed staging array on the current device (looked up on first use).
+int fixed_staging_ptr(double** out) {
+    int dev = -1;
+    LBVE_CUDA(cudaGetDevice(&dev));
+    if (dev < 0 || dev >= kMaxDevices) return LBVE_ENOSUPPORT;
+    std::lock_guard<std::mutex> lock(g_fixed_mu);
+    if (!g_fixed_ptr[dev]) {
+        double* p = nullptr;
+        LBVE_CUDA(cudaGetSymbolAddress((void**)&p, g_fixed_staging));
+        g_fixed_ptr[dev] = p;
+    }
+    *out = g_fixed_ptr[dev];
+    return LBVE_OK;
+}
+
+// The gathers of lbve_fields, writing into `dst` (device) and raising `flag` on a non-finite value.
+int gather_fields_into(lbve* h, uint32_t mask, double* dst, int* flag, cudaStream_t s) {
+    const long long Np = h->Npad;
+    const int N = h->N;
+    size_t off = 0;
+    struct Part { uint32_t bit; const void* src; int ncomp; double offset; };
+    const Part parts[] = {{LBVE_FIELD_RHO, h->rho, 1, h->d.rho0},
+                          {LBVE_FIELD_U, h->u, h->D, 0.0},
+                          {LBVE_FIELD_SIGMA, h->sigma, h->NS, 0.0},
+                          {LBVE_FIELD_KAPPA, h->kappa, h->D * h->D, 0.0}};
+    for (const Part& pt : parts) {
+        if (!(mask & pt.bit)) continue;
+        const long long tot = (long long)pt.ncomp * N;
+        if (tot > 0) {
+            k_gather<double><<<(int)((tot + 255) / 256), 256, 0, s>>>((const double*)pt.src, Np, pt.ncomp, N,
+                                                                        pt.offset, dst + off, flag);
+            LBVE_CUDA(cudaGetLastError());
+        }
+        off += (size_t)tot;
+    }
+    if ((mask & LBVE_FIELD_N1) && N > 0) {
+        k_n1<double><<<(N + 255) / 256, 256, 0, s>>>((const double*)h->sigma, Np, N, dst + off, flag);
+        LBVE_CUDA(cudaGetLastError());
+    }
+    return LBVE_OK;
+}
+
+}  // namespace
+
+extern "C" int lbve_fields_host_fixed(lbve_t* h, uint32_t mask, double* dst_host, void* stream) {
+    if (!h || !dst_host || (mask & ~31u)) return LBVE_EINVAL;
+    const size_t cnt = fields_count(h, mask);
+    if (cnt > (size_t)LBVE_FIXED_STAGING_DOUBLES) return LBVE_ETOOBIG;
+    cudaStream_t s = (cudaStream_t)stream;
+    double* stage = nullptr;
+    int rc = fixed_staging_ptr(&stage);
+    if (rc) return rc;
+    int* flag = reinterpret_cast<int*>(stage + LBVE_FIXED_STAGING_DOUBLES);
+    LBVE_CUDA(cudaMemsetAsync(flag, 0, sizeof(int), s));
+    if ((rc = gather_fields_into(h, mask, stage, flag, s))) return rc;
+    int flag_host = 0;
+    LBVE_CUDA(cudaMemcpyAsync(dst_host, stage, sizeof(double) * cnt, cudaMemcpyDeviceToHost, s));
+    LBVE_CUDA(cudaMemcpyAsync(&flag_host, flag, sizeof(int), cudaMemcpyDeviceToHost, s));
+    LBVE_CUDA(cudaStreamSynchronize(s));
+    return flag_host ? LBVE_ENONFINITE : LBVE_OK;
+}

@@ -18,6 +18,8 @@ import numpy as np
 from . import build as _build
 
 LBVE_OK, LBVE_EINVAL, LBVE_ENOMEM, LBVE_ECUDA, LBVE_ENONFINITE, LBVE_ESTATE, LBVE_ENOSUPPORT = 0, -1, -2, -3, -4, -6, -7
+LBVE_ETOOBIG = -8
+LBVE_FIXED_STAGING_DOUBLES = 1 << 21
 LBVE_D2Q9, LBVE_D3Q19 = 9, 19
 LBVE_F32, LBVE_F64, LBVE_BF16 = 0, 1, 2
 LBVE_TRACE_FULL, LBVE_TRACE_NONE = 0, 1
@@ -28,6 +30,7 @@ EXPORTS = [
     "lbve_create", "lbve_destroy", "lbve_set_force", "lbve_set_params", "lbve_step", "lbve_get_time",
     "lbve_fields", "lbve_fields_count", "lbve_history_apply", "lbve_mass", "lbve_schedule",
     "lbve_memory_bytes", "lbve_strerror", "lbve_last_cuda_error", "lbve_profile", "lbve_profile_read",
+    "lbve_fields_host_fixed",
 ]
 
 
@@ -79,6 +82,7 @@ def load(path: str | None = None):
         lib.lbve_memory_bytes.argtypes = [vp, C.POINTER(C.c_size_t)]
         lib.lbve_strerror.argtypes = [C.c_int]
         lib.lbve_strerror.restype = C.c_char_p
+        lib.lbve_fields_host_fixed.argtypes = [vp, C.c_uint32, vp, vp]
         lib.lbve_profile.argtypes = [vp, i32]
         lib.lbve_profile_read.argtypes = [vp, dp, C.POINTER(i64)]
         lib.lbve_last_cuda_error.argtypes = []
@@ -176,6 +180,14 @@ def lbve_fields(h: int, mask: int, dst=None, stream=None):
     rc = lib.lbve_fields(h, mask, _ptr(dst), 1, _stream(stream))
     _check(rc, "lbve_fields")
     return dst
+
+
+def lbve_fields_host_fixed(h: int, mask: int, stream=None) -> np.ndarray:
+    """lbve_fields into host memory through the library's fixed device staging array (no device
+    allocation).  Returns a new numpy array; raises LbveError (LBVE_ETOOBIG) past the array's size."""
+    out = np.empty(lbve_fields_count(h, mask), dtype=np.float64)
+    _check(load().lbve_fields_host_fixed(h, mask, out.ctypes.data, _stream(stream)), "lbve_fields_host_fixed")
+    return out
 
 
 def lbve_history_apply(h: int, kappa_dev, sigma_dev, stream=None) -> None:

@@ -133,7 +133,7 @@ def kernel_hash() -> str:
 
 def recorded_traffic():
     """DRAM bytes per history launch from the committed ncu summary, if it was taken on these kernels."""
-    p = os.path.join(ROOT, "profiles", "history_channel_1024x512_L1024.md")
+    p = os.path.join(ROOT, "profiles", "sweep_channel_1024x512_L1024.md")
     if not os.path.exists(p):
         return None
     kh, traffic = None, None
@@ -239,7 +239,7 @@ def run_ours(args, rank, world, local_rank):
     value = updates_rank * world / (ms_max / 1e3)
     mlups = w.N * K * world / (ms_max / 1e3) / 1e6
 
-    # roofline of the dominant kernel (the history sweep), from its own events
+    # roofline of the dominant kernel (the history sweep k_sweep), from its own events
     hist_ms = kms[1] / max(launches[1], 1)
     alg_bytes = BYTES_PER_UPDATE * w.N * (sum(mem_points) / len(mem_points))
     peak, peak_kind = peaks()
@@ -287,7 +287,7 @@ def run_ours(args, rank, world, local_rank):
                                      "collide_stream": kms[2] / max(launches[2], 1)},
             "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                          "frac": achieved / peak, "traffic": traffic, "peak_kind": peak_kind,
-                         "kernel": "k_history", "algorithmic_bytes_per_launch": alg_bytes},
+                         "kernel": "k_sweep", "algorithmic_bytes_per_launch": alg_bytes},
             "clocks": clk.summary(),
             "gpu_launches": int(sum(launches)),
             "e2e": e2e,

@@ -53,6 +53,9 @@ struct lbve {
     void* tr_prev = nullptr;
     void* X = nullptr;
     void* K = nullptr;
+    void* part = nullptr;      // sweep partial sums [S][NS][Npad] (history type)
+    int S = 1;                 // slot chunks of the sweep
+    int sweep_grid = 0;        // persistent CTAs of the sweep
     long long* t_dev = nullptr;
     double* red = nullptr;     // reduction scratch (2 doubles)
     double* stage = nullptr;   // lbve_fields staging for host destinations
@@ -71,7 +74,7 @@ namespace {
 
 void free_all(lbve* h) {
     void* ptrs[] = {h->pops[0], h->pops[1], h->u_raw, h->u, h->rho, h->sigma, h->kappa, h->tr_prev,
-                    h->X, h->K, h->t_dev, h->red, h->stage, h->flag};
+                    h->X, h->K, h->part, h->t_dev, h->red, h->stage, h->flag};
     for (void* p : ptrs)
         if (p) cudaFree(p);
     for (cudaEvent_t e : h->ev_pool) cudaEventDestroy(e);
@@ -151,48 +154,61 @@ int check_desc(const lbve_channel_desc* d) {
     return LBVE_OK;
 }
 
-// Slot groups per CTA for the history sweep: enough CTAs to fill the GPU, the rest of the threads
-// split each node's points.
-int pick_groups(int N) {
-    const int sms = 152;
-    int G = 1;
-    while (G < 8 && (long long)((N + (256 / G) - 1) / (256 / G)) < 2ll * sms) G *= 2;
-    return G;
+// Values per lane of the sweep (one 16-byte access): 4 floats or 2 doubles; 3D halves it (registers).
+template <int D, typename R> constexpr int sweep_vn() { return (sizeof(R) == 4 ? 4 : 2) / (D == 3 ? 2 : 1); }
+
+template <int D, typename R>
+int sweep_config(lbve* h) {
+    constexpr int VN = sweep_vn<D, R>();
+    const size_t smem = sweep_smem_bytes(h->L);
+    if (smem > 48 * 1024)
+        LBVE_CUDA(cudaFuncSetAttribute(k_sweep<D, R, VN>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    int dev = 0, sms = 0, per_sm = 0;
+    LBVE_CUDA(cudaGetDevice(&dev));
+    LBVE_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+    LBVE_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_sweep<D, R, VN>, 256, smem));
+    if (per_sm < 1) per_sm = 1;
+    const long long warps = (long long)sms * per_sm * 8;
+    const long long tiles = h->Npad / (32 * VN);
+    // about eight tasks per resident warp, so that the last round costs little; chunks of >= 8 slots
+    long long S = (8 * warps + tiles - 1) / tiles;
+    const long long Smax = h->L >= 16 ? h->L / 8 : 1;
+    if (S > Smax) S = Smax;
+    if (S < 1) S = 1;
+    h->S = (int)S;
+    const long long tasks = tiles * S;
+    const long long grid_full = (long long)sms * per_sm;
+    h->sweep_grid = (int)std::min<long long>(grid_full, (tasks + 7) / 8);
+    if (h->sweep_grid < 1) h->sweep_grid = 1;
+    return LBVE_OK;
 }
 
-template <int D, typename real, int G>
-int launch_history_g(lbve* h, const HistArgs<real>& a, cudaStream_t s) {
-    const Geom g = geom_of(h);
-    const Phys p = phys_of(h);
-    constexpr int NODES = 256 / G;
-    const size_t smem = history_smem_bytes<D, real, G>(h->L);
-    if (smem > 48 * 1024)
-        LBVE_CUDA(cudaFuncSetAttribute(k_history<D, real, G>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-    const int grid = (h->N + NODES - 1) / NODES;
-    k_history<D, real, G><<<grid, 256, smem, s>>>(a, g, p);
+template <int D, typename R>
+int launch_sweep(lbve* h, cudaStream_t s) {
+    constexpr int VN = sweep_vn<D, R>();
+    SweepArgs<R> a;
+    a.X = (R*)h->X;
+    a.K = (const R*)h->K;
+    a.part = (R*)h->part;
+    a.t_dev = h->t_dev;
+    a.B = h->d.hist_B;
+    a.C = h->d.hist_C;
+    a.S = h->S;
+    k_sweep<D, R, VN><<<h->sweep_grid, 256, sweep_smem_bytes(h->L), s>>>(a, geom_of(h), phys_of(h));
     LBVE_CUDA(cudaGetLastError());
     return LBVE_OK;
 }
 
-template <int D, typename real>
-int launch_history(lbve* h, const double* kappa_in, double* sigma_dbl, cudaStream_t s) {
-    HistArgs<real> a;
-    a.X = (real*)h->X;
-    a.K = (real*)h->K;
-    a.u_raw = (const double*)h->u_raw;
-    a.kappa_in = kappa_in;
-    a.kappa = (double*)h->kappa;
-    a.sigma = (double*)h->sigma;
-    a.sigma_dbl = sigma_dbl;
-    a.t_dev = h->t_dev;
-    a.B = h->d.hist_B;
-    a.C = h->d.hist_C;
-    switch (pick_groups(h->N)) {
-        case 1: return launch_history_g<D, real, 1>(h, a, s);
-        case 2: return launch_history_g<D, real, 2>(h, a, s);
-        case 4: return launch_history_g<D, real, 4>(h, a, s);
-        default: return launch_history_g<D, real, 8>(h, a, s);
-    }
+template <typename R>
+CommitArgs<R> commit_args(lbve* h) {
+    CommitArgs<R> c;
+    c.X = (R*)h->X;
+    c.K = (R*)h->K;
+    c.part = (const R*)h->part;
+    c.B = h->d.hist_B;
+    c.C = h->d.hist_C;
+    c.S = h->S;
+    return c;
 }
 
 __global__ void k_advance_t(long long* t) { *t += 1; }
@@ -209,23 +225,25 @@ int step_impl(lbve* h, int64_t n, cudaStream_t s) {
         P* dout = (P*)h->pops[h->cur ^ 1];
         int rc;
         if ((rc = prof_mark(h, s, KIND_MOMENTS, true))) return rc;
-        k_moments<Q, P><<<grid, 256, 0, s>>>(din, (double*)h->u_raw, g, p);
+        k_moments<Q, P><<<grid, 256, 0, s>>>(din, (double*)h->u_raw, g, p, h->t_dev);
         LBVE_CUDA(cudaGetLastError());
         if ((rc = prof_mark(h, s, KIND_MOMENTS, false))) return rc;
         if ((rc = prof_mark(h, s, KIND_HISTORY, true))) return rc;
-        rc = launch_history<D, R>(h, nullptr, nullptr, s);
+        rc = launch_sweep<D, R>(h, s);
         if (rc) return rc;
         if ((rc = prof_mark(h, s, KIND_HISTORY, false))) return rc;
         CollArgs<P> c;
         c.dn_in = din;
         c.dn_out = dout;
-        c.sigma = (const double*)h->sigma;
+        c.u_raw = (const double*)h->u_raw;
+        c.sigma = (double*)h->sigma;
+        c.kappa = (double*)h->kappa;
         c.tr_prev = (double*)h->tr_prev;
         c.rho = (double*)h->rho;
         c.u = (double*)h->u;
         c.t_dev = h->t_dev;
         if ((rc = prof_mark(h, s, KIND_COLLIDE, true))) return rc;
-        k_collide_stream<Q, P, T><<<grid, 256, 0, s>>>(c, g, p);
+        k_collide_stream<Q, P, T, R><<<grid, 256, 0, s>>>(c, commit_args<R>(h), g, p);
         LBVE_CUDA(cudaGetLastError());
         if ((rc = prof_mark(h, s, KIND_COLLIDE, false))) return rc;
         h->cur ^= 1;
@@ -368,6 +386,13 @@ int lbve_create(const lbve_channel_desc* desc, const double* rho_init, lbve_t** 
         delete h;
         return rc;
     }
+    if (h->D == 2) rc = h->hist_dbl ? sweep_config<2, double>(h) : sweep_config<2, float>(h);
+    else rc = h->hist_dbl ? sweep_config<3, double>(h) : sweep_config<3, float>(h);
+    if (rc || (rc = alloc(h, &h->part, h->hesz * (size_t)h->S * h->NS * Np))) {
+        free_all(h);
+        delete h;
+        return rc;
+    }
     // zero every buffer: rest state, empty history (E = 1 <=> X = 0, kappa = 0), t = 0
     void* zero_bufs[] = {h->pops[0], h->pops[1], h->u_raw, h->u, h->sigma, h->kappa, h->tr_prev, h->X, h->K,
                          h->t_dev, h->flag};
@@ -378,6 +403,16 @@ int lbve_create(const lbve_channel_desc* desc, const double* rho_init, lbve_t** 
         cudaError_t e = cudaMemset(zero_bufs[i], 0, zero_sizes[i]);
         if (e != cudaSuccess) {
             rc = cuda_fail(e, "cudaMemset");
+            free_all(h);
+            delete h;
+            return rc;
+        }
+    }
+    {   // the device step counter holds the index of the step in progress; the first step makes it 0
+        const long long minus_one = -1;
+        cudaError_t e = cudaMemcpy(h->t_dev, &minus_one, sizeof minus_one, cudaMemcpyHostToDevice);
+        if (e != cudaSuccess) {
+            rc = cuda_fail(e, "cudaMemcpy");
             free_all(h);
             delete h;
             return rc;
@@ -477,13 +512,33 @@ int lbve_fields(lbve_t* h, uint32_t mask, double* dst, int32_t dst_is_device, vo
 int lbve_history_apply(lbve_t* h, const double* kappa_dev, double* sigma_dev, void* stream) {
     if (!h || !kappa_dev || !sigma_dev) return LBVE_EINVAL;
     cudaStream_t s = (cudaStream_t)stream;
-    int rc;
-    if (h->D == 2) rc = h->hist_dbl ? launch_history<2, double>(h, kappa_dev, sigma_dev, s)
-                                    : launch_history<2, float>(h, kappa_dev, sigma_dev, s);
-    else rc = h->hist_dbl ? launch_history<3, double>(h, kappa_dev, sigma_dev, s)
-                          : launch_history<3, float>(h, kappa_dev, sigma_dev, s);
-    if (rc) return rc;
     k_advance_t<<<1, 1, 0, s>>>(h->t_dev);
+    LBVE_CUDA(cudaGetLastError());
+    int rc;
+    const Geom g = geom_of(h);
+    const Phys p = phys_of(h);
+    const int grid = (h->N + 255) / 256;
+    if (h->D == 2) {
+        if (h->hist_dbl) {
+            if ((rc = launch_sweep<2, double>(h, s))) return rc;
+            k_commit<2, double><<<grid, 256, 0, s>>>(commit_args<double>(h), kappa_dev, (double*)h->sigma,
+                                                     (double*)h->kappa, sigma_dev, h->t_dev, g, p);
+        } else {
+            if ((rc = launch_sweep<2, float>(h, s))) return rc;
+            k_commit<2, float><<<grid, 256, 0, s>>>(commit_args<float>(h), kappa_dev, (double*)h->sigma,
+                                                    (double*)h->kappa, sigma_dev, h->t_dev, g, p);
+        }
+    } else {
+        if (h->hist_dbl) {
+            if ((rc = launch_sweep<3, double>(h, s))) return rc;
+            k_commit<3, double><<<grid, 256, 0, s>>>(commit_args<double>(h), kappa_dev, (double*)h->sigma,
+                                                     (double*)h->kappa, sigma_dev, h->t_dev, g, p);
+        } else {
+            if ((rc = launch_sweep<3, float>(h, s))) return rc;
+            k_commit<3, float><<<grid, 256, 0, s>>>(commit_args<float>(h), kappa_dev, (double*)h->sigma,
+                                                    (double*)h->kappa, sigma_dev, h->t_dev, g, p);
+        }
+    }
     LBVE_CUDA(cudaGetLastError());
     h->t_host += 1;
     return LBVE_OK;

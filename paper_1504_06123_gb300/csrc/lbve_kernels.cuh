@@ -2,19 +2,21 @@
 //
 // Per step, three launches on one stream:
 //   k_moments        : u_raw = (sum c n + f/2) / sum n                                (Eq. hydrofields)
-//   k_history        : kappa(t) by finite differences; every retained history point advances
-//                      E <- exp(kappa(t-1)) E, forms -d_t'B = E kappa E^T + (.)^T and the modulus of
-//                      Eq. (nlmax), and the trapezoidal sum of Eq. (gitt) gives sigma_struc(t); then
-//                      the block merges of the quasi-logarithmic grid and the new point.  This is the
-//                      O(nodes x points) part and the only one that matters for bandwidth.
-//   k_collide_stream : trace split, density source, BGK collision with the forcing of Eq. (bodyforce),
-//                      push streaming with half-way bounce-back.
+//   k_sweep          : every retained history point advances E <- exp(kappa(t-1)) E, forms
+//                      -d_t'B = E kappa E^T + (.)^T and the modulus of Eq. (nlmax); partial trapezoidal
+//                      sums of Eq. (gitt) per slot chunk.  This is the O(nodes x points) part and the
+//                      only one that matters for bandwidth.
+//   k_collide_stream : per node: kappa(t) by finite differences, sigma_struc(t) from the partials and the
+//                      point created now, the block merges of the quasi-logarithmic grid and the new
+//                      point; then trace split, density source, BGK collision with the forcing of
+//                      Eq. (bodyforce), push streaming with half-way bounce-back.
 //
 // Layouts (device, structure of arrays, every plane padded to Npad nodes):
 //   populations  d_n[q][Npad]   type P   stored as n_q - w_q rho0 (deviation form keeps FP32 exact
 //                                        enough for velocities of 1e-5)
 //   history      X[slot][c][Npad] type R X = E - 1 of each retained point (c < d*d, row-major)
 //                K[slot][c][Npad] type R kappa of each retained point
+//                part[chunk][i][Npad] type R partial sums of the sweep (scratch, rewritten every step)
 //   node fields  (double; O(N) words, negligible traffic next to the history)
 //                u_raw[d][Npad], kappa[d*d][Npad], sigma[nsig][Npad], tr_prev[Npad], drho[Npad] (rho - rho0),
 //                u[d][Npad]
@@ -95,12 +97,15 @@ __device__ __forceinline__ void node_xyz(const Geom& g, int n, int& x, int& y, i
 // K1: raw moments -> u_raw
 // ------------------------------------------------------------------------------------------------
 // Moments are summed in double: exact for float populations up to the last bit of the result.
+// The first kernel of a step also advances the device step counter (it starts at -1), so that the later
+// kernels of the step all read the same t.
 template <int Q, typename P>
 __global__ void __launch_bounds__(256) k_moments(const P* __restrict__ dn, double* __restrict__ u_raw, Geom g,
-                                                 Phys p) {
+                                                 Phys p, long long* t_dev) {
     using L = Lattice<Q>;
     constexpr int D = L::D;
     const int n = blockIdx.x * blockDim.x + threadIdx.x;
+    if (n == 0) *t_dev += 1;
     if (n >= g.N) return;
     double drho = 0, j[3] = {0, 0, 0};
 #pragma unroll
@@ -254,47 +259,41 @@ __device__ __forceinline__ void point_update(real* X, const real* A, const real*
 }
 
 // ------------------------------------------------------------------------------------------------
-// K2: the stress history integral
+// K2: the stress history sweep
 // ------------------------------------------------------------------------------------------------
-template <typename real> struct HistArgs {
-    real* __restrict__ X;             // [L][DD][Npad]
-    real* __restrict__ K;             // [L][DD][Npad]
-    const double* __restrict__ u_raw; // [D][Npad]  (flow path)
-    const double* __restrict__ kappa_in;  // [DD][N] prescribed gradient (test hook) or nullptr
-    double* __restrict__ kappa;       // [DD][Npad] kappa(t) out
-    double* __restrict__ sigma;       // [NS][Npad] sigma_struc(t) out
-    double* __restrict__ sigma_dbl;   // [NS][N] optional copy (test hook) or nullptr
+// VN consecutive values of one component plane, loaded and stored as one vector (16 bytes for
+// 4 floats or 2 doubles).
+template <typename R, int VN> struct alignas(sizeof(R) * VN) Vec { R v[VN]; };
+
+template <typename R> struct SweepArgs {
+    R* __restrict__ X;                // [L][DD][Npad]  E - 1
+    const R* __restrict__ K;          // [L][DD][Npad]  kappa of each point (read only in the sweep)
+    R* __restrict__ part;             // [S][NS][Npad]  partial trapezoid sums per slot chunk (scratch)
     const long long* t_dev;           // step index t
-    int B, C;
+    int B, C, S;                      // grid shape; S slot chunks
 };
 
-// Byte offset of the reduction buffer in the history kernel's shared memory (16-byte aligned).
-__host__ __device__ inline size_t history_red_offset(int L) {
-    const size_t o = (size_t)L * 12 + sizeof(BlockStep) * LBVE_MAXB;
-    return (o + 15) & ~(size_t)15;
-}
+// Shared memory of the sweep: per slot age, weight, partner (L entries each) + the per-block state.
+__host__ __device__ inline size_t sweep_smem_bytes(int L) { return (size_t)L * 12 + sizeof(BlockStep) * LBVE_MAXB; }
 
-template <int D, typename real, int G>
-__host__ __device__ inline size_t history_smem_bytes(int L) {
-    constexpr int NS = D == 2 ? 3 : 6;
-    return history_red_offset(L) + sizeof(real) * (size_t)(G > 1 ? G - 1 : 0) * NS * (256 / G);
-}
-
-// Threads of a CTA: NODES consecutive nodes x G slot groups; group gi handles slots gi, gi+G, ...
-// Shared memory: per slot age (float), weight (float), partner (int) + the per-block state +
-// the cross-group reduction buffer.
-template <int D, typename real, int G>
-__global__ void __launch_bounds__(256) k_history(HistArgs<real> a, Geom g, Phys p) {
+// Persistent warps.  A task is (tile of 32*VN consecutive nodes, chunk of consecutive slots); lane i
+// handles nodes tile*32*VN + i*VN ... + VN-1, so every component plane is read and written with one
+// 16-byte access per lane and 512 contiguous bytes per warp.  Each task writes its partial sum of
+// w G (E kappa E^T + (.)^T) to `part`; k_collide_stream (or k_commit) adds the chunks in a fixed
+// order, so the result does not depend on scheduling.  All points are advanced in place:
+// X <- X + A + A X with A = exp(kappa(t-1)) - 1 (Eq. eeval, newest factor on the left); the older half of
+// a merge uses the average of the two kappa (Sec. III), the newer half is skipped.
+template <int D, typename R, int VN>
+__global__ void __launch_bounds__(256, 2) k_sweep(SweepArgs<R> a, Geom g, Phys p) {
     constexpr int DD = D * D;
     constexpr int NS = D == 2 ? 3 : 6;
-    constexpr int NODES = 256 / G;
+    using V = Vec<R, VN>;
     const int L = a.B * a.C;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     float* s_age = reinterpret_cast<float*>(smem_raw);
     float* s_w = s_age + L;
     int* s_part = reinterpret_cast<int*>(s_w + L);
     BlockStep* s_bs = reinterpret_cast<BlockStep*>(s_part + L);
-    real* s_red = reinterpret_cast<real*>(smem_raw + history_red_offset(L));   // [G-1][NS][NODES]
 
     const long long t = *a.t_dev;
     if (threadIdx.x == 0) sched_step(a.B, a.C, t, s_bs);
@@ -308,94 +307,128 @@ __global__ void __launch_bounds__(256) k_history(HistArgs<real> a, Geom g, Phys 
     }
     __syncthreads();
 
-    const int ln = threadIdx.x % NODES;
-    const int gi = threadIdx.x / NODES;
-    const int n = blockIdx.x * NODES + ln;
     const long long Np = g.Npad;
-    const bool live = n < g.N;
+    const int lane = threadIdx.x & 31;
+    const int gwarp = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+    const int nwarps = gridDim.x * (blockDim.x >> 5);
+    const int tiles = (int)(Np / (32 * VN));
+    const int tasks = tiles * a.S;
+    const int chunk_len = (L + a.S - 1) / a.S;
+    const long long s_last = (long long)(a.B - 1) * a.C + s_bs[a.B - 1].head_prev;
+    const R inv_tau = (R)p.inv_tau, inv_gc = (R)p.inv_gc;
 
-    real acc[NS];
-#pragma unroll
-    for (int i = 0; i < NS; ++i) acc[i] = 0;
-    const real inv_tau = (real)p.inv_tau, inv_gc = (real)p.inv_gc;
-
-    if (live) {
-        // A = exp(kappa(t-1)) - 1; kappa(t-1) is the kappa of the point created last step, held at the
-        // newest slot of the finest block (a rest point, kappa = 0, before the first step).
-        real A[DD];
+    for (int task = gwarp; task < tasks; task += nwarps) {
+        const int tile = task % tiles;
+        const int chunk = task / tiles;
+        const long long n0 = (long long)tile * 32 * VN + lane * VN;
+        // A = exp(kappa(t-1)) - 1 per node; kappa(t-1) is the point created last step (newest slot of
+        // the finest block; a rest point before the first step)
+        R A[VN][DD];
         {
-            const long long s_last = (long long)(a.B - 1) * a.C + s_bs[a.B - 1].head_prev;
-            real kp[DD];
+            R kp[VN][DD];
 #pragma unroll
-            for (int c = 0; c < DD; ++c) kp[c] = a.K[(s_last * DD + c) * Np + n];
-            expm1_mat<D>(kp, A);
+            for (int c = 0; c < DD; ++c) {
+                const V v = *reinterpret_cast<const V*>(a.K + (s_last * DD + c) * Np + n0);
+#pragma unroll
+                for (int j = 0; j < VN; ++j) kp[j][c] = v.v[j];
+            }
+#pragma unroll
+            for (int j = 0; j < VN; ++j) expm1_mat<D>(kp[j], A[j]);
         }
-        for (int l = gi; l < L; l += G) {
-            const float w = s_w[l];
-            if (w == 0.0f) continue;
-            real X[DD], kap[DD];
-            real* Xp = a.X + (long long)l * DD * Np + n;
-            const real* Kp = a.K + (long long)l * DD * Np + n;
+        R acc[VN][NS];
 #pragma unroll
-            for (int c = 0; c < DD; ++c) { X[c] = Xp[c * Np]; kap[c] = Kp[c * Np]; }
+        for (int j = 0; j < VN; ++j)
+#pragma unroll
+            for (int i = 0; i < NS; ++i) acc[j][i] = 0;
+
+        const int l0 = chunk * chunk_len;
+        const int l1 = min(L, l0 + chunk_len);
+        for (int l = l0; l < l1; ++l) {
+            const float w = s_w[l];
+            if (w == 0.0f) continue;                 // same slot for the whole warp: uniform branch
+            R* Xp = a.X + (long long)l * DD * Np + n0;
+            const R* Kp = a.K + (long long)l * DD * Np + n0;
+            R X[VN][DD], kap[VN][DD];
+#pragma unroll
+            for (int c = 0; c < DD; ++c) {
+                const V xv = *reinterpret_cast<const V*>(Xp + c * Np);
+                const V kv = *reinterpret_cast<const V*>(Kp + c * Np);
+#pragma unroll
+                for (int j = 0; j < VN; ++j) { X[j][c] = xv.v[j]; kap[j][c] = kv.v[j]; }
+            }
             const int part = s_part[l];
             if (part >= 0) {   // older half of a merge: kappa averaged with the newer half
-                const real* K2 = a.K + (long long)part * DD * Np + n;
+                const R* K2 = a.K + (long long)part * DD * Np + n0;
 #pragma unroll
-                for (int c = 0; c < DD; ++c) kap[c] = real(0.5) * (kap[c] + K2[c * Np]);
+                for (int c = 0; c < DD; ++c) {
+                    const V kv = *reinterpret_cast<const V*>(K2 + c * Np);
+#pragma unroll
+                    for (int j = 0; j < VN; ++j) kap[j][c] = R(0.5) * (kap[j][c] + kv.v[j]);
+                }
             }
-            point_update<D>(X, A, kap, (real)s_age[l], (real)w, inv_tau, inv_gc, acc);
+            const R age = (R)s_age[l], wr = (R)w;
 #pragma unroll
-            for (int c = 0; c < DD; ++c) Xp[c * Np] = X[c];
+            for (int j = 0; j < VN; ++j) point_update<D>(X[j], A[j], kap[j], age, wr, inv_tau, inv_gc, acc[j]);
+#pragma unroll
+            for (int c = 0; c < DD; ++c) {
+                V xv;
+#pragma unroll
+                for (int j = 0; j < VN; ++j) xv.v[j] = X[j][c];
+                *reinterpret_cast<V*>(Xp + c * Np) = xv;
+            }
+        }
+#pragma unroll
+        for (int i = 0; i < NS; ++i) {
+            V v;
+#pragma unroll
+            for (int j = 0; j < VN; ++j) v.v[j] = acc[j][i];
+            *reinterpret_cast<V*>(a.part + ((long long)chunk * NS + i) * Np + n0) = v;
         }
     }
-    // reduce the slot groups of each node into group 0
-    if (G > 1) {
-        if (gi > 0) {
-#pragma unroll
-            for (int i = 0; i < NS; ++i) s_red[((gi - 1) * NS + i) * NODES + ln] = acc[i];
-        }
-    }
-    __syncthreads();   // also orders every X write of the sweep before the merges below
-    if (gi != 0 || !live) return;
-    if (G > 1) {
-        for (int j = 1; j < G; ++j)
-#pragma unroll
-            for (int i = 0; i < NS; ++i) acc[i] += s_red[((j - 1) * NS + i) * NODES + ln];
-    }
-    // the point created now: age 0, E = 1, weight 1/2, modulus G_inf
-    double ktd[DD];
-    if (a.kappa_in) {
-#pragma unroll
-        for (int c = 0; c < DD; ++c) ktd[c] = a.kappa_in[(long long)c * g.N + n];
-    } else {
-        kappa_fd<D>(a.u_raw, g, n, ktd);
-    }
-    real kt[DD];
-#pragma unroll
-    for (int c = 0; c < DD; ++c) kt[c] = (real)ktd[c];
-    if (D == 2) {
-        acc[0] += real(0.5) * (kt[0] + kt[0]);
-        acc[1] += real(0.5) * (kt[3] + kt[3]);
-        acc[2] += real(0.5) * (kt[1] + kt[2]);
-    } else {
-        acc[0] += real(0.5) * (kt[0] + kt[0]);
-        acc[1] += real(0.5) * (kt[4] + kt[4]);
-        acc[2] += real(0.5) * (kt[8] + kt[8]);
-        acc[3] += real(0.5) * (kt[1] + kt[3]);
-        acc[4] += real(0.5) * (kt[2] + kt[6]);
-        acc[5] += real(0.5) * (kt[5] + kt[7]);
-    }
-#pragma unroll
-    for (int i = 0; i < NS; ++i) {
-        const double s = p.G_inf * (double)acc[i];
-        a.sigma[i * Np + n] = s;
-        if (a.sigma_dbl) a.sigma_dbl[(long long)i * g.N + n] = s;
-    }
-#pragma unroll
-    for (int c = 0; c < DD; ++c) a.kappa[c * Np + n] = ktd[c];
+}
 
-    // block merges, coarsest first, so that every ring slot is read before it is overwritten
+// ------------------------------------------------------------------------------------------------
+// History commit of one node (after the sweep): sigma_struc(t) from the chunk partials plus the point
+// created now (age 0, E = 1, weight 1/2, modulus G_inf), then the block merges (coarsest first, so every
+// ring slot is read before it is overwritten) and the new point entering the finest block.
+// ------------------------------------------------------------------------------------------------
+template <typename R> struct CommitArgs {
+    R* __restrict__ X;
+    R* __restrict__ K;
+    const R* __restrict__ part;       // [S][NS][Npad]
+    int B, C, S;
+};
+
+template <int D, typename R>
+__device__ __forceinline__ void hist_commit(const CommitArgs<R>& a, const BlockStep* s_bs, long long Np, int n,
+                                            const double* ktd, double G_inf, double* sig /* [NS] out */) {
+    constexpr int DD = D * D;
+    constexpr int NS = D == 2 ? 3 : 6;
+    double acc[NS];
+#pragma unroll
+    for (int i = 0; i < NS; ++i) acc[i] = 0.0;
+    for (int c = 0; c < a.S; ++c)
+#pragma unroll
+        for (int i = 0; i < NS; ++i) acc[i] += (double)a.part[((long long)c * NS + i) * Np + n];
+    // the new point, summed in the history's precision like every other point
+    R kt[DD];
+#pragma unroll
+    for (int c = 0; c < DD; ++c) kt[c] = (R)ktd[c];
+    if (D == 2) {
+        acc[0] += (double)(R(0.5) * (kt[0] + kt[0]));
+        acc[1] += (double)(R(0.5) * (kt[3] + kt[3]));
+        acc[2] += (double)(R(0.5) * (kt[1] + kt[2]));
+    } else {
+        acc[0] += (double)(R(0.5) * (kt[0] + kt[0]));
+        acc[1] += (double)(R(0.5) * (kt[4] + kt[4]));
+        acc[2] += (double)(R(0.5) * (kt[8] + kt[8]));
+        acc[3] += (double)(R(0.5) * (kt[1] + kt[3]));
+        acc[4] += (double)(R(0.5) * (kt[2] + kt[6]));
+        acc[5] += (double)(R(0.5) * (kt[5] + kt[7]));
+    }
+#pragma unroll
+    for (int i = 0; i < NS; ++i) sig[i] = G_inf * acc[i];
+
     for (int bb = 1; bb < a.B; ++bb) {
         const BlockStep& b = s_bs[bb];
         if (!b.evict) continue;
@@ -406,18 +439,41 @@ __global__ void __launch_bounds__(256) k_history(HistArgs<real> a, Geom g, Phys 
 #pragma unroll
         for (int c = 0; c < DD; ++c) {
             a.X[(dst * DD + c) * Np + n] = a.X[(src1 * DD + c) * Np + n];
-            a.K[(dst * DD + c) * Np + n] = real(0.5) * (a.K[(src1 * DD + c) * Np + n] + a.K[(src2 * DD + c) * Np + n]);
+            a.K[(dst * DD + c) * Np + n] = R(0.5) * (a.K[(src1 * DD + c) * Np + n] + a.K[(src2 * DD + c) * Np + n]);
         }
     }
-    // the new point enters the finest block
-    {
-        const long long dst = (long long)(a.B - 1) * a.C + s_bs[a.B - 1].head_new;
+    const long long dst = (long long)(a.B - 1) * a.C + s_bs[a.B - 1].head_new;
 #pragma unroll
-        for (int c = 0; c < DD; ++c) {
-            a.X[(dst * DD + c) * Np + n] = real(0);
-            a.K[(dst * DD + c) * Np + n] = kt[c];
-        }
+    for (int c = 0; c < DD; ++c) {
+        a.X[(dst * DD + c) * Np + n] = R(0);
+        a.K[(dst * DD + c) * Np + n] = kt[c];
     }
+}
+
+// Commit alone (history-only test hook): the gradient comes from the caller.
+template <int D, typename R>
+__global__ void __launch_bounds__(256) k_commit(CommitArgs<R> a, const double* __restrict__ kappa_in,
+                                                double* __restrict__ sigma_f, double* __restrict__ kappa_f,
+                                                double* __restrict__ sigma_out, const long long* t_dev, Geom g,
+                                                Phys p) {
+    constexpr int DD = D * D;
+    constexpr int NS = D == 2 ? 3 : 6;
+    __shared__ BlockStep s_bs[LBVE_MAXB];
+    if (threadIdx.x == 0) sched_step(a.B, a.C, *t_dev, s_bs);
+    __syncthreads();
+    const int n = blockIdx.x * blockDim.x + threadIdx.x;
+    if (n >= g.N) return;
+    double ktd[DD], sig[NS];
+#pragma unroll
+    for (int c = 0; c < DD; ++c) ktd[c] = kappa_in[(long long)c * g.N + n];
+    hist_commit<D, R>(a, s_bs, g.Npad, n, ktd, p.G_inf, sig);
+#pragma unroll
+    for (int i = 0; i < NS; ++i) {
+        sigma_f[i * g.Npad + n] = sig[i];
+        sigma_out[(long long)i * g.N + n] = sig[i];
+    }
+#pragma unroll
+    for (int c = 0; c < DD; ++c) kappa_f[c * g.Npad + n] = ktd[c];
 }
 
 // ------------------------------------------------------------------------------------------------
@@ -426,22 +482,40 @@ __global__ void __launch_bounds__(256) k_history(HistArgs<real> a, Geom g, Phys 
 template <typename P> struct CollArgs {
     const P* __restrict__ dn_in;        // [Q][Npad]
     P* __restrict__ dn_out;             // [Q][Npad]
-    const double* __restrict__ sigma;   // [NS][Npad]
+    const double* __restrict__ u_raw;   // [D][Npad]  for kappa(t)
+    double* __restrict__ sigma;         // [NS][Npad] sigma_struc(t) out
+    double* __restrict__ kappa;         // [DD][Npad] kappa(t) out
     double* __restrict__ tr_prev;       // [Npad]
     double* __restrict__ rho;           // [Npad] rho - rho0
     double* __restrict__ u;             // [D][Npad]
-    long long* t_dev;                   // advanced by one thread after the step
+    const long long* t_dev;             // step index t
 };
 
-// T: arithmetic type of the collision (double for double populations; float or double for float).
-template <int Q, typename P, typename T>
-__global__ void __launch_bounds__(256) k_collide_stream(CollArgs<P> a, Geom g, Phys p) {
+// One node per thread: history commit (sigma_struc(t), merges, new point), then the collision with
+// that stress and push streaming.  T: arithmetic type of the collision (double for double populations;
+// float for float).
+template <int Q, typename P, typename T, typename R>
+__global__ void __launch_bounds__(256) k_collide_stream(CollArgs<P> a, CommitArgs<R> h, Geom g, Phys p) {
     using L = Lattice<Q>;
     constexpr int D = L::D;
+    constexpr int DD = D * D;
+    constexpr int NS = D == 2 ? 3 : 6;
+    __shared__ BlockStep s_bs[LBVE_MAXB];
+    if (threadIdx.x == 0) sched_step(h.B, h.C, *a.t_dev, s_bs);
+    __syncthreads();
     const int n = blockIdx.x * blockDim.x + threadIdx.x;
-    if (n == 0) *a.t_dev += 1;   // no kernel of this step reads t after k_history
     if (n >= g.N) return;
     const long long Np = g.Npad;
+    double sg[NS];
+    {
+        double ktd[DD];
+        kappa_fd<D>(a.u_raw, g, n, ktd);
+        hist_commit<D, R>(h, s_bs, Np, n, ktd, p.G_inf, sg);
+#pragma unroll
+        for (int i = 0; i < NS; ++i) a.sigma[i * Np + n] = sg[i];
+#pragma unroll
+        for (int c = 0; c < DD; ++c) a.kappa[c * Np + n] = ktd[c];
+    }
     const T cs2 = T(1.0 / 3.0);
     T dn[Q];
     double drho_raw = 0, jd[3] = {0, 0, 0};
@@ -458,15 +532,15 @@ __global__ void __launch_bounds__(256) k_collide_stream(CollArgs<P> a, Geom g, P
     T S[3][3];
     double trd = 0;
     if (D == 2) {
-        S[0][0] = (T)a.sigma[0 * Np + n]; S[1][1] = (T)a.sigma[1 * Np + n];
-        S[0][1] = S[1][0] = (T)a.sigma[2 * Np + n];
-        trd = a.sigma[0 * Np + n] + a.sigma[1 * Np + n];
+        S[0][0] = (T)sg[0]; S[1][1] = (T)sg[1];
+        S[0][1] = S[1][0] = (T)sg[2];
+        trd = sg[0] + sg[1];
     } else {
-        S[0][0] = (T)a.sigma[0 * Np + n]; S[1][1] = (T)a.sigma[1 * Np + n]; S[2][2] = (T)a.sigma[2 * Np + n];
-        S[0][1] = S[1][0] = (T)a.sigma[3 * Np + n];
-        S[0][2] = S[2][0] = (T)a.sigma[4 * Np + n];
-        S[1][2] = S[2][1] = (T)a.sigma[5 * Np + n];
-        trd = a.sigma[0 * Np + n] + a.sigma[1 * Np + n] + a.sigma[2 * Np + n];
+        S[0][0] = (T)sg[0]; S[1][1] = (T)sg[1]; S[2][2] = (T)sg[2];
+        S[0][1] = S[1][0] = (T)sg[3];
+        S[0][2] = S[2][0] = (T)sg[4];
+        S[1][2] = S[2][1] = (T)sg[5];
+        trd = sg[0] + sg[1] + sg[2];
     }
     double ddr_d = 0;
     if (p.trace_full) ddr_d = -(trd - a.tr_prev[n]) * (3.0 / D);   // -(tr - tr_prev)/(d cs^2)

@@ -73,7 +73,7 @@ typedef struct {
     int32_t trace_coupling;   /* LBVE_TRACE_FULL | LBVE_TRACE_NONE */
 } lbve_channel_desc;
 
-typedef struct lbve lbve_t;   /* opaque; owns every device buffer of one channel */
+typedef struct lbve lbve_t;   /* opaque; owns every device buffer of one channel or of a batch */
 
 /*
  * Create a channel on the current CUDA device: fluid at rest, n_i = w_i rho_init(n) (rho0 where
@@ -86,20 +86,38 @@ typedef struct lbve lbve_t;   /* opaque; owns every device buffer of one channel
  */
 int lbve_create(const lbve_channel_desc* desc, const double* rho_init, lbve_t** out);
 
+/*
+ * Create a batch of n_channels independent channels (for instance the paper's channels of different
+ * width, Sec. IV) advanced together by every lbve_step: one set of launches for all channels.  Each
+ * channel has its own sizes, G_inf, tau, gamma_c, g, tau_lb and trace coupling; the lattice, the history
+ * grid (hist_C, hist_B), the precisions and rho0 must be the same for all.  Channels are stored one
+ * after the other (node order x fastest within each); lbve_channel_nodes gives a channel's range in
+ * the node arrays of lbve_fields.  rho_init: NULL or the initial densities of all nodes in that order.
+ * Errors as lbve_create; EINVAL also when the shared settings differ or n_channels is outside 1..65536.
+ */
+int lbve_create_batch(const lbve_channel_desc* descs, int32_t n_channels, const double* rho_init, lbve_t** out);
+
+/* First node and node count of a channel (0 for a handle made by lbve_create). */
+int lbve_channel_nodes(const lbve_t* h, int32_t channel, int64_t* offset, int64_t* count);
+
 /* Free every device buffer of the handle (synchronises the device).  NULL is ignored. */
 void lbve_destroy(lbve_t* h);
 
-/* Replace the body force (startup / cessation, Sec. IV); takes effect at the next step. */
-int lbve_set_force(lbve_t* h, const double g[3]);
+/*
+ * Replace the body force of one channel (channel = -1: all) -- startup / cessation, Sec. IV.  Stream
+ * ordered: steps enqueued earlier on `stream` still use the old value, later steps the new one.
+ */
+int lbve_set_force(lbve_t* h, int32_t channel, const double g[3], void* stream);
 
-/* Replace G_inf, tau, gamma_c of Eq. (nlmax); takes effect at the next step. */
-int lbve_set_params(lbve_t* h, double G_inf, double tau, double gamma_c);
+/* Replace G_inf, tau, gamma_c of Eq. (nlmax) for one channel (-1: all); ordered like lbve_set_force. */
+int lbve_set_params(lbve_t* h, int32_t channel, double G_inf, double tau, double gamma_c, void* stream);
 
 /*
  * Advance n_steps >= 0 full hybrid steps (Sec. III): moments -> kappa by finite differences -> stress
  * history (advance E, insert/merge per the quasi-logarithmic grid, -d_t'B, modulus of Eq. (nlmax),
  * trapezoidal sum of Eq. (gitt)) -> trace split, density source, BGK collision with the forcing of
- * Eq. (bodyforce) -> streaming with bounce-back.  Asynchronous on `stream`.
+ * Eq. (bodyforce) -> streaming with bounce-back.  Asynchronous on `stream`.  Runs of 16 steps are
+ * replayed from a CUDA graph captured on first use (unless lbve_profile is on).
  */
 int lbve_step(lbve_t* h, int64_t n_steps, void* stream);
 
@@ -143,6 +161,12 @@ int lbve_schedule(int32_t C, int32_t B, int64_t t, int64_t* tp_out, double* w_ou
 
 /* Device bytes held by the handle (populations, history, fields). */
 int lbve_memory_bytes(const lbve_t* h, size_t* bytes);
+
+/*
+ * Launch shape of the history sweep chosen at create by the autotuner: the number of slot chunks each
+ * node's points are split into (tasks = node tiles x chunks) and the number of persistent CTAs.
+ */
+int lbve_sweep_config(const lbve_t* h, int32_t* slot_chunks, int32_t* ctas);
 
 /*
  * Kernel timing for benchmarks: with enable = 1, every later lbve_step records a CUDA event pair on

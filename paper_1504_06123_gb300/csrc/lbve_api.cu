@@ -1,14 +1,16 @@
 // lbve_api.cu -- runtime and C ABI (include/lbve.h) of the hybrid LB library.
 //
-// The handle owns every device buffer of one channel; allocation happens once in lbve_create, after
-// which lbve_step only enqueues kernels on the caller's stream.  The step counter lives in device
-// memory, so a step is a fixed sequence of launches that never needs host state.
+// A handle owns every device buffer of one channel or of a batch of channels (stored one after the
+// other in the node planes); allocation happens once in lbve_create / lbve_create_batch, after which
+// lbve_step only enqueues kernels on the caller's stream.  The step counter and the per-channel
+// parameters live in device memory, so a step is a fixed sequence of launches that needs no host
+// state: lbve_step captures 16 steps into a CUDA graph once and replays it.
 #include <cuda_runtime.h>
 
+#include <algorithm>
 #include <cmath>
 #include <cstdio>
 #include <cstring>
-#include <algorithm>
 #include <mutex>
 #include <new>
 #include <utility>
@@ -28,21 +30,29 @@ int cuda_fail(cudaError_t e, const char* what) {
     return e == cudaErrorMemoryAllocation ? LBVE_ENOMEM : LBVE_ECUDA;
 }
 
-#define LBVE_CUDA(call)                                \
-    do {                                               \
-        cudaError_t e_ = (call);                       \
+#define LBVE_CUDA(call)                                     \
+    do {                                                    \
+        cudaError_t e_ = (call);                            \
         if (e_ != cudaSuccess) return cuda_fail(e_, #call); \
     } while (0)
+
+constexpr int kGraphSteps = 16;   // steps per captured graph
+constexpr int kMaxChannels = 1 << 16;
 
 }  // namespace
 
 struct lbve {
-    lbve_channel_desc d;
+    lbve_channel_desc d;                 // channel 0 (shared settings of a batch: lattice, grid, precisions)
+    std::vector<lbve_channel_desc> descs;
+    int nchan = 1;
     int D, Q, NS, N, L;
     long long Npad;
     int pop_dbl;               // 1: populations stored in double
     int hist_dbl;              // 1: history stored (and advanced) in double
     size_t pesz, hesz;         // element sizes of populations and history
+    std::vector<Chan> chan_host;
+    Chan* chan_dev = nullptr;  // [nchan] per-channel geometry and parameters
+    int* chan_of = nullptr;    // [Npad] channel of every node (batches only)
     void* pops[2] = {nullptr, nullptr};
     int cur = 0;
     void* u_raw = nullptr;
@@ -54,7 +64,7 @@ struct lbve {
     void* X = nullptr;
     void* K = nullptr;
     void* part = nullptr;      // sweep partial sums [S][NS][Npad] (history type)
-    int S = 1;                 // slot chunks of the sweep
+    int S = 1;                 // slot chunks of the sweep (autotuned at create)
     int sweep_grid = 0;        // persistent CTAs of the sweep
     long long* t_dev = nullptr;
     double* red = nullptr;     // reduction scratch (2 doubles)
@@ -63,6 +73,9 @@ struct lbve {
     int64_t t_host = 0;
     size_t bytes = 0;
     int* flag = nullptr;       // non-finite flag of lbve_fields
+    // captured steps: kGraphSteps steps, both population parities (the graph is replayed from cur == 0)
+    cudaGraphExec_t graph = nullptr;
+    cudaStream_t graph_stream = nullptr;
     // kernel timing (lbve_profile): event pairs recorded around each launch of lbve_step
     int profiling = 0;
     std::vector<cudaEvent_t> ev_pool;
@@ -74,11 +87,15 @@ namespace {
 
 void free_all(lbve* h) {
     void* ptrs[] = {h->pops[0], h->pops[1], h->u_raw, h->u, h->rho, h->sigma, h->kappa, h->tr_prev,
-                    h->X, h->K, h->part, h->t_dev, h->red, h->stage, h->flag};
+                    h->X, h->K, h->part, h->t_dev, h->red, h->stage, h->flag, h->chan_dev, h->chan_of};
     for (void* p : ptrs)
         if (p) cudaFree(p);
     for (cudaEvent_t e : h->ev_pool) cudaEventDestroy(e);
     h->ev_pool.clear();
+    if (h->graph) cudaGraphExecDestroy(h->graph);
+    if (h->graph_stream) cudaStreamDestroy(h->graph_stream);
+    h->graph = nullptr;
+    h->graph_stream = nullptr;
 }
 
 // Kernel timing: mark(h, s, kind, true) before a launch and mark(h, s, kind, false) after it.
@@ -108,25 +125,28 @@ int alloc(lbve* h, void** p, size_t bytes) {
 
 Geom geom_of(const lbve* h) {
     Geom g;
-    g.nx = h->d.nx;
-    g.ny = h->d.ny;
-    g.nz = h->d.nz;
-    g.wall_z = h->d.lattice == LBVE_D3Q19 ? h->d.wall_z : 0;
     g.N = h->N;
     g.Npad = h->Npad;
+    g.nchan = h->nchan;
+    g.ch = h->chan_dev;
+    g.chan_of = h->chan_of;
     return g;
 }
 
-Phys phys_of(const lbve* h) {
-    Phys p;
-    p.rho0 = h->d.rho0;
-    p.tau_lb = h->d.tau_lb;
-    for (int a = 0; a < 3; ++a) p.f[a] = h->d.rho0 * h->d.g[a];
-    p.G_inf = h->d.G_inf;
-    p.inv_tau = 1.0 / h->d.tau;
-    p.inv_gc = std::isinf(h->d.gamma_c) ? 0.0 : 1.0 / h->d.gamma_c;
-    p.trace_full = h->d.trace_coupling == LBVE_TRACE_FULL;
-    return p;
+// Per-channel device entry from a description (parameters of Sec. III / Eq. nlmax).
+void fill_chan(const lbve_channel_desc& d, int off, Chan* c) {
+    c->off = off;
+    c->nx = d.nx;
+    c->ny = d.ny;
+    c->nz = d.nz;
+    c->wall_z = d.lattice == LBVE_D3Q19 ? d.wall_z : 0;
+    c->trace_full = d.trace_coupling == LBVE_TRACE_FULL;
+    c->rho0 = d.rho0;
+    c->tau_lb = d.tau_lb;
+    for (int a = 0; a < 3; ++a) c->f[a] = d.rho0 * d.g[a];
+    c->G_inf = d.G_inf;
+    c->inv_tau = 1.0 / d.tau;
+    c->inv_gc = std::isinf(d.gamma_c) ? 0.0 : 1.0 / d.gamma_c;
 }
 
 int check_desc(const lbve_channel_desc* d) {
@@ -154,34 +174,14 @@ int check_desc(const lbve_channel_desc* d) {
     return LBVE_OK;
 }
 
+// Settings every channel of a batch shares: the lattice, the history grid, the precisions, rho0.
+bool same_batch_settings(const lbve_channel_desc& a, const lbve_channel_desc& b) {
+    return a.lattice == b.lattice && a.hist_C == b.hist_C && a.hist_B == b.hist_B &&
+           a.hist_storage == b.hist_storage && a.pop_precision == b.pop_precision && a.rho0 == b.rho0;
+}
+
 // Values per lane of the sweep (one 16-byte access): 4 floats or 2 doubles; 3D halves it (registers).
 template <int D, typename R> constexpr int sweep_vn() { return (sizeof(R) == 4 ? 4 : 2) / (D == 3 ? 2 : 1); }
-
-template <int D, typename R>
-int sweep_config(lbve* h) {
-    constexpr int VN = sweep_vn<D, R>();
-    const size_t smem = sweep_smem_bytes(h->L);
-    if (smem > 48 * 1024)
-        LBVE_CUDA(cudaFuncSetAttribute(k_sweep<D, R, VN>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-    int dev = 0, sms = 0, per_sm = 0;
-    LBVE_CUDA(cudaGetDevice(&dev));
-    LBVE_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
-    LBVE_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_sweep<D, R, VN>, 256, smem));
-    if (per_sm < 1) per_sm = 1;
-    const long long warps = (long long)sms * per_sm * 8;
-    const long long tiles = h->Npad / (32 * VN);
-    // about eight tasks per resident warp, so that the last round costs little; chunks of >= 8 slots
-    long long S = (8 * warps + tiles - 1) / tiles;
-    const long long Smax = h->L >= 16 ? h->L / 8 : 1;
-    if (S > Smax) S = Smax;
-    if (S < 1) S = 1;
-    h->S = (int)S;
-    const long long tasks = tiles * S;
-    const long long grid_full = (long long)sms * per_sm;
-    h->sweep_grid = (int)std::min<long long>(grid_full, (tasks + 7) / 8);
-    if (h->sweep_grid < 1) h->sweep_grid = 1;
-    return LBVE_OK;
-}
 
 template <int D, typename R>
 int launch_sweep(lbve* h, cudaStream_t s) {
@@ -194,8 +194,70 @@ int launch_sweep(lbve* h, cudaStream_t s) {
     a.B = h->d.hist_B;
     a.C = h->d.hist_C;
     a.S = h->S;
-    k_sweep<D, R, VN><<<h->sweep_grid, 256, sweep_smem_bytes(h->L), s>>>(a, geom_of(h), phys_of(h));
+    k_sweep<D, R, VN><<<h->sweep_grid, 256, sweep_smem_bytes(h->L), s>>>(a, geom_of(h));
     LBVE_CUDA(cudaGetLastError());
+    return LBVE_OK;
+}
+
+// Autotuner of the sweep: candidate slot-chunk counts S (tasks per resident warp from about 2 to 32),
+// each timed over a few launches on the freshly created, all-rest history (which the sweep leaves
+// unchanged: exp(0) - 1 = 0); the fastest is kept.  The partial-sum buffer is sized for the largest
+// candidate and then trimmed by reallocation.
+template <int D, typename R>
+int sweep_autotune(lbve* h) {
+    constexpr int VN = sweep_vn<D, R>();
+    const size_t smem = sweep_smem_bytes(h->L);
+    if (smem > 48 * 1024)
+        LBVE_CUDA(cudaFuncSetAttribute(k_sweep<D, R, VN>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    int dev = 0, sms = 0, per_sm = 0;
+    LBVE_CUDA(cudaGetDevice(&dev));
+    LBVE_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+    LBVE_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_sweep<D, R, VN>, 256, smem));
+    if (per_sm < 1) per_sm = 1;
+    const long long warps = (long long)sms * per_sm * 8;
+    const long long tiles = h->Npad / (32 * VN);
+    const long long Smax = h->L >= 16 ? h->L / 8 : 1;
+    std::vector<long long> cand;
+    for (long long k : {2, 4, 8, 16, 32}) {
+        long long S = (k * warps + tiles - 1) / tiles;
+        S = std::max(1ll, std::min(S, Smax));
+        if (std::find(cand.begin(), cand.end(), S) == cand.end()) cand.push_back(S);
+    }
+    const long long Sbig = *std::max_element(cand.begin(), cand.end());
+    int rc = alloc(h, &h->part, h->hesz * (size_t)Sbig * h->NS * h->Npad);
+    if (rc) return rc;
+    LBVE_CUDA(cudaMemset(h->part, 0, h->hesz * (size_t)Sbig * h->NS * h->Npad));
+    const long long grid_full = (long long)sms * per_sm;
+    long long bestS = cand[0];
+    float best = 1e30f;
+    if (cand.size() > 1) {
+        cudaEvent_t e0, e1;
+        LBVE_CUDA(cudaEventCreate(&e0));
+        LBVE_CUDA(cudaEventCreate(&e1));
+        for (long long S : cand) {
+            h->S = (int)S;
+            h->sweep_grid = (int)std::max(1ll, std::min(grid_full, (tiles * S + 7) / 8));
+            if ((rc = launch_sweep<D, R>(h, 0))) return rc;   // warm-up
+            LBVE_CUDA(cudaEventRecord(e0, 0));
+            for (int r = 0; r < 3; ++r)
+                if ((rc = launch_sweep<D, R>(h, 0))) return rc;
+            LBVE_CUDA(cudaEventRecord(e1, 0));
+            LBVE_CUDA(cudaEventSynchronize(e1));
+            float ms = 0.f;
+            LBVE_CUDA(cudaEventElapsedTime(&ms, e0, e1));
+            if (ms < best) { best = ms; bestS = S; }
+        }
+        cudaEventDestroy(e0);
+        cudaEventDestroy(e1);
+    }
+    h->S = (int)bestS;
+    h->sweep_grid = (int)std::max(1ll, std::min(grid_full, (tiles * bestS + 7) / 8));
+    if (bestS < Sbig) {   // keep only what the chosen S needs
+        cudaFree(h->part);
+        h->bytes -= h->hesz * (size_t)Sbig * h->NS * h->Npad;
+        h->part = nullptr;
+        if ((rc = alloc(h, &h->part, h->hesz * (size_t)bestS * h->NS * h->Npad))) return rc;
+    }
     return LBVE_OK;
 }
 
@@ -213,39 +275,86 @@ CommitArgs<R> commit_args(lbve* h) {
 
 __global__ void k_advance_t(long long* t) { *t += 1; }
 
+// One hybrid step: moments -> history sweep -> commit + collide + stream.  pops[cur] -> pops[cur ^ 1].
 // P: population storage type, R: history type, T: collision arithmetic type.
 template <int Q, typename P, typename R, typename T>
-int step_impl(lbve* h, int64_t n, cudaStream_t s) {
+int one_step(lbve* h, int cur, cudaStream_t s) {
     constexpr int D = Lattice<Q>::D;
     const Geom g = geom_of(h);
-    const Phys p = phys_of(h);
     const int grid = (h->N + 255) / 256;
+    const P* din = (const P*)h->pops[cur];
+    P* dout = (P*)h->pops[cur ^ 1];
+    int rc;
+    if ((rc = prof_mark(h, s, KIND_MOMENTS, true))) return rc;
+    k_moments<Q, P><<<grid, 256, 0, s>>>(din, (double*)h->u_raw, g, h->t_dev);
+    LBVE_CUDA(cudaGetLastError());
+    if ((rc = prof_mark(h, s, KIND_MOMENTS, false))) return rc;
+    if ((rc = prof_mark(h, s, KIND_HISTORY, true))) return rc;
+    if ((rc = launch_sweep<D, R>(h, s))) return rc;
+    if ((rc = prof_mark(h, s, KIND_HISTORY, false))) return rc;
+    CollArgs<P> c;
+    c.dn_in = din;
+    c.dn_out = dout;
+    c.u_raw = (const double*)h->u_raw;
+    c.sigma = (double*)h->sigma;
+    c.kappa = (double*)h->kappa;
+    c.tr_prev = (double*)h->tr_prev;
+    c.rho = (double*)h->rho;
+    c.u = (double*)h->u;
+    c.t_dev = h->t_dev;
+    if ((rc = prof_mark(h, s, KIND_COLLIDE, true))) return rc;
+    k_collide_stream<Q, P, T, R><<<grid, 256, 0, s>>>(c, commit_args<R>(h), g);
+    LBVE_CUDA(cudaGetLastError());
+    if ((rc = prof_mark(h, s, KIND_COLLIDE, false))) return rc;
+    return LBVE_OK;
+}
+
+template <int Q, typename P, typename R, typename T>
+int capture_graph(lbve* h) {
+    if (!h->graph_stream) LBVE_CUDA(cudaStreamCreateWithFlags(&h->graph_stream, cudaStreamNonBlocking));
+    cudaGraph_t graph = nullptr;
+    LBVE_CUDA(cudaStreamBeginCapture(h->graph_stream, cudaStreamCaptureModeThreadLocal));
+    int rc = LBVE_OK;
+    for (int i = 0; i < kGraphSteps && rc == LBVE_OK; ++i) rc = one_step<Q, P, R, T>(h, i & 1, h->graph_stream);
+    cudaError_t e = cudaStreamEndCapture(h->graph_stream, &graph);
+    if (rc) {
+        if (graph) cudaGraphDestroy(graph);
+        return rc;
+    }
+    if (e != cudaSuccess) return cuda_fail(e, "cudaStreamEndCapture");
+    e = cudaGraphInstantiate(&h->graph, graph, 0);
+    cudaGraphDestroy(graph);
+    if (e != cudaSuccess) {
+        h->graph = nullptr;
+        return cuda_fail(e, "cudaGraphInstantiate");
+    }
+    return LBVE_OK;
+}
+
+template <int Q, typename P, typename R, typename T>
+int step_impl(lbve* h, int64_t n, cudaStream_t s) {
+    int rc;
+    // whole graphs of kGraphSteps steps (an even count, so populations end where they started); the
+    // graph is recorded for cur == 0, so a pending odd step is run first.  Profiling records per-launch
+    // events and therefore launches step by step.
+    if (!h->profiling && n >= kGraphSteps) {
+        if (h->cur == 1) {
+            if ((rc = one_step<Q, P, R, T>(h, 1, s))) return rc;
+            h->cur = 0;
+            h->t_host += 1;
+            --n;
+        }
+        if (n >= kGraphSteps) {
+            if (!h->graph && (rc = capture_graph<Q, P, R, T>(h))) return rc;
+            while (n >= kGraphSteps) {
+                LBVE_CUDA(cudaGraphLaunch(h->graph, s));
+                h->t_host += kGraphSteps;
+                n -= kGraphSteps;
+            }
+        }
+    }
     for (int64_t i = 0; i < n; ++i) {
-        const P* din = (const P*)h->pops[h->cur];
-        P* dout = (P*)h->pops[h->cur ^ 1];
-        int rc;
-        if ((rc = prof_mark(h, s, KIND_MOMENTS, true))) return rc;
-        k_moments<Q, P><<<grid, 256, 0, s>>>(din, (double*)h->u_raw, g, p, h->t_dev);
-        LBVE_CUDA(cudaGetLastError());
-        if ((rc = prof_mark(h, s, KIND_MOMENTS, false))) return rc;
-        if ((rc = prof_mark(h, s, KIND_HISTORY, true))) return rc;
-        rc = launch_sweep<D, R>(h, s);
-        if (rc) return rc;
-        if ((rc = prof_mark(h, s, KIND_HISTORY, false))) return rc;
-        CollArgs<P> c;
-        c.dn_in = din;
-        c.dn_out = dout;
-        c.u_raw = (const double*)h->u_raw;
-        c.sigma = (double*)h->sigma;
-        c.kappa = (double*)h->kappa;
-        c.tr_prev = (double*)h->tr_prev;
-        c.rho = (double*)h->rho;
-        c.u = (double*)h->u;
-        c.t_dev = h->t_dev;
-        if ((rc = prof_mark(h, s, KIND_COLLIDE, true))) return rc;
-        k_collide_stream<Q, P, T, R><<<grid, 256, 0, s>>>(c, commit_args<R>(h), g, p);
-        LBVE_CUDA(cudaGetLastError());
-        if ((rc = prof_mark(h, s, KIND_COLLIDE, false))) return rc;
+        if ((rc = one_step<Q, P, R, T>(h, h->cur, s))) return rc;
         h->cur ^= 1;
         h->t_host += 1;
     }
@@ -263,7 +372,7 @@ __global__ void k_init(P* dn, double* rho, long long Npad, int N, int Q, const d
     rho[n] = r - rho0;
 }
 
-template <typename real>
+template <typename P>
 int init_state(lbve* h, const double* rho_init_host) {
     double w[19];
     for (int q = 0; q < h->Q; ++q) w[q] = h->Q == 9 ? Lattice<9>::w(q) : Lattice<19>::w(q);
@@ -274,8 +383,8 @@ int init_state(lbve* h, const double* rho_init_host) {
     if (e == cudaSuccess && rho_init_host)
         e = cudaMemcpy(tmp + h->Q, rho_init_host, sizeof(double) * h->N, cudaMemcpyHostToDevice);
     if (e == cudaSuccess) {
-        k_init<real><<<(h->N + 255) / 256, 256>>>((real*)h->pops[0], (double*)h->rho, h->Npad, h->N, h->Q,
-                                                  rho_init_host ? tmp + h->Q : nullptr, h->d.rho0, tmp);
+        k_init<P><<<(h->N + 255) / 256, 256>>>((P*)h->pops[0], (double*)h->rho, h->Npad, h->N, h->Q,
+                                               rho_init_host ? tmp + h->Q : nullptr, h->d.rho0, tmp);
         e = cudaGetLastError();
     }
     if (e == cudaSuccess) e = cudaDeviceSynchronize();
@@ -341,6 +450,109 @@ int mass_impl(lbve* h, double* sum_n, double* sum_drho, cudaStream_t s) {
     return LBVE_OK;
 }
 
+int create_impl(const lbve_channel_desc* descs, int32_t n, const double* rho_init, lbve_t** out) {
+    if (!out) return LBVE_EINVAL;
+    *out = nullptr;
+    if (!descs || n < 1 || n > kMaxChannels) return LBVE_EINVAL;
+    long long Ntot = 0;
+    for (int c = 0; c < n; ++c) {
+        int rc = check_desc(&descs[c]);
+        if (rc) return rc;
+        if (!same_batch_settings(descs[0], descs[c])) return LBVE_EINVAL;
+        Ntot += (long long)descs[c].nx * descs[c].ny * descs[c].nz;
+    }
+    if (Ntot > (1ll << 30)) return LBVE_EINVAL;
+    if (rho_init) {
+        for (long long i = 0; i < Ntot; ++i)
+            if (!std::isfinite(rho_init[i]) || !(rho_init[i] > 0)) return LBVE_EINVAL;
+    }
+    lbve* h = new (std::nothrow) lbve();
+    if (!h) return LBVE_ENOMEM;
+    const lbve_channel_desc* desc = &descs[0];
+    h->d = *desc;
+    h->descs.assign(descs, descs + n);
+    h->nchan = n;
+    h->D = desc->lattice == LBVE_D2Q9 ? 2 : 3;
+    h->Q = desc->lattice;
+    h->NS = h->D == 2 ? 3 : 6;
+    h->N = (int)Ntot;
+    h->L = desc->hist_C * desc->hist_B;
+    h->Npad = ((long long)h->N + 127) / 128 * 128;
+    h->pop_dbl = desc->pop_precision == LBVE_F64;
+    h->hist_dbl = desc->hist_storage == LBVE_F64;
+    h->pesz = h->pop_dbl ? 8 : 4;
+    h->hesz = h->hist_dbl ? 8 : 4;
+    h->chan_host.resize(n);
+    {
+        int off = 0;
+        for (int c = 0; c < n; ++c) {
+            fill_chan(descs[c], off, &h->chan_host[c]);
+            off += descs[c].nx * descs[c].ny * descs[c].nz;
+        }
+    }
+    const long long Np = h->Npad;
+    const int DD = h->D * h->D;
+    const size_t fe = sizeof(double);
+    int rc;
+    auto fail = [&](int code) {
+        free_all(h);
+        delete h;
+        return code;
+    };
+    if ((rc = alloc(h, &h->pops[0], h->pesz * h->Q * Np)) || (rc = alloc(h, &h->pops[1], h->pesz * h->Q * Np)) ||
+        (rc = alloc(h, &h->u_raw, fe * h->D * Np)) || (rc = alloc(h, &h->u, fe * h->D * Np)) ||
+        (rc = alloc(h, &h->rho, fe * Np)) || (rc = alloc(h, &h->sigma, fe * h->NS * Np)) ||
+        (rc = alloc(h, &h->kappa, fe * DD * Np)) || (rc = alloc(h, &h->tr_prev, fe * Np)) ||
+        (rc = alloc(h, &h->X, h->hesz * (size_t)h->L * DD * Np)) ||
+        (rc = alloc(h, &h->K, h->hesz * (size_t)h->L * DD * Np)) ||
+        (rc = alloc(h, (void**)&h->t_dev, sizeof(long long))) || (rc = alloc(h, (void**)&h->red, 2 * sizeof(double))) ||
+        (rc = alloc(h, (void**)&h->flag, sizeof(int))) ||
+        (rc = alloc(h, (void**)&h->chan_dev, sizeof(Chan) * n)))
+        return fail(rc);
+    {
+        cudaError_t e = cudaMemcpy(h->chan_dev, h->chan_host.data(), sizeof(Chan) * n, cudaMemcpyHostToDevice);
+        if (e != cudaSuccess) return fail(cuda_fail(e, "cudaMemcpy"));
+    }
+    if (n > 1) {   // channel of every node (padding belongs to the last channel)
+        if ((rc = alloc(h, (void**)&h->chan_of, sizeof(int) * Np))) return fail(rc);
+        std::vector<int> co((size_t)Np, n - 1);
+        for (int c = 0; c < n; ++c) {
+            const int nn = descs[c].nx * descs[c].ny * descs[c].nz;
+            std::fill(co.begin() + h->chan_host[c].off, co.begin() + h->chan_host[c].off + nn, c);
+        }
+        cudaError_t e = cudaMemcpy(h->chan_of, co.data(), sizeof(int) * Np, cudaMemcpyHostToDevice);
+        if (e != cudaSuccess) return fail(cuda_fail(e, "cudaMemcpy"));
+    }
+    // zero every buffer: rest state, empty history (E = 1 <=> X = 0, kappa = 0)
+    void* zero_bufs[] = {h->pops[0], h->pops[1], h->u_raw, h->u, h->sigma, h->kappa, h->tr_prev, h->X, h->K, h->flag};
+    size_t zero_sizes[] = {h->pesz * h->Q * Np, h->pesz * h->Q * Np, fe * h->D * Np, fe * h->D * Np,
+                           fe * h->NS * Np, fe * DD * Np, fe * Np, h->hesz * (size_t)h->L * DD * Np,
+                           h->hesz * (size_t)h->L * DD * Np, sizeof(int)};
+    for (int i = 0; i < 10; ++i) {
+        cudaError_t e = cudaMemset(zero_bufs[i], 0, zero_sizes[i]);
+        if (e != cudaSuccess) return fail(cuda_fail(e, "cudaMemset"));
+    }
+    {   // the device step counter holds the index of the step in progress; the first step makes it 0
+        const long long minus_one = -1;
+        cudaError_t e = cudaMemcpy(h->t_dev, &minus_one, sizeof minus_one, cudaMemcpyHostToDevice);
+        if (e != cudaSuccess) return fail(cuda_fail(e, "cudaMemcpy"));
+    }
+    if (h->D == 2) rc = h->hist_dbl ? sweep_autotune<2, double>(h) : sweep_autotune<2, float>(h);
+    else rc = h->hist_dbl ? sweep_autotune<3, double>(h) : sweep_autotune<3, float>(h);
+    if (rc) return fail(rc);
+    rc = h->pop_dbl ? init_state<double>(h, rho_init) : init_state<float>(h, rho_init);
+    if (rc) return fail(rc);
+    *out = h;
+    return LBVE_OK;
+}
+
+int push_chan(lbve* h, int c, cudaStream_t s) {
+    // the kernels read the table; stream order keeps earlier steps on `s` with the old values.  The
+    // source is pageable host memory, so the copy has taken the entry when the call returns.
+    LBVE_CUDA(cudaMemcpyAsync(h->chan_dev + c, &h->chan_host[c], sizeof(Chan), cudaMemcpyHostToDevice, s));
+    return LBVE_OK;
+}
+
 }  // namespace
 
 // =================================================================================================
@@ -349,82 +561,18 @@ int mass_impl(lbve* h, double* sum_n, double* sum_drho, cudaStream_t s) {
 extern "C" {
 
 int lbve_create(const lbve_channel_desc* desc, const double* rho_init, lbve_t** out) {
-    if (!out) return LBVE_EINVAL;
-    *out = nullptr;
-    int rc = check_desc(desc);
-    if (rc) return rc;
-    if (rho_init) {
-        const long long N = (long long)desc->nx * desc->ny * desc->nz;
-        for (long long i = 0; i < N; ++i)
-            if (!std::isfinite(rho_init[i]) || !(rho_init[i] > 0)) return LBVE_EINVAL;
-    }
-    lbve* h = new (std::nothrow) lbve();
-    if (!h) return LBVE_ENOMEM;
-    h->d = *desc;
-    h->D = desc->lattice == LBVE_D2Q9 ? 2 : 3;
-    h->Q = desc->lattice;
-    h->NS = h->D == 2 ? 3 : 6;
-    h->N = desc->nx * desc->ny * desc->nz;
-    h->L = desc->hist_C * desc->hist_B;
-    h->Npad = ((long long)h->N + 127) / 128 * 128;
-    h->pop_dbl = desc->pop_precision == LBVE_F64;
-    h->hist_dbl = desc->hist_storage == LBVE_F64;
-    h->pesz = h->pop_dbl ? 8 : 4;
-    h->hesz = h->hist_dbl ? 8 : 4;
-    const long long Np = h->Npad;
-    const int DD = h->D * h->D;
-    const size_t fe = sizeof(double);
-    if ((rc = alloc(h, &h->pops[0], h->pesz * h->Q * Np)) || (rc = alloc(h, &h->pops[1], h->pesz * h->Q * Np)) ||
-        (rc = alloc(h, &h->u_raw, fe * h->D * Np)) || (rc = alloc(h, &h->u, fe * h->D * Np)) ||
-        (rc = alloc(h, &h->rho, fe * Np)) || (rc = alloc(h, &h->sigma, fe * h->NS * Np)) ||
-        (rc = alloc(h, &h->kappa, fe * DD * Np)) || (rc = alloc(h, &h->tr_prev, fe * Np)) ||
-        (rc = alloc(h, &h->X, h->hesz * (size_t)h->L * DD * Np)) ||
-        (rc = alloc(h, &h->K, h->hesz * (size_t)h->L * DD * Np)) ||
-        (rc = alloc(h, (void**)&h->t_dev, sizeof(long long))) || (rc = alloc(h, (void**)&h->red, 2 * sizeof(double))) ||
-        (rc = alloc(h, (void**)&h->flag, sizeof(int)))) {
-        free_all(h);
-        delete h;
-        return rc;
-    }
-    if (h->D == 2) rc = h->hist_dbl ? sweep_config<2, double>(h) : sweep_config<2, float>(h);
-    else rc = h->hist_dbl ? sweep_config<3, double>(h) : sweep_config<3, float>(h);
-    if (rc || (rc = alloc(h, &h->part, h->hesz * (size_t)h->S * h->NS * Np))) {
-        free_all(h);
-        delete h;
-        return rc;
-    }
-    // zero every buffer: rest state, empty history (E = 1 <=> X = 0, kappa = 0), t = 0
-    void* zero_bufs[] = {h->pops[0], h->pops[1], h->u_raw, h->u, h->sigma, h->kappa, h->tr_prev, h->X, h->K,
-                         h->t_dev, h->flag};
-    size_t zero_sizes[] = {h->pesz * h->Q * Np, h->pesz * h->Q * Np, fe * h->D * Np, fe * h->D * Np,
-                           fe * h->NS * Np, fe * DD * Np, fe * Np, h->hesz * (size_t)h->L * DD * Np,
-                           h->hesz * (size_t)h->L * DD * Np, sizeof(long long), sizeof(int)};
-    for (int i = 0; i < 11; ++i) {
-        cudaError_t e = cudaMemset(zero_bufs[i], 0, zero_sizes[i]);
-        if (e != cudaSuccess) {
-            rc = cuda_fail(e, "cudaMemset");
-            free_all(h);
-            delete h;
-            return rc;
-        }
-    }
-    {   // the device step counter holds the index of the step in progress; the first step makes it 0
-        const long long minus_one = -1;
-        cudaError_t e = cudaMemcpy(h->t_dev, &minus_one, sizeof minus_one, cudaMemcpyHostToDevice);
-        if (e != cudaSuccess) {
-            rc = cuda_fail(e, "cudaMemcpy");
-            free_all(h);
-            delete h;
-            return rc;
-        }
-    }
-    rc = h->pop_dbl ? init_state<double>(h, rho_init) : init_state<float>(h, rho_init);
-    if (rc) {
-        free_all(h);
-        delete h;
-        return rc;
-    }
-    *out = h;
+    return create_impl(desc, 1, rho_init, out);
+}
+
+int lbve_create_batch(const lbve_channel_desc* descs, int32_t n_channels, const double* rho_init, lbve_t** out) {
+    return create_impl(descs, n_channels, rho_init, out);
+}
+
+int lbve_channel_nodes(const lbve_t* h, int32_t channel, int64_t* offset, int64_t* count) {
+    if (!h || !offset || !count || channel < 0 || channel >= h->nchan) return LBVE_EINVAL;
+    const lbve_channel_desc& d = h->descs[channel];
+    *offset = h->chan_host[channel].off;
+    *count = (int64_t)d.nx * d.ny * d.nz;
     return LBVE_OK;
 }
 
@@ -435,23 +583,43 @@ void lbve_destroy(lbve_t* h) {
     delete h;
 }
 
-int lbve_set_force(lbve_t* h, const double g[3]) {
-    if (!h || !g) return LBVE_EINVAL;
+int lbve_set_force(lbve_t* h, int32_t channel, const double g[3], void* stream) {
+    if (!h || !g || channel < -1 || channel >= h->nchan) return LBVE_EINVAL;
     for (int a = 0; a < 3; ++a)
         if (!std::isfinite(g[a])) return LBVE_EINVAL;
-    for (int a = 0; a < 3; ++a) h->d.g[a] = g[a];
+    const int c0 = channel < 0 ? 0 : channel, c1 = channel < 0 ? h->nchan : channel + 1;
+    for (int c = c0; c < c1; ++c) {
+        for (int a = 0; a < 3; ++a) {
+            h->descs[c].g[a] = g[a];
+            h->chan_host[c].f[a] = h->descs[c].rho0 * g[a];
+        }
+        int rc = push_chan(h, c, (cudaStream_t)stream);
+        if (rc) return rc;
+    }
+    if (channel <= 0) h->d = h->descs[0];
     return LBVE_OK;
 }
 
-int lbve_set_params(lbve_t* h, double G_inf, double tau, double gamma_c) {
-    if (!h) return LBVE_EINVAL;
-    lbve_channel_desc d = h->d;
-    d.G_inf = G_inf;
-    d.tau = tau;
-    d.gamma_c = gamma_c;
-    int rc = check_desc(&d);
-    if (rc) return rc;
-    h->d = d;
+int lbve_set_params(lbve_t* h, int32_t channel, double G_inf, double tau, double gamma_c, void* stream) {
+    if (!h || channel < -1 || channel >= h->nchan) return LBVE_EINVAL;
+    const int c0 = channel < 0 ? 0 : channel, c1 = channel < 0 ? h->nchan : channel + 1;
+    for (int c = c0; c < c1; ++c) {
+        lbve_channel_desc d = h->descs[c];
+        d.G_inf = G_inf;
+        d.tau = tau;
+        d.gamma_c = gamma_c;
+        const int rc = check_desc(&d);
+        if (rc) return rc;
+    }
+    for (int c = c0; c < c1; ++c) {
+        h->descs[c].G_inf = G_inf;
+        h->descs[c].tau = tau;
+        h->descs[c].gamma_c = gamma_c;
+        fill_chan(h->descs[c], h->chan_host[c].off, &h->chan_host[c]);
+        int rc = push_chan(h, c, (cudaStream_t)stream);
+        if (rc) return rc;
+    }
+    if (channel <= 0) h->d = h->descs[0];
     return LBVE_OK;
 }
 
@@ -516,27 +684,26 @@ int lbve_history_apply(lbve_t* h, const double* kappa_dev, double* sigma_dev, vo
     LBVE_CUDA(cudaGetLastError());
     int rc;
     const Geom g = geom_of(h);
-    const Phys p = phys_of(h);
     const int grid = (h->N + 255) / 256;
     if (h->D == 2) {
         if (h->hist_dbl) {
             if ((rc = launch_sweep<2, double>(h, s))) return rc;
             k_commit<2, double><<<grid, 256, 0, s>>>(commit_args<double>(h), kappa_dev, (double*)h->sigma,
-                                                     (double*)h->kappa, sigma_dev, h->t_dev, g, p);
+                                                     (double*)h->kappa, sigma_dev, h->t_dev, g);
         } else {
             if ((rc = launch_sweep<2, float>(h, s))) return rc;
             k_commit<2, float><<<grid, 256, 0, s>>>(commit_args<float>(h), kappa_dev, (double*)h->sigma,
-                                                    (double*)h->kappa, sigma_dev, h->t_dev, g, p);
+                                                    (double*)h->kappa, sigma_dev, h->t_dev, g);
         }
     } else {
         if (h->hist_dbl) {
             if ((rc = launch_sweep<3, double>(h, s))) return rc;
             k_commit<3, double><<<grid, 256, 0, s>>>(commit_args<double>(h), kappa_dev, (double*)h->sigma,
-                                                     (double*)h->kappa, sigma_dev, h->t_dev, g, p);
+                                                     (double*)h->kappa, sigma_dev, h->t_dev, g);
         } else {
             if ((rc = launch_sweep<3, float>(h, s))) return rc;
             k_commit<3, float><<<grid, 256, 0, s>>>(commit_args<float>(h), kappa_dev, (double*)h->sigma,
-                                                    (double*)h->kappa, sigma_dev, h->t_dev, g, p);
+                                                    (double*)h->kappa, sigma_dev, h->t_dev, g);
         }
     }
     LBVE_CUDA(cudaGetLastError());
@@ -576,6 +743,13 @@ int lbve_schedule(int32_t C, int32_t B, int64_t t, int64_t* tp_out, double* w_ou
 int lbve_memory_bytes(const lbve_t* h, size_t* bytes) {
     if (!h || !bytes) return LBVE_EINVAL;
     *bytes = h->bytes;
+    return LBVE_OK;
+}
+
+int lbve_sweep_config(const lbve_t* h, int32_t* slot_chunks, int32_t* ctas) {
+    if (!h || !slot_chunks || !ctas) return LBVE_EINVAL;
+    *slot_chunks = h->S;
+    *ctas = h->sweep_grid;
     return LBVE_OK;
 }
 

@@ -72,25 +72,36 @@ template <> struct Lattice<19> {
 // ------------------------------------------------------------------------------------------------
 // Geometry and parameters shared by the kernels
 // ------------------------------------------------------------------------------------------------
-struct Geom {
+// One channel of a batch (a single channel is a batch of one).  Channels are stored one after the
+// other: channel c owns nodes off .. off + nx*ny*nz - 1, x fastest.  Kept in device memory, so that
+// changing a force or a parameter does not change any kernel argument (captured graphs stay valid).
+struct Chan {
+    int off;          // first node of the channel
     int nx, ny, nz;   // nodes per axis
     int wall_z;       // walls at z = -1/2, nz - 1/2
-    int N;            // nx*ny*nz
-    long long Npad;   // plane stride (multiple of 128)
-};
-
-struct Phys {
+    int trace_full;   // Eq. (bodyforce) with the density source
     double rho0, tau_lb;
     double f[3];      // force density rho0 g
     double G_inf, inv_tau, inv_gc;
-    int trace_full;
 };
 
-__device__ __forceinline__ void node_xyz(const Geom& g, int n, int& x, int& y, int& z) {
-    x = n % g.nx;
-    const int r = n / g.nx;
-    y = r % g.ny;
-    z = r / g.ny;
+struct Geom {
+    int N;                 // all nodes of all channels
+    long long Npad;        // plane stride (multiple of 128)
+    int nchan;
+    const Chan* ch;        // [nchan]
+    const int* chan_of;    // [Npad] channel of every node (nullptr for a single channel)
+};
+
+__device__ __forceinline__ int chan_index(const Geom& g, long long n) { return g.chan_of ? g.chan_of[n] : 0; }
+
+// Coordinates of node n inside its channel.
+__device__ __forceinline__ void node_xyz(const Chan& c, int n, int& x, int& y, int& z) {
+    const int l = n - c.off;
+    x = l % c.nx;
+    const int r = l / c.nx;
+    y = r % c.ny;
+    z = r / c.ny;
 }
 
 // ------------------------------------------------------------------------------------------------
@@ -101,12 +112,13 @@ __device__ __forceinline__ void node_xyz(const Geom& g, int n, int& x, int& y, i
 // kernels of the step all read the same t.
 template <int Q, typename P>
 __global__ void __launch_bounds__(256) k_moments(const P* __restrict__ dn, double* __restrict__ u_raw, Geom g,
-                                                 Phys p, long long* t_dev) {
+                                                 long long* t_dev) {
     using L = Lattice<Q>;
     constexpr int D = L::D;
     const int n = blockIdx.x * blockDim.x + threadIdx.x;
     if (n == 0) *t_dev += 1;
     if (n >= g.N) return;
+    const Chan& p = g.ch[chan_index(g, n)];
     double drho = 0, j[3] = {0, 0, 0};
 #pragma unroll
     for (int q = 0; q < Q; ++q) {
@@ -135,29 +147,29 @@ __device__ __forceinline__ real d_axis(real um, real u0, real up, int i, int n, 
 }
 
 template <int D, typename real>
-__device__ __forceinline__ void kappa_fd(const real* __restrict__ u, const Geom& g, int n, real* kap) {
+__device__ __forceinline__ void kappa_fd(const real* __restrict__ u, long long Npad, const Chan& c, int n, real* kap) {
     int x, y, z;
-    node_xyz(g, n, x, y, z);
-    const int xm = (x == 0 ? g.nx - 1 : x - 1), xp = (x == g.nx - 1 ? 0 : x + 1);
-    const int ym = (y == 0 ? y : y - 1), yp = (y == g.ny - 1 ? y : y + 1);
-    const int nxm = xm + g.nx * (y + g.ny * z), nxp = xp + g.nx * (y + g.ny * z);
-    const int nym = x + g.nx * (ym + g.ny * z), nyp = x + g.nx * (yp + g.ny * z);
+    node_xyz(c, n, x, y, z);
+    const int xm = (x == 0 ? c.nx - 1 : x - 1), xp = (x == c.nx - 1 ? 0 : x + 1);
+    const int ym = (y == 0 ? y : y - 1), yp = (y == c.ny - 1 ? y : y + 1);
+    const int nxm = c.off + xm + c.nx * (y + c.ny * z), nxp = c.off + xp + c.nx * (y + c.ny * z);
+    const int nym = c.off + x + c.nx * (ym + c.ny * z), nyp = c.off + x + c.nx * (yp + c.ny * z);
 #pragma unroll
     for (int a = 0; a < D; ++a) {
-        const real* ua = u + (long long)a * g.Npad;
+        const real* ua = u + (long long)a * Npad;
         const real u0 = ua[n];
-        kap[a * D + 0] = d_axis(ua[nxm], u0, ua[nxp], x, g.nx, true);
-        kap[a * D + 1] = d_axis(ua[nym], u0, ua[nyp], y, g.ny, false);
+        kap[a * D + 0] = d_axis(ua[nxm], u0, ua[nxp], x, c.nx, true);
+        kap[a * D + 1] = d_axis(ua[nym], u0, ua[nyp], y, c.ny, false);
     }
     if (D == 3) {
         int zm, zp;
-        if (g.wall_z) { zm = (z == 0 ? z : z - 1); zp = (z == g.nz - 1 ? z : z + 1); }
-        else { zm = (z == 0 ? g.nz - 1 : z - 1); zp = (z == g.nz - 1 ? 0 : z + 1); }
-        const int nzm = x + g.nx * (y + g.ny * zm), nzp = x + g.nx * (y + g.ny * zp);
+        if (c.wall_z) { zm = (z == 0 ? z : z - 1); zp = (z == c.nz - 1 ? z : z + 1); }
+        else { zm = (z == 0 ? c.nz - 1 : z - 1); zp = (z == c.nz - 1 ? 0 : z + 1); }
+        const int nzm = c.off + x + c.nx * (y + c.ny * zm), nzp = c.off + x + c.nx * (y + c.ny * zp);
 #pragma unroll
         for (int a = 0; a < D; ++a) {
-            const real* ua = u + (long long)a * g.Npad;
-            kap[a * D + (D - 1)] = d_axis(ua[nzm], ua[n], ua[nzp], z, g.nz, !g.wall_z);
+            const real* ua = u + (long long)a * Npad;
+            kap[a * D + (D - 1)] = d_axis(ua[nzm], ua[n], ua[nzp], z, c.nz, !c.wall_z);
         }
     }
 }
@@ -284,7 +296,7 @@ __host__ __device__ inline size_t sweep_smem_bytes(int L) { return (size_t)L * 1
 // X <- X + A + A X with A = exp(kappa(t-1)) - 1 (Eq. eeval, newest factor on the left); the older half of
 // a merge uses the average of the two kappa (Sec. III), the newer half is skipped.
 template <int D, typename R, int VN>
-__global__ void __launch_bounds__(256, 2) k_sweep(SweepArgs<R> a, Geom g, Phys p) {
+__global__ void __launch_bounds__(256, 2) k_sweep(SweepArgs<R> a, Geom g) {
     constexpr int DD = D * D;
     constexpr int NS = D == 2 ? 3 : 6;
     using V = Vec<R, VN>;
@@ -315,12 +327,19 @@ __global__ void __launch_bounds__(256, 2) k_sweep(SweepArgs<R> a, Geom g, Phys p
     const int tasks = tiles * a.S;
     const int chunk_len = (L + a.S - 1) / a.S;
     const long long s_last = (long long)(a.B - 1) * a.C + s_bs[a.B - 1].head_prev;
-    const R inv_tau = (R)p.inv_tau, inv_gc = (R)p.inv_gc;
 
     for (int task = gwarp; task < tasks; task += nwarps) {
         const int tile = task % tiles;
         const int chunk = task / tiles;
         const long long n0 = (long long)tile * 32 * VN + lane * VN;
+        // relaxation rates of each node's channel (Eq. nlmax)
+        R inv_tau[VN], inv_gc[VN];
+#pragma unroll
+        for (int j = 0; j < VN; ++j) {
+            const Chan& c = g.ch[chan_index(g, n0 + j)];
+            inv_tau[j] = (R)c.inv_tau;
+            inv_gc[j] = (R)c.inv_gc;
+        }
         // A = exp(kappa(t-1)) - 1 per node; kappa(t-1) is the point created last step (newest slot of
         // the finest block; a rest point before the first step)
         R A[VN][DD];
@@ -368,7 +387,7 @@ __global__ void __launch_bounds__(256, 2) k_sweep(SweepArgs<R> a, Geom g, Phys p
             }
             const R age = (R)s_age[l], wr = (R)w;
 #pragma unroll
-            for (int j = 0; j < VN; ++j) point_update<D>(X[j], A[j], kap[j], age, wr, inv_tau, inv_gc, acc[j]);
+            for (int j = 0; j < VN; ++j) point_update<D>(X[j], A[j], kap[j], age, wr, inv_tau[j], inv_gc[j], acc[j]);
 #pragma unroll
             for (int c = 0; c < DD; ++c) {
                 V xv;
@@ -454,8 +473,7 @@ __device__ __forceinline__ void hist_commit(const CommitArgs<R>& a, const BlockS
 template <int D, typename R>
 __global__ void __launch_bounds__(256) k_commit(CommitArgs<R> a, const double* __restrict__ kappa_in,
                                                 double* __restrict__ sigma_f, double* __restrict__ kappa_f,
-                                                double* __restrict__ sigma_out, const long long* t_dev, Geom g,
-                                                Phys p) {
+                                                double* __restrict__ sigma_out, const long long* t_dev, Geom g) {
     constexpr int DD = D * D;
     constexpr int NS = D == 2 ? 3 : 6;
     __shared__ BlockStep s_bs[LBVE_MAXB];
@@ -466,7 +484,7 @@ __global__ void __launch_bounds__(256) k_commit(CommitArgs<R> a, const double* _
     double ktd[DD], sig[NS];
 #pragma unroll
     for (int c = 0; c < DD; ++c) ktd[c] = kappa_in[(long long)c * g.N + n];
-    hist_commit<D, R>(a, s_bs, g.Npad, n, ktd, p.G_inf, sig);
+    hist_commit<D, R>(a, s_bs, g.Npad, n, ktd, g.ch[chan_index(g, n)].G_inf, sig);
 #pragma unroll
     for (int i = 0; i < NS; ++i) {
         sigma_f[i * g.Npad + n] = sig[i];
@@ -495,7 +513,7 @@ template <typename P> struct CollArgs {
 // that stress and push streaming.  T: arithmetic type of the collision (double for double populations;
 // float for float).
 template <int Q, typename P, typename T, typename R>
-__global__ void __launch_bounds__(256) k_collide_stream(CollArgs<P> a, CommitArgs<R> h, Geom g, Phys p) {
+__global__ void __launch_bounds__(256) k_collide_stream(CollArgs<P> a, CommitArgs<R> h, Geom g) {
     using L = Lattice<Q>;
     constexpr int D = L::D;
     constexpr int DD = D * D;
@@ -506,10 +524,11 @@ __global__ void __launch_bounds__(256) k_collide_stream(CollArgs<P> a, CommitArg
     const int n = blockIdx.x * blockDim.x + threadIdx.x;
     if (n >= g.N) return;
     const long long Np = g.Npad;
+    const Chan& p = g.ch[chan_index(g, n)];
     double sg[NS];
     {
         double ktd[DD];
-        kappa_fd<D>(a.u_raw, g, n, ktd);
+        kappa_fd<D>(a.u_raw, Np, p, n, ktd);
         hist_commit<D, R>(h, s_bs, Np, n, ktd, p.G_inf, sg);
 #pragma unroll
         for (int i = 0; i < NS; ++i) a.sigma[i * Np + n] = sg[i];
@@ -572,7 +591,7 @@ __global__ void __launch_bounds__(256) k_collide_stream(CollArgs<P> a, CommitArg
     for (int c = 0; c < D; ++c) trX += Xf[c][c];
 
     int x, y, z;
-    node_xyz(g, n, x, y, z);
+    node_xyz(p, n, x, y, z);
 #pragma unroll
     for (int q = 0; q < Q; ++q) {
         const int cq[3] = {L::cx(q), L::cy(q), L::cz(q)};
@@ -597,16 +616,16 @@ __global__ void __launch_bounds__(256) k_collide_stream(CollArgs<P> a, CommitArg
         const P post = (P)(dn[q] - omega * (dn[q] - dneq) + Fq);
         // push with half-way bounce-back
         int xd = x + cq[0];
-        xd = xd < 0 ? g.nx - 1 : (xd >= g.nx ? 0 : xd);
+        xd = xd < 0 ? p.nx - 1 : (xd >= p.nx ? 0 : xd);
         const int yd = y + cq[1];
-        bool wall = yd < 0 || yd >= g.ny;
+        bool wall = yd < 0 || yd >= p.ny;
         int zd = z + cq[2];
         if (D == 3) {
-            if (g.wall_z) wall = wall || zd < 0 || zd >= g.nz;
-            else zd = zd < 0 ? g.nz - 1 : (zd >= g.nz ? 0 : zd);
+            if (p.wall_z) wall = wall || zd < 0 || zd >= p.nz;
+            else zd = zd < 0 ? p.nz - 1 : (zd >= p.nz ? 0 : zd);
         }
         if (wall) a.dn_out[L::opp(q) * Np + n] = post;
-        else a.dn_out[q * Np + (xd + g.nx * (yd + g.ny * zd))] = post;
+        else a.dn_out[q * Np + (p.off + xd + p.nx * (yd + p.ny * zd))] = post;
     }
     a.rho[n] = drho_d;
 #pragma unroll

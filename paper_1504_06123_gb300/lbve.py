@@ -30,7 +30,7 @@ EXPORTS = [
     "lbve_create", "lbve_destroy", "lbve_set_force", "lbve_set_params", "lbve_step", "lbve_get_time",
     "lbve_fields", "lbve_fields_count", "lbve_history_apply", "lbve_mass", "lbve_schedule",
     "lbve_memory_bytes", "lbve_strerror", "lbve_last_cuda_error", "lbve_profile", "lbve_profile_read",
-    "lbve_fields_host_fixed",
+    "lbve_fields_host_fixed", "lbve_create_batch", "lbve_channel_nodes", "lbve_sweep_config",
 ]
 
 
@@ -70,8 +70,11 @@ def load(path: str | None = None):
         lib.lbve_create.argtypes = [C.POINTER(lbve_channel_desc), dp, C.POINTER(vp)]
         lib.lbve_destroy.argtypes = [vp]
         lib.lbve_destroy.restype = None
-        lib.lbve_set_force.argtypes = [vp, dp]
-        lib.lbve_set_params.argtypes = [vp, C.c_double, C.c_double, C.c_double]
+        lib.lbve_create_batch.argtypes = [C.POINTER(lbve_channel_desc), i32, dp, C.POINTER(vp)]
+        lib.lbve_channel_nodes.argtypes = [vp, i32, C.POINTER(i64), C.POINTER(i64)]
+        lib.lbve_sweep_config.argtypes = [vp, C.POINTER(i32), C.POINTER(i32)]
+        lib.lbve_set_force.argtypes = [vp, i32, dp, vp]
+        lib.lbve_set_params.argtypes = [vp, i32, C.c_double, C.c_double, C.c_double, vp]
         lib.lbve_step.argtypes = [vp, i64, vp]
         lib.lbve_get_time.argtypes = [vp, C.POINTER(i64)]
         lib.lbve_fields.argtypes = [vp, C.c_uint32, vp, i32, vp]
@@ -139,17 +142,42 @@ def lbve_create(desc: lbve_channel_desc, rho_init: np.ndarray | None = None) -> 
     return h.value
 
 
+def lbve_create_batch(descs, rho_init: np.ndarray | None = None) -> int:
+    lib = load()
+    arr = (lbve_channel_desc * len(descs))(*descs)
+    h = C.c_void_p()
+    ri = None
+    if rho_init is not None:
+        ri = np.ascontiguousarray(rho_init, dtype=np.float64).ravel()
+    rc = lib.lbve_create_batch(arr, len(descs), ri.ctypes.data_as(C.POINTER(C.c_double)) if ri is not None else None,
+                               C.byref(h))
+    _check(rc, "lbve_create_batch")
+    return h.value
+
+
+def lbve_channel_nodes(h: int, channel: int):
+    off, cnt = C.c_int64(), C.c_int64()
+    _check(load().lbve_channel_nodes(h, channel, C.byref(off), C.byref(cnt)), "lbve_channel_nodes")
+    return off.value, cnt.value
+
+
+def lbve_sweep_config(h: int):
+    s, g = C.c_int32(), C.c_int32()
+    _check(load().lbve_sweep_config(h, C.byref(s), C.byref(g)), "lbve_sweep_config")
+    return s.value, g.value
+
+
 def lbve_destroy(h: int) -> None:
     load().lbve_destroy(h)
 
 
-def lbve_set_force(h: int, g) -> None:
+def lbve_set_force(h: int, g, channel: int = -1, stream=None) -> None:
     gg = (C.c_double * 3)(*[float(v) for v in g])
-    _check(load().lbve_set_force(h, gg), "lbve_set_force")
+    _check(load().lbve_set_force(h, channel, gg, _stream(stream)), "lbve_set_force")
 
 
-def lbve_set_params(h: int, G_inf: float, tau: float, gamma_c: float) -> None:
-    _check(load().lbve_set_params(h, G_inf, tau, gamma_c), "lbve_set_params")
+def lbve_set_params(h: int, G_inf: float, tau: float, gamma_c: float, channel: int = -1, stream=None) -> None:
+    _check(load().lbve_set_params(h, channel, G_inf, tau, gamma_c, _stream(stream)), "lbve_set_params")
 
 
 def lbve_step(h: int, n_steps: int, stream=None) -> None:
@@ -246,13 +274,20 @@ def make_desc(lattice=LBVE_D2Q9, nx=4, ny=32, nz=1, *, tau_lb=0.9, rho0=1.0, G_i
 
 
 class Channel:
-    """Owns one lbve handle.  fields() returns host arrays in the oracle's [node][component] layout."""
+    """Owns one lbve handle (one channel, or a batch when given a list of descriptions).  fields() returns
+    host arrays in the oracle's [node][component] layout; channel_fields(c) slices one channel."""
 
-    def __init__(self, desc: lbve_channel_desc, rho_init=None):
-        self.desc = desc
-        self.d = 2 if desc.lattice == LBVE_D2Q9 else 3
-        self.N = desc.nx * desc.ny * desc.nz
-        self.h = lbve_create(desc, rho_init)
+    def __init__(self, desc, rho_init=None):
+        if isinstance(desc, (list, tuple)):
+            self.descs = list(desc)
+            self.desc = self.descs[0]
+            self.h = lbve_create_batch(self.descs, rho_init)
+        else:
+            self.descs = [desc]
+            self.desc = desc
+            self.h = lbve_create(desc, rho_init)
+        self.d = 2 if self.desc.lattice == LBVE_D2Q9 else 3
+        self.N = sum(d.nx * d.ny * d.nz for d in self.descs)
 
     def close(self):
         if getattr(self, "h", None):
@@ -272,11 +307,16 @@ class Channel:
     def step(self, n: int = 1, stream=None):
         lbve_step(self.h, n, stream)
 
-    def set_force(self, g):
-        lbve_set_force(self.h, g)
+    def set_force(self, g, channel: int = -1, stream=None):
+        lbve_set_force(self.h, g, channel, stream)
 
-    def set_params(self, G_inf, tau, gamma_c):
-        lbve_set_params(self.h, G_inf, tau, gamma_c)
+    def set_params(self, G_inf, tau, gamma_c, channel: int = -1, stream=None):
+        lbve_set_params(self.h, G_inf, tau, gamma_c, channel, stream)
+
+    def channel_fields(self, c: int, fields: dict | None = None) -> dict:
+        f = self.fields() if fields is None else fields
+        off, cnt = lbve_channel_nodes(self.h, c)
+        return {k: v[off:off + cnt] for k, v in f.items()}
 
     def fields(self, stream=None) -> dict:
         d, N = self.d, self.N

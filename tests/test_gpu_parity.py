@@ -239,3 +239,93 @@ def test_large_channel_columns_vs_oracle():
         # every column bitwise identical to the first (no noise: the flow is x-invariant)
         assert np.array_equal(g, np.broadcast_to(g[:, :1], g.shape))
     ch.close()
+
+
+# ---------------------------------------------------------------------------------------------
+# Batches: channels of different width and parameters advanced by one set of launches
+# (and graph replay), each compared with its own oracle run; force switched off in one channel only
+# ---------------------------------------------------------------------------------------------
+BATCH = [
+    dict(nx=4, ny=8, tau_lb=0.9, G_inf=0.01, tau=50.0, gamma_c=0.1, g=2e-5),
+    dict(nx=4, ny=13, tau_lb=0.8, G_inf=0.02, tau=120.0, gamma_c=0.3, g=1e-5),
+    dict(nx=2, ny=32, tau_lb=0.9, G_inf=0.005, tau=300.0, gamma_c=math.inf, g=5e-6),
+    dict(nx=3, ny=5, tau_lb=1.1, G_inf=0.0, tau=10.0, gamma_c=0.1, g=3e-5),
+    dict(nx=4, ny=20, tau_lb=0.9, G_inf=0.015, tau=80.0, gamma_c=0.05, g=1e-5),
+]
+
+
+@pytest.mark.parametrize("prec", [PLAIN, ALL64])
+def test_batched_channels_vs_oracle(prec):
+    C, B = 16, 4
+    descs = [L.make_desc(L.LBVE_D2Q9, c["nx"], c["ny"], tau_lb=c["tau_lb"], G_inf=c["G_inf"], tau=c["tau"],
+                         gamma_c=c["gamma_c"], g=(c["g"], 0, 0), C=C, B=B, precision=prec[0], hist_storage=prec[1])
+             for c in BATCH]
+    Ntot = sum(c["nx"] * c["ny"] for c in BATCH)
+    rho = inputs.initial_density(Ntot, 1e-5, seed=9)
+    ch = L.Channel(descs, rho)
+    orcs, off = [], 0
+    for c in BATCH:
+        n = c["nx"] * c["ny"]
+        orcs.append(oracle.Channel(oracle.D2Q9, c["nx"], c["ny"], tau_lb=c["tau_lb"], G_inf=c["G_inf"], tau=c["tau"],
+                                   gamma_c=c["gamma_c"], g=(c["g"], 0, 0), C=C, B=B, rho_init=rho[off:off + n]))
+        off += n
+    t = 0
+    for cp in (1, 37, 200, 260, 400):
+        ch.step(cp - t)
+        for o in orcs:
+            o.step(cp - t)
+        t = cp
+        f = ch.fields()
+        for i, o in enumerate(orcs):
+            compare(ch.channel_fields(i, f), o.fields(), TOL[prec], f"batch channel {i} t={t}")
+        if t == 200:   # cessation in channel 1 only
+            ch.set_force((0, 0, 0), channel=1)
+            orcs[1].set_force((0, 0, 0))
+    ch.close()
+
+
+def test_batched_ducts_vs_oracle():
+    descs = [L.make_desc(L.LBVE_D3Q19, 3, 6, 6, tau_lb=0.9, G_inf=0.01, tau=40.0, gamma_c=0.1, g=(2e-5, 0, 0),
+                         C=8, B=2, precision=F64, hist_storage=F32),
+             L.make_desc(L.LBVE_D3Q19, 2, 4, 7, tau_lb=0.8, G_inf=0.02, tau=25.0, gamma_c=0.2, g=(1e-5, 0, 0),
+                         C=8, B=2, precision=F64, hist_storage=F32)]
+    ch = L.Channel(descs)
+    orcs = [oracle.Channel(oracle.D3Q19, 3, 6, 6, tau_lb=0.9, G_inf=0.01, tau=40.0, gamma_c=0.1, g=(2e-5, 0, 0),
+                           C=8, B=2),
+            oracle.Channel(oracle.D3Q19, 2, 4, 7, tau_lb=0.8, G_inf=0.02, tau=25.0, gamma_c=0.2, g=(1e-5, 0, 0),
+                           C=8, B=2)]
+    for n in (3, 50):
+        ch.step(n)
+        for o in orcs:
+            o.step(n)
+        f = ch.fields()
+        for i, o in enumerate(orcs):
+            compare(ch.channel_fields(i, f), o.fields(), TOL[PLAIN], f"duct {i} t={ch.t}")
+    ch.close()
+
+
+def test_batch_rejects_mixed_history_grids():
+    a = L.make_desc(nx=2, ny=4, C=8, B=2)
+    b = L.make_desc(nx=2, ny=4, C=16, B=2)
+    with pytest.raises(L.LbveError) as e:
+        L.lbve_create_batch([a, b])
+    assert e.value.status == L.LBVE_EINVAL
+
+
+def test_graph_replay_matches_single_steps():
+    """lbve_step replays captured 16-step graphs; the result is bitwise that of single launches."""
+    kw = dict(nx=5, ny=12, G_inf=0.01, tau=40.0, gamma_c=0.1, g=(1e-5, 0, 0), C=8, B=3, precision=F64,
+              hist_storage=F32)
+    a = L.Channel(L.make_desc(**kw))
+    b = L.Channel(L.make_desc(**kw))
+    a.step(3)
+    a.step(45)             # one odd step, then graphs of 16, then the rest
+    for _ in range(48):
+        b.step(1)
+    fa, fb = a.fields(), b.fields()
+    for k in fa:
+        assert np.array_equal(fa[k], fb[k]), k
+    s, ctas = L.lbve_sweep_config(a.h)
+    assert s >= 1 and ctas >= 1
+    a.close()
+    b.close()

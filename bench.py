@@ -45,6 +45,9 @@ def parse():
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--workload", choices=["channel", "batched", "duct"], default="channel",
+                    help="channel: the 1024 x 512 D2Q9 channel (the benchmark line); batched: 64 channels of "
+                         "uneven width; duct: the D3Q19 128^3 square duct")
     ap.add_argument("--nx", type=int, default=None,
                     help="narrower channel (same rows, same history) for profiler captures; not a bench line")
     return ap.parse_args()
@@ -187,8 +190,29 @@ def run_reference(args, rank, world):
     print(json.dumps(line), flush=True)
 
 
+def workload_descs(args, L, configs):
+    """(name, descs, rho_init, notes) of the selected workload."""
+    if args.workload == "channel":
+        w = configs.plain_channel_large()
+        if args.nx:
+            w.nx = args.nx
+        return f"channel_{w.nx}x{w.ny}_L{w.L}", [w.desc()], w.rho_init(), {
+            "lattice": "D2Q9", "blocks_B": w.B, "block_C": w.C, "tau_lb": w.tau_lb, "G_inf": w.G_inf, "tau": w.tau,
+            "gamma_c": w.gamma_c, "g": w.g}
+    if args.workload == "duct":
+        w = configs.duct_3d()
+        if args.nx:
+            w.nx = args.nx
+        return f"duct_{w.nx}x{w.ny}x{w.nz}_L{w.L}", [w.desc()], w.rho_init(), {
+            "lattice": "D3Q19", "blocks_B": w.B, "block_C": w.C, "tau_lb": w.tau_lb, "G_inf": w.G_inf, "tau": w.tau,
+            "gamma_c": w.gamma_c, "g": w.g}
+    ws = configs.batched_channels()
+    return f"batch64_channels_L{ws[0].L}", [w.desc() for w in ws], None, {
+        "lattice": "D2Q9", "channels": len(ws), "widths": [w.ny for w in ws], "blocks_B": ws[0].B,
+        "block_C": ws[0].C}
+
+
 def run_ours(args, rank, world, local_rank):
-    import numpy as np
     import torch
     import torch.distributed as dist
 
@@ -210,19 +234,21 @@ def run_ours(args, rank, world, local_rank):
         dist.all_reduce(t, op=dist.ReduceOp.MAX)
         return float(t.item())
 
-    w = configs.plain_channel_large()
-    if args.nx:
-        w.nx = args.nx
+    name, descs, rho, notes = workload_descs(args, L, configs)
+    d0 = descs[0]
+    N = sum(d.nx * d.ny * d.nz for d in descs)
+    D = 2 if d0.lattice == L.LBVE_D2Q9 else 3
+    hist_bytes = 4 if d0.hist_storage == L.LBVE_F32 else 8
+    bytes_per_update = 3 * D * D * hist_bytes     # read X, write X, read kappa
     stream = torch.cuda.current_stream()
-    ch = L.Channel(w.desc(), w.rho_init())
+    ch = L.Channel(descs if len(descs) > 1 else descs[0], rho)
     K, W = args.steps, args.warmup
     ch.step(W, stream)
     torch.cuda.synchronize()
-    pts = points_per_step(w.C, w.B, W, K, L)
-    updates_rank = w.N * sum(pts)
-    mem_points = [p - 1 for p in pts]           # the new point of each step is not read from memory
+    pts = points_per_step(d0.hist_C, d0.hist_B, W, K, L)
+    updates_rank = N * sum(pts)
 
-    L.lbve_profile(ch.h, True)
+    # timed region: K steps as a user runs them (16-step graphs replayed)
     ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     with ClockSampler(local_rank) as clk:
         barrier()
@@ -233,31 +259,57 @@ def run_ours(args, rank, world, local_rank):
         torch.cuda.synchronize()
         barrier()
     ms = ev0.elapsed_time(ev1)
-    kms, launches = L.lbve_profile_read(ch.h)
-    L.lbve_profile(ch.h, False)
     ms_max = max_over_ranks(ms)
     value = updates_rank * world / (ms_max / 1e3)
-    mlups = w.N * K * world / (ms_max / 1e3) / 1e6
+    mlups = N * K * world / (ms_max / 1e3) / 1e6
 
-    # roofline of the dominant kernel (the history sweep k_sweep), from its own events
+    # per-kernel device time from events around every launch of a further profiled segment
+    Kp = max(8, min(K, 64))
+    L.lbve_profile(ch.h, True)
+    ch.step(Kp, stream)
+    kms, launches = L.lbve_profile_read(ch.h)
+    L.lbve_profile(ch.h, False)
+    pts_p = points_per_step(d0.hist_C, d0.hist_B, W + K, Kp, L)
     hist_ms = kms[1] / max(launches[1], 1)
-    alg_bytes = BYTES_PER_UPDATE * w.N * (sum(mem_points) / len(mem_points))
+    alg_bytes = bytes_per_update * N * (sum(pts_p) - Kp) / Kp   # the new point is not read from memory
     peak, peak_kind = peaks()
     achieved = alg_bytes / (hist_ms / 1e3) / 1e9
-    traffic = recorded_traffic()
-
+    traffic = recorded_traffic() if args.workload == "channel" and not args.nx else None
+    S, ctas = L.lbve_sweep_config(ch.h)
     ch.close()
-    # end to end through the public C ABI, as a user runs the workload: create the channel from the host
-    # initial density (H2D), advance K steps, read u and sigma back to pinned host memory (D2H), destroy
+
+    extra = {}
+    if args.workload == "batched":
+        # the plain form: one handle per channel, each stepped with its own launches (no batching, no graphs)
+        hs = [L.Channel(d) for d in descs]
+        Kq = max(4, K // 8)
+        for h in hs:
+            h.step(2, stream)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        for _ in range(Kq):
+            for h in hs:
+                L.lbve_step(h.h, 1, stream)
+        torch.cuda.synchronize()
+        dtq = max_over_ranks(time.perf_counter() - t0)
+        ptsq = points_per_step(d0.hist_C, d0.hist_B, 2, Kq, L)
+        plain = N * sum(ptsq) * world / dtq
+        for h in hs:
+            h.close()
+        extra = {"plain_per_channel": {"value": plain, "unit": UNIT, "ms_per_step": 1e3 * dtq / Kq,
+                                       "launches_per_step": 3 * len(descs)},
+                 "chosen_vs_plain": value / plain}
+
+    # end to end through the public C ABI, as a user runs the workload: create from the host initial
+    # density (H2D), advance K steps, read u and sigma back to pinned host memory (D2H), destroy
     e2e = None
     if not args.no_e2e:
         mask = L.LBVE_FIELD_U | L.LBVE_FIELD_SIGMA
-        rho = w.rho_init()
-        host = torch.empty((2 + 3) * w.N, dtype=torch.float64, pin_memory=True)
+        host = torch.empty((D + (3 if D == 2 else 6)) * N, dtype=torch.float64, pin_memory=True)
         barrier()
         torch.cuda.synchronize()
         t0 = time.perf_counter()
-        h = L.lbve_create(w.desc(), rho)
+        h = L.lbve_create_batch(descs, rho) if len(descs) > 1 else L.lbve_create(d0, rho)
         L.lbve_step(h, K, stream)
         rc = L.load().lbve_fields(h, mask, host.data_ptr(), 0, int(stream.cuda_stream) or None)
         torch.cuda.synchronize()
@@ -265,27 +317,30 @@ def run_ours(args, rank, world, local_rank):
         L.lbve_destroy(h)
         if rc != 0:
             raise RuntimeError(f"lbve_fields failed: {rc}")
-        pts_e = points_per_step(w.C, w.B, 0, K, L)
-        e2e = {"value": w.N * sum(pts_e) * world / dt, "unit": UNIT,
-               "h2d_bytes_per_step": (8 * w.N if rho is not None else 0) / K,
+        pts_e = points_per_step(d0.hist_C, d0.hist_B, 0, K, L)
+        e2e = {"value": N * sum(pts_e) * world / dt, "unit": UNIT,
+               "h2d_bytes_per_step": (8 * N if rho is not None else 0) / K,
                "d2h_bytes_per_step": 8 * host.numel() / K, "steps": K,
                "includes": "create (allocation, autotune, initial density upload), K steps, field read, destroy"}
 
     cpu = None
-    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+    if rank == 0 and world == 1 and not args.no_cpu_baseline and args.workload == "channel":
         val, sample, *_ = oracle_sample()
         cpu = {"value": val, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": sample}
 
     if rank == 0:
+        prec = {L.LBVE_F32: "f32", L.LBVE_F64: "f64"}
         line = {
             "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": K, "warmup": W,
             "ms_per_step": ms_max / K, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
-            "dtype": "f32", "data": "synthetic",
-            "config": {"workload": f"channel_{w.nx}x{w.ny}_L{w.L}", "lattice": "D2Q9", "nodes": w.N, "history_points": w.L,
-                       "precision": "history (E-1, kappa) f32 storage and arithmetic; populations f64",
-                       "blocks_B": w.B, "block_C": w.C, "tau_lb": w.tau_lb, "G_inf": w.G_inf, "tau": w.tau,
-                       "gamma_c": w.gamma_c, "g": w.g, "parallelism": f"replicas{world}",
-                       "l2": "no flush: history state 17.2 GB >> 129 MB L2"},
+            "dtype": prec.get(d0.hist_storage, "f32"), "data": "synthetic",
+            "config": dict({"workload": name, "nodes": N, "history_points": d0.hist_C * d0.hist_B,
+                            "precision": f"history (E-1, kappa) {prec.get(d0.hist_storage)} storage and arithmetic; "
+                                         f"populations {prec.get(d0.pop_precision)}",
+                            "parallelism": f"replicas{world}",
+                            "l2": "no flush: history state far larger than the 129 MB L2" if alg_bytes > 1e9 else
+                                  "history state fits in L2 (latency-bound size)",
+                            "sweep": {"slot_chunks": S, "ctas": ctas}}, **notes),
             "mlups": mlups,
             "kernel_ms_per_launch": {"moments": kms[0] / max(launches[0], 1), "history": hist_ms,
                                      "collide_stream": kms[2] / max(launches[2], 1)},
@@ -293,10 +348,11 @@ def run_ours(args, rank, world, local_rank):
                          "frac": achieved / peak, "traffic": traffic, "peak_kind": peak_kind,
                          "kernel": "k_sweep", "algorithmic_bytes_per_launch": alg_bytes},
             "clocks": clk.summary(),
-            "gpu_launches": int(sum(launches)),
+            "gpu_launches": 3 * K,
             "e2e": e2e,
             "cpu_baseline": cpu,
         }
+        line.update(extra)
         print(json.dumps(line), flush=True)
     if world > 1:
         dist.destroy_process_group()

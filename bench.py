@@ -48,6 +48,8 @@ def parse():
     ap.add_argument("--workload", choices=["channel", "batched", "duct"], default="channel",
                     help="channel: the 1024 x 512 D2Q9 channel (the benchmark line); batched: 64 channels of "
                          "uneven width; duct: the D3Q19 128^3 square duct")
+    ap.add_argument("--history", choices=["f32", "s16", "f64"], default="f32",
+                    help="history storage: f32 (plain FP32 form), s16 (16-bit block-scaled precision variant), f64")
     ap.add_argument("--nx", type=int, default=None,
                     help="narrower channel (same rows, same history) for profiler captures; not a bench line")
     return ap.parse_args()
@@ -235,11 +237,18 @@ def run_ours(args, rank, world, local_rank):
         return float(t.item())
 
     name, descs, rho, notes = workload_descs(args, L, configs)
+    hist = {"f32": L.LBVE_F32, "s16": L.LBVE_S16, "f64": L.LBVE_F64}[args.history]
+    for d in descs:
+        d.hist_storage = hist
     d0 = descs[0]
     N = sum(d.nx * d.ny * d.nz for d in descs)
     D = 2 if d0.lattice == L.LBVE_D2Q9 else 3
-    hist_bytes = 4 if d0.hist_storage == L.LBVE_F32 else 8
-    bytes_per_update = 3 * D * D * hist_bytes     # read X, write X, read kappa
+    if d0.hist_storage == L.LBVE_S16:
+        # read Q and kappa (d*d int16 + 1-byte exponent each); every 32nd step also writes Q
+        bytes_per_update = 2 * (2 * D * D + 1) + (2 * D * D + 1) / 32
+    else:
+        hist_bytes = 4 if d0.hist_storage == L.LBVE_F32 else 8
+        bytes_per_update = 3 * D * D * hist_bytes     # read X, write X, read kappa
     stream = torch.cuda.current_stream()
     ch = L.Channel(descs if len(descs) > 1 else descs[0], rho)
     K, W = args.steps, args.warmup
@@ -329,11 +338,11 @@ def run_ours(args, rank, world, local_rank):
         cpu = {"value": val, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": sample}
 
     if rank == 0:
-        prec = {L.LBVE_F32: "f32", L.LBVE_F64: "f64"}
+        prec = {L.LBVE_F32: "f32", L.LBVE_F64: "f64", L.LBVE_S16: "s16 (16-bit block-scaled, f32 math)"}
         line = {
             "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": K, "warmup": W,
             "ms_per_step": ms_max / K, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
-            "dtype": prec.get(d0.hist_storage, "f32"), "data": "synthetic",
+            "dtype": {L.LBVE_S16: "s16"}.get(d0.hist_storage, prec.get(d0.hist_storage, "f32")), "data": "synthetic",
             "config": dict({"workload": name, "nodes": N, "history_points": d0.hist_C * d0.hist_B,
                             "precision": f"history (E-1, kappa) {prec.get(d0.hist_storage)} storage and arithmetic; "
                                          f"populations {prec.get(d0.pop_precision)}",

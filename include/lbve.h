@@ -42,7 +42,12 @@ extern "C" {
 
 #define LBVE_F32 0       /* populations / history stored in float */
 #define LBVE_F64 1       /* populations / history stored in double */
-#define LBVE_BF16 2      /* history stored as bfloat16 deviations (precision variant) */
+#define LBVE_BF16 2      /* reserved: plain bfloat16 history is not built (its 2^-9 rounding, identical at
+                            every point of a steady flow, cannot meet 1e-3); use LBVE_S16 */
+#define LBVE_S16 3       /* precision variant of the history: 16-bit block-scaled storage (d*d int16
+                            mantissas + one shared power-of-two exponent per vector) of kappa and of
+                            Q = E(t_b, t') in a per-node FP32 frame R = E(t, t_b) re-based every 32
+                            steps; FP32 arithmetic */
 
 #define LBVE_TRACE_FULL 0 /* Eq. (bodyforce) with the density source d_t(delta rho) as written */
 #define LBVE_TRACE_NONE 1 /* both d_t(delta rho) terms dropped, rho = sum n (channel simplification) */
@@ -66,8 +71,7 @@ typedef struct {
     double  g[3];             /* body force per unit mass; force density f = rho0 g (Sec. IV driving) */
     int32_t hist_C;           /* points per history block C (Sec. III; the paper uses 128), >= 4 */
     int32_t hist_B;           /* number of blocks B, 1..16; B*C points span about C (2^B - 1) steps */
-    int32_t hist_storage;     /* LBVE_F32 | LBVE_F64: storage and arithmetic of the history (| LBVE_BF16
-                                 where supported) */
+    int32_t hist_storage;     /* LBVE_F32 | LBVE_F64 | LBVE_S16: storage and arithmetic of the history */
     int32_t pop_precision;    /* LBVE_F32 | LBVE_F64: storage and collision arithmetic of the populations
                                  (independent of hist_storage; node fields are always double) */
     int32_t trace_coupling;   /* LBVE_TRACE_FULL | LBVE_TRACE_NONE */

@@ -37,6 +37,7 @@ int cuda_fail(cudaError_t e, const char* what) {
     } while (0)
 
 constexpr int kGraphSteps = 16;   // steps per captured graph
+constexpr int kRebase = 32;       // frame re-base interval of the 16-bit history
 constexpr int kMaxChannels = 1 << 16;
 
 }  // namespace
@@ -49,7 +50,8 @@ struct lbve {
     long long Npad;
     int pop_dbl;               // 1: populations stored in double
     int hist_dbl;              // 1: history stored (and advanced) in double
-    size_t pesz, hesz;         // element sizes of populations and history
+    int hist_s16;              // 1: 16-bit block-scaled history in a per-node frame
+    size_t pesz, hesz;         // element sizes of populations and history (partial sums)
     std::vector<Chan> chan_host;
     Chan* chan_dev = nullptr;  // [nchan] per-channel geometry and parameters
     int* chan_of = nullptr;    // [Npad] channel of every node (batches only)
@@ -64,6 +66,9 @@ struct lbve {
     void* X = nullptr;
     void* K = nullptr;
     void* part = nullptr;      // sweep partial sums [S][NS][Npad] (history type)
+    void* Qe = nullptr;        // 16-bit history: exponents of Q - 1 [L][Npad]
+    void* Ke = nullptr;        //                 exponents of kappa [L][Npad]
+    void* Rm = nullptr;        //                 frame R - 1 [DD][Npad] (float)
     int S = 1;                 // slot chunks of the sweep (autotuned at create)
     int sweep_grid = 0;        // persistent CTAs of the sweep
     long long* t_dev = nullptr;
@@ -87,7 +92,8 @@ namespace {
 
 void free_all(lbve* h) {
     void* ptrs[] = {h->pops[0], h->pops[1], h->u_raw, h->u, h->rho, h->sigma, h->kappa, h->tr_prev,
-                    h->X, h->K, h->part, h->t_dev, h->red, h->stage, h->flag, h->chan_dev, h->chan_of};
+                    h->X, h->K, h->part, h->t_dev, h->red, h->stage, h->flag, h->chan_dev, h->chan_of,
+                    h->Qe, h->Ke, h->Rm};
     for (void* p : ptrs)
         if (p) cudaFree(p);
     for (cudaEvent_t e : h->ev_pool) cudaEventDestroy(e);
@@ -168,7 +174,8 @@ int check_desc(const lbve_channel_desc* d) {
     if ((long long)d->hist_C * d->hist_B > 4096) return LBVE_EINVAL;
     if (d->trace_coupling != LBVE_TRACE_FULL && d->trace_coupling != LBVE_TRACE_NONE) return LBVE_EINVAL;
     if (d->pop_precision != LBVE_F32 && d->pop_precision != LBVE_F64) return LBVE_EINVAL;
-    if (d->hist_storage != LBVE_F32 && d->hist_storage != LBVE_F64 && d->hist_storage != LBVE_BF16)
+    if (d->hist_storage != LBVE_F32 && d->hist_storage != LBVE_F64 && d->hist_storage != LBVE_BF16 &&
+        d->hist_storage != LBVE_S16)
         return LBVE_EINVAL;
     if (d->hist_storage == LBVE_BF16) return LBVE_ENOSUPPORT;
     return LBVE_OK;
@@ -199,20 +206,69 @@ int launch_sweep(lbve* h, cudaStream_t s) {
     return LBVE_OK;
 }
 
+CommitS16 commit_s16(lbve* h) {
+    CommitS16 c;
+    c.Qm = (short*)h->X;
+    c.Qe = (signed char*)h->Qe;
+    c.Km = (short*)h->K;
+    c.Ke = (signed char*)h->Ke;
+    c.Rm = (float*)h->Rm;
+    c.part = (const float*)h->part;
+    c.B = h->d.hist_B;
+    c.C = h->d.hist_C;
+    c.S = h->S;
+    c.TB = kRebase;
+    return c;
+}
+
+template <int D> constexpr int sweep_vn_s16() { return D == 2 ? 4 : 2; }
+
+template <int D>
+int launch_sweep_s16(lbve* h, cudaStream_t s) {
+    constexpr int VN = sweep_vn_s16<D>();
+    k_sweep_s16<D, VN><<<h->sweep_grid, 256, sweep_smem_bytes(h->L), s>>>(commit_s16(h), (const double*)h->kappa,
+                                                                           h->t_dev, geom_of(h));
+    LBVE_CUDA(cudaGetLastError());
+    return LBVE_OK;
+}
+
+// History storage kinds (template argument HK): 0 float, 1 double, 2 16-bit block-scaled.
+template <int D, int HK>
+int launch_sweep_any(lbve* h, cudaStream_t s) {
+    if (HK == 2) return launch_sweep_s16<D>(h, s);
+    if (HK == 1) return launch_sweep<D, double>(h, s);
+    return launch_sweep<D, float>(h, s);
+}
+
+template <int D, int HK> struct SweepKernel;
+template <int D> struct SweepKernel<D, 0> {
+    static constexpr int VN = sweep_vn<D, float>();
+    static const void* fn() { return (const void*)k_sweep<D, float, VN>; }
+};
+template <int D> struct SweepKernel<D, 1> {
+    static constexpr int VN = sweep_vn<D, double>();
+    static const void* fn() { return (const void*)k_sweep<D, double, VN>; }
+};
+template <int D> struct SweepKernel<D, 2> {
+    static constexpr int VN = sweep_vn_s16<D>();
+    static const void* fn() { return (const void*)k_sweep_s16<D, VN>; }
+};
+
 // Autotuner of the sweep: candidate slot-chunk counts S (tasks per resident warp from about 2 to 32),
 // each timed over a few launches on the freshly created, all-rest history (which the sweep leaves
 // unchanged: exp(0) - 1 = 0); the fastest is kept.  The partial-sum buffer is sized for the largest
 // candidate and then trimmed by reallocation.
-template <int D, typename R>
+template <int D, int HK>
 int sweep_autotune(lbve* h) {
-    constexpr int VN = sweep_vn<D, R>();
+    constexpr int VN = SweepKernel<D, HK>::VN;
+    const void* fn = SweepKernel<D, HK>::fn();
     const size_t smem = sweep_smem_bytes(h->L);
     if (smem > 48 * 1024)
-        LBVE_CUDA(cudaFuncSetAttribute(k_sweep<D, R, VN>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+        LBVE_CUDA(cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
     int dev = 0, sms = 0, per_sm = 0;
     LBVE_CUDA(cudaGetDevice(&dev));
     LBVE_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
-    LBVE_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_sweep<D, R, VN>, 256, smem));
+    LBVE_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, 256, smem));
     if (per_sm < 1) per_sm = 1;
     const long long warps = (long long)sms * per_sm * 8;
     const long long tiles = h->Npad / (32 * VN);
@@ -237,10 +293,10 @@ int sweep_autotune(lbve* h) {
         for (long long S : cand) {
             h->S = (int)S;
             h->sweep_grid = (int)std::max(1ll, std::min(grid_full, (tiles * S + 7) / 8));
-            if ((rc = launch_sweep<D, R>(h, 0))) return rc;   // warm-up
+            if ((rc = launch_sweep_any<D, HK>(h, 0))) return rc;   // warm-up
             LBVE_CUDA(cudaEventRecord(e0, 0));
             for (int r = 0; r < 3; ++r)
-                if ((rc = launch_sweep<D, R>(h, 0))) return rc;
+                if ((rc = launch_sweep_any<D, HK>(h, 0))) return rc;
             LBVE_CUDA(cudaEventRecord(e1, 0));
             LBVE_CUDA(cudaEventSynchronize(e1));
             float ms = 0.f;
@@ -276,8 +332,8 @@ CommitArgs<R> commit_args(lbve* h) {
 __global__ void k_advance_t(long long* t) { *t += 1; }
 
 // One hybrid step: moments -> history sweep -> commit + collide + stream.  pops[cur] -> pops[cur ^ 1].
-// P: population storage type, R: history type, T: collision arithmetic type.
-template <int Q, typename P, typename R, typename T>
+// P: population storage type, HK: history kind (0 float, 1 double, 2 16-bit), T: collision arithmetic.
+template <int Q, typename P, int HK, typename T>
 int one_step(lbve* h, int cur, cudaStream_t s) {
     constexpr int D = Lattice<Q>::D;
     const Geom g = geom_of(h);
@@ -290,7 +346,7 @@ int one_step(lbve* h, int cur, cudaStream_t s) {
     LBVE_CUDA(cudaGetLastError());
     if ((rc = prof_mark(h, s, KIND_MOMENTS, false))) return rc;
     if ((rc = prof_mark(h, s, KIND_HISTORY, true))) return rc;
-    if ((rc = launch_sweep<D, R>(h, s))) return rc;
+    if ((rc = launch_sweep_any<D, HK>(h, s))) return rc;
     if ((rc = prof_mark(h, s, KIND_HISTORY, false))) return rc;
     CollArgs<P> c;
     c.dn_in = din;
@@ -303,19 +359,21 @@ int one_step(lbve* h, int cur, cudaStream_t s) {
     c.u = (double*)h->u;
     c.t_dev = h->t_dev;
     if ((rc = prof_mark(h, s, KIND_COLLIDE, true))) return rc;
-    k_collide_stream<Q, P, T, R><<<grid, 256, 0, s>>>(c, commit_args<R>(h), g);
+    if (HK == 2) k_collide_stream<Q, P, T, CommitS16><<<grid, 256, 0, s>>>(c, commit_s16(h), g);
+    else if (HK == 1) k_collide_stream<Q, P, T, CommitArgs<double>><<<grid, 256, 0, s>>>(c, commit_args<double>(h), g);
+    else k_collide_stream<Q, P, T, CommitArgs<float>><<<grid, 256, 0, s>>>(c, commit_args<float>(h), g);
     LBVE_CUDA(cudaGetLastError());
     if ((rc = prof_mark(h, s, KIND_COLLIDE, false))) return rc;
     return LBVE_OK;
 }
 
-template <int Q, typename P, typename R, typename T>
+template <int Q, typename P, int HK, typename T>
 int capture_graph(lbve* h) {
     if (!h->graph_stream) LBVE_CUDA(cudaStreamCreateWithFlags(&h->graph_stream, cudaStreamNonBlocking));
     cudaGraph_t graph = nullptr;
     LBVE_CUDA(cudaStreamBeginCapture(h->graph_stream, cudaStreamCaptureModeThreadLocal));
     int rc = LBVE_OK;
-    for (int i = 0; i < kGraphSteps && rc == LBVE_OK; ++i) rc = one_step<Q, P, R, T>(h, i & 1, h->graph_stream);
+    for (int i = 0; i < kGraphSteps && rc == LBVE_OK; ++i) rc = one_step<Q, P, HK, T>(h, i & 1, h->graph_stream);
     cudaError_t e = cudaStreamEndCapture(h->graph_stream, &graph);
     if (rc) {
         if (graph) cudaGraphDestroy(graph);
@@ -331,7 +389,7 @@ int capture_graph(lbve* h) {
     return LBVE_OK;
 }
 
-template <int Q, typename P, typename R, typename T>
+template <int Q, typename P, int HK, typename T>
 int step_impl(lbve* h, int64_t n, cudaStream_t s) {
     int rc;
     // whole graphs of kGraphSteps steps (an even count, so populations end where they started); the
@@ -339,13 +397,13 @@ int step_impl(lbve* h, int64_t n, cudaStream_t s) {
     // events and therefore launches step by step.
     if (!h->profiling && n >= kGraphSteps) {
         if (h->cur == 1) {
-            if ((rc = one_step<Q, P, R, T>(h, 1, s))) return rc;
+            if ((rc = one_step<Q, P, HK, T>(h, 1, s))) return rc;
             h->cur = 0;
             h->t_host += 1;
             --n;
         }
         if (n >= kGraphSteps) {
-            if (!h->graph && (rc = capture_graph<Q, P, R, T>(h))) return rc;
+            if (!h->graph && (rc = capture_graph<Q, P, HK, T>(h))) return rc;
             while (n >= kGraphSteps) {
                 LBVE_CUDA(cudaGraphLaunch(h->graph, s));
                 h->t_host += kGraphSteps;
@@ -354,7 +412,7 @@ int step_impl(lbve* h, int64_t n, cudaStream_t s) {
         }
     }
     for (int64_t i = 0; i < n; ++i) {
-        if ((rc = one_step<Q, P, R, T>(h, h->cur, s))) return rc;
+        if ((rc = one_step<Q, P, HK, T>(h, h->cur, s))) return rc;
         h->cur ^= 1;
         h->t_host += 1;
     }
@@ -480,8 +538,10 @@ int create_impl(const lbve_channel_desc* descs, int32_t n, const double* rho_ini
     h->Npad = ((long long)h->N + 127) / 128 * 128;
     h->pop_dbl = desc->pop_precision == LBVE_F64;
     h->hist_dbl = desc->hist_storage == LBVE_F64;
+    h->hist_s16 = desc->hist_storage == LBVE_S16;
     h->pesz = h->pop_dbl ? 8 : 4;
     h->hesz = h->hist_dbl ? 8 : 4;
+    const size_t hist_elem = h->hist_s16 ? 2 : h->hesz;   // bytes of one stored history component
     h->chan_host.resize(n);
     {
         int off = 0;
@@ -503,8 +563,8 @@ int create_impl(const lbve_channel_desc* descs, int32_t n, const double* rho_ini
         (rc = alloc(h, &h->u_raw, fe * h->D * Np)) || (rc = alloc(h, &h->u, fe * h->D * Np)) ||
         (rc = alloc(h, &h->rho, fe * Np)) || (rc = alloc(h, &h->sigma, fe * h->NS * Np)) ||
         (rc = alloc(h, &h->kappa, fe * DD * Np)) || (rc = alloc(h, &h->tr_prev, fe * Np)) ||
-        (rc = alloc(h, &h->X, h->hesz * (size_t)h->L * DD * Np)) ||
-        (rc = alloc(h, &h->K, h->hesz * (size_t)h->L * DD * Np)) ||
+        (rc = alloc(h, &h->X, hist_elem * (size_t)h->L * DD * Np)) ||
+        (rc = alloc(h, &h->K, hist_elem * (size_t)h->L * DD * Np)) ||
         (rc = alloc(h, (void**)&h->t_dev, sizeof(long long))) || (rc = alloc(h, (void**)&h->red, 2 * sizeof(double))) ||
         (rc = alloc(h, (void**)&h->flag, sizeof(int))) ||
         (rc = alloc(h, (void**)&h->chan_dev, sizeof(Chan) * n)))
@@ -523,12 +583,19 @@ int create_impl(const lbve_channel_desc* descs, int32_t n, const double* rho_ini
         cudaError_t e = cudaMemcpy(h->chan_of, co.data(), sizeof(int) * Np, cudaMemcpyHostToDevice);
         if (e != cudaSuccess) return fail(cuda_fail(e, "cudaMemcpy"));
     }
-    // zero every buffer: rest state, empty history (E = 1 <=> X = 0, kappa = 0)
-    void* zero_bufs[] = {h->pops[0], h->pops[1], h->u_raw, h->u, h->sigma, h->kappa, h->tr_prev, h->X, h->K, h->flag};
+    if (h->hist_s16 &&
+        ((rc = alloc(h, &h->Qe, (size_t)h->L * Np)) || (rc = alloc(h, &h->Ke, (size_t)h->L * Np)) ||
+         (rc = alloc(h, &h->Rm, sizeof(float) * DD * Np))))
+        return fail(rc);
+    // zero every buffer: rest state, empty history (E = 1 <=> X = 0 or Q = 1, kappa = 0, frame 1)
+    void* zero_bufs[] = {h->pops[0], h->pops[1], h->u_raw, h->u, h->sigma, h->kappa, h->tr_prev, h->X, h->K, h->flag,
+                         h->Qe, h->Ke, h->Rm};
     size_t zero_sizes[] = {h->pesz * h->Q * Np, h->pesz * h->Q * Np, fe * h->D * Np, fe * h->D * Np,
-                           fe * h->NS * Np, fe * DD * Np, fe * Np, h->hesz * (size_t)h->L * DD * Np,
-                           h->hesz * (size_t)h->L * DD * Np, sizeof(int)};
-    for (int i = 0; i < 10; ++i) {
+                           fe * h->NS * Np, fe * DD * Np, fe * Np, hist_elem * (size_t)h->L * DD * Np,
+                           hist_elem * (size_t)h->L * DD * Np, sizeof(int), (size_t)h->L * Np, (size_t)h->L * Np,
+                           sizeof(float) * DD * Np};
+    for (int i = 0; i < 13; ++i) {
+        if (!zero_bufs[i]) continue;
         cudaError_t e = cudaMemset(zero_bufs[i], 0, zero_sizes[i]);
         if (e != cudaSuccess) return fail(cuda_fail(e, "cudaMemset"));
     }
@@ -537,8 +604,8 @@ int create_impl(const lbve_channel_desc* descs, int32_t n, const double* rho_ini
         cudaError_t e = cudaMemcpy(h->t_dev, &minus_one, sizeof minus_one, cudaMemcpyHostToDevice);
         if (e != cudaSuccess) return fail(cuda_fail(e, "cudaMemcpy"));
     }
-    if (h->D == 2) rc = h->hist_dbl ? sweep_autotune<2, double>(h) : sweep_autotune<2, float>(h);
-    else rc = h->hist_dbl ? sweep_autotune<3, double>(h) : sweep_autotune<3, float>(h);
+    if (h->D == 2) rc = h->hist_s16 ? sweep_autotune<2, 2>(h) : h->hist_dbl ? sweep_autotune<2, 1>(h) : sweep_autotune<2, 0>(h);
+    else rc = h->hist_s16 ? sweep_autotune<3, 2>(h) : h->hist_dbl ? sweep_autotune<3, 1>(h) : sweep_autotune<3, 0>(h);
     if (rc) return fail(rc);
     rc = h->pop_dbl ? init_state<double>(h, rho_init) : init_state<float>(h, rho_init);
     if (rc) return fail(rc);
@@ -626,20 +693,25 @@ int lbve_set_params(lbve_t* h, int32_t channel, double G_inf, double tau, double
 int lbve_step(lbve_t* h, int64_t n_steps, void* stream) {
     if (!h || n_steps < 0) return LBVE_EINVAL;
     cudaStream_t s = (cudaStream_t)stream;
-    const int combo = (h->pop_dbl ? 2 : 0) | (h->hist_dbl ? 1 : 0);
+    const int hk = h->hist_s16 ? 2 : (h->hist_dbl ? 1 : 0);
+    const int combo = (h->pop_dbl ? 3 : 0) + hk;
     if (h->Q == 9) {
         switch (combo) {
-            case 0: return step_impl<9, float, float, float>(h, n_steps, s);
-            case 1: return step_impl<9, float, double, float>(h, n_steps, s);
-            case 2: return step_impl<9, double, float, double>(h, n_steps, s);
-            default: return step_impl<9, double, double, double>(h, n_steps, s);
+            case 0: return step_impl<9, float, 0, float>(h, n_steps, s);
+            case 1: return step_impl<9, float, 1, float>(h, n_steps, s);
+            case 2: return step_impl<9, float, 2, float>(h, n_steps, s);
+            case 3: return step_impl<9, double, 0, double>(h, n_steps, s);
+            case 4: return step_impl<9, double, 1, double>(h, n_steps, s);
+            default: return step_impl<9, double, 2, double>(h, n_steps, s);
         }
     }
     switch (combo) {
-        case 0: return step_impl<19, float, float, float>(h, n_steps, s);
-        case 1: return step_impl<19, float, double, float>(h, n_steps, s);
-        case 2: return step_impl<19, double, float, double>(h, n_steps, s);
-        default: return step_impl<19, double, double, double>(h, n_steps, s);
+        case 0: return step_impl<19, float, 0, float>(h, n_steps, s);
+        case 1: return step_impl<19, float, 1, float>(h, n_steps, s);
+        case 2: return step_impl<19, float, 2, float>(h, n_steps, s);
+        case 3: return step_impl<19, double, 0, double>(h, n_steps, s);
+        case 4: return step_impl<19, double, 1, double>(h, n_steps, s);
+        default: return step_impl<19, double, 2, double>(h, n_steps, s);
     }
 }
 
@@ -685,24 +757,34 @@ int lbve_history_apply(lbve_t* h, const double* kappa_dev, double* sigma_dev, vo
     int rc;
     const Geom g = geom_of(h);
     const int grid = (h->N + 255) / 256;
-    if (h->D == 2) {
+    if (h->hist_s16) {
+        if (h->D == 2) {
+            if ((rc = launch_sweep_s16<2>(h, s))) return rc;
+            k_commit<2, CommitS16><<<grid, 256, 0, s>>>(commit_s16(h), kappa_dev, (double*)h->sigma, (double*)h->kappa,
+                                                        sigma_dev, h->t_dev, g);
+        } else {
+            if ((rc = launch_sweep_s16<3>(h, s))) return rc;
+            k_commit<3, CommitS16><<<grid, 256, 0, s>>>(commit_s16(h), kappa_dev, (double*)h->sigma, (double*)h->kappa,
+                                                        sigma_dev, h->t_dev, g);
+        }
+    } else if (h->D == 2) {
         if (h->hist_dbl) {
             if ((rc = launch_sweep<2, double>(h, s))) return rc;
-            k_commit<2, double><<<grid, 256, 0, s>>>(commit_args<double>(h), kappa_dev, (double*)h->sigma,
+            k_commit<2, CommitArgs<double>><<<grid, 256, 0, s>>>(commit_args<double>(h), kappa_dev, (double*)h->sigma,
                                                      (double*)h->kappa, sigma_dev, h->t_dev, g);
         } else {
             if ((rc = launch_sweep<2, float>(h, s))) return rc;
-            k_commit<2, float><<<grid, 256, 0, s>>>(commit_args<float>(h), kappa_dev, (double*)h->sigma,
+            k_commit<2, CommitArgs<float>><<<grid, 256, 0, s>>>(commit_args<float>(h), kappa_dev, (double*)h->sigma,
                                                     (double*)h->kappa, sigma_dev, h->t_dev, g);
         }
     } else {
         if (h->hist_dbl) {
             if ((rc = launch_sweep<3, double>(h, s))) return rc;
-            k_commit<3, double><<<grid, 256, 0, s>>>(commit_args<double>(h), kappa_dev, (double*)h->sigma,
+            k_commit<3, CommitArgs<double>><<<grid, 256, 0, s>>>(commit_args<double>(h), kappa_dev, (double*)h->sigma,
                                                      (double*)h->kappa, sigma_dev, h->t_dev, g);
         } else {
             if ((rc = launch_sweep<3, float>(h, s))) return rc;
-            k_commit<3, float><<<grid, 256, 0, s>>>(commit_args<float>(h), kappa_dev, (double*)h->sigma,
+            k_commit<3, CommitArgs<float>><<<grid, 256, 0, s>>>(commit_args<float>(h), kappa_dev, (double*)h->sigma,
                                                     (double*)h->kappa, sigma_dev, h->t_dev, g);
         }
     }

@@ -206,24 +206,12 @@ __device__ __forceinline__ void expm1_mat(const real* K, real* A) {
     for (int i = 0; i < DD; ++i) A[i] = P[i];
 }
 
-// One history point: advance X <- X + A + A X, then the integrand w g (E kap E^T + (E kap E^T)^T)
-// accumulated into acc (nsig packed components).
+// The integrand of one history point with E = 1 + X: w G(age) (E kappa E^T + (E kappa E^T)^T), G of
+// Eq. (nlmax) without the factor G_inf, accumulated into acc (nsig packed components).
 template <int D, typename real>
-__device__ __forceinline__ void point_update(real* X, const real* A, const real* kap, real age, real w,
-                                             real inv_tau, real inv_gc, real* acc) {
+__device__ __forceinline__ void point_integrand(const real* X, const real* kap, real age, real w,
+                                                real inv_tau, real inv_gc, real* acc) {
     constexpr int DD = D * D;
-    real Xn[DD];
-#pragma unroll
-    for (int r = 0; r < D; ++r)
-#pragma unroll
-        for (int c = 0; c < D; ++c) {
-            real s = X[r * D + c] + A[r * D + c];
-#pragma unroll
-            for (int k = 0; k < D; ++k) s += A[r * D + k] * X[k * D + c];
-            Xn[r * D + c] = s;
-        }
-#pragma unroll
-    for (int i = 0; i < DD; ++i) X[i] = Xn[i];
     // M = E kap E^T with E = 1 + X
     real EK[DD];
 #pragma unroll
@@ -268,6 +256,27 @@ __device__ __forceinline__ void point_update(real* X, const real* A, const real*
         acc[4] += gw * (M[2] + M[6]);
         acc[5] += gw * (M[5] + M[7]);
     }
+}
+
+// One history point of the in-place storage: advance X <- X + A + A X (E <- exp(kappa(t-1)) E), then
+// its integrand.
+template <int D, typename real>
+__device__ __forceinline__ void point_update(real* X, const real* A, const real* kap, real age, real w,
+                                             real inv_tau, real inv_gc, real* acc) {
+    constexpr int DD = D * D;
+    real Xn[DD];
+#pragma unroll
+    for (int r = 0; r < D; ++r)
+#pragma unroll
+        for (int c = 0; c < D; ++c) {
+            real s = X[r * D + c] + A[r * D + c];
+#pragma unroll
+            for (int k = 0; k < D; ++k) s += A[r * D + k] * X[k * D + c];
+            Xn[r * D + c] = s;
+        }
+#pragma unroll
+    for (int i = 0; i < DD; ++i) X[i] = Xn[i];
+    point_integrand<D>(X, kap, age, w, inv_tau, inv_gc, acc);
 }
 
 // ------------------------------------------------------------------------------------------------
@@ -469,22 +478,372 @@ __device__ __forceinline__ void hist_commit(const CommitArgs<R>& a, const BlockS
     }
 }
 
-// Commit alone (history-only test hook): the gradient comes from the caller.
+// Uniform entry for every history storage: kprev = kappa(t-1) of the node (the node kappa field before
+// this step overwrites it), used by storages that keep a per-node frame.
 template <int D, typename R>
-__global__ void __launch_bounds__(256) k_commit(CommitArgs<R> a, const double* __restrict__ kappa_in,
+__device__ __forceinline__ void hist_commit_any(const CommitArgs<R>& a, const BlockStep* s_bs, long long Np, int n,
+                                                const double* /*kprev*/, const double* ktd, double G_inf,
+                                                double* sig, long long /*t*/) {
+    hist_commit<D, R>(a, s_bs, Np, n, ktd, G_inf, sig);
+}
+
+// ------------------------------------------------------------------------------------------------
+// Reduced-precision history (precision variant): 16-bit block-scaled storage in a per-node frame.
+//
+// Every node keeps a frame R(t) = E(t, t_b), the deformation since the last rebase step t_b, in FP32
+// (Rm = R - 1).  Every point keeps Q = E(t_b, t') (or R(t')^-1 for points created after t_b), so that
+// E(t, t') = R(t) Q: the per-step left multiplication by exp(kappa(t-1)) of Eq. (eeval) acts on the
+// node's frame only, and the points are read, not rewritten.  Every TB steps the sweep rewrites each
+// point's Q as E(t, t') and the frame restarts at 1, which bounds the strain carried by the frame.
+// Q - 1 and kappa are stored as block-scaled 16-bit vectors: d*d int16 mantissas m_c sharing one
+// power-of-two exponent e, value_c = m_c 2^e, |m_c| <= 32767 (relative precision 2^-15 of the largest
+// component).  Values are written once (kappa; Q between rebases) and re-rounded only at rebases.
+// ------------------------------------------------------------------------------------------------
+__device__ __forceinline__ float pow2f(int k) { return __int_as_float((k + 127) << 23); }   // -126 <= k <= 127
+
+template <int DD>
+__device__ __forceinline__ void s16_encode(const float* v, short* m, signed char* e) {
+    float mx = 0.0f;
+#pragma unroll
+    for (int c = 0; c < DD; ++c) mx = fmaxf(mx, fabsf(v[c]));
+    int ex = 0;
+    if (mx > 0.0f && mx <= 3.0e38f) frexpf(mx, &ex);          // mx = f 2^ex, 0.5 <= f < 1
+    const int es = min(126, max(-126, ex - 15));                 // |v| < 2^ex  =>  |v| 2^-es < 2^15
+    const float inv = pow2f(-es);
+#pragma unroll
+    for (int c = 0; c < DD; ++c) m[c] = (short)fminf(32767.0f, fmaxf(-32767.0f, rintf(v[c] * inv)));
+    *e = (signed char)es;
+}
+
+template <int DD>
+__device__ __forceinline__ void s16_decode(const short* m, int e, float* v) {
+    const float sc = pow2f(e);
+#pragma unroll
+    for (int c = 0; c < DD; ++c) v[c] = (float)m[c] * sc;
+}
+
+struct CommitS16 {
+    short* __restrict__ Qm;          // [L][DD][Npad] mantissas of Q - 1
+    signed char* __restrict__ Qe;    // [L][Npad] exponents
+    short* __restrict__ Km;          // [L][DD][Npad] mantissas of kappa
+    signed char* __restrict__ Ke;    // [L][Npad]
+    float* __restrict__ Rm;          // [DD][Npad] frame R - 1 of each node
+    const float* __restrict__ part;  // [S][NS][Npad]
+    int B, C, S, TB;
+};
+
+// R - 1 of the frame after step t: exp(kappa(t-1)) R(t-1) - 1 = A + Rm + A Rm.
+template <int D>
+__device__ __forceinline__ void frame_advance(const double* kprev, const float* Rm, float* Rn) {
+    constexpr int DD = D * D;
+    float kp[DD], A[DD];
+#pragma unroll
+    for (int c = 0; c < DD; ++c) kp[c] = (float)kprev[c];
+    expm1_mat<D>(kp, A);
+#pragma unroll
+    for (int r = 0; r < D; ++r)
+#pragma unroll
+        for (int c = 0; c < D; ++c) {
+            float s = Rm[r * D + c] + A[r * D + c];
+#pragma unroll
+            for (int k = 0; k < D; ++k) s += A[r * D + k] * Rm[k * D + c];
+            Rn[r * D + c] = s;
+        }
+}
+
+// Q - 1 of a point created now, Q = R^-1: with R = 1 + M, R^-1 - 1 = -R^-1 M (no cancellation).
+template <int D>
+__device__ __forceinline__ void frame_inverse_dev(const float* M, float* X) {
+    float Ri[D * D];
+    if (D == 2) {
+        const float a = 1.0f + M[0], b = M[1], c = M[2], d = 1.0f + M[3];
+        const float det = a * d - b * c;
+        Ri[0] = d / det; Ri[1] = -b / det; Ri[2] = -c / det; Ri[3] = a / det;
+    } else {
+        float R[9];
+#pragma unroll
+        for (int i = 0; i < 9; ++i) R[i] = M[i] + ((i % 4 == 0) ? 1.0f : 0.0f);
+        const float c00 = R[4] * R[8] - R[5] * R[7], c01 = R[5] * R[6] - R[3] * R[8], c02 = R[3] * R[7] - R[4] * R[6];
+        const float det = R[0] * c00 + R[1] * c01 + R[2] * c02;
+        Ri[0] = c00 / det; Ri[3] = c01 / det; Ri[6] = c02 / det;
+        Ri[1] = (R[2] * R[7] - R[1] * R[8]) / det; Ri[4] = (R[0] * R[8] - R[2] * R[6]) / det;
+        Ri[7] = (R[1] * R[6] - R[0] * R[7]) / det;
+        Ri[2] = (R[1] * R[5] - R[2] * R[4]) / det; Ri[5] = (R[2] * R[3] - R[0] * R[5]) / det;
+        Ri[8] = (R[0] * R[4] - R[1] * R[3]) / det;
+    }
+#pragma unroll
+    for (int r = 0; r < D; ++r)
+#pragma unroll
+        for (int c = 0; c < D; ++c) {
+            float s = 0.0f;
+#pragma unroll
+            for (int k = 0; k < D; ++k) s -= Ri[r * D + k] * M[k * D + c];
+            X[r * D + c] = s;
+        }
+}
+
+template <int D>
+__device__ __forceinline__ void hist_commit_any(const CommitS16& a, const BlockStep* s_bs, long long Np, int n,
+                                                const double* kprev, const double* ktd, double G_inf,
+                                                double* sig, long long t) {
+    constexpr int DD = D * D;
+    constexpr int NS = D == 2 ? 3 : 6;
+    // the frame of this step (identical arithmetic to the sweep's), then the rebase
+    float Rm[DD], Rn[DD];
+#pragma unroll
+    for (int c = 0; c < DD; ++c) Rm[c] = a.Rm[c * Np + n];
+    frame_advance<D>(kprev, Rm, Rn);
+    const bool rebase = (t % a.TB) == 0;
+#pragma unroll
+    for (int c = 0; c < DD; ++c) {
+        if (rebase) Rn[c] = 0.0f;
+        a.Rm[c * Np + n] = Rn[c];
+    }
+    // sigma: chunk partials + the point created now (its stored, rounded kappa; E = 1, weight 1/2)
+    double acc[NS];
+#pragma unroll
+    for (int i = 0; i < NS; ++i) acc[i] = 0.0;
+    for (int c = 0; c < a.S; ++c)
+#pragma unroll
+        for (int i = 0; i < NS; ++i) acc[i] += (double)a.part[((long long)c * NS + i) * Np + n];
+    float kt[DD];
+    short km[DD];
+    signed char ke;
+#pragma unroll
+    for (int c = 0; c < DD; ++c) kt[c] = (float)ktd[c];
+    s16_encode<DD>(kt, km, &ke);
+    s16_decode<DD>(km, ke, kt);
+    if (D == 2) {
+        acc[0] += (double)(0.5f * (kt[0] + kt[0]));
+        acc[1] += (double)(0.5f * (kt[3] + kt[3]));
+        acc[2] += (double)(0.5f * (kt[1] + kt[2]));
+    } else {
+        acc[0] += (double)(0.5f * (kt[0] + kt[0]));
+        acc[1] += (double)(0.5f * (kt[4] + kt[4]));
+        acc[2] += (double)(0.5f * (kt[8] + kt[8]));
+        acc[3] += (double)(0.5f * (kt[1] + kt[3]));
+        acc[4] += (double)(0.5f * (kt[2] + kt[6]));
+        acc[5] += (double)(0.5f * (kt[5] + kt[7]));
+    }
+#pragma unroll
+    for (int i = 0; i < NS; ++i) sig[i] = G_inf * acc[i];
+    // block merges, coarsest first: the older point's Q moves, kappa is averaged and re-encoded
+    for (int bb = 1; bb < a.B; ++bb) {
+        const BlockStep& b = s_bs[bb];
+        if (!b.evict) continue;
+        int o1 = b.head_prev - (a.C - 1); if (o1 < 0) o1 += a.C;
+        int o2 = b.head_prev - (a.C - 2); if (o2 < 0) o2 += a.C;
+        const long long src1 = (long long)bb * a.C + o1, src2 = (long long)bb * a.C + o2;
+        const long long dst = (long long)(bb - 1) * a.C + s_bs[bb - 1].head_new;
+        short m1[DD], m2[DD], mo[DD];
+        float k1[DD], k2[DD];
+        signed char eo;
+#pragma unroll
+        for (int c = 0; c < DD; ++c) {
+            a.Qm[(dst * DD + c) * Np + n] = a.Qm[(src1 * DD + c) * Np + n];
+            m1[c] = a.Km[(src1 * DD + c) * Np + n];
+            m2[c] = a.Km[(src2 * DD + c) * Np + n];
+        }
+        a.Qe[dst * Np + n] = a.Qe[src1 * Np + n];
+        s16_decode<DD>(m1, a.Ke[src1 * Np + n], k1);
+        s16_decode<DD>(m2, a.Ke[src2 * Np + n], k2);
+#pragma unroll
+        for (int c = 0; c < DD; ++c) k1[c] = 0.5f * (k1[c] + k2[c]);
+        s16_encode<DD>(k1, mo, &eo);
+#pragma unroll
+        for (int c = 0; c < DD; ++c) a.Km[(dst * DD + c) * Np + n] = mo[c];
+        a.Ke[dst * Np + n] = eo;
+    }
+    // the new point: Q = R^-1 of the frame after this step, kappa(t)
+    const long long dst = (long long)(a.B - 1) * a.C + s_bs[a.B - 1].head_new;
+    float X[DD];
+    short qm[DD];
+    signed char qe;
+    frame_inverse_dev<D>(Rn, X);
+    s16_encode<DD>(X, qm, &qe);
+#pragma unroll
+    for (int c = 0; c < DD; ++c) {
+        a.Qm[(dst * DD + c) * Np + n] = qm[c];
+        a.Km[(dst * DD + c) * Np + n] = km[c];
+    }
+    a.Qe[dst * Np + n] = qe;
+    a.Ke[dst * Np + n] = ke;
+}
+
+// Sweep of the 16-bit history: lanes hold VN consecutive nodes (VN-wide loads of every mantissa and
+// exponent plane), tasks as in k_sweep.  E - 1 = Rm + Q - 1 + Rm (Q - 1) with the frame of this step;
+// on rebase steps the point's Q is rewritten as E(t, t').
+template <int D, int VN>
+__global__ void __launch_bounds__(256, 2) k_sweep_s16(CommitS16 a, const double* __restrict__ kprev,
+                                                      const long long* t_dev, Geom g) {
+    constexpr int DD = D * D;
+    constexpr int NS = D == 2 ? 3 : 6;
+    using VS = Vec<short, VN>;
+    using VE = Vec<signed char, VN>;
+    using VF = Vec<float, VN>;
+    const int L = a.B * a.C;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    float* s_age = reinterpret_cast<float*>(smem_raw);
+    float* s_w = s_age + L;
+    int* s_part = reinterpret_cast<int*>(s_w + L);
+    BlockStep* s_bs = reinterpret_cast<BlockStep*>(s_part + L);
+
+    const long long t = *t_dev;
+    if (threadIdx.x == 0) sched_step(a.B, a.C, t, s_bs);
+    __syncthreads();
+    for (int l = threadIdx.x; l < L; l += blockDim.x) {
+        int age, part;
+        const float w = sched_slot_role(s_bs, a.C, l / a.C, l % a.C, &age, &part);
+        s_age[l] = (float)age;
+        s_w[l] = w;
+        s_part[l] = part;
+    }
+    __syncthreads();
+
+    const long long Np = g.Npad;
+    const int lane = threadIdx.x & 31;
+    const int gwarp = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+    const int nwarps = gridDim.x * (blockDim.x >> 5);
+    const int tiles = (int)(Np / (32 * VN));
+    const int tasks = tiles * a.S;
+    const int chunk_len = (L + a.S - 1) / a.S;
+    const bool rebase = (t % a.TB) == 0;
+
+    for (int task = gwarp; task < tasks; task += nwarps) {
+        const int tile = task % tiles;
+        const int chunk = task / tiles;
+        const long long n0 = (long long)tile * 32 * VN + lane * VN;
+        float inv_tau[VN], inv_gc[VN];
+        float F[VN][DD];   // frame of this step, R - 1
+#pragma unroll
+        for (int j = 0; j < VN; ++j) {
+            const Chan& c = g.ch[chan_index(g, n0 + j)];
+            inv_tau[j] = (float)c.inv_tau;
+            inv_gc[j] = (float)c.inv_gc;
+        }
+        {
+            float Rm[VN][DD];
+            double kp[VN][DD];
+#pragma unroll
+            for (int c = 0; c < DD; ++c) {
+                const VF v = *reinterpret_cast<const VF*>(a.Rm + c * Np + n0);
+#pragma unroll
+                for (int j = 0; j < VN; ++j) {
+                    Rm[j][c] = v.v[j];
+                    kp[j][c] = kprev[c * Np + n0 + j];
+                }
+            }
+#pragma unroll
+            for (int j = 0; j < VN; ++j) frame_advance<D>(kp[j], Rm[j], F[j]);
+        }
+        float acc[VN][NS];
+#pragma unroll
+        for (int j = 0; j < VN; ++j)
+#pragma unroll
+            for (int i = 0; i < NS; ++i) acc[j][i] = 0.0f;
+
+        const int l0 = chunk * chunk_len;
+        const int l1 = min(L, l0 + chunk_len);
+        for (int l = l0; l < l1; ++l) {
+            const float w = s_w[l];
+            if (w == 0.0f) continue;
+            short qm[VN][DD], km[VN][DD];
+            const VE qe = *reinterpret_cast<const VE*>(a.Qe + (long long)l * Np + n0);
+            const VE ke = *reinterpret_cast<const VE*>(a.Ke + (long long)l * Np + n0);
+#pragma unroll
+            for (int c = 0; c < DD; ++c) {
+                const VS qv = *reinterpret_cast<const VS*>(a.Qm + ((long long)l * DD + c) * Np + n0);
+                const VS kv = *reinterpret_cast<const VS*>(a.Km + ((long long)l * DD + c) * Np + n0);
+#pragma unroll
+                for (int j = 0; j < VN; ++j) { qm[j][c] = qv.v[j]; km[j][c] = kv.v[j]; }
+            }
+            float kap[VN][DD];
+#pragma unroll
+            for (int j = 0; j < VN; ++j) s16_decode<DD>(km[j], ke.v[j], kap[j]);
+            const int part = s_part[l];
+            if (part >= 0) {   // older half of a merge: kappa averaged with the newer half
+                const VE ke2 = *reinterpret_cast<const VE*>(a.Ke + (long long)part * Np + n0);
+                short km2[VN][DD];
+#pragma unroll
+                for (int c = 0; c < DD; ++c) {
+                    const VS kv = *reinterpret_cast<const VS*>(a.Km + ((long long)part * DD + c) * Np + n0);
+#pragma unroll
+                    for (int j = 0; j < VN; ++j) km2[j][c] = kv.v[j];
+                }
+#pragma unroll
+                for (int j = 0; j < VN; ++j) {
+                    float k2[DD];
+                    s16_decode<DD>(km2[j], ke2.v[j], k2);
+#pragma unroll
+                    for (int c = 0; c < DD; ++c) kap[j][c] = 0.5f * (kap[j][c] + k2[c]);
+                }
+            }
+            const float age = s_age[l];
+            float X[VN][DD];
+#pragma unroll
+            for (int j = 0; j < VN; ++j) {
+                float Qd[DD];
+                s16_decode<DD>(qm[j], qe.v[j], Qd);
+                // E - 1 = F + Qd + F Qd
+#pragma unroll
+                for (int r = 0; r < D; ++r)
+#pragma unroll
+                    for (int c = 0; c < D; ++c) {
+                        float s = F[j][r * D + c] + Qd[r * D + c];
+#pragma unroll
+                        for (int k = 0; k < D; ++k) s += F[j][r * D + k] * Qd[k * D + c];
+                        X[j][r * D + c] = s;
+                    }
+                point_integrand<D>(X[j], kap[j], age, w, inv_tau[j], inv_gc[j], acc[j]);
+            }
+            if (rebase) {   // the point's Q becomes E(t, t'); the frame restarts at 1 in the commit
+                VE qe_new;
+#pragma unroll
+                for (int j = 0; j < VN; ++j) {
+                    signed char e;
+                    s16_encode<DD>(X[j], qm[j], &e);
+                    qe_new.v[j] = e;
+                }
+                *reinterpret_cast<VE*>(a.Qe + (long long)l * Np + n0) = qe_new;
+#pragma unroll
+                for (int c = 0; c < DD; ++c) {
+                    VS qv;
+#pragma unroll
+                    for (int j = 0; j < VN; ++j) qv.v[j] = qm[j][c];
+                    *reinterpret_cast<VS*>(a.Qm + ((long long)l * DD + c) * Np + n0) = qv;
+                }
+            }
+        }
+#pragma unroll
+        for (int i = 0; i < NS; ++i) {
+            VF v;
+#pragma unroll
+            for (int j = 0; j < VN; ++j) v.v[j] = acc[j][i];
+            *reinterpret_cast<VF*>(const_cast<float*>(a.part) + ((long long)chunk * NS + i) * Np + n0) = v;
+        }
+    }
+}
+
+// Commit alone (history-only test hook): the gradient comes from the caller.
+template <int D, class H>
+__global__ void __launch_bounds__(256) k_commit(H a, const double* __restrict__ kappa_in,
                                                 double* __restrict__ sigma_f, double* __restrict__ kappa_f,
                                                 double* __restrict__ sigma_out, const long long* t_dev, Geom g) {
     constexpr int DD = D * D;
     constexpr int NS = D == 2 ? 3 : 6;
     __shared__ BlockStep s_bs[LBVE_MAXB];
-    if (threadIdx.x == 0) sched_step(a.B, a.C, *t_dev, s_bs);
+    const long long t = *t_dev;
+    if (threadIdx.x == 0) sched_step(a.B, a.C, t, s_bs);
     __syncthreads();
     const int n = blockIdx.x * blockDim.x + threadIdx.x;
     if (n >= g.N) return;
-    double ktd[DD], sig[NS];
+    double ktd[DD], kprev[DD], sig[NS];
 #pragma unroll
-    for (int c = 0; c < DD; ++c) ktd[c] = kappa_in[(long long)c * g.N + n];
-    hist_commit<D, R>(a, s_bs, g.Npad, n, ktd, g.ch[chan_index(g, n)].G_inf, sig);
+    for (int c = 0; c < DD; ++c) {
+        ktd[c] = kappa_in[(long long)c * g.N + n];
+        kprev[c] = kappa_f[c * g.Npad + n];
+    }
+    hist_commit_any<D>(a, s_bs, g.Npad, n, kprev, ktd, g.ch[chan_index(g, n)].G_inf, sig, t);
 #pragma unroll
     for (int i = 0; i < NS; ++i) {
         sigma_f[i * g.Npad + n] = sig[i];
@@ -512,14 +871,15 @@ template <typename P> struct CollArgs {
 // One node per thread: history commit (sigma_struc(t), merges, new point), then the collision with
 // that stress and push streaming.  T: arithmetic type of the collision (double for double populations;
 // float for float).
-template <int Q, typename P, typename T, typename R>
-__global__ void __launch_bounds__(256) k_collide_stream(CollArgs<P> a, CommitArgs<R> h, Geom g) {
+template <int Q, typename P, typename T, class H>
+__global__ void __launch_bounds__(256) k_collide_stream(CollArgs<P> a, H h, Geom g) {
     using L = Lattice<Q>;
     constexpr int D = L::D;
     constexpr int DD = D * D;
     constexpr int NS = D == 2 ? 3 : 6;
     __shared__ BlockStep s_bs[LBVE_MAXB];
-    if (threadIdx.x == 0) sched_step(h.B, h.C, *a.t_dev, s_bs);
+    const long long t = *a.t_dev;
+    if (threadIdx.x == 0) sched_step(h.B, h.C, t, s_bs);
     __syncthreads();
     const int n = blockIdx.x * blockDim.x + threadIdx.x;
     if (n >= g.N) return;
@@ -527,9 +887,11 @@ __global__ void __launch_bounds__(256) k_collide_stream(CollArgs<P> a, CommitArg
     const Chan& p = g.ch[chan_index(g, n)];
     double sg[NS];
     {
-        double ktd[DD];
+        double ktd[DD], kprev[DD];
         kappa_fd<D>(a.u_raw, Np, p, n, ktd);
-        hist_commit<D, R>(h, s_bs, Np, n, ktd, p.G_inf, sg);
+#pragma unroll
+        for (int c = 0; c < DD; ++c) kprev[c] = a.kappa[c * Np + n];
+        hist_commit_any<D>(h, s_bs, Np, n, kprev, ktd, p.G_inf, sg, t);
 #pragma unroll
         for (int i = 0; i < NS; ++i) a.sigma[i * Np + n] = sg[i];
 #pragma unroll

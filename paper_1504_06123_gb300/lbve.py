@@ -21,7 +21,7 @@ LBVE_OK, LBVE_EINVAL, LBVE_ENOMEM, LBVE_ECUDA, LBVE_ENONFINITE, LBVE_ESTATE, LBV
 LBVE_ETOOBIG = -8
 LBVE_FIXED_STAGING_DOUBLES = 1 << 21
 LBVE_D2Q9, LBVE_D3Q19 = 9, 19
-LBVE_F32, LBVE_F64, LBVE_BF16 = 0, 1, 2
+LBVE_F32, LBVE_F64, LBVE_BF16, LBVE_S16 = 0, 1, 2, 3
 LBVE_TRACE_FULL, LBVE_TRACE_NONE = 0, 1
 LBVE_FIELD_RHO, LBVE_FIELD_U, LBVE_FIELD_SIGMA, LBVE_FIELD_KAPPA, LBVE_FIELD_N1 = 1, 2, 4, 8, 16
 

@@ -9,6 +9,7 @@ to rounding, e.g. u_y in channel flow):
                                                                steps and measured against a flow that has
                                                                decayed 40x after cessation: 1.3e-5 seen)
   FP64                                               <= 1e-11
+  16-bit block-scaled history (LBVE_S16), FP64 populations <= 1e-3 (the stated bar of the precision variant)
 Integer/structural results (x-invariance, history grid) are compared exactly.
 """
 import math
@@ -23,10 +24,10 @@ from paper_1504_06123_gb300 import lbve as L
 torch = pytest.importorskip("torch")
 pytestmark = pytest.mark.gpu
 
-F32, F64 = L.LBVE_F32, L.LBVE_F64
+F32, F64, S16 = L.LBVE_F32, L.LBVE_F64, L.LBVE_S16
 # (population precision, history precision) -> tolerance
-PLAIN, ALL32, ALL64 = (F64, F32), (F32, F32), (F64, F64)
-TOL = {PLAIN: 1e-5, ALL32: 5e-5, ALL64: 1e-11, F32: 1e-5, F64: 1e-11}
+PLAIN, ALL32, ALL64, RED = (F64, F32), (F32, F32), (F64, F64), (F64, S16)
+TOL = {PLAIN: 1e-5, ALL32: 5e-5, ALL64: 1e-11, RED: 1e-3, F32: 1e-5, F64: 1e-11, S16: 1e-3}
 
 
 def rel_err(x, ref):
@@ -55,15 +56,17 @@ def compare(gpu: dict, orc: dict, tol: float, what: str):
     assert e <= tol, f"{what}: rho normwise error {e:.3e}"
     dr_ref = orc["rho"] - 1.0
     if np.max(np.abs(dr_ref)) >= 1e-6:
+        # the density deviation carries the trace of sigma (second order in the shear, like N1): its
+        # relative error is 10x that of sigma's field-wise error
         e = np.max(np.abs((gpu["rho"] - 1.0) - dr_ref)) / np.max(np.abs(dr_ref))
-        tol_dr = 1e-3 if tol > 1e-8 else 1e-9
+        tol_dr = 1e-9 if tol <= 1e-8 else max(1e-3, 10 * tol)
         assert e <= tol_dr, f"{what}: rho deviation error {e:.3e} > {tol_dr:.0e}"
 
 
 # ---------------------------------------------------------------------------------------------
 # The history integral alone (Sec. III steps on a prescribed gradient): lbve_history_apply
 # ---------------------------------------------------------------------------------------------
-@pytest.mark.parametrize("prec", [L.LBVE_F32, L.LBVE_F64])
+@pytest.mark.parametrize("prec", [L.LBVE_F32, L.LBVE_F64, L.LBVE_S16])
 @pytest.mark.parametrize("lattice,nx,ny,nz,C,B", [
     (L.LBVE_D2Q9, 7, 115, 1, 16, 4),      # 805 nodes: several tiles + ragged tail
     (L.LBVE_D2Q9, 1, 9, 1, 8, 1),         # uniform ring, tiny
@@ -97,7 +100,7 @@ def test_history_apply_vs_oracle(prec, lattice, nx, ny, nz, C, B):
 # ---------------------------------------------------------------------------------------------
 # Full hybrid step: startup and cessation in the small channel (plain FP32 and FP64)
 # ---------------------------------------------------------------------------------------------
-@pytest.mark.parametrize("prec", [PLAIN, ALL32, ALL64])
+@pytest.mark.parametrize("prec", [PLAIN, ALL32, ALL64, RED])
 @pytest.mark.parametrize("C,B", [(256, 1), (64, 4)])
 def test_small_channel_startup_cessation(prec, C, B):
     w = configs.plain_channel_small()
@@ -132,7 +135,7 @@ def test_small_channel_startup_cessation(prec, C, B):
     dict(lattice=L.LBVE_D3Q19, nx=2, ny=5, nz=4, C=4, B=3, G_inf=0.01, tau=25.0, gamma_c=0.1, g=2e-5,
          wall_z=0, noise=1e-4),
 ])
-@pytest.mark.parametrize("prec", [PLAIN, ALL32, ALL64])
+@pytest.mark.parametrize("prec", [PLAIN, ALL32, ALL64, RED])
 def test_edge_cases_vs_oracle(case, prec):
     c = dict(case)
     noise = c.pop("noise", 0.0)
@@ -153,6 +156,8 @@ def test_edge_cases_vs_oracle(case, prec):
     # with density noise the first step's gradients (~1e-9, from the noise alone) are below what an
     # FP32 velocity difference resolves; compare once the driven flow dominates
     first = 1 if (noise == 0 or prec == ALL64) else None
+    if prec == RED and noise:
+        first = None
     for n in (1, 5, 60, 200):
         ch.step(n)
         orc.step(n)
@@ -254,7 +259,7 @@ BATCH = [
 ]
 
 
-@pytest.mark.parametrize("prec", [PLAIN, ALL64])
+@pytest.mark.parametrize("prec", [PLAIN, ALL64, RED])
 def test_batched_channels_vs_oracle(prec):
     C, B = 16, 4
     descs = [L.make_desc(L.LBVE_D2Q9, c["nx"], c["ny"], tau_lb=c["tau_lb"], G_inf=c["G_inf"], tau=c["tau"],
@@ -329,3 +334,28 @@ def test_graph_replay_matches_single_steps():
     assert s >= 1 and ctas >= 1
     a.close()
     b.close()
+
+
+# ---------------------------------------------------------------------------------------------
+# Precision variant on the duct: 32^3 sub-run of the 128^3 workload's parameters, per-field errors
+# ---------------------------------------------------------------------------------------------
+def test_duct_subrun_reduced_precision_per_field():
+    w = configs.duct_3d()
+    n, C, B, steps = 32, 32, 4, 40
+    # the sub-run keeps the duct's parameters; its force keeps the Peclet number of the smaller duct
+    g = configs.force_for_peclet(30.0, n / 2, w.tau_lb, w.G_inf, w.tau, w.gamma_c)
+    orc = oracle.Channel(oracle.D3Q19, n, n, n, tau_lb=w.tau_lb, G_inf=w.G_inf, tau=w.tau, gamma_c=w.gamma_c,
+                         g=(g, 0, 0), C=C, B=B)
+    ch = L.Channel(L.make_desc(L.LBVE_D3Q19, n, n, n, tau_lb=w.tau_lb, G_inf=w.G_inf, tau=w.tau, gamma_c=w.gamma_c,
+                               g=(g, 0, 0), C=C, B=B, precision=F64, hist_storage=S16))
+    ch.step(steps)
+    orc.step(steps)
+    f, o = ch.fields(), orc.fields()
+    errs = {k: rel_err(f[k], o[k]) for k in ("u", "sigma", "kappa")}
+    errs["sigma_xy"] = rel_err(f["sigma"][:, 3], o["sigma"][:, 3])
+    errs["n1_on_sigma_scale"] = float(np.max(np.abs(f["n1"] - o["n1"])) / np.max(np.abs(o["sigma"])))
+    errs["rho"] = rel_err(f["rho"], o["rho"])
+    print("duct 32^3 S16 per-field errors:", {k: f"{v:.2e}" for k, v in errs.items()})
+    for k, v in errs.items():
+        assert v <= TOL[RED], (k, v)
+    ch.close()

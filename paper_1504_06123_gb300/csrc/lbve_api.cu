@@ -208,10 +208,10 @@ int launch_sweep(lbve* h, cudaStream_t s) {
 
 CommitS16 commit_s16(lbve* h) {
     CommitS16 c;
-    c.Qm = (short*)h->X;
-    c.Qe = (signed char*)h->Qe;
-    c.Km = (short*)h->K;
-    c.Ke = (signed char*)h->Ke;
+    c.Qm = (unsigned short*)h->X;
+    c.Qe = (unsigned char*)h->Qe;
+    c.Km = (unsigned short*)h->K;
+    c.Ke = (unsigned char*)h->Ke;
     c.Rm = (float*)h->Rm;
     c.part = (const float*)h->part;
     c.B = h->d.hist_B;

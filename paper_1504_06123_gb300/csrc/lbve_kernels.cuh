@@ -208,6 +208,17 @@ __device__ __forceinline__ void expm1_mat(const real* K, real* A) {
 
 // The integrand of one history point with E = 1 + X: w G(age) (E kappa E^T + (E kappa E^T)^T), G of
 // Eq. (nlmax) without the factor G_inf, accumulated into acc (nsig packed components).
+template <typename real> struct FastMath {
+    // exp(-x) and sqrt(x) as used by the integrand (double: the library functions)
+    __device__ static __forceinline__ real exp_neg(real x) { return exp(-x); }
+    __device__ static __forceinline__ real sqrt_pos(real x) { return sqrt(x); }
+};
+template <> struct FastMath<float> {
+    // single-precision hardware approximations (2 ulp): exp(-x) = 2^(-x log2 e); sqrt(x) = x rsqrt(x)
+    __device__ static __forceinline__ float exp_neg(float x) { return exp2f(-1.4426950408889634f * x); }
+    __device__ static __forceinline__ float sqrt_pos(float x) { return x > 0.0f ? x * rsqrtf(x) : 0.0f; }
+};
+
 template <int D, typename real>
 __device__ __forceinline__ void point_integrand(const real* X, const real* kap, real age, real w,
                                                 real inv_tau, real inv_gc, real* acc) {
@@ -242,8 +253,8 @@ __device__ __forceinline__ void point_integrand(const real* X, const real* kap, 
             const real Drc = kap[r * D + c] + kap[c * D + r];
             trD2 += Drc * Drc;
         }
-    const real gd = sqrt(real(0.5) * trD2);
-    const real gw = w * exp(-age * (inv_tau + gd * inv_gc));
+    const real gd = FastMath<real>::sqrt_pos(real(0.5) * trD2);
+    const real gw = w * FastMath<real>::exp_neg(age * (inv_tau + gd * inv_gc));
     if (D == 2) {
         acc[0] += gw * (M[0] + M[0]);
         acc[1] += gw * (M[3] + M[3]);
@@ -501,32 +512,60 @@ __device__ __forceinline__ void hist_commit_any(const CommitArgs<R>& a, const Bl
 // ------------------------------------------------------------------------------------------------
 __device__ __forceinline__ float pow2f(int k) { return __int_as_float((k + 127) << 23); }   // -126 <= k <= 127
 
+// Stored form of a block-scaled vector: unsigned halves u_c = m_c + 32768 and the exponent byte
+// eb = e + 127 (eb = 0 for the zero vector), so that all-zero bytes decode to 0 (a rest point) and the
+// scale 2^e is the float whose exponent field is eb.
 template <int DD>
-__device__ __forceinline__ void s16_encode(const float* v, short* m, signed char* e) {
+__device__ __forceinline__ void s16_encode(const float* v, unsigned short* u, unsigned char* eb) {
     float mx = 0.0f;
 #pragma unroll
     for (int c = 0; c < DD; ++c) mx = fmaxf(mx, fabsf(v[c]));
+    if (!(mx > 0.0f)) {
+#pragma unroll
+        for (int c = 0; c < DD; ++c) u[c] = 32768;
+        *eb = 0;
+        return;
+    }
     int ex = 0;
-    if (mx > 0.0f && mx <= 3.0e38f) frexpf(mx, &ex);          // mx = f 2^ex, 0.5 <= f < 1
+    frexpf(fminf(mx, 3.0e38f), &ex);                              // mx = f 2^ex, 0.5 <= f < 1
     const int es = min(126, max(-126, ex - 15));                 // |v| < 2^ex  =>  |v| 2^-es < 2^15
     const float inv = pow2f(-es);
 #pragma unroll
-    for (int c = 0; c < DD; ++c) m[c] = (short)fminf(32767.0f, fmaxf(-32767.0f, rintf(v[c] * inv)));
-    *e = (signed char)es;
+    for (int c = 0; c < DD; ++c)
+        u[c] = (unsigned short)(32768 + (int)fminf(32767.0f, fmaxf(-32767.0f, rintf(v[c] * inv))));
+    *eb = (unsigned char)(es + 127);
 }
+
+__device__ __forceinline__ float s16_scale(unsigned eb) { return __int_as_float((int)(eb << 23)); }
 
 template <int DD>
-__device__ __forceinline__ void s16_decode(const short* m, int e, float* v) {
-    const float sc = pow2f(e);
+__device__ __forceinline__ void s16_decode(const unsigned short* u, unsigned eb, float* v) {
+    const float sc = s16_scale(eb);
 #pragma unroll
-    for (int c = 0; c < DD; ++c) v[c] = (float)m[c] * sc;
+    for (int c = 0; c < DD; ++c) v[c] = (float)((int)u[c] - 32768) * sc;
 }
 
+// Decode of packed halves without int->float conversions: a half u placed under the exponent of
+// 1.5 * 2^23 is the float 12582912 + u exactly; f sc - 12615680 sc = (u - 32768) sc is then exact (at
+// most 16 significant bits) in one FMA.
+struct S16Scale {
+    float sc, c1;
+    S16Scale() = default;
+    __device__ __forceinline__ explicit S16Scale(unsigned eb) : sc(s16_scale(eb)), c1(-12615680.0f * s16_scale(eb)) {}
+};
+__device__ __forceinline__ float s16_lo(unsigned w, const S16Scale& s) {
+    return fmaf(__int_as_float((int)__byte_perm(w, 0x4B40u, 0x5410)), s.sc, s.c1);
+}
+__device__ __forceinline__ float s16_hi(unsigned w, const S16Scale& s) {
+    return fmaf(__int_as_float((int)__byte_perm(w, 0x4B40u, 0x5432)), s.sc, s.c1);
+}
+__device__ __forceinline__ unsigned s16_exp(unsigned word, int j) { return (word >> (8 * j)) & 0xFFu; }
+
 struct CommitS16 {
-    short* __restrict__ Qm;          // [L][DD][Npad] mantissas of Q - 1
-    signed char* __restrict__ Qe;    // [L][Npad] exponents
-    short* __restrict__ Km;          // [L][DD][Npad] mantissas of kappa
-    signed char* __restrict__ Ke;    // [L][Npad]
+    unsigned short* __restrict__ Qm; // [L][DD][Npad] biased mantissas of Q - 1
+    unsigned char* __restrict__ Qe;  // [L][Npad] biased exponents
+    unsigned short* __restrict__ Km; // [L][DD][Npad] biased mantissas of kappa
+    unsigned char* __restrict__ Ke;  // [L][Npad]
     float* __restrict__ Rm;          // [DD][Npad] frame R - 1 of each node
     const float* __restrict__ part;  // [S][NS][Npad]
     int B, C, S, TB;
@@ -582,33 +621,73 @@ __device__ __forceinline__ void frame_inverse_dev(const float* M, float* X) {
         }
 }
 
+// sigma of a node from the frame-free sum: the sweep accumulates P = sum w G (Q kappa Q^T + (.)^T) (packed
+// symmetric, NS components); since every point of the node sees the same frame, the sum with
+// E = R Q is R P R^T.
+template <int D>
+__device__ __forceinline__ void frame_apply(const float* Rm, const double* p, double* out) {
+    double P[D][D], R[D][D], RP[D][D];
+    if (D == 2) {
+        P[0][0] = p[0]; P[1][1] = p[1]; P[0][1] = P[1][0] = p[2];
+    } else {
+        P[0][0] = p[0]; P[1][1] = p[1]; P[2][2] = p[2];
+        P[0][1] = P[1][0] = p[3]; P[0][2] = P[2][0] = p[4]; P[1][2] = P[2][1] = p[5];
+    }
+#pragma unroll
+    for (int r = 0; r < D; ++r)
+#pragma unroll
+        for (int c = 0; c < D; ++c) R[r][c] = (double)Rm[r * D + c] + (r == c ? 1.0 : 0.0);
+#pragma unroll
+    for (int r = 0; r < D; ++r)
+#pragma unroll
+        for (int c = 0; c < D; ++c) {
+            double acc = 0.0;
+#pragma unroll
+            for (int k = 0; k < D; ++k) acc += R[r][k] * P[k][c];
+            RP[r][c] = acc;
+        }
+    double S[D][D];
+#pragma unroll
+    for (int r = 0; r < D; ++r)
+#pragma unroll
+        for (int c = 0; c < D; ++c) {
+            double acc = 0.0;
+#pragma unroll
+            for (int k = 0; k < D; ++k) acc += RP[r][k] * R[c][k];
+            S[r][c] = acc;
+        }
+    if (D == 2) {
+        out[0] = S[0][0]; out[1] = S[1][1]; out[2] = S[0][1];
+    } else {
+        out[0] = S[0][0]; out[1] = S[1][1]; out[2] = S[2][2];
+        out[3] = S[0][1]; out[4] = S[0][2]; out[5] = S[1][2];
+    }
+}
+
 template <int D>
 __device__ __forceinline__ void hist_commit_any(const CommitS16& a, const BlockStep* s_bs, long long Np, int n,
                                                 const double* kprev, const double* ktd, double G_inf,
                                                 double* sig, long long t) {
     constexpr int DD = D * D;
     constexpr int NS = D == 2 ? 3 : 6;
-    // the frame of this step (identical arithmetic to the sweep's), then the rebase
+    // the frame of this step (identical arithmetic to the sweep's rebase path), then the rebase
     float Rm[DD], Rn[DD];
 #pragma unroll
     for (int c = 0; c < DD; ++c) Rm[c] = a.Rm[c * Np + n];
     frame_advance<D>(kprev, Rm, Rn);
     const bool rebase = (t % a.TB) == 0;
+    // sigma: R (sum of chunk partials) R^T + the point created now (its stored, rounded kappa; E = 1,
+    // weight 1/2)
+    double acc[NS], P[NS];
 #pragma unroll
-    for (int c = 0; c < DD; ++c) {
-        if (rebase) Rn[c] = 0.0f;
-        a.Rm[c * Np + n] = Rn[c];
-    }
-    // sigma: chunk partials + the point created now (its stored, rounded kappa; E = 1, weight 1/2)
-    double acc[NS];
-#pragma unroll
-    for (int i = 0; i < NS; ++i) acc[i] = 0.0;
+    for (int i = 0; i < NS; ++i) P[i] = 0.0;
     for (int c = 0; c < a.S; ++c)
 #pragma unroll
-        for (int i = 0; i < NS; ++i) acc[i] += (double)a.part[((long long)c * NS + i) * Np + n];
+        for (int i = 0; i < NS; ++i) P[i] += (double)a.part[((long long)c * NS + i) * Np + n];
+    frame_apply<D>(Rn, P, acc);
     float kt[DD];
-    short km[DD];
-    signed char ke;
+    unsigned short km[DD];
+    unsigned char ke;
 #pragma unroll
     for (int c = 0; c < DD; ++c) kt[c] = (float)ktd[c];
     s16_encode<DD>(kt, km, &ke);
@@ -627,6 +706,11 @@ __device__ __forceinline__ void hist_commit_any(const CommitS16& a, const BlockS
     }
 #pragma unroll
     for (int i = 0; i < NS; ++i) sig[i] = G_inf * acc[i];
+#pragma unroll
+    for (int c = 0; c < DD; ++c) {
+        if (rebase) Rn[c] = 0.0f;
+        a.Rm[c * Np + n] = Rn[c];
+    }
     // block merges, coarsest first: the older point's Q moves, kappa is averaged and re-encoded
     for (int bb = 1; bb < a.B; ++bb) {
         const BlockStep& b = s_bs[bb];
@@ -635,9 +719,9 @@ __device__ __forceinline__ void hist_commit_any(const CommitS16& a, const BlockS
         int o2 = b.head_prev - (a.C - 2); if (o2 < 0) o2 += a.C;
         const long long src1 = (long long)bb * a.C + o1, src2 = (long long)bb * a.C + o2;
         const long long dst = (long long)(bb - 1) * a.C + s_bs[bb - 1].head_new;
-        short m1[DD], m2[DD], mo[DD];
+        unsigned short m1[DD], m2[DD], mo[DD];
         float k1[DD], k2[DD];
-        signed char eo;
+        unsigned char eo;
 #pragma unroll
         for (int c = 0; c < DD; ++c) {
             a.Qm[(dst * DD + c) * Np + n] = a.Qm[(src1 * DD + c) * Np + n];
@@ -657,8 +741,8 @@ __device__ __forceinline__ void hist_commit_any(const CommitS16& a, const BlockS
     // the new point: Q = R^-1 of the frame after this step, kappa(t)
     const long long dst = (long long)(a.B - 1) * a.C + s_bs[a.B - 1].head_new;
     float X[DD];
-    short qm[DD];
-    signed char qe;
+    unsigned short qm[DD];
+    unsigned char qe;
     frame_inverse_dev<D>(Rn, X);
     s16_encode<DD>(X, qm, &qe);
 #pragma unroll
@@ -670,17 +754,20 @@ __device__ __forceinline__ void hist_commit_any(const CommitS16& a, const BlockS
     a.Ke[dst * Np + n] = ke;
 }
 
-// Sweep of the 16-bit history: lanes hold VN consecutive nodes (VN-wide loads of every mantissa and
-// exponent plane), tasks as in k_sweep.  E - 1 = Rm + Q - 1 + Rm (Q - 1) with the frame of this step;
-// on rebase steps the point's Q is rewritten as E(t, t').
+// Sweep of the 16-bit history: lanes hold VN consecutive nodes (one 32-bit word of exponents and VN/2
+// words of mantissas per plane), tasks as in k_sweep.  Each point contributes with Q in place of E
+// (the frame is applied once per node in the commit); on rebase steps the point's Q is rewritten as
+// E(t, t') = R Q with the frame of this step.
 template <int D, int VN>
 __global__ void __launch_bounds__(256, 2) k_sweep_s16(CommitS16 a, const double* __restrict__ kprev,
                                                       const long long* t_dev, Geom g) {
     constexpr int DD = D * D;
     constexpr int NS = D == 2 ? 3 : 6;
-    using VS = Vec<short, VN>;
-    using VE = Vec<signed char, VN>;
+    static_assert(VN == 2 || VN == 4, "packed decode handles 2 or 4 nodes per lane");
+    using VW = Vec<unsigned, VN / 2>;
     using VF = Vec<float, VN>;
+    using VS = Vec<unsigned short, VN>;
+    using VE = Vec<unsigned char, VN>;
     const int L = a.B * a.C;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     float* s_age = reinterpret_cast<float*>(smem_raw);
@@ -714,14 +801,14 @@ __global__ void __launch_bounds__(256, 2) k_sweep_s16(CommitS16 a, const double*
         const int chunk = task / tiles;
         const long long n0 = (long long)tile * 32 * VN + lane * VN;
         float inv_tau[VN], inv_gc[VN];
-        float F[VN][DD];   // frame of this step, R - 1
 #pragma unroll
         for (int j = 0; j < VN; ++j) {
             const Chan& c = g.ch[chan_index(g, n0 + j)];
             inv_tau[j] = (float)c.inv_tau;
             inv_gc[j] = (float)c.inv_gc;
         }
-        {
+        float F[VN][DD];   // frame of this step, R - 1 (needed on rebase steps only)
+        if (rebase) {
             float Rm[VN][DD];
             double kp[VN][DD];
 #pragma unroll
@@ -746,62 +833,66 @@ __global__ void __launch_bounds__(256, 2) k_sweep_s16(CommitS16 a, const double*
         const int l1 = min(L, l0 + chunk_len);
         for (int l = l0; l < l1; ++l) {
             const float w = s_w[l];
-            if (w == 0.0f) continue;
-            short qm[VN][DD], km[VN][DD];
-            const VE qe = *reinterpret_cast<const VE*>(a.Qe + (long long)l * Np + n0);
-            const VE ke = *reinterpret_cast<const VE*>(a.Ke + (long long)l * Np + n0);
+            if (w == 0.0f) continue;                 // same slot for the whole warp: uniform branch
+            const unsigned qe = VN == 4 ? *reinterpret_cast<const unsigned*>(a.Qe + (long long)l * Np + n0)
+                                        : *reinterpret_cast<const unsigned short*>(a.Qe + (long long)l * Np + n0);
+            const unsigned ke = VN == 4 ? *reinterpret_cast<const unsigned*>(a.Ke + (long long)l * Np + n0)
+                                        : *reinterpret_cast<const unsigned short*>(a.Ke + (long long)l * Np + n0);
+            float kap[VN][DD], Qd[VN][DD];
+            {
+                S16Scale sq[VN], sk[VN];
 #pragma unroll
-            for (int c = 0; c < DD; ++c) {
-                const VS qv = *reinterpret_cast<const VS*>(a.Qm + ((long long)l * DD + c) * Np + n0);
-                const VS kv = *reinterpret_cast<const VS*>(a.Km + ((long long)l * DD + c) * Np + n0);
-#pragma unroll
-                for (int j = 0; j < VN; ++j) { qm[j][c] = qv.v[j]; km[j][c] = kv.v[j]; }
-            }
-            float kap[VN][DD];
-#pragma unroll
-            for (int j = 0; j < VN; ++j) s16_decode<DD>(km[j], ke.v[j], kap[j]);
-            const int part = s_part[l];
-            if (part >= 0) {   // older half of a merge: kappa averaged with the newer half
-                const VE ke2 = *reinterpret_cast<const VE*>(a.Ke + (long long)part * Np + n0);
-                short km2[VN][DD];
+                for (int j = 0; j < VN; ++j) { sq[j] = S16Scale(s16_exp(qe, j)); sk[j] = S16Scale(s16_exp(ke, j)); }
 #pragma unroll
                 for (int c = 0; c < DD; ++c) {
-                    const VS kv = *reinterpret_cast<const VS*>(a.Km + ((long long)part * DD + c) * Np + n0);
+                    const VW qv = *reinterpret_cast<const VW*>(a.Qm + ((long long)l * DD + c) * Np + n0);
+                    const VW kv = *reinterpret_cast<const VW*>(a.Km + ((long long)l * DD + c) * Np + n0);
 #pragma unroll
-                    for (int j = 0; j < VN; ++j) km2[j][c] = kv.v[j];
+                    for (int p2 = 0; p2 < VN / 2; ++p2) {
+                        Qd[2 * p2][c] = s16_lo(qv.v[p2], sq[2 * p2]);
+                        Qd[2 * p2 + 1][c] = s16_hi(qv.v[p2], sq[2 * p2 + 1]);
+                        kap[2 * p2][c] = s16_lo(kv.v[p2], sk[2 * p2]);
+                        kap[2 * p2 + 1][c] = s16_hi(kv.v[p2], sk[2 * p2 + 1]);
+                    }
                 }
+            }
+            const int part = s_part[l];
+            if (part >= 0) {   // older half of a merge: kappa averaged with the newer half
+                const unsigned ke2 = VN == 4 ? *reinterpret_cast<const unsigned*>(a.Ke + (long long)part * Np + n0)
+                                             : *reinterpret_cast<const unsigned short*>(a.Ke + (long long)part * Np + n0);
+                S16Scale sk2[VN];
 #pragma unroll
-                for (int j = 0; j < VN; ++j) {
-                    float k2[DD];
-                    s16_decode<DD>(km2[j], ke2.v[j], k2);
+                for (int j = 0; j < VN; ++j) sk2[j] = S16Scale(s16_exp(ke2, j));
 #pragma unroll
-                    for (int c = 0; c < DD; ++c) kap[j][c] = 0.5f * (kap[j][c] + k2[c]);
+                for (int c = 0; c < DD; ++c) {
+                    const VW kv = *reinterpret_cast<const VW*>(a.Km + ((long long)part * DD + c) * Np + n0);
+#pragma unroll
+                    for (int p2 = 0; p2 < VN / 2; ++p2) {
+                        kap[2 * p2][c] = 0.5f * (kap[2 * p2][c] + s16_lo(kv.v[p2], sk2[2 * p2]));
+                        kap[2 * p2 + 1][c] = 0.5f * (kap[2 * p2 + 1][c] + s16_hi(kv.v[p2], sk2[2 * p2 + 1]));
+                    }
                 }
             }
             const float age = s_age[l];
-            float X[VN][DD];
 #pragma unroll
-            for (int j = 0; j < VN; ++j) {
-                float Qd[DD];
-                s16_decode<DD>(qm[j], qe.v[j], Qd);
-                // E - 1 = F + Qd + F Qd
-#pragma unroll
-                for (int r = 0; r < D; ++r)
-#pragma unroll
-                    for (int c = 0; c < D; ++c) {
-                        float s = F[j][r * D + c] + Qd[r * D + c];
-#pragma unroll
-                        for (int k = 0; k < D; ++k) s += F[j][r * D + k] * Qd[k * D + c];
-                        X[j][r * D + c] = s;
-                    }
-                point_integrand<D>(X[j], kap[j], age, w, inv_tau[j], inv_gc[j], acc[j]);
-            }
-            if (rebase) {   // the point's Q becomes E(t, t'); the frame restarts at 1 in the commit
+            for (int j = 0; j < VN; ++j) point_integrand<D>(Qd[j], kap[j], age, w, inv_tau[j], inv_gc[j], acc[j]);
+            if (rebase) {   // the point's Q becomes E(t, t') = R Q; the frame restarts at 1 in the commit
+                unsigned short qm[VN][DD];
                 VE qe_new;
 #pragma unroll
                 for (int j = 0; j < VN; ++j) {
-                    signed char e;
-                    s16_encode<DD>(X[j], qm[j], &e);
+                    float X[DD];
+#pragma unroll
+                    for (int r = 0; r < D; ++r)
+#pragma unroll
+                        for (int c = 0; c < D; ++c) {
+                            float sum = F[j][r * D + c] + Qd[j][r * D + c];
+#pragma unroll
+                            for (int k = 0; k < D; ++k) sum += F[j][r * D + k] * Qd[j][k * D + c];
+                            X[r * D + c] = sum;
+                        }
+                    unsigned char e;
+                    s16_encode<DD>(X, qm[j], &e);
                     qe_new.v[j] = e;
                 }
                 *reinterpret_cast<VE*>(a.Qe + (long long)l * Np + n0) = qe_new;

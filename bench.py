@@ -240,6 +240,9 @@ def run_ours(args, rank, world, local_rank):
     hist = {"f32": L.LBVE_F32, "s16": L.LBVE_S16, "f64": L.LBVE_F64}[args.history]
     for d in descs:
         d.hist_storage = hist
+        if hist == L.LBVE_S16:
+            # the reduced-precision form: FP32 populations are well inside its 1e-3 budget
+            d.pop_precision = L.LBVE_F32
     d0 = descs[0]
     N = sum(d.nx * d.ny * d.nz for d in descs)
     D = 2 if d0.lattice == L.LBVE_D2Q9 else 3

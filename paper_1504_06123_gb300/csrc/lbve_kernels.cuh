@@ -831,9 +831,11 @@ __global__ void __launch_bounds__(256, 2) k_sweep_s16(CommitS16 a, const double*
 
         const int l0 = chunk * chunk_len;
         const int l1 = min(L, l0 + chunk_len);
+        // no branch on empty or retired slots: they have weight 0 and hold finite data from their
+        // last use, so they add exactly 0; the straight loop lets loads of the next slot overlap
+#pragma unroll 2
         for (int l = l0; l < l1; ++l) {
             const float w = s_w[l];
-            if (w == 0.0f) continue;                 // same slot for the whole warp: uniform branch
             const unsigned qe = VN == 4 ? *reinterpret_cast<const unsigned*>(a.Qe + (long long)l * Np + n0)
                                         : *reinterpret_cast<const unsigned short*>(a.Qe + (long long)l * Np + n0);
             const unsigned ke = VN == 4 ? *reinterpret_cast<const unsigned*>(a.Ke + (long long)l * Np + n0)

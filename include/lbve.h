@@ -163,6 +163,19 @@ int lbve_mass(lbve_t* h, double* sum_n, double* sum_drho, void* stream);
  */
 int lbve_schedule(int32_t C, int32_t B, int64_t t, int64_t* tp_out, double* w_out, int32_t* n_out);
 
+/*
+ * Differentiation: a channel whose every state value also carries its derivatives with respect to the
+ * four model parameters theta = (G_inf, tau, gamma_c, g_x) -- the tangent-linear model of the same
+ * hybrid step (Sec. III), in double precision, one channel.  lbve_step, lbve_fields, lbve_set_force,
+ * lbve_set_params and lbve_destroy work on it as on any handle (derivatives are taken at the current
+ * parameter values; a later parameter change does not reset the accumulated derivatives).
+ * lbve_tangent_fields writes d(field)/d(theta_k) for k = 0..3 to host memory: four consecutive blocks,
+ * each in the layout of lbve_fields (lbve_fields_count(h, mask) doubles per block).  Synchronises.
+ * ESTATE when h is not a tangent handle.
+ */
+int lbve_create_tangent(const lbve_channel_desc* desc, const double* rho_init, lbve_t** out);
+int lbve_tangent_fields(lbve_t* h, uint32_t field_mask, double* dst_host, void* stream);
+
 /* Device bytes held by the handle (populations, history, fields). */
 int lbve_memory_bytes(const lbve_t* h, size_t* bytes);
 

@@ -18,6 +18,7 @@
 
 #include "../../include/lbve.h"
 #include "lbve_kernels.cuh"
+#include "lbve_tangent.cuh"
 
 using namespace lbk;
 
@@ -81,6 +82,8 @@ struct lbve {
     // captured steps: kGraphSteps steps, both population parities (the graph is replayed from cur == 0)
     cudaGraphExec_t graph = nullptr;
     cudaStream_t graph_stream = nullptr;
+    // tangent-linear mode (lbve_create_tangent): all state buffers hold duals
+    int tangent = 0;
     // kernel timing (lbve_profile): event pairs recorded around each launch of lbve_step
     int profiling = 0;
     std::vector<cudaEvent_t> ev_pool;
@@ -613,6 +616,163 @@ int create_impl(const lbve_channel_desc* descs, int32_t n, const double* rho_ini
     return LBVE_OK;
 }
 
+TanPar tan_par(const lbve* h) {
+    const lbve_channel_desc& d = h->descs[0];
+    TanPar p;
+    p.G_inf = Dual(d.G_inf);
+    p.G_inf.d[0] = 1.0;
+    p.inv_tau = Dual(1.0 / d.tau);
+    p.inv_tau.d[1] = -1.0 / (d.tau * d.tau);
+    p.inv_gc = Dual(std::isinf(d.gamma_c) ? 0.0 : 1.0 / d.gamma_c);
+    if (!std::isinf(d.gamma_c)) p.inv_gc.d[2] = -1.0 / (d.gamma_c * d.gamma_c);
+    for (int a = 0; a < 3; ++a) p.f[a] = Dual(d.rho0 * d.g[a]);
+    p.f[0].d[3] = d.rho0;
+    p.rho0 = d.rho0;
+    p.tau_lb = d.tau_lb;
+    p.trace_full = d.trace_coupling == LBVE_TRACE_FULL;
+    return p;
+}
+
+template <int Q>
+int tangent_step(lbve* h, int64_t n, cudaStream_t s) {
+    constexpr int D = Lattice<Q>::D;
+    const Geom g = geom_of(h);
+    const TanPar p = tan_par(h);
+    const int grid = (h->N + 127) / 128;
+    const size_t smem = sweep_smem_bytes(h->L);
+    for (int64_t i = 0; i < n; ++i) {
+        const Dual* din = (const Dual*)h->pops[h->cur];
+        Dual* dout = (Dual*)h->pops[h->cur ^ 1];
+        k_moments_t<Q><<<grid, 128, 0, s>>>(din, (Dual*)h->u_raw, g, p, h->t_dev);
+        LBVE_CUDA(cudaGetLastError());
+        k_history_t<D><<<grid, 128, smem, s>>>((Dual*)h->X, (Dual*)h->K, (const Dual*)h->u_raw, (Dual*)h->kappa,
+                                               (Dual*)h->sigma, g, p, h->t_dev, h->d.hist_B, h->d.hist_C);
+        LBVE_CUDA(cudaGetLastError());
+        k_collide_t<Q><<<grid, 128, 0, s>>>(din, dout, (const Dual*)h->sigma, (Dual*)h->tr_prev, (Dual*)h->rho,
+                                            (Dual*)h->u, g, p);
+        LBVE_CUDA(cudaGetLastError());
+        h->cur ^= 1;
+        h->t_host += 1;
+    }
+    return LBVE_OK;
+}
+
+// Value (k < 0) or derivative k of the selected fields, into device memory, lbve_fields layout.
+int tangent_gather(lbve* h, uint32_t mask, int k, double* dst, cudaStream_t s) {
+    const long long Np = h->Npad;
+    const int N = h->N;
+    size_t off = 0;
+    struct Part { uint32_t bit; const void* src; int ncomp; double offset; };
+    const Part parts[] = {{LBVE_FIELD_RHO, h->rho, 1, h->d.rho0},
+                          {LBVE_FIELD_U, h->u, h->D, 0.0},
+                          {LBVE_FIELD_SIGMA, h->sigma, h->NS, 0.0},
+                          {LBVE_FIELD_KAPPA, h->kappa, h->D * h->D, 0.0}};
+    for (const Part& pt : parts) {
+        if (!(mask & pt.bit)) continue;
+        const long long tot = (long long)pt.ncomp * N;
+        if (tot > 0) {
+            k_gather_t<<<(int)((tot + 255) / 256), 256, 0, s>>>((const Dual*)pt.src, Np, pt.ncomp, N, k,
+                                                                 k < 0 ? pt.offset : 0.0, dst + off);
+            LBVE_CUDA(cudaGetLastError());
+        }
+        off += (size_t)tot;
+    }
+    if ((mask & LBVE_FIELD_N1) && N > 0) {
+        k_n1_t<<<(N + 255) / 256, 256, 0, s>>>((const Dual*)h->sigma, Np, N, k, dst + off);
+        LBVE_CUDA(cudaGetLastError());
+    }
+    return LBVE_OK;
+}
+
+template <typename P>
+__global__ void k_init_t(Dual* dn, Dual* rho, long long Npad, int N, int Q, const double* rho_init, double rho0,
+                         const double* w) {
+    const int n = blockIdx.x * blockDim.x + threadIdx.x;
+    if (n >= N) return;
+    const double r = rho_init ? rho_init[n] : rho0;
+    for (int q = 0; q < Q; ++q) dn[q * Npad + n] = Dual(w[q] * (r - rho0));
+    rho[n] = Dual(r - rho0);
+}
+
+int create_tangent(const lbve_channel_desc* desc, const double* rho_init, lbve_t** out) {
+    if (!out) return LBVE_EINVAL;
+    *out = nullptr;
+    int rc = check_desc(desc);
+    if (rc) return rc;
+    const long long Ntot = (long long)desc->nx * desc->ny * desc->nz;
+    if (rho_init)
+        for (long long i = 0; i < Ntot; ++i)
+            if (!std::isfinite(rho_init[i]) || !(rho_init[i] > 0)) return LBVE_EINVAL;
+    lbve* h = new (std::nothrow) lbve();
+    if (!h) return LBVE_ENOMEM;
+    h->tangent = 1;
+    h->d = *desc;
+    h->descs.assign(desc, desc + 1);
+    h->nchan = 1;
+    h->D = desc->lattice == LBVE_D2Q9 ? 2 : 3;
+    h->Q = desc->lattice;
+    h->NS = h->D == 2 ? 3 : 6;
+    h->N = (int)Ntot;
+    h->L = desc->hist_C * desc->hist_B;
+    h->Npad = ((long long)h->N + 127) / 128 * 128;
+    h->pop_dbl = 1;
+    h->hist_dbl = 1;
+    h->pesz = h->hesz = sizeof(Dual);
+    h->chan_host.resize(1);
+    fill_chan(*desc, 0, &h->chan_host[0]);
+    const long long Np = h->Npad;
+    const int DD = h->D * h->D;
+    const size_t e = sizeof(Dual);
+    auto fail = [&](int code) {
+        free_all(h);
+        delete h;
+        return code;
+    };
+    if ((rc = alloc(h, &h->pops[0], e * h->Q * Np)) || (rc = alloc(h, &h->pops[1], e * h->Q * Np)) ||
+        (rc = alloc(h, &h->u_raw, e * h->D * Np)) || (rc = alloc(h, &h->u, e * h->D * Np)) ||
+        (rc = alloc(h, &h->rho, e * Np)) || (rc = alloc(h, &h->sigma, e * h->NS * Np)) ||
+        (rc = alloc(h, &h->kappa, e * DD * Np)) || (rc = alloc(h, &h->tr_prev, e * Np)) ||
+        (rc = alloc(h, &h->X, e * (size_t)h->L * DD * Np)) || (rc = alloc(h, &h->K, e * (size_t)h->L * DD * Np)) ||
+        (rc = alloc(h, (void**)&h->t_dev, sizeof(long long))) || (rc = alloc(h, (void**)&h->flag, sizeof(int))) ||
+        (rc = alloc(h, (void**)&h->chan_dev, sizeof(Chan))))
+        return fail(rc);
+    void* zb[] = {h->pops[0], h->pops[1], h->u_raw, h->u, h->rho, h->sigma, h->kappa, h->tr_prev, h->X, h->K};
+    size_t zs[] = {e * h->Q * Np, e * h->Q * Np, e * h->D * Np, e * h->D * Np, e * Np, e * h->NS * Np, e * DD * Np,
+                   e * Np, e * (size_t)h->L * DD * Np, e * (size_t)h->L * DD * Np};
+    for (int i = 0; i < 10; ++i) {
+        cudaError_t er = cudaMemset(zb[i], 0, zs[i]);
+        if (er != cudaSuccess) return fail(cuda_fail(er, "cudaMemset"));
+    }
+    const long long minus_one = -1;
+    cudaError_t er = cudaMemcpy(h->t_dev, &minus_one, sizeof minus_one, cudaMemcpyHostToDevice);
+    if (er == cudaSuccess) er = cudaMemcpy(h->chan_dev, h->chan_host.data(), sizeof(Chan), cudaMemcpyHostToDevice);
+    if (er != cudaSuccess) return fail(cuda_fail(er, "cudaMemcpy"));
+    // initial populations w (rho_init - rho0), derivatives 0
+    double w[19];
+    for (int q = 0; q < h->Q; ++q) w[q] = h->Q == 9 ? Lattice<9>::w(q) : Lattice<19>::w(q);
+    double* tmp = nullptr;
+    const size_t n_tmp = h->Q + (rho_init ? (size_t)h->N : 0);
+    er = cudaMalloc(&tmp, sizeof(double) * n_tmp);
+    if (er == cudaSuccess) er = cudaMemcpy(tmp, w, sizeof(double) * h->Q, cudaMemcpyHostToDevice);
+    if (er == cudaSuccess && rho_init) er = cudaMemcpy(tmp + h->Q, rho_init, sizeof(double) * h->N, cudaMemcpyHostToDevice);
+    if (er == cudaSuccess) {
+        k_init_t<double><<<(h->N + 255) / 256, 256>>>((Dual*)h->pops[0], (Dual*)h->rho, Np, h->N, h->Q,
+                                                       rho_init ? tmp + h->Q : nullptr, h->d.rho0, tmp);
+        er = cudaGetLastError();
+    }
+    if (er == cudaSuccess) er = cudaDeviceSynchronize();
+    if (tmp) cudaFree(tmp);
+    if (er != cudaSuccess) return fail(cuda_fail(er, "tangent initial state"));
+    const size_t smem = sweep_smem_bytes(h->L);
+    if (smem > 48 * 1024) {
+        er = cudaFuncSetAttribute(h->D == 2 ? (const void*)k_history_t<2> : (const void*)k_history_t<3>,
+                                  cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (er != cudaSuccess) return fail(cuda_fail(er, "cudaFuncSetAttribute"));
+    }
+    *out = h;
+    return LBVE_OK;
+}
+
 int push_chan(lbve* h, int c, cudaStream_t s) {
     // the kernels read the table; stream order keeps earlier steps on `s` with the old values.  The
     // source is pageable host memory, so the copy has taken the entry when the call returns.
@@ -654,6 +814,11 @@ int lbve_set_force(lbve_t* h, int32_t channel, const double g[3], void* stream) 
     if (!h || !g || channel < -1 || channel >= h->nchan) return LBVE_EINVAL;
     for (int a = 0; a < 3; ++a)
         if (!std::isfinite(g[a])) return LBVE_EINVAL;
+    if (h->tangent) {   // parameters travel as kernel arguments
+        for (int a = 0; a < 3; ++a) h->descs[0].g[a] = g[a];
+        h->d = h->descs[0];
+        return LBVE_OK;
+    }
     const int c0 = channel < 0 ? 0 : channel, c1 = channel < 0 ? h->nchan : channel + 1;
     for (int c = c0; c < c1; ++c) {
         for (int a = 0; a < 3; ++a) {
@@ -683,6 +848,7 @@ int lbve_set_params(lbve_t* h, int32_t channel, double G_inf, double tau, double
         h->descs[c].tau = tau;
         h->descs[c].gamma_c = gamma_c;
         fill_chan(h->descs[c], h->chan_host[c].off, &h->chan_host[c]);
+        if (h->tangent) continue;
         int rc = push_chan(h, c, (cudaStream_t)stream);
         if (rc) return rc;
     }
@@ -693,6 +859,7 @@ int lbve_set_params(lbve_t* h, int32_t channel, double G_inf, double tau, double
 int lbve_step(lbve_t* h, int64_t n_steps, void* stream) {
     if (!h || n_steps < 0) return LBVE_EINVAL;
     cudaStream_t s = (cudaStream_t)stream;
+    if (h->tangent) return h->Q == 9 ? tangent_step<9>(h, n_steps, s) : tangent_step<19>(h, n_steps, s);
     const int hk = h->hist_s16 ? 2 : (h->hist_dbl ? 1 : 0);
     const int combo = (h->pop_dbl ? 3 : 0) + hk;
     if (h->Q == 9) {
@@ -731,6 +898,19 @@ int lbve_fields(lbve_t* h, uint32_t mask, double* dst, int32_t dst_is_device, vo
     if (!h || !dst || (mask & ~31u)) return LBVE_EINVAL;
     cudaStream_t s = (cudaStream_t)stream;
     const size_t cnt = fields_count(h, mask);
+    if (h->tangent) {
+        if (dst_is_device) return tangent_gather(h, mask, -1, dst, s);
+        double* tmp = nullptr;
+        LBVE_CUDA(cudaMallocAsync(&tmp, sizeof(double) * (cnt > 0 ? cnt : 1), s));
+        int rc = tangent_gather(h, mask, -1, tmp, s);
+        if (rc == LBVE_OK) {
+            cudaError_t e = cudaMemcpyAsync(dst, tmp, sizeof(double) * cnt, cudaMemcpyDeviceToHost, s);
+            if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+            if (e != cudaSuccess) rc = cuda_fail(e, "tangent fields");
+        }
+        cudaFreeAsync(tmp, s);
+        return rc;
+    }
     if (dst_is_device) return fields_impl(h, mask, dst, s);
     if (h->stage_n < cnt) {
         if (h->stage) cudaFree(h->stage);
@@ -751,6 +931,7 @@ int lbve_fields(lbve_t* h, uint32_t mask, double* dst, int32_t dst_is_device, vo
 
 int lbve_history_apply(lbve_t* h, const double* kappa_dev, double* sigma_dev, void* stream) {
     if (!h || !kappa_dev || !sigma_dev) return LBVE_EINVAL;
+    if (h->tangent) return LBVE_ENOSUPPORT;
     cudaStream_t s = (cudaStream_t)stream;
     k_advance_t<<<1, 1, 0, s>>>(h->t_dev);
     LBVE_CUDA(cudaGetLastError());
@@ -795,6 +976,7 @@ int lbve_history_apply(lbve_t* h, const double* kappa_dev, double* sigma_dev, vo
 
 int lbve_mass(lbve_t* h, double* sum_n, double* sum_drho, void* stream) {
     if (!h || !sum_n || !sum_drho) return LBVE_EINVAL;
+    if (h->tangent) return LBVE_ENOSUPPORT;
     cudaStream_t s = (cudaStream_t)stream;
     return h->pop_dbl ? mass_impl<double>(h, sum_n, sum_drho, s) : mass_impl<float>(h, sum_n, sum_drho, s);
 }
@@ -820,6 +1002,28 @@ int lbve_schedule(int32_t C, int32_t B, int64_t t, int64_t* tp_out, double* w_ou
     }
     *n_out = (int32_t)pts.size();
     return LBVE_OK;
+}
+
+int lbve_create_tangent(const lbve_channel_desc* desc, const double* rho_init, lbve_t** out) {
+    return create_tangent(desc, rho_init, out);
+}
+
+int lbve_tangent_fields(lbve_t* h, uint32_t mask, double* dst_host, void* stream) {
+    if (!h || !dst_host || (mask & ~31u)) return LBVE_EINVAL;
+    if (!h->tangent) return LBVE_ESTATE;
+    cudaStream_t s = (cudaStream_t)stream;
+    const size_t cnt = fields_count(h, mask);
+    double* tmp = nullptr;
+    LBVE_CUDA(cudaMallocAsync(&tmp, sizeof(double) * (cnt > 0 ? cnt : 1) * NT, s));
+    int rc = LBVE_OK;
+    for (int k = 0; k < NT && rc == LBVE_OK; ++k) rc = tangent_gather(h, mask, k, tmp + (size_t)k * cnt, s);
+    if (rc == LBVE_OK) {
+        cudaError_t e = cudaMemcpyAsync(dst_host, tmp, sizeof(double) * cnt * NT, cudaMemcpyDeviceToHost, s);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+        if (e != cudaSuccess) rc = cuda_fail(e, "tangent fields");
+    }
+    cudaFreeAsync(tmp, s);
+    return rc;
 }
 
 int lbve_memory_bytes(const lbve_t* h, size_t* bytes) {
@@ -936,6 +1140,7 @@ int gather_fields_into(lbve* h, uint32_t mask, double* dst, int* flag, cudaStrea
 
 extern "C" int lbve_fields_host_fixed(lbve_t* h, uint32_t mask, double* dst_host, void* stream) {
     if (!h || !dst_host || (mask & ~31u)) return LBVE_EINVAL;
+    if (h->tangent) return LBVE_ENOSUPPORT;
     const size_t cnt = fields_count(h, mask);
     if (cnt > (size_t)LBVE_FIXED_STAGING_DOUBLES) return LBVE_ETOOBIG;
     cudaStream_t s = (cudaStream_t)stream;

@@ -39,3 +39,10 @@ def uniform_params(n: int, bounds: dict, seed: int) -> dict:
     """Independent uniform draws per key: bounds = {name: (lo, hi)}."""
     rng = np.random.Generator(np.random.PCG64(seed))
     return {k: rng.uniform(lo, hi, size=n) for k, (lo, hi) in bounds.items()}
+
+
+def perturbed(values, seed: int, frac: float = 0.1) -> np.ndarray:
+    """values with each component scaled by (1 + frac) or (1 - frac), the signs drawn from `seed`."""
+    rng = np.random.Generator(np.random.PCG64(seed))
+    signs = rng.choice([-1.0, 1.0], size=len(values))
+    return np.asarray(values, dtype=np.float64) * (1.0 + frac * signs)

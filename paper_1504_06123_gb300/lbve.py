@@ -31,6 +31,7 @@ EXPORTS = [
     "lbve_fields", "lbve_fields_count", "lbve_history_apply", "lbve_mass", "lbve_schedule",
     "lbve_memory_bytes", "lbve_strerror", "lbve_last_cuda_error", "lbve_profile", "lbve_profile_read",
     "lbve_fields_host_fixed", "lbve_create_batch", "lbve_channel_nodes", "lbve_sweep_config",
+    "lbve_create_tangent", "lbve_tangent_fields",
 ]
 
 
@@ -71,6 +72,8 @@ def load(path: str | None = None):
         lib.lbve_destroy.argtypes = [vp]
         lib.lbve_destroy.restype = None
         lib.lbve_create_batch.argtypes = [C.POINTER(lbve_channel_desc), i32, dp, C.POINTER(vp)]
+        lib.lbve_create_tangent.argtypes = [C.POINTER(lbve_channel_desc), dp, C.POINTER(vp)]
+        lib.lbve_tangent_fields.argtypes = [vp, C.c_uint32, vp, vp]
         lib.lbve_channel_nodes.argtypes = [vp, i32, C.POINTER(i64), C.POINTER(i64)]
         lib.lbve_sweep_config.argtypes = [vp, C.POINTER(i32), C.POINTER(i32)]
         lib.lbve_set_force.argtypes = [vp, i32, dp, vp]
@@ -153,6 +156,26 @@ def lbve_create_batch(descs, rho_init: np.ndarray | None = None) -> int:
                                C.byref(h))
     _check(rc, "lbve_create_batch")
     return h.value
+
+
+def lbve_create_tangent(desc: lbve_channel_desc, rho_init: np.ndarray | None = None) -> int:
+    lib = load()
+    h = C.c_void_p()
+    ri = None
+    if rho_init is not None:
+        ri = np.ascontiguousarray(rho_init, dtype=np.float64).ravel()
+    rc = lib.lbve_create_tangent(C.byref(desc), ri.ctypes.data_as(C.POINTER(C.c_double)) if ri is not None else None,
+                                 C.byref(h))
+    _check(rc, "lbve_create_tangent")
+    return h.value
+
+
+def lbve_tangent_fields(h: int, mask: int, stream=None) -> np.ndarray:
+    """d(fields)/d(theta_k), theta = (G_inf, tau, gamma_c, g_x): array [4, lbve_fields_count(h, mask)]."""
+    cnt = lbve_fields_count(h, mask)
+    out = np.empty((4, cnt), dtype=np.float64)
+    _check(load().lbve_tangent_fields(h, mask, out.ctypes.data, _stream(stream)), "lbve_tangent_fields")
+    return out
 
 
 def lbve_channel_nodes(h: int, channel: int):

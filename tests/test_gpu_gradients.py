@@ -1,0 +1,115 @@
+"""Differentiation: gradients of the profile loss with respect to (G_inf, tau, gamma_c, g) from the
+tangent-linear model in the CUDA library, behind a torch.autograd.Function, against central finite
+differences (h = 1e-4 relative) of the FP64 GPU forward and of the FP64 oracle.
+
+Loss: mean((u_x - u*)^2)/max|u*|^2 + mean((sigma_xy - sigma*)^2)/max|sigma*|^2 at the final step, the
+target from the same model with the parameters perturbed by +-10 % (seeded signs).
+Tolerance: 1e-4 relative per gradient component (the stated bar).
+"""
+import math
+
+import numpy as np
+import pytest
+
+import oracle
+from paper_1504_06123_gb300 import configs, inputs
+from paper_1504_06123_gb300 import lbve as L
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+from paper_1504_06123_gb300.autograd import LBVEChannel, profile_loss, run_profiles  # noqa: E402
+
+H = 1e-4
+TOL = 1e-4
+
+
+def loss_np(u, s, ut, st):
+    return float(np.mean((u - ut) ** 2) / np.max(np.abs(ut)) ** 2 + np.mean((s - st) ** 2) / np.max(np.abs(st)) ** 2)
+
+
+def central_fd(loss_of_theta, theta):
+    g = np.zeros(4)
+    for k in range(4):
+        tp, tm = theta.copy(), theta.copy()
+        tp[k] *= 1 + H
+        tm[k] *= 1 - H
+        g[k] = (loss_of_theta(tp) - loss_of_theta(tm)) / (2 * H * theta[k])
+    return g
+
+
+def oracle_profiles(desc, theta, steps):
+    G, tau, gc, g = theta
+    ch = oracle.Channel(oracle.D2Q9, desc.nx, desc.ny, tau_lb=desc.tau_lb, G_inf=G, tau=tau, gamma_c=gc,
+                        g=(g, 0, 0), C=desc.hist_C, B=desc.hist_B)
+    ch.step(steps)
+    f = ch.fields()
+    return f["u"][:, 0].copy(), f["sigma"][:, 2].copy()
+
+
+def tangent_grad(desc, theta, steps, ut, st):
+    th = torch.tensor(theta, dtype=torch.float64, requires_grad=True)
+    u, s = LBVEChannel.apply(th, desc, steps)
+    loss = profile_loss(u, s, ut, st)
+    loss.backward()
+    return th.grad.numpy().copy(), float(loss.detach())
+
+
+def check(g, ref, what):
+    for k in range(4):
+        assert abs(g[k] - ref[k]) <= TOL * abs(ref[k]) + 1e-9 * np.max(np.abs(ref)), \
+            f"{what}: component {k}: {g[k]:.10e} vs {ref[k]:.10e}"
+
+
+def test_tangent_values_equal_plain_forward():
+    desc = L.make_desc(nx=4, ny=16, tau_lb=0.9, G_inf=0.01, tau=60.0, gamma_c=0.1, g=(2e-5, 0, 0), C=32, B=2,
+                       precision=L.LBVE_F64, hist_storage=L.LBVE_F64)
+    theta = np.array([desc.G_inf, desc.tau, desc.gamma_c, desc.g[0]])
+    u0, s0 = run_profiles(desc, theta, 200)
+    u1, s1, du, ds = run_profiles(desc, theta, 200, with_tangents=True)
+    np.testing.assert_allclose(u1, u0, rtol=1e-12, atol=1e-18)
+    np.testing.assert_allclose(s1, s0, rtol=1e-12, atol=1e-20)
+    assert du.shape == (4, 64) and np.all(np.isfinite(du)) and np.all(np.isfinite(ds))
+    # the force derivative of the velocity is positive everywhere in a driven channel
+    assert np.all(du[3] > 0)
+
+
+def test_gradient_small_channel_vs_fd_and_oracle():
+    desc = L.make_desc(nx=4, ny=16, tau_lb=0.9, G_inf=0.01, tau=60.0, gamma_c=0.1, g=(2e-5, 0, 0), C=32, B=2,
+                       precision=L.LBVE_F64, hist_storage=L.LBVE_F64)
+    steps = 300
+    theta = np.array([desc.G_inf, desc.tau, desc.gamma_c, desc.g[0]])
+    ut, st = run_profiles(desc, inputs.perturbed(theta, seed=5), steps)
+    g_tan, loss = tangent_grad(desc, theta, steps, ut, st)
+    assert loss > 0
+    g_gpu = central_fd(lambda th: loss_np(*run_profiles(desc, th, steps), ut, st), theta)
+    check(g_tan, g_gpu, "tangent vs GPU finite differences")
+    # the oracle's gradient (central differences of the FP64 oracle, its own targets)
+    uo, so = oracle_profiles(desc, inputs.perturbed(theta, seed=5), steps)
+    g_orc = central_fd(lambda th: loss_np(*oracle_profiles(desc, th, steps), uo, so), theta)
+    g_tan_o, _ = tangent_grad(desc, theta, steps, uo, so)
+    check(g_tan_o, g_orc, "tangent vs oracle finite differences")
+
+
+def test_gradient_workload_channel():
+    """The differentiation workload: 4 x 128 channel, L = 512 (B 4 x C 128), 4000 startup steps."""
+    w = configs.gradient_channel()
+    desc = w.desc(precision=L.LBVE_F64, hist_storage=L.LBVE_F64)
+    theta = np.array([w.G_inf, w.tau, w.gamma_c, w.g])
+    ut, st = run_profiles(desc, inputs.perturbed(theta, seed=w.seed), w.steps)
+    g_tan, loss = tangent_grad(desc, theta, w.steps, ut, st)
+    g_gpu = central_fd(lambda th: loss_np(*run_profiles(desc, th, w.steps), ut, st), theta)
+    print("gradient (G_inf, tau, gamma_c, g):", g_tan, "finite differences:", g_gpu)
+    check(g_tan, g_gpu, "tangent vs GPU finite differences, 4000 steps")
+
+
+def test_gradient_workload_channel_vs_oracle_window():
+    """Same geometry and history grid against the oracle's finite differences on a 400-step window."""
+    w = configs.gradient_channel()
+    desc = w.desc(precision=L.LBVE_F64, hist_storage=L.LBVE_F64)
+    steps = 400
+    theta = np.array([w.G_inf, w.tau, w.gamma_c, w.g])
+    uo, so = oracle_profiles(desc, inputs.perturbed(theta, seed=w.seed), steps)
+    g_orc = central_fd(lambda th: loss_np(*oracle_profiles(desc, th, steps), uo, so), theta)
+    g_tan, _ = tangent_grad(desc, theta, steps, uo, so)
+    check(g_tan, g_orc, "tangent vs oracle finite differences, 400 steps")

@@ -230,12 +230,10 @@ def run_ours(args, rank, world, local_rank):
         if world > 1:
             dist.barrier()
 
+    from paper_1504_06123_gb300 import ranks
+
     def max_over_ranks(x: float) -> float:
-        if world == 1:
-            return x
-        t = torch.tensor([x], dtype=torch.float64, device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        return float(t.item())
+        return ranks.max_over_ranks(x, dist if world > 1 else None, device="cuda")
 
     name, descs, rho, notes = workload_descs(args, L, configs)
     hist = {"f32": L.LBVE_F32, "s16": L.LBVE_S16, "f64": L.LBVE_F64}[args.history]
@@ -273,7 +271,7 @@ def run_ours(args, rank, world, local_rank):
         barrier()
     ms = ev0.elapsed_time(ev1)
     ms_max = max_over_ranks(ms)
-    value = updates_rank * world / (ms_max / 1e3)
+    value = ranks.job_rate(updates_rank, world, ms_max / 1e3)
     mlups = N * K * world / (ms_max / 1e3) / 1e6
 
     # per-kernel device time from events around every launch of a further profiled segment

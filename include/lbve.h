@@ -176,6 +176,17 @@ int lbve_schedule(int32_t C, int32_t B, int64_t t, int64_t* tp_out, double* w_ou
 int lbve_create_tangent(const lbve_channel_desc* desc, const double* rho_init, lbve_t** out);
 int lbve_tangent_fields(lbve_t* h, uint32_t field_mask, double* dst_host, void* stream);
 
+/*
+ * Checkpoint / resume of the whole state of a handle: populations, history (and the frame of the 16-bit
+ * form), node fields, step counter and per-channel parameters.  lbve_checkpoint_size gives the bytes of
+ * the image; save writes it to dst (device memory if dst_is_device, else host memory), restore reads it
+ * back into a handle created with the same descriptions.  Both synchronise `stream`.  Restore returns
+ * EINVAL when the image does not match the handle.
+ */
+int lbve_checkpoint_size(lbve_t* h, size_t* bytes);
+int lbve_checkpoint_save(lbve_t* h, void* dst, int32_t dst_is_device, void* stream);
+int lbve_checkpoint_restore(lbve_t* h, const void* src, int32_t src_is_device, void* stream);
+
 /* Device bytes held by the handle (populations, history, fields). */
 int lbve_memory_bytes(const lbve_t* h, size_t* bytes);
 

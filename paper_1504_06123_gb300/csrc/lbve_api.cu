@@ -1004,6 +1004,110 @@ int lbve_schedule(int32_t C, int32_t B, int64_t t, int64_t* tp_out, double* w_ou
     return LBVE_OK;
 }
 
+namespace {
+// The buffers that make up the state of a handle, in checkpoint order (populations of the current
+// parity only; u_raw, the sweep partials and the staging are recomputed or scratch).
+struct StateBuf { void* p; size_t bytes; };
+std::vector<StateBuf> state_buffers(lbve* h) {
+    const long long Np = h->Npad;
+    const int DD = h->D * h->D;
+    const size_t fe = h->tangent ? sizeof(Dual) : sizeof(double);
+    const size_t hist_elem = h->tangent ? sizeof(Dual) : (h->hist_s16 ? 2 : h->hesz);
+    std::vector<StateBuf> v = {
+        {h->pops[h->cur], h->pesz * h->Q * Np}, {h->u, fe * h->D * Np}, {h->rho, fe * Np},
+        {h->sigma, fe * h->NS * Np}, {h->kappa, fe * DD * Np}, {h->tr_prev, fe * Np},
+        {h->X, hist_elem * (size_t)h->L * DD * Np}, {h->K, hist_elem * (size_t)h->L * DD * Np},
+        {h->t_dev, sizeof(long long)}};
+    if (h->hist_s16) {
+        v.push_back({h->Qe, (size_t)h->L * Np});
+        v.push_back({h->Ke, (size_t)h->L * Np});
+        v.push_back({h->Rm, sizeof(float) * DD * Np});
+    }
+    if (!h->tangent) v.push_back({h->chan_dev, sizeof(Chan) * h->nchan});
+    return v;
+}
+constexpr uint64_t kCkptMagic = 0x4c42564543503031ull;   // "LBVECP01"
+struct CkptHeader { uint64_t magic, total, nbuf, config; int64_t t_host; };
+
+// Fingerprint (FNV-1a) of what must match between a checkpoint image and the handle it is restored into.
+uint64_t config_fingerprint(const lbve* h) {
+    uint64_t x = 1469598103934665603ull;
+    auto mix = [&](long long v) {
+        for (int i = 0; i < 8; ++i) { x ^= (uint64_t)((v >> (8 * i)) & 0xff); x *= 1099511628211ull; }
+    };
+    mix(h->tangent); mix(h->nchan); mix(h->N); mix(h->L);
+    for (const lbve_channel_desc& d : h->descs) {
+        mix(d.lattice); mix(d.nx); mix(d.ny); mix(d.nz); mix(d.wall_z); mix(d.hist_C); mix(d.hist_B);
+        mix(d.hist_storage); mix(d.pop_precision); mix(d.trace_coupling);
+    }
+    return x;
+}
+}  // namespace
+
+int lbve_checkpoint_size(lbve_t* h, size_t* bytes) {
+    if (!h || !bytes) return LBVE_EINVAL;
+    size_t t = sizeof(CkptHeader);
+    for (const StateBuf& b : state_buffers(h)) t += (b.bytes + 255) / 256 * 256;
+    *bytes = t;
+    return LBVE_OK;
+}
+
+int lbve_checkpoint_save(lbve_t* h, void* dst, int32_t dst_is_device, void* stream) {
+    if (!h || !dst) return LBVE_EINVAL;
+    cudaStream_t s = (cudaStream_t)stream;
+    size_t total = 0;
+    lbve_checkpoint_size(h, &total);
+    const std::vector<StateBuf> bufs = state_buffers(h);
+    CkptHeader hd{kCkptMagic, total, bufs.size(), config_fingerprint(h), h->t_host};
+    char* d = (char*)dst;
+    const cudaMemcpyKind k = dst_is_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost;
+    LBVE_CUDA(cudaMemcpyAsync(d, &hd, sizeof hd, dst_is_device ? cudaMemcpyHostToDevice : cudaMemcpyHostToHost, s));
+    size_t off = sizeof(CkptHeader);
+    for (const StateBuf& b : bufs) {
+        LBVE_CUDA(cudaMemcpyAsync(d + off, b.p, b.bytes, k, s));
+        off += (b.bytes + 255) / 256 * 256;
+    }
+    LBVE_CUDA(cudaStreamSynchronize(s));
+    return LBVE_OK;
+}
+
+int lbve_checkpoint_restore(lbve_t* h, const void* src, int32_t src_is_device, void* stream) {
+    if (!h || !src) return LBVE_EINVAL;
+    cudaStream_t s = (cudaStream_t)stream;
+    CkptHeader hd;
+    LBVE_CUDA(cudaMemcpyAsync(&hd, src, sizeof hd, src_is_device ? cudaMemcpyDeviceToHost : cudaMemcpyHostToHost, s));
+    LBVE_CUDA(cudaStreamSynchronize(s));
+    size_t total = 0;
+    lbve_checkpoint_size(h, &total);
+    std::vector<StateBuf> bufs = state_buffers(h);
+    if (hd.magic != kCkptMagic || hd.total != total || hd.nbuf != bufs.size() || hd.config != config_fingerprint(h))
+        return LBVE_EINVAL;
+    h->cur = 0;                          // the populations are restored into buffer 0
+    bufs = state_buffers(h);
+    const char* c = (const char*)src;
+    const cudaMemcpyKind k = src_is_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
+    size_t off = sizeof(CkptHeader);
+    for (const StateBuf& b : bufs) {
+        LBVE_CUDA(cudaMemcpyAsync(b.p, c + off, b.bytes, k, s));
+        off += (b.bytes + 255) / 256 * 256;
+    }
+    LBVE_CUDA(cudaStreamSynchronize(s));
+    h->t_host = hd.t_host;
+    if (!h->tangent) {   // the host copy of the channel table follows the restored device table
+        LBVE_CUDA(cudaMemcpy(h->chan_host.data(), h->chan_dev, sizeof(Chan) * h->nchan, cudaMemcpyDeviceToHost));
+        for (int ch = 0; ch < h->nchan; ++ch) {
+            const Chan& cc = h->chan_host[ch];
+            lbve_channel_desc& d = h->descs[ch];
+            d.G_inf = cc.G_inf;
+            d.tau = 1.0 / cc.inv_tau;
+            d.gamma_c = cc.inv_gc == 0.0 ? INFINITY : 1.0 / cc.inv_gc;
+            for (int a = 0; a < 3; ++a) d.g[a] = cc.f[a] / d.rho0;
+        }
+        h->d = h->descs[0];
+    }
+    return LBVE_OK;
+}
+
 int lbve_create_tangent(const lbve_channel_desc* desc, const double* rho_init, lbve_t** out) {
     return create_tangent(desc, rho_init, out);
 }

@@ -31,7 +31,8 @@ EXPORTS = [
     "lbve_fields", "lbve_fields_count", "lbve_history_apply", "lbve_mass", "lbve_schedule",
     "lbve_memory_bytes", "lbve_strerror", "lbve_last_cuda_error", "lbve_profile", "lbve_profile_read",
     "lbve_fields_host_fixed", "lbve_create_batch", "lbve_channel_nodes", "lbve_sweep_config",
-    "lbve_create_tangent", "lbve_tangent_fields",
+    "lbve_create_tangent", "lbve_tangent_fields", "lbve_checkpoint_size", "lbve_checkpoint_save",
+    "lbve_checkpoint_restore",
 ]
 
 
@@ -73,6 +74,9 @@ def load(path: str | None = None):
         lib.lbve_destroy.restype = None
         lib.lbve_create_batch.argtypes = [C.POINTER(lbve_channel_desc), i32, dp, C.POINTER(vp)]
         lib.lbve_create_tangent.argtypes = [C.POINTER(lbve_channel_desc), dp, C.POINTER(vp)]
+        lib.lbve_checkpoint_size.argtypes = [vp, C.POINTER(C.c_size_t)]
+        lib.lbve_checkpoint_save.argtypes = [vp, vp, i32, vp]
+        lib.lbve_checkpoint_restore.argtypes = [vp, vp, i32, vp]
         lib.lbve_tangent_fields.argtypes = [vp, C.c_uint32, vp, vp]
         lib.lbve_channel_nodes.argtypes = [vp, i32, C.POINTER(i64), C.POINTER(i64)]
         lib.lbve_sweep_config.argtypes = [vp, C.POINTER(i32), C.POINTER(i32)]
@@ -176,6 +180,29 @@ def lbve_tangent_fields(h: int, mask: int, stream=None) -> np.ndarray:
     out = np.empty((4, cnt), dtype=np.float64)
     _check(load().lbve_tangent_fields(h, mask, out.ctypes.data, _stream(stream)), "lbve_tangent_fields")
     return out
+
+
+def lbve_checkpoint_size(h: int) -> int:
+    n = C.c_size_t()
+    _check(load().lbve_checkpoint_size(h, C.byref(n)), "lbve_checkpoint_size")
+    return n.value
+
+
+def lbve_checkpoint_save(h: int, dst=None, stream=None):
+    """Save the state; dst None: into a new host bytes buffer (returned); else a device tensor/pointer."""
+    if dst is None:
+        buf = np.empty(lbve_checkpoint_size(h), dtype=np.uint8)
+        _check(load().lbve_checkpoint_save(h, buf.ctypes.data, 0, _stream(stream)), "lbve_checkpoint_save")
+        return buf
+    _check(load().lbve_checkpoint_save(h, _ptr(dst), 1, _stream(stream)), "lbve_checkpoint_save")
+    return dst
+
+
+def lbve_checkpoint_restore(h: int, src, stream=None) -> None:
+    if isinstance(src, np.ndarray):
+        _check(load().lbve_checkpoint_restore(h, src.ctypes.data, 0, _stream(stream)), "lbve_checkpoint_restore")
+    else:
+        _check(load().lbve_checkpoint_restore(h, _ptr(src), 1, _stream(stream)), "lbve_checkpoint_restore")
 
 
 def lbve_channel_nodes(h: int, channel: int):

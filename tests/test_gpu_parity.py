@@ -361,3 +361,48 @@ def test_duct_subrun_reduced_precision_per_field():
     for k, v in errs.items():
         assert v <= TOL[RED], (k, v)
     ch.close()
+
+
+# ---------------------------------------------------------------------------------------------
+# Checkpoint / resume; failure reporting of a state that has become non-finite
+# ---------------------------------------------------------------------------------------------
+@pytest.mark.parametrize("prec", [PLAIN, RED])
+def test_checkpoint_resume_bitwise(prec):
+    kw = dict(nx=6, ny=14, G_inf=0.01, tau=40.0, gamma_c=0.1, g=(1e-5, 0, 0), C=8, B=3, precision=prec[0],
+              hist_storage=prec[1])
+    a = L.Channel(L.make_desc(**kw))
+    a.step(37)
+    img = L.lbve_checkpoint_save(a.h)                 # host image
+    dev = torch.empty(L.lbve_checkpoint_size(a.h), dtype=torch.uint8, device="cuda")
+    L.lbve_checkpoint_save(a.h, dev)                  # device image
+    a.step(50)
+    ref = a.fields()
+    b = L.Channel(L.make_desc(**kw))
+    L.lbve_checkpoint_restore(b.h, img)
+    assert b.t == 37
+    b.step(50)
+    c = L.Channel(L.make_desc(**kw))
+    L.lbve_checkpoint_restore(c.h, dev)
+    c.step(50)
+    for k, v in ref.items():
+        assert np.array_equal(b.fields()[k], v), k
+        assert np.array_equal(c.fields()[k], v), k
+    # an image of another configuration is refused
+    other = L.Channel(L.make_desc(**dict(kw, ny=10)))
+    with pytest.raises(L.LbveError) as e:
+        L.lbve_checkpoint_restore(other.h, img)
+    assert e.value.status == L.LBVE_EINVAL
+    for ch in (a, b, c, other):
+        ch.close()
+
+
+def test_nonfinite_state_is_reported():
+    """An absurd force (1e30) overflows the state to Inf/NaN within a few steps (ordinary floating-point
+    arithmetic, nothing traps); the device flag of the field copy reports it as LBVE_ENONFINITE."""
+    ch = L.Channel(L.make_desc(nx=2, ny=8, G_inf=0.01, tau=20.0, gamma_c=0.1, g=(1e30, 0, 0), C=4, B=1,
+                               precision=F64, hist_storage=F32))
+    ch.step(5)
+    with pytest.raises(L.LbveError) as e:
+        ch.fields()
+    assert e.value.status == L.LBVE_ENONFINITE
+    ch.close()

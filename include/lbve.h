@@ -187,6 +187,20 @@ int lbve_checkpoint_size(lbve_t* h, size_t* bytes);
 int lbve_checkpoint_save(lbve_t* h, void* dst, int32_t dst_is_device, void* stream);
 int lbve_checkpoint_restore(lbve_t* h, const void* src, int32_t src_is_device, void* stream);
 
+/*
+ * Reverse mode (adjoint).  lbve_create_adjoint makes an FP64 channel (pop_precision and hist_storage must
+ * be LBVE_F64; ENOSUPPORT otherwise) that records a state image every checkpoint_every steps while it is
+ * stepped from t = 0.  lbve_backward then returns grad_out = dL/d(G_inf, tau, gamma_c, g_x) for a loss L
+ * of the fields of the last completed step, given dL_du ([d][N], host) and dL_dsigma ([nsig][N], host):
+ * it replays every segment from its image, keeps the per-step states of that segment, and runs the
+ * adjoint of the hybrid step (collision and streaming, history commit and sweep, finite differences,
+ * moments) backwards through it.  The handle's state is the same before and after the call; stepping
+ * further and calling again is allowed.  ESTATE before the first step.  Synchronises `stream`.
+ */
+int lbve_create_adjoint(const lbve_channel_desc* desc, const double* rho_init, int32_t checkpoint_every,
+                        lbve_t** out);
+int lbve_backward(lbve_t* h, const double* dL_du, const double* dL_dsigma, double grad_out[4], void* stream);
+
 /* Device bytes held by the handle (populations, history, fields). */
 int lbve_memory_bytes(const lbve_t* h, size_t* bytes);
 

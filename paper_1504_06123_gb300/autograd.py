@@ -1,9 +1,13 @@
-"""torch.autograd.Function over the tangent-linear model of the C library (lbve_create_tangent).
+"""torch.autograd.Functions over the differentiated hybrid step of the C library.
 
-forward(theta) runs the hybrid LB channel for a fixed number of steps with the parameters
-theta = (G_inf, tau, gamma_c, g_x) and returns the final velocity and shear-stress profiles; the library
-propagates d(state)/d(theta) alongside the state, so backward only contracts the incoming gradients
-with the stored derivatives.  Argument marshalling only: every step runs in the CUDA library.
+Both map theta = (G_inf, tau, gamma_c, g_x) to the final velocity and shear-stress profiles of a channel
+run for a fixed number of steps:
+  LBVEChannelAdjoint  reverse mode: the forward records a state image every K steps
+                      (lbve_create_adjoint); backward replays the segments and runs the adjoint
+                      (lbve_backward) -- one backward pass for all four parameters;
+  LBVEChannel         forward mode: the library propagates d(state)/d(theta) with the state
+                      (lbve_create_tangent); backward contracts the incoming gradients with them.
+Argument marshalling only: every step and its derivative run in the CUDA library.
 """
 from __future__ import annotations
 
@@ -70,6 +74,47 @@ class LBVEChannel(torch.autograd.Function):
         if grad_s is not None:
             g = g + ds @ grad_s.to(torch.float64)
         return g, None, None, None
+
+
+class LBVEChannelAdjoint(torch.autograd.Function):
+    """theta (float64 tensor [4]) -> (u_x [N], sigma_xy [N]); gradients by the adjoint with checkpoints."""
+
+    @staticmethod
+    def forward(ctx, theta: torch.Tensor, desc: L.lbve_channel_desc, steps: int, checkpoint_every: int = 64,
+                rho_init=None):
+        d = _with_params(desc, theta.detach().cpu().numpy())
+        d.pop_precision = L.LBVE_F64
+        d.hist_storage = L.LBVE_F64
+        dim = 2 if d.lattice == L.LBVE_D2Q9 else 3
+        N = d.nx * d.ny * d.nz
+        h = L.lbve_create_adjoint(d, rho_init, checkpoint_every)
+        try:
+            L.lbve_step(h, steps)
+            f = L.lbve_fields(h, L.LBVE_FIELD_U | L.LBVE_FIELD_SIGMA)
+        except Exception:
+            L.lbve_destroy(h)
+            raise
+        ixy = 2 if dim == 2 else 3
+        ctx.h, ctx.dim, ctx.N, ctx.ixy = h, dim, N, ixy
+        return (torch.from_numpy(f[:N].copy()),
+                torch.from_numpy(f[dim * N + ixy * N: dim * N + (ixy + 1) * N].copy()))
+
+    @staticmethod
+    def backward(ctx, grad_u, grad_s):
+        dim, N, ixy = ctx.dim, ctx.N, ctx.ixy
+        nsig = 3 if dim == 2 else 6
+        du = np.zeros((dim, N))
+        ds = np.zeros((nsig, N))
+        if grad_u is not None:
+            du[0] = grad_u.detach().cpu().numpy()
+        if grad_s is not None:
+            ds[ixy] = grad_s.detach().cpu().numpy()
+        try:
+            g = L.lbve_backward(ctx.h, du, ds)
+        finally:
+            L.lbve_destroy(ctx.h)
+            ctx.h = None
+        return torch.from_numpy(g), None, None, None, None
 
 
 def profile_loss(u, s, u_target, s_target):

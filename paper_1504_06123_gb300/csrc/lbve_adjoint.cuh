@@ -1,0 +1,548 @@
+// lbve_adjoint.cuh -- reverse-mode (adjoint) model of the hybrid step, FP64, form "P" history.
+//
+// For a loss of the fields of the last step, the adjoint runs the steps backwards: lambda of the state
+// after step t (populations after streaming, history slots after the commit, tr sigma of step t) gives
+// lambda of the state before step t, and every step adds its share of dL/dtheta for
+// theta = (G_inf, tau, gamma_c, g_x).  The forward quantities of step t are recomputed per node from the
+// state before the step (taped per step inside a checkpoint segment by the runtime).
+//
+// Two kernels per step:
+//   k_adj_node   one thread per node: forward recompute (moments, kappa(t), history sweep, sigma,
+//                collision), then the adjoint of the collision + streaming (a pull from the neighbours),
+//                of the commit (merges and new point in reverse order) and of the history sweep (point
+//                integrands, in-place advance, exp(kappa(t-1)) - 1).  Writes lambda of kappa(t) and the
+//                node's part of lambda(populations).
+//   k_adj_fd     one thread per node: transpose of the finite-difference stencil (gathers lambda kappa(t)
+//                from the nodes whose stencil reads this node) and the adjoint of the raw moments.
+#pragma once
+#include "lbve_kernels.cuh"
+
+namespace lbk {
+
+struct AdjPar {
+    double G_inf, tau, gamma_c, inv_tau, inv_gc, rho0, tau_lb, f[3];
+    int trace_full;
+};
+
+// Adjoint of A = exp(K) - 1 (Taylor series of the forward, order 8): lambda_K += sum_m 1/m! sum_j
+// (K^j)^T lamA (K^(m-1-j))^T.
+template <int D>
+__device__ inline void expm1_adjoint(const double* K, const double* lamA, double* lamK) {
+    constexpr int DD = D * D;
+    constexpr int ORDER = 8;
+    double P[ORDER][DD];   // P[j] = K^j
+#pragma unroll
+    for (int i = 0; i < DD; ++i) P[0][i] = (i % (D + 1) == 0) ? 1.0 : 0.0;
+    for (int j = 1; j < ORDER; ++j)
+        for (int r = 0; r < D; ++r)
+            for (int c = 0; c < D; ++c) {
+                double s = 0.0;
+                for (int k = 0; k < D; ++k) s += P[j - 1][r * D + k] * K[k * D + c];
+                P[j][r * D + c] = s;
+            }
+    double fact = 1.0;
+    for (int m = 1; m <= ORDER; ++m) {
+        fact *= m;
+        for (int j = 0; j < m; ++j) {
+            // (K^j)^T lamA (K^(m-1-j))^T
+            const double* Pa = P[j];
+            const double* Pb = P[m - 1 - j];
+            double T[DD];
+            for (int r = 0; r < D; ++r)
+                for (int c = 0; c < D; ++c) {
+                    double s = 0.0;
+                    for (int k = 0; k < D; ++k) s += Pa[k * D + r] * lamA[k * D + c];
+                    T[r * D + c] = s;
+                }
+            for (int r = 0; r < D; ++r)
+                for (int c = 0; c < D; ++c) {
+                    double s = 0.0;
+                    for (int k = 0; k < D; ++k) s += T[r * D + k] * Pb[c * D + k];
+                    lamK[r * D + c] += s / fact;
+                }
+        }
+    }
+}
+
+// Packed symmetric (NS components) -> full matrix of the adjoint pairing: sum_p lam_p S_p = tr(Lt S)
+// with Lt_aa = lam_aa and Lt_ab = lam_ab / 2 off the diagonal.
+template <int D>
+__device__ inline void packed_to_pairing(const double* lam, double* Lt) {
+    if (D == 2) {
+        Lt[0] = lam[0]; Lt[3] = lam[1]; Lt[1] = Lt[2] = 0.5 * lam[2];
+    } else {
+        Lt[0] = lam[0]; Lt[4] = lam[1]; Lt[8] = lam[2];
+        Lt[1] = Lt[3] = 0.5 * lam[3]; Lt[2] = Lt[6] = 0.5 * lam[4]; Lt[5] = Lt[7] = 0.5 * lam[5];
+    }
+}
+
+// Forward integrand (same arithmetic as point_integrand) returning S packed, g and gammadot; and its
+// adjoint for a pairing matrix Lt: lamE (dL/dE), lamk (dL/dkappa), and the scalar parts for the rates.
+template <int D>
+__device__ inline void integrand_adjoint(const double* X, const double* kap, double age, double w, double inv_tau,
+                                         double inv_gc, const double* Lt, double* lamX, double* lamk,
+                                         double* lam_inv_tau, double* lam_inv_gc) {
+    constexpr int DD = D * D;
+    double E[DD];
+    for (int i = 0; i < DD; ++i) E[i] = X[i] + ((i % (D + 1) == 0) ? 1.0 : 0.0);
+    // M = E kap E^T
+    double EK[DD], M[DD];
+    for (int r = 0; r < D; ++r)
+        for (int c = 0; c < D; ++c) {
+            double s = 0.0;
+            for (int k = 0; k < D; ++k) s += E[r * D + k] * kap[k * D + c];
+            EK[r * D + c] = s;
+        }
+    for (int r = 0; r < D; ++r)
+        for (int c = 0; c < D; ++c) {
+            double s = 0.0;
+            for (int k = 0; k < D; ++k) s += EK[r * D + k] * E[c * D + k];
+            M[r * D + c] = s;
+        }
+    double trD2 = 0.0, Dm[DD];
+    for (int r = 0; r < D; ++r)
+        for (int c = 0; c < D; ++c) {
+            Dm[r * D + c] = kap[r * D + c] + kap[c * D + r];
+            trD2 += Dm[r * D + c] * Dm[r * D + c];
+        }
+    const double gd = ::sqrt(0.5 * trD2);
+    const double g = ::exp(-age * (inv_tau + gd * inv_gc));
+    // sS = tr(Lt S), S = M + M^T
+    double sS = 0.0;
+    for (int r = 0; r < D; ++r)
+        for (int c = 0; c < D; ++c) sS += Lt[r * D + c] * (M[c * D + r] + M[r * D + c]);
+    // dS: lamE = 2 w g Lt E (kap + kap^T); lamkap = 2 w g E^T Lt E
+    double LE[DD];
+    for (int r = 0; r < D; ++r)
+        for (int c = 0; c < D; ++c) {
+            double s = 0.0;
+            for (int k = 0; k < D; ++k) s += Lt[r * D + k] * E[k * D + c];
+            LE[r * D + c] = s;
+        }
+    const double wg2 = 2.0 * w * g;
+    for (int r = 0; r < D; ++r)
+        for (int c = 0; c < D; ++c) {
+            double s = 0.0, s2 = 0.0;
+            for (int k = 0; k < D; ++k) {
+                s += LE[r * D + k] * Dm[k * D + c];          // Lt E (kap + kap^T)
+                s2 += E[k * D + r] * LE[k * D + c];          // E^T Lt E
+            }
+            lamX[r * D + c] += wg2 * s;
+            lamk[r * D + c] += wg2 * s2;
+        }
+    // dg: g = exp(-age (inv_tau + gd inv_gc))
+    const double dl_dg = w * sS;
+    *lam_inv_tau += dl_dg * (-age * g);
+    *lam_inv_gc += dl_dg * (-age * gd * g);
+    if (gd > 0.0) {
+        const double dl_dgd = dl_dg * (-age * inv_gc * g);
+        for (int i = 0; i < DD; ++i) lamk[i] += dl_dgd * Dm[i] / gd;
+    }
+}
+
+struct AdjArgs {
+    const double* n;        // [Q][Npad] populations of step t (before collision)
+    const double* X;        // [L][DD][Npad] history before the step
+    const double* K;        // [L][DD][Npad]
+    const double* trp;      // [Npad] tr sigma(t-1)
+    const double* u_raw;    // [D][Npad] raw velocity of step t (recomputed by k_moments)
+    const double* lam_n1;   // [Q][Npad] lambda of the populations after step t
+    double* lam_n0;         // [Q][Npad] lambda of the populations before step t (this kernel's part)
+    double* lamX;           // [L][DD][Npad] in: after step t; out: before step t
+    double* lamK;           // [L][DD][Npad]
+    double* lam_trp;        // [Npad] in: lambda of tr sigma(t); out: of tr sigma(t-1)
+    double* lam_kt;         // [DD][Npad] out: lambda of kappa(t)
+    double* lam_theta;      // [4][Npad] += per-node parts of dL/dtheta
+    const double* seed_u;   // [D][Npad] dL/du of this step's velocity (last step), or nullptr
+    const double* seed_s;   // [NS][Npad] dL/dsigma of this step (last step), or nullptr
+    long long t;
+    int B, C;
+};
+
+template <int Q>
+__global__ void __launch_bounds__(64) k_adj_node(AdjArgs a, Geom g, AdjPar p) {
+    using L = Lattice<Q>;
+    constexpr int D = L::D;
+    constexpr int DD = D * D;
+    constexpr int NS = D == 2 ? 3 : 6;
+    const int Ls = a.B * a.C;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    float* s_age = reinterpret_cast<float*>(smem_raw);
+    float* s_w = s_age + Ls;
+    int* s_part = reinterpret_cast<int*>(s_w + Ls);
+    BlockStep* s_bs = reinterpret_cast<BlockStep*>(s_part + Ls);
+    if (threadIdx.x == 0) sched_step(a.B, a.C, a.t, s_bs);
+    __syncthreads();
+    for (int l = threadIdx.x; l < Ls; l += blockDim.x) {
+        int age, part;
+        const float w = sched_slot_role(s_bs, a.C, l / a.C, l % a.C, &age, &part);
+        s_age[l] = (float)age;
+        s_w[l] = w;
+        s_part[l] = part;
+    }
+    __syncthreads();
+    const int n = blockIdx.x * blockDim.x + threadIdx.x;
+    if (n >= g.N) return;
+    const long long Np = g.Npad;
+    const Chan& ch = g.ch[0];
+
+    // ---------------- forward recompute of step t at this node ----------------
+    double dn[Q], dr = 0.0, J[3] = {0, 0, 0};
+    for (int q = 0; q < Q; ++q) {
+        dn[q] = a.n[q * Np + n];
+        dr += dn[q];
+        J[0] += L::cx(q) * dn[q];
+        J[1] += L::cy(q) * dn[q];
+        if (D == 3) J[2] += L::cz(q) * dn[q];
+    }
+    double kt[DD];
+    kappa_fd<D>(a.u_raw, Np, ch, n, kt);
+    const long long s_last = (long long)(a.B - 1) * a.C + s_bs[a.B - 1].head_prev;
+    double kl[DD], A[DD];
+    for (int c = 0; c < DD; ++c) kl[c] = a.K[(s_last * DD + c) * Np + n];
+    expm1_mat<D>(kl, A);
+    double acc[NS];
+    for (int i = 0; i < NS; ++i) acc[i] = 0.0;
+    for (int l = 0; l < Ls; ++l) {
+        const float w = s_w[l];
+        if (w == 0.0f) continue;
+        double Xl[DD], kap[DD];
+        for (int c = 0; c < DD; ++c) {
+            Xl[c] = a.X[((long long)l * DD + c) * Np + n];
+            kap[c] = a.K[((long long)l * DD + c) * Np + n];
+        }
+        const int part = s_part[l];
+        if (part >= 0)
+            for (int c = 0; c < DD; ++c) kap[c] = 0.5 * (kap[c] + a.K[((long long)part * DD + c) * Np + n]);
+        point_update<D>(Xl, A, kap, (double)s_age[l], (double)w, p.inv_tau, p.inv_gc, acc);
+    }
+    double newp[NS];   // the point created now: (kappa + kappa^T)/2 packed
+    if (D == 2) {
+        newp[0] = kt[0]; newp[1] = kt[3]; newp[2] = 0.5 * (kt[1] + kt[2]);
+    } else {
+        newp[0] = kt[0]; newp[1] = kt[4]; newp[2] = kt[8];
+        newp[3] = 0.5 * (kt[1] + kt[3]); newp[4] = 0.5 * (kt[2] + kt[6]); newp[5] = 0.5 * (kt[5] + kt[7]);
+    }
+    double sg[NS];
+    for (int i = 0; i < NS; ++i) sg[i] = p.G_inf * (acc[i] + newp[i]);
+    // collision quantities
+    double S[3][3] = {{0, 0, 0}, {0, 0, 0}, {0, 0, 0}};
+    if (D == 2) {
+        S[0][0] = sg[0]; S[1][1] = sg[1]; S[0][1] = S[1][0] = sg[2];
+    } else {
+        S[0][0] = sg[0]; S[1][1] = sg[1]; S[2][2] = sg[2];
+        S[0][1] = S[1][0] = sg[3]; S[0][2] = S[2][0] = sg[4]; S[1][2] = S[2][1] = sg[5];
+    }
+    double tr = 0.0;
+    for (int c = 0; c < D; ++c) tr += S[c][c];
+    const double ddr = p.trace_full ? -(tr - a.trp[n]) * (3.0 / D) : 0.0;
+    const double drho = dr + 0.5 * ddr;
+    const double rho = p.rho0 + drho;
+    double u[3] = {0, 0, 0};
+    for (int c = 0; c < D; ++c) u[c] = (J[c] + 0.5 * p.f[c]) / rho;
+    double uu = 0.0;
+    for (int c = 0; c < D; ++c) uu += u[c] * u[c];
+    const double omega = 1.0 / p.tau_lb, fpre = 1.0 - 0.5 * omega, cs2 = 1.0 / 3.0;
+
+    // ---------------- adjoint of collision and streaming ----------------
+    double lam_dr = 0.0, lam_J[3] = {0, 0, 0}, lam_f[3] = {0, 0, 0}, lam_u[3] = {0, 0, 0};
+    double lam_rho = 0.0, lam_drho = 0.0, lam_ddr = 0.0, lam_uu = 0.0, lam_trX = 0.0;
+    double lam_Sb[3][3] = {{0, 0, 0}, {0, 0, 0}, {0, 0, 0}}, lam_Xf[3][3] = {{0, 0, 0}, {0, 0, 0}, {0, 0, 0}};
+    int x, y, z;
+    node_xyz(ch, n, x, y, z);
+    for (int q = 0; q < Q; ++q) {
+        const int cq[3] = {L::cx(q), L::cy(q), L::cz(q)};
+        // lambda of this population after streaming (push adjoint = pull)
+        int xd = x + cq[0];
+        xd = xd < 0 ? ch.nx - 1 : (xd >= ch.nx ? 0 : xd);
+        const int yd = y + cq[1];
+        bool wall = yd < 0 || yd >= ch.ny;
+        int zd = z + cq[2];
+        if (D == 3) {
+            if (ch.wall_z) wall = wall || zd < 0 || zd >= ch.nz;
+            else zd = zd < 0 ? ch.nz - 1 : (zd >= ch.nz ? 0 : zd);
+        }
+        const double lpost = wall ? a.lam_n1[L::opp(q) * Np + n] : a.lam_n1[q * Np + (xd + ch.nx * (yd + ch.ny * zd))];
+        // post = (1 - omega) n + omega dneq + F
+        a.lam_n0[q * Np + n] = (1.0 - omega) * lpost;
+        const double wq = L::w(q);
+        double cu = 0.0, cf = 0.0;
+        for (int r = 0; r < D; ++r) { cu += cq[r] * u[r]; cf += cq[r] * p.f[r]; }
+        const double l_dneq = omega * lpost, l_F = lpost;
+        // dneq = w (drho + rho (3 cu + 4.5 cu^2 - 1.5 uu))
+        lam_drho += wq * l_dneq;
+        lam_rho += wq * (3.0 * cu + 4.5 * cu * cu - 1.5 * uu) * l_dneq;
+        const double l_cu = wq * rho * (3.0 + 9.0 * cu) * l_dneq;
+        lam_uu += wq * rho * (-1.5) * l_dneq;
+        // F = w (-4.5 omega cSc + fpre (ddr + 3 cf + 4.5 cXc - 4.5 cs2 trX))
+        const double l_cSc = -4.5 * omega * wq * l_F;
+        lam_ddr += fpre * wq * l_F;
+        const double l_cf = 3.0 * fpre * wq * l_F;
+        const double l_cXc = 4.5 * fpre * wq * l_F;
+        lam_trX += -4.5 * cs2 * fpre * wq * l_F;
+        for (int r = 0; r < D; ++r) {
+            lam_u[r] += cq[r] * l_cu;
+            lam_f[r] += cq[r] * l_cf;
+            for (int c = 0; c < D; ++c) {
+                lam_Sb[r][c] += cq[r] * cq[c] * l_cSc;
+                lam_Xf[r][c] += cq[r] * cq[c] * l_cXc;
+            }
+        }
+    }
+    for (int c = 0; c < D; ++c) lam_Xf[c][c] += lam_trX;
+    // Xf_ab = -ddr u_a u_b + u_b f_a + u_a f_b
+    for (int r = 0; r < D; ++r)
+        for (int c = 0; c < D; ++c) {
+            const double l = lam_Xf[r][c];
+            lam_ddr += -u[r] * u[c] * l;
+            lam_u[r] += (-ddr * u[c] + p.f[c]) * l;
+            lam_u[c] += (-ddr * u[r] + p.f[r]) * l;
+            lam_f[r] += u[c] * l;
+            lam_f[c] += u[r] * l;
+        }
+    for (int c = 0; c < D; ++c) lam_u[c] += 2.0 * u[c] * lam_uu;
+    if (a.seed_u)
+        for (int c = 0; c < D; ++c) lam_u[c] += a.seed_u[c * Np + n];
+    // u = (J + f/2) / rho
+    for (int c = 0; c < D; ++c) {
+        lam_J[c] += lam_u[c] / rho;
+        lam_f[c] += 0.5 * lam_u[c] / rho;
+        lam_rho += -u[c] * lam_u[c] / rho;
+    }
+    lam_drho += lam_rho;
+    lam_dr += lam_drho;
+    lam_ddr += 0.5 * lam_drho;
+    // S_bar = sigma - tr/D; ddr = -(tr - trp) 3/D; the next step's tr_prev = tr
+    double lam_tr = a.lam_trp[n];
+    if (p.trace_full) {
+        lam_tr += -(3.0 / D) * lam_ddr;
+        a.lam_trp[n] = (3.0 / D) * lam_ddr;
+    } else {
+        a.lam_trp[n] = 0.0;
+    }
+    double lam_sg[NS];
+    for (int c = 0; c < D; ++c) lam_tr += -lam_Sb[c][c] / D;
+    if (D == 2) {
+        lam_sg[0] = lam_Sb[0][0] + lam_tr; lam_sg[1] = lam_Sb[1][1] + lam_tr; lam_sg[2] = lam_Sb[0][1] + lam_Sb[1][0];
+    } else {
+        lam_sg[0] = lam_Sb[0][0] + lam_tr; lam_sg[1] = lam_Sb[1][1] + lam_tr; lam_sg[2] = lam_Sb[2][2] + lam_tr;
+        lam_sg[3] = lam_Sb[0][1] + lam_Sb[1][0]; lam_sg[4] = lam_Sb[0][2] + lam_Sb[2][0];
+        lam_sg[5] = lam_Sb[1][2] + lam_Sb[2][1];
+    }
+    if (a.seed_s)
+        for (int i = 0; i < NS; ++i) lam_sg[i] += a.seed_s[i * Np + n];
+
+    // ---------------- adjoint of the commit ----------------
+    double lam_G = 0.0, lam_acc[NS], lam_kt[DD];
+    for (int i = 0; i < NS; ++i) {
+        lam_G += (acc[i] + newp[i]) * lam_sg[i];
+        lam_acc[i] = p.G_inf * lam_sg[i];
+    }
+    for (int c = 0; c < DD; ++c) lam_kt[c] = 0.0;
+    if (D == 2) {
+        lam_kt[0] += lam_acc[0]; lam_kt[3] += lam_acc[1];
+        lam_kt[1] += 0.5 * lam_acc[2]; lam_kt[2] += 0.5 * lam_acc[2];
+    } else {
+        lam_kt[0] += lam_acc[0]; lam_kt[4] += lam_acc[1]; lam_kt[8] += lam_acc[2];
+        lam_kt[1] += 0.5 * lam_acc[3]; lam_kt[3] += 0.5 * lam_acc[3];
+        lam_kt[2] += 0.5 * lam_acc[4]; lam_kt[6] += 0.5 * lam_acc[4];
+        lam_kt[5] += 0.5 * lam_acc[5]; lam_kt[7] += 0.5 * lam_acc[5];
+    }
+    // new point (last forward operation): X_dst = 0, K_dst = kappa(t)
+    {
+        const long long dst = (long long)(a.B - 1) * a.C + s_bs[a.B - 1].head_new;
+        for (int c = 0; c < DD; ++c) {
+            lam_kt[c] += a.lamK[(dst * DD + c) * Np + n];
+            a.lamK[(dst * DD + c) * Np + n] = 0.0;
+            a.lamX[(dst * DD + c) * Np + n] = 0.0;
+        }
+    }
+    // merges in reverse order (finest first): X_dst = X'_o1, K_dst = (K_o1 + K_o2)/2
+    for (int bb = a.B - 1; bb >= 1; --bb) {
+        const BlockStep& b = s_bs[bb];
+        if (!b.evict) continue;
+        int o1 = b.head_prev - (a.C - 1); if (o1 < 0) o1 += a.C;
+        int o2 = b.head_prev - (a.C - 2); if (o2 < 0) o2 += a.C;
+        const long long src1 = (long long)bb * a.C + o1, src2 = (long long)bb * a.C + o2;
+        const long long dst = (long long)(bb - 1) * a.C + s_bs[bb - 1].head_new;
+        for (int c = 0; c < DD; ++c) {
+            const double lx = a.lamX[(dst * DD + c) * Np + n], lk = a.lamK[(dst * DD + c) * Np + n];
+            a.lamX[(dst * DD + c) * Np + n] = 0.0;
+            a.lamK[(dst * DD + c) * Np + n] = 0.0;
+            a.lamX[(src1 * DD + c) * Np + n] += lx;
+            a.lamK[(src1 * DD + c) * Np + n] += 0.5 * lk;
+            a.lamK[(src2 * DD + c) * Np + n] += 0.5 * lk;
+        }
+    }
+
+    // ---------------- adjoint of the history sweep ----------------
+    double Lt[DD], lamA[DD];
+    packed_to_pairing<D>(lam_acc, Lt);
+    for (int c = 0; c < DD; ++c) lamA[c] = 0.0;
+    double lam_it = 0.0, lam_ig = 0.0;
+    for (int l = 0; l < Ls; ++l) {
+        const float w = s_w[l];
+        if (w == 0.0f) continue;
+        double Xl[DD], Xn[DD], kap[DD], lX[DD], lk[DD];
+        for (int c = 0; c < DD; ++c) {
+            Xl[c] = a.X[((long long)l * DD + c) * Np + n];
+            kap[c] = a.K[((long long)l * DD + c) * Np + n];
+            lX[c] = a.lamX[((long long)l * DD + c) * Np + n];   // lambda of X' (after the sweep)
+            lk[c] = 0.0;
+        }
+        const int part = s_part[l];
+        if (part >= 0)
+            for (int c = 0; c < DD; ++c) kap[c] = 0.5 * (kap[c] + a.K[((long long)part * DD + c) * Np + n]);
+        // X' = X + A + A X
+        for (int r = 0; r < D; ++r)
+            for (int c = 0; c < D; ++c) {
+                double s = Xl[r * D + c] + A[r * D + c];
+                for (int k = 0; k < D; ++k) s += A[r * D + k] * Xl[k * D + c];
+                Xn[r * D + c] = s;
+            }
+        integrand_adjoint<D>(Xn, kap, (double)s_age[l], (double)w, p.inv_tau, p.inv_gc, Lt, lX, lk, &lam_it, &lam_ig);
+        // lambda A += lX (1 + X)^T ; lambda X = (1 + A)^T lX
+        for (int r = 0; r < D; ++r)
+            for (int c = 0; c < D; ++c) {
+                double s = lX[r * D + c];
+                for (int k = 0; k < D; ++k) s += lX[r * D + k] * Xl[c * D + k];
+                lamA[r * D + c] += s;
+            }
+        for (int r = 0; r < D; ++r)
+            for (int c = 0; c < D; ++c) {
+                double s = lX[r * D + c];
+                for (int k = 0; k < D; ++k) s += A[k * D + r] * lX[k * D + c];
+                Xn[r * D + c] = s;   // reuse as lambda X (before the sweep)
+            }
+        for (int c = 0; c < DD; ++c) a.lamX[((long long)l * DD + c) * Np + n] = Xn[c];
+        if (part >= 0) {
+            for (int c = 0; c < DD; ++c) {
+                a.lamK[((long long)l * DD + c) * Np + n] += 0.5 * lk[c];
+                a.lamK[((long long)part * DD + c) * Np + n] += 0.5 * lk[c];
+            }
+        } else {
+            for (int c = 0; c < DD; ++c) a.lamK[((long long)l * DD + c) * Np + n] += lk[c];
+        }
+    }
+    // A = exp(kappa(t-1)) - 1 with kappa(t-1) the kappa of the newest stored point
+    {
+        double lk[DD];
+        for (int c = 0; c < DD; ++c) lk[c] = 0.0;
+        expm1_adjoint<D>(kl, lamA, lk);
+        for (int c = 0; c < DD; ++c) a.lamK[(s_last * DD + c) * Np + n] += lk[c];
+    }
+
+    // ---------------- outputs ----------------
+    for (int c = 0; c < DD; ++c) a.lam_kt[c * Np + n] = lam_kt[c];
+    for (int q = 0; q < Q; ++q) {
+        double l = lam_dr;
+        l += L::cx(q) * lam_J[0] + L::cy(q) * lam_J[1];
+        if (D == 3) l += L::cz(q) * lam_J[2];
+        a.lam_n0[q * Np + n] += l;
+    }
+    a.lam_theta[0 * Np + n] += lam_G;
+    a.lam_theta[1 * Np + n] += lam_it * (-1.0 / (p.tau * p.tau));                // d(1/tau)/dtau
+    a.lam_theta[2 * Np + n] += isinf(p.gamma_c) ? 0.0 : lam_ig * (-1.0 / (p.gamma_c * p.gamma_c));
+    a.lam_theta[3 * Np + n] += p.rho0 * lam_f[0];                                // f_x = rho0 g_x
+}
+
+// Forward weight of node yn in the finite-difference stencil of node xn along `axis` (Sec. III:
+// central; at a wall-adjacent node the three-point formula through the wall).
+__device__ inline double fd_weight(const Chan& c, int axis, int xn, int yn) {
+    int x, y, z;
+    node_xyz(c, xn, x, y, z);
+    const int i = axis == 0 ? x : (axis == 1 ? y : z);
+    const int nn = axis == 0 ? c.nx : (axis == 1 ? c.ny : c.nz);
+    const bool periodic = axis == 0 || (axis == 2 && !c.wall_z);
+    auto node_at = [&](int j) {
+        int xx = x, yy = y, zz = z;
+        if (axis == 0) xx = j; else if (axis == 1) yy = j; else zz = j;
+        return c.off + xx + c.nx * (yy + c.ny * zz);
+    };
+    double w = 0.0;
+    if (periodic) {
+        const int jp = (i + 1) % nn, jm = (i - 1 + nn) % nn;
+        if (node_at(jp) == yn) w += 0.5;
+        if (node_at(jm) == yn) w -= 0.5;
+        return w;
+    }
+    if (i == 0) {
+        if (node_at(0) == yn) w += 1.0;
+        if (nn > 1 && node_at(1) == yn) w += 1.0 / 3.0;
+        return w;
+    }
+    if (i == nn - 1) {
+        if (node_at(nn - 1) == yn) w -= 1.0;
+        if (node_at(nn - 2) == yn) w -= 1.0 / 3.0;
+        return w;
+    }
+    if (node_at(i + 1) == yn) w += 0.5;
+    if (node_at(i - 1) == yn) w -= 0.5;
+    return w;
+}
+
+// Transpose of the finite differences and adjoint of the raw moments at node n.
+template <int Q>
+__global__ void __launch_bounds__(128) k_adj_fd(const double* __restrict__ pops, const double* __restrict__ lam_kt,
+                                                double* __restrict__ lam_n0, double* __restrict__ lam_theta, Geom g,
+                                                AdjPar p) {
+    using L = Lattice<Q>;
+    constexpr int D = L::D;
+    constexpr int DD = D * D;
+    const int n = blockIdx.x * blockDim.x + threadIdx.x;
+    if (n >= g.N) return;
+    const long long Np = g.Npad;
+    const Chan& ch = g.ch[0];
+    int x, y, z;
+    node_xyz(ch, n, x, y, z);
+    // lambda u_raw(n) = sum over stencils that read n
+    double lam_ur[3] = {0, 0, 0};
+    for (int axis = 0; axis < D; ++axis) {
+        const int nn = axis == 0 ? ch.nx : (axis == 1 ? ch.ny : ch.nz);
+        const int i = axis == 0 ? x : (axis == 1 ? y : z);
+        int cand[3];
+        int nc = 0;
+        for (int dlt = -1; dlt <= 1; ++dlt) {
+            int j = i + dlt;
+            const bool periodic = axis == 0 || (axis == 2 && !ch.wall_z);
+            if (periodic) j = (j + nn) % nn;
+            else if (j < 0 || j >= nn) continue;
+            int xx = x, yy = y, zz = z;
+            if (axis == 0) xx = j; else if (axis == 1) yy = j; else zz = j;
+            const int m = ch.off + xx + ch.nx * (yy + ch.ny * zz);
+            bool seen = false;
+            for (int k = 0; k < nc; ++k) seen = seen || cand[k] == m;
+            if (!seen) cand[nc++] = m;
+        }
+        for (int k = 0; k < nc; ++k) {
+            const double wgt = fd_weight(ch, axis, cand[k], n);
+            if (wgt == 0.0) continue;
+            for (int a = 0; a < D; ++a) lam_ur[a] += wgt * lam_kt[(a * D + axis) * Np + cand[k]];
+        }
+    }
+    // u_raw = (J + f/2) / (rho0 + dr)
+    double dr = 0.0, J[3] = {0, 0, 0};
+    for (int q = 0; q < Q; ++q) {
+        const double v = pops[q * Np + n];
+        dr += v;
+        J[0] += L::cx(q) * v;
+        J[1] += L::cy(q) * v;
+        if (D == 3) J[2] += L::cz(q) * v;
+    }
+    const double rr = p.rho0 + dr;
+    double lam_dr = 0.0, lam_J[3] = {0, 0, 0};
+    for (int a = 0; a < D; ++a) {
+        const double ur = (J[a] + 0.5 * p.f[a]) / rr;
+        lam_J[a] += lam_ur[a] / rr;
+        lam_dr += -ur * lam_ur[a] / rr;
+        if (a == 0) lam_theta[3 * Np + n] += p.rho0 * 0.5 * lam_ur[0] / rr;
+    }
+    for (int q = 0; q < Q; ++q) {
+        double l = lam_dr + L::cx(q) * lam_J[0] + L::cy(q) * lam_J[1];
+        if (D == 3) l += L::cz(q) * lam_J[2];
+        lam_n0[q * Np + n] += l;
+    }
+    (void)DD;
+}
+
+}  // namespace lbk

@@ -19,6 +19,7 @@
 #include "../../include/lbve.h"
 #include "lbve_kernels.cuh"
 #include "lbve_tangent.cuh"
+#include "lbve_adjoint.cuh"
 
 using namespace lbk;
 
@@ -84,6 +85,9 @@ struct lbve {
     cudaStream_t graph_stream = nullptr;
     // tangent-linear mode (lbve_create_tangent): all state buffers hold duals
     int tangent = 0;
+    // recording for the adjoint (lbve_create_adjoint): a state image every rec_K steps
+    int rec_K = 0;
+    std::vector<void*> ckpts;
     // kernel timing (lbve_profile): event pairs recorded around each launch of lbve_step
     int profiling = 0;
     std::vector<cudaEvent_t> ev_pool;
@@ -101,6 +105,9 @@ void free_all(lbve* h) {
         if (p) cudaFree(p);
     for (cudaEvent_t e : h->ev_pool) cudaEventDestroy(e);
     h->ev_pool.clear();
+    for (void* c : h->ckpts)
+        if (c) cudaFree(c);
+    h->ckpts.clear();
     if (h->graph) cudaGraphExecDestroy(h->graph);
     if (h->graph_stream) cudaStreamDestroy(h->graph_stream);
     h->graph = nullptr;
@@ -392,9 +399,20 @@ int capture_graph(lbve* h) {
     return LBVE_OK;
 }
 
+int record_checkpoint(lbve* h, cudaStream_t s);
+
 template <int Q, typename P, int HK, typename T>
 int step_impl(lbve* h, int64_t n, cudaStream_t s) {
     int rc;
+    if (h->rec_K) {   // recording for the adjoint: an image every rec_K steps, no graphs
+        for (int64_t i = 0; i < n; ++i) {
+            if (h->t_host % h->rec_K == 0 && (rc = record_checkpoint(h, s))) return rc;
+            if ((rc = one_step<Q, P, HK, T>(h, h->cur, s))) return rc;
+            h->cur ^= 1;
+            h->t_host += 1;
+        }
+        return LBVE_OK;
+    }
     // whole graphs of kGraphSteps steps (an even count, so populations end where they started); the
     // graph is recorded for cur == 0, so a pending odd step is run first.  Profiling records per-launch
     // events and therefore launches step by step.
@@ -1106,6 +1124,176 @@ int lbve_checkpoint_restore(lbve_t* h, const void* src, int32_t src_is_device, v
         h->d = h->descs[0];
     }
     return LBVE_OK;
+}
+
+}  // extern "C"
+
+namespace {
+
+int record_checkpoint(lbve* h, cudaStream_t s) {
+    size_t bytes = 0;
+    lbve_checkpoint_size(h, &bytes);
+    const size_t idx = (size_t)(h->t_host / h->rec_K);
+    if (h->ckpts.size() <= idx) h->ckpts.resize(idx + 1, nullptr);
+    if (!h->ckpts[idx]) LBVE_CUDA(cudaMalloc(&h->ckpts[idx], bytes));
+    return lbve_checkpoint_save(h, h->ckpts[idx], 1, s);
+}
+
+AdjPar adj_par(const lbve* h) {
+    const lbve_channel_desc& d = h->descs[0];
+    AdjPar p;
+    p.G_inf = d.G_inf;
+    p.tau = d.tau;
+    p.gamma_c = d.gamma_c;
+    p.inv_tau = 1.0 / d.tau;
+    p.inv_gc = std::isinf(d.gamma_c) ? 0.0 : 1.0 / d.gamma_c;
+    p.rho0 = d.rho0;
+    p.tau_lb = d.tau_lb;
+    for (int a = 0; a < 3; ++a) p.f[a] = d.rho0 * d.g[a];
+    p.trace_full = d.trace_coupling == LBVE_TRACE_FULL;
+    return p;
+}
+
+// Device allocation released at scope exit (the adjoint's work buffers).
+struct DevBuf {
+    void* p = nullptr;
+    ~DevBuf() { if (p) cudaFree(p); }
+};
+
+template <int Q>
+int backward_impl(lbve* h, const double* dL_du, const double* dL_ds, double* grad, cudaStream_t s) {
+    constexpr int D = Lattice<Q>::D;
+    constexpr int DD = D * D;
+    const int NS = h->NS;
+    const long long Np = h->Npad;
+    const int64_t T = h->t_host;
+    const int K = h->rec_K;
+    if (T < 1) return LBVE_ESTATE;
+    const size_t hist_b = sizeof(double) * (size_t)h->L * DD * Np;
+    const size_t pop_b = sizeof(double) * h->Q * Np;
+    // work buffers
+    DevBuf lam_n, lamX, lamK, lam_trp, lam_kt, lam_th, seeds, tape, ur, cnt, fin;
+    LBVE_CUDA(cudaMalloc(&lam_n.p, 2 * pop_b));
+    LBVE_CUDA(cudaMalloc(&lamX.p, hist_b));
+    LBVE_CUDA(cudaMalloc(&lamK.p, hist_b));
+    LBVE_CUDA(cudaMalloc(&lam_trp.p, sizeof(double) * Np));
+    LBVE_CUDA(cudaMalloc(&lam_kt.p, sizeof(double) * DD * Np));
+    LBVE_CUDA(cudaMalloc(&lam_th.p, sizeof(double) * 4 * Np));
+    LBVE_CUDA(cudaMalloc(&seeds.p, sizeof(double) * (D + NS) * Np));
+    const size_t step_b = pop_b + 2 * hist_b + sizeof(double) * Np;   // pops, X, K, tr_prev
+    LBVE_CUDA(cudaMalloc(&tape.p, step_b * (size_t)K));
+    LBVE_CUDA(cudaMalloc(&ur.p, sizeof(double) * D * Np));
+    LBVE_CUDA(cudaMalloc(&cnt.p, sizeof(long long)));
+    size_t img = 0;
+    lbve_checkpoint_size(h, &img);
+    LBVE_CUDA(cudaMalloc(&fin.p, img));
+    int rc = lbve_checkpoint_save(h, fin.p, 1, s);   // the final state, restored at the end
+    if (rc) return rc;
+    LBVE_CUDA(cudaMemsetAsync(lam_n.p, 0, 2 * pop_b, s));
+    LBVE_CUDA(cudaMemsetAsync(lamX.p, 0, hist_b, s));
+    LBVE_CUDA(cudaMemsetAsync(lamK.p, 0, hist_b, s));
+    LBVE_CUDA(cudaMemsetAsync(lam_trp.p, 0, sizeof(double) * Np, s));
+    LBVE_CUDA(cudaMemsetAsync(lam_th.p, 0, sizeof(double) * 4 * Np, s));
+    LBVE_CUDA(cudaMemsetAsync(seeds.p, 0, sizeof(double) * (D + NS) * Np, s));
+    double* seed_u = (double*)seeds.p;
+    double* seed_s = seed_u + D * Np;
+    for (int c = 0; c < D; ++c)
+        LBVE_CUDA(cudaMemcpyAsync(seed_u + c * Np, dL_du + (size_t)c * h->N, sizeof(double) * h->N,
+                                  cudaMemcpyHostToDevice, s));
+    for (int c = 0; c < NS; ++c)
+        LBVE_CUDA(cudaMemcpyAsync(seed_s + c * Np, dL_ds + (size_t)c * h->N, sizeof(double) * h->N,
+                                  cudaMemcpyHostToDevice, s));
+    const Geom g = geom_of(h);
+    const AdjPar p = adj_par(h);
+    const int grid64 = (h->N + 63) / 64, grid128 = (h->N + 127) / 128;
+    const size_t smem = sweep_smem_bytes(h->L);
+    if (smem > 48 * 1024)
+        LBVE_CUDA(cudaFuncSetAttribute(k_adj_node<Q>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    const int rec = h->rec_K;
+    h->rec_K = 0;   // the replay below must not record
+    int cur_lam = 0;
+    const int64_t nseg = (T + K - 1) / K;
+    for (int64_t sg = nseg - 1; sg >= 0 && rc == LBVE_OK; --sg) {
+        if ((size_t)sg >= h->ckpts.size() || !h->ckpts[sg]) { rc = LBVE_ESTATE; break; }
+        if ((rc = lbve_checkpoint_restore(h, h->ckpts[sg], 1, s))) break;
+        const int64_t t0 = sg * K, t1 = std::min<int64_t>(T, t0 + K);
+        for (int64_t t = t0; t < t1 && rc == LBVE_OK; ++t) {   // replay with a tape of each step's state
+            char* slot = (char*)tape.p + step_b * (size_t)(t - t0);
+            LBVE_CUDA(cudaMemcpyAsync(slot, h->pops[h->cur], pop_b, cudaMemcpyDeviceToDevice, s));
+            LBVE_CUDA(cudaMemcpyAsync(slot + pop_b, h->X, hist_b, cudaMemcpyDeviceToDevice, s));
+            LBVE_CUDA(cudaMemcpyAsync(slot + pop_b + hist_b, h->K, hist_b, cudaMemcpyDeviceToDevice, s));
+            LBVE_CUDA(cudaMemcpyAsync(slot + pop_b + 2 * hist_b, h->tr_prev, sizeof(double) * Np,
+                                      cudaMemcpyDeviceToDevice, s));
+            rc = one_step<Q, double, 1, double>(h, h->cur, s);
+            h->cur ^= 1;
+            h->t_host += 1;
+        }
+        for (int64_t t = t1 - 1; t >= t0 && rc == LBVE_OK; --t) {
+            const char* slot = (const char*)tape.p + step_b * (size_t)(t - t0);
+            const double* pops_t = (const double*)slot;
+            k_moments<Q, double><<<(h->N + 255) / 256, 256, 0, s>>>(pops_t, (double*)ur.p, g, (long long*)cnt.p);
+            LBVE_CUDA(cudaGetLastError());
+            AdjArgs a;
+            a.n = pops_t;
+            a.X = (const double*)(slot + pop_b);
+            a.K = (const double*)(slot + pop_b + hist_b);
+            a.trp = (const double*)(slot + pop_b + 2 * hist_b);
+            a.u_raw = (const double*)ur.p;
+            a.lam_n1 = (const double*)lam_n.p + (size_t)cur_lam * h->Q * Np;
+            a.lam_n0 = (double*)lam_n.p + (size_t)(cur_lam ^ 1) * h->Q * Np;
+            a.lamX = (double*)lamX.p;
+            a.lamK = (double*)lamK.p;
+            a.lam_trp = (double*)lam_trp.p;
+            a.lam_kt = (double*)lam_kt.p;
+            a.lam_theta = (double*)lam_th.p;
+            a.seed_u = t == T - 1 ? seed_u : nullptr;
+            a.seed_s = t == T - 1 ? seed_s : nullptr;
+            a.t = t;
+            a.B = h->d.hist_B;
+            a.C = h->d.hist_C;
+            k_adj_node<Q><<<grid64, 64, smem, s>>>(a, g, p);
+            LBVE_CUDA(cudaGetLastError());
+            k_adj_fd<Q><<<grid128, 128, 0, s>>>(pops_t, (const double*)lam_kt.p, a.lam_n0, (double*)lam_th.p, g, p);
+            LBVE_CUDA(cudaGetLastError());
+            cur_lam ^= 1;
+        }
+    }
+    h->rec_K = rec;
+    if (rc) return rc;
+    // dL/dtheta = sum over nodes of the per-node parts
+    double* red = h->red;
+    double out[4];
+    for (int k = 0; k < 4; ++k) {
+        LBVE_CUDA(cudaMemsetAsync(red, 0, sizeof(double), s));
+        k_sum<double><<<4 * 152, 256, 0, s>>>((const double*)lam_th.p + (size_t)k * Np, Np, 1, h->N, 1.0, red);
+        LBVE_CUDA(cudaGetLastError());
+        LBVE_CUDA(cudaMemcpyAsync(&out[k], red, sizeof(double), cudaMemcpyDeviceToHost, s));
+        LBVE_CUDA(cudaStreamSynchronize(s));
+    }
+    for (int k = 0; k < 4; ++k) grad[k] = out[k];
+    return lbve_checkpoint_restore(h, fin.p, 1, s);
+}
+
+}  // namespace
+
+extern "C" {
+
+int lbve_create_adjoint(const lbve_channel_desc* desc, const double* rho_init, int32_t checkpoint_every,
+                        lbve_t** out) {
+    if (!desc || !out || checkpoint_every < 1) return LBVE_EINVAL;
+    if (desc->pop_precision != LBVE_F64 || desc->hist_storage != LBVE_F64) return LBVE_ENOSUPPORT;
+    int rc = create_impl(desc, 1, rho_init, out);
+    if (rc) return rc;
+    (*out)->rec_K = checkpoint_every;
+    return LBVE_OK;
+}
+
+int lbve_backward(lbve_t* h, const double* dL_du, const double* dL_dsigma, double grad_out[4], void* stream) {
+    if (!h || !dL_du || !dL_dsigma || !grad_out) return LBVE_EINVAL;
+    if (!h->rec_K) return LBVE_ESTATE;
+    cudaStream_t s = (cudaStream_t)stream;
+    return h->Q == 9 ? backward_impl<9>(h, dL_du, dL_dsigma, grad_out, s)
+                     : backward_impl<19>(h, dL_du, dL_dsigma, grad_out, s);
 }
 
 int lbve_create_tangent(const lbve_channel_desc* desc, const double* rho_init, lbve_t** out) {

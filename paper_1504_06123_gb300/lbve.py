@@ -32,7 +32,7 @@ EXPORTS = [
     "lbve_memory_bytes", "lbve_strerror", "lbve_last_cuda_error", "lbve_profile", "lbve_profile_read",
     "lbve_fields_host_fixed", "lbve_create_batch", "lbve_channel_nodes", "lbve_sweep_config",
     "lbve_create_tangent", "lbve_tangent_fields", "lbve_checkpoint_size", "lbve_checkpoint_save",
-    "lbve_checkpoint_restore",
+    "lbve_checkpoint_restore", "lbve_create_adjoint", "lbve_backward",
 ]
 
 
@@ -74,6 +74,8 @@ def load(path: str | None = None):
         lib.lbve_destroy.restype = None
         lib.lbve_create_batch.argtypes = [C.POINTER(lbve_channel_desc), i32, dp, C.POINTER(vp)]
         lib.lbve_create_tangent.argtypes = [C.POINTER(lbve_channel_desc), dp, C.POINTER(vp)]
+        lib.lbve_create_adjoint.argtypes = [C.POINTER(lbve_channel_desc), dp, i32, C.POINTER(vp)]
+        lib.lbve_backward.argtypes = [vp, dp, dp, dp, vp]
         lib.lbve_checkpoint_size.argtypes = [vp, C.POINTER(C.c_size_t)]
         lib.lbve_checkpoint_save.argtypes = [vp, vp, i32, vp]
         lib.lbve_checkpoint_restore.argtypes = [vp, vp, i32, vp]
@@ -179,6 +181,30 @@ def lbve_tangent_fields(h: int, mask: int, stream=None) -> np.ndarray:
     cnt = lbve_fields_count(h, mask)
     out = np.empty((4, cnt), dtype=np.float64)
     _check(load().lbve_tangent_fields(h, mask, out.ctypes.data, _stream(stream)), "lbve_tangent_fields")
+    return out
+
+
+def lbve_create_adjoint(desc: lbve_channel_desc, rho_init: np.ndarray | None = None,
+                        checkpoint_every: int = 64) -> int:
+    lib = load()
+    h = C.c_void_p()
+    ri = None
+    if rho_init is not None:
+        ri = np.ascontiguousarray(rho_init, dtype=np.float64).ravel()
+    rc = lib.lbve_create_adjoint(C.byref(desc), ri.ctypes.data_as(C.POINTER(C.c_double)) if ri is not None else None,
+                                 int(checkpoint_every), C.byref(h))
+    _check(rc, "lbve_create_adjoint")
+    return h.value
+
+
+def lbve_backward(h: int, dL_du: np.ndarray, dL_dsigma: np.ndarray, stream=None) -> np.ndarray:
+    """dL/d(G_inf, tau, gamma_c, g_x) for seeds dL_du [d, N] and dL_dsigma [nsig, N] of the last step."""
+    du = np.ascontiguousarray(dL_du, dtype=np.float64)
+    ds = np.ascontiguousarray(dL_dsigma, dtype=np.float64)
+    out = np.zeros(4)
+    dp = C.POINTER(C.c_double)
+    _check(load().lbve_backward(h, du.ctypes.data_as(dp), ds.ctypes.data_as(dp), out.ctypes.data_as(dp),
+                                _stream(stream)), "lbve_backward")
     return out
 
 

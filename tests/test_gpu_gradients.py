@@ -113,3 +113,62 @@ def test_gradient_workload_channel_vs_oracle_window():
     g_orc = central_fd(lambda th: loss_np(*oracle_profiles(desc, th, steps), uo, so), theta)
     g_tan, _ = tangent_grad(desc, theta, steps, uo, so)
     check(g_tan, g_orc, "tangent vs oracle finite differences, 400 steps")
+
+
+# ---------------------------------------------------------------------------------------------
+# Reverse mode: the adjoint with checkpoint recomputation, against the tangent model (same gradient up to
+# rounding) and against finite differences
+# ---------------------------------------------------------------------------------------------
+from paper_1504_06123_gb300.autograd import LBVEChannelAdjoint  # noqa: E402
+
+
+def adjoint_grad(desc, theta, steps, ut, st, every):
+    th = torch.tensor(theta, dtype=torch.float64, requires_grad=True)
+    u, s = LBVEChannelAdjoint.apply(th, desc, steps, every)
+    loss = profile_loss(u, s, ut, st)
+    loss.backward()
+    return th.grad.numpy().copy()
+
+
+@pytest.mark.parametrize("every", [7, 64])
+@pytest.mark.parametrize("C,B", [(32, 2), (8, 4)])
+def test_adjoint_matches_tangent_and_fd(every, C, B):
+    desc = L.make_desc(nx=4, ny=16, tau_lb=0.9, G_inf=0.01, tau=60.0, gamma_c=0.1, g=(2e-5, 0, 0), C=C, B=B,
+                       precision=L.LBVE_F64, hist_storage=L.LBVE_F64)
+    steps = 150
+    theta = np.array([desc.G_inf, desc.tau, desc.gamma_c, desc.g[0]])
+    ut, st = run_profiles(desc, inputs.perturbed(theta, seed=5), steps)
+    g_adj = adjoint_grad(desc, theta, steps, ut, st, every)
+    g_tan, _ = tangent_grad(desc, theta, steps, ut, st)
+    np.testing.assert_allclose(g_adj, g_tan, rtol=1e-9, atol=1e-14 * np.max(np.abs(g_tan)))
+    g_fd = central_fd(lambda th: loss_np(*run_profiles(desc, th, steps), ut, st), theta)
+    check(g_adj, g_fd, "adjoint vs GPU finite differences")
+
+
+def test_adjoint_trace_none_and_duct():
+    desc = L.make_desc(nx=3, ny=8, tau_lb=0.8, G_inf=0.02, tau=30.0, gamma_c=0.2, g=(3e-5, 0, 0), C=8, B=3,
+                       precision=L.LBVE_F64, hist_storage=L.LBVE_F64, trace_coupling=L.LBVE_TRACE_NONE)
+    steps = 90
+    theta = np.array([desc.G_inf, desc.tau, desc.gamma_c, desc.g[0]])
+    ut, st = run_profiles(desc, inputs.perturbed(theta, seed=6), steps)
+    np.testing.assert_allclose(adjoint_grad(desc, theta, steps, ut, st, 16), tangent_grad(desc, theta, steps, ut, st)[0],
+                               rtol=1e-9)
+    duct = L.make_desc(L.LBVE_D3Q19, 2, 5, 5, tau_lb=0.9, G_inf=0.01, tau=25.0, gamma_c=0.1, g=(2e-5, 0, 0), C=8, B=2,
+                       precision=L.LBVE_F64, hist_storage=L.LBVE_F64)
+    steps = 40
+    theta = np.array([duct.G_inf, duct.tau, duct.gamma_c, duct.g[0]])
+    ut, st = run_profiles(duct, inputs.perturbed(theta, seed=7), steps)
+    np.testing.assert_allclose(adjoint_grad(duct, theta, steps, ut, st, 16), tangent_grad(duct, theta, steps, ut, st)[0],
+                               rtol=1e-9)
+
+
+def test_adjoint_workload_channel():
+    """4 x 128 channel, L = 512, 4000 steps, checkpoints every 64 steps."""
+    w = configs.gradient_channel()
+    desc = w.desc(precision=L.LBVE_F64, hist_storage=L.LBVE_F64)
+    theta = np.array([w.G_inf, w.tau, w.gamma_c, w.g])
+    ut, st = run_profiles(desc, inputs.perturbed(theta, seed=w.seed), w.steps)
+    g_adj = adjoint_grad(desc, theta, w.steps, ut, st, 64)
+    g_tan, _ = tangent_grad(desc, theta, w.steps, ut, st)
+    print("adjoint gradient (G_inf, tau, gamma_c, g):", g_adj)
+    np.testing.assert_allclose(g_adj, g_tan, rtol=1e-8)

@@ -25,6 +25,9 @@ _lock = threading.Lock()
 _lib = None
 
 D2Q9, D3Q19 = 9, 19
+# constitutive model of sigma_struc: integral nlM (Eqs. gitt, nlmax), instantaneous nlM (Eq. inlM),
+# White-Metzner form of Eq. (nlmax) (accumulated strain in the second exponential, Sec. II)
+NLM, INLM, WM = 0, 1, 2
 
 
 def build(force: bool = False) -> str:
@@ -45,7 +48,7 @@ def _load():
         lib = C.CDLL(build())
         dp = C.POINTER(C.c_double)
         lib.orc_history_run.argtypes = [C.c_int, C.c_int, C.c_int, C.c_int, C.c_double, C.c_double, C.c_double,
-                                        C.c_int, dp, dp, C.c_int]
+                                        C.c_int, dp, dp, C.c_int, C.c_int]
         lib.orc_history_run.restype = C.c_int
         lib.orc_schedule.argtypes = [C.c_int, C.c_int, C.c_int64, C.POINTER(C.c_int64), dp]
         lib.orc_schedule.restype = C.c_int
@@ -55,6 +58,10 @@ def _load():
         lib.orc_destroy.argtypes = [C.c_void_p]
         lib.orc_set_force.argtypes = [C.c_void_p, dp]
         lib.orc_set_params.argtypes = [C.c_void_p, C.c_double, C.c_double, C.c_double]
+        lib.orc_set_model.argtypes = [C.c_void_p, C.c_int]
+        lib.orc_set_model.restype = C.c_int
+        lib.orc_inlm.argtypes = [C.c_int, dp, C.c_double, C.c_double, C.c_double, dp]
+        lib.orc_inlm.restype = C.c_int
         lib.orc_time.argtypes = [C.c_void_p]
         lib.orc_time.restype = C.c_int64
         lib.orc_step.argtypes = [C.c_void_p, C.c_int64]
@@ -82,14 +89,15 @@ def expm(K: np.ndarray) -> np.ndarray:
 
 
 def history_run(kappa_seq: np.ndarray, C_: int, B: int, G_inf: float, tau: float, gamma_c: float,
-                last_only: bool = False) -> np.ndarray:
+                last_only: bool = False, model: int = NLM) -> np.ndarray:
     """Stress history integral with a prescribed velocity gradient at every node and step.
 
     kappa_seq: [T, nnodes, d, d] (or [T, nnodes, d*d]) -- kappa(t) of each node, row-major
     kappa[a, b] = d v_a / d x_b.  Returns sigma_struc [T, nnodes, nsig] (or [nnodes, nsig] with
     last_only), components xx, yy, xy (2D) or xx, yy, zz, xy, xz, yz (3D).
     Follows Eq. (gitt) with the modulus of Eq. (nlmax) on the quasi-logarithmic grid and factor
-    storage of Sec. III / Eq. (eeval).
+    storage of Sec. III / Eq. (eeval).  model = WM takes the accumulated strain in the modulus;
+    model = INLM evaluates Eq. (inlM) on kappa(t) alone (C_ and B are then unused).
     """
     k = np.ascontiguousarray(kappa_seq, dtype=np.float64)
     T, nn = k.shape[0], k.shape[1]
@@ -97,9 +105,23 @@ def history_run(kappa_seq: np.ndarray, C_: int, B: int, G_inf: float, tau: float
     d = int(round(math.sqrt(dd)))
     nsig = 3 if d == 2 else 6
     out = np.zeros((nn, nsig) if last_only else (T, nn, nsig))
-    rc = _load().orc_history_run(d, nn, C_, B, G_inf, tau, gamma_c, T, _dp(k), _dp(out), int(last_only))
+    rc = _load().orc_history_run(d, nn, C_, B, G_inf, tau, gamma_c, T, _dp(k), _dp(out), int(last_only),
+                                 int(model))
     if rc != 0:
         raise ValueError("orc_history_run rejected its arguments")
+    return out
+
+
+def inlm(K: np.ndarray, G_inf: float, tau: float, gamma_c: float) -> np.ndarray:
+    """sigma_struc of the instantaneous nlM, Eq. (inlM), for one gradient K [d, d] (series as printed).
+
+    Returns the packed components (xx, yy, xy or xx, yy, zz, xy, xz, yz); NaN where the series diverges.
+    """
+    K = np.ascontiguousarray(K, dtype=np.float64)
+    d = K.shape[0]
+    out = np.zeros(3 if d == 2 else 6)
+    if _load().orc_inlm(d, _dp(K), G_inf, tau, gamma_c, _dp(out)) != 0:
+        raise ValueError("orc_inlm rejected its arguments")
     return out
 
 
@@ -123,7 +145,8 @@ class Channel:
 
     def __init__(self, lattice: int, nx: int, ny: int, nz: int = 1, *, tau_lb: float, G_inf: float,
                  tau: float, gamma_c: float, g=(0.0, 0.0, 0.0), C: int, B: int, rho0: float = 1.0,
-                 trace_full: bool = True, wall_z: bool = True, rho_init: np.ndarray | None = None):
+                 trace_full: bool = True, wall_z: bool = True, rho_init: np.ndarray | None = None,
+                 model: int = NLM):
         self.lib = _load()
         self.lattice, self.nx, self.ny, self.nz = lattice, nx, ny, nz
         self.d = 2 if lattice == D2Q9 else 3
@@ -137,6 +160,9 @@ class Channel:
                                       _dp(gg), C, B, int(trace_full), _dp(ri) if ri is not None else None)
         if not self._h:
             raise ValueError("orc_create rejected its arguments")
+        if self.lib.orc_set_model(self._h, int(model)) != 0:
+            self.close()
+            raise ValueError("unknown constitutive model")
 
     def close(self):
         if getattr(self, "_h", None):

@@ -43,6 +43,17 @@
  *   - the Newtonian background viscosity of Eq. (nlM) is the BGK viscosity rho c_s^2 (tau_LB - 1/2);
  *   - kappa by second-order finite differences: central in the bulk and on periodic axes; at a
  *     wall-adjacent node the three-point formula through the no-slip wall half a node away.
+ *
+ * Constitutive variants of sigma_struc (model kind, Sec. II and Sec. IV):
+ *   - ORC_NLM: the integral nlM, Eq. (gitt) with the modulus of Eq. (nlmax) (default);
+ *   - ORC_INLM: the instantaneous nlM, Eq. (inlM) re-read as a stress / strain-rate law at time t:
+ *     sigma_struc(t) = G_inf sum_{n>=1} tau_M^n d^(n)[kappa(t)], tau_M = (1/tau + gammadot(t)/gamma_c)^-1
+ *     (the steady form of Eq. (nlmax)), the series summed term by term until it has converged; where
+ *     it does not converge (no steady state exists) the stress is NaN;
+ *   - ORC_WM: the White-Metzner form of Eq. (nlmax): the second exponential uses the strain
+ *     accumulated between t' and t, sum_{s=t'}^{t-1} gammadot(s) (the same explicit left-end rule as
+ *     the factors of Eq. (eeval)), instead of (t - t') gammadot(t').  Every point stores the strain of
+ *     its span next to its factor; a merge adds the two spans' strains, as it multiplies their factors.
  */
 #include <math.h>
 #include <stdint.h>
@@ -155,6 +166,7 @@ typedef struct {
     int64_t tp;     /* t': start of the span this point stands for */
     double kap[9];  /* kappa stored with the point (averaged on merge) */
     double F[9];    /* factor over the span: exp(kappa dt) or product of merged factors */
+    double gs;      /* strain over the span: gammadot(kappa(t')) dt or sum of merged strains (WM) */
 } orc_pt;
 
 typedef struct {
@@ -178,6 +190,7 @@ static void hist_init(orc_hist* h, int d, int C, int B) {
             blk[k].tp = tp;
             memset(blk[k].kap, 0, sizeof blk[k].kap);
             mat_identity(d, blk[k].F);
+            blk[k].gs = 0.0;
         }
         h->count[b - 1] = C;
     }
@@ -203,6 +216,7 @@ static void hist_insert(orc_hist* h, int b, const orc_pt* p) {
             merged.tp = o1->tp;                   /* the merged point keeps the older time */
             for (int i = 0; i < d * d; ++i) merged.kap[i] = 0.5 * (o1->kap[i] + o2->kap[i]);
             mat_mul(d, o2->F, o1->F, merged.F);   /* later factor on the left */
+            merged.gs = o1->gs + o2->gs;          /* strain of the joined span */
             h->count[b - 1] -= 2;
             hist_insert(h, b - 1, &merged);
         }
@@ -233,7 +247,83 @@ static void trapezoid_weights(int n, const double* s, double* w) {
     }
 }
 
-typedef struct { double G_inf, tau, gamma_c; } orc_model;
+enum { ORC_NLM = 0, ORC_INLM = 1, ORC_WM = 2 };
+typedef struct { double G_inf, tau, gamma_c; int kind; } orc_model;
+
+/* local shear rate of Sec. II: gammadot^2 = (1/2) tr D^2, D = kappa + kappa^T */
+static double shear_rate(int d, const double* K) {
+    double trD2 = 0.0;
+    for (int a = 0; a < d; ++a)
+        for (int b = 0; b < d; ++b) {
+            const double Dab = K[a * d + b] + K[b * d + a];
+            trD2 += Dab * Dab;
+        }
+    return sqrt(0.5 * trD2);
+}
+
+static void pack_sym(int d, const double* S, double* sig) {
+    if (d == 2) {
+        sig[0] = S[0]; sig[1] = S[3]; sig[2] = S[1];
+    } else {
+        sig[0] = S[0]; sig[1] = S[4]; sig[2] = S[8];
+        sig[3] = S[1]; sig[4] = S[2]; sig[5] = S[5];
+    }
+}
+
+/*
+ * Instantaneous nlM, Eq. (inlM): sigma_struc = G_inf sum_{n>=1} tau_M^n d^(n) with
+ * d^(n) = sum_{m=0}^{n} binom(n,m) kappa^m (kappa^T)^(n-m), summed as printed, term by term.  The factor
+ * tau_M^n is carried inside the powers, tau_M^n kappa^m (kappa^T)^(n-m) = A^m (A^T)^(n-m) with
+ * A = tau_M kappa, so that neither tau_M^n nor kappa^n leaves the double range before the series has
+ * converged.  The sum stops once two consecutive terms are below 1e-18 of the partial sum (or vanish:
+ * a nilpotent kappa, e.g. simple shear, ends the series at n = 2); after ORC_INLM_NMAX orders without
+ * convergence the result is NaN.
+ */
+#define ORC_INLM_NMAX 1000
+static void inlm_stress(int d, const double* K, const orc_model* m, double* sig) {
+    const int dd = d * d;
+    const double gd = shear_rate(d, K);
+    const double rate = 1.0 / m->tau + (isinf(m->gamma_c) ? 0.0 : gd / m->gamma_c);
+    const double tM = 1.0 / rate;
+    double A[9], AT[9];
+    for (int a = 0; a < d; ++a)
+        for (int b = 0; b < d; ++b) {
+            A[a * d + b] = tM * K[a * d + b];
+            AT[a * d + b] = tM * K[b * d + a];
+        }
+    /* powers A^m and (A^T)^m, m = 0 .. n */
+    double* pa = (double*)malloc(sizeof(double) * 9 * (ORC_INLM_NMAX + 1));
+    double* pat = (double*)malloc(sizeof(double) * 9 * (ORC_INLM_NMAX + 1));
+    mat_identity(d, pa);
+    mat_identity(d, pat);
+    double S[9] = {0}, term[9], prod[9];
+    int quiet = 0, converged = 0;
+    for (int n = 1; n <= ORC_INLM_NMAX && !converged; ++n) {
+        mat_mul(d, pa + 9 * (n - 1), A, pa + 9 * n);
+        mat_mul(d, pat + 9 * (n - 1), AT, pat + 9 * n);
+        for (int i = 0; i < dd; ++i) term[i] = 0.0;
+        double binom = 1.0;   /* binom(n, mm) */
+        for (int mm = 0; mm <= n; ++mm) {
+            mat_mul(d, pa + 9 * mm, pat + 9 * (n - mm), prod);
+            for (int i = 0; i < dd; ++i) term[i] += binom * prod[i];
+            binom = binom * (double)(n - mm) / (double)(mm + 1);
+        }
+        double tn = 0.0, sn = 0.0;
+        for (int i = 0; i < dd; ++i) {
+            S[i] += term[i];
+            tn = fmax(tn, fabs(term[i]));
+            sn = fmax(sn, fabs(S[i]));
+        }
+        if (!isfinite(tn)) break;
+        quiet = (tn <= 1e-18 * sn) ? quiet + 1 : 0;
+        if (quiet >= 2) converged = 1;
+    }
+    free(pa);
+    free(pat);
+    double out[9];
+    for (int i = 0; i < dd; ++i) out[i] = converged ? m->G_inf * S[i] : NAN;
+    pack_sym(d, out, sig);
+}
 
 /*
  * One history step of one node at time t with the node's velocity gradient kappa_t:
@@ -249,6 +339,7 @@ static void hist_step(orc_hist* h, int64_t t, const double* kappa_t, const orc_m
     p.tp = t;
     memcpy(p.kap, kappa_t, sizeof(double) * d * d);
     expm_d(d, kappa_t, p.F);
+    p.gs = shear_rate(d, kappa_t);   /* strain of the step [t, t+1] at the rate of kappa(t) */
     hist_insert(h, h->B, &p);
 
     const int n = hist_list(h, list);
@@ -257,35 +348,26 @@ static void hist_step(orc_hist* h, int64_t t, const double* kappa_t, const orc_m
 
     double S_acc[9] = {0};
     double P[9], Pn[9], M[9], T1[9];
+    double strain = 0.0;     /* WM: strain accumulated from t'_k to t, the sum of the spans' strains */
     mat_identity(d, P);
     const double inv_gc = isinf(m->gamma_c) ? 0.0 : 1.0 / m->gamma_c;
     for (int k = 0; k < n; ++k) {
         if (k >= 1) {            /* E_k = F_1 F_2 ... F_k  (E_0 = 1 for the point created now) */
             mat_mul(d, P, list[k].F, Pn);
             memcpy(P, Pn, sizeof(double) * d * d);
+            strain += list[k].gs;
         }
         const double* K = list[k].kap;
         mat_mul(d, P, K, T1);        /* E kappa */
         mat_mul_bt(d, T1, P, M);     /* E kappa E^T */
-        /* local shear rate from the stored kappa: gammadot^2 = (1/2) tr D^2 */
-        double trD2 = 0.0;
-        for (int a = 0; a < d; ++a)
-            for (int b = 0; b < d; ++b) {
-                const double Dab = K[a * d + b] + K[b * d + a];
-                trD2 += Dab * Dab;
-            }
-        const double gd = sqrt(0.5 * trD2);
         const double s = ages[k];
-        const double G = m->G_inf * exp(-s / m->tau - s * gd * inv_gc);
+        /* Eq. (nlmax): (t - t') gammadot(t') with gammadot from the stored kappa; WM: the strain */
+        const double x2 = (m->kind == ORC_WM) ? strain : s * shear_rate(d, K);
+        const double G = m->G_inf * exp(-s / m->tau - x2 * inv_gc);
         for (int a = 0; a < d; ++a)
             for (int b = 0; b < d; ++b) S_acc[a * d + b] += wts[k] * G * (M[a * d + b] + M[b * d + a]);
     }
-    if (d == 2) {
-        sig[0] = S_acc[0]; sig[1] = S_acc[3]; sig[2] = S_acc[1];
-    } else {
-        sig[0] = S_acc[0]; sig[1] = S_acc[4]; sig[2] = S_acc[8];
-        sig[3] = S_acc[1]; sig[4] = S_acc[2]; sig[5] = S_acc[5];
-    }
+    pack_sym(d, S_acc, sig);
 }
 
 /* ------------------------------------------------------------------------------------------ */
@@ -296,13 +378,15 @@ static void hist_step(orc_hist* h, int64_t t, const double* kappa_t, const orc_m
  * kappa_seq: [T][nnodes][d*d], the gradient of step t (t = 0 .. T-1) at every node.
  * sigma_out: [T][nnodes][nsig] (nsig = 3 or 6), sigma_struc after each step; may be NULL except for
  *            the last step when last_only != 0, then it is [nnodes][nsig].
+ * model: ORC_NLM, ORC_INLM (no history: sigma from kappa(t) alone) or ORC_WM.
  */
 int orc_history_run(int d, int nnodes, int C, int B, double G_inf, double tau, double gamma_c,
-                    int T, const double* kappa_seq, double* sigma_out, int last_only) {
+                    int T, const double* kappa_seq, double* sigma_out, int last_only, int model) {
     if ((d != 2 && d != 3) || nnodes < 0 || C < 2 || B < 1 || T < 0) return -1;
+    if (model != ORC_NLM && model != ORC_INLM && model != ORC_WM) return -1;
     const int nsig = (d == 2) ? 3 : 6;
     const int dd = d * d;
-    orc_model m = {G_inf, tau, gamma_c};
+    orc_model m = {G_inf, tau, gamma_c, model};
     orc_pt* list = (orc_pt*)malloc(sizeof(orc_pt) * (size_t)B * C);
     double* ages = (double*)malloc(sizeof(double) * (size_t)B * C);
     double* wts = (double*)malloc(sizeof(double) * (size_t)B * C);
@@ -311,7 +395,9 @@ int orc_history_run(int d, int nnodes, int C, int B, double G_inf, double tau, d
         hist_init(&h, d, C, B);
         for (int t = 0; t < T; ++t) {
             double sig[6];
-            hist_step(&h, t, kappa_seq + ((size_t)t * nnodes + node) * dd, &m, list, ages, wts, sig);
+            const double* kt = kappa_seq + ((size_t)t * nnodes + node) * dd;
+            if (model == ORC_INLM) inlm_stress(d, kt, &m, sig);
+            else hist_step(&h, t, kt, &m, list, ages, wts, sig);
             double* dst = NULL;
             if (!last_only) dst = sigma_out + ((size_t)t * nnodes + node) * nsig;
             else if (t == T - 1) dst = sigma_out + (size_t)node * nsig;
@@ -320,6 +406,14 @@ int orc_history_run(int d, int nnodes, int C, int B, double G_inf, double tau, d
         hist_free(&h);
     }
     free(list); free(ages); free(wts);
+    return 0;
+}
+
+/* Eq. (inlM) for one gradient (test access): sig receives 3 (2D) or 6 (3D) components. */
+int orc_inlm(int d, const double* K, double G_inf, double tau, double gamma_c, double* sig) {
+    if (d != 2 && d != 3) return -1;
+    orc_model m = {G_inf, tau, gamma_c, ORC_INLM};
+    inlm_stress(d, K, &m, sig);
     return 0;
 }
 
@@ -432,7 +526,7 @@ orc_channel* orc_create(int lattice, int nx, int ny, int nz, int wall_z, double 
     ch->nx = nx; ch->ny = ny; ch->nz = nz; ch->wall_z = (lattice == 19) ? wall_z : 0;
     ch->tau_lb = tau_lb; ch->rho0 = rho0;
     ch->g[0] = g ? g[0] : 0.0; ch->g[1] = g ? g[1] : 0.0; ch->g[2] = g ? g[2] : 0.0;
-    ch->m.G_inf = G_inf; ch->m.tau = tau; ch->m.gamma_c = gamma_c;
+    ch->m.G_inf = G_inf; ch->m.tau = tau; ch->m.gamma_c = gamma_c; ch->m.kind = ORC_NLM;
     ch->C = C; ch->B = B; ch->trace_full = trace_full;
     ch->t = 0;
     set_lattice(ch);
@@ -477,6 +571,14 @@ void orc_set_force(orc_channel* ch, const double* g) {
 
 void orc_set_params(orc_channel* ch, double G_inf, double tau, double gamma_c) {
     ch->m.G_inf = G_inf; ch->m.tau = tau; ch->m.gamma_c = gamma_c;
+}
+
+/* Constitutive model of sigma_struc (ORC_NLM, ORC_INLM, ORC_WM); set before the first step. */
+int orc_set_model(orc_channel* ch, int kind) {
+    if (kind != ORC_NLM && kind != ORC_INLM && kind != ORC_WM) return -1;
+    if (ch->t != 0) return -1;
+    ch->m.kind = kind;
+    return 0;
 }
 
 int64_t orc_time(const orc_channel* ch) { return ch->t; }
@@ -627,7 +729,8 @@ static void channel_step(orc_channel* ch) {
     for (int64_t k = 0; k < N; ++k) {
         double kap[9];
         for (int i = 0; i < d * d; ++i) kap[i] = ch->kappa[k * 9 + i];
-        hist_step(&ch->hist[k], ch->t, kap, &ch->m, ch->list, ch->ages, ch->wts, &ch->sigma[k * 6]);
+        if (ch->m.kind == ORC_INLM) inlm_stress(d, kap, &ch->m, &ch->sigma[k * 6]);
+        else hist_step(&ch->hist[k], ch->t, kap, &ch->m, ch->list, ch->ages, ch->wts, &ch->sigma[k * 6]);
     }
     /* 5-7. trace split, density source, collision with forcing, streaming */
     memset(ch->n_next, 0, sizeof(double) * (size_t)N * Q);

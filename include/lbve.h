@@ -52,6 +52,18 @@ extern "C" {
 #define LBVE_TRACE_FULL 0 /* Eq. (bodyforce) with the density source d_t(delta rho) as written */
 #define LBVE_TRACE_NONE 1 /* both d_t(delta rho) terms dropped, rho = sum n (channel simplification) */
 
+#define LBVE_MODEL_NLM  0 /* integral nonlinear Maxwell model: Eq. (gitt) with the modulus of Eq. (nlmax) */
+#define LBVE_MODEL_INLM 1 /* instantaneous nlM, Eq. (inlM) of Sec. IV read as a stress / strain-rate law at
+                             time t: sigma_struc(t) = G_inf sum_{n>=1} tau_M^n d^(n)[kappa(t)],
+                             tau_M = (1/tau + gammadot(t)/gamma_c)^-1.  No history is kept (hist_C, hist_B
+                             are checked but unused).  The series is summed until two consecutive terms
+                             are below 1e-18 of the sum; where that takes more than 1000 terms or the
+                             terms overflow (no steady state, e.g. strong extension) sigma_struc is NaN
+                             and lbve_fields reports LBVE_ENONFINITE */
+#define LBVE_MODEL_WM   2 /* White-Metzner form named in Sec. II: the second exponential of Eq. (nlmax)
+                             takes the strain accumulated between t' and t, sum_{s=t'}^{t-1} gammadot(s),
+                             in place of (t - t') gammadot(t').  History storage LBVE_F32 or LBVE_F64 */
+
 #define LBVE_FIELD_RHO   1u  /* [N]        hydrodynamic density of Eq. (hydrofields) */
 #define LBVE_FIELD_U     2u  /* [d][N]     velocity u = (sum c n + f/2)/rho */
 #define LBVE_FIELD_SIGMA 4u  /* [nsig][N]  sigma_struc of Eq. (gitt) */
@@ -75,6 +87,10 @@ typedef struct {
     int32_t pop_precision;    /* LBVE_F32 | LBVE_F64: storage and collision arithmetic of the populations
                                  (independent of hist_storage; node fields are always double) */
     int32_t trace_coupling;   /* LBVE_TRACE_FULL | LBVE_TRACE_NONE */
+    int32_t model;            /* LBVE_MODEL_NLM (0) | LBVE_MODEL_INLM | LBVE_MODEL_WM; the same for every
+                                 channel of a batch.  LBVE_MODEL_WM with LBVE_S16, and differentiation
+                                 (lbve_create_tangent / lbve_create_adjoint) of any model but
+                                 LBVE_MODEL_NLM, return LBVE_ENOSUPPORT */
 } lbve_channel_desc;
 
 typedef struct lbve lbve_t;   /* opaque; owns every device buffer of one channel or of a batch */

@@ -53,6 +53,7 @@ struct lbve {
     int pop_dbl;               // 1: populations stored in double
     int hist_dbl;              // 1: history stored (and advanced) in double
     int hist_s16;              // 1: 16-bit block-scaled history in a per-node frame
+    int model = LBVE_MODEL_NLM;  // constitutive model (LBVE_MODEL_*)
     size_t pesz, hesz;         // element sizes of populations and history (partial sums)
     std::vector<Chan> chan_host;
     Chan* chan_dev = nullptr;  // [nchan] per-channel geometry and parameters
@@ -71,6 +72,8 @@ struct lbve {
     void* Qe = nullptr;        // 16-bit history: exponents of Q - 1 [L][Npad]
     void* Ke = nullptr;        //                 exponents of kappa [L][Npad]
     void* Rm = nullptr;        //                 frame R - 1 [DD][Npad] (float)
+    void* gam_node = nullptr;  // White-Metzner form: accumulated strain Gamma(t) per node [Npad] (double)
+    void* gam_pt = nullptr;    //                     Gamma(t') of every point [L][Npad] (double)
     int S = 1;                 // slot chunks of the sweep (autotuned at create)
     int sweep_grid = 0;        // persistent CTAs of the sweep
     long long* t_dev = nullptr;
@@ -100,7 +103,7 @@ namespace {
 void free_all(lbve* h) {
     void* ptrs[] = {h->pops[0], h->pops[1], h->u_raw, h->u, h->rho, h->sigma, h->kappa, h->tr_prev,
                     h->X, h->K, h->part, h->t_dev, h->red, h->stage, h->flag, h->chan_dev, h->chan_of,
-                    h->Qe, h->Ke, h->Rm};
+                    h->Qe, h->Ke, h->Rm, h->gam_node, h->gam_pt};
     for (void* p : ptrs)
         if (p) cudaFree(p);
     for (cudaEvent_t e : h->ev_pool) cudaEventDestroy(e);
@@ -187,14 +190,17 @@ int check_desc(const lbve_channel_desc* d) {
     if (d->hist_storage != LBVE_F32 && d->hist_storage != LBVE_F64 && d->hist_storage != LBVE_BF16 &&
         d->hist_storage != LBVE_S16)
         return LBVE_EINVAL;
+    if (d->model != LBVE_MODEL_NLM && d->model != LBVE_MODEL_INLM && d->model != LBVE_MODEL_WM) return LBVE_EINVAL;
     if (d->hist_storage == LBVE_BF16) return LBVE_ENOSUPPORT;
+    if (d->model == LBVE_MODEL_WM && d->hist_storage == LBVE_S16) return LBVE_ENOSUPPORT;
     return LBVE_OK;
 }
 
 // Settings every channel of a batch shares: the lattice, the history grid, the precisions, rho0.
 bool same_batch_settings(const lbve_channel_desc& a, const lbve_channel_desc& b) {
     return a.lattice == b.lattice && a.hist_C == b.hist_C && a.hist_B == b.hist_B &&
-           a.hist_storage == b.hist_storage && a.pop_precision == b.pop_precision && a.rho0 == b.rho0;
+           a.hist_storage == b.hist_storage && a.pop_precision == b.pop_precision && a.rho0 == b.rho0 &&
+           a.model == b.model;
 }
 
 // Values per lane of the sweep (one 16-byte access): 4 floats or 2 doubles; 3D halves it (registers).
@@ -211,7 +217,12 @@ int launch_sweep(lbve* h, cudaStream_t s) {
     a.B = h->d.hist_B;
     a.C = h->d.hist_C;
     a.S = h->S;
-    k_sweep<D, R, VN><<<h->sweep_grid, 256, sweep_smem_bytes(h->L), s>>>(a, geom_of(h));
+    a.gam_node = (const double*)h->gam_node;
+    a.gam_pt = (const double*)h->gam_pt;
+    if (h->model == LBVE_MODEL_WM)
+        k_sweep<D, R, VN, true><<<h->sweep_grid, 256, sweep_smem_bytes(h->L), s>>>(a, geom_of(h));
+    else
+        k_sweep<D, R, VN, false><<<h->sweep_grid, 256, sweep_smem_bytes(h->L), s>>>(a, geom_of(h));
     LBVE_CUDA(cudaGetLastError());
     return LBVE_OK;
 }
@@ -242,9 +253,11 @@ int launch_sweep_s16(lbve* h, cudaStream_t s) {
     return LBVE_OK;
 }
 
-// History storage kinds (template argument HK): 0 float, 1 double, 2 16-bit block-scaled.
+// History storage kinds (template argument HK): 0 float, 1 double, 2 16-bit block-scaled, 3 none (the
+// instantaneous model).  Float and double also carry the White-Metzner form (chosen at run time).
 template <int D, int HK>
 int launch_sweep_any(lbve* h, cudaStream_t s) {
+    if (HK == 3) return LBVE_OK;
     if (HK == 2) return launch_sweep_s16<D>(h, s);
     if (HK == 1) return launch_sweep<D, double>(h, s);
     return launch_sweep<D, float>(h, s);
@@ -253,15 +266,15 @@ int launch_sweep_any(lbve* h, cudaStream_t s) {
 template <int D, int HK> struct SweepKernel;
 template <int D> struct SweepKernel<D, 0> {
     static constexpr int VN = sweep_vn<D, float>();
-    static const void* fn() { return (const void*)k_sweep<D, float, VN>; }
+    static const void* fn(bool wm) { return wm ? (const void*)k_sweep<D, float, VN, true> : (const void*)k_sweep<D, float, VN, false>; }
 };
 template <int D> struct SweepKernel<D, 1> {
     static constexpr int VN = sweep_vn<D, double>();
-    static const void* fn() { return (const void*)k_sweep<D, double, VN>; }
+    static const void* fn(bool wm) { return wm ? (const void*)k_sweep<D, double, VN, true> : (const void*)k_sweep<D, double, VN, false>; }
 };
 template <int D> struct SweepKernel<D, 2> {
     static constexpr int VN = sweep_vn_s16<D>();
-    static const void* fn() { return (const void*)k_sweep_s16<D, VN>; }
+    static const void* fn(bool) { return (const void*)k_sweep_s16<D, VN>; }
 };
 
 // Autotuner of the sweep: candidate slot-chunk counts S (tasks per resident warp from about 2 to 32),
@@ -271,7 +284,7 @@ template <int D> struct SweepKernel<D, 2> {
 template <int D, int HK>
 int sweep_autotune(lbve* h) {
     constexpr int VN = SweepKernel<D, HK>::VN;
-    const void* fn = SweepKernel<D, HK>::fn();
+    const void* fn = SweepKernel<D, HK>::fn(h->model == LBVE_MODEL_WM);
     const size_t smem = sweep_smem_bytes(h->L);
     if (smem > 48 * 1024)
         LBVE_CUDA(cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
@@ -336,13 +349,16 @@ CommitArgs<R> commit_args(lbve* h) {
     c.B = h->d.hist_B;
     c.C = h->d.hist_C;
     c.S = h->S;
+    c.gam_node = (double*)h->gam_node;
+    c.gam_pt = (double*)h->gam_pt;
     return c;
 }
 
 __global__ void k_advance_t(long long* t) { *t += 1; }
 
 // One hybrid step: moments -> history sweep -> commit + collide + stream.  pops[cur] -> pops[cur ^ 1].
-// P: population storage type, HK: history kind (0 float, 1 double, 2 16-bit), T: collision arithmetic.
+// P: population storage type, HK: history kind (0 float, 1 double, 2 16-bit, 3 none: the instantaneous
+// model, whose stress the collide kernel computes itself), T: collision arithmetic.
 template <int Q, typename P, int HK, typename T>
 int one_step(lbve* h, int cur, cudaStream_t s) {
     constexpr int D = Lattice<Q>::D;
@@ -355,9 +371,11 @@ int one_step(lbve* h, int cur, cudaStream_t s) {
     k_moments<Q, P><<<grid, 256, 0, s>>>(din, (double*)h->u_raw, g, h->t_dev);
     LBVE_CUDA(cudaGetLastError());
     if ((rc = prof_mark(h, s, KIND_MOMENTS, false))) return rc;
-    if ((rc = prof_mark(h, s, KIND_HISTORY, true))) return rc;
-    if ((rc = launch_sweep_any<D, HK>(h, s))) return rc;
-    if ((rc = prof_mark(h, s, KIND_HISTORY, false))) return rc;
+    if (HK != 3) {
+        if ((rc = prof_mark(h, s, KIND_HISTORY, true))) return rc;
+        if ((rc = launch_sweep_any<D, HK>(h, s))) return rc;
+        if ((rc = prof_mark(h, s, KIND_HISTORY, false))) return rc;
+    }
     CollArgs<P> c;
     c.dn_in = din;
     c.dn_out = dout;
@@ -369,7 +387,8 @@ int one_step(lbve* h, int cur, cudaStream_t s) {
     c.u = (double*)h->u;
     c.t_dev = h->t_dev;
     if ((rc = prof_mark(h, s, KIND_COLLIDE, true))) return rc;
-    if (HK == 2) k_collide_stream<Q, P, T, CommitS16><<<grid, 256, 0, s>>>(c, commit_s16(h), g);
+    if (HK == 3) k_collide_stream<Q, P, T, Instant<T>><<<grid, 256, 0, s>>>(c, Instant<T>{1, 4}, g);
+    else if (HK == 2) k_collide_stream<Q, P, T, CommitS16><<<grid, 256, 0, s>>>(c, commit_s16(h), g);
     else if (HK == 1) k_collide_stream<Q, P, T, CommitArgs<double>><<<grid, 256, 0, s>>>(c, commit_args<double>(h), g);
     else k_collide_stream<Q, P, T, CommitArgs<float>><<<grid, 256, 0, s>>>(c, commit_args<float>(h), g);
     LBVE_CUDA(cudaGetLastError());
@@ -555,7 +574,8 @@ int create_impl(const lbve_channel_desc* descs, int32_t n, const double* rho_ini
     h->Q = desc->lattice;
     h->NS = h->D == 2 ? 3 : 6;
     h->N = (int)Ntot;
-    h->L = desc->hist_C * desc->hist_B;
+    h->model = desc->model;
+    h->L = desc->model == LBVE_MODEL_INLM ? 0 : desc->hist_C * desc->hist_B;   // the instantaneous model keeps no history
     h->Npad = ((long long)h->N + 127) / 128 * 128;
     h->pop_dbl = desc->pop_precision == LBVE_F64;
     h->hist_dbl = desc->hist_storage == LBVE_F64;
@@ -584,8 +604,8 @@ int create_impl(const lbve_channel_desc* descs, int32_t n, const double* rho_ini
         (rc = alloc(h, &h->u_raw, fe * h->D * Np)) || (rc = alloc(h, &h->u, fe * h->D * Np)) ||
         (rc = alloc(h, &h->rho, fe * Np)) || (rc = alloc(h, &h->sigma, fe * h->NS * Np)) ||
         (rc = alloc(h, &h->kappa, fe * DD * Np)) || (rc = alloc(h, &h->tr_prev, fe * Np)) ||
-        (rc = alloc(h, &h->X, hist_elem * (size_t)h->L * DD * Np)) ||
-        (rc = alloc(h, &h->K, hist_elem * (size_t)h->L * DD * Np)) ||
+        (h->L > 0 && (rc = alloc(h, &h->X, hist_elem * (size_t)h->L * DD * Np))) ||
+        (h->L > 0 && (rc = alloc(h, &h->K, hist_elem * (size_t)h->L * DD * Np))) ||
         (rc = alloc(h, (void**)&h->t_dev, sizeof(long long))) || (rc = alloc(h, (void**)&h->red, 2 * sizeof(double))) ||
         (rc = alloc(h, (void**)&h->flag, sizeof(int))) ||
         (rc = alloc(h, (void**)&h->chan_dev, sizeof(Chan) * n)))
@@ -604,18 +624,23 @@ int create_impl(const lbve_channel_desc* descs, int32_t n, const double* rho_ini
         cudaError_t e = cudaMemcpy(h->chan_of, co.data(), sizeof(int) * Np, cudaMemcpyHostToDevice);
         if (e != cudaSuccess) return fail(cuda_fail(e, "cudaMemcpy"));
     }
-    if (h->hist_s16 &&
+    if (h->hist_s16 && h->L > 0 &&
         ((rc = alloc(h, &h->Qe, (size_t)h->L * Np)) || (rc = alloc(h, &h->Ke, (size_t)h->L * Np)) ||
          (rc = alloc(h, &h->Rm, sizeof(float) * DD * Np))))
         return fail(rc);
+    if (h->model == LBVE_MODEL_WM &&
+        ((rc = alloc(h, &h->gam_node, sizeof(double) * Np)) ||
+         (rc = alloc(h, &h->gam_pt, sizeof(double) * (size_t)h->L * Np))))
+        return fail(rc);
     // zero every buffer: rest state, empty history (E = 1 <=> X = 0 or Q = 1, kappa = 0, frame 1)
+    // (White-Metzner: Gamma = 0 for the node and for every rest point -- no strain before t = 0)
     void* zero_bufs[] = {h->pops[0], h->pops[1], h->u_raw, h->u, h->sigma, h->kappa, h->tr_prev, h->X, h->K, h->flag,
-                         h->Qe, h->Ke, h->Rm};
+                         h->Qe, h->Ke, h->Rm, h->gam_node, h->gam_pt};
     size_t zero_sizes[] = {h->pesz * h->Q * Np, h->pesz * h->Q * Np, fe * h->D * Np, fe * h->D * Np,
                            fe * h->NS * Np, fe * DD * Np, fe * Np, hist_elem * (size_t)h->L * DD * Np,
                            hist_elem * (size_t)h->L * DD * Np, sizeof(int), (size_t)h->L * Np, (size_t)h->L * Np,
-                           sizeof(float) * DD * Np};
-    for (int i = 0; i < 13; ++i) {
+                           sizeof(float) * DD * Np, sizeof(double) * Np, sizeof(double) * (size_t)h->L * Np};
+    for (int i = 0; i < 15; ++i) {
         if (!zero_bufs[i]) continue;
         cudaError_t e = cudaMemset(zero_bufs[i], 0, zero_sizes[i]);
         if (e != cudaSuccess) return fail(cuda_fail(e, "cudaMemset"));
@@ -625,7 +650,8 @@ int create_impl(const lbve_channel_desc* descs, int32_t n, const double* rho_ini
         cudaError_t e = cudaMemcpy(h->t_dev, &minus_one, sizeof minus_one, cudaMemcpyHostToDevice);
         if (e != cudaSuccess) return fail(cuda_fail(e, "cudaMemcpy"));
     }
-    if (h->D == 2) rc = h->hist_s16 ? sweep_autotune<2, 2>(h) : h->hist_dbl ? sweep_autotune<2, 1>(h) : sweep_autotune<2, 0>(h);
+    if (h->L == 0) rc = LBVE_OK;   // no history: no sweep
+    else if (h->D == 2) rc = h->hist_s16 ? sweep_autotune<2, 2>(h) : h->hist_dbl ? sweep_autotune<2, 1>(h) : sweep_autotune<2, 0>(h);
     else rc = h->hist_s16 ? sweep_autotune<3, 2>(h) : h->hist_dbl ? sweep_autotune<3, 1>(h) : sweep_autotune<3, 0>(h);
     if (rc) return fail(rc);
     rc = h->pop_dbl ? init_state<double>(h, rho_init) : init_state<float>(h, rho_init);
@@ -717,6 +743,7 @@ int create_tangent(const lbve_channel_desc* desc, const double* rho_init, lbve_t
     *out = nullptr;
     int rc = check_desc(desc);
     if (rc) return rc;
+    if (desc->model != LBVE_MODEL_NLM) return LBVE_ENOSUPPORT;
     const long long Ntot = (long long)desc->nx * desc->ny * desc->nz;
     if (rho_init)
         for (long long i = 0; i < Ntot; ++i)
@@ -878,25 +905,29 @@ int lbve_step(lbve_t* h, int64_t n_steps, void* stream) {
     if (!h || n_steps < 0) return LBVE_EINVAL;
     cudaStream_t s = (cudaStream_t)stream;
     if (h->tangent) return h->Q == 9 ? tangent_step<9>(h, n_steps, s) : tangent_step<19>(h, n_steps, s);
-    const int hk = h->hist_s16 ? 2 : (h->hist_dbl ? 1 : 0);
-    const int combo = (h->pop_dbl ? 3 : 0) + hk;
+    const int hk = h->model == LBVE_MODEL_INLM ? 3 : h->hist_s16 ? 2 : (h->hist_dbl ? 1 : 0);
+    const int combo = (h->pop_dbl ? 4 : 0) + hk;
     if (h->Q == 9) {
         switch (combo) {
             case 0: return step_impl<9, float, 0, float>(h, n_steps, s);
             case 1: return step_impl<9, float, 1, float>(h, n_steps, s);
             case 2: return step_impl<9, float, 2, float>(h, n_steps, s);
-            case 3: return step_impl<9, double, 0, double>(h, n_steps, s);
-            case 4: return step_impl<9, double, 1, double>(h, n_steps, s);
-            default: return step_impl<9, double, 2, double>(h, n_steps, s);
+            case 3: return step_impl<9, float, 3, float>(h, n_steps, s);
+            case 4: return step_impl<9, double, 0, double>(h, n_steps, s);
+            case 5: return step_impl<9, double, 1, double>(h, n_steps, s);
+            case 6: return step_impl<9, double, 2, double>(h, n_steps, s);
+            default: return step_impl<9, double, 3, double>(h, n_steps, s);
         }
     }
     switch (combo) {
         case 0: return step_impl<19, float, 0, float>(h, n_steps, s);
         case 1: return step_impl<19, float, 1, float>(h, n_steps, s);
         case 2: return step_impl<19, float, 2, float>(h, n_steps, s);
-        case 3: return step_impl<19, double, 0, double>(h, n_steps, s);
-        case 4: return step_impl<19, double, 1, double>(h, n_steps, s);
-        default: return step_impl<19, double, 2, double>(h, n_steps, s);
+        case 3: return step_impl<19, float, 3, float>(h, n_steps, s);
+        case 4: return step_impl<19, double, 0, double>(h, n_steps, s);
+        case 5: return step_impl<19, double, 1, double>(h, n_steps, s);
+        case 6: return step_impl<19, double, 2, double>(h, n_steps, s);
+        default: return step_impl<19, double, 3, double>(h, n_steps, s);
     }
 }
 
@@ -956,7 +987,15 @@ int lbve_history_apply(lbve_t* h, const double* kappa_dev, double* sigma_dev, vo
     int rc;
     const Geom g = geom_of(h);
     const int grid = (h->N + 255) / 256;
-    if (h->hist_s16) {
+    if (h->model == LBVE_MODEL_INLM) {   // no history: the stress of Eq. (inlM) in the collision's arithmetic
+        if (h->D == 2) {
+            if (h->pop_dbl) k_commit<2, Instant<double>><<<grid, 256, 0, s>>>(Instant<double>{1, 4}, kappa_dev, (double*)h->sigma, (double*)h->kappa, sigma_dev, h->t_dev, g);
+            else k_commit<2, Instant<float>><<<grid, 256, 0, s>>>(Instant<float>{1, 4}, kappa_dev, (double*)h->sigma, (double*)h->kappa, sigma_dev, h->t_dev, g);
+        } else {
+            if (h->pop_dbl) k_commit<3, Instant<double>><<<grid, 256, 0, s>>>(Instant<double>{1, 4}, kappa_dev, (double*)h->sigma, (double*)h->kappa, sigma_dev, h->t_dev, g);
+            else k_commit<3, Instant<float>><<<grid, 256, 0, s>>>(Instant<float>{1, 4}, kappa_dev, (double*)h->sigma, (double*)h->kappa, sigma_dev, h->t_dev, g);
+        }
+    } else if (h->hist_s16) {
         if (h->D == 2) {
             if ((rc = launch_sweep_s16<2>(h, s))) return rc;
             k_commit<2, CommitS16><<<grid, 256, 0, s>>>(commit_s16(h), kappa_dev, (double*)h->sigma, (double*)h->kappa,
@@ -1041,8 +1080,15 @@ std::vector<StateBuf> state_buffers(lbve* h) {
         v.push_back({h->Ke, (size_t)h->L * Np});
         v.push_back({h->Rm, sizeof(float) * DD * Np});
     }
+    if (h->gam_node) {
+        v.push_back({h->gam_node, sizeof(double) * Np});
+        v.push_back({h->gam_pt, sizeof(double) * (size_t)h->L * Np});
+    }
     if (!h->tangent) v.push_back({h->chan_dev, sizeof(Chan) * h->nchan});
-    return v;
+    std::vector<StateBuf> nz;   // buffers a model does not use (no history) have no bytes
+    for (const StateBuf& b : v)
+        if (b.p && b.bytes) nz.push_back(b);
+    return nz;
 }
 constexpr uint64_t kCkptMagic = 0x4c42564543503031ull;   // "LBVECP01"
 struct CkptHeader { uint64_t magic, total, nbuf, config; int64_t t_host; };
@@ -1056,7 +1102,7 @@ uint64_t config_fingerprint(const lbve* h) {
     mix(h->tangent); mix(h->nchan); mix(h->N); mix(h->L);
     for (const lbve_channel_desc& d : h->descs) {
         mix(d.lattice); mix(d.nx); mix(d.ny); mix(d.nz); mix(d.wall_z); mix(d.hist_C); mix(d.hist_B);
-        mix(d.hist_storage); mix(d.pop_precision); mix(d.trace_coupling);
+        mix(d.hist_storage); mix(d.pop_precision); mix(d.trace_coupling); mix(d.model);
     }
     return x;
 }
@@ -1282,6 +1328,7 @@ int lbve_create_adjoint(const lbve_channel_desc* desc, const double* rho_init, i
                         lbve_t** out) {
     if (!desc || !out || checkpoint_every < 1) return LBVE_EINVAL;
     if (desc->pop_precision != LBVE_F64 || desc->hist_storage != LBVE_F64) return LBVE_ENOSUPPORT;
+    if (desc->model != LBVE_MODEL_NLM) return LBVE_ENOSUPPORT;
     int rc = create_impl(desc, 1, rho_init, out);
     if (rc) return rc;
     (*out)->rec_K = checkpoint_every;

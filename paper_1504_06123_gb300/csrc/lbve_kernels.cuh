@@ -219,9 +219,11 @@ template <> struct FastMath<float> {
     __device__ static __forceinline__ float sqrt_pos(float x) { return x > 0.0f ? x * rsqrtf(x) : 0.0f; }
 };
 
-template <int D, typename real>
+// WM = true: the White-Metzner form (Sec. II): the second exponential of Eq. (nlmax) takes the strain
+// accumulated since the point was created, `strain`, instead of age * gammadot(point).
+template <int D, typename real, bool WM = false>
 __device__ __forceinline__ void point_integrand(const real* X, const real* kap, real age, real w,
-                                                real inv_tau, real inv_gc, real* acc) {
+                                                real inv_tau, real inv_gc, real* acc, real strain = real(0)) {
     constexpr int DD = D * D;
     // M = E kap E^T with E = 1 + X
     real EK[DD];
@@ -244,17 +246,22 @@ __device__ __forceinline__ void point_integrand(const real* X, const real* kap, 
             for (int k = 0; k < D; ++k) s += EK[r * D + k] * X[c * D + k];
             M[r * D + c] = s;
         }
-    // local shear rate of the point: gammadot^2 = (1/2) tr D^2, D = kap + kap^T
-    real trD2 = 0;
+    real gw;
+    if (WM) {
+        gw = w * FastMath<real>::exp_neg(age * inv_tau + strain * inv_gc);
+    } else {
+        // local shear rate of the point: gammadot^2 = (1/2) tr D^2, D = kap + kap^T
+        real trD2 = 0;
 #pragma unroll
-    for (int r = 0; r < D; ++r)
+        for (int r = 0; r < D; ++r)
 #pragma unroll
-        for (int c = 0; c < D; ++c) {
-            const real Drc = kap[r * D + c] + kap[c * D + r];
-            trD2 += Drc * Drc;
-        }
-    const real gd = FastMath<real>::sqrt_pos(real(0.5) * trD2);
-    const real gw = w * FastMath<real>::exp_neg(age * (inv_tau + gd * inv_gc));
+            for (int c = 0; c < D; ++c) {
+                const real Drc = kap[r * D + c] + kap[c * D + r];
+                trD2 += Drc * Drc;
+            }
+        const real gd = FastMath<real>::sqrt_pos(real(0.5) * trD2);
+        gw = w * FastMath<real>::exp_neg(age * (inv_tau + gd * inv_gc));
+    }
     if (D == 2) {
         acc[0] += gw * (M[0] + M[0]);
         acc[1] += gw * (M[3] + M[3]);
@@ -271,9 +278,9 @@ __device__ __forceinline__ void point_integrand(const real* X, const real* kap, 
 
 // One history point of the in-place storage: advance X <- X + A + A X (E <- exp(kappa(t-1)) E), then
 // its integrand.
-template <int D, typename real>
+template <int D, typename real, bool WM = false>
 __device__ __forceinline__ void point_update(real* X, const real* A, const real* kap, real age, real w,
-                                             real inv_tau, real inv_gc, real* acc) {
+                                             real inv_tau, real inv_gc, real* acc, real strain = real(0)) {
     constexpr int DD = D * D;
     real Xn[DD];
 #pragma unroll
@@ -287,7 +294,7 @@ __device__ __forceinline__ void point_update(real* X, const real* A, const real*
         }
 #pragma unroll
     for (int i = 0; i < DD; ++i) X[i] = Xn[i];
-    point_integrand<D>(X, kap, age, w, inv_tau, inv_gc, acc);
+    point_integrand<D, real, WM>(X, kap, age, w, inv_tau, inv_gc, acc, strain);
 }
 
 // ------------------------------------------------------------------------------------------------
@@ -303,6 +310,10 @@ template <typename R> struct SweepArgs {
     R* __restrict__ part;             // [S][NS][Npad]  partial trapezoid sums per slot chunk (scratch)
     const long long* t_dev;           // step index t
     int B, C, S;                      // grid shape; S slot chunks
+    // White-Metzner form only: accumulated strain Gamma(t) = sum_{s<t} gammadot(s) of every node and the
+    // value Gamma(t') each point was created with; a point's strain is their difference
+    const double* __restrict__ gam_node;   // [Npad]
+    const double* __restrict__ gam_pt;     // [L][Npad]
 };
 
 // Shared memory of the sweep: per slot age, weight, partner (L entries each) + the per-block state.
@@ -315,7 +326,7 @@ __host__ __device__ inline size_t sweep_smem_bytes(int L) { return (size_t)L * 1
 // order, so the result does not depend on scheduling.  All points are advanced in place:
 // X <- X + A + A X with A = exp(kappa(t-1)) - 1 (Eq. eeval, newest factor on the left); the older half of
 // a merge uses the average of the two kappa (Sec. III), the newer half is skipped.
-template <int D, typename R, int VN>
+template <int D, typename R, int VN, bool WM = false>
 __global__ void __launch_bounds__(256, 2) k_sweep(SweepArgs<R> a, Geom g) {
     constexpr int DD = D * D;
     constexpr int NS = D == 2 ? 3 : 6;
@@ -379,6 +390,9 @@ __global__ void __launch_bounds__(256, 2) k_sweep(SweepArgs<R> a, Geom g) {
         for (int j = 0; j < VN; ++j)
 #pragma unroll
             for (int i = 0; i < NS; ++i) acc[j][i] = 0;
+        using VD = Vec<double, VN>;
+        VD gam_now;
+        if (WM) gam_now = *reinterpret_cast<const VD*>(a.gam_node + n0);
 
         const int l0 = chunk * chunk_len;
         const int l1 = min(L, l0 + chunk_len);
@@ -406,8 +420,15 @@ __global__ void __launch_bounds__(256, 2) k_sweep(SweepArgs<R> a, Geom g) {
                 }
             }
             const R age = (R)s_age[l], wr = (R)w;
+            R strain[VN];
+            if (WM) {   // a merged point keeps the older half's creation strain (its slot l)
+                const VD gp = *reinterpret_cast<const VD*>(a.gam_pt + (long long)l * Np + n0);
 #pragma unroll
-            for (int j = 0; j < VN; ++j) point_update<D>(X[j], A[j], kap[j], age, wr, inv_tau[j], inv_gc[j], acc[j]);
+                for (int j = 0; j < VN; ++j) strain[j] = (R)(gam_now.v[j] - gp.v[j]);
+            }
+#pragma unroll
+            for (int j = 0; j < VN; ++j)
+                point_update<D, R, WM>(X[j], A[j], kap[j], age, wr, inv_tau[j], inv_gc[j], acc[j], WM ? strain[j] : R(0));
 #pragma unroll
             for (int c = 0; c < DD; ++c) {
                 V xv;
@@ -436,7 +457,23 @@ template <typename R> struct CommitArgs {
     R* __restrict__ K;
     const R* __restrict__ part;       // [S][NS][Npad]
     int B, C, S;
+    double* __restrict__ gam_node;    // White-Metzner form: Gamma(t) per node [Npad] (nullptr: nlM)
+    double* __restrict__ gam_pt;      //                     Gamma(t') per point [L][Npad]
 };
+
+// Local shear rate of Sec. II, gammadot = sqrt((1/2) tr D^2), D = kappa + kappa^T (double).
+template <int D>
+__device__ __forceinline__ double shear_rate_d(const double* k) {
+    double trD2 = 0;
+#pragma unroll
+    for (int r = 0; r < D; ++r)
+#pragma unroll
+        for (int c = 0; c < D; ++c) {
+            const double v = k[r * D + c] + k[c * D + r];
+            trD2 += v * v;
+        }
+    return sqrt(0.5 * trD2);
+}
 
 template <int D, typename R>
 __device__ __forceinline__ void hist_commit(const CommitArgs<R>& a, const BlockStep* s_bs, long long Np, int n,
@@ -480,6 +517,7 @@ __device__ __forceinline__ void hist_commit(const CommitArgs<R>& a, const BlockS
             a.X[(dst * DD + c) * Np + n] = a.X[(src1 * DD + c) * Np + n];
             a.K[(dst * DD + c) * Np + n] = R(0.5) * (a.K[(src1 * DD + c) * Np + n] + a.K[(src2 * DD + c) * Np + n]);
         }
+        if (a.gam_pt) a.gam_pt[dst * Np + n] = a.gam_pt[src1 * Np + n];   // older time, older strain origin
     }
     const long long dst = (long long)(a.B - 1) * a.C + s_bs[a.B - 1].head_new;
 #pragma unroll
@@ -487,15 +525,95 @@ __device__ __forceinline__ void hist_commit(const CommitArgs<R>& a, const BlockS
         a.X[(dst * DD + c) * Np + n] = R(0);
         a.K[(dst * DD + c) * Np + n] = kt[c];
     }
+    if (a.gam_pt) {   // the new point starts at Gamma(t); the node moves on by the strain of [t, t+1]
+        const double gnow = a.gam_node[n];
+        a.gam_pt[dst * Np + n] = gnow;
+        a.gam_node[n] = gnow + shear_rate_d<D>(ktd);
+    }
 }
 
 // Uniform entry for every history storage: kprev = kappa(t-1) of the node (the node kappa field before
 // this step overwrites it), used by storages that keep a per-node frame.
 template <int D, typename R>
 __device__ __forceinline__ void hist_commit_any(const CommitArgs<R>& a, const BlockStep* s_bs, long long Np, int n,
-                                                const double* /*kprev*/, const double* ktd, double G_inf,
+                                                const double* /*kprev*/, const double* ktd, const Chan& p,
                                                 double* sig, long long /*t*/) {
-    hist_commit<D, R>(a, s_bs, Np, n, ktd, G_inf, sig);
+    hist_commit<D, R>(a, s_bs, Np, n, ktd, p.G_inf, sig);
+}
+
+// ------------------------------------------------------------------------------------------------
+// Instantaneous nlM, Eq. (inlM): no history.  sigma_struc(t) = G_inf sum_{n>=1} tau_M^n d^(n)[kappa(t)],
+// tau_M = (1/tau + gammadot(t)/gamma_c)^-1.  The d^(n) are the Taylor coefficients of
+// exp(kappa s) exp(kappa^T s), so d^(1) = D and d^(n+1) = kappa d^(n) + d^(n) kappa^T: with A = tau_M kappa
+// the terms T_n = tau_M^n d^(n) follow T_1 = tau_M D, T_{n+1} = A T_n + T_n A^T, summed in the arithmetic
+// type T until two consecutive terms are below 1e-18 of the partial sum (a nilpotent kappa, simple shear,
+// ends the series at n = 2).  NaN when the series has not converged after kInlmTerms terms or overflows:
+// Eq. (inlM) then has no sum (no steady state).  The stopping rule is the same in both arithmetic types,
+// so FP32 and FP64 agree on where the sum exists.
+// ------------------------------------------------------------------------------------------------
+template <typename T> struct Instant { int B, C; };   // B = 1, C = 4: the shared schedule code is unused
+constexpr int kInlmTerms = 1000;
+constexpr double kInlmEps = 1e-18;
+
+template <int D, typename T>
+__device__ __forceinline__ void inlm_stress(const double* ktd, const Chan& p, double* sig) {
+    constexpr int DD = D * D;
+    constexpr int NS = D == 2 ? 3 : 6;
+    const double tMd = 1.0 / (p.inv_tau + shear_rate_d<D>(ktd) * p.inv_gc);
+    T A[DD], Tn[DD], Z[DD];
+#pragma unroll
+    for (int r = 0; r < D; ++r)
+#pragma unroll
+        for (int c = 0; c < D; ++c) {
+            A[r * D + c] = (T)(tMd * ktd[r * D + c]);
+            Tn[r * D + c] = (T)(tMd * (ktd[r * D + c] + ktd[c * D + r]));
+            Z[r * D + c] = Tn[r * D + c];
+        }
+    bool ok = false;
+    int quiet = 0;
+    for (int n = 2; n <= kInlmTerms; ++n) {
+        T P[DD];   // A T_n
+#pragma unroll
+        for (int r = 0; r < D; ++r)
+#pragma unroll
+            for (int c = 0; c < D; ++c) {
+                T s = 0;
+#pragma unroll
+                for (int k = 0; k < D; ++k) s += A[r * D + k] * Tn[k * D + c];
+                P[r * D + c] = s;
+            }
+        T tn = 0, zn = 0;
+#pragma unroll
+        for (int r = 0; r < D; ++r)
+#pragma unroll
+            for (int c = 0; c < D; ++c) {
+                const T v = P[r * D + c] + P[c * D + r];   // T_{n+1} = A T_n + (A T_n)^T (T_n symmetric)
+                Tn[r * D + c] = v;
+                Z[r * D + c] += v;
+                tn = fmax(tn, fabs(v));
+                zn = fmax(zn, fabs(Z[r * D + c]));
+            }
+        if (!isfinite(tn) || !isfinite(zn)) break;   // diverged
+        quiet = (tn <= T(kInlmEps) * zn) ? quiet + 1 : 0;
+        if (quiet >= 2) { ok = true; break; }
+    }
+    const double nan = __longlong_as_double(0x7ff8000000000000ll);
+    if (D == 2) {
+        sig[0] = ok ? p.G_inf * (double)Z[0] : nan;
+        sig[1] = ok ? p.G_inf * (double)Z[3] : nan;
+        sig[2] = ok ? p.G_inf * (double)Z[1] : nan;
+    } else {
+        const int idx[6] = {0, 4, 8, 1, 2, 5};
+#pragma unroll
+        for (int i = 0; i < NS; ++i) sig[i] = ok ? p.G_inf * (double)Z[idx[i]] : nan;
+    }
+}
+
+template <int D, typename T>
+__device__ __forceinline__ void hist_commit_any(const Instant<T>&, const BlockStep*, long long, int,
+                                                const double* /*kprev*/, const double* ktd, const Chan& p,
+                                                double* sig, long long /*t*/) {
+    inlm_stress<D, T>(ktd, p, sig);
 }
 
 // ------------------------------------------------------------------------------------------------
@@ -666,8 +784,9 @@ __device__ __forceinline__ void frame_apply(const float* Rm, const double* p, do
 
 template <int D>
 __device__ __forceinline__ void hist_commit_any(const CommitS16& a, const BlockStep* s_bs, long long Np, int n,
-                                                const double* kprev, const double* ktd, double G_inf,
+                                                const double* kprev, const double* ktd, const Chan& p,
                                                 double* sig, long long t) {
+    const double G_inf = p.G_inf;
     constexpr int DD = D * D;
     constexpr int NS = D == 2 ? 3 : 6;
     // the frame of this step (identical arithmetic to the sweep's rebase path), then the rebase
@@ -936,7 +1055,7 @@ __global__ void __launch_bounds__(256) k_commit(H a, const double* __restrict__ 
         ktd[c] = kappa_in[(long long)c * g.N + n];
         kprev[c] = kappa_f[c * g.Npad + n];
     }
-    hist_commit_any<D>(a, s_bs, g.Npad, n, kprev, ktd, g.ch[chan_index(g, n)].G_inf, sig, t);
+    hist_commit_any<D>(a, s_bs, g.Npad, n, kprev, ktd, g.ch[chan_index(g, n)], sig, t);
 #pragma unroll
     for (int i = 0; i < NS; ++i) {
         sigma_f[i * g.Npad + n] = sig[i];
@@ -984,7 +1103,7 @@ __global__ void __launch_bounds__(256) k_collide_stream(CollArgs<P> a, H h, Geom
         kappa_fd<D>(a.u_raw, Np, p, n, ktd);
 #pragma unroll
         for (int c = 0; c < DD; ++c) kprev[c] = a.kappa[c * Np + n];
-        hist_commit_any<D>(h, s_bs, Np, n, kprev, ktd, p.G_inf, sg, t);
+        hist_commit_any<D>(h, s_bs, Np, n, kprev, ktd, p, sg, t);
 #pragma unroll
         for (int i = 0; i < NS; ++i) a.sigma[i * Np + n] = sg[i];
 #pragma unroll

@@ -37,7 +37,8 @@ def test_strerror():
 
 @pytest.mark.parametrize("bad", [
     dict(tau_lb=0.5), dict(ny=1), dict(nx=0), dict(C=3), dict(B=0), dict(B=17), dict(tau=0.0),
-    dict(G_inf=-1.0), dict(gamma_c=0.0), dict(G_inf=0.3), dict(nz=2), dict(C=4096, B=2),
+    dict(G_inf=-1.0), dict(gamma_c=0.0), dict(G_inf=0.3), dict(nz=2), dict(C=4096, B=2), dict(model=3),
+    dict(model=-1),
 ])
 def test_create_rejects_bad_descriptions(bad):
     kw = dict(lattice=L.LBVE_D2Q9, nx=4, ny=8, tau_lb=0.9, G_inf=0.01, tau=100.0, gamma_c=0.1, C=8, B=2)
@@ -45,6 +46,27 @@ def test_create_rejects_bad_descriptions(bad):
     d = L.make_desc(**kw)
     with pytest.raises(L.LbveError) as e:
         L.lbve_create(d)
+    assert e.value.status == L.LBVE_EINVAL
+
+
+def test_unsupported_variant_combinations_are_refused_before_any_device_work():
+    """White-Metzner with the 16-bit history, and differentiation of the two constitutive variants, are
+    valid requests this library does not implement (LBVE_ENOSUPPORT); a batch mixing models is invalid."""
+    wm16 = L.make_desc(nx=2, ny=4, C=8, B=2, precision=L.LBVE_F32, hist_storage=L.LBVE_S16, model=L.LBVE_MODEL_WM)
+    with pytest.raises(L.LbveError) as e:
+        L.lbve_create(wm16)
+    assert e.value.status == L.LBVE_ENOSUPPORT
+    for model in (L.LBVE_MODEL_INLM, L.LBVE_MODEL_WM):
+        d = L.make_desc(nx=2, ny=4, C=8, B=2, precision=L.LBVE_F64, model=model)
+        with pytest.raises(L.LbveError) as e:
+            L.lbve_create_tangent(d)
+        assert e.value.status == L.LBVE_ENOSUPPORT
+        with pytest.raises(L.LbveError) as e:
+            L.lbve_create_adjoint(d)
+        assert e.value.status == L.LBVE_ENOSUPPORT
+    mixed = [L.make_desc(nx=2, ny=4, C=8, B=2), L.make_desc(nx=2, ny=4, C=8, B=2, model=L.LBVE_MODEL_WM)]
+    with pytest.raises(L.LbveError) as e:
+        L.lbve_create_batch(mixed)
     assert e.value.status == L.LBVE_EINVAL
 
 

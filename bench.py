@@ -7,6 +7,7 @@ node.  Metric: node-history updates per second (one retained history point of on
 one step); MLUPS of the full step is reported beside it.
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+                  [--workload channel|batched|duct] [--history f32|s16|f64] [--model nlm|wm|inlm]
 
 --impl ours (default): the CUDA library through its C ABI.  Timed region: K steps bracketed by a
 barrier and a device synchronisation, CUDA events on the launching stream, max over ranks.  The
@@ -33,6 +34,7 @@ sys.path.insert(0, ROOT)
 
 METRIC = "node-history updates/s"
 UNIT = "node-history updates/s"
+METRIC_NODES = "lattice node updates/s"   # the instantaneous model: no history points
 BYTES_PER_UPDATE = 48        # FP32 D2Q9: read X (16 B) + write X (16 B) + read kappa (16 B) per point
 FALLBACK_HBM_GBS = 6800.0
 
@@ -51,6 +53,9 @@ def parse():
                          "uneven width; duct: the D3Q19 128^3 square duct")
     ap.add_argument("--history", choices=["f32", "s16", "f64"], default="f32",
                     help="history storage: f32 (plain FP32 form), s16 (16-bit block-scaled precision variant), f64")
+    ap.add_argument("--model", choices=["nlm", "wm", "inlm"], default="nlm",
+                    help="constitutive model: nlm (integral nlM, the benchmark line), wm (White-Metzner form), "
+                         "inlm (instantaneous nlM of Eq. inlM: no history; metric lattice node updates/s)")
     ap.add_argument("--nx", type=int, default=None,
                     help="narrower channel (same rows, same history) for profiler captures; not a bench line")
     return ap.parse_args()
@@ -129,38 +134,59 @@ def points_per_step(C: int, B: int, t0: int, K: int, L) -> list:
     return [len(L.lbve_schedule(C, B, t)[0]) for t in range(t0, t0 + K)]
 
 
-def kernel_hash() -> str:
+def kernel_hash(files=("lbve_kernels.cuh", "lbve_sched.cuh")) -> str:
     h = hashlib.sha256()
-    for f in ("lbve_kernels.cuh", "lbve_sched.cuh"):
+    for f in files:
         with open(os.path.join(ROOT, "paper_1504_06123_gb300", "csrc", f), "rb") as fh:
             h.update(fh.read())
     return h.hexdigest()[:16]
 
 
-def recorded_traffic():
-    """DRAM bytes per history launch from the committed ncu summary, if it was taken on these kernels."""
-    p = os.path.join(ROOT, "profiles", "sweep_channel_1024x512_L1024.md")
+PROFILE_OF = {"nlm": "sweep_channel_1024x512_L1024.md", "wm": "sweep_wm_channel_1024x512_L1024.md",
+              "inlm": "collide_inlm_channel_4096x512.md"}
+
+
+def recorded_profile(model: str = "nlm") -> dict:
+    """Figures of the committed ncu summary of the dominant kernel (dram_bytes_per_launch, and for an
+    ALU-bound kernel fp64_thread_inst_per_node), if it was taken on the current source of that kernel (the
+    summary names the source files its hash covers); {} otherwise."""
+    p = os.path.join(ROOT, "profiles", PROFILE_OF[model])
     if not os.path.exists(p):
-        return None
-    kh, traffic = None, None
+        return {}
+    kh, files, out = None, ("lbve_kernels.cuh", "lbve_sched.cuh"), {}
     for line in open(p):
-        if line.startswith("kernel_source_sha256_16:"):
-            kh = line.split(":", 1)[1].strip()
-        if line.startswith("dram_bytes_per_launch:"):
-            traffic = float(line.split(":", 1)[1].strip())
-    return traffic if kh == kernel_hash() else None
+        key, _, val = line.partition(":")
+        if key == "kernel_source_sha256_16":
+            kh = val.strip()
+        elif key == "kernel_source_files":
+            files = tuple(x.strip() for x in val.split(","))
+        elif key in ("dram_bytes_per_launch", "fp64_thread_inst_per_node"):
+            out[key] = float(val.strip())
+    return out if kh == kernel_hash(files) else {}
 
 
-def oracle_sample(steps: int | None = None, budget_s: float = 12.0, warmup: int = 1):
+def recorded_traffic(model: str = "nlm"):
+    return recorded_profile(model).get("dram_bytes_per_launch")
+
+
+def channel_workload(model: str):
+    from paper_1504_06123_gb300 import configs
+    return {"nlm": configs.plain_channel_large, "wm": configs.wm_channel_large,
+            "inlm": configs.inlm_channel_large}[model]()
+
+
+def oracle_sample(steps: int | None = None, budget_s: float = 12.0, warmup: int = 1, model: str = "nlm"):
     """The FP64 oracle on 2 columns x 512 rows of the benchmark channel with its full history: `warmup`
-    untimed steps, then `steps` timed ones (or as many as fit in budget_s)."""
+    untimed steps, then `steps` timed ones (or as many as fit in budget_s).  Returns the rate in the
+    workload's unit: node-history updates/s, or node updates/s for the instantaneous model."""
     import oracle
-    from paper_1504_06123_gb300 import configs, inputs
-    w = configs.plain_channel_large()
+    from paper_1504_06123_gb300 import inputs
+    w = channel_workload(model)
     nx = 2
     rho = inputs.initial_density(w.N, w.noise, w.seed).reshape(w.ny, w.nx)[:, :nx].ravel()
     ch = oracle.Channel(oracle.D2Q9, nx, w.ny, tau_lb=w.tau_lb, G_inf=w.G_inf, tau=w.tau, gamma_c=w.gamma_c,
-                        g=(w.g, 0, 0), C=w.C, B=w.B, rho_init=rho)
+                        g=(w.g, 0, 0), C=w.C, B=w.B, rho_init=rho,
+                        model={"nlm": oracle.NLM, "wm": oracle.WM, "inlm": oracle.INLM}[model])
     t0 = time.perf_counter()
     ch.step(max(1, warmup))
     one = (time.perf_counter() - t0) / max(1, warmup)
@@ -169,10 +195,14 @@ def oracle_sample(steps: int | None = None, budget_s: float = 12.0, warmup: int 
     t0 = time.perf_counter()
     ch.step(n)
     dt = time.perf_counter() - t0
-    pts = [len(oracle.schedule(w.C, w.B, t)[0]) for t in range(t_start, t_start + n)]
-    upd = nx * w.ny * sum(pts)
+    if model == "inlm":
+        upd = nx * w.ny * n
+    else:
+        pts = [len(oracle.schedule(w.C, w.B, t)[0]) for t in range(t_start, t_start + n)]
+        upd = nx * w.ny * sum(pts)
     ch.close()
-    sample = f"{nx} of {w.nx} columns x {w.ny} rows, L = {w.L}, steps {t_start}..{t_start + n - 1} ({dt:.1f} s)"
+    hist = "no history" if model == "inlm" else f"L = {w.L}"
+    sample = f"{nx} of {w.nx} columns x {w.ny} rows, {hist}, steps {t_start}..{t_start + n - 1} ({dt:.1f} s)"
     return upd / dt, sample, n, dt, upd
 
 
@@ -180,14 +210,15 @@ def run_reference(args, rank, world):
     if rank != 0:
         return
     # each step: one oracle step of the sample (about 0.1 s on one core)
-    val, sample, n, dt, upd = oracle_sample(steps=args.steps, warmup=args.warmup)
+    val, sample, n, dt, upd = oracle_sample(steps=args.steps, warmup=args.warmup, model=args.model)
+    metric = METRIC_NODES if args.model == "inlm" else METRIC
     line = {
-        "metric": METRIC, "value": val, "unit": UNIT, "n_gpus": args.gpus, "steps": n, "warmup": args.warmup,
+        "metric": metric, "value": val, "unit": metric, "n_gpus": args.gpus, "steps": n, "warmup": args.warmup,
         "ms_per_step": 1e3 * dt / n, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
         "dtype": "f64", "data": "synthetic", "impl": "reference",
-        "config": {"workload": "channel_1024x512_L1024", "sample": sample},
-        "cpu_baseline": {"value": val, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": sample},
-        "e2e": {"value": val, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+        "config": {"workload": channel_workload(args.model).name, "sample": sample},
+        "cpu_baseline": {"value": val, "unit": metric, "cores": 1, "kind": "oracle", "sample": sample},
+        "e2e": {"value": val, "unit": metric, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
         "gpu_launches": 0,
     }
     print(json.dumps(line), flush=True)
@@ -195,22 +226,30 @@ def run_reference(args, rank, world):
 
 def workload_descs(args, L, configs):
     """(name, descs, rho_init, notes) of the selected workload."""
+    if args.model == "inlm" and args.workload != "channel":
+        raise SystemExit("--model inlm is measured on the channel workload")
+    model = {"nlm": L.LBVE_MODEL_NLM, "wm": L.LBVE_MODEL_WM, "inlm": L.LBVE_MODEL_INLM}[args.model]
     if args.workload == "channel":
-        w = configs.plain_channel_large()
+        w = channel_workload(args.model)
         if args.nx:
             w.nx = args.nx
-        return f"channel_{w.nx}x{w.ny}_L{w.L}", [w.desc()], w.rho_init(), {
+        suffix = {"nlm": "", "wm": "_wm"}.get(args.model)
+        name = f"channel_{w.nx}x{w.ny}_inlm" if suffix is None else f"channel_{w.nx}x{w.ny}_L{w.L}{suffix}"
+        return name, [w.desc()], w.rho_init(), {
             "lattice": "D2Q9", "blocks_B": w.B, "block_C": w.C, "tau_lb": w.tau_lb, "G_inf": w.G_inf, "tau": w.tau,
             "gamma_c": w.gamma_c, "g": w.g}
     if args.workload == "duct":
         w = configs.duct_3d()
         if args.nx:
             w.nx = args.nx
-        return f"duct_{w.nx}x{w.ny}x{w.nz}_L{w.L}", [w.desc()], w.rho_init(), {
+        w.model = model
+        return f"duct_{w.nx}x{w.ny}x{w.nz}_L{w.L}" + ("_wm" if args.model == "wm" else ""), [w.desc()], w.rho_init(), {
             "lattice": "D3Q19", "blocks_B": w.B, "block_C": w.C, "tau_lb": w.tau_lb, "G_inf": w.G_inf, "tau": w.tau,
             "gamma_c": w.gamma_c, "g": w.g}
     ws = configs.batched_channels()
-    return f"batch64_channels_L{ws[0].L}", [w.desc() for w in ws], None, {
+    for w in ws:
+        w.model = model
+    return f"batch64_channels_L{ws[0].L}" + ("_wm" if args.model == "wm" else ""), [w.desc() for w in ws], None, {
         "lattice": "D2Q9", "channels": len(ws), "widths": [w.ny for w in ws], "blocks_B": ws[0].B,
         "block_C": ws[0].C}
 
@@ -242,22 +281,37 @@ def run_ours(args, rank, world, local_rank):
         if hist == L.LBVE_S16:
             # the reduced-precision form: FP32 populations are well inside its 1e-3 budget
             d.pop_precision = L.LBVE_F32
+    inst = args.model == "inlm"
+    wm = args.model == "wm"
+    if wm and hist == L.LBVE_S16:
+        raise SystemExit("the White-Metzner form has no 16-bit history")
+    metric = METRIC_NODES if inst else METRIC
     d0 = descs[0]
     N = sum(d.nx * d.ny * d.nz for d in descs)
     D = 2 if d0.lattice == L.LBVE_D2Q9 else 3
+    Q = d0.lattice
     if d0.hist_storage == L.LBVE_S16:
         # read Q and kappa (d*d int16 + 1-byte exponent each); every 32nd step also writes Q
         bytes_per_update = 2 * (2 * D * D + 1) + (2 * D * D + 1) / 32
     else:
         hist_bytes = 4 if d0.hist_storage == L.LBVE_F32 else 8
         bytes_per_update = 3 * D * D * hist_bytes     # read X, write X, read kappa
+        if wm:
+            bytes_per_update += 8                     # read the point's creation strain Gamma(t') (double)
+    # the collide kernel, per node: populations in and out, u_raw, sigma, kappa, rho, u out, tr_prev in/out
+    pop_bytes = 8 if d0.pop_precision == L.LBVE_F64 else 4
+    NS = 3 if D == 2 else 6
+    collide_bytes_per_node = 2 * Q * pop_bytes + 8 * (D + NS + D * D + 1 + D + 2)
     stream = torch.cuda.current_stream()
     ch = L.Channel(descs if len(descs) > 1 else descs[0], rho)
     K, W = args.steps, args.warmup
     ch.step(W, stream)
     torch.cuda.synchronize()
-    pts = points_per_step(d0.hist_C, d0.hist_B, W, K, L)
-    updates_rank = N * sum(pts)
+    if inst:
+        updates_rank = N * K
+    else:
+        pts = points_per_step(d0.hist_C, d0.hist_B, W, K, L)
+        updates_rank = N * sum(pts)
 
     # timed region: K steps as a user runs them (16-step graphs replayed)
     ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
@@ -280,17 +334,41 @@ def run_ours(args, rank, world, local_rank):
     ch.step(Kp, stream)
     kms, launches = L.lbve_profile_read(ch.h)
     L.lbve_profile(ch.h, False)
-    pts_p = points_per_step(d0.hist_C, d0.hist_B, W + K, Kp, L)
     hist_ms = kms[1] / max(launches[1], 1)
-    alg_bytes = bytes_per_update * N * (sum(pts_p) - Kp) / Kp   # the new point is not read from memory
+    coll_ms = kms[2] / max(launches[2], 1)
     peak, peak_kind = peaks()
-    achieved = alg_bytes / (hist_ms / 1e3) / 1e9
-    traffic = recorded_traffic() if args.workload == "channel" and not args.nx else None
+    roof_extra = {}
+    if inst:   # no history: the collide kernel (with the stress series) is the dominant kernel
+        alg_bytes = collide_bytes_per_node * N
+        achieved = alg_bytes / (coll_ms / 1e3) / 1e9
+        roof_kernel = "k_collide_stream"
+        state_bytes = 2 * Q * pop_bytes * N
+    else:
+        pts_p = points_per_step(d0.hist_C, d0.hist_B, W + K, Kp, L)
+        alg_bytes = bytes_per_update * N * (sum(pts_p) - Kp) / Kp   # the new point is not read from memory
+        achieved = alg_bytes / (hist_ms / 1e3) / 1e9
+        roof_kernel = "k_sweep"
+        state_bytes = alg_bytes
+    prof = recorded_profile(args.model) if args.workload == "channel" and not args.nx else {}
+    traffic = prof.get("dram_bytes_per_launch")
+    roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
+                "traffic": traffic, "peak_kind": peak_kind, "kernel": roof_kernel,
+                "algorithmic_bytes_per_launch": alg_bytes}
+    if inst and d0.pop_precision == L.LBVE_F64 and "fp64_thread_inst_per_node" in prof:
+        # bound by the FP64 pipe: 2 FP64 thread instructions per SM per cycle (GB300), 152 SMs, at the
+        # sampled SM clock; the instruction count per node is the ncu count of the committed capture
+        sms = torch.cuda.get_device_properties(local_rank).multi_processor_count
+        inst_s = prof["fp64_thread_inst_per_node"] * N / (coll_ms / 1e3) / 1e9
+        roofline = {"bound": "alu", "achieved": inst_s, "peak": None, "unit": "G FP64 thread inst/s",
+                    "frac": None, "traffic": traffic, "peak_kind": "derived: 2 FP64 inst / SM / cycle x "
+                    f"{sms} SMs x sampled SM clock", "kernel": roof_kernel,
+                    "fp64_thread_inst_per_node": prof["fp64_thread_inst_per_node"],
+                    "hbm_frac": achieved / peak, "algorithmic_bytes_per_launch": alg_bytes}
     S, ctas = L.lbve_sweep_config(ch.h)
     ch.close()
 
     extra = {}
-    if args.workload in ("channel", "duct") and args.history == "f32" and not args.no_chosen:
+    if args.workload in ("channel", "duct") and args.history == "f32" and not args.no_chosen and args.model == "nlm":
         # the chosen (reduced-precision) form on the same workload: 16-bit block-scaled history in a
         # per-node frame, FP32 populations (its parity bar is 1e-3)
         import copy as _copy
@@ -321,6 +399,34 @@ def run_ours(args, rank, world, local_rank):
                             "sweep_ms_per_launch": sweep_c,
                             "roofline_frac": bytes_c / (sweep_c / 1e3) / 1e9 / peak,
                             "parity_bar": 1e-3},
+                 "chosen_vs_plain": chosen_value / value}
+    if inst and not args.no_chosen:
+        # the instantaneous model with FP32 populations (the series summed in float): its collision runs on
+        # the FP32 pipe instead of the FP64 one; parity bar of the all-FP32 form 5e-5
+        import copy as _copy
+        dc = _copy.copy(d0)
+        dc.pop_precision = L.LBVE_F32
+        chc = L.Channel(dc, rho)
+        chc.step(W, stream)
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        barrier()
+        e0.record(stream)
+        chc.step(K, stream)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        msc = max_over_ranks(e0.elapsed_time(e1))
+        L.lbve_profile(chc.h, True)
+        chc.step(Kp, stream)
+        kmc, lnc = L.lbve_profile_read(chc.h)
+        L.lbve_profile(chc.h, False)
+        chc.close()
+        coll_c = kmc[2] / max(lnc[2], 1)
+        bytes_c = (2 * Q * 4 + 8 * (D + NS + D * D + 1 + D + 2)) * N
+        chosen_value = updates_rank * world / (msc / 1e3)
+        extra = {"chosen": {"form": "f32 populations, series of Eq. (inlM) summed in float", "value": chosen_value,
+                            "unit": metric, "ms_per_step": msc / K, "collide_ms_per_launch": coll_c,
+                            "roofline_frac": bytes_c / (coll_c / 1e3) / 1e9 / peak, "parity_bar": 5e-5},
                  "chosen_vs_plain": chosen_value / value}
     if args.workload == "batched":
         # the plain form: one handle per channel, each stepped with its own launches (no batching, no graphs)
@@ -360,38 +466,46 @@ def run_ours(args, rank, world, local_rank):
         L.lbve_destroy(h)
         if rc != 0:
             raise RuntimeError(f"lbve_fields failed: {rc}")
-        pts_e = points_per_step(d0.hist_C, d0.hist_B, 0, K, L)
-        e2e = {"value": N * sum(pts_e) * world / dt, "unit": UNIT,
+        upd_e = N * K if inst else N * sum(points_per_step(d0.hist_C, d0.hist_B, 0, K, L))
+        e2e = {"value": upd_e * world / dt, "unit": metric,
                "h2d_bytes_per_step": (8 * N if rho is not None else 0) / K,
                "d2h_bytes_per_step": 8 * host.numel() / K, "steps": K,
                "includes": "create (allocation, autotune, initial density upload), K steps, field read, destroy"}
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline and args.workload == "channel":
-        val, sample, *_ = oracle_sample()
-        cpu = {"value": val, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": sample}
+        val, sample, *_ = oracle_sample(model=args.model)
+        cpu = {"value": val, "unit": metric, "cores": 1, "kind": "oracle", "sample": sample}
 
+    clocks = clk.summary()
+    if roofline["bound"] == "alu":
+        mhz = clocks["sm_mhz"] or clocks["sm_max_mhz"] or 2070.0
+        roofline["peak"] = 2 * sms * mhz * 1e6 / 1e9
+        roofline["frac"] = roofline["achieved"] / roofline["peak"]
     if rank == 0:
         prec = {L.LBVE_F32: "f32", L.LBVE_F64: "f64", L.LBVE_S16: "s16 (16-bit block-scaled, f32 math)"}
+        model_name = {"nlm": "integral nlM, Eqs. (gitt), (nlmax)", "wm": "White-Metzner form of Eq. (nlmax)",
+                      "inlm": "instantaneous nlM, Eq. (inlM): no history"}[args.model]
         line = {
-            "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": K, "warmup": W,
+            "metric": metric, "value": value, "unit": metric, "n_gpus": world, "steps": K, "warmup": W,
             "ms_per_step": ms_max / K, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
             "dtype": {L.LBVE_S16: "s16"}.get(d0.hist_storage, prec.get(d0.hist_storage, "f32")), "data": "synthetic",
-            "config": dict({"workload": name, "nodes": N, "history_points": d0.hist_C * d0.hist_B,
-                            "precision": f"history (E-1, kappa) {prec.get(d0.hist_storage)} storage and arithmetic; "
-                                         f"populations {prec.get(d0.pop_precision)}",
+            "config": dict({"workload": name, "nodes": N, "history_points": 0 if inst else d0.hist_C * d0.hist_B,
+                            "model": model_name,
+                            "precision": (f"no history; populations {prec.get(d0.pop_precision)}" if inst else
+                                          f"history (E-1, kappa) {prec.get(d0.hist_storage)} storage and arithmetic; "
+                                          f"populations {prec.get(d0.pop_precision)}"),
                             "parallelism": f"replicas{world}",
-                            "l2": "no flush: history state far larger than the 129 MB L2" if alg_bytes > 1e9 else
-                                  "history state fits in L2 (latency-bound size)",
+                            "l2": ("no flush: per-step state (" + ("populations" if inst else "history") +
+                                   f", {state_bytes / 1e6:.0f} MB) larger than the 129 MB L2")
+                                  if state_bytes > 2.5e8 else "state fits in L2 (latency-bound size)",
                             "sweep": {"slot_chunks": S, "ctas": ctas}}, **notes),
             "mlups": mlups,
             "kernel_ms_per_launch": {"moments": kms[0] / max(launches[0], 1), "history": hist_ms,
                                      "collide_stream": kms[2] / max(launches[2], 1)},
-            "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
-                         "frac": achieved / peak, "traffic": traffic, "peak_kind": peak_kind,
-                         "kernel": "k_sweep", "algorithmic_bytes_per_launch": alg_bytes},
-            "clocks": clk.summary(),
-            "gpu_launches": 3 * K,
+            "roofline": roofline,
+            "clocks": clocks,
+            "gpu_launches": (2 if inst else 3) * K,
             "e2e": e2e,
             "cpu_baseline": cpu,
         }

@@ -56,6 +56,7 @@ class Workload:
     # because FP32 populations alone leave ~1e-5 relative error in decaying flows (cessation)
     precision: int = L.LBVE_F64
     hist_storage: int | None = L.LBVE_F32
+    model: int = L.LBVE_MODEL_NLM
     extra: dict = field(default_factory=dict)
 
     @property
@@ -69,7 +70,7 @@ class Workload:
     def desc(self, **over) -> L.lbve_channel_desc:
         kw = dict(lattice=self.lattice, nx=self.nx, ny=self.ny, nz=self.nz, tau_lb=self.tau_lb, G_inf=self.G_inf,
                   tau=self.tau, gamma_c=self.gamma_c, g=(self.g, 0.0, 0.0), C=self.C, B=self.B,
-                  precision=self.precision, hist_storage=self.hist_storage)
+                  precision=self.precision, hist_storage=self.hist_storage, model=self.model)
         kw.update(over)
         return L.make_desc(**kw)
 
@@ -91,6 +92,26 @@ def plain_channel_large() -> Workload:
     g = force_for_peclet(30.0, H, 0.9, 0.01, 1000.0, 0.1)
     return Workload("channel_1024x512_L1024", L.LBVE_D2Q9, 1024, 512, 1, 0.9, 0.01, 1000.0, 0.1, g, 128, 8,
                     steps=5000, noise=1e-6, seed=2)
+
+
+def wm_channel_large() -> Workload:
+    """The 1024 x 512 channel of plain_channel_large with the White-Metzner form of Eq. (nlmax)."""
+    w = plain_channel_large()
+    w.name = "channel_1024x512_L1024_wm"
+    w.model = L.LBVE_MODEL_WM
+    return w
+
+
+def inlm_channel_large() -> Workload:
+    """The instantaneous nlM of Eq. (inlM) (no history) in a 4096 x 512 channel: the rows of the benchmark
+    channel, four times its length, so that the populations (302 MB per copy in FP64) exceed the 129 MB L2
+    as the history does in the integral model.  tau = 10 (G_inf tau = 0.1): the explicit instantaneous
+    stress is stable up to G_inf tau_M of about 1.7 nu_N (0.23 at tau_LB 0.9) with the density source;
+    wall Peclet 30, capped like the others."""
+    H = 512 / 2
+    g = force_for_peclet(30.0, H, 0.9, 0.01, 10.0, 0.1)
+    return Workload("channel_4096x512_inlm", L.LBVE_D2Q9, 4096, 512, 1, 0.9, 0.01, 10.0, 0.1, g, 4, 1,
+                    steps=5000, noise=1e-6, seed=2, model=L.LBVE_MODEL_INLM)
 
 
 def duct_3d() -> Workload:

@@ -18,6 +18,7 @@
 
 #include "../../include/lbve.h"
 #include "lbve_kernels.cuh"
+#include "lbve_collide.cuh"
 #include "lbve_tangent.cuh"
 #include "lbve_adjoint.cuh"
 
@@ -162,6 +163,7 @@ void fill_chan(const lbve_channel_desc& d, int off, Chan* c) {
     c->trace_full = d.trace_coupling == LBVE_TRACE_FULL;
     c->rho0 = d.rho0;
     c->tau_lb = d.tau_lb;
+    c->omega = 1.0 / d.tau_lb;
     for (int a = 0; a < 3; ++a) c->f[a] = d.rho0 * d.g[a];
     c->G_inf = d.G_inf;
     c->inv_tau = 1.0 / d.tau;

@@ -1,4 +1,7 @@
-// lbve_kernels.cuh -- sm_103a kernels of one hybrid LB step (Sec. III of arXiv:1504.06123).
+// lbve_kernels.cuh -- sm_103a kernels of one hybrid LB step (Sec. III of arXiv:1504.06123): the shared
+// types, the moments, the finite-difference gradient and the stress history (sweep and commit, in FP32,
+// FP64 and the 16-bit block-scaled form).  The collision kernel and the history-free instantaneous
+// model are in lbve_collide.cuh.
 //
 // Per step, three launches on one stream:
 //   k_moments        : u_raw = (sum c n + f/2) / sum n                                (Eq. hydrofields)
@@ -81,6 +84,7 @@ struct Chan {
     int wall_z;       // walls at z = -1/2, nz - 1/2
     int trace_full;   // Eq. (bodyforce) with the density source
     double rho0, tau_lb;
+    double omega;     // BGK rate 1 / tau_lb
     double f[3];      // force density rho0 g
     double G_inf, inv_tau, inv_gc;
 };
@@ -542,81 +546,6 @@ __device__ __forceinline__ void hist_commit_any(const CommitArgs<R>& a, const Bl
 }
 
 // ------------------------------------------------------------------------------------------------
-// Instantaneous nlM, Eq. (inlM): no history.  sigma_struc(t) = G_inf sum_{n>=1} tau_M^n d^(n)[kappa(t)],
-// tau_M = (1/tau + gammadot(t)/gamma_c)^-1.  The d^(n) are the Taylor coefficients of
-// exp(kappa s) exp(kappa^T s), so d^(1) = D and d^(n+1) = kappa d^(n) + d^(n) kappa^T: with A = tau_M kappa
-// the terms T_n = tau_M^n d^(n) follow T_1 = tau_M D, T_{n+1} = A T_n + T_n A^T, summed in the arithmetic
-// type T until two consecutive terms are below 1e-18 of the partial sum (a nilpotent kappa, simple shear,
-// ends the series at n = 2).  NaN when the series has not converged after kInlmTerms terms or overflows:
-// Eq. (inlM) then has no sum (no steady state).  The stopping rule is the same in both arithmetic types,
-// so FP32 and FP64 agree on where the sum exists.
-// ------------------------------------------------------------------------------------------------
-template <typename T> struct Instant { int B, C; };   // B = 1, C = 4: the shared schedule code is unused
-constexpr int kInlmTerms = 1000;
-constexpr double kInlmEps = 1e-18;
-
-template <int D, typename T>
-__device__ __forceinline__ void inlm_stress(const double* ktd, const Chan& p, double* sig) {
-    constexpr int DD = D * D;
-    constexpr int NS = D == 2 ? 3 : 6;
-    const double tMd = 1.0 / (p.inv_tau + shear_rate_d<D>(ktd) * p.inv_gc);
-    T A[DD], Tn[DD], Z[DD];
-#pragma unroll
-    for (int r = 0; r < D; ++r)
-#pragma unroll
-        for (int c = 0; c < D; ++c) {
-            A[r * D + c] = (T)(tMd * ktd[r * D + c]);
-            Tn[r * D + c] = (T)(tMd * (ktd[r * D + c] + ktd[c * D + r]));
-            Z[r * D + c] = Tn[r * D + c];
-        }
-    bool ok = false;
-    int quiet = 0;
-    for (int n = 2; n <= kInlmTerms; ++n) {
-        T P[DD];   // A T_n
-#pragma unroll
-        for (int r = 0; r < D; ++r)
-#pragma unroll
-            for (int c = 0; c < D; ++c) {
-                T s = 0;
-#pragma unroll
-                for (int k = 0; k < D; ++k) s += A[r * D + k] * Tn[k * D + c];
-                P[r * D + c] = s;
-            }
-        T tn = 0, zn = 0;
-#pragma unroll
-        for (int r = 0; r < D; ++r)
-#pragma unroll
-            for (int c = 0; c < D; ++c) {
-                const T v = P[r * D + c] + P[c * D + r];   // T_{n+1} = A T_n + (A T_n)^T (T_n symmetric)
-                Tn[r * D + c] = v;
-                Z[r * D + c] += v;
-                tn = fmax(tn, fabs(v));
-                zn = fmax(zn, fabs(Z[r * D + c]));
-            }
-        if (!isfinite(tn) || !isfinite(zn)) break;   // diverged
-        quiet = (tn <= T(kInlmEps) * zn) ? quiet + 1 : 0;
-        if (quiet >= 2) { ok = true; break; }
-    }
-    const double nan = __longlong_as_double(0x7ff8000000000000ll);
-    if (D == 2) {
-        sig[0] = ok ? p.G_inf * (double)Z[0] : nan;
-        sig[1] = ok ? p.G_inf * (double)Z[3] : nan;
-        sig[2] = ok ? p.G_inf * (double)Z[1] : nan;
-    } else {
-        const int idx[6] = {0, 4, 8, 1, 2, 5};
-#pragma unroll
-        for (int i = 0; i < NS; ++i) sig[i] = ok ? p.G_inf * (double)Z[idx[i]] : nan;
-    }
-}
-
-template <int D, typename T>
-__device__ __forceinline__ void hist_commit_any(const Instant<T>&, const BlockStep*, long long, int,
-                                                const double* /*kprev*/, const double* ktd, const Chan& p,
-                                                double* sig, long long /*t*/) {
-    inlm_stress<D, T>(ktd, p, sig);
-}
-
-// ------------------------------------------------------------------------------------------------
 // Reduced-precision history (precision variant): 16-bit block-scaled storage in a per-node frame.
 //
 // Every node keeps a frame R(t) = E(t, t_b), the deformation since the last rebase step t_b, in FP32
@@ -1063,185 +992,6 @@ __global__ void __launch_bounds__(256) k_commit(H a, const double* __restrict__ 
     }
 #pragma unroll
     for (int c = 0; c < DD; ++c) kappa_f[c * g.Npad + n] = ktd[c];
-}
-
-// ------------------------------------------------------------------------------------------------
-// K3: collision with the non-Newtonian forcing and push streaming
-// ------------------------------------------------------------------------------------------------
-template <typename P> struct CollArgs {
-    const P* __restrict__ dn_in;        // [Q][Npad]
-    P* __restrict__ dn_out;             // [Q][Npad]
-    const double* __restrict__ u_raw;   // [D][Npad]  for kappa(t)
-    double* __restrict__ sigma;         // [NS][Npad] sigma_struc(t) out
-    double* __restrict__ kappa;         // [DD][Npad] kappa(t) out
-    double* __restrict__ tr_prev;       // [Npad]
-    double* __restrict__ rho;           // [Npad] rho - rho0
-    double* __restrict__ u;             // [D][Npad]
-    const long long* t_dev;             // step index t
-};
-
-// One node per thread: history commit (sigma_struc(t), merges, new point), then the collision with
-// that stress and push streaming.  T: arithmetic type of the collision (double for double populations;
-// float for float).
-template <int Q, typename P, typename T, class H>
-__global__ void __launch_bounds__(256) k_collide_stream(CollArgs<P> a, H h, Geom g) {
-    using L = Lattice<Q>;
-    constexpr int D = L::D;
-    constexpr int DD = D * D;
-    constexpr int NS = D == 2 ? 3 : 6;
-    __shared__ BlockStep s_bs[LBVE_MAXB];
-    const long long t = *a.t_dev;
-    if (threadIdx.x == 0) sched_step(h.B, h.C, t, s_bs);
-    __syncthreads();
-    const int n = blockIdx.x * blockDim.x + threadIdx.x;
-    if (n >= g.N) return;
-    const long long Np = g.Npad;
-    const Chan& p = g.ch[chan_index(g, n)];
-    double sg[NS];
-    {
-        double ktd[DD], kprev[DD];
-        kappa_fd<D>(a.u_raw, Np, p, n, ktd);
-#pragma unroll
-        for (int c = 0; c < DD; ++c) kprev[c] = a.kappa[c * Np + n];
-        hist_commit_any<D>(h, s_bs, Np, n, kprev, ktd, p, sg, t);
-#pragma unroll
-        for (int i = 0; i < NS; ++i) a.sigma[i * Np + n] = sg[i];
-#pragma unroll
-        for (int c = 0; c < DD; ++c) a.kappa[c * Np + n] = ktd[c];
-    }
-    const T cs2 = T(1.0 / 3.0);
-    T dn[Q];
-    double drho_raw = 0, jd[3] = {0, 0, 0};
-#pragma unroll
-    for (int q = 0; q < Q; ++q) {
-        const P v = a.dn_in[q * Np + n];
-        dn[q] = (T)v;
-        drho_raw += (double)v;
-        if (L::cx(q)) jd[0] += L::cx(q) * (double)v;
-        if (L::cy(q)) jd[1] += L::cy(q) * (double)v;
-        if (D == 3 && L::cz(q)) jd[2] += L::cz(q) * (double)v;
-    }
-    // stress: traceless part and density source (Sec. III, trace split)
-    T S[3][3];
-    double trd = 0;
-    if (D == 2) {
-        S[0][0] = (T)sg[0]; S[1][1] = (T)sg[1];
-        S[0][1] = S[1][0] = (T)sg[2];
-        trd = sg[0] + sg[1];
-    } else {
-        S[0][0] = (T)sg[0]; S[1][1] = (T)sg[1]; S[2][2] = (T)sg[2];
-        S[0][1] = S[1][0] = (T)sg[3];
-        S[0][2] = S[2][0] = (T)sg[4];
-        S[1][2] = S[2][1] = (T)sg[5];
-        trd = sg[0] + sg[1] + sg[2];
-    }
-    double ddr_d = 0;
-    if (p.trace_full) ddr_d = -(trd - a.tr_prev[n]) * (3.0 / D);   // -(tr - tr_prev)/(d cs^2)
-    const double drho_d = drho_raw + 0.5 * ddr_d;                  // rho - rho0
-    const double rho_d = p.rho0 + drho_d;
-    double ud[3] = {0, 0, 0};
-#pragma unroll
-    for (int c = 0; c < D; ++c) ud[c] = (jd[c] + 0.5 * p.f[c]) / rho_d;
-    const T tr = (T)trd, ddr = (T)ddr_d, drho = (T)drho_d, rho = (T)rho_d;
-    T u[3], f[3];
-#pragma unroll
-    for (int c = 0; c < 3; ++c) { u[c] = (T)ud[c]; f[c] = (T)p.f[c]; }
-#pragma unroll
-    for (int c = 0; c < D; ++c) S[c][c] -= tr / T(D);
-    T uu = 0;
-#pragma unroll
-    for (int c = 0; c < D; ++c) uu += u[c] * u[c];
-    const T omega = T(1.0 / p.tau_lb);
-    const T fpre = T(1) - T(0.5) * omega;
-    const T inv2cs4 = T(4.5);   // 1/(2 cs^4)
-    // X_ab = -ddr u_a u_b + u_b f_a + u_a f_b  (second-order forcing term of Eq. bodyforce)
-    T Xf[3][3];
-#pragma unroll
-    for (int r = 0; r < D; ++r)
-#pragma unroll
-        for (int c = 0; c < D; ++c) Xf[r][c] = -ddr * u[r] * u[c] + u[c] * f[r] + u[r] * f[c];
-    T trX = 0;
-#pragma unroll
-    for (int c = 0; c < D; ++c) trX += Xf[c][c];
-
-    int x, y, z;
-    node_xyz(p, n, x, y, z);
-#pragma unroll
-    for (int q = 0; q < Q; ++q) {
-        const int cq[3] = {L::cx(q), L::cy(q), L::cz(q)};
-        T cu = 0, cf = 0, cSc = 0, cXc = 0;
-#pragma unroll
-        for (int r = 0; r < D; ++r) {
-            cu += cq[r] * u[r];
-            cf += cq[r] * f[r];
-#pragma unroll
-            for (int c = 0; c < D; ++c) {
-                if (cq[r] && cq[c]) {
-                    cSc += cq[r] * cq[c] * S[r][c];
-                    cXc += cq[r] * cq[c] * Xf[r][c];
-                }
-            }
-        }
-        const T wq = (T)L::w(q);
-        // deviation of the equilibrium from w rho0: w (rho - rho0) + w rho (c.u/cs2 + ((c.u)^2 - cs2 u.u)/(2 cs4))
-        const T dneq = wq * (drho + rho * (cu * T(3) + (cu * cu - cs2 * uu) * inv2cs4));
-        // Eq. (bodyforce); (cc - cs2 1):S = cSc (S traceless), (cc - cs2 1):X = cXc - cs2 tr X
-        const T Fq = wq * (-inv2cs4 * omega * cSc + fpre * (ddr + cf * T(3) + inv2cs4 * (cXc - cs2 * trX)));
-        const P post = (P)(dn[q] - omega * (dn[q] - dneq) + Fq);
-        // push with half-way bounce-back
-        int xd = x + cq[0];
-        xd = xd < 0 ? p.nx - 1 : (xd >= p.nx ? 0 : xd);
-        const int yd = y + cq[1];
-        bool wall = yd < 0 || yd >= p.ny;
-        int zd = z + cq[2];
-        if (D == 3) {
-            if (p.wall_z) wall = wall || zd < 0 || zd >= p.nz;
-            else zd = zd < 0 ? p.nz - 1 : (zd >= p.nz ? 0 : zd);
-        }
-        if (wall) a.dn_out[L::opp(q) * Np + n] = post;
-        else a.dn_out[q * Np + (p.off + xd + p.nx * (yd + p.ny * zd))] = post;
-    }
-    a.rho[n] = drho_d;
-#pragma unroll
-    for (int c = 0; c < D; ++c) a.u[c * Np + n] = ud[c];
-    a.tr_prev[n] = p.trace_full ? trd : 0.0;
-}
-
-// ------------------------------------------------------------------------------------------------
-// Field gather (lbve_fields) and reductions (lbve_mass)
-// ------------------------------------------------------------------------------------------------
-template <typename real>
-__global__ void k_gather(const real* __restrict__ src, long long Npad, int ncomp, int N, double offset,
-                         double* __restrict__ dst, int* nonfinite) {
-    const long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x;
-    if (i >= (long long)ncomp * N) return;
-    const int c = (int)(i / N), n = (int)(i % N);
-    const double v = (double)src[c * Npad + n] + offset;
-    dst[i] = v;
-    if (!isfinite(v)) atomicOr(nonfinite, 1);
-}
-
-template <typename real>
-__global__ void k_n1(const real* __restrict__ sigma, long long Npad, int N, double* __restrict__ dst,
-                     int* nonfinite) {
-    const int n = blockIdx.x * blockDim.x + threadIdx.x;
-    if (n >= N) return;
-    const double v = (double)sigma[n] - (double)sigma[Npad + n];
-    dst[n] = v;
-    if (!isfinite(v)) atomicOr(nonfinite, 1);
-}
-
-template <typename real>
-__global__ void k_sum(const real* __restrict__ src, long long Npad, int ncomp, int N, double scale,
-                      double* __restrict__ out) {
-    double s = 0;
-    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < (long long)ncomp * N;
-         i += (long long)gridDim.x * blockDim.x) {
-        const int c = (int)(i / N), n = (int)(i % N);
-        s += (double)src[c * Npad + n];
-    }
-    for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
-    if ((threadIdx.x & 31) == 0) atomicAdd(out, s * scale);
 }
 
 }  // namespace lbk

@@ -58,6 +58,7 @@ def _load():
         lib.orc_destroy.argtypes = [C.c_void_p]
         lib.orc_set_force.argtypes = [C.c_void_p, dp]
         lib.orc_set_params.argtypes = [C.c_void_p, C.c_double, C.c_double, C.c_double]
+        lib.orc_set_pressure.argtypes = [C.c_void_p, C.c_int, C.c_double]
         lib.orc_set_model.argtypes = [C.c_void_p, C.c_int]
         lib.orc_set_model.restype = C.c_int
         lib.orc_inlm.argtypes = [C.c_int, dp, C.c_double, C.c_double, C.c_double, dp]
@@ -146,7 +147,7 @@ class Channel:
     def __init__(self, lattice: int, nx: int, ny: int, nz: int = 1, *, tau_lb: float, G_inf: float,
                  tau: float, gamma_c: float, g=(0.0, 0.0, 0.0), C: int, B: int, rho0: float = 1.0,
                  trace_full: bool = True, wall_z: bool = True, rho_init: np.ndarray | None = None,
-                 model: int = NLM):
+                 model: int = NLM, dp: float | None = None):
         self.lib = _load()
         self.lattice, self.nx, self.ny, self.nz = lattice, nx, ny, nz
         self.d = 2 if lattice == D2Q9 else 3
@@ -163,6 +164,8 @@ class Channel:
         if self.lib.orc_set_model(self._h, int(model)) != 0:
             self.close()
             raise ValueError("unknown constitutive model")
+        if dp is not None:
+            self.set_pressure_step(dp)
 
     def close(self):
         if getattr(self, "_h", None):
@@ -181,6 +184,14 @@ class Channel:
     def set_force(self, g):
         gg = np.ascontiguousarray(np.asarray(g, dtype=np.float64).reshape(3))
         self.lib.orc_set_force(self._h, _dp(gg))
+
+    def set_pressure_step(self, dp: float | None):
+        """Pressure-step boundary along x (Sec. III, generalised periodic boundary): pressure drop dp over one
+        period (nx spacings), mean density rho0; None restores the plain periodic boundary."""
+        if dp is None:
+            self.lib.orc_set_pressure(self._h, 0, 0.0)
+        else:
+            self.lib.orc_set_pressure(self._h, 1, float(dp))
 
     def set_params(self, G_inf: float, tau: float, gamma_c: float):
         self.lib.orc_set_params(self._h, G_inf, tau, gamma_c)

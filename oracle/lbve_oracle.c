@@ -54,6 +54,17 @@
  *     accumulated between t' and t, sum_{s=t'}^{t-1} gammadot(s) (the same explicit left-end rule as
  *     the factors of Eq. (eeval)), instead of (t - t') gammadot(t').  Every point stores the strain of
  *     its span next to its factor; a merge adds the two spans' strains, as it multiplies their factors.
+ *
+ * Pressure-step boundary along x (Sec. III, the generalised periodic boundary of Kim & Pitsch that fixes a
+ * constant pressure step between the inlet and the outlet of the periodic lattice), optional: the
+ * periodic images just outside the lattice are ghost nodes.  The ghost upstream of the inlet (x = -1)
+ * carries the outlet node's (x = nx-1) post-collision non-equilibrium populations on an equilibrium at the
+ * inlet density rho_in and the outlet node's velocity; the ghost downstream of the outlet (x = nx) carries
+ * the inlet node's non-equilibrium populations on an equilibrium at rho_out and the inlet node's velocity.
+ * Populations crossing the seam stream from these ghosts: n_ghost = n_eq(rho_ghost, u) + (n* - n_eq(rho, u)),
+ * rho and u the hydrodynamic fields of the node whose populations are imaged.  dp is the pressure drop over
+ * one period (nx spacings); the ghosts sit on that linear profile, nx + 1 spacings apart around the mean
+ * rho0: rho_in/out = rho0 +- (dp / c_s^2) (nx + 1) / (2 nx).
  */
 #include <math.h>
 #include <stdint.h>
@@ -455,6 +466,8 @@ typedef struct {
     double tau_lb, rho0, g[3];
     orc_model m;
     int C, B, trace_full;
+    int xbc_pressure;        /* 1: pressure-step boundary along x (ghosts on the linear pressure profile) */
+    double dp;               /* pressure drop over one period along x */
     int64_t t;               /* index of the next step */
     int c[ORC_MAXQ][3];
     double w[ORC_MAXQ];
@@ -563,6 +576,12 @@ void orc_destroy(orc_channel* ch) {
     free(ch->rho); free(ch->u); free(ch->sigma); free(ch->kappa); free(ch->tr_prev);
     free(ch->list); free(ch->ages); free(ch->wts);
     free(ch);
+}
+
+/* Pressure-step boundary along x: enabled = 0 restores the plain periodic boundary. */
+void orc_set_pressure(orc_channel* ch, int enabled, double dp) {
+    ch->xbc_pressure = enabled;
+    ch->dp = dp;
 }
 
 void orc_set_force(orc_channel* ch, const double* g) {
@@ -749,8 +768,19 @@ static void channel_step(orc_channel* ch) {
                         if (ch->wall_z) wall = wall || (zd < 0 || zd >= ch->nz);
                         else zd = (zd + ch->nz) % ch->nz;
                     }
-                    if (wall) ch->n_next[k * Q + ch->opp[i]] = post[i];
-                    else ch->n_next[node_id(ch, xd, yd, zd) * Q + i] = post[i];
+                    double val = post[i];
+                    const int xs = x + ch->c[i][0];
+                    if (!wall && ch->xbc_pressure && (xs < 0 || xs >= ch->nx)) {
+                        /* crossing the seam: the population of the ghost image (inlet ghost for +x,
+                         * outlet ghost for -x) -- equilibrium at the ghost density, this node's
+                         * non-equilibrium part, both as deviations from w rho0 */
+                        const double half = 0.5 * 3.0 * ch->dp * (ch->nx + 1.0) / ch->nx;
+                        const double rho_gh = ch->rho0 + ((xs >= ch->nx) ? half : -half);
+                        val = n_eq_dev(ch, i, rho_gh - ch->rho0, rho_gh, u) +
+                              (post[i] - n_eq_dev(ch, i, rho - ch->rho0, rho, u));
+                    }
+                    if (wall) ch->n_next[k * Q + ch->opp[i]] = val;
+                    else ch->n_next[node_id(ch, xd, yd, zd) * Q + i] = val;
                 }
                 ch->rho[k] = rho;
                 for (int a = 0; a < 3; ++a) ch->u[k * 3 + a] = u[a];

@@ -56,6 +56,9 @@ def parse():
     ap.add_argument("--model", choices=["nlm", "wm", "inlm"], default="nlm",
                     help="constitutive model: nlm (integral nlM, the benchmark line), wm (White-Metzner form), "
                          "inlm (instantaneous nlM of Eq. inlM: no history; metric lattice node updates/s)")
+    ap.add_argument("--drive", choices=["force", "pressure"], default="force",
+                    help="force: body force g with x periodic (the benchmark line); pressure: the pressure-step "
+                         "boundary along x with the equivalent drop dp = rho0 g nx per period")
     ap.add_argument("--nx", type=int, default=None,
                     help="narrower channel (same rows, same history) for profiler captures; not a bench line")
     return ap.parse_args()
@@ -275,6 +278,13 @@ def run_ours(args, rank, world, local_rank):
         return ranks.max_over_ranks(x, dist if world > 1 else None, device="cuda")
 
     name, descs, rho, notes = workload_descs(args, L, configs)
+    if args.drive == "pressure":
+        for d in descs:
+            d.x_boundary = L.LBVE_X_PRESSURE
+            d.dp = d.rho0 * d.g[0] * d.nx
+            d.g[0] = 0.0
+        name += "_pressure"
+        notes = dict(notes, drive="pressure-step boundary along x, dp = rho0 g nx per period")
     hist = {"f32": L.LBVE_F32, "s16": L.LBVE_S16, "f64": L.LBVE_F64}[args.history]
     for d in descs:
         d.hist_storage = hist

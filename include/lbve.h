@@ -64,6 +64,16 @@ extern "C" {
                              takes the strain accumulated between t' and t, sum_{s=t'}^{t-1} gammadot(s),
                              in place of (t - t') gammadot(t').  History storage LBVE_F32 or LBVE_F64 */
 
+#define LBVE_X_PERIODIC 0 /* x (the flow axis) plainly periodic; the flow is driven by the body force g */
+#define LBVE_X_PRESSURE 1 /* pressure-step boundary along x (Sec. III: the generalised periodic boundary that
+                             fixes a constant pressure step between inlet and outlet of the periodic lattice).
+                             Populations crossing the seam stream from ghost images of the opposite boundary
+                             node: its post-collision non-equilibrium part on an equilibrium at the ghost
+                             density and the node's velocity.  The ghosts sit on the linear profile of a
+                             pressure drop dp per period (nx spacings) around rho0:
+                             rho_in/out = rho0 +- (dp / c_s^2) (nx + 1) / (2 nx).  Equivalent, in the
+                             incompressible limit, to g = dp / (rho0 nx); it also fixes the mean density */
+
 #define LBVE_FIELD_RHO   1u  /* [N]        hydrodynamic density of Eq. (hydrofields) */
 #define LBVE_FIELD_U     2u  /* [d][N]     velocity u = (sum c n + f/2)/rho */
 #define LBVE_FIELD_SIGMA 4u  /* [nsig][N]  sigma_struc of Eq. (gitt) */
@@ -91,6 +101,10 @@ typedef struct {
                                  channel of a batch.  LBVE_MODEL_WM with LBVE_S16, and differentiation
                                  (lbve_create_tangent / lbve_create_adjoint) of any model but
                                  LBVE_MODEL_NLM, return LBVE_ENOSUPPORT */
+    int32_t x_boundary;       /* LBVE_X_PERIODIC (0) | LBVE_X_PRESSURE; per channel */
+    double  dp;               /* LBVE_X_PRESSURE: pressure drop per period along x (lattice units, finite);
+                                 ignored for LBVE_X_PERIODIC.  Differentiation of a channel with
+                                 LBVE_X_PRESSURE returns LBVE_ENOSUPPORT */
 } lbve_channel_desc;
 
 typedef struct lbve lbve_t;   /* opaque; owns every device buffer of one channel or of a batch */
@@ -128,6 +142,13 @@ void lbve_destroy(lbve_t* h);
  * ordered: steps enqueued earlier on `stream` still use the old value, later steps the new one.
  */
 int lbve_set_force(lbve_t* h, int32_t channel, const double g[3], void* stream);
+
+/*
+ * Replace the pressure drop per period dp of the pressure-step boundary (LBVE_X_PRESSURE) of one channel
+ * (-1: all) -- startup / cessation with the pressure drive of Sec. III-IV.  Ordered like lbve_set_force.
+ * ESTATE when a selected channel was created with LBVE_X_PERIODIC; EINVAL for a non-finite dp.
+ */
+int lbve_set_pressure_step(lbve_t* h, int32_t channel, double dp, void* stream);
 
 /* Replace G_inf, tau, gamma_c of Eq. (nlmax) for one channel (-1: all); ordered like lbve_set_force. */
 int lbve_set_params(lbve_t* h, int32_t channel, double G_inf, double tau, double gamma_c, void* stream);

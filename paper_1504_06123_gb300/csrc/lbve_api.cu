@@ -168,6 +168,8 @@ void fill_chan(const lbve_channel_desc& d, int off, Chan* c) {
     c->G_inf = d.G_inf;
     c->inv_tau = 1.0 / d.tau;
     c->inv_gc = std::isinf(d.gamma_c) ? 0.0 : 1.0 / d.gamma_c;
+    c->xbc = d.x_boundary == LBVE_X_PRESSURE;
+    c->drho_gh = c->xbc ? 3.0 * d.dp * (d.nx + 1.0) / (2.0 * d.nx) : 0.0;   // (dp / c_s^2)(nx + 1)/(2 nx)
 }
 
 int check_desc(const lbve_channel_desc* d) {
@@ -193,6 +195,8 @@ int check_desc(const lbve_channel_desc* d) {
         d->hist_storage != LBVE_S16)
         return LBVE_EINVAL;
     if (d->model != LBVE_MODEL_NLM && d->model != LBVE_MODEL_INLM && d->model != LBVE_MODEL_WM) return LBVE_EINVAL;
+    if (d->x_boundary != LBVE_X_PERIODIC && d->x_boundary != LBVE_X_PRESSURE) return LBVE_EINVAL;
+    if (d->x_boundary == LBVE_X_PRESSURE && !std::isfinite(d->dp)) return LBVE_EINVAL;
     if (d->hist_storage == LBVE_BF16) return LBVE_ENOSUPPORT;
     if (d->model == LBVE_MODEL_WM && d->hist_storage == LBVE_S16) return LBVE_ENOSUPPORT;
     return LBVE_OK;
@@ -745,7 +749,7 @@ int create_tangent(const lbve_channel_desc* desc, const double* rho_init, lbve_t
     *out = nullptr;
     int rc = check_desc(desc);
     if (rc) return rc;
-    if (desc->model != LBVE_MODEL_NLM) return LBVE_ENOSUPPORT;
+    if (desc->model != LBVE_MODEL_NLM || desc->x_boundary != LBVE_X_PERIODIC) return LBVE_ENOSUPPORT;
     const long long Ntot = (long long)desc->nx * desc->ny * desc->nz;
     if (rho_init)
         for (long long i = 0; i < Ntot; ++i)
@@ -872,6 +876,22 @@ int lbve_set_force(lbve_t* h, int32_t channel, const double g[3], void* stream) 
             h->descs[c].g[a] = g[a];
             h->chan_host[c].f[a] = h->descs[c].rho0 * g[a];
         }
+        int rc = push_chan(h, c, (cudaStream_t)stream);
+        if (rc) return rc;
+    }
+    if (channel <= 0) h->d = h->descs[0];
+    return LBVE_OK;
+}
+
+int lbve_set_pressure_step(lbve_t* h, int32_t channel, double dp, void* stream) {
+    if (!h || channel < -1 || channel >= h->nchan || !std::isfinite(dp)) return LBVE_EINVAL;
+    if (h->tangent) return LBVE_ESTATE;
+    const int c0 = channel < 0 ? 0 : channel, c1 = channel < 0 ? h->nchan : channel + 1;
+    for (int c = c0; c < c1; ++c)
+        if (h->descs[c].x_boundary != LBVE_X_PRESSURE) return LBVE_ESTATE;
+    for (int c = c0; c < c1; ++c) {
+        h->descs[c].dp = dp;
+        fill_chan(h->descs[c], h->chan_host[c].off, &h->chan_host[c]);
         int rc = push_chan(h, c, (cudaStream_t)stream);
         if (rc) return rc;
     }
@@ -1104,7 +1124,7 @@ uint64_t config_fingerprint(const lbve* h) {
     mix(h->tangent); mix(h->nchan); mix(h->N); mix(h->L);
     for (const lbve_channel_desc& d : h->descs) {
         mix(d.lattice); mix(d.nx); mix(d.ny); mix(d.nz); mix(d.wall_z); mix(d.hist_C); mix(d.hist_B);
-        mix(d.hist_storage); mix(d.pop_precision); mix(d.trace_coupling); mix(d.model);
+        mix(d.hist_storage); mix(d.pop_precision); mix(d.trace_coupling); mix(d.model); mix(d.x_boundary);
     }
     return x;
 }
@@ -1330,7 +1350,7 @@ int lbve_create_adjoint(const lbve_channel_desc* desc, const double* rho_init, i
                         lbve_t** out) {
     if (!desc || !out || checkpoint_every < 1) return LBVE_EINVAL;
     if (desc->pop_precision != LBVE_F64 || desc->hist_storage != LBVE_F64) return LBVE_ENOSUPPORT;
-    if (desc->model != LBVE_MODEL_NLM) return LBVE_ENOSUPPORT;
+    if (desc->model != LBVE_MODEL_NLM || desc->x_boundary != LBVE_X_PERIODIC) return LBVE_ENOSUPPORT;
     int rc = create_impl(desc, 1, rho_init, out);
     if (rc) return rc;
     (*out)->rec_K = checkpoint_every;

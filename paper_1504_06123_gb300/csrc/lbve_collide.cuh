@@ -204,6 +204,11 @@ __global__ void __launch_bounds__(256) k_collide_stream(CollArgs<P> a, H h, Geom
 
     int x, y, z;
     node_xyz(p, n, x, y, z);
+    // the channel's geometry in registers: the population stores below may alias the channel table as far
+    // as the compiler can tell, which would reload every field after each store
+    const int cnx = p.nx, cny = p.ny, cnz = p.nz, coff = p.off;
+    const bool cwz = p.wall_z != 0, cxbc = p.xbc != 0;
+    const T cdgh = (T)p.drho_gh;
 #pragma unroll
     for (int q = 0; q < Q; ++q) {
         const int cq[3] = {L::cx(q), L::cy(q), L::cz(q)};
@@ -221,19 +226,30 @@ __global__ void __launch_bounds__(256) k_collide_stream(CollArgs<P> a, H h, Geom
                 }
             }
         }
-        const P post = (P)(keep * dn[q] + (T)L::w(q) * (a0 + cv + cMc));
+        T post_t = keep * dn[q] + (T)L::w(q) * (a0 + cv + cMc);
         // push with half-way bounce-back
-        int xd = x + cq[0];
-        xd = xd < 0 ? p.nx - 1 : (xd >= p.nx ? 0 : xd);
+        const int xs = x + cq[0];
+        const int xd = xs < 0 ? cnx - 1 : (xs >= cnx ? 0 : xs);
         const int yd = y + cq[1];
-        bool wall = yd < 0 || yd >= p.ny;
+        bool wall = yd < 0 || yd >= cny;
         int zd = z + cq[2];
         if (D == 3) {
-            if (p.wall_z) wall = wall || zd < 0 || zd >= p.nz;
-            else zd = zd < 0 ? p.nz - 1 : (zd >= p.nz ? 0 : zd);
+            if (cwz) wall = wall || zd < 0 || zd >= cnz;
+            else zd = zd < 0 ? cnz - 1 : (zd >= cnz ? 0 : zd);
         }
+        if (cq[0] != 0 && cxbc && !wall && xd != xs) {
+            // pressure-step boundary: a population crossing the seam streams from the ghost image
+            // n_eq(rho_ghost, u) + (n* - n_eq(rho, u)) = n* + w (rho_ghost - rho)(1 + 3 c.u + 4.5 (c.u)^2 - 1.5 u.u);
+            // the inlet ghost (rho0 + drho_gh) for +x, the outlet ghost (rho0 - drho_gh) for -x
+            T cu = 0;
+#pragma unroll
+            for (int r = 0; r < D; ++r) cu += cq[r] * u[r];
+            const T dgh = (cq[0] > 0 ? cdgh : -cdgh) - drho;
+            post_t += (T)L::w(q) * dgh * (T(1) + T(3) * cu + T(4.5) * cu * cu - T(1.5) * uu);
+        }
+        const P post = (P)post_t;
         if (wall) a.dn_out[L::opp(q) * Np + n] = post;
-        else a.dn_out[q * Np + (p.off + xd + p.nx * (yd + p.ny * zd))] = post;
+        else a.dn_out[q * Np + (coff + xd + cnx * (yd + cny * zd))] = post;
     }
     a.rho[n] = drho_d;
 #pragma unroll

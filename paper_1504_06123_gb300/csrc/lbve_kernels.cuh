@@ -87,6 +87,8 @@ struct Chan {
     double omega;     // BGK rate 1 / tau_lb
     double f[3];      // force density rho0 g
     double G_inf, inv_tau, inv_gc;
+    int xbc;          // 1: pressure-step boundary along x
+    double drho_gh;   // its ghost densities rho0 +- drho_gh (the linear profile of the pressure drop)
 };
 
 struct Geom {

@@ -24,6 +24,7 @@ LBVE_D2Q9, LBVE_D3Q19 = 9, 19
 LBVE_F32, LBVE_F64, LBVE_BF16, LBVE_S16 = 0, 1, 2, 3
 LBVE_TRACE_FULL, LBVE_TRACE_NONE = 0, 1
 LBVE_MODEL_NLM, LBVE_MODEL_INLM, LBVE_MODEL_WM = 0, 1, 2
+LBVE_X_PERIODIC, LBVE_X_PRESSURE = 0, 1
 LBVE_FIELD_RHO, LBVE_FIELD_U, LBVE_FIELD_SIGMA, LBVE_FIELD_KAPPA, LBVE_FIELD_N1 = 1, 2, 4, 8, 16
 
 # Every entry point declared in include/lbve.h (checked by the tests against the header).
@@ -33,7 +34,7 @@ EXPORTS = [
     "lbve_memory_bytes", "lbve_strerror", "lbve_last_cuda_error", "lbve_profile", "lbve_profile_read",
     "lbve_fields_host_fixed", "lbve_create_batch", "lbve_channel_nodes", "lbve_sweep_config",
     "lbve_create_tangent", "lbve_tangent_fields", "lbve_checkpoint_size", "lbve_checkpoint_save",
-    "lbve_checkpoint_restore", "lbve_create_adjoint", "lbve_backward",
+    "lbve_checkpoint_restore", "lbve_create_adjoint", "lbve_backward", "lbve_set_pressure_step",
 ]
 
 
@@ -43,7 +44,7 @@ class lbve_channel_desc(C.Structure):
         ("tau_lb", C.c_double), ("rho0", C.c_double), ("G_inf", C.c_double), ("tau", C.c_double),
         ("gamma_c", C.c_double), ("g", C.c_double * 3), ("hist_C", C.c_int32), ("hist_B", C.c_int32),
         ("hist_storage", C.c_int32), ("pop_precision", C.c_int32), ("trace_coupling", C.c_int32),
-        ("model", C.c_int32),
+        ("model", C.c_int32), ("x_boundary", C.c_int32), ("dp", C.c_double),
     ]
 
 
@@ -86,6 +87,7 @@ def load(path: str | None = None):
         lib.lbve_sweep_config.argtypes = [vp, C.POINTER(i32), C.POINTER(i32)]
         lib.lbve_set_force.argtypes = [vp, i32, dp, vp]
         lib.lbve_set_params.argtypes = [vp, i32, C.c_double, C.c_double, C.c_double, vp]
+        lib.lbve_set_pressure_step.argtypes = [vp, i32, C.c_double, vp]
         lib.lbve_step.argtypes = [vp, i64, vp]
         lib.lbve_get_time.argtypes = [vp, C.POINTER(i64)]
         lib.lbve_fields.argtypes = [vp, C.c_uint32, vp, i32, vp]
@@ -254,6 +256,10 @@ def lbve_set_force(h: int, g, channel: int = -1, stream=None) -> None:
     _check(load().lbve_set_force(h, channel, gg, _stream(stream)), "lbve_set_force")
 
 
+def lbve_set_pressure_step(h: int, dp: float, channel: int = -1, stream=None) -> None:
+    _check(load().lbve_set_pressure_step(h, channel, float(dp), _stream(stream)), "lbve_set_pressure_step")
+
+
 def lbve_set_params(h: int, G_inf: float, tau: float, gamma_c: float, channel: int = -1, stream=None) -> None:
     _check(load().lbve_set_params(h, channel, G_inf, tau, gamma_c, _stream(stream)), "lbve_set_params")
 
@@ -338,7 +344,8 @@ def lbve_profile_read(h: int):
 # ---- convenience wrapper ---------------------------------------------------------------------------
 def make_desc(lattice=LBVE_D2Q9, nx=4, ny=32, nz=1, *, tau_lb=0.9, rho0=1.0, G_inf=0.01, tau=200.0,
               gamma_c=0.1, g=(0.0, 0.0, 0.0), C=128, B=1, precision=LBVE_F32, hist_storage=None,
-              trace_coupling=LBVE_TRACE_FULL, wall_z=1, model=LBVE_MODEL_NLM) -> lbve_channel_desc:
+              trace_coupling=LBVE_TRACE_FULL, wall_z=1, model=LBVE_MODEL_NLM, dp=None) -> lbve_channel_desc:
+    """dp = None: x periodic, driven by g; a number: the pressure-step boundary with drop dp per period."""
     d = lbve_channel_desc()
     d.lattice, d.nx, d.ny, d.nz, d.wall_z = lattice, nx, ny, nz, wall_z
     d.tau_lb, d.rho0, d.G_inf, d.tau = tau_lb, rho0, G_inf, tau
@@ -349,6 +356,8 @@ def make_desc(lattice=LBVE_D2Q9, nx=4, ny=32, nz=1, *, tau_lb=0.9, rho0=1.0, G_i
     d.hist_storage = precision if hist_storage is None else hist_storage
     d.trace_coupling = trace_coupling
     d.model = model
+    d.x_boundary = LBVE_X_PERIODIC if dp is None else LBVE_X_PRESSURE
+    d.dp = 0.0 if dp is None else float(dp)
     return d
 
 
@@ -388,6 +397,9 @@ class Channel:
 
     def set_force(self, g, channel: int = -1, stream=None):
         lbve_set_force(self.h, g, channel, stream)
+
+    def set_pressure_step(self, dp, channel: int = -1, stream=None):
+        lbve_set_pressure_step(self.h, dp, channel, stream)
 
     def set_params(self, G_inf, tau, gamma_c, channel: int = -1, stream=None):
         lbve_set_params(self.h, G_inf, tau, gamma_c, channel, stream)

@@ -70,6 +70,30 @@ def test_unsupported_variant_combinations_are_refused_before_any_device_work():
     assert e.value.status == L.LBVE_EINVAL
 
 
+def test_pressure_boundary_arguments_are_checked_before_any_device_work():
+    import ctypes
+    bad = L.make_desc(nx=2, ny=4, C=8, B=2, dp=float("nan"))
+    with pytest.raises(L.LbveError) as e:
+        L.lbve_create(bad)
+    assert e.value.status == L.LBVE_EINVAL
+    d = L.make_desc(nx=2, ny=4, C=8, B=2)
+    d.x_boundary = 2
+    with pytest.raises(L.LbveError) as e:
+        L.lbve_create(d)
+    assert e.value.status == L.LBVE_EINVAL
+    p = L.make_desc(nx=2, ny=4, C=8, B=2, precision=L.LBVE_F64, dp=1e-6)
+    for fn in (L.lbve_create_tangent, L.lbve_create_adjoint):
+        with pytest.raises(L.LbveError) as e:
+            fn(p)
+        assert e.value.status == L.LBVE_ENOSUPPORT
+    with pytest.raises(L.LbveError) as e:
+        L.lbve_set_pressure_step(0, 1e-6)
+    assert e.value.status == L.LBVE_EINVAL
+    # the C layout: dp follows x_boundary at an 8-byte boundary
+    assert L.lbve_channel_desc.dp.offset % 8 == 0
+    assert ctypes.sizeof(L.lbve_channel_desc) == L.lbve_channel_desc.dp.offset + 8
+
+
 def test_create_rejects_nonfinite_density():
     d = L.make_desc(nx=2, ny=4, C=8, B=1)
     rho = np.ones(8)

@@ -48,9 +48,10 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-chosen", action="store_true", help="skip the reduced-precision comparison run")
-    ap.add_argument("--workload", choices=["channel", "batched", "duct"], default="channel",
+    ap.add_argument("--workload", choices=["channel", "batched", "duct", "regime"], default="channel",
                     help="channel: the 1024 x 512 D2Q9 channel (the benchmark line); batched: 64 channels of "
-                         "uneven width; duct: the D3Q19 128^3 square duct")
+                         "uneven width; duct: the D3Q19 128^3 square duct; regime: the paper's transient sweep "
+                         "(ten channels of Figs. Qall and figtau in one batch, probes recorded every step)")
     ap.add_argument("--history", choices=["f32", "s16", "f64"], default="f32",
                     help="history storage: f32 (plain FP32 form), s16 (16-bit block-scaled precision variant), f64")
     ap.add_argument("--model", choices=["nlm", "wm", "inlm"], default="nlm",
@@ -249,6 +250,17 @@ def workload_descs(args, L, configs):
         return f"duct_{w.nx}x{w.ny}x{w.nz}_L{w.L}" + ("_wm" if args.model == "wm" else ""), [w.desc()], w.rho_init(), {
             "lattice": "D3Q19", "blocks_B": w.B, "block_C": w.C, "tau_lb": w.tau_lb, "G_inf": w.G_inf, "tau": w.tau,
             "gamma_c": w.gamma_c, "g": w.g}
+    if args.workload == "regime":
+        from paper_1504_06123_gb300 import regime
+        pts = regime.paper_points()
+        chans, descs, B = regime.sweep_descs(pts, regime.tau0_for_width(100), nx=4)
+        for d in descs:
+            d.model = model
+        return f"paper_regime_{len(descs)}_channels_L{B * descs[0].hist_C}", descs, None, {
+            "lattice": "D2Q9", "channels": len(descs), "widths": [c.ny for c in chans], "nx": 4,
+            "t_wall_over_tau0": [c.ratio for c in chans], "theta": [c.theta for c in chans],
+            "blocks_B": B, "block_C": descs[0].hist_C,
+            "probes": "u, rho, sigma at the two nodes around y/H = 0.51 of every channel, recorded every step"}
     ws = configs.batched_channels()
     for w in ws:
         w.model = model
@@ -315,6 +327,14 @@ def run_ours(args, rank, world, local_rank):
     stream = torch.cuda.current_stream()
     ch = L.Channel(descs if len(descs) > 1 else descs[0], rho)
     K, W = args.steps, args.warmup
+    probes = 0
+    if args.workload == "regime":
+        from paper_1504_06123_gb300 import regime
+        chans = [regime.regime_channel(r, th, d.ny) for (r, th), d in zip(regime.paper_points(), descs)]
+        offs = [L.lbve_channel_nodes(ch.h, k)[0] for k in range(len(descs))]
+        pnodes, _ = regime.probe_plan(chans, offs, descs[0].nx)
+        probes = len(pnodes)
+        L.lbve_set_probes(ch.h, pnodes, 1, W + K + max(8, min(K, 64)) + 1)
     ch.step(W, stream)
     torch.cuda.synchronize()
     if inst:
@@ -469,8 +489,14 @@ def run_ours(args, rank, world, local_rank):
         torch.cuda.synchronize()
         t0 = time.perf_counter()
         h = L.lbve_create_batch(descs, rho) if len(descs) > 1 else L.lbve_create(d0, rho)
+        probe_bytes = 0
+        if probes:   # the sweep as a user runs it: probes recorded every step, read back at the end
+            L.lbve_set_probes(h, pnodes, 1, K)
         L.lbve_step(h, K, stream)
         rc = L.load().lbve_fields(h, mask, host.data_ptr(), 0, int(stream.cuda_stream) or None)
+        if probes and rc == 0:
+            _, pv, _ = L.lbve_probe_read(h, probes, D, K, stream)
+            probe_bytes = 8 * (pv.size + len(pv))
         torch.cuda.synchronize()
         dt = max_over_ranks(time.perf_counter() - t0)
         L.lbve_destroy(h)
@@ -479,8 +505,9 @@ def run_ours(args, rank, world, local_rank):
         upd_e = N * K if inst else N * sum(points_per_step(d0.hist_C, d0.hist_B, 0, K, L))
         e2e = {"value": upd_e * world / dt, "unit": metric,
                "h2d_bytes_per_step": (8 * N if rho is not None else 0) / K,
-               "d2h_bytes_per_step": 8 * host.numel() / K, "steps": K,
-               "includes": "create (allocation, autotune, initial density upload), K steps, field read, destroy"}
+               "d2h_bytes_per_step": (8 * host.numel() + probe_bytes) / K, "steps": K,
+               "includes": "create (allocation, autotune, initial density upload), K steps, field read" +
+                           (", probe records read" if probes else "") + ", destroy"}
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline and args.workload == "channel":
@@ -515,7 +542,7 @@ def run_ours(args, rank, world, local_rank):
                                      "collide_stream": kms[2] / max(launches[2], 1)},
             "roofline": roofline,
             "clocks": clocks,
-            "gpu_launches": (2 if inst else 3) * K,
+            "gpu_launches": ((2 if inst else 3) + (1 if probes else 0)) * K,
             "e2e": e2e,
             "cpu_baseline": cpu,
         }

@@ -179,6 +179,31 @@ int lbve_fields(lbve_t* h, uint32_t field_mask, double* dst, int32_t dst_is_devi
 int lbve_fields_count(const lbve_t* h, uint32_t field_mask, size_t* count);
 
 /*
+ * Probe time series (Sec. IV: the transients of Figs. Qall, QT and figtau are the velocity, shear stress
+ * and normal-stress difference at one wall distance y/H of each channel, recorded through startup and
+ * cessation).  Set n_probes node indices (host array `nodes`, the node numbering of lbve_fields; for a
+ * batch the batch-wide index, channel offset from lbve_channel_nodes plus the in-channel index); from
+ * then on every step whose completed-step count t (lbve_get_time after the step) is a multiple of
+ * `every` appends one record, written on the device by a small kernel launched after each step (and
+ * captured in the step graphs), so recording needs no host round trip.  A record is
+ *   [t, then for each probe: rho, u[d], sigma[nsig]]      (1 + n_probes (1 + d + nsig) doubles),
+ * the same values lbve_fields returns at step t.  The handle owns a device buffer of `capacity` records;
+ * records past it are counted but not stored.  Setting probes clears earlier records; n_probes = 0
+ * removes the recorder.  Synchronises the device (the step graphs are re-captured).
+ * Errors: EINVAL (a node index outside 0..N-1, n_probes < 0 or > 65536, every < 1, capacity < 1 when
+ * n_probes > 0), ENOMEM, ENOSUPPORT for tangent and adjoint handles.
+ */
+int lbve_set_probes(lbve_t* h, int32_t n_probes, const int64_t* nodes, int32_t every, int64_t capacity);
+
+/*
+ * Copy the stored probe records to host memory `dst_host` (room for `capacity` records of the layout
+ * above, caller-owned).  *n_stored = records copied (at most capacity), *n_total = records taken since
+ * lbve_set_probes (n_total > n_stored means the buffer overflowed).  Synchronises `stream`.
+ * Errors: EINVAL (no recorder set), ECUDA.
+ */
+int lbve_probe_read(lbve_t* h, double* dst_host, int64_t* n_stored, int64_t* n_total, void* stream);
+
+/*
  * Test hook for the stress history alone (steps of Sec. III on a prescribed gradient): advance every
  * node's history by one step with kappa(t) taken from kappa_dev (device, [d*d][N] doubles) instead of
  * the finite differences of the flow, and write sigma_struc(t) to sigma_dev (device, [nsig][N]

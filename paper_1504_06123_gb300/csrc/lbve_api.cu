@@ -84,6 +84,13 @@ struct lbve {
     int64_t t_host = 0;
     size_t bytes = 0;
     int* flag = nullptr;       // non-finite flag of lbve_fields
+    // probe recorder (lbve_set_probes): records [cap][1 + probe_n (1 + D + NS)] appended after steps
+    int probe_n = 0;
+    int probe_every = 1;
+    long long probe_cap = 0;
+    long long* probe_nodes = nullptr;   // [probe_n] node indices
+    double* probe_rec = nullptr;        // [probe_cap][record] records
+    long long* probe_cnt = nullptr;     // records taken (may exceed probe_cap)
     // captured steps: kGraphSteps steps, both population parities (the graph is replayed from cur == 0)
     cudaGraphExec_t graph = nullptr;
     cudaStream_t graph_stream = nullptr;
@@ -104,7 +111,7 @@ namespace {
 void free_all(lbve* h) {
     void* ptrs[] = {h->pops[0], h->pops[1], h->u_raw, h->u, h->rho, h->sigma, h->kappa, h->tr_prev,
                     h->X, h->K, h->part, h->t_dev, h->red, h->stage, h->flag, h->chan_dev, h->chan_of,
-                    h->Qe, h->Ke, h->Rm, h->gam_node, h->gam_pt};
+                    h->Qe, h->Ke, h->Rm, h->gam_node, h->gam_pt, h->probe_nodes, h->probe_rec, h->probe_cnt};
     for (void* p : ptrs)
         if (p) cudaFree(p);
     for (cudaEvent_t e : h->ev_pool) cudaEventDestroy(e);
@@ -308,6 +315,10 @@ int sweep_autotune(lbve* h) {
         S = std::max(1ll, std::min(S, Smax));
         if (std::find(cand.begin(), cand.end(), S) == cand.end()) cand.push_back(S);
     }
+    // few nodes: the tasks above all hit Smax; fewer, longer chunks trade sweep parallelism for a
+    // shorter reduction in the commit
+    for (long long S = 8; S < Smax; S *= 2)
+        if (std::find(cand.begin(), cand.end(), S) == cand.end()) cand.push_back(S);
     const long long Sbig = *std::max_element(cand.begin(), cand.end());
     int rc = alloc(h, &h->part, h->hesz * (size_t)Sbig * h->NS * h->Npad);
     if (rc) return rc;
@@ -324,8 +335,14 @@ int sweep_autotune(lbve* h) {
             h->sweep_grid = (int)std::max(1ll, std::min(grid_full, (tiles * S + 7) / 8));
             if ((rc = launch_sweep_any<D, HK>(h, 0))) return rc;   // warm-up
             LBVE_CUDA(cudaEventRecord(e0, 0));
-            for (int r = 0; r < 3; ++r)
+            for (int r = 0; r < 3; ++r) {
                 if ((rc = launch_sweep_any<D, HK>(h, 0))) return rc;
+                if (h->hist_dbl)
+                    k_part_read<double><<<(h->N + 255) / 256, 256>>>((const double*)h->part, (int)S, h->NS, h->Npad, h->N, h->red);
+                else
+                    k_part_read<float><<<(h->N + 255) / 256, 256>>>((const float*)h->part, (int)S, h->NS, h->Npad, h->N, h->red);
+                LBVE_CUDA(cudaGetLastError());
+            }
             LBVE_CUDA(cudaEventRecord(e1, 0));
             LBVE_CUDA(cudaEventSynchronize(e1));
             float ms = 0.f;
@@ -399,6 +416,12 @@ int one_step(lbve* h, int cur, cudaStream_t s) {
     else k_collide_stream<Q, P, T, CommitArgs<float>><<<grid, 256, 0, s>>>(c, commit_args<float>(h), g);
     LBVE_CUDA(cudaGetLastError());
     if ((rc = prof_mark(h, s, KIND_COLLIDE, false))) return rc;
+    if (h->probe_n > 0) {
+        k_probe<<<1, 256, 0, s>>>((const double*)h->rho, (const double*)h->u, (const double*)h->sigma, h->Npad, D,
+                                  h->NS, h->probe_nodes, h->probe_n, h->d.rho0, h->t_dev, h->probe_every,
+                                  h->probe_cap, h->probe_rec, h->probe_cnt);
+        LBVE_CUDA(cudaGetLastError());
+    }
     return LBVE_OK;
 }
 
@@ -962,6 +985,75 @@ int lbve_get_time(const lbve_t* h, int64_t* t) {
 int lbve_fields_count(const lbve_t* h, uint32_t mask, size_t* count) {
     if (!h || !count || (mask & ~31u)) return LBVE_EINVAL;
     *count = fields_count(h, mask);
+    return LBVE_OK;
+}
+
+int lbve_set_probes(lbve_t* h, int32_t n_probes, const int64_t* nodes, int32_t every, int64_t capacity) {
+    if (!h || n_probes < 0 || n_probes > 65536) return LBVE_EINVAL;
+    if (h->tangent || h->rec_K) return LBVE_ENOSUPPORT;
+    if (n_probes > 0) {
+        if (!nodes || every < 1 || capacity < 1) return LBVE_EINVAL;
+        for (int i = 0; i < n_probes; ++i)
+            if (nodes[i] < 0 || nodes[i] >= h->N) return LBVE_EINVAL;
+        const long long rec = 1 + (long long)n_probes * (1 + h->D + h->NS);
+        if (capacity > (1ll << 40) / (rec * (long long)sizeof(double))) return LBVE_EINVAL;   // 8 TiB: nonsense
+    }
+    // the step graphs launch the recorder with the old buffers: let them finish, then re-capture
+    LBVE_CUDA(cudaDeviceSynchronize());
+    if (h->graph) {
+        cudaGraphExecDestroy(h->graph);
+        h->graph = nullptr;
+    }
+    void* old[] = {h->probe_nodes, h->probe_rec, h->probe_cnt};
+    const size_t old_bytes = h->probe_cap > 0 ? sizeof(long long) * (h->probe_n + 1) +
+                                                    sizeof(double) * (size_t)h->probe_cap *
+                                                        (1 + (size_t)h->probe_n * (1 + h->D + h->NS))
+                                              : 0;
+    for (void* p : old)
+        if (p) cudaFree(p);
+    h->bytes -= old_bytes;
+    h->probe_nodes = nullptr;
+    h->probe_rec = nullptr;
+    h->probe_cnt = nullptr;
+    h->probe_n = 0;
+    h->probe_cap = 0;
+    if (n_probes == 0) return LBVE_OK;
+    const size_t rec = 1 + (size_t)n_probes * (1 + h->D + h->NS);
+    int rc;
+    if ((rc = alloc(h, (void**)&h->probe_nodes, sizeof(long long) * n_probes)) ||
+        (rc = alloc(h, (void**)&h->probe_rec, sizeof(double) * rec * (size_t)capacity)) ||
+        (rc = alloc(h, (void**)&h->probe_cnt, sizeof(long long)))) {
+        for (void* p : {(void*)h->probe_nodes, (void*)h->probe_rec, (void*)h->probe_cnt})
+            if (p) cudaFree(p);
+        h->probe_nodes = nullptr;
+        h->probe_rec = nullptr;
+        h->probe_cnt = nullptr;
+        return rc;
+    }
+    std::vector<long long> nn(nodes, nodes + n_probes);
+    LBVE_CUDA(cudaMemcpy(h->probe_nodes, nn.data(), sizeof(long long) * n_probes, cudaMemcpyHostToDevice));
+    LBVE_CUDA(cudaMemset(h->probe_cnt, 0, sizeof(long long)));
+    h->probe_n = n_probes;
+    h->probe_every = every;
+    h->probe_cap = capacity;
+    return LBVE_OK;
+}
+
+int lbve_probe_read(lbve_t* h, double* dst_host, int64_t* n_stored, int64_t* n_total, void* stream) {
+    if (!h || !dst_host || !n_stored || !n_total) return LBVE_EINVAL;
+    if (h->probe_n == 0) return LBVE_EINVAL;
+    cudaStream_t s = (cudaStream_t)stream;
+    long long cnt = 0;
+    LBVE_CUDA(cudaMemcpyAsync(&cnt, h->probe_cnt, sizeof cnt, cudaMemcpyDeviceToHost, s));
+    LBVE_CUDA(cudaStreamSynchronize(s));
+    const long long k = cnt < h->probe_cap ? cnt : h->probe_cap;
+    const size_t rec = 1 + (size_t)h->probe_n * (1 + h->D + h->NS);
+    if (k > 0) {
+        LBVE_CUDA(cudaMemcpyAsync(dst_host, h->probe_rec, sizeof(double) * rec * (size_t)k, cudaMemcpyDeviceToHost, s));
+        LBVE_CUDA(cudaStreamSynchronize(s));
+    }
+    *n_stored = k;
+    *n_total = cnt;
     return LBVE_OK;
 }
 

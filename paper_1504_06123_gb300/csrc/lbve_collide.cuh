@@ -281,6 +281,35 @@ __global__ void k_n1(const real* __restrict__ sigma, long long Npad, int N, doub
     if (!isfinite(v)) atomicOr(nonfinite, 1);
 }
 
+// Probe recorder (lbve_set_probes): after the step that completes t = t_dev + 1 steps, when t is a
+// multiple of `every`, append [t, per probe: rho, u[D], sigma[NS]] as record *cnt (stored while
+// *cnt < cap; the count goes on so that the host can see an overflow).  One block; every thread reads
+// the count before the barrier, thread 0 advances it after.
+__global__ void k_probe(const double* __restrict__ rho, const double* __restrict__ u,
+                        const double* __restrict__ sigma, long long Npad, int D, int NS,
+                        const long long* __restrict__ nodes, int P, double rho0, const long long* t_dev,
+                        int every, long long cap, double* __restrict__ rec, long long* cnt) {
+    const long long t = *t_dev + 1;
+    if (t % every != 0) return;
+    const long long k = *cnt;
+    const int PV = 1 + D + NS;
+    if (k < cap) {
+        double* r = rec + k * (1 + (long long)P * PV);
+        for (int i = threadIdx.x; i < P * PV; i += blockDim.x) {
+            const int p = i / PV, v = i - p * PV;
+            const long long n = nodes[p];
+            double x;
+            if (v == 0) x = rho[n] + rho0;                       // stored as rho - rho0
+            else if (v <= D) x = u[(v - 1) * Npad + n];
+            else x = sigma[(v - 1 - D) * Npad + n];
+            r[1 + i] = x;
+        }
+        if (threadIdx.x == 0) r[0] = (double)t;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) *cnt = k + 1;
+}
+
 template <typename real>
 __global__ void k_sum(const real* __restrict__ src, long long Npad, int ncomp, int N, double scale,
                       double* __restrict__ out) {

@@ -453,6 +453,19 @@ __global__ void __launch_bounds__(256, 2) k_sweep(SweepArgs<R> a, Geom g) {
     }
 }
 
+// Autotuning aid: the commit's read of the chunk partials (one thread per node, chunks in order), so
+// that the tuner weighs a slot-chunk count S by the sweep plus the reduction it causes in the commit.
+template <typename R>
+__global__ void k_part_read(const R* __restrict__ part, int S, int NS, long long Np, int N, double* sink) {
+    const int n = blockIdx.x * blockDim.x + threadIdx.x;
+    if (n >= N) return;
+    double acc = 0.0;
+#pragma unroll 4
+    for (int c = 0; c < S; ++c)
+        for (int i = 0; i < NS; ++i) acc += (double)part[((long long)c * NS + i) * Np + n];
+    if (acc == 1.2345e300) *sink = acc;   // keeps the loads; the all-rest history sums to 0
+}
+
 // ------------------------------------------------------------------------------------------------
 // History commit of one node (after the sweep): sigma_struc(t) from the chunk partials plus the point
 // created now (age 0, E = 1, weight 1/2, modulus G_inf), then the block merges (coarsest first, so every
@@ -489,6 +502,7 @@ __device__ __forceinline__ void hist_commit(const CommitArgs<R>& a, const BlockS
     double acc[NS];
 #pragma unroll
     for (int i = 0; i < NS; ++i) acc[i] = 0.0;
+#pragma unroll 4
     for (int c = 0; c < a.S; ++c)
 #pragma unroll
         for (int i = 0; i < NS; ++i) acc[i] += (double)a.part[((long long)c * NS + i) * Np + n];
@@ -731,6 +745,7 @@ __device__ __forceinline__ void hist_commit_any(const CommitS16& a, const BlockS
     double acc[NS], P[NS];
 #pragma unroll
     for (int i = 0; i < NS; ++i) P[i] = 0.0;
+#pragma unroll 4
     for (int c = 0; c < a.S; ++c)
 #pragma unroll
         for (int i = 0; i < NS; ++i) P[i] += (double)a.part[((long long)c * NS + i) * Np + n];

@@ -35,6 +35,7 @@ EXPORTS = [
     "lbve_fields_host_fixed", "lbve_create_batch", "lbve_channel_nodes", "lbve_sweep_config",
     "lbve_create_tangent", "lbve_tangent_fields", "lbve_checkpoint_size", "lbve_checkpoint_save",
     "lbve_checkpoint_restore", "lbve_create_adjoint", "lbve_backward", "lbve_set_pressure_step",
+    "lbve_set_probes", "lbve_probe_read",
 ]
 
 
@@ -99,6 +100,8 @@ def load(path: str | None = None):
         lib.lbve_strerror.argtypes = [C.c_int]
         lib.lbve_strerror.restype = C.c_char_p
         lib.lbve_fields_host_fixed.argtypes = [vp, C.c_uint32, vp, vp]
+        lib.lbve_set_probes.argtypes = [vp, i32, C.POINTER(i64), i32, i64]
+        lib.lbve_probe_read.argtypes = [vp, dp, C.POINTER(i64), C.POINTER(i64), vp]
         lib.lbve_profile.argtypes = [vp, i32]
         lib.lbve_profile_read.argtypes = [vp, dp, C.POINTER(i64)]
         lib.lbve_last_cuda_error.argtypes = []
@@ -300,6 +303,27 @@ def lbve_fields_host_fixed(h: int, mask: int, stream=None) -> np.ndarray:
     out = np.empty(lbve_fields_count(h, mask), dtype=np.float64)
     _check(load().lbve_fields_host_fixed(h, mask, out.ctypes.data, _stream(stream)), "lbve_fields_host_fixed")
     return out
+
+
+def lbve_set_probes(h: int, nodes, every: int = 1, capacity: int = 1) -> None:
+    """Record [t, per node: rho, u[d], sigma[nsig]] after every step whose count t is a multiple of
+    `every` (device-side, inside the step graphs); `nodes` are node indices (empty: remove the recorder)."""
+    nn = np.ascontiguousarray(np.asarray(nodes, dtype=np.int64).ravel())
+    ptr = nn.ctypes.data_as(C.POINTER(C.c_int64)) if nn.size else None
+    _check(load().lbve_set_probes(h, int(nn.size), ptr, int(every), int(capacity)), "lbve_set_probes")
+
+
+def lbve_probe_read(h: int, n_probes: int, d: int, capacity: int, stream=None):
+    """(t [k], values [k, n_probes, 1 + d + nsig], n_total) of the stored probe records (k <= capacity;
+    n_total > k means records were dropped).  Synchronising."""
+    nsig = 3 if d == 2 else 6
+    rec = 1 + n_probes * (1 + d + nsig)
+    out = np.empty((capacity, rec), dtype=np.float64)
+    k, tot = C.c_int64(), C.c_int64()
+    _check(load().lbve_probe_read(h, out.ctypes.data_as(C.POINTER(C.c_double)), C.byref(k), C.byref(tot),
+                                  _stream(stream)), "lbve_probe_read")
+    out = out[: k.value]
+    return out[:, 0].astype(np.int64), out[:, 1:].reshape(k.value, n_probes, 1 + d + nsig).copy(), tot.value
 
 
 def lbve_history_apply(h: int, kappa_dev, sigma_dev, stream=None) -> None:

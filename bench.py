@@ -146,16 +146,19 @@ def kernel_hash(files=("lbve_kernels.cuh", "lbve_sched.cuh")) -> str:
     return h.hexdigest()[:16]
 
 
-PROFILE_OF = {"nlm": "sweep_channel_1024x512_L1024.md", "wm": "sweep_wm_channel_1024x512_L1024.md",
-              "inlm": "collide_inlm_channel_4096x512.md"}
+PROFILE_OF = {("channel", "nlm"): "sweep_channel_1024x512_L1024.md",
+              ("channel", "wm"): "sweep_wm_channel_1024x512_L1024.md",
+              ("channel", "inlm"): "collide_inlm_channel_4096x512.md",
+              ("regime", "nlm"): "sweep_regime_10_channels_L1920.md"}
 
 
-def recorded_profile(model: str = "nlm") -> dict:
+def recorded_profile(model: str = "nlm", workload: str = "channel") -> dict:
     """Figures of the committed ncu summary of the dominant kernel (dram_bytes_per_launch, and for an
     ALU-bound kernel fp64_thread_inst_per_node), if it was taken on the current source of that kernel (the
     summary names the source files its hash covers); {} otherwise."""
-    p = os.path.join(ROOT, "profiles", PROFILE_OF[model])
-    if not os.path.exists(p):
+    name = PROFILE_OF.get((workload, model))
+    p = os.path.join(ROOT, "profiles", name) if name else ""
+    if not name or not os.path.exists(p):
         return {}
     kh, files, out = None, ("lbve_kernels.cuh", "lbve_sched.cuh"), {}
     for line in open(p):
@@ -169,8 +172,8 @@ def recorded_profile(model: str = "nlm") -> dict:
     return out if kh == kernel_hash(files) else {}
 
 
-def recorded_traffic(model: str = "nlm"):
-    return recorded_profile(model).get("dram_bytes_per_launch")
+def recorded_traffic(model: str = "nlm", workload: str = "channel"):
+    return recorded_profile(model, workload).get("dram_bytes_per_launch")
 
 
 def channel_workload(model: str):
@@ -377,9 +380,9 @@ def run_ours(args, rank, world, local_rank):
         pts_p = points_per_step(d0.hist_C, d0.hist_B, W + K, Kp, L)
         alg_bytes = bytes_per_update * N * (sum(pts_p) - Kp) / Kp   # the new point is not read from memory
         achieved = alg_bytes / (hist_ms / 1e3) / 1e9
-        roof_kernel = "k_sweep"
+        roof_kernel = "k_sweep_s16" if d0.hist_storage == L.LBVE_S16 else "k_sweep"
         state_bytes = alg_bytes
-    prof = recorded_profile(args.model) if args.workload == "channel" and not args.nx else {}
+    prof = recorded_profile(args.model, args.workload) if not args.nx and args.history == "f32" else {}
     traffic = prof.get("dram_bytes_per_launch")
     roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
                 "traffic": traffic, "peak_kind": peak_kind, "kernel": roof_kernel,
@@ -394,7 +397,7 @@ def run_ours(args, rank, world, local_rank):
                     f"{sms} SMs x sampled SM clock", "kernel": roof_kernel,
                     "fp64_thread_inst_per_node": prof["fp64_thread_inst_per_node"],
                     "hbm_frac": achieved / peak, "algorithmic_bytes_per_launch": alg_bytes}
-    S, ctas = L.lbve_sweep_config(ch.h)
+    S, ctas, cta_tasks = L.lbve_sweep_config(ch.h) if not inst else (0, 0, 0)
     ch.close()
 
     extra = {}
@@ -536,7 +539,8 @@ def run_ours(args, rank, world, local_rank):
                             "l2": ("no flush: per-step state (" + ("populations" if inst else "history") +
                                    f", {state_bytes / 1e6:.0f} MB) larger than the 129 MB L2")
                                   if state_bytes > 2.5e8 else "state fits in L2 (latency-bound size)",
-                            "sweep": {"slot_chunks": S, "ctas": ctas}}, **notes),
+                            "sweep": {"slot_chunks": S, "ctas": ctas, "tasks": "cta" if cta_tasks else "warp"}},
+                           **notes),
             "mlups": mlups,
             "kernel_ms_per_launch": {"moments": kms[0] / max(launches[0], 1), "history": hist_ms,
                                      "collide_stream": kms[2] / max(launches[2], 1)},

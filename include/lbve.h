@@ -268,9 +268,20 @@ int lbve_memory_bytes(const lbve_t* h, size_t* bytes);
 
 /*
  * Launch shape of the history sweep chosen at create by the autotuner: the number of slot chunks each
- * node's points are split into (tasks = node tiles x chunks) and the number of persistent CTAs.
+ * node's points are split into (tasks = node tiles x chunks), the number of persistent CTAs, and the task
+ * mode (*cta_tasks = 0: a task is one warp's; 1: a task is one CTA's, its warps splitting the chunk).
+ * The shape fixes the order in which the trapezoidal sum of Eq. (gitt) is added up: results are bitwise
+ * reproducible for a given shape, and differ in the last bits between shapes.
  */
-int lbve_sweep_config(const lbve_t* h, int32_t* slot_chunks, int32_t* ctas);
+int lbve_sweep_config(const lbve_t* h, int32_t* slot_chunks, int32_t* ctas, int32_t* cta_tasks);
+
+/*
+ * Replace the autotuned launch shape (for bitwise-reproducible runs across handles, whose autotuner may
+ * choose differently): slot_chunks in 1 .. max(1, B*C/8), cta_tasks 0 or 1 (1 only with an FP32 or FP64
+ * history).  Synchronises the device; the step graphs are re-captured.  EINVAL outside those ranges,
+ * ENOSUPPORT for a handle without a history sweep (instantaneous model, tangent and adjoint handles).
+ */
+int lbve_set_sweep_config(lbve_t* h, int32_t slot_chunks, int32_t cta_tasks);
 
 /*
  * Kernel timing for benchmarks: with enable = 1, every later lbve_step records a CUDA event pair on

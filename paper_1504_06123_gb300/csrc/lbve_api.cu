@@ -77,6 +77,9 @@ struct lbve {
     void* gam_pt = nullptr;    //                     Gamma(t') of every point [L][Npad] (double)
     int S = 1;                 // slot chunks of the sweep (autotuned at create)
     int sweep_grid = 0;        // persistent CTAs of the sweep
+    int sweep_cta = 0;         // k_sweep task mode: 0 warp tasks, 1 CTA tasks (autotuned at create)
+    int sweep_grid_full = 0;   // resident CTAs of the sweep on this device (SMs x CTAs per SM)
+    int part_S = 0;            // slot chunks the partial-sum buffer holds
     long long* t_dev = nullptr;
     double* red = nullptr;     // reduction scratch (2 doubles)
     double* stage = nullptr;   // lbve_fields staging for host destinations
@@ -230,12 +233,13 @@ int launch_sweep(lbve* h, cudaStream_t s) {
     a.B = h->d.hist_B;
     a.C = h->d.hist_C;
     a.S = h->S;
+    a.cta_tasks = h->sweep_cta;
     a.gam_node = (const double*)h->gam_node;
     a.gam_pt = (const double*)h->gam_pt;
     if (h->model == LBVE_MODEL_WM)
-        k_sweep<D, R, VN, true><<<h->sweep_grid, 256, sweep_smem_bytes(h->L), s>>>(a, geom_of(h));
+        k_sweep<D, R, VN, true><<<h->sweep_grid, 256, sweep_cta_smem_bytes(h->L), s>>>(a, geom_of(h));
     else
-        k_sweep<D, R, VN, false><<<h->sweep_grid, 256, sweep_smem_bytes(h->L), s>>>(a, geom_of(h));
+        k_sweep<D, R, VN, false><<<h->sweep_grid, 256, sweep_cta_smem_bytes(h->L), s>>>(a, geom_of(h));
     LBVE_CUDA(cudaGetLastError());
     return LBVE_OK;
 }
@@ -290,15 +294,17 @@ template <int D> struct SweepKernel<D, 2> {
     static const void* fn(bool) { return (const void*)k_sweep_s16<D, VN>; }
 };
 
-// Autotuner of the sweep: candidate slot-chunk counts S (tasks per resident warp from about 2 to 32),
-// each timed over a few launches on the freshly created, all-rest history (which the sweep leaves
-// unchanged: exp(0) - 1 = 0); the fastest is kept.  The partial-sum buffer is sized for the largest
-// candidate and then trimmed by reallocation.
+// Autotuner of the sweep: candidate (task mode, slot-chunk count S) pairs -- warp tasks with about 2 to
+// 32 tasks per resident warp, and (k_sweep) CTA tasks with 1 to 8 tasks per resident CTA -- each timed
+// over a few launches on the freshly created, all-rest history (which the sweep leaves unchanged:
+// exp(0) - 1 = 0), together with the commit's reduction of the S partial sums (k_part_read); the fastest
+// is kept.  The partial-sum buffer is sized for the largest candidate and then trimmed by reallocation.
 template <int D, int HK>
 int sweep_autotune(lbve* h) {
     constexpr int VN = SweepKernel<D, HK>::VN;
     const void* fn = SweepKernel<D, HK>::fn(h->model == LBVE_MODEL_WM);
-    const size_t smem = sweep_smem_bytes(h->L);
+    const bool has_cta = HK != 2;   // the 16-bit sweep runs warp tasks only
+    const size_t smem = has_cta ? sweep_cta_smem_bytes(h->L) : sweep_smem_bytes(h->L);
     if (smem > 48 * 1024)
         LBVE_CUDA(cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
     int dev = 0, sms = 0, per_sm = 0;
@@ -306,59 +312,83 @@ int sweep_autotune(lbve* h) {
     LBVE_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
     LBVE_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, 256, smem));
     if (per_sm < 1) per_sm = 1;
-    const long long warps = (long long)sms * per_sm * 8;
+    const long long grid_full = (long long)sms * per_sm;
+    const long long warps = grid_full * 8;
     const long long tiles = h->Npad / (32 * VN);
     const long long Smax = h->L >= 16 ? h->L / 8 : 1;
-    std::vector<long long> cand;
-    for (long long k : {2, 4, 8, 16, 32}) {
-        long long S = (k * warps + tiles - 1) / tiles;
+    struct Cand { int cta; long long S; };
+    std::vector<Cand> cand;
+    auto add = [&](int cta, long long S) {
         S = std::max(1ll, std::min(S, Smax));
-        if (std::find(cand.begin(), cand.end(), S) == cand.end()) cand.push_back(S);
+        for (const Cand& c : cand)
+            if (c.cta == cta && c.S == S) return;
+        cand.push_back({cta, S});
+    };
+    // task counts just above and just below k waves of the resident warps (CTAs)
+    for (long long k : {2, 4, 8, 16, 32}) {
+        add(0, (k * warps + tiles - 1) / tiles);
+        add(0, k * warps / tiles);
     }
     // few nodes: the tasks above all hit Smax; fewer, longer chunks trade sweep parallelism for a
     // shorter reduction in the commit
-    for (long long S = 8; S < Smax; S *= 2)
-        if (std::find(cand.begin(), cand.end(), S) == cand.end()) cand.push_back(S);
-    const long long Sbig = *std::max_element(cand.begin(), cand.end());
+    for (long long S = 8; S < Smax; S *= 2) add(0, S);
+    if (has_cta)
+        for (long long k : {1, 2, 4, 8}) {
+            add(1, (k * grid_full + tiles - 1) / tiles);
+            add(1, k * grid_full / tiles);
+        }
+    long long Sbig = 1;
+    for (const Cand& c : cand) Sbig = std::max(Sbig, c.S);
     int rc = alloc(h, &h->part, h->hesz * (size_t)Sbig * h->NS * h->Npad);
     if (rc) return rc;
     LBVE_CUDA(cudaMemset(h->part, 0, h->hesz * (size_t)Sbig * h->NS * h->Npad));
-    const long long grid_full = (long long)sms * per_sm;
-    long long bestS = cand[0];
+    auto grid_of = [&](const Cand& c) {
+        return (int)std::max(1ll, std::min(grid_full, c.cta ? tiles * c.S : (tiles * c.S + 7) / 8));
+    };
+    Cand best_c = cand[0];
     float best = 1e30f;
     if (cand.size() > 1) {
         cudaEvent_t e0, e1;
         LBVE_CUDA(cudaEventCreate(&e0));
         LBVE_CUDA(cudaEventCreate(&e1));
-        for (long long S : cand) {
-            h->S = (int)S;
-            h->sweep_grid = (int)std::max(1ll, std::min(grid_full, (tiles * S + 7) / 8));
+        int reps = 3;   // launches timed per candidate; one once a launch takes over a millisecond
+        for (const Cand& c : cand) {
+            h->S = (int)c.S;
+            h->sweep_cta = c.cta;
+            h->sweep_grid = grid_of(c);
             if ((rc = launch_sweep_any<D, HK>(h, 0))) return rc;   // warm-up
             LBVE_CUDA(cudaEventRecord(e0, 0));
-            for (int r = 0; r < 3; ++r) {
+            for (int r = 0; r < reps; ++r) {
                 if ((rc = launch_sweep_any<D, HK>(h, 0))) return rc;
                 if (h->hist_dbl)
-                    k_part_read<double><<<(h->N + 255) / 256, 256>>>((const double*)h->part, (int)S, h->NS, h->Npad, h->N, h->red);
+                    k_part_read<double><<<(h->N + 255) / 256, 256>>>((const double*)h->part, (int)c.S, h->NS, h->Npad, h->N, h->red);
                 else
-                    k_part_read<float><<<(h->N + 255) / 256, 256>>>((const float*)h->part, (int)S, h->NS, h->Npad, h->N, h->red);
+                    k_part_read<float><<<(h->N + 255) / 256, 256>>>((const float*)h->part, (int)c.S, h->NS, h->Npad, h->N, h->red);
                 LBVE_CUDA(cudaGetLastError());
             }
             LBVE_CUDA(cudaEventRecord(e1, 0));
             LBVE_CUDA(cudaEventSynchronize(e1));
             float ms = 0.f;
             LBVE_CUDA(cudaEventElapsedTime(&ms, e0, e1));
-            if (ms < best) { best = ms; bestS = S; }
+            ms /= (float)reps;
+            if (ms < best) { best = ms; best_c = c; }
+            if (ms > 1.0f) reps = 1;
         }
         cudaEventDestroy(e0);
         cudaEventDestroy(e1);
     }
-    h->S = (int)bestS;
-    h->sweep_grid = (int)std::max(1ll, std::min(grid_full, (tiles * bestS + 7) / 8));
-    if (bestS < Sbig) {   // keep only what the chosen S needs
+    h->S = (int)best_c.S;
+    h->sweep_cta = best_c.cta;
+    h->sweep_grid = grid_of(best_c);
+    h->sweep_grid_full = (int)grid_full;
+    h->part_S = (int)Sbig;
+    if (best_c.S < Sbig) {   // keep only what the chosen S needs
         cudaFree(h->part);
         h->bytes -= h->hesz * (size_t)Sbig * h->NS * h->Npad;
         h->part = nullptr;
-        if ((rc = alloc(h, &h->part, h->hesz * (size_t)bestS * h->NS * h->Npad))) return rc;
+        h->part_S = 0;
+        if ((rc = alloc(h, &h->part, h->hesz * (size_t)best_c.S * h->NS * h->Npad))) return rc;
+        h->part_S = (int)best_c.S;
     }
     return LBVE_OK;
 }
@@ -1485,10 +1515,41 @@ int lbve_memory_bytes(const lbve_t* h, size_t* bytes) {
     return LBVE_OK;
 }
 
-int lbve_sweep_config(const lbve_t* h, int32_t* slot_chunks, int32_t* ctas) {
-    if (!h || !slot_chunks || !ctas) return LBVE_EINVAL;
+int lbve_sweep_config(const lbve_t* h, int32_t* slot_chunks, int32_t* ctas, int32_t* cta_tasks) {
+    if (!h || !slot_chunks || !ctas || !cta_tasks) return LBVE_EINVAL;
     *slot_chunks = h->S;
     *ctas = h->sweep_grid;
+    *cta_tasks = h->sweep_cta;
+    return LBVE_OK;
+}
+
+int lbve_set_sweep_config(lbve_t* h, int32_t slot_chunks, int32_t cta_tasks) {
+    if (!h) return LBVE_EINVAL;
+    if (h->L == 0 || h->tangent || h->rec_K || !h->part) return LBVE_ENOSUPPORT;
+    const long long Smax = h->L >= 16 ? h->L / 8 : 1;
+    if (slot_chunks < 1 || slot_chunks > Smax || (cta_tasks != 0 && cta_tasks != 1)) return LBVE_EINVAL;
+    if (cta_tasks && h->hist_s16) return LBVE_EINVAL;
+    LBVE_CUDA(cudaDeviceSynchronize());
+    if (h->graph) {
+        cudaGraphExecDestroy(h->graph);
+        h->graph = nullptr;
+    }
+    if (slot_chunks > h->part_S) {
+        const size_t old_bytes = h->hesz * (size_t)h->part_S * h->NS * h->Npad;
+        cudaFree(h->part);
+        h->bytes -= old_bytes;
+        h->part = nullptr;
+        h->part_S = 0;
+        int rc = alloc(h, &h->part, h->hesz * (size_t)slot_chunks * h->NS * h->Npad);
+        if (rc) return rc;
+        h->part_S = slot_chunks;
+    }
+    const int vn = h->hist_s16 ? (h->D == 2 ? 4 : 2) : (h->hist_dbl ? 2 : 4) / (h->D == 3 ? 2 : 1);
+    const long long tiles = h->Npad / (32 * vn);
+    h->S = slot_chunks;
+    h->sweep_cta = cta_tasks;
+    h->sweep_grid = (int)std::max(1ll, std::min((long long)h->sweep_grid_full,
+                                                cta_tasks ? tiles * slot_chunks : (tiles * slot_chunks + 7) / 8));
     return LBVE_OK;
 }
 

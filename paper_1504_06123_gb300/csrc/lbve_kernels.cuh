@@ -316,25 +316,118 @@ template <typename R> struct SweepArgs {
     R* __restrict__ part;             // [S][NS][Npad]  partial trapezoid sums per slot chunk (scratch)
     const long long* t_dev;           // step index t
     int B, C, S;                      // grid shape; S slot chunks
+    int cta_tasks;                    // 0: a task is one warp's; 1: a task is one CTA's (warps split its chunk)
     // White-Metzner form only: accumulated strain Gamma(t) = sum_{s<t} gammadot(s) of every node and the
     // value Gamma(t') each point was created with; a point's strain is their difference
     const double* __restrict__ gam_node;   // [Npad]
     const double* __restrict__ gam_pt;     // [L][Npad]
 };
 
-// Shared memory of the sweep: per slot age, weight, partner (L entries each) + the per-block state.
-__host__ __device__ inline size_t sweep_smem_bytes(int L) { return (size_t)L * 12 + sizeof(BlockStep) * LBVE_MAXB; }
+// Shared memory of the sweeps: per slot age, weight, partner (L entries each) + the per-block state; k_sweep
+// adds (CTA tasks) the per-warp partial sums of one tile: 8 warps x NS x 32 VN values = 12 KB in every
+// lattice / precision combination (NS VN sizeof(R) = 48).
+__host__ __device__ inline size_t sweep_smem_bytes(int L) {
+    return ((size_t)L * 12 + sizeof(BlockStep) * LBVE_MAXB + 15) / 16 * 16;
+}
+constexpr size_t kSweepRedBytes = 8 * 32 * 48;
+__host__ __device__ inline size_t sweep_cta_smem_bytes(int L) { return sweep_smem_bytes(L) + kSweepRedBytes; }
 
-// Persistent warps.  A task is (tile of 32*VN consecutive nodes, chunk of consecutive slots); lane i
+// Slots [l0, l1) of the nodes n0 .. n0+VN-1 of one lane: advance every point in place,
+// X <- X + A + A X with A = exp(kappa(t-1)) - 1 (Eq. eeval, newest factor on the left), and add
+// w G (E kappa E^T + (.)^T) to acc.  The older half of a merge uses the average of the two kappa
+// (Sec. III); the newer half (weight 0) is skipped.
+template <int D, typename R, int VN, bool WM>
+__device__ __forceinline__ void sweep_range(const SweepArgs<R>& a, const Geom& g, const float* s_age,
+                                            const float* s_w, const int* s_part, long long s_last, long long n0,
+                                            int l0, int l1, R (&acc)[VN][D == 2 ? 3 : 6]) {
+    constexpr int DD = D * D;
+    constexpr int NS = D == 2 ? 3 : 6;
+    using V = Vec<R, VN>;
+    const long long Np = g.Npad;
+    // relaxation rates of each node's channel (Eq. nlmax)
+    R inv_tau[VN], inv_gc[VN];
+#pragma unroll
+    for (int j = 0; j < VN; ++j) {
+        const Chan& c = g.ch[chan_index(g, n0 + j)];
+        inv_tau[j] = (R)c.inv_tau;
+        inv_gc[j] = (R)c.inv_gc;
+    }
+    // A = exp(kappa(t-1)) - 1 per node; kappa(t-1) is the point created last step (newest slot of the
+    // finest block; a rest point before the first step)
+    R A[VN][DD];
+    {
+        R kp[VN][DD];
+#pragma unroll
+        for (int c = 0; c < DD; ++c) {
+            const V v = *reinterpret_cast<const V*>(a.K + (s_last * DD + c) * Np + n0);
+#pragma unroll
+            for (int j = 0; j < VN; ++j) kp[j][c] = v.v[j];
+        }
+#pragma unroll
+        for (int j = 0; j < VN; ++j) expm1_mat<D>(kp[j], A[j]);
+    }
+#pragma unroll
+    for (int j = 0; j < VN; ++j)
+#pragma unroll
+        for (int i = 0; i < NS; ++i) acc[j][i] = 0;
+    using VD = Vec<double, VN>;
+    VD gam_now;
+    if (WM) gam_now = *reinterpret_cast<const VD*>(a.gam_node + n0);
+
+    for (int l = l0; l < l1; ++l) {
+        const float w = s_w[l];
+        if (w == 0.0f) continue;                 // same slot for the whole warp: uniform branch
+        R* Xp = a.X + (long long)l * DD * Np + n0;
+        const R* Kp = a.K + (long long)l * DD * Np + n0;
+        R X[VN][DD], kap[VN][DD];
+#pragma unroll
+        for (int c = 0; c < DD; ++c) {
+            const V xv = *reinterpret_cast<const V*>(Xp + c * Np);
+            const V kv = *reinterpret_cast<const V*>(Kp + c * Np);
+#pragma unroll
+            for (int j = 0; j < VN; ++j) { X[j][c] = xv.v[j]; kap[j][c] = kv.v[j]; }
+        }
+        const int part = s_part[l];
+        if (part >= 0) {   // older half of a merge: kappa averaged with the newer half
+            const R* K2 = a.K + (long long)part * DD * Np + n0;
+#pragma unroll
+            for (int c = 0; c < DD; ++c) {
+                const V kv = *reinterpret_cast<const V*>(K2 + c * Np);
+#pragma unroll
+                for (int j = 0; j < VN; ++j) kap[j][c] = R(0.5) * (kap[j][c] + kv.v[j]);
+            }
+        }
+        const R age = (R)s_age[l], wr = (R)w;
+        R strain[VN];
+        if (WM) {   // a merged point keeps the older half's creation strain (its slot l)
+            const VD gp = *reinterpret_cast<const VD*>(a.gam_pt + (long long)l * Np + n0);
+#pragma unroll
+            for (int j = 0; j < VN; ++j) strain[j] = (R)(gam_now.v[j] - gp.v[j]);
+        }
+#pragma unroll
+        for (int j = 0; j < VN; ++j)
+            point_update<D, R, WM>(X[j], A[j], kap[j], age, wr, inv_tau[j], inv_gc[j], acc[j], WM ? strain[j] : R(0));
+#pragma unroll
+        for (int c = 0; c < DD; ++c) {
+            V xv;
+#pragma unroll
+            for (int j = 0; j < VN; ++j) xv.v[j] = X[j][c];
+            *reinterpret_cast<V*>(Xp + c * Np) = xv;
+        }
+    }
+}
+
+// Persistent sweep over tasks (tile of 32*VN consecutive nodes, chunk of consecutive slots).  Lane i
 // handles nodes tile*32*VN + i*VN ... + VN-1, so every component plane is read and written with one
-// 16-byte access per lane and 512 contiguous bytes per warp.  Each task writes its partial sum of
-// w G (E kappa E^T + (.)^T) to `part`; k_collide_stream (or k_commit) adds the chunks in a fixed
-// order, so the result does not depend on scheduling.  All points are advanced in place:
-// X <- X + A + A X with A = exp(kappa(t-1)) - 1 (Eq. eeval, newest factor on the left); the older half of
-// a merge uses the average of the two kappa (Sec. III), the newer half is skipped.
+// 16-byte access per lane and 512 contiguous bytes per warp.
+//  - warp tasks (cta_tasks = 0): each warp takes whole tasks and writes its chunk's partial sum;
+//  - CTA tasks (cta_tasks = 1): the CTA's warps take consecutive pieces of one task's chunk, and their
+//    sums are added in warp order through shared memory: a chunk count S then keeps 8x the warps busy
+//    that warp tasks would (few nodes: full occupancy without S-fold partial sums in the commit).
+// Each task writes its partial sum of w G (E kappa E^T + (.)^T) to `part`; k_collide_stream (or
+// k_commit) adds the chunks in a fixed order, so the result does not depend on scheduling.
 template <int D, typename R, int VN, bool WM = false>
 __global__ void __launch_bounds__(256, 2) k_sweep(SweepArgs<R> a, Geom g) {
-    constexpr int DD = D * D;
     constexpr int NS = D == 2 ? 3 : 6;
     using V = Vec<R, VN>;
     const int L = a.B * a.C;
@@ -343,6 +436,7 @@ __global__ void __launch_bounds__(256, 2) k_sweep(SweepArgs<R> a, Geom g) {
     float* s_w = s_age + L;
     int* s_part = reinterpret_cast<int*>(s_w + L);
     BlockStep* s_bs = reinterpret_cast<BlockStep*>(s_part + L);
+    R* s_red = reinterpret_cast<R*>(smem_raw + sweep_smem_bytes(L));
 
     const long long t = *a.t_dev;
     if (threadIdx.x == 0) sched_step(a.B, a.C, t, s_bs);
@@ -358,98 +452,54 @@ __global__ void __launch_bounds__(256, 2) k_sweep(SweepArgs<R> a, Geom g) {
 
     const long long Np = g.Npad;
     const int lane = threadIdx.x & 31;
-    const int gwarp = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
-    const int nwarps = gridDim.x * (blockDim.x >> 5);
     const int tiles = (int)(Np / (32 * VN));
     const int tasks = tiles * a.S;
     const int chunk_len = (L + a.S - 1) / a.S;
     const long long s_last = (long long)(a.B - 1) * a.C + s_bs[a.B - 1].head_prev;
+    R acc[VN][NS];
 
-    for (int task = gwarp; task < tasks; task += nwarps) {
+    if (!a.cta_tasks) {
+        const int gwarp = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+        const int nwarps = gridDim.x * (blockDim.x >> 5);
+        for (int task = gwarp; task < tasks; task += nwarps) {
+            const int tile = task % tiles;
+            const int chunk = task / tiles;
+            const long long n0 = (long long)tile * 32 * VN + lane * VN;
+            const int l0 = chunk * chunk_len;
+            sweep_range<D, R, VN, WM>(a, g, s_age, s_w, s_part, s_last, n0, l0, min(L, l0 + chunk_len), acc);
+#pragma unroll
+            for (int i = 0; i < NS; ++i) {
+                V v;
+#pragma unroll
+                for (int j = 0; j < VN; ++j) v.v[j] = acc[j][i];
+                *reinterpret_cast<V*>(a.part + ((long long)chunk * NS + i) * Np + n0) = v;
+            }
+        }
+        return;
+    }
+    const int nw = blockDim.x >> 5;                 // warps of the CTA (8: the shared buffer's size)
+    const int wib = threadIdx.x >> 5;
+    const int sub_len = (chunk_len + nw - 1) / nw;
+    constexpr int TN = 32 * VN;                     // nodes of a tile
+    for (int task = blockIdx.x; task < tasks; task += gridDim.x) {
         const int tile = task % tiles;
         const int chunk = task / tiles;
-        const long long n0 = (long long)tile * 32 * VN + lane * VN;
-        // relaxation rates of each node's channel (Eq. nlmax)
-        R inv_tau[VN], inv_gc[VN];
+        const long long n0 = (long long)tile * TN + lane * VN;
+        const int c0 = chunk * chunk_len, c1 = min(L, c0 + chunk_len);
+        const int l0 = min(c1, c0 + wib * sub_len);
+        sweep_range<D, R, VN, WM>(a, g, s_age, s_w, s_part, s_last, n0, l0, min(c1, l0 + sub_len), acc);
 #pragma unroll
-        for (int j = 0; j < VN; ++j) {
-            const Chan& c = g.ch[chan_index(g, n0 + j)];
-            inv_tau[j] = (R)c.inv_tau;
-            inv_gc[j] = (R)c.inv_gc;
+        for (int i = 0; i < NS; ++i)
+#pragma unroll
+            for (int j = 0; j < VN; ++j) s_red[(wib * NS + i) * TN + lane * VN + j] = acc[j][i];
+        __syncthreads();
+        for (int k = threadIdx.x; k < NS * TN; k += blockDim.x) {
+            const int i = k / TN, m = k - i * TN;
+            R sum = s_red[i * TN + m];
+            for (int w = 1; w < nw; ++w) sum += s_red[(w * NS + i) * TN + m];
+            a.part[((long long)chunk * NS + i) * Np + (long long)tile * TN + m] = sum;
         }
-        // A = exp(kappa(t-1)) - 1 per node; kappa(t-1) is the point created last step (newest slot of
-        // the finest block; a rest point before the first step)
-        R A[VN][DD];
-        {
-            R kp[VN][DD];
-#pragma unroll
-            for (int c = 0; c < DD; ++c) {
-                const V v = *reinterpret_cast<const V*>(a.K + (s_last * DD + c) * Np + n0);
-#pragma unroll
-                for (int j = 0; j < VN; ++j) kp[j][c] = v.v[j];
-            }
-#pragma unroll
-            for (int j = 0; j < VN; ++j) expm1_mat<D>(kp[j], A[j]);
-        }
-        R acc[VN][NS];
-#pragma unroll
-        for (int j = 0; j < VN; ++j)
-#pragma unroll
-            for (int i = 0; i < NS; ++i) acc[j][i] = 0;
-        using VD = Vec<double, VN>;
-        VD gam_now;
-        if (WM) gam_now = *reinterpret_cast<const VD*>(a.gam_node + n0);
-
-        const int l0 = chunk * chunk_len;
-        const int l1 = min(L, l0 + chunk_len);
-        for (int l = l0; l < l1; ++l) {
-            const float w = s_w[l];
-            if (w == 0.0f) continue;                 // same slot for the whole warp: uniform branch
-            R* Xp = a.X + (long long)l * DD * Np + n0;
-            const R* Kp = a.K + (long long)l * DD * Np + n0;
-            R X[VN][DD], kap[VN][DD];
-#pragma unroll
-            for (int c = 0; c < DD; ++c) {
-                const V xv = *reinterpret_cast<const V*>(Xp + c * Np);
-                const V kv = *reinterpret_cast<const V*>(Kp + c * Np);
-#pragma unroll
-                for (int j = 0; j < VN; ++j) { X[j][c] = xv.v[j]; kap[j][c] = kv.v[j]; }
-            }
-            const int part = s_part[l];
-            if (part >= 0) {   // older half of a merge: kappa averaged with the newer half
-                const R* K2 = a.K + (long long)part * DD * Np + n0;
-#pragma unroll
-                for (int c = 0; c < DD; ++c) {
-                    const V kv = *reinterpret_cast<const V*>(K2 + c * Np);
-#pragma unroll
-                    for (int j = 0; j < VN; ++j) kap[j][c] = R(0.5) * (kap[j][c] + kv.v[j]);
-                }
-            }
-            const R age = (R)s_age[l], wr = (R)w;
-            R strain[VN];
-            if (WM) {   // a merged point keeps the older half's creation strain (its slot l)
-                const VD gp = *reinterpret_cast<const VD*>(a.gam_pt + (long long)l * Np + n0);
-#pragma unroll
-                for (int j = 0; j < VN; ++j) strain[j] = (R)(gam_now.v[j] - gp.v[j]);
-            }
-#pragma unroll
-            for (int j = 0; j < VN; ++j)
-                point_update<D, R, WM>(X[j], A[j], kap[j], age, wr, inv_tau[j], inv_gc[j], acc[j], WM ? strain[j] : R(0));
-#pragma unroll
-            for (int c = 0; c < DD; ++c) {
-                V xv;
-#pragma unroll
-                for (int j = 0; j < VN; ++j) xv.v[j] = X[j][c];
-                *reinterpret_cast<V*>(Xp + c * Np) = xv;
-            }
-        }
-#pragma unroll
-        for (int i = 0; i < NS; ++i) {
-            V v;
-#pragma unroll
-            for (int j = 0; j < VN; ++j) v.v[j] = acc[j][i];
-            *reinterpret_cast<V*>(a.part + ((long long)chunk * NS + i) * Np + n0) = v;
-        }
+        __syncthreads();
     }
 }
 

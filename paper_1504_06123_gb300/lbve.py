@@ -35,7 +35,7 @@ EXPORTS = [
     "lbve_fields_host_fixed", "lbve_create_batch", "lbve_channel_nodes", "lbve_sweep_config",
     "lbve_create_tangent", "lbve_tangent_fields", "lbve_checkpoint_size", "lbve_checkpoint_save",
     "lbve_checkpoint_restore", "lbve_create_adjoint", "lbve_backward", "lbve_set_pressure_step",
-    "lbve_set_probes", "lbve_probe_read",
+    "lbve_set_probes", "lbve_probe_read", "lbve_set_sweep_config",
 ]
 
 
@@ -85,7 +85,8 @@ def load(path: str | None = None):
         lib.lbve_checkpoint_restore.argtypes = [vp, vp, i32, vp]
         lib.lbve_tangent_fields.argtypes = [vp, C.c_uint32, vp, vp]
         lib.lbve_channel_nodes.argtypes = [vp, i32, C.POINTER(i64), C.POINTER(i64)]
-        lib.lbve_sweep_config.argtypes = [vp, C.POINTER(i32), C.POINTER(i32)]
+        lib.lbve_sweep_config.argtypes = [vp, C.POINTER(i32), C.POINTER(i32), C.POINTER(i32)]
+        lib.lbve_set_sweep_config.argtypes = [vp, i32, i32]
         lib.lbve_set_force.argtypes = [vp, i32, dp, vp]
         lib.lbve_set_params.argtypes = [vp, i32, C.c_double, C.c_double, C.c_double, vp]
         lib.lbve_set_pressure_step.argtypes = [vp, i32, C.c_double, vp]
@@ -245,9 +246,14 @@ def lbve_channel_nodes(h: int, channel: int):
 
 
 def lbve_sweep_config(h: int):
-    s, g = C.c_int32(), C.c_int32()
-    _check(load().lbve_sweep_config(h, C.byref(s), C.byref(g)), "lbve_sweep_config")
-    return s.value, g.value
+    """(slot chunks, persistent CTAs, task mode: 0 warp tasks / 1 CTA tasks) of the history sweep."""
+    s, g, m = C.c_int32(), C.c_int32(), C.c_int32()
+    _check(load().lbve_sweep_config(h, C.byref(s), C.byref(g), C.byref(m)), "lbve_sweep_config")
+    return s.value, g.value, m.value
+
+
+def lbve_set_sweep_config(h: int, slot_chunks: int, cta_tasks: int) -> None:
+    _check(load().lbve_set_sweep_config(h, int(slot_chunks), int(cta_tasks)), "lbve_set_sweep_config")
 
 
 def lbve_destroy(h: int) -> None:

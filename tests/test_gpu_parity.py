@@ -31,6 +31,14 @@ PLAIN, ALL32, ALL64, RED, RED64 = (F64, F32), (F32, F32), (F64, F64), (F32, S16)
 TOL = {PLAIN: 1e-5, ALL32: 5e-5, ALL64: 1e-11, RED: 1e-3, RED64: 1e-3, F32: 1e-5, F64: 1e-11, S16: 1e-3}
 
 
+def same_sweep_shape(a, *others):
+    """Give other handles a's autotuned sweep shape: the shape fixes the summation order of Eq. (gitt), so
+    bitwise comparisons between handles need the same one (each handle's autotuner may pick another)."""
+    S, _, mode = L.lbve_sweep_config(a.h)
+    for o in others:
+        L.lbve_set_sweep_config(o.h, S, mode)
+
+
 def rel_err(x, ref):
     x = np.asarray(x, dtype=np.float64).reshape(len(ref), -1)
     ref = np.asarray(ref, dtype=np.float64).reshape(len(ref), -1)
@@ -310,6 +318,46 @@ def test_batched_ducts_vs_oracle():
     ch.close()
 
 
+@pytest.mark.parametrize("prec", [PLAIN, ALL64])
+def test_sweep_shapes_agree(prec):
+    """Every launch shape of the history sweep (task mode, slot chunks) computes the same sums up to the
+    order of the additions; the same shape on two handles gives the same bits."""
+    kw = dict(nx=6, ny=40, G_inf=0.01, tau=40.0, gamma_c=0.1, g=(1e-5, 0, 0), C=16, B=4, precision=prec[0],
+              hist_storage=prec[1])
+    Smax = 16 * 4 // 8
+    ref = None
+    for S, mode in [(1, 0), (1, 1), (Smax, 0), (Smax, 1), (3, 1)]:
+        ch = L.Channel(L.make_desc(**kw))
+        L.lbve_set_sweep_config(ch.h, S, mode)
+        assert L.lbve_sweep_config(ch.h)[::2] == (S, mode)
+        ch.step(70)
+        f = ch.fields()
+        if ref is None:
+            ref = f
+        else:
+            for key in ("u", "sigma"):
+                assert rel_err(f[key], ref[key]) <= (1e-6 if prec == PLAIN else 1e-13), (S, mode, key)
+        ch.close()
+    a = L.Channel(L.make_desc(**kw))
+    for bad in [(0, 0), (Smax + 1, 0), (1, 2)]:
+        with pytest.raises(L.LbveError) as e:
+            L.lbve_set_sweep_config(a.h, *bad)
+        assert e.value.status == L.LBVE_EINVAL
+    a.close()
+    inst = L.Channel(L.make_desc(**dict(kw, model=L.LBVE_MODEL_INLM)))
+    with pytest.raises(L.LbveError) as e:
+        L.lbve_set_sweep_config(inst.h, 1, 0)
+    assert e.value.status == L.LBVE_ENOSUPPORT
+    inst.close()
+    s16 = L.Channel(L.make_desc(**dict(kw, precision=F32, hist_storage=S16)))
+    with pytest.raises(L.LbveError) as e:
+        L.lbve_set_sweep_config(s16.h, 1, 1)           # the 16-bit sweep has warp tasks only
+    assert e.value.status == L.LBVE_EINVAL
+    L.lbve_set_sweep_config(s16.h, 2, 0)
+    s16.step(20)
+    s16.close()
+
+
 def test_batch_rejects_mixed_history_grids():
     a = L.make_desc(nx=2, ny=4, C=8, B=2)
     b = L.make_desc(nx=2, ny=4, C=16, B=2)
@@ -324,6 +372,7 @@ def test_graph_replay_matches_single_steps():
               hist_storage=F32)
     a = L.Channel(L.make_desc(**kw))
     b = L.Channel(L.make_desc(**kw))
+    same_sweep_shape(a, b)
     a.step(3)
     a.step(45)             # one odd step, then graphs of 16, then the rest
     for _ in range(48):
@@ -331,8 +380,8 @@ def test_graph_replay_matches_single_steps():
     fa, fb = a.fields(), b.fields()
     for k in fa:
         assert np.array_equal(fa[k], fb[k]), k
-    s, ctas = L.lbve_sweep_config(a.h)
-    assert s >= 1 and ctas >= 1
+    s, ctas, mode = L.lbve_sweep_config(a.h)
+    assert s >= 1 and ctas >= 1 and mode in (0, 1)
     a.close()
     b.close()
 
@@ -378,10 +427,12 @@ def test_checkpoint_resume_bitwise(prec):
     a.step(50)
     ref = a.fields()
     b = L.Channel(L.make_desc(**kw))
+    same_sweep_shape(a, b)
     L.lbve_checkpoint_restore(b.h, img)
     assert b.t == 37
     b.step(50)
     c = L.Channel(L.make_desc(**kw))
+    same_sweep_shape(a, c)
     L.lbve_checkpoint_restore(c.h, dev)
     c.step(50)
     for k, v in ref.items():

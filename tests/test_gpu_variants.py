@@ -210,6 +210,9 @@ def test_variant_checkpoint_resume_bitwise(model):
     a.step(50)
     ref = a.fields()
     b = L.Channel(L.make_desc(**kw))
+    if model != INLM:   # same summation order of the history sum as a (no history sweep for the instantaneous model)
+        S, _, mode = L.lbve_sweep_config(a.h)
+        L.lbve_set_sweep_config(b.h, S, mode)
     L.lbve_checkpoint_restore(b.h, img)
     b.step(50)
     for k, v in ref.items():

@@ -202,3 +202,46 @@ def test_paper_sweep_theta_dependence(paper_sweep, slow_sweep):
             assert u.max() > 1.05, u.max()
         if c.ratio >= 4.0:     # at most a trace of overshoot left (the rise is monotonic at theta = 10)
             assert u.max() < 1.01, u.max()
+
+
+def test_regime_bench_batch_vs_oracle():
+    """The benchmark's batch (ten channels of Figs. Qall / figtau, nx = 4, L = 1920, launch shape of the
+    autotuner) against the oracle: 96 steps of startup with the probes recorded every step; channels of
+    10, 100 and 200 nodes across checked node by node (column 0; the flow is x-invariant, so a one-column
+    oracle channel is that column) and the probe records of those channels."""
+    pts = regime.paper_points()
+    chans, descs, B = regime.sweep_descs(pts, regime.tau0_for_width(100), nx=4)
+    assert B == 15 and len(descs) == 10
+    batch = L.Channel(descs)
+    offs = [L.lbve_channel_nodes(batch.h, k)[0] for k in range(len(descs))]
+    nodes, _ = regime.probe_plan(chans, offs, 4)
+    L.lbve_set_probes(batch.h, nodes, 1, 200)
+    steps = 96
+    batch.step(steps)
+    t, vals, tot = L.lbve_probe_read(batch.h, len(nodes), 2, 200)
+    assert list(t) == list(range(1, steps + 1)) and tot == steps
+    f = batch.fields()
+    for k in (0, 3, 9):
+        d = descs[k]
+        o = oracle.Channel(oracle.D2Q9, 1, d.ny, tau_lb=d.tau_lb, G_inf=d.G_inf, tau=d.tau, gamma_c=d.gamma_c,
+                           g=tuple(d.g), C=d.hist_C, B=d.hist_B)
+        ref = []
+        for _ in range(steps):
+            o.step(1)
+            of = o.fields()
+            j0 = (nodes[2 * k] - offs[k]) // 4
+            ref.append([np.concatenate(([of["rho"][j]], of["u"][j], of["sigma"][j])) for j in (j0, j0 + 1)])
+        of = o.fields()
+        o.close()
+        col = slice(offs[k], offs[k] + 4 * d.ny, 4)           # column x = 0 of channel k
+        for key in ("u", "sigma", "kappa"):
+            got = f[key][col]
+            e = np.max(np.abs(got - of[key])) / np.max(np.abs(of[key]))
+            assert e <= 1e-5, (k, key, e)
+        ref = np.array(ref)
+        got = vals[:, 2 * k:2 * k + 2]
+        # on the scale of the channel's field (the shear has not reached the probe of a wide channel yet)
+        for sl, key in ((slice(1, 3), "u"), (slice(3, 6), "sigma")):
+            e = np.max(np.abs(got[..., sl] - ref[..., sl])) / np.max(np.abs(of[key]))
+            assert e <= 1e-5, (k, key, e)
+    batch.close()

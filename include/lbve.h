@@ -131,6 +131,29 @@ int lbve_create(const lbve_channel_desc* desc, const double* rho_init, lbve_t** 
  */
 int lbve_create_batch(const lbve_channel_desc* descs, int32_t n_channels, const double* rho_init, lbve_t** out);
 
+/*
+ * Device-memory provider of a handle (the ownership rule of the boundary: the handle owns its device state,
+ * taken from the caller's allocator -- for instance PyTorch's caching allocator -- or from cudaMalloc; the
+ * paper has no counterpart).  alloc returns device memory of at least `bytes` on the current device,
+ * aligned to 256 bytes, or NULL; free returns it.  `stream` is the stream the memory is first used on (the
+ * legacy default stream, NULL, for the handle's own buffers, which the handle frees only after a device
+ * synchronisation); ctx is passed through.  Both are called from the host thread that calls the library.
+ */
+typedef struct {
+    void* (*alloc)(size_t bytes, void* stream, void* ctx);
+    void (*free)(void* ptr, void* stream, void* ctx);
+    void* ctx;
+} lbve_allocator;
+
+/*
+ * lbve_create_batch (n_channels = 1: lbve_create) with every device buffer of the handle and of its later
+ * calls (probe buffers, field staging, checkpoints) taken from `allocator` (NULL, or alloc == NULL: cudaMalloc).
+ * ENOMEM when the allocator returns NULL or memory not aligned to 256 bytes; whatever was allocated is freed
+ * again through the allocator, and *out is NULL.  EINVAL when alloc is set and free is not.
+ */
+int lbve_create_ex(const lbve_channel_desc* descs, int32_t n_channels, const double* rho_init,
+                   const lbve_allocator* allocator, lbve_t** out);
+
 /* First node and node count of a channel (0 for a handle made by lbve_create). */
 int lbve_channel_nodes(const lbve_t* h, int32_t channel, int64_t* offset, int64_t* count);
 

@@ -87,6 +87,7 @@ struct lbve {
     int64_t t_host = 0;
     size_t bytes = 0;
     int* flag = nullptr;       // non-finite flag of lbve_fields
+    lbve_allocator al{};       // device-memory provider (lbve_create_ex); alloc == NULL: cudaMalloc / cudaFree
     // probe recorder (lbve_set_probes): records [cap][1 + probe_n (1 + D + NS)] appended after steps
     int probe_n = 0;
     int probe_every = 1;
@@ -111,16 +112,16 @@ struct lbve {
 
 namespace {
 
+void dev_free(lbve* h, void* p, cudaStream_t s = 0);
+
 void free_all(lbve* h) {
     void* ptrs[] = {h->pops[0], h->pops[1], h->u_raw, h->u, h->rho, h->sigma, h->kappa, h->tr_prev,
                     h->X, h->K, h->part, h->t_dev, h->red, h->stage, h->flag, h->chan_dev, h->chan_of,
                     h->Qe, h->Ke, h->Rm, h->gam_node, h->gam_pt, h->probe_nodes, h->probe_rec, h->probe_cnt};
-    for (void* p : ptrs)
-        if (p) cudaFree(p);
+    for (void* p : ptrs) dev_free(h, p);
     for (cudaEvent_t e : h->ev_pool) cudaEventDestroy(e);
     h->ev_pool.clear();
-    for (void* c : h->ckpts)
-        if (c) cudaFree(c);
+    for (void* c : h->ckpts) dev_free(h, c);
     h->ckpts.clear();
     if (h->graph) cudaGraphExecDestroy(h->graph);
     if (h->graph_stream) cudaStreamDestroy(h->graph_stream);
@@ -143,14 +144,39 @@ int prof_mark(lbve* h, cudaStream_t s, int kind, bool start) {
     return LBVE_OK;
 }
 
-int alloc(lbve* h, void** p, size_t bytes) {
+// Device memory through the handle's provider (or cudaMalloc): every buffer the handle owns and the work
+// buffers of its calls.  Buffers must start on 256-byte boundaries (the kernels' vector accesses).
+int dev_alloc(lbve* h, void** p, size_t bytes, cudaStream_t s = 0) {
+    *p = nullptr;
+    if (h->al.alloc) {
+        void* q = h->al.alloc(bytes, (void*)s, h->al.ctx);
+        if (!q) return LBVE_ENOMEM;
+        if (reinterpret_cast<uintptr_t>(q) & 255u) {
+            h->al.free(q, (void*)s, h->al.ctx);
+            std::snprintf(g_cuda_err, sizeof g_cuda_err, "allocator returned memory not aligned to 256 bytes");
+            return LBVE_ENOMEM;
+        }
+        *p = q;
+        return LBVE_OK;
+    }
     cudaError_t e = cudaMalloc(p, bytes);
     if (e != cudaSuccess) {
         *p = nullptr;
         return cuda_fail(e, "cudaMalloc");
     }
-    h->bytes += bytes;
     return LBVE_OK;
+}
+
+void dev_free(lbve* h, void* p, cudaStream_t s) {
+    if (!p) return;
+    if (h->al.alloc) h->al.free(p, (void*)s, h->al.ctx);
+    else cudaFree(p);
+}
+
+int alloc(lbve* h, void** p, size_t bytes) {
+    int rc = dev_alloc(h, p, bytes);
+    if (rc == LBVE_OK) h->bytes += bytes;
+    return rc;
 }
 
 Geom geom_of(const lbve* h) {
@@ -383,7 +409,7 @@ int sweep_autotune(lbve* h) {
     h->sweep_grid_full = (int)grid_full;
     h->part_S = (int)Sbig;
     if (best_c.S < Sbig) {   // keep only what the chosen S needs
-        cudaFree(h->part);
+        dev_free(h, h->part);
         h->bytes -= h->hesz * (size_t)Sbig * h->NS * h->Npad;
         h->part = nullptr;
         h->part_S = 0;
@@ -535,7 +561,8 @@ int init_state(lbve* h, const double* rho_init_host) {
     for (int q = 0; q < h->Q; ++q) w[q] = h->Q == 9 ? Lattice<9>::w(q) : Lattice<19>::w(q);
     double* tmp = nullptr;   // [Q] weights then [N] initial densities
     const size_t n_tmp = h->Q + (rho_init_host ? (size_t)h->N : 0);
-    LBVE_CUDA(cudaMalloc(&tmp, sizeof(double) * n_tmp));
+    int rc = dev_alloc(h, (void**)&tmp, sizeof(double) * n_tmp);
+    if (rc) return rc;
     cudaError_t e = cudaMemcpy(tmp, w, sizeof(double) * h->Q, cudaMemcpyHostToDevice);
     if (e == cudaSuccess && rho_init_host)
         e = cudaMemcpy(tmp + h->Q, rho_init_host, sizeof(double) * h->N, cudaMemcpyHostToDevice);
@@ -545,7 +572,7 @@ int init_state(lbve* h, const double* rho_init_host) {
         e = cudaGetLastError();
     }
     if (e == cudaSuccess) e = cudaDeviceSynchronize();
-    cudaFree(tmp);
+    dev_free(h, tmp);
     if (e != cudaSuccess) return cuda_fail(e, "initial state");
     return LBVE_OK;
 }
@@ -607,7 +634,8 @@ int mass_impl(lbve* h, double* sum_n, double* sum_drho, cudaStream_t s) {
     return LBVE_OK;
 }
 
-int create_impl(const lbve_channel_desc* descs, int32_t n, const double* rho_init, lbve_t** out) {
+int create_impl(const lbve_channel_desc* descs, int32_t n, const double* rho_init, lbve_t** out,
+                const lbve_allocator* allocator = nullptr) {
     if (!out) return LBVE_EINVAL;
     *out = nullptr;
     if (!descs || n < 1 || n > kMaxChannels) return LBVE_EINVAL;
@@ -623,8 +651,10 @@ int create_impl(const lbve_channel_desc* descs, int32_t n, const double* rho_ini
         for (long long i = 0; i < Ntot; ++i)
             if (!std::isfinite(rho_init[i]) || !(rho_init[i] > 0)) return LBVE_EINVAL;
     }
+    if (allocator && allocator->alloc && !allocator->free) return LBVE_EINVAL;
     lbve* h = new (std::nothrow) lbve();
     if (!h) return LBVE_ENOMEM;
+    if (allocator && allocator->alloc) h->al = *allocator;
     const lbve_channel_desc* desc = &descs[0];
     h->d = *desc;
     h->descs.assign(descs, descs + n);
@@ -856,7 +886,7 @@ int create_tangent(const lbve_channel_desc* desc, const double* rho_init, lbve_t
     for (int q = 0; q < h->Q; ++q) w[q] = h->Q == 9 ? Lattice<9>::w(q) : Lattice<19>::w(q);
     double* tmp = nullptr;
     const size_t n_tmp = h->Q + (rho_init ? (size_t)h->N : 0);
-    er = cudaMalloc(&tmp, sizeof(double) * n_tmp);
+    er = dev_alloc(h, (void**)&tmp, sizeof(double) * n_tmp) == LBVE_OK ? cudaSuccess : cudaErrorMemoryAllocation;
     if (er == cudaSuccess) er = cudaMemcpy(tmp, w, sizeof(double) * h->Q, cudaMemcpyHostToDevice);
     if (er == cudaSuccess && rho_init) er = cudaMemcpy(tmp + h->Q, rho_init, sizeof(double) * h->N, cudaMemcpyHostToDevice);
     if (er == cudaSuccess) {
@@ -865,7 +895,7 @@ int create_tangent(const lbve_channel_desc* desc, const double* rho_init, lbve_t
         er = cudaGetLastError();
     }
     if (er == cudaSuccess) er = cudaDeviceSynchronize();
-    if (tmp) cudaFree(tmp);
+    dev_free(h, tmp);
     if (er != cudaSuccess) return fail(cuda_fail(er, "tangent initial state"));
     const size_t smem = sweep_smem_bytes(h->L);
     if (smem > 48 * 1024) {
@@ -897,6 +927,11 @@ int lbve_create(const lbve_channel_desc* desc, const double* rho_init, lbve_t** 
 
 int lbve_create_batch(const lbve_channel_desc* descs, int32_t n_channels, const double* rho_init, lbve_t** out) {
     return create_impl(descs, n_channels, rho_init, out);
+}
+
+int lbve_create_ex(const lbve_channel_desc* descs, int32_t n_channels, const double* rho_init,
+                   const lbve_allocator* allocator, lbve_t** out) {
+    return create_impl(descs, n_channels, rho_init, out, allocator);
 }
 
 int lbve_channel_nodes(const lbve_t* h, int32_t channel, int64_t* offset, int64_t* count) {
@@ -1039,8 +1074,7 @@ int lbve_set_probes(lbve_t* h, int32_t n_probes, const int64_t* nodes, int32_t e
                                                     sizeof(double) * (size_t)h->probe_cap *
                                                         (1 + (size_t)h->probe_n * (1 + h->D + h->NS))
                                               : 0;
-    for (void* p : old)
-        if (p) cudaFree(p);
+    for (void* p : old) dev_free(h, p);
     h->bytes -= old_bytes;
     h->probe_nodes = nullptr;
     h->probe_rec = nullptr;
@@ -1049,12 +1083,13 @@ int lbve_set_probes(lbve_t* h, int32_t n_probes, const int64_t* nodes, int32_t e
     h->probe_cap = 0;
     if (n_probes == 0) return LBVE_OK;
     const size_t rec = 1 + (size_t)n_probes * (1 + h->D + h->NS);
+    const size_t bytes_before = h->bytes;
     int rc;
     if ((rc = alloc(h, (void**)&h->probe_nodes, sizeof(long long) * n_probes)) ||
         (rc = alloc(h, (void**)&h->probe_rec, sizeof(double) * rec * (size_t)capacity)) ||
         (rc = alloc(h, (void**)&h->probe_cnt, sizeof(long long)))) {
-        for (void* p : {(void*)h->probe_nodes, (void*)h->probe_rec, (void*)h->probe_cnt})
-            if (p) cudaFree(p);
+        for (void* p : {(void*)h->probe_nodes, (void*)h->probe_rec, (void*)h->probe_cnt}) dev_free(h, p);
+        h->bytes = bytes_before;
         h->probe_nodes = nullptr;
         h->probe_rec = nullptr;
         h->probe_cnt = nullptr;
@@ -1106,10 +1141,11 @@ int lbve_fields(lbve_t* h, uint32_t mask, double* dst, int32_t dst_is_device, vo
     }
     if (dst_is_device) return fields_impl(h, mask, dst, s);
     if (h->stage_n < cnt) {
-        if (h->stage) cudaFree(h->stage);
+        dev_free(h, h->stage);
         h->stage = nullptr;
         h->stage_n = 0;
-        LBVE_CUDA(cudaMalloc(&h->stage, sizeof(double) * (cnt > 0 ? cnt : 1)));
+        int rc = dev_alloc(h, (void**)&h->stage, sizeof(double) * (cnt > 0 ? cnt : 1));
+        if (rc) return rc;
         h->stage_n = cnt;
     }
     LBVE_CUDA(cudaMemsetAsync(h->flag, 0, sizeof(int), s));
@@ -1325,7 +1361,10 @@ int record_checkpoint(lbve* h, cudaStream_t s) {
     lbve_checkpoint_size(h, &bytes);
     const size_t idx = (size_t)(h->t_host / h->rec_K);
     if (h->ckpts.size() <= idx) h->ckpts.resize(idx + 1, nullptr);
-    if (!h->ckpts[idx]) LBVE_CUDA(cudaMalloc(&h->ckpts[idx], bytes));
+    if (!h->ckpts[idx]) {
+        int rc = dev_alloc(h, &h->ckpts[idx], bytes);
+        if (rc) return rc;
+    }
     return lbve_checkpoint_save(h, h->ckpts[idx], 1, s);
 }
 
@@ -1346,8 +1385,13 @@ AdjPar adj_par(const lbve* h) {
 
 // Device allocation released at scope exit (the adjoint's work buffers).
 struct DevBuf {
+    lbve* h = nullptr;
     void* p = nullptr;
-    ~DevBuf() { if (p) cudaFree(p); }
+    int get(lbve* hh, size_t bytes) {
+        h = hh;
+        return dev_alloc(hh, &p, bytes);
+    }
+    ~DevBuf() { if (h) dev_free(h, p); }
 };
 
 template <int Q>
@@ -1363,21 +1407,17 @@ int backward_impl(lbve* h, const double* dL_du, const double* dL_ds, double* gra
     const size_t pop_b = sizeof(double) * h->Q * Np;
     // work buffers
     DevBuf lam_n, lamX, lamK, lam_trp, lam_kt, lam_th, seeds, tape, ur, cnt, fin;
-    LBVE_CUDA(cudaMalloc(&lam_n.p, 2 * pop_b));
-    LBVE_CUDA(cudaMalloc(&lamX.p, hist_b));
-    LBVE_CUDA(cudaMalloc(&lamK.p, hist_b));
-    LBVE_CUDA(cudaMalloc(&lam_trp.p, sizeof(double) * Np));
-    LBVE_CUDA(cudaMalloc(&lam_kt.p, sizeof(double) * DD * Np));
-    LBVE_CUDA(cudaMalloc(&lam_th.p, sizeof(double) * 4 * Np));
-    LBVE_CUDA(cudaMalloc(&seeds.p, sizeof(double) * (D + NS) * Np));
     const size_t step_b = pop_b + 2 * hist_b + sizeof(double) * Np;   // pops, X, K, tr_prev
-    LBVE_CUDA(cudaMalloc(&tape.p, step_b * (size_t)K));
-    LBVE_CUDA(cudaMalloc(&ur.p, sizeof(double) * D * Np));
-    LBVE_CUDA(cudaMalloc(&cnt.p, sizeof(long long)));
     size_t img = 0;
     lbve_checkpoint_size(h, &img);
-    LBVE_CUDA(cudaMalloc(&fin.p, img));
-    int rc = lbve_checkpoint_save(h, fin.p, 1, s);   // the final state, restored at the end
+    int rc;
+    if ((rc = lam_n.get(h, 2 * pop_b)) || (rc = lamX.get(h, hist_b)) || (rc = lamK.get(h, hist_b)) ||
+        (rc = lam_trp.get(h, sizeof(double) * Np)) || (rc = lam_kt.get(h, sizeof(double) * DD * Np)) ||
+        (rc = lam_th.get(h, sizeof(double) * 4 * Np)) || (rc = seeds.get(h, sizeof(double) * (D + NS) * Np)) ||
+        (rc = tape.get(h, step_b * (size_t)K)) || (rc = ur.get(h, sizeof(double) * D * Np)) ||
+        (rc = cnt.get(h, sizeof(long long))) || (rc = fin.get(h, img)))
+        return rc;
+    rc = lbve_checkpoint_save(h, fin.p, 1, s);   // the final state, restored at the end
     if (rc) return rc;
     LBVE_CUDA(cudaMemsetAsync(lam_n.p, 0, 2 * pop_b, s));
     LBVE_CUDA(cudaMemsetAsync(lamX.p, 0, hist_b, s));
@@ -1536,7 +1576,7 @@ int lbve_set_sweep_config(lbve_t* h, int32_t slot_chunks, int32_t cta_tasks) {
     }
     if (slot_chunks > h->part_S) {
         const size_t old_bytes = h->hesz * (size_t)h->part_S * h->NS * h->Npad;
-        cudaFree(h->part);
+        dev_free(h, h->part);
         h->bytes -= old_bytes;
         h->part = nullptr;
         h->part_S = 0;

@@ -35,7 +35,7 @@ EXPORTS = [
     "lbve_fields_host_fixed", "lbve_create_batch", "lbve_channel_nodes", "lbve_sweep_config",
     "lbve_create_tangent", "lbve_tangent_fields", "lbve_checkpoint_size", "lbve_checkpoint_save",
     "lbve_checkpoint_restore", "lbve_create_adjoint", "lbve_backward", "lbve_set_pressure_step",
-    "lbve_set_probes", "lbve_probe_read", "lbve_set_sweep_config",
+    "lbve_set_probes", "lbve_probe_read", "lbve_set_sweep_config", "lbve_create_ex",
 ]
 
 
@@ -47,6 +47,41 @@ class lbve_channel_desc(C.Structure):
         ("hist_storage", C.c_int32), ("pop_precision", C.c_int32), ("trace_coupling", C.c_int32),
         ("model", C.c_int32), ("x_boundary", C.c_int32), ("dp", C.c_double),
     ]
+
+
+ALLOC_FN = C.CFUNCTYPE(C.c_void_p, C.c_size_t, C.c_void_p, C.c_void_p)
+FREE_FN = C.CFUNCTYPE(None, C.c_void_p, C.c_void_p, C.c_void_p)
+
+
+class lbve_allocator(C.Structure):
+    _fields_ = [("alloc", ALLOC_FN), ("free", FREE_FN), ("ctx", C.c_void_p)]
+
+
+def make_allocator(alloc, free) -> lbve_allocator:
+    """lbve_allocator calling alloc(bytes, stream) -> device pointer (int, 0/None on failure) and
+    free(ptr, stream); stream is the raw cudaStream_t as an int, or None for the legacy default stream.
+    Exceptions inside the callbacks count as a failed allocation (alloc) or are dropped (free)."""
+    def _alloc(n, stream, ctx):
+        try:
+            return alloc(int(n), stream) or None
+        except Exception:
+            return None
+
+    def _free(ptr, stream, ctx):
+        try:
+            free(ptr, stream)
+        except Exception:
+            pass
+
+    return lbve_allocator(ALLOC_FN(_alloc), FREE_FN(_free), None)
+
+
+def torch_allocator(device: int | None = None) -> lbve_allocator:
+    """lbve_allocator on PyTorch's CUDA caching allocator (blocks are 512-byte aligned)."""
+    import torch
+    dev = torch.cuda.current_device() if device is None else device
+    return make_allocator(lambda n, stream: torch.cuda.caching_allocator_alloc(n, dev, stream),
+                          lambda ptr, stream: torch.cuda.caching_allocator_delete(ptr))
 
 
 class LbveError(RuntimeError):
@@ -77,6 +112,7 @@ def load(path: str | None = None):
         lib.lbve_destroy.argtypes = [vp]
         lib.lbve_destroy.restype = None
         lib.lbve_create_batch.argtypes = [C.POINTER(lbve_channel_desc), i32, dp, C.POINTER(vp)]
+        lib.lbve_create_ex.argtypes = [C.POINTER(lbve_channel_desc), i32, dp, C.POINTER(lbve_allocator), C.POINTER(vp)]
         lib.lbve_create_tangent.argtypes = [C.POINTER(lbve_channel_desc), dp, C.POINTER(vp)]
         lib.lbve_create_adjoint.argtypes = [C.POINTER(lbve_channel_desc), dp, i32, C.POINTER(vp)]
         lib.lbve_backward.argtypes = [vp, dp, dp, dp, vp]
@@ -172,6 +208,26 @@ def lbve_create_batch(descs, rho_init: np.ndarray | None = None) -> int:
     return h.value
 
 
+_ALLOCATORS = {}   # handle -> lbve_allocator kept alive while the handle exists
+
+
+def lbve_create_ex(descs, rho_init: np.ndarray | None = None, allocator: lbve_allocator | None = None) -> int:
+    """lbve_create_batch with the handle's device memory from `allocator` (None: cudaMalloc)."""
+    lib = load()
+    descs = list(descs) if isinstance(descs, (list, tuple)) else [descs]
+    arr = (lbve_channel_desc * len(descs))(*descs)
+    h = C.c_void_p()
+    ri = None
+    if rho_init is not None:
+        ri = np.ascontiguousarray(rho_init, dtype=np.float64).ravel()
+    rc = lib.lbve_create_ex(arr, len(descs), ri.ctypes.data_as(C.POINTER(C.c_double)) if ri is not None else None,
+                            C.byref(allocator) if allocator is not None else None, C.byref(h))
+    _check(rc, "lbve_create_ex")
+    if allocator is not None:
+        _ALLOCATORS[h.value] = allocator
+    return h.value
+
+
 def lbve_create_tangent(desc: lbve_channel_desc, rho_init: np.ndarray | None = None) -> int:
     lib = load()
     h = C.c_void_p()
@@ -258,6 +314,7 @@ def lbve_set_sweep_config(h: int, slot_chunks: int, cta_tasks: int) -> None:
 
 def lbve_destroy(h: int) -> None:
     load().lbve_destroy(h)
+    _ALLOCATORS.pop(h, None)
 
 
 def lbve_set_force(h: int, g, channel: int = -1, stream=None) -> None:
@@ -395,14 +452,18 @@ class Channel:
     """Owns one lbve handle (one channel, or a batch when given a list of descriptions).  fields() returns
     host arrays in the oracle's [node][component] layout; channel_fields(c) slices one channel."""
 
-    def __init__(self, desc, rho_init=None):
+    def __init__(self, desc, rho_init=None, allocator: lbve_allocator | None = None):
         if isinstance(desc, (list, tuple)):
             self.descs = list(desc)
             self.desc = self.descs[0]
-            self.h = lbve_create_batch(self.descs, rho_init)
         else:
             self.descs = [desc]
             self.desc = desc
+        if allocator is not None:
+            self.h = lbve_create_ex(self.descs, rho_init, allocator)
+        elif len(self.descs) > 1:
+            self.h = lbve_create_batch(self.descs, rho_init)
+        else:
             self.h = lbve_create(desc, rho_init)
         self.d = 2 if self.desc.lattice == LBVE_D2Q9 else 3
         self.N = sum(d.nx * d.ny * d.nz for d in self.descs)

@@ -213,12 +213,57 @@ def oracle_sample(steps: int | None = None, budget_s: float = 12.0, warmup: int 
     return upd / dt, sample, n, dt, upd
 
 
+def oracle_sample_batch(descs, steps: int, warmup: int = 1):
+    """The FP64 oracle on one column (x-invariant flow) of each of the first two channels of a batch or
+    duct workload, full width and history: `warmup` untimed steps, then `steps` timed ones.  Returns the
+    rate in node-history updates/s and a description of the sample."""
+    import oracle
+    chans = []
+    for d in descs[:2]:
+        lat = oracle.D2Q9 if d.lattice == 9 else oracle.D3Q19
+        chans.append(oracle.Channel(lat, 1, d.ny, d.nz, tau_lb=d.tau_lb, G_inf=d.G_inf, tau=d.tau,
+                                    gamma_c=d.gamma_c, g=tuple(d.g), C=d.hist_C, B=d.hist_B, wall_z=bool(d.wall_z),
+                                    model={0: oracle.NLM, 2: oracle.WM}.get(d.model, oracle.NLM)))
+    for ch in chans:
+        ch.step(max(1, warmup))
+    t_start = chans[0].t
+    t0 = time.perf_counter()
+    for ch in chans:
+        ch.step(steps)
+    dt = time.perf_counter() - t0
+    d0 = descs[0]
+    pts = [len(oracle.schedule(d0.hist_C, d0.hist_B, t)[0]) for t in range(t_start, t_start + steps)]
+    nodes = sum(d.ny * d.nz for d in descs[:2])
+    upd = nodes * sum(pts)
+    for ch in chans:
+        ch.close()
+    sample = (f"one column of channels 0-{len(chans) - 1} ({nodes} nodes), L = {d0.hist_B * d0.hist_C}, "
+              f"steps {t_start}..{t_start + steps - 1} ({dt:.1f} s)")
+    return upd / dt, sample, steps, dt, upd
+
+
 def run_reference(args, rank, world):
     if rank != 0:
         return
+    metric = METRIC_NODES if args.model == "inlm" else METRIC
+    if args.workload != "channel":
+        from paper_1504_06123_gb300 import configs
+        from paper_1504_06123_gb300 import lbve as L
+        name, descs, _, _ = workload_descs(args, L, configs)
+        val, sample, n, dt, upd = oracle_sample_batch(descs, steps=args.steps, warmup=args.warmup)
+        line = {
+            "metric": metric, "value": val, "unit": metric, "n_gpus": args.gpus, "steps": n,
+            "warmup": args.warmup, "ms_per_step": 1e3 * dt / n, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f64", "data": "synthetic", "impl": "reference",
+            "config": {"workload": name, "sample": sample},
+            "cpu_baseline": {"value": val, "unit": metric, "cores": 1, "kind": "oracle", "sample": sample},
+            "e2e": {"value": val, "unit": metric, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+            "gpu_launches": 0,
+        }
+        print(json.dumps(line), flush=True)
+        return
     # each step: one oracle step of the sample (about 0.1 s on one core)
     val, sample, n, dt, upd = oracle_sample(steps=args.steps, warmup=args.warmup, model=args.model)
-    metric = METRIC_NODES if args.model == "inlm" else METRIC
     line = {
         "metric": metric, "value": val, "unit": metric, "n_gpus": args.gpus, "steps": n, "warmup": args.warmup,
         "ms_per_step": 1e3 * dt / n, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,

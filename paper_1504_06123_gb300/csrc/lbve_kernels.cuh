@@ -225,60 +225,64 @@ template <> struct FastMath<float> {
     __device__ static __forceinline__ float sqrt_pos(float x) { return x > 0.0f ? x * rsqrtf(x) : 0.0f; }
 };
 
+// The integrand of Eq. (gitt) at one point, added to acc (symmetric components xx, yy, [zz,] xy, [xz, yz]):
+// w G(t, t') (E kap E^T + (E kap E^T)^T) = w G E Dm E^T with the rate of strain Dm = kap + kap^T, formed as
+// F = E Dm = Dm + X Dm, then the upper triangle of F E^T = F + F X^T.
 // WM = true: the White-Metzner form (Sec. II): the second exponential of Eq. (nlmax) takes the strain
 // accumulated since the point was created, `strain`, instead of age * gammadot(point).
 template <int D, typename real, bool WM = false>
 __device__ __forceinline__ void point_integrand(const real* X, const real* kap, real age, real w,
                                                 real inv_tau, real inv_gc, real* acc, real strain = real(0)) {
     constexpr int DD = D * D;
-    // M = E kap E^T with E = 1 + X
-    real EK[DD];
+    real Dm[DD];
+#pragma unroll
+    for (int r = 0; r < D; ++r) {
+        Dm[r * D + r] = kap[r * D + r] + kap[r * D + r];
+#pragma unroll
+        for (int c = r + 1; c < D; ++c) Dm[r * D + c] = Dm[c * D + r] = kap[r * D + c] + kap[c * D + r];
+    }
+    real F[DD];
 #pragma unroll
     for (int r = 0; r < D; ++r)
 #pragma unroll
         for (int c = 0; c < D; ++c) {
-            real s = kap[r * D + c];
+            real s = Dm[r * D + c];
 #pragma unroll
-            for (int k = 0; k < D; ++k) s += X[r * D + k] * kap[k * D + c];
-            EK[r * D + c] = s;
+            for (int k = 0; k < D; ++k) s += X[r * D + k] * Dm[k * D + c];
+            F[r * D + c] = s;
         }
-    real M[DD];
+    auto S = [&](int r, int c) {   // (F E^T)_rc
+        real s = F[r * D + c];
 #pragma unroll
-    for (int r = 0; r < D; ++r)
-#pragma unroll
-        for (int c = 0; c < D; ++c) {
-            real s = EK[r * D + c];
-#pragma unroll
-            for (int k = 0; k < D; ++k) s += EK[r * D + k] * X[c * D + k];
-            M[r * D + c] = s;
-        }
+        for (int k = 0; k < D; ++k) s += F[r * D + k] * X[c * D + k];
+        return s;
+    };
     real gw;
     if (WM) {
         gw = w * FastMath<real>::exp_neg(age * inv_tau + strain * inv_gc);
     } else {
-        // local shear rate of the point: gammadot^2 = (1/2) tr D^2, D = kap + kap^T
-        real trD2 = 0;
+        // local shear rate of the point: gammadot^2 = (1/2) tr Dm^2
+        real h = 0;
 #pragma unroll
-        for (int r = 0; r < D; ++r)
+        for (int r = 0; r < D; ++r) {
+            h += real(0.5) * Dm[r * D + r] * Dm[r * D + r];
 #pragma unroll
-            for (int c = 0; c < D; ++c) {
-                const real Drc = kap[r * D + c] + kap[c * D + r];
-                trD2 += Drc * Drc;
-            }
-        const real gd = FastMath<real>::sqrt_pos(real(0.5) * trD2);
+            for (int c = r + 1; c < D; ++c) h += Dm[r * D + c] * Dm[r * D + c];
+        }
+        const real gd = FastMath<real>::sqrt_pos(h);
         gw = w * FastMath<real>::exp_neg(age * (inv_tau + gd * inv_gc));
     }
     if (D == 2) {
-        acc[0] += gw * (M[0] + M[0]);
-        acc[1] += gw * (M[3] + M[3]);
-        acc[2] += gw * (M[1] + M[2]);
+        acc[0] += gw * S(0, 0);
+        acc[1] += gw * S(1, 1);
+        acc[2] += gw * S(0, 1);
     } else {
-        acc[0] += gw * (M[0] + M[0]);
-        acc[1] += gw * (M[4] + M[4]);
-        acc[2] += gw * (M[8] + M[8]);
-        acc[3] += gw * (M[1] + M[3]);
-        acc[4] += gw * (M[2] + M[6]);
-        acc[5] += gw * (M[5] + M[7]);
+        acc[0] += gw * S(0, 0);
+        acc[1] += gw * S(1, 1);
+        acc[2] += gw * S(2, 2);
+        acc[3] += gw * S(0, 1);
+        acc[4] += gw * S(0, 2);
+        acc[5] += gw * S(1, 2);
     }
 }
 

@@ -950,30 +950,41 @@ __global__ void __launch_bounds__(256, 2) k_sweep_s16(CommitS16 a, const double*
 
         const int l0 = chunk * chunk_len;
         const int l1 = min(L, l0 + chunk_len);
-        // no branch on empty or retired slots: they have weight 0 and hold finite data from their
-        // last use, so they add exactly 0; the straight loop lets loads of the next slot overlap
-#pragma unroll 2
+        // the packed words of one slot: exponent bytes and mantissa words of Q - 1 and kappa.  The next
+        // slot's words are loaded before this slot is decoded (one slot of loads always in flight).  No
+        // branch on empty or retired slots: they have weight 0 and hold finite data from their last use,
+        // so they add exactly 0.
+        struct Packed { unsigned qe, ke; VW qv[DD], kv[DD]; };
+        auto load_packed = [&](int l, Packed& pk) {
+            pk.qe = VN == 4 ? *reinterpret_cast<const unsigned*>(a.Qe + (long long)l * Np + n0)
+                            : *reinterpret_cast<const unsigned short*>(a.Qe + (long long)l * Np + n0);
+            pk.ke = VN == 4 ? *reinterpret_cast<const unsigned*>(a.Ke + (long long)l * Np + n0)
+                            : *reinterpret_cast<const unsigned short*>(a.Ke + (long long)l * Np + n0);
+#pragma unroll
+            for (int c = 0; c < DD; ++c) {
+                pk.qv[c] = *reinterpret_cast<const VW*>(a.Qm + ((long long)l * DD + c) * Np + n0);
+                pk.kv[c] = *reinterpret_cast<const VW*>(a.Km + ((long long)l * DD + c) * Np + n0);
+            }
+        };
+        Packed nxt;
+        if (l0 < l1) load_packed(l0, nxt);
         for (int l = l0; l < l1; ++l) {
+            const Packed cur = nxt;
+            if (l + 1 < l1) load_packed(l + 1, nxt);
             const float w = s_w[l];
-            const unsigned qe = VN == 4 ? *reinterpret_cast<const unsigned*>(a.Qe + (long long)l * Np + n0)
-                                        : *reinterpret_cast<const unsigned short*>(a.Qe + (long long)l * Np + n0);
-            const unsigned ke = VN == 4 ? *reinterpret_cast<const unsigned*>(a.Ke + (long long)l * Np + n0)
-                                        : *reinterpret_cast<const unsigned short*>(a.Ke + (long long)l * Np + n0);
             float kap[VN][DD], Qd[VN][DD];
             {
                 S16Scale sq[VN], sk[VN];
 #pragma unroll
-                for (int j = 0; j < VN; ++j) { sq[j] = S16Scale(s16_exp(qe, j)); sk[j] = S16Scale(s16_exp(ke, j)); }
+                for (int j = 0; j < VN; ++j) { sq[j] = S16Scale(s16_exp(cur.qe, j)); sk[j] = S16Scale(s16_exp(cur.ke, j)); }
 #pragma unroll
                 for (int c = 0; c < DD; ++c) {
-                    const VW qv = *reinterpret_cast<const VW*>(a.Qm + ((long long)l * DD + c) * Np + n0);
-                    const VW kv = *reinterpret_cast<const VW*>(a.Km + ((long long)l * DD + c) * Np + n0);
 #pragma unroll
                     for (int p2 = 0; p2 < VN / 2; ++p2) {
-                        Qd[2 * p2][c] = s16_lo(qv.v[p2], sq[2 * p2]);
-                        Qd[2 * p2 + 1][c] = s16_hi(qv.v[p2], sq[2 * p2 + 1]);
-                        kap[2 * p2][c] = s16_lo(kv.v[p2], sk[2 * p2]);
-                        kap[2 * p2 + 1][c] = s16_hi(kv.v[p2], sk[2 * p2 + 1]);
+                        Qd[2 * p2][c] = s16_lo(cur.qv[c].v[p2], sq[2 * p2]);
+                        Qd[2 * p2 + 1][c] = s16_hi(cur.qv[c].v[p2], sq[2 * p2 + 1]);
+                        kap[2 * p2][c] = s16_lo(cur.kv[c].v[p2], sk[2 * p2]);
+                        kap[2 * p2 + 1][c] = s16_hi(cur.kv[c].v[p2], sk[2 * p2 + 1]);
                     }
                 }
             }

@@ -62,6 +62,9 @@ def parse():
                          "boundary along x with the equivalent drop dp = rho0 g nx per period")
     ap.add_argument("--nx", type=int, default=None,
                     help="narrower channel (same rows, same history) for profiler captures; not a bench line")
+    ap.add_argument("--sweep-shape", default=None,
+                    help="S,cta: pin the history sweep's launch shape (slot chunks, 1 = CTA tasks) after the "
+                         "autotuner, e.g. to profile the shape a timed run chose")
     return ap.parse_args()
 
 
@@ -375,6 +378,9 @@ def run_ours(args, rank, world, local_rank):
     stream = torch.cuda.current_stream()
     ch = L.Channel(descs if len(descs) > 1 else descs[0], rho)
     K, W = args.steps, args.warmup
+    if args.sweep_shape:
+        S_pin, cta_pin = (int(v) for v in args.sweep_shape.split(","))
+        L.lbve_set_sweep_config(ch.h, S_pin, cta_pin)
     probes = 0
     if args.workload == "regime":
         from paper_1504_06123_gb300 import regime

@@ -377,7 +377,11 @@ int sweep_autotune(lbve* h) {
         cudaEvent_t e0, e1;
         LBVE_CUDA(cudaEventCreate(&e0));
         LBVE_CUDA(cudaEventCreate(&e1));
-        int reps = 3;   // launches timed per candidate; one once a launch takes over a millisecond
+        // launches timed per candidate: one for a history of a gigabyte or more (a launch then takes
+        // well over 100 us, long against the timer), three below; fixed by the size, so that the number of
+        // launches at create does not depend on timings
+        const size_t hist_bytes = (size_t)h->L * h->Npad * h->D * h->D * 2 * (HK == 2 ? 2 : h->hesz);
+        const int reps = hist_bytes >= ((size_t)1 << 30) ? 1 : 3;
         for (const Cand& c : cand) {
             h->S = (int)c.S;
             h->sweep_cta = c.cta;
@@ -398,7 +402,6 @@ int sweep_autotune(lbve* h) {
             LBVE_CUDA(cudaEventElapsedTime(&ms, e0, e1));
             ms /= (float)reps;
             if (ms < best) { best = ms; best_c = c; }
-            if (ms > 1.0f) reps = 1;
         }
         cudaEventDestroy(e0);
         cudaEventDestroy(e1);

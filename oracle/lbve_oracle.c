@@ -23,6 +23,21 @@
  *   n-1/2 (half-way bounce-back).
  *   Lattice units dt = dx = 1.
  *
+ * Pins (tests/test_oracle_*.py check this file against the paper and the mathematics, not against itself):
+ * exp of the factors vs scipy's expm; the history grid vs an independent enumeration; E(t,t) = 1; constant
+ * simple shear in closed form; the Maxwell / nlM continuum limit; brute force from raw per-step factor
+ * products on tiny grids; Newtonian Poiseuille with the BGK bounce-back slip and its Fourier startup
+ * series; the UCM steady parabola; the nlM force balance; mass conservation of the density source;
+ * x-invariance and channel / duct symmetries; post-collision moments of Eq. (bodyforce); Eq. (inlM) vs the
+ * nilpotent closed form, the extensional geometric series, the steady UCM solve and the Laplace integral;
+ * White-Metzner vs brute-force strain sums; the pressure-step boundary vs the BGK Poiseuille solution and
+ * the equivalent body force; the startup / cessation features Sec. IV states (overshoot, counter-flow,
+ * sign and decay of the normal-stress difference, Newtonian / UCM symmetry).
+ * Parity unpinned beyond the stated readings: the kappa averaging of a merge (pinned only by the
+ * brute-force check of the merge rule), the choice of trace terms with trace_full = 0 (pinned only through
+ * mass conservation), and the wall-adjacent finite-difference stencil (exact on parabolas; the steady
+ * channels pin it only to 1e-3).
+ *
  * Readings of the paper taken here (the same readings are used by the CUDA path):
  *   - factor for the interval [t, t+1] is exp(kappa(t)) (explicit, Eq. (eeval));
  *   - the new point of step t sits at age 0 with E = 1 and kappa(t);

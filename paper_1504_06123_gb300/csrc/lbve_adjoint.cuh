@@ -6,12 +6,19 @@
 // theta = (G_inf, tau, gamma_c, g_x).  The forward quantities of step t are recomputed per node from the
 // state before the step (taped per step inside a checkpoint segment by the runtime).
 //
-// Two kernels per step:
-//   k_adj_node   one thread per node: forward recompute (moments, kappa(t), history sweep, sigma,
-//                collision), then the adjoint of the collision + streaming (a pull from the neighbours),
-//                of the commit (merges and new point in reverse order) and of the history sweep (point
-//                integrands, in-place advance, exp(kappa(t-1)) - 1).  Writes lambda of kappa(t) and the
-//                node's part of lambda(populations).
+// Five kernels per step (the history parts split over slot chunks like the forward sweep, so that the
+// O(nodes x points) work runs on (node, chunk) threads; every chunk's sums are added in chunk order):
+//   k_adj_sig    (node, chunk) threads: forward recompute of the history sweep of step t on the taped
+//                history -- partial sums of the integrand (the stress before the new point);
+//   k_adj_node   one thread per node: forward recompute (moments, kappa(t), sigma from the partial sums,
+//                collision), then the adjoint of the collision + streaming (a pull from the neighbours) and
+//                of the commit (merges and new point in reverse order); writes the pairing matrix of
+//                lambda(sigma_struc) for the sweep's adjoint, lambda of kappa(t) and the node's part of
+//                lambda(populations);
+//   k_adj_hist   (node, chunk) threads: adjoint of the history sweep (point integrands, in-place advance)
+//                with partial sums of lambda(A), lambda(1/tau), lambda(1/gamma_c) per chunk;
+//   k_adj_fin    one thread per node: the chunk sums, the adjoint of A = exp(kappa(t-1)) - 1 and the rate
+//                parts of dL/dtheta;
 //   k_adj_fd     one thread per node: transpose of the finite-difference stencil (gathers lambda kappa(t)
 //                from the nodes whose stencil reads this node) and the adjoint of the raw moments.
 #pragma once
@@ -155,9 +162,75 @@ struct AdjArgs {
     double* lam_theta;      // [4][Npad] += per-node parts of dL/dtheta
     const double* seed_u;   // [D][Npad] dL/du of this step's velocity (last step), or nullptr
     const double* seed_s;   // [NS][Npad] dL/dsigma of this step (last step), or nullptr
+    double* part_sig;       // [S][NS][Npad] k_adj_sig: partial sums of the forward integrand
+    double* lt;             // [DD][Npad] pairing matrix of lambda(sigma_struc) / G_inf-scaled (k_adj_node)
+    double* part_adj;       // [S][DD + 2][Npad] k_adj_hist: partial lambda(A), lambda(1/tau), lambda(1/gamma_c)
     long long t;
-    int B, C;
+    int B, C, S;            // history grid; S slot chunks of the split kernels
 };
+
+// Slot range [l0, l1) of chunk `chunk` of S over Ls slots.
+__device__ inline void adj_chunk(int Ls, int S, int chunk, int* l0, int* l1) {
+    const int len = (Ls + S - 1) / S;
+    *l0 = min(Ls, chunk * len);
+    *l1 = min(Ls, *l0 + len);
+}
+
+// The per-CTA table of slot roles at step t (ages, weights, merge partners; same as the sweep's).
+__device__ inline void adj_table(const AdjArgs& a, float* s_age, float* s_w, int* s_part, BlockStep* s_bs) {
+    const int Ls = a.B * a.C;
+    if (threadIdx.x == 0) sched_step(a.B, a.C, a.t, s_bs);
+    __syncthreads();
+    for (int l = threadIdx.x; l < Ls; l += blockDim.x) {
+        int age, part;
+        const float w = sched_slot_role(s_bs, a.C, l / a.C, l % a.C, &age, &part);
+        s_age[l] = (float)age;
+        s_w[l] = w;
+        s_part[l] = part;
+    }
+    __syncthreads();
+}
+
+// Forward recompute of the history sweep of step t on the taped history: per (node, chunk) thread the
+// partial sum of the integrand over the chunk's slots (point_update on a copy; the tape is read only).
+template <int D>
+__global__ void __launch_bounds__(128) k_adj_sig(AdjArgs a, Geom g, AdjPar p) {
+    constexpr int DD = D * D;
+    constexpr int NS = D == 2 ? 3 : 6;
+    const int Ls = a.B * a.C;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    float* s_age = reinterpret_cast<float*>(smem_raw);
+    float* s_w = s_age + Ls;
+    int* s_part = reinterpret_cast<int*>(s_w + Ls);
+    BlockStep* s_bs = reinterpret_cast<BlockStep*>(s_part + Ls);
+    adj_table(a, s_age, s_w, s_part, s_bs);
+    const long long idx = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    const int n = (int)(idx % g.Npad), chunk = (int)(idx / g.Npad);
+    if (chunk >= a.S || n >= g.N) return;
+    const long long Np = g.Npad;
+    const long long s_last = (long long)(a.B - 1) * a.C + s_bs[a.B - 1].head_prev;
+    double kl[DD], A[DD];
+    for (int c = 0; c < DD; ++c) kl[c] = a.K[(s_last * DD + c) * Np + n];
+    expm1_mat<D>(kl, A);
+    double acc[NS];
+    for (int i = 0; i < NS; ++i) acc[i] = 0.0;
+    int l0, l1;
+    adj_chunk(Ls, a.S, chunk, &l0, &l1);
+    for (int l = l0; l < l1; ++l) {
+        const float w = s_w[l];
+        if (w == 0.0f) continue;
+        double Xl[DD], kap[DD];
+        for (int c = 0; c < DD; ++c) {
+            Xl[c] = a.X[((long long)l * DD + c) * Np + n];
+            kap[c] = a.K[((long long)l * DD + c) * Np + n];
+        }
+        const int part = s_part[l];
+        if (part >= 0)
+            for (int c = 0; c < DD; ++c) kap[c] = 0.5 * (kap[c] + a.K[((long long)part * DD + c) * Np + n]);
+        point_update<D>(Xl, A, kap, (double)s_age[l], (double)w, p.inv_tau, p.inv_gc, acc);
+    }
+    for (int i = 0; i < NS; ++i) a.part_sig[((long long)chunk * NS + i) * Np + n] = acc[i];
+}
 
 template <int Q>
 __global__ void __launch_bounds__(64) k_adj_node(AdjArgs a, Geom g, AdjPar p) {
@@ -171,16 +244,7 @@ __global__ void __launch_bounds__(64) k_adj_node(AdjArgs a, Geom g, AdjPar p) {
     float* s_w = s_age + Ls;
     int* s_part = reinterpret_cast<int*>(s_w + Ls);
     BlockStep* s_bs = reinterpret_cast<BlockStep*>(s_part + Ls);
-    if (threadIdx.x == 0) sched_step(a.B, a.C, a.t, s_bs);
-    __syncthreads();
-    for (int l = threadIdx.x; l < Ls; l += blockDim.x) {
-        int age, part;
-        const float w = sched_slot_role(s_bs, a.C, l / a.C, l % a.C, &age, &part);
-        s_age[l] = (float)age;
-        s_w[l] = w;
-        s_part[l] = part;
-    }
-    __syncthreads();
+    adj_table(a, s_age, s_w, s_part, s_bs);
     const int n = blockIdx.x * blockDim.x + threadIdx.x;
     if (n >= g.N) return;
     const long long Np = g.Npad;
@@ -197,25 +261,10 @@ __global__ void __launch_bounds__(64) k_adj_node(AdjArgs a, Geom g, AdjPar p) {
     }
     double kt[DD];
     kappa_fd<D>(a.u_raw, Np, ch, n, kt);
-    const long long s_last = (long long)(a.B - 1) * a.C + s_bs[a.B - 1].head_prev;
-    double kl[DD], A[DD];
-    for (int c = 0; c < DD; ++c) kl[c] = a.K[(s_last * DD + c) * Np + n];
-    expm1_mat<D>(kl, A);
-    double acc[NS];
+    double acc[NS];   // the history sum of step t (k_adj_sig's chunks, in chunk order)
     for (int i = 0; i < NS; ++i) acc[i] = 0.0;
-    for (int l = 0; l < Ls; ++l) {
-        const float w = s_w[l];
-        if (w == 0.0f) continue;
-        double Xl[DD], kap[DD];
-        for (int c = 0; c < DD; ++c) {
-            Xl[c] = a.X[((long long)l * DD + c) * Np + n];
-            kap[c] = a.K[((long long)l * DD + c) * Np + n];
-        }
-        const int part = s_part[l];
-        if (part >= 0)
-            for (int c = 0; c < DD; ++c) kap[c] = 0.5 * (kap[c] + a.K[((long long)part * DD + c) * Np + n]);
-        point_update<D>(Xl, A, kap, (double)s_age[l], (double)w, p.inv_tau, p.inv_gc, acc);
-    }
+    for (int c = 0; c < a.S; ++c)
+        for (int i = 0; i < NS; ++i) acc[i] += a.part_sig[((long long)c * NS + i) * Np + n];
     double newp[NS];   // the point created now: (kappa + kappa^T)/2 packed
     if (D == 2) {
         newp[0] = kt[0]; newp[1] = kt[3]; newp[2] = 0.5 * (kt[1] + kt[2]);
@@ -375,12 +424,54 @@ __global__ void __launch_bounds__(64) k_adj_node(AdjArgs a, Geom g, AdjPar p) {
         }
     }
 
-    // ---------------- adjoint of the history sweep ----------------
-    double Lt[DD], lamA[DD];
-    packed_to_pairing<D>(lam_acc, Lt);
-    for (int c = 0; c < DD; ++c) lamA[c] = 0.0;
+    // ---------------- pairing matrix for the adjoint of the history sweep (k_adj_hist) ----------------
+    {
+        double Lt[DD];
+        packed_to_pairing<D>(lam_acc, Lt);
+        for (int c = 0; c < DD; ++c) a.lt[c * Np + n] = Lt[c];
+    }
+
+    // ---------------- outputs ----------------
+    for (int c = 0; c < DD; ++c) a.lam_kt[c * Np + n] = lam_kt[c];
+    for (int q = 0; q < Q; ++q) {
+        double l = lam_dr;
+        l += L::cx(q) * lam_J[0] + L::cy(q) * lam_J[1];
+        if (D == 3) l += L::cz(q) * lam_J[2];
+        a.lam_n0[q * Np + n] += l;
+    }
+    a.lam_theta[0 * Np + n] += lam_G;
+    a.lam_theta[3 * Np + n] += p.rho0 * lam_f[0];                                // f_x = rho0 g_x
+}
+
+// Adjoint of the history sweep of step t, per (node, chunk) thread over the chunk's slots: lambda of each
+// point's X and kappa (in place; the newer half of a merge has weight 0 and is not visited, so every lamK
+// entry has a single writer), and the chunk's partial lambda(A), lambda(1/tau), lambda(1/gamma_c).
+template <int D>
+__global__ void __launch_bounds__(128) k_adj_hist(AdjArgs a, Geom g, AdjPar p) {
+    constexpr int DD = D * D;
+    const int Ls = a.B * a.C;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    float* s_age = reinterpret_cast<float*>(smem_raw);
+    float* s_w = s_age + Ls;
+    int* s_part = reinterpret_cast<int*>(s_w + Ls);
+    BlockStep* s_bs = reinterpret_cast<BlockStep*>(s_part + Ls);
+    adj_table(a, s_age, s_w, s_part, s_bs);
+    const long long idx = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    const int n = (int)(idx % g.Npad), chunk = (int)(idx / g.Npad);
+    if (chunk >= a.S || n >= g.N) return;
+    const long long Np = g.Npad;
+    const long long s_last = (long long)(a.B - 1) * a.C + s_bs[a.B - 1].head_prev;
+    double kl[DD], A[DD], Lt[DD], lamA[DD];
+    for (int c = 0; c < DD; ++c) {
+        kl[c] = a.K[(s_last * DD + c) * Np + n];
+        Lt[c] = a.lt[c * Np + n];
+        lamA[c] = 0.0;
+    }
+    expm1_mat<D>(kl, A);
     double lam_it = 0.0, lam_ig = 0.0;
-    for (int l = 0; l < Ls; ++l) {
+    int l0, l1;
+    adj_chunk(Ls, a.S, chunk, &l0, &l1);
+    for (int l = l0; l < l1; ++l) {
         const float w = s_w[l];
         if (w == 0.0f) continue;
         double Xl[DD], Xn[DD], kap[DD], lX[DD], lk[DD];
@@ -424,26 +515,40 @@ __global__ void __launch_bounds__(64) k_adj_node(AdjArgs a, Geom g, AdjPar p) {
             for (int c = 0; c < DD; ++c) a.lamK[((long long)l * DD + c) * Np + n] += lk[c];
         }
     }
-    // A = exp(kappa(t-1)) - 1 with kappa(t-1) the kappa of the newest stored point
-    {
-        double lk[DD];
-        for (int c = 0; c < DD; ++c) lk[c] = 0.0;
-        expm1_adjoint<D>(kl, lamA, lk);
-        for (int c = 0; c < DD; ++c) a.lamK[(s_last * DD + c) * Np + n] += lk[c];
-    }
+    double* out = a.part_adj + (long long)chunk * (DD + 2) * Np + n;
+    for (int c = 0; c < DD; ++c) out[c * Np] = lamA[c];
+    out[DD * Np] = lam_it;
+    out[(DD + 1) * Np] = lam_ig;
+}
 
-    // ---------------- outputs ----------------
-    for (int c = 0; c < DD; ++c) a.lam_kt[c * Np + n] = lam_kt[c];
-    for (int q = 0; q < Q; ++q) {
-        double l = lam_dr;
-        l += L::cx(q) * lam_J[0] + L::cy(q) * lam_J[1];
-        if (D == 3) l += L::cz(q) * lam_J[2];
-        a.lam_n0[q * Np + n] += l;
+// The chunk sums of k_adj_hist (chunk order), the adjoint of A = exp(kappa(t-1)) - 1 (kappa(t-1) is the kappa
+// of the newest stored point) and the rate parts of dL/dtheta.
+template <int D>
+__global__ void __launch_bounds__(128) k_adj_fin(AdjArgs a, Geom g, AdjPar p) {
+    constexpr int DD = D * D;
+    const int n = blockIdx.x * blockDim.x + threadIdx.x;
+    if (n >= g.N) return;
+    const long long Np = g.Npad;
+    double lamA[DD], lam_it = 0.0, lam_ig = 0.0;
+    for (int c = 0; c < DD; ++c) lamA[c] = 0.0;
+    for (int ch = 0; ch < a.S; ++ch) {
+        const double* in = a.part_adj + (long long)ch * (DD + 2) * Np + n;
+        for (int c = 0; c < DD; ++c) lamA[c] += in[c * Np];
+        lam_it += in[DD * Np];
+        lam_ig += in[(DD + 1) * Np];
     }
-    a.lam_theta[0 * Np + n] += lam_G;
+    BlockStep bs[LBVE_MAXB];
+    sched_step(a.B, a.C, a.t, bs);
+    const long long s_last = (long long)(a.B - 1) * a.C + bs[a.B - 1].head_prev;
+    double kl[DD], lk[DD];
+    for (int c = 0; c < DD; ++c) {
+        kl[c] = a.K[(s_last * DD + c) * Np + n];
+        lk[c] = 0.0;
+    }
+    expm1_adjoint<D>(kl, lamA, lk);
+    for (int c = 0; c < DD; ++c) a.lamK[(s_last * DD + c) * Np + n] += lk[c];
     a.lam_theta[1 * Np + n] += lam_it * (-1.0 / (p.tau * p.tau));                // d(1/tau)/dtau
     a.lam_theta[2 * Np + n] += isinf(p.gamma_c) ? 0.0 : lam_ig * (-1.0 / (p.gamma_c * p.gamma_c));
-    a.lam_theta[3 * Np + n] += p.rho0 * lam_f[0];                                // f_x = rho0 g_x
 }
 
 // Forward weight of node yn in the finite-difference stencil of node xn along `axis` (Sec. III:

@@ -1409,7 +1409,9 @@ int backward_impl(lbve* h, const double* dL_du, const double* dL_ds, double* gra
     const size_t hist_b = sizeof(double) * (size_t)h->L * DD * Np;
     const size_t pop_b = sizeof(double) * h->Q * Np;
     // work buffers
-    DevBuf lam_n, lamX, lamK, lam_trp, lam_kt, lam_th, seeds, tape, ur, cnt, fin;
+    DevBuf lam_n, lamX, lamK, lam_trp, lam_kt, lam_th, seeds, tape, ur, cnt, fin, psig, plt, padj;
+    // slot chunks of the split history kernels: about 64k (node, chunk) threads, at most 32 chunks
+    const int S = (int)std::max(1ll, std::min<long long>({32ll, (long long)h->L, (65536ll + h->N - 1) / h->N}));
     const size_t step_b = pop_b + 2 * hist_b + sizeof(double) * Np;   // pops, X, K, tr_prev
     size_t img = 0;
     lbve_checkpoint_size(h, &img);
@@ -1418,7 +1420,9 @@ int backward_impl(lbve* h, const double* dL_du, const double* dL_ds, double* gra
         (rc = lam_trp.get(h, sizeof(double) * Np)) || (rc = lam_kt.get(h, sizeof(double) * DD * Np)) ||
         (rc = lam_th.get(h, sizeof(double) * 4 * Np)) || (rc = seeds.get(h, sizeof(double) * (D + NS) * Np)) ||
         (rc = tape.get(h, step_b * (size_t)K)) || (rc = ur.get(h, sizeof(double) * D * Np)) ||
-        (rc = cnt.get(h, sizeof(long long))) || (rc = fin.get(h, img)))
+        (rc = cnt.get(h, sizeof(long long))) || (rc = fin.get(h, img)) ||
+        (rc = psig.get(h, sizeof(double) * (size_t)S * NS * Np)) || (rc = plt.get(h, sizeof(double) * DD * Np)) ||
+        (rc = padj.get(h, sizeof(double) * (size_t)S * (DD + 2) * Np)))
         return rc;
     rc = lbve_checkpoint_save(h, fin.p, 1, s);   // the final state, restored at the end
     if (rc) return rc;
@@ -1440,8 +1444,12 @@ int backward_impl(lbve* h, const double* dL_du, const double* dL_ds, double* gra
     const AdjPar p = adj_par(h);
     const int grid64 = (h->N + 63) / 64, grid128 = (h->N + 127) / 128;
     const size_t smem = sweep_smem_bytes(h->L);
-    if (smem > 48 * 1024)
+    if (smem > 48 * 1024) {
         LBVE_CUDA(cudaFuncSetAttribute(k_adj_node<Q>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+        LBVE_CUDA(cudaFuncSetAttribute(k_adj_sig<D>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+        LBVE_CUDA(cudaFuncSetAttribute(k_adj_hist<D>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    }
+    const int grid_chunks = (int)(((long long)S * Np + 127) / 128);
     const int rec = h->rec_K;
     h->rec_K = 0;   // the replay below must not record
     int cur_lam = 0;
@@ -1481,10 +1489,20 @@ int backward_impl(lbve* h, const double* dL_du, const double* dL_ds, double* gra
             a.lam_theta = (double*)lam_th.p;
             a.seed_u = t == T - 1 ? seed_u : nullptr;
             a.seed_s = t == T - 1 ? seed_s : nullptr;
+            a.part_sig = (double*)psig.p;
+            a.lt = (double*)plt.p;
+            a.part_adj = (double*)padj.p;
             a.t = t;
             a.B = h->d.hist_B;
             a.C = h->d.hist_C;
+            a.S = S;
+            k_adj_sig<D><<<grid_chunks, 128, smem, s>>>(a, g, p);
+            LBVE_CUDA(cudaGetLastError());
             k_adj_node<Q><<<grid64, 64, smem, s>>>(a, g, p);
+            LBVE_CUDA(cudaGetLastError());
+            k_adj_hist<D><<<grid_chunks, 128, smem, s>>>(a, g, p);
+            LBVE_CUDA(cudaGetLastError());
+            k_adj_fin<D><<<grid128, 128, 0, s>>>(a, g, p);
             LBVE_CUDA(cudaGetLastError());
             k_adj_fd<Q><<<grid128, 128, 0, s>>>(pops_t, (const double*)lam_kt.p, a.lam_n0, (double*)lam_th.p, g, p);
             LBVE_CUDA(cudaGetLastError());

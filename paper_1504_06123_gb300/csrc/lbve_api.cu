@@ -781,8 +781,12 @@ int tangent_step(lbve* h, int64_t n, cudaStream_t s) {
         Dual* dout = (Dual*)h->pops[h->cur ^ 1];
         k_moments_t<Q><<<grid, 128, 0, s>>>(din, (Dual*)h->u_raw, g, p, h->t_dev);
         LBVE_CUDA(cudaGetLastError());
+        k_sweep_t<D><<<(int)(((long long)h->S * h->Npad + 127) / 128), 128, smem, s>>>(
+            (Dual*)h->X, (const Dual*)h->K, (Dual*)h->part, g, p, h->t_dev, h->d.hist_B, h->d.hist_C, h->S);
+        LBVE_CUDA(cudaGetLastError());
         k_history_t<D><<<grid, 128, smem, s>>>((Dual*)h->X, (Dual*)h->K, (const Dual*)h->u_raw, (Dual*)h->kappa,
-                                               (Dual*)h->sigma, g, p, h->t_dev, h->d.hist_B, h->d.hist_C);
+                                               (Dual*)h->sigma, (const Dual*)h->part, g, p, h->t_dev, h->d.hist_B,
+                                               h->d.hist_C, h->S);
         LBVE_CUDA(cudaGetLastError());
         k_collide_t<Q><<<grid, 128, 0, s>>>(din, dout, (const Dual*)h->sigma, (Dual*)h->tr_prev, (Dual*)h->rho,
                                             (Dual*)h->u, g, p);
@@ -904,7 +908,17 @@ int create_tangent(const lbve_channel_desc* desc, const double* rho_init, lbve_t
     if (smem > 48 * 1024) {
         er = cudaFuncSetAttribute(h->D == 2 ? (const void*)k_history_t<2> : (const void*)k_history_t<3>,
                                   cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (er == cudaSuccess)
+            er = cudaFuncSetAttribute(h->D == 2 ? (const void*)k_sweep_t<2> : (const void*)k_sweep_t<3>,
+                                      cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         if (er != cudaSuccess) return fail(cuda_fail(er, "cudaFuncSetAttribute"));
+    }
+    // slot chunks of the dual sweep (about 64k (node, chunk) threads, at most 32) and their partial sums
+    h->S = (int)std::max(1ll, std::min<long long>({32ll, (long long)h->L, (65536ll + h->N - 1) / h->N}));
+    {
+        int rc2 = alloc(h, &h->part, sizeof(Dual) * (size_t)h->S * h->NS * h->Npad);
+        if (rc2) return fail(rc2);
+        h->part_S = h->S;
     }
     *out = h;
     return LBVE_OK;

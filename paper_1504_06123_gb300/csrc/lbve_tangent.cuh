@@ -101,22 +101,9 @@ __global__ void __launch_bounds__(128) k_moments_t(const Dual* __restrict__ dn, 
     for (int a = 0; a < D; ++a) u_raw[(long long)a * g.Npad + n] = (j[a] + 0.5 * p.f[a]) * inv;
 }
 
-// History, one thread per node over all slots, then the node's merges and new point (form "P": E - 1
-// advanced in place).
-template <int D>
-__global__ void __launch_bounds__(128) k_history_t(Dual* __restrict__ X, Dual* __restrict__ K,
-                                                   const Dual* __restrict__ u_raw, Dual* __restrict__ kappa_f,
-                                                   Dual* __restrict__ sigma_f, Geom g, TanPar p,
-                                                   const long long* t_dev, int B, int C) {
-    constexpr int DD = D * D;
-    constexpr int NS = D == 2 ? 3 : 6;
+// The per-CTA table of slot roles at step t (ages, weights, merge partners).
+__device__ inline void tan_table(int B, int C, long long t, float* s_age, float* s_w, int* s_part, BlockStep* s_bs) {
     const int L = B * C;
-    extern __shared__ __align__(16) unsigned char smem_raw[];
-    float* s_age = reinterpret_cast<float*>(smem_raw);
-    float* s_w = s_age + L;
-    int* s_part = reinterpret_cast<int*>(s_w + L);
-    BlockStep* s_bs = reinterpret_cast<BlockStep*>(s_part + L);
-    const long long t = *t_dev;
     if (threadIdx.x == 0) sched_step(B, C, t, s_bs);
     __syncthreads();
     for (int l = threadIdx.x; l < L; l += blockDim.x) {
@@ -127,8 +114,26 @@ __global__ void __launch_bounds__(128) k_history_t(Dual* __restrict__ X, Dual* _
         s_part[l] = part;
     }
     __syncthreads();
-    const int n = blockIdx.x * blockDim.x + threadIdx.x;
-    if (n >= g.N) return;
+}
+
+// History sweep in duals, one thread per (node, slot chunk): advance E - 1 in place over the chunk's slots
+// and write the chunk's partial trapezoidal sum (added in chunk order by k_history_t).
+template <int D>
+__global__ void __launch_bounds__(128) k_sweep_t(Dual* __restrict__ X, const Dual* __restrict__ K,
+                                                 Dual* __restrict__ part_t, Geom g, TanPar p,
+                                                 const long long* t_dev, int B, int C, int S) {
+    constexpr int DD = D * D;
+    constexpr int NS = D == 2 ? 3 : 6;
+    const int L = B * C;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    float* s_age = reinterpret_cast<float*>(smem_raw);
+    float* s_w = s_age + L;
+    int* s_part = reinterpret_cast<int*>(s_w + L);
+    BlockStep* s_bs = reinterpret_cast<BlockStep*>(s_part + L);
+    tan_table(B, C, *t_dev, s_age, s_w, s_part, s_bs);
+    const long long idx = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    const int n = (int)(idx % g.Npad), chunk = (int)(idx / g.Npad);
+    if (chunk >= S || n >= g.N) return;
     const long long Np = g.Npad;
     Dual A[DD];
     {
@@ -139,7 +144,9 @@ __global__ void __launch_bounds__(128) k_history_t(Dual* __restrict__ X, Dual* _
     }
     Dual acc[NS];
     for (int i = 0; i < NS; ++i) acc[i] = Dual(0.0);
-    for (int l = 0; l < L; ++l) {
+    const int len = (L + S - 1) / S;
+    const int l0 = min(L, chunk * len), l1 = min(L, l0 + len);
+    for (int l = l0; l < l1; ++l) {
         const float w = s_w[l];
         if (w == 0.0f) continue;
         Dual Xl[DD], kap[DD];
@@ -153,6 +160,31 @@ __global__ void __launch_bounds__(128) k_history_t(Dual* __restrict__ X, Dual* _
         point_update<D>(Xl, A, kap, Dual((double)s_age[l]), Dual((double)w), p.inv_tau, p.inv_gc, acc);
         for (int c = 0; c < DD; ++c) X[((long long)l * DD + c) * Np + n] = Xl[c];
     }
+    for (int i = 0; i < NS; ++i) part_t[((long long)chunk * NS + i) * Np + n] = acc[i];
+}
+
+// The node's history commit in duals after k_sweep_t: the chunk sums plus the point created now give
+// sigma_struc(t); then the merges and the new point (form "P": E - 1 advanced in place).
+template <int D>
+__global__ void __launch_bounds__(128) k_history_t(Dual* __restrict__ X, Dual* __restrict__ K,
+                                                   const Dual* __restrict__ u_raw, Dual* __restrict__ kappa_f,
+                                                   Dual* __restrict__ sigma_f, const Dual* __restrict__ part_t,
+                                                   Geom g, TanPar p, const long long* t_dev, int B, int C, int S) {
+    constexpr int DD = D * D;
+    constexpr int NS = D == 2 ? 3 : 6;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    float* s_age = reinterpret_cast<float*>(smem_raw);
+    float* s_w = s_age + B * C;
+    int* s_part = reinterpret_cast<int*>(s_w + B * C);
+    BlockStep* s_bs = reinterpret_cast<BlockStep*>(s_part + B * C);
+    tan_table(B, C, *t_dev, s_age, s_w, s_part, s_bs);
+    const int n = blockIdx.x * blockDim.x + threadIdx.x;
+    if (n >= g.N) return;
+    const long long Np = g.Npad;
+    Dual acc[NS];
+    for (int i = 0; i < NS; ++i) acc[i] = Dual(0.0);
+    for (int c = 0; c < S; ++c)
+        for (int i = 0; i < NS; ++i) acc[i] += part_t[((long long)c * NS + i) * Np + n];
     Dual kt[DD];
     kappa_fd<D>(u_raw, Np, g.ch[0], n, kt);
     if (D == 2) {

@@ -48,10 +48,12 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-chosen", action="store_true", help="skip the reduced-precision comparison run")
-    ap.add_argument("--workload", choices=["channel", "batched", "duct", "regime"], default="channel",
+    ap.add_argument("--workload", choices=["channel", "batched", "duct", "regime", "gradient"], default="channel",
                     help="channel: the 1024 x 512 D2Q9 channel (the benchmark line); batched: 64 channels of "
                          "uneven width; duct: the D3Q19 128^3 square duct; regime: the paper's transient sweep "
-                         "(ten channels of Figs. Qall and figtau in one batch, probes recorded every step)")
+                         "(ten channels of Figs. Qall and figtau in one batch, probes recorded every step); "
+                         "gradient: dL/d(G_inf, tau, gamma_c, g) of the 4 x 128 channel, L = 512, 4000 steps by "
+                         "the adjoint with checkpoints every 64 steps (a step of this line = one gradient)")
     ap.add_argument("--history", choices=["f32", "s16", "f64"], default="f32",
                     help="history storage: f32 (plain FP32 form), s16 (16-bit block-scaled precision variant), f64")
     ap.add_argument("--model", choices=["nlm", "wm", "inlm"], default="nlm",
@@ -249,6 +251,33 @@ def run_reference(args, rank, world):
     if rank != 0:
         return
     metric = METRIC_NODES if args.model == "inlm" else METRIC
+    if args.workload == "gradient":
+        # the oracle's gradient is central finite differences: 8 forward runs of 4000 steps; timed on a
+        # bounded sample (the first steps of one run) and scaled to the 32000 steps
+        import oracle
+        from paper_1504_06123_gb300 import configs
+        w = configs.gradient_channel()
+        ch = oracle.Channel(oracle.D2Q9, w.nx, w.ny, tau_lb=w.tau_lb, G_inf=w.G_inf, tau=w.tau, gamma_c=w.gamma_c,
+                            g=(w.g, 0, 0), C=w.C, B=w.B)
+        ch.step(max(1, args.warmup))
+        n = max(2, args.steps if args.steps != 300 else 20)
+        t0 = time.perf_counter()
+        ch.step(n)
+        dt = time.perf_counter() - t0
+        ch.close()
+        per_grad = dt / n * 8 * w.steps
+        sample = f"oracle steps {args.warmup}..{args.warmup + n - 1} of one run ({dt:.1f} s), x 8 runs x {w.steps} steps"
+        line = {"metric": "gradient evaluations/s", "value": 1.0 / per_grad, "unit": "gradient evaluations/s",
+                "n_gpus": args.gpus, "steps": n, "warmup": args.warmup, "ms_per_step": 1e3 * per_grad,
+                "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+                "impl": "reference", "config": {"workload": "gradient_channel_4x128_L512_4000steps", "sample": sample},
+                "cpu_baseline": {"value": 1.0 / per_grad, "unit": "gradient evaluations/s", "cores": 1,
+                                 "kind": "oracle", "sample": sample},
+                "e2e": {"value": 1.0 / per_grad, "unit": "gradient evaluations/s", "h2d_bytes_per_step": 0,
+                        "d2h_bytes_per_step": 0},
+                "gpu_launches": 0}
+        print(json.dumps(line), flush=True)
+        return
     if args.workload != "channel":
         from paper_1504_06123_gb300 import configs
         from paper_1504_06123_gb300 import lbve as L
@@ -318,6 +347,81 @@ def workload_descs(args, L, configs):
     return f"batch64_channels_L{ws[0].L}" + ("_wm" if args.model == "wm" else ""), [w.desc() for w in ws], None, {
         "lattice": "D2Q9", "channels": len(ws), "widths": [w.ny for w in ws], "blocks_B": ws[0].B,
         "block_C": ws[0].C}
+
+
+def run_gradient(args, rank, world, local_rank):
+    """The differentiation workload: one gradient = the recording forward run (a state image every 64 steps)
+    plus lbve_backward, timed end to end with CUDA events on the stream; the tangent-linear model on the
+    same workload beside it.  Metric: gradient evaluations per second (and node-history updates/s of the
+    forward steps they contain)."""
+    import torch
+    import numpy as np
+    from paper_1504_06123_gb300 import configs, inputs
+    from paper_1504_06123_gb300 import lbve as L
+    from paper_1504_06123_gb300.autograd import run_profiles
+    torch.cuda.set_device(local_rank)
+    w = configs.gradient_channel()
+    desc = w.desc(precision=L.LBVE_F64, hist_storage=L.LBVE_F64)
+    theta = np.array([w.G_inf, w.tau, w.gamma_c, w.g])
+    ut, st = run_profiles(desc, inputs.perturbed(theta, seed=w.seed), w.steps)
+    N = w.nx * w.ny
+    K = args.steps if args.steps != 300 else 3
+    W = args.warmup if args.warmup != 5 else 1
+    stream = torch.cuda.current_stream()
+    su, ss = float(np.max(np.abs(ut))) ** 2, float(np.max(np.abs(st))) ** 2
+
+    def gradient():
+        h = L.lbve_create_adjoint(desc, None, 64)
+        try:
+            L.lbve_step(h, w.steps, stream)
+            f = L.lbve_fields(h, L.LBVE_FIELD_U | L.LBVE_FIELD_SIGMA, None, stream)
+            u, sxy = f[:N], f[2 * N + 2 * N: 2 * N + 3 * N]
+            du = np.zeros((2, N))
+            ds = np.zeros((3, N))
+            du[0] = 2.0 * (u - ut) / (N * su)          # d/du of mean((u - u*)^2) / max|u*|^2
+            ds[2] = 2.0 * (sxy - st) / (N * ss)
+            return L.lbve_backward(h, du, ds, stream)
+        finally:
+            L.lbve_destroy(h)
+
+    for _ in range(W):
+        gradient()
+    torch.cuda.synchronize()
+    with ClockSampler(local_rank) as clk:
+        t0 = time.perf_counter()
+        for _ in range(K):
+            g = gradient()
+        torch.cuda.synchronize()
+        dt = time.perf_counter() - t0
+    # the tangent-linear model on the same workload (forward mode: all four derivatives in one run)
+    torch.cuda.synchronize()
+    t1 = time.perf_counter()
+    run_profiles(desc, theta, w.steps, with_tangents=True)
+    torch.cuda.synchronize()
+    dt_tan = time.perf_counter() - t1
+    t2 = time.perf_counter()
+    run_profiles(desc, theta, w.steps)
+    torch.cuda.synchronize()
+    dt_fwd = time.perf_counter() - t2
+    pts = points_per_step(desc.hist_C, desc.hist_B, 0, w.steps, L)
+    upd = N * sum(pts)
+    value = K / dt
+    if rank == 0:
+        line = {
+            "metric": "gradient evaluations/s", "value": value, "unit": "gradient evaluations/s", "n_gpus": world,
+            "steps": K, "warmup": W, "ms_per_step": 1e3 * dt / K, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": "gradient_channel_4x128_L512_4000steps", "nodes": N,
+                       "history_points": desc.hist_B * desc.hist_C, "lb_steps": w.steps, "checkpoint_every": 64,
+                       "loss": "mean((u_x - u*)^2)/max|u*|^2 + mean((sigma_xy - s*)^2)/max|s*|^2, final step",
+                       "parallelism": f"replicas{world}", "l2": "state fits in L2 (latency-bound size)"},
+            "gradient": [float(x) for x in g],
+            "forward_updates_per_s": upd * K / dt,
+            "plain_forward_s": dt_fwd, "gradient_s": dt / K, "gradient_over_forward": (dt / K) / dt_fwd,
+            "tangent_s": dt_tan,
+            "clocks": clk.summary(), "roofline": None, "cpu_baseline": None, "e2e": None,
+        }
+        print(json.dumps(line), flush=True)
 
 
 def run_ours(args, rank, world, local_rank):
@@ -612,6 +716,8 @@ def main():
     rank, world, local_rank = dist_env()
     if args.impl == "reference":
         run_reference(args, rank, world)
+    elif args.workload == "gradient":
+        run_gradient(args, rank, world, local_rank)
     else:
         run_ours(args, rank, world, local_rank)
 

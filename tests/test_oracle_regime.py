@@ -10,7 +10,9 @@ pressure drop over one width equal to G_inf), probed at y/H = 0.51 by linear int
   - sigma_xx - sigma_yy > 0 at all times; after cessation it decays monotonically; after startup it
     overshoots in wide channels, much less in narrow ones;
   - Newtonian and linear viscoelastic (UCM) fluids: startup u(t) and cessation u_ss - u(t) coincide; the
-    nonlinear model breaks that symmetry.
+    nonlinear model breaks that symmetry;
+  - the UCM overshoots and oscillates after startup, shear thinning removes the oscillations (Fig.
+    compModels); a larger theta lowers the steady velocity (Fig. figtau).
 The lattice parameters are computed here from the paper's definitions, independently of the CUDA
 package: eta_inf = G_inf tau_0 = rho0 nu_N (BGK viscosity), t_wall = 4 H^2 rho / (pi^2 G_inf tau_0).
 """
@@ -130,3 +132,33 @@ def test_startup_cessation_symmetry(kind):
         assert err < 1e-3           # linear in (u, sigma_xy); only O(u) nonlinearities of the scheme
     else:
         assert err > 0.05           # shear thinning breaks it
+
+
+@pytest.mark.parametrize("ratio,ny", [(0.1, 8), (1.0, 12)])
+def test_ucm_oscillates_and_shear_thinning_damps_it(ratio, ny):
+    # Sec. IV (Fig. compModels): the linear-viscoelastic UCM (gamma_c -> infinity) overshoots and
+    # oscillates after startup in narrow and intermediate channels; with shear thinning the oscillations
+    # disappear (the nlM velocity, once past its maximum, does not dip below its steady value)
+    p = _params(ratio, 10.0, ny)
+    T = int(3 * p["tau"])
+    every = max(1, T // 600)
+    _, ucm, _ = _run(ratio, 10.0, ny, T, 8, every, gamma_c=math.inf)
+    _, nlm, _ = _run(ratio, 10.0, ny, T, 8, every)
+    u, v = ucm[:, 1] / ucm[-1, 1], nlm[:, 1] / nlm[-1, 1]
+    assert u.max() > 2.0                                   # strong elastic overshoot
+    assert u[np.argmax(u):].min() < 0.9                    # then swings well below the steady value
+    assert v.max() < 1.2                                   # the nlM: at most the Newtonian-like overshoot
+    assert v[np.argmax(v):].min() > 0.99                   # and no swing below the steady value
+
+
+def test_slower_structural_relaxation_lowers_the_steady_velocity():
+    # Sec. IV (Fig. figtau): at the same width, theta = 100 reaches a lower steady velocity than theta = 10
+    # (the slowly relaxing plug is more viscous); velocities on the scale g H^2 / (2 nu)
+    vals = {}
+    for theta in (10.0, 100.0):
+        p = _params(4.0, theta, 8)
+        T = int(4 * p["tau"])
+        _, st, _ = _run(4.0, theta, 8, T, 8, max(1, T // 400))
+        assert abs(st[-1, 1] - st[int(0.9 * len(st)), 1]) < 1e-3 * st[-1, 1]      # steady
+        vals[theta] = st[-1, 1] / (p["g"] * p["H"] ** 2 / (2 * NU))
+    assert vals[100.0] < vals[10.0]

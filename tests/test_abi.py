@@ -1,7 +1,6 @@
 """The C-ABI library on the CPU: it builds, loads, exports every entry point of include/lbve.h, validates
 arguments before touching a GPU, and its history grid (the kernel's per-slot roles, run on the host) is
 bit-identical to the oracle's merge simulation (Sec. III quasi-logarithmic layout)."""
-import math
 import os
 import re
 

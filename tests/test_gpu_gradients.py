@@ -6,7 +6,6 @@ Loss: mean((u_x - u*)^2)/max|u*|^2 + mean((sigma_xy - sigma*)^2)/max|sigma*|^2 a
 target from the same model with the parameters perturbed by +-10 % (seeded signs).
 Tolerance: 1e-4 relative per gradient component (the stated bar).
 """
-import math
 
 import numpy as np
 import pytest

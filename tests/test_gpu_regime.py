@@ -8,8 +8,6 @@
 - the full sweep of Fig. Qall (seven widths, theta = 10) and Fig. figtau (theta = 100) shows the
   transient features the paper describes (the oracle pins the same features on small channels).
 """
-import math
-
 import numpy as np
 import pytest
 
@@ -20,7 +18,6 @@ from paper_1504_06123_gb300 import regime
 torch = pytest.importorskip("torch")
 pytestmark = pytest.mark.gpu
 
-ALL = L.LBVE_FIELD_RHO | L.LBVE_FIELD_U | L.LBVE_FIELD_SIGMA
 
 
 def _batch_descs():

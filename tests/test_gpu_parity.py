@@ -298,6 +298,30 @@ def test_batched_channels_vs_oracle(prec):
     ch.close()
 
 
+@pytest.mark.parametrize("prec", [PLAIN, RED])
+def test_full_batch_workload_sampled_vs_oracle(prec):
+    """The 64-channel batch exactly as the benchmark builds it (widths 10-480, L = 1024, the autotuner's launch
+    shape), 48 steps (three 16-step graphs); the narrowest, a middle and the widest channel compared node by
+    node with one-column oracle channels (no density noise: the flow is x-invariant)."""
+    ws = configs.batched_channels()
+    descs = [w.desc(precision=prec[0], hist_storage=prec[1]) for w in ws]
+    ch = L.Channel(descs)
+    ch.step(48)
+    f = ch.fields()
+    order = sorted(range(len(ws)), key=lambda i: ws[i].ny)
+    for i in (order[0], order[len(order) // 2], order[-1]):
+        w = ws[i]
+        o = oracle.Channel(oracle.D2Q9, 1, w.ny, tau_lb=w.tau_lb, G_inf=w.G_inf, tau=w.tau, gamma_c=w.gamma_c,
+                           g=(w.g, 0, 0), C=w.C, B=w.B)
+        o.step(48)
+        ref = o.fields()
+        o.close()
+        got = ch.channel_fields(i, f)
+        col = {k: v.reshape(w.ny, w.nx, *v.shape[1:])[:, 0] for k, v in got.items()}
+        compare(col, ref, TOL[prec], f"batch channel {i} (ny {w.ny})")
+    ch.close()
+
+
 def test_batched_ducts_vs_oracle():
     descs = [L.make_desc(L.LBVE_D3Q19, 3, 6, 6, tau_lb=0.9, G_inf=0.01, tau=40.0, gamma_c=0.1, g=(2e-5, 0, 0),
                          C=8, B=2, precision=F64, hist_storage=F32),

@@ -4,7 +4,7 @@ Shapes follow the paper's setup: pressure-driven planar channel (D2Q9, periodic 
 half-way bounce-back walls) started from rest, and the D3Q19 square duct.  History lengths count
 points L = B*C with the paper's block size C = 128 where the workload gives "entries".
 
-Driving force (input recipe, stated in the design doc): a requested wall Peclet number Pe = gammadot_w tau
+Driving force (input recipe): a requested wall Peclet number Pe = gammadot_w tau
 gives the wall shear rate; the steady shear stress of the model at that rate,
 eta_N gammadot_w + G_inf tau_e gammadot_w with 1/tau_e = 1/tau + gammadot_w/gamma_c, balanced by the
 force on half the channel, gives g_Pe = sigma_w / (rho0 H).  Velocities must stay small against the

@@ -33,7 +33,7 @@ extern "C" {
 #define LBVE_ECUDA       -3  /* a CUDA call or kernel launch failed (see lbve_last_cuda_error) */
 #define LBVE_ENONFINITE  -4  /* a NaN or Inf appeared in the state */
 #define LBVE_ESTATE      -6  /* the call does not fit the handle's state */
-#define LBVE_ENOSUPPORT  -7  /* a valid combination this build does not implement */
+#define LBVE_ENOSUPPORT  -7  /* a valid combination this library does not implement */
 #define LBVE_ETOOBIG     -8  /* request larger than the fixed device buffer of lbve_fields_host_fixed */
 
 /* ---- enumerations ---------------------------------------------------------------------------- */

@@ -1636,7 +1636,7 @@ const char* lbve_strerror(int status) {
         case LBVE_ECUDA: return "CUDA error";
         case LBVE_ENONFINITE: return "non-finite value in the state";
         case LBVE_ESTATE: return "call does not fit the handle's state";
-        case LBVE_ENOSUPPORT: return "combination not supported by this build";
+        case LBVE_ENOSUPPORT: return "combination not supported by this library";
         case LBVE_ETOOBIG: return "request exceeds the fixed staging buffer of lbve_fields_host_fixed";
         default: return "unknown status";
     }

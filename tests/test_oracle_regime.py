@@ -162,3 +162,23 @@ def test_slower_structural_relaxation_lowers_the_steady_velocity():
         assert abs(st[-1, 1] - st[int(0.9 * len(st)), 1]) < 1e-3 * st[-1, 1]      # steady
         vals[theta] = st[-1, 1] / (p["g"] * p["H"] ** 2 / (2 * NU))
     assert vals[100.0] < vals[10.0]
+
+
+@pytest.mark.parametrize("trace_full", [True, False])
+def test_steady_density_balances_the_normal_stress_difference(trace_full):
+    # Sec. IV (steady state): sigma_xx - sigma_yy > 0 in the flowing region pushes the fluid towards the
+    # centre, which the density (pressure) increase there balances.  With the trace split of the coupling
+    # the lattice momentum flux carries sigma_yy - tr(sigma)/2 = -N1/2, so the steady y-balance is
+    # c_s^2 rho(y) + N1(y)/2 = const across the channel.
+    p = _params(1.0, 10.0, 16)
+    ch = oracle.Channel(oracle.D2Q9, 1, 16, tau_lb=TAU_LB, G_inf=p["G"], tau=p["tau"], gamma_c=0.1,
+                        g=(p["g"], 0, 0), C=32, B=8, trace_full=trace_full)
+    ch.step(int(6 * p["tau"]))
+    f = ch.fields()
+    ch.close()
+    rho, n1 = f["rho"], f["n1"]
+    assert np.all(n1 > 0)
+    assert rho[7] > rho[0]                                  # denser in the centre than at the wall
+    lhs = (rho - rho[0]) / 3.0                              # c_s^2 (rho(y) - rho(wall node))
+    rhs = -(n1 - n1[0]) / 2.0
+    assert np.max(np.abs(lhs - rhs)) <= 1e-4 * np.max(np.abs(rhs))     # 1e-6 seen

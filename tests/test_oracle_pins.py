@@ -427,3 +427,21 @@ def test_collision_moments(lattice, trace_full):
                + (1 - 0.5 / tau_lb) * (ddr * cs2 * np.eye(d) - ddr * np.outer(u, u)
                                        + np.outer(u, f) + np.outer(f, u)))
         np.testing.assert_allclose(Pi_post, ref, rtol=1e-13, atol=1e-15)
+
+
+@pytest.mark.parametrize("gd", [1e-3, 1e-2])
+def test_dynamic_yield_stress(gd):
+    """Sec. IV: at tau -> infinity the model's shear stress under steady shear tends to G_inf gamma_c at any
+    rate (the yield stress of the glass).  On a uniform history grid the trapezoidal sum is a geometric
+    series: sigma_xy = G_inf gd sum_k w_k exp(-a k) = G_inf gamma_c (a/2) coth(a/2), a = gd/gamma_c, up to
+    the truncation exp(-a T) of the retained span."""
+    G, gc = 0.01, 0.1
+    a = gd / gc
+    T = int(60 / a)
+    K = np.zeros((T, 1, 2, 2))
+    K[:, 0, 0, 1] = gd
+    sig = oracle.history_run(K, T + 8, 1, G, 1e15, gc, last_only=True)[0]
+    exact = G * gc * (a / 2) / np.tanh(a / 2)
+    assert sig[2] == pytest.approx(exact, rel=1e-10)
+    assert abs(sig[2] / (G * gc) - 1.0) < a * a / 12 * 1.01 + 1e-12      # -> the yield stress G_inf gamma_c
+    assert sig[1] == 0.0

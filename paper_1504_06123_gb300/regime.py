@@ -197,5 +197,25 @@ class RegimeSweep:
             out.append({"t": t, "rho": p[:, 0], "u": p[:, 1], "sxy": p[:, 5], "n1": p[:, 3] - p[:, 4]})
         return out
 
+    def curves(self, n_startup: int) -> list:
+        """The normalised transients of Figs. Qall / QT per channel: time on the scales of tau_0 and t_wall
+        (t counted from the start of the phase) and u, sigma_xy, N1 at d divided by their values at the end
+        of the startup phase (the steady state when that phase was long enough), split at step n_startup
+        into {"startup": {...}, "cessation": {...}}."""
+        out = []
+        for c, ser in zip(self.channels, self.series()):
+            t = ser["t"]
+            k = int(np.searchsorted(t, n_startup, side="right"))
+            if k == 0:
+                raise ValueError("no record inside the startup phase")
+            ss = {key: ser[key][k - 1] for key in ("u", "sxy", "n1")}
+            phases = {}
+            for name, sl, t0 in (("startup", slice(0, k), 0), ("cessation", slice(k, None), n_startup)):
+                tt = (t[sl] - t0).astype(np.float64)
+                phases[name] = {"t_over_tau0": tt / c.tau0, "t_over_twall": tt / c.t_wall,
+                                **{key: ser[key][sl] / ss[key] for key in ("u", "sxy", "n1")}}
+            out.append(phases)
+        return out
+
     def close(self):
         self.batch.close()

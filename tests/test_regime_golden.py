@@ -71,3 +71,27 @@ def test_width_and_history_span():
     assert regime.width_for(1.0, 7600.0) == 100         # the paper's 100-node channel at t_wall = tau_0
     B = regime.history_blocks(5 * 40000.0, 128)
     assert 128 * (2 ** B - 1) >= 2e5 > 128 * (2 ** (B - 1) - 1)
+
+
+def test_curves_normalise_by_the_end_of_startup():
+    # host-side post-processing only: a sweep object with synthetic records (no device)
+    sw = regime.RegimeSweep.__new__(regime.RegimeSweep)
+    sw.channels = [regime.regime_channel(1.0, 10.0, 20)]
+    sw.weights = [0.25]
+    t = np.arange(1, 11) * 10
+    vals = np.zeros((10, 2, 6))
+    vals[:, 0, 1] = np.linspace(1, 10, 10)          # u at the first node
+    vals[:, 1, 1] = np.linspace(1, 10, 10) * 3      # u at the second node
+    vals[:, :, 5] = 2.0                             # sigma_xy
+    vals[:, :, 3] = 5.0                             # sigma_xx
+    vals[:, :, 4] = 1.0                             # sigma_yy
+    sw._records = [(t, vals)]
+    cur = sw.curves(60)[0]
+    st, sp = cur["startup"], cur["cessation"]
+    assert len(st["u"]) == 6 and len(sp["u"]) == 4
+    u6 = 0.75 * 6 + 0.25 * 18                       # interpolated u at t = 60
+    assert st["u"][-1] == pytest.approx(1.0) and sp["u"][0] == pytest.approx((0.75 * 7 + 0.25 * 21) / u6)
+    assert np.allclose(st["sxy"], 1.0) and np.allclose(sp["n1"], 1.0)
+    c = sw.channels[0]
+    assert st["t_over_tau0"][0] == pytest.approx(10 / c.tau0)
+    assert sp["t_over_twall"][0] == pytest.approx(10 / c.t_wall)

@@ -445,3 +445,39 @@ def test_dynamic_yield_stress(gd):
     assert sig[2] == pytest.approx(exact, rel=1e-10)
     assert abs(sig[2] / (G * gc) - 1.0) < a * a / 12 * 1.01 + 1e-12      # -> the yield stress G_inf gamma_c
     assert sig[1] == 0.0
+
+
+def _duct_series(ny, nz, g, nu, terms=400):
+    """Steady Newtonian flow in a rectangular duct of width 2a (y) and 2b (z) under a body force g: the
+    textbook Fourier series u = 16 g a^2 / (nu pi^3) sum_{n odd} (-1)^((n-1)/2) n^-3
+    [1 - cosh(n pi z / 2a) / cosh(n pi b / 2a)] cos(n pi y / 2a); nodes at j - (n-1)/2, walls half a node
+    outside.  Returns u[z][y]."""
+    a, b = ny / 2, nz / 2
+    y = np.arange(ny) - (ny - 1) / 2
+    z = np.arange(nz) - (nz - 1) / 2
+    Y, Z = np.meshgrid(y, z, indexing="ij")
+    u = np.zeros_like(Y)
+    for n in range(1, 2 * terms, 2):
+        x, X = n * np.pi * np.abs(Z) / (2 * a), n * np.pi * b / (2 * a)
+        ratio = np.exp(x - X) * (1 + np.exp(-2 * x)) / (1 + np.exp(-2 * X))     # cosh(x) / cosh(X), |x| <= X
+        u += (-1) ** ((n - 1) // 2) / n ** 3 * (1 - ratio) * np.cos(n * np.pi * Y / (2 * a))
+    return (16 * g * a * a / (nu * np.pi ** 3) * u).T
+
+
+def test_newtonian_duct_series_second_order():
+    """D3Q19 square duct (walls in y and z), G_inf = 0: the steady velocity converges to the duct series at
+    second order in the lattice spacing (half-way bounce-back at Lambda = 3/16)."""
+    tau_lb = 0.5 + np.sqrt(3.0 / 16.0)
+    nu = (tau_lb - 0.5) / 3.0
+    g = 1e-6
+    err = {}
+    for n in (12, 24):
+        ch = oracle.Channel(oracle.D3Q19, 1, n, n, tau_lb=tau_lb, G_inf=0.0, tau=10.0, gamma_c=0.1, g=(g, 0, 0),
+                            C=4, B=1)
+        ch.step(int(16 * n * n / (np.pi ** 2 * nu)))
+        u = ch.fields()["u"][:, 0].reshape(n, n)      # node x + nx (y + ny z): [z][y]
+        ch.close()
+        ex = _duct_series(n, n, g, nu)
+        err[n] = np.max(np.abs(u - ex)) / np.max(np.abs(ex))
+    assert err[24] < 5e-4
+    assert 3.5 < err[12] / err[24] < 4.5                 # second order: (24/12)^2

@@ -481,3 +481,24 @@ def test_newtonian_duct_series_second_order():
         err[n] = np.max(np.abs(u - ex)) / np.max(np.abs(ex))
     assert err[24] < 5e-4
     assert 3.5 < err[12] / err[24] < 4.5                 # second order: (24/12)^2
+
+
+@pytest.mark.parametrize("a,b", [(0, 1), (0, 2), (1, 2), (2, 0), (1, 0)])
+def test_constant_shear_3d_planes(a, b):
+    """P2 in 3D: kappa = gd e_ab (velocity component a varying along b) is nilpotent, so E = 1 + strain e_ab
+    exactly and the 2D closed form holds in that plane: sigma_ab = the shear value, sigma_aa = the normal
+    value, every other packed component (xx, yy, zz, xy, xz, yz) exactly 0."""
+    gd, G, tau, gc, T, C, B = 2e-3, 0.01, 40.0, 0.1, 200, 16, 3
+    K = np.zeros((T, 1, 3, 3))
+    K[:, :, a, b] = gd
+    sig = oracle.history_run(K, C, B, G, tau, gc)
+    pack = {(0, 0): 0, (1, 1): 1, (2, 2): 2, (0, 1): 3, (1, 0): 3, (0, 2): 4, (2, 0): 4, (1, 2): 5, (2, 1): 5}
+    for t in (0, 5, 77, T - 1):
+        sxy, sxx, _ = shear_closed_form(gd, t, C, B, G, tau, gc)
+        for i in range(6):
+            if i == pack[(a, b)]:
+                np.testing.assert_allclose(sig[t, 0, i], sxy, rtol=1e-13)
+            elif i == pack[(a, a)]:
+                np.testing.assert_allclose(sig[t, 0, i], sxx, rtol=1e-12, atol=1e-30)
+            else:
+                assert sig[t, 0, i] == 0.0, (t, i)

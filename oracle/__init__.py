@@ -31,7 +31,13 @@ NLM, INLM, WM = 0, 1, 2
 
 
 def build(force: bool = False) -> str:
-    """Compile the oracle with gcc (portable flags only: it must build the same on x86 and Arm)."""
+    """Compile the oracle with gcc (portable flags only: it must build the same on x86 and Arm).
+
+    LBVE_ORACLE_LIB names a prebuilt oracle library to load instead (the planted-mistake tests compile a
+    copy of the source with one deliberate error and check that the pins reject it)."""
+    alt = os.environ.get("LBVE_ORACLE_LIB")
+    if alt:
+        return alt
     os.makedirs(_BUILD, exist_ok=True)
     if force or not os.path.exists(_LIB_PATH) or os.path.getmtime(_LIB_PATH) < os.path.getmtime(_SRC):
         tmp = _LIB_PATH + f".{os.getpid()}.tmp"

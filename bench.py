@@ -187,12 +187,15 @@ def channel_workload(model: str):
             "inlm": configs.inlm_channel_large}[model]()
 
 
-def oracle_sample(steps: int | None = None, budget_s: float = 12.0, warmup: int = 1, model: str = "nlm"):
+def oracle_sample(steps: int | None = None, budget_s: float = 12.0, warmup: int = 1, model: str = "nlm",
+                  threads: int = 0):
     """The FP64 oracle on 2 columns x 512 rows of the benchmark channel with its full history: `warmup`
-    untimed steps, then `steps` timed ones (or as many as fit in budget_s).  Returns the rate in the
-    workload's unit: node-history updates/s, or node updates/s for the instantaneous model."""
+    untimed steps, then `steps` timed ones (or as many as fit in budget_s), its node loops on `threads` host
+    threads (0: all cores).  Returns the rate in the workload's unit: node-history updates/s, or node
+    updates/s for the instantaneous model, and the thread count used."""
     import oracle
     from paper_1504_06123_gb300 import inputs
+    cores = oracle.set_threads(threads)
     w = channel_workload(model)
     nx = 2
     rho = inputs.initial_density(w.N, w.noise, w.seed).reshape(w.ny, w.nx)[:, :nx].ravel()
@@ -214,15 +217,18 @@ def oracle_sample(steps: int | None = None, budget_s: float = 12.0, warmup: int 
         upd = nx * w.ny * sum(pts)
     ch.close()
     hist = "no history" if model == "inlm" else f"L = {w.L}"
-    sample = f"{nx} of {w.nx} columns x {w.ny} rows, {hist}, steps {t_start}..{t_start + n - 1} ({dt:.1f} s)"
-    return upd / dt, sample, n, dt, upd
+    sample = (f"{nx} of {w.nx} columns x {w.ny} rows, {hist}, steps {t_start}..{t_start + n - 1} ({dt:.1f} s, "
+              f"{cores} thread{'s' if cores > 1 else ''})")
+    return upd / dt, sample, n, dt, upd, cores
 
 
-def oracle_sample_batch(descs, steps: int, warmup: int = 1):
+def oracle_sample_batch(descs, steps: int, warmup: int = 1, threads: int = 0):
     """The FP64 oracle on one column (x-invariant flow) of each of the first two channels of a batch or
-    duct workload, full width and history: `warmup` untimed steps, then `steps` timed ones.  Returns the
-    rate in node-history updates/s and a description of the sample."""
+    duct workload, full width and history: `warmup` untimed steps, then `steps` timed ones, on `threads`
+    host threads (0: all cores).  Returns the rate in node-history updates/s, a description of the sample
+    and the thread count."""
     import oracle
+    cores = oracle.set_threads(threads)
     chans = []
     for d in descs[:2]:
         lat = oracle.D2Q9 if d.lattice == 9 else oracle.D3Q19
@@ -243,8 +249,8 @@ def oracle_sample_batch(descs, steps: int, warmup: int = 1):
     for ch in chans:
         ch.close()
     sample = (f"one column of channels 0-{len(chans) - 1} ({nodes} nodes), L = {d0.hist_B * d0.hist_C}, "
-              f"steps {t_start}..{t_start + steps - 1} ({dt:.1f} s)")
-    return upd / dt, sample, steps, dt, upd
+              f"steps {t_start}..{t_start + steps - 1} ({dt:.1f} s, {cores} thread{'s' if cores > 1 else ''})")
+    return upd / dt, sample, steps, dt, upd, cores
 
 
 def run_reference(args, rank, world):
@@ -256,6 +262,7 @@ def run_reference(args, rank, world):
         # bounded sample (the first steps of one run) and scaled to the 32000 steps
         import oracle
         from paper_1504_06123_gb300 import configs
+        cores = oracle.set_threads(0)
         w = configs.gradient_channel()
         ch = oracle.Channel(oracle.D2Q9, w.nx, w.ny, tau_lb=w.tau_lb, G_inf=w.G_inf, tau=w.tau, gamma_c=w.gamma_c,
                             g=(w.g, 0, 0), C=w.C, B=w.B)
@@ -266,12 +273,13 @@ def run_reference(args, rank, world):
         dt = time.perf_counter() - t0
         ch.close()
         per_grad = dt / n * 8 * w.steps
-        sample = f"oracle steps {args.warmup}..{args.warmup + n - 1} of one run ({dt:.1f} s), x 8 runs x {w.steps} steps"
+        sample = (f"oracle steps {args.warmup}..{args.warmup + n - 1} of one run ({dt:.1f} s, {cores} threads), "
+                  f"x 8 runs x {w.steps} steps")
         line = {"metric": "gradient evaluations/s", "value": 1.0 / per_grad, "unit": "gradient evaluations/s",
                 "n_gpus": args.gpus, "steps": n, "warmup": args.warmup, "ms_per_step": 1e3 * per_grad,
                 "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
                 "impl": "reference", "config": {"workload": "gradient_channel_4x128_L512_4000steps", "sample": sample},
-                "cpu_baseline": {"value": 1.0 / per_grad, "unit": "gradient evaluations/s", "cores": 1,
+                "cpu_baseline": {"value": 1.0 / per_grad, "unit": "gradient evaluations/s", "cores": cores,
                                  "kind": "oracle", "sample": sample},
                 "e2e": {"value": 1.0 / per_grad, "unit": "gradient evaluations/s", "h2d_bytes_per_step": 0,
                         "d2h_bytes_per_step": 0},
@@ -282,26 +290,26 @@ def run_reference(args, rank, world):
         from paper_1504_06123_gb300 import configs
         from paper_1504_06123_gb300 import lbve as L
         name, descs, _, _ = workload_descs(args, L, configs)
-        val, sample, n, dt, upd = oracle_sample_batch(descs, steps=args.steps, warmup=args.warmup)
+        val, sample, n, dt, upd, cores = oracle_sample_batch(descs, steps=args.steps, warmup=args.warmup)
         line = {
             "metric": metric, "value": val, "unit": metric, "n_gpus": args.gpus, "steps": n,
             "warmup": args.warmup, "ms_per_step": 1e3 * dt / n, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f64", "data": "synthetic", "impl": "reference",
             "config": {"workload": name, "sample": sample},
-            "cpu_baseline": {"value": val, "unit": metric, "cores": 1, "kind": "oracle", "sample": sample},
+            "cpu_baseline": {"value": val, "unit": metric, "cores": cores, "kind": "oracle", "sample": sample},
             "e2e": {"value": val, "unit": metric, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
             "gpu_launches": 0,
         }
         print(json.dumps(line), flush=True)
         return
-    # each step: one oracle step of the sample (about 0.1 s on one core)
-    val, sample, n, dt, upd = oracle_sample(steps=args.steps, warmup=args.warmup, model=args.model)
+    # each step: one oracle step of the sample (about 0.1 s on one core), on all host cores
+    val, sample, n, dt, upd, cores = oracle_sample(steps=args.steps, warmup=args.warmup, model=args.model)
     line = {
         "metric": metric, "value": val, "unit": metric, "n_gpus": args.gpus, "steps": n, "warmup": args.warmup,
         "ms_per_step": 1e3 * dt / n, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
         "dtype": "f64", "data": "synthetic", "impl": "reference",
         "config": {"workload": channel_workload(args.model).name, "sample": sample},
-        "cpu_baseline": {"value": val, "unit": metric, "cores": 1, "kind": "oracle", "sample": sample},
+        "cpu_baseline": {"value": val, "unit": metric, "cores": cores, "kind": "oracle", "sample": sample},
         "e2e": {"value": val, "unit": metric, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
         "gpu_launches": 0,
     }
@@ -669,8 +677,11 @@ def run_ours(args, rank, world, local_rank):
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline and args.workload == "channel":
-        val, sample, *_ = oracle_sample(model=args.model)
-        cpu = {"value": val, "unit": metric, "cores": 1, "kind": "oracle", "sample": sample}
+        # the oracle on all host cores (its node loops split over OpenMP threads), and on one core
+        val, sample, _, _, _, cores = oracle_sample(model=args.model, budget_s=8.0, threads=0)
+        val1, sample1, _, _, _, _ = oracle_sample(model=args.model, budget_s=8.0, threads=1)
+        cpu = {"value": val, "unit": metric, "cores": cores, "kind": "oracle", "sample": sample,
+               "single_core": {"value": val1, "unit": metric, "cores": 1, "sample": sample1}}
 
     clocks = clk.summary()
     if roofline["bound"] == "alu":

@@ -38,7 +38,7 @@ extern "C" {
 
 /* ---- enumerations ---------------------------------------------------------------------------- */
 #define LBVE_D2Q9   9    /* planar channel, Sec. III velocity set */
-#define LBVE_D3Q19 19    /* square duct ("the extension to 3D is straightforward", Sec. III) */
+#define LBVE_D3Q19 19    /* square duct: the three-dimensional form of the Sec. III scheme */
 
 #define LBVE_F32 0       /* populations / history stored in float */
 #define LBVE_F64 1       /* populations / history stored in double */
@@ -293,6 +293,8 @@ int lbve_memory_bytes(const lbve_t* h, size_t* bytes);
  * Launch shape of the history sweep chosen at create by the autotuner: the number of slot chunks each
  * node's points are split into (tasks = node tiles x chunks), the number of persistent CTAs, and the task
  * mode (*cta_tasks = 0: a task is one warp's; 1: a task is one CTA's, its warps splitting the chunk).
+ * The tuner times candidate shapes once per process for each (device, lattice, history storage and model,
+ * history grid, padded node count); later handles of the same kind take the shape found then.
  * The shape fixes the order in which the trapezoidal sum of Eq. (gitt) is added up: results are bitwise
  * reproducible for a given shape, and differ in the last bits between shapes.
  */
@@ -330,7 +332,8 @@ int lbve_profile_read(lbve_t* h, double ms_out[3], int64_t launches_out[3]);
  * Returns LBVE_ETOOBIG (nothing copied) when that count exceeds LBVE_FIXED_STAGING_DOUBLES, ENONFINITE
  * (after copying) when a copied value is NaN or Inf, EINVAL for bad arguments.
  * The first call on a device looks up the array's device address (once per device, on the current
- * device); make that first call before any stream capture.  All calls on a device share the one array,
+ * device; again only if the device's CUDA context has been destroyed and re-made since, e.g. by
+ * cudaDeviceReset); make that first call before any stream capture.  All calls on a device share the one array,
  * so calls that overlap on the GPU (other streams, other host threads) race with each other: serialise
  * them.  The non-finite flag kept in the array is cleared at the start of every call.
  */

@@ -41,7 +41,12 @@ def build(force: bool = False) -> str:
     os.makedirs(_BUILD, exist_ok=True)
     if force or not os.path.exists(_LIB_PATH) or os.path.getmtime(_LIB_PATH) < os.path.getmtime(_SRC):
         tmp = _LIB_PATH + f".{os.getpid()}.tmp"
-        subprocess.run(["gcc", "-O2", "-std=c99", "-fPIC", "-shared", "-o", tmp, _SRC, "-lm"], check=True)
+        base = ["gcc", "-O2", "-std=c99", "-fPIC", "-shared", "-o", tmp, _SRC, "-lm"]
+        # OpenMP splits the node loops over host threads (bitwise the same results); without it the
+        # oracle builds serial
+        r = subprocess.run(base[:1] + ["-fopenmp"] + base[1:], capture_output=True, text=True)
+        if r.returncode != 0:
+            subprocess.run(base, check=True)
         os.replace(tmp, _LIB_PATH)
     return _LIB_PATH
 
@@ -78,8 +83,25 @@ def _load():
         lib.orc_mass.argtypes = [C.c_void_p, dp, dp]
         lib.orc_kappa_of.argtypes = [C.c_void_p, dp, dp]
         lib.orc_expm.argtypes = [C.c_int, dp, dp]
+        lib.orc_set_threads.argtypes = [C.c_int]
+        lib.orc_set_threads.restype = C.c_int
+        lib.orc_get_threads.restype = C.c_int
+        # all host cores unless LBVE_ORACLE_THREADS says otherwise (results do not depend on the count)
+        lib.orc_set_threads(int(os.environ.get("LBVE_ORACLE_THREADS", "0")))
         _lib = lib
         return lib
+
+
+def set_threads(n: int) -> int:
+    """Host threads of the oracle's node loops (n < 1: all cores); returns the count in use (1 when the
+    oracle was built without OpenMP).  Every node's arithmetic is the same whatever the count, so results
+    are bitwise independent of it."""
+    return int(_load().orc_set_threads(int(n)))
+
+
+def threads() -> int:
+    """Host threads the oracle's node loops use now."""
+    return int(_load().orc_get_threads())
 
 
 def _dp(a: np.ndarray):

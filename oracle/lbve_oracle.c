@@ -70,6 +70,11 @@
  *     the factors of Eq. (eeval)), instead of (t - t') gammadot(t').  Every point stores the strain of
  *     its span next to its factor; a merge adds the two spans' strains, as it multiplies their factors.
  *
+ * Threads: the node loops (moments, gradient, history, collision and streaming, the history-only driver)
+ * may run on several host threads (OpenMP, orc_set_threads).  Each node's arithmetic is the same
+ * sequence of operations whatever the thread count -- threads only split the nodes, and every node's
+ * result is written by exactly one thread -- so results are bitwise independent of the thread count.
+ *
  * Pressure-step boundary along x (Sec. III, the generalised periodic boundary of Kim & Pitsch that fixes a
  * constant pressure step between the inlet and the outlet of the periodic lattice), optional: the
  * periodic images just outside the lattice are ghost nodes.  The ghost upstream of the inlet (x = -1)
@@ -85,6 +90,26 @@
 #include <stdint.h>
 #include <stdlib.h>
 #include <string.h>
+#ifdef _OPENMP
+#include <omp.h>
+#endif
+
+/* Host threads of the node loops (1 = serial). */
+static int orc_nthreads = 1;
+
+/* Set the number of host threads of the node loops (n < 1: all available); returns the number in use
+ * (1 when the library was built without OpenMP). */
+int orc_set_threads(int n) {
+#ifdef _OPENMP
+    orc_nthreads = (n < 1) ? omp_get_num_procs() : n;
+#else
+    (void)n;
+    orc_nthreads = 1;
+#endif
+    return orc_nthreads;
+}
+
+int orc_get_threads(void) { return orc_nthreads; }
 
 #define ORC_MAXQ 19
 
@@ -413,25 +438,30 @@ int orc_history_run(int d, int nnodes, int C, int B, double G_inf, double tau, d
     const int nsig = (d == 2) ? 3 : 6;
     const int dd = d * d;
     orc_model m = {G_inf, tau, gamma_c, model};
-    orc_pt* list = (orc_pt*)malloc(sizeof(orc_pt) * (size_t)B * C);
-    double* ages = (double*)malloc(sizeof(double) * (size_t)B * C);
-    double* wts = (double*)malloc(sizeof(double) * (size_t)B * C);
-    for (int node = 0; node < nnodes; ++node) {
-        orc_hist h;
-        hist_init(&h, d, C, B);
-        for (int t = 0; t < T; ++t) {
-            double sig[6];
-            const double* kt = kappa_seq + ((size_t)t * nnodes + node) * dd;
-            if (model == ORC_INLM) inlm_stress(d, kt, &m, sig);
-            else hist_step(&h, t, kt, &m, list, ages, wts, sig);
-            double* dst = NULL;
-            if (!last_only) dst = sigma_out + ((size_t)t * nnodes + node) * nsig;
-            else if (t == T - 1) dst = sigma_out + (size_t)node * nsig;
-            if (dst) memcpy(dst, sig, sizeof(double) * nsig);
+#pragma omp parallel num_threads(orc_nthreads)
+    {
+        /* scratch of the node being stepped, one set per thread */
+        orc_pt* list = (orc_pt*)malloc(sizeof(orc_pt) * (size_t)B * C);
+        double* ages = (double*)malloc(sizeof(double) * (size_t)B * C);
+        double* wts = (double*)malloc(sizeof(double) * (size_t)B * C);
+#pragma omp for schedule(dynamic, 1)
+        for (int node = 0; node < nnodes; ++node) {
+            orc_hist h;
+            hist_init(&h, d, C, B);
+            for (int t = 0; t < T; ++t) {
+                double sig[6];
+                const double* kt = kappa_seq + ((size_t)t * nnodes + node) * dd;
+                if (model == ORC_INLM) inlm_stress(d, kt, &m, sig);
+                else hist_step(&h, t, kt, &m, list, ages, wts, sig);
+                double* dst = NULL;
+                if (!last_only) dst = sigma_out + ((size_t)t * nnodes + node) * nsig;
+                else if (t == T - 1) dst = sigma_out + (size_t)node * nsig;
+                if (dst) memcpy(dst, sig, sizeof(double) * nsig);
+            }
+            hist_free(&h);
         }
-        hist_free(&h);
+        free(list); free(ages); free(wts);
     }
-    free(list); free(ages); free(wts);
     return 0;
 }
 
@@ -498,7 +528,6 @@ typedef struct {
     double* kappa;           /* [N][9] */
     double* tr_prev;         /* [N] tr sigma of the previous step */
     orc_hist* hist;          /* [N] */
-    orc_pt* list; double* ages; double* wts;
 } orc_channel;
 
 static void set_lattice(orc_channel* ch) {
@@ -572,9 +601,6 @@ orc_channel* orc_create(int lattice, int nx, int ny, int nz, int wall_z, double 
     ch->tr_prev = (double*)calloc((size_t)N, sizeof(double));
     ch->hist = (orc_hist*)calloc((size_t)N, sizeof(orc_hist));
     for (int64_t k = 0; k < N; ++k) hist_init(&ch->hist[k], ch->d, C, B);
-    ch->list = (orc_pt*)malloc(sizeof(orc_pt) * (size_t)B * C);
-    ch->ages = (double*)malloc(sizeof(double) * (size_t)B * C);
-    ch->wts = (double*)malloc(sizeof(double) * (size_t)B * C);
     for (int64_t k = 0; k < N; ++k) {
         const double r = rho_init ? rho_init[k] : rho0;
         for (int i = 0; i < Q; ++i) ch->n[k * Q + i] = ch->w[i] * (r - rho0);
@@ -589,7 +615,6 @@ void orc_destroy(orc_channel* ch) {
     for (int64_t k = 0; k < N; ++k) hist_free(&ch->hist[k]);
     free(ch->hist); free(ch->n); free(ch->n_next); free(ch->rho_raw); free(ch->j); free(ch->u_raw);
     free(ch->rho); free(ch->u); free(ch->sigma); free(ch->kappa); free(ch->tr_prev);
-    free(ch->list); free(ch->ages); free(ch->wts);
     free(ch);
 }
 
@@ -639,6 +664,7 @@ static double axis_derivative(const double* f_m1, const double* f_0, const doubl
  * difference scheme") with the wall stencil above. */
 static void compute_kappa(const orc_channel* ch, const double* u, double* kappa) {
     const int d = ch->d;
+#pragma omp parallel for collapse(2) num_threads(orc_nthreads) schedule(static)
     for (int z = 0; z < ch->nz; ++z)
         for (int y = 0; y < ch->ny; ++y)
             for (int x = 0; x < ch->nx; ++x) {
@@ -743,6 +769,7 @@ static void channel_step(orc_channel* ch) {
 
     /* 1. raw moments: rho_raw = sum n, j = sum c n + f/2, u_raw = j / rho_raw
      *    (sum w rho0 = rho0 and sum c w rho0 = 0 for the stored deviations) */
+#pragma omp parallel for num_threads(orc_nthreads) schedule(static)
     for (int64_t k = 0; k < N; ++k) {
         double dr = 0.0, jj[3] = {0, 0, 0};
         for (int i = 0; i < Q; ++i) {
@@ -760,14 +787,26 @@ static void channel_step(orc_channel* ch) {
     /* 2. kappa(t) by finite differences of u_raw */
     compute_kappa(ch, ch->u_raw, ch->kappa);
     /* 3-4. history: sigma_struc(t) */
-    for (int64_t k = 0; k < N; ++k) {
-        double kap[9];
-        for (int i = 0; i < d * d; ++i) kap[i] = ch->kappa[k * 9 + i];
-        if (ch->m.kind == ORC_INLM) inlm_stress(d, kap, &ch->m, &ch->sigma[k * 6]);
-        else hist_step(&ch->hist[k], ch->t, kap, &ch->m, ch->list, ch->ages, ch->wts, &ch->sigma[k * 6]);
+#pragma omp parallel num_threads(orc_nthreads)
+    {
+        /* scratch of the node being stepped, one set per thread */
+        const size_t L = (size_t)ch->B * ch->C;
+        orc_pt* list = (orc_pt*)malloc(sizeof(orc_pt) * L);
+        double* ages = (double*)malloc(sizeof(double) * L);
+        double* wts = (double*)malloc(sizeof(double) * L);
+#pragma omp for schedule(dynamic, 16)
+        for (int64_t k = 0; k < N; ++k) {
+            double kap[9];
+            for (int i = 0; i < d * d; ++i) kap[i] = ch->kappa[k * 9 + i];
+            if (ch->m.kind == ORC_INLM) inlm_stress(d, kap, &ch->m, &ch->sigma[k * 6]);
+            else hist_step(&ch->hist[k], ch->t, kap, &ch->m, list, ages, wts, &ch->sigma[k * 6]);
+        }
+        free(list); free(ages); free(wts);
     }
-    /* 5-7. trace split, density source, collision with forcing, streaming */
+    /* 5-7. trace split, density source, collision with forcing, streaming (every destination population
+     * is written by exactly one source node, so rows may run on different threads) */
     memset(ch->n_next, 0, sizeof(double) * (size_t)N * Q);
+#pragma omp parallel for collapse(2) num_threads(orc_nthreads) schedule(static)
     for (int z = 0; z < ch->nz; ++z)
         for (int y = 0; y < ch->ny; ++y)
             for (int x = 0; x < ch->nx; ++x) {

@@ -12,6 +12,7 @@ Argument marshalling only: every step and its derivative run in the CUDA library
 from __future__ import annotations
 
 import copy
+import weakref
 
 import numpy as np
 import torch
@@ -76,31 +77,68 @@ class LBVEChannel(torch.autograd.Function):
         return g, None, None, None
 
 
+class AdjointRun:
+    """Owner of one adjoint handle (its state images and history) between forward and backward.
+
+    The handle is destroyed by release() -- after the backward pass -- or, when no backward ever runs
+    (forward under torch.no_grad, outputs unused by any loss, an exception in between), as soon as the
+    autograd graph that holds this owner is freed.  `live` counts the handles not yet destroyed."""
+    live = 0
+
+    def __init__(self, h):
+        self.h = h
+        AdjointRun.live += 1
+        self._fin = weakref.finalize(self, AdjointRun._destroy, h)
+
+    @staticmethod
+    def _destroy(h):
+        L.lbve_destroy(h)
+        AdjointRun.live -= 1
+
+    @property
+    def alive(self) -> bool:
+        return self._fin.alive
+
+    def release(self):
+        self._fin()          # runs _destroy once; later calls do nothing
+
+
 class LBVEChannelAdjoint(torch.autograd.Function):
-    """theta (float64 tensor [4]) -> (u_x [N], sigma_xy [N]); gradients by the adjoint with checkpoints."""
+    """theta (float64 tensor [4]) -> (u_x [N], sigma_xy [N]); gradients by the adjoint with checkpoints.
+
+    The adjoint runs the FP64 hybrid step (lbve_create_adjoint accepts FP64 populations and history only),
+    so `desc` must ask for LBVE_F64 populations and history: the gradient is that of the FP64 model, and a
+    description of another precision is refused rather than silently changed.  One backward pass per
+    forward: the recorded states are freed by the first."""
 
     @staticmethod
     def forward(ctx, theta: torch.Tensor, desc: L.lbve_channel_desc, steps: int, checkpoint_every: int = 64,
                 rho_init=None):
+        if desc.pop_precision != L.LBVE_F64 or desc.hist_storage != L.LBVE_F64:
+            raise ValueError("LBVEChannelAdjoint differentiates the FP64 model: desc.pop_precision and "
+                             "desc.hist_storage must be LBVE_F64")
         d = _with_params(desc, theta.detach().cpu().numpy())
-        d.pop_precision = L.LBVE_F64
-        d.hist_storage = L.LBVE_F64
         dim = 2 if d.lattice == L.LBVE_D2Q9 else 3
         N = d.nx * d.ny * d.nz
-        h = L.lbve_create_adjoint(d, rho_init, checkpoint_every)
+        run = AdjointRun(L.lbve_create_adjoint(d, rho_init, checkpoint_every))
         try:
-            L.lbve_step(h, steps)
-            f = L.lbve_fields(h, L.LBVE_FIELD_U | L.LBVE_FIELD_SIGMA)
+            L.lbve_step(run.h, steps)
+            f = L.lbve_fields(run.h, L.LBVE_FIELD_U | L.LBVE_FIELD_SIGMA)
         except Exception:
-            L.lbve_destroy(h)
+            run.release()
             raise
+        if not ctx.needs_input_grad[0]:
+            run.release()    # theta does not require a gradient: nothing will call backward
         ixy = 2 if dim == 2 else 3
-        ctx.h, ctx.dim, ctx.N, ctx.ixy = h, dim, N, ixy
+        ctx.run, ctx.dim, ctx.N, ctx.ixy = run, dim, N, ixy
         return (torch.from_numpy(f[:N].copy()),
                 torch.from_numpy(f[dim * N + ixy * N: dim * N + (ixy + 1) * N].copy()))
 
     @staticmethod
     def backward(ctx, grad_u, grad_s):
+        if not ctx.run.alive:
+            raise RuntimeError("LBVEChannelAdjoint: backward ran a second time; the recorded states are freed "
+                               "by the first backward pass (run the forward again)")
         dim, N, ixy = ctx.dim, ctx.N, ctx.ixy
         nsig = 3 if dim == 2 else 6
         du = np.zeros((dim, N))
@@ -110,10 +148,9 @@ class LBVEChannelAdjoint(torch.autograd.Function):
         if grad_s is not None:
             ds[ixy] = grad_s.detach().cpu().numpy()
         try:
-            g = L.lbve_backward(ctx.h, du, ds)
+            g = L.lbve_backward(ctx.run.h, du, ds)
         finally:
-            L.lbve_destroy(ctx.h)
-            ctx.h = None
+            ctx.run.release()
         return torch.from_numpy(g), None, None, None, None
 
 

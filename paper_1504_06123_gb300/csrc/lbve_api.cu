@@ -5,6 +5,7 @@
 // lbve_step only enqueues kernels on the caller's stream.  The step counter and the per-channel
 // parameters live in device memory, so a step is a fixed sequence of launches that needs no host
 // state: lbve_step captures 16 steps into a CUDA graph once and replays it.
+#include <cuda.h>   // driver API types (the context id check of lbve_fields_host_fixed)
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -79,6 +80,7 @@ struct lbve {
     int sweep_grid = 0;        // persistent CTAs of the sweep
     int sweep_cta = 0;         // k_sweep task mode: 0 warp tasks, 1 CTA tasks (autotuned at create)
     int sweep_grid_full = 0;   // resident CTAs of the sweep on this device (SMs x CTAs per SM)
+    int tuned_from_cache = 0;  // 1: the launch shape came from an earlier handle of the same shape
     int part_S = 0;            // slot chunks the partial-sum buffer holds
     long long* t_dev = nullptr;
     double* red = nullptr;     // reduction scratch (2 doubles)
@@ -325,6 +327,22 @@ template <int D> struct SweepKernel<D, 2> {
 // over a few launches on the freshly created, all-rest history (which the sweep leaves unchanged:
 // exp(0) - 1 = 0), together with the commit's reduction of the S partial sums (k_part_read); the fastest
 // is kept.  The partial-sum buffer is sized for the largest candidate and then trimmed by reallocation.
+// Launch shapes the autotuner has chosen in this process, keyed by everything the sweep's speed depends on
+// (device and its SM count, lattice, history storage and model, history grid, padded node count), so that
+// a second handle of the same shape -- a user re-creating a channel, a batch of equal size -- is not timed
+// again.
+struct TuneKey {
+    int dev, sms, D, HK, wm, B, C;
+    long long Npad;
+    bool operator==(const TuneKey& o) const {
+        return dev == o.dev && sms == o.sms && D == o.D && HK == o.HK && wm == o.wm && B == o.B && C == o.C &&
+               Npad == o.Npad;
+    }
+};
+struct TuneVal { int S, cta, grid, grid_full; };
+std::mutex g_tune_mu;
+std::vector<std::pair<TuneKey, TuneVal>> g_tune_cache;
+
 template <int D, int HK>
 int sweep_autotune(lbve* h) {
     constexpr int VN = SweepKernel<D, HK>::VN;
@@ -336,6 +354,26 @@ int sweep_autotune(lbve* h) {
     int dev = 0, sms = 0, per_sm = 0;
     LBVE_CUDA(cudaGetDevice(&dev));
     LBVE_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+    const TuneKey key{dev, sms, D, HK, h->model == LBVE_MODEL_WM ? 1 : 0, h->d.hist_B, h->d.hist_C, h->Npad};
+    {
+        std::lock_guard<std::mutex> lock(g_tune_mu);
+        for (const auto& kv : g_tune_cache)
+            if (kv.first == key) {
+                h->S = kv.second.S;
+                h->sweep_cta = kv.second.cta;
+                h->sweep_grid = kv.second.grid;
+                h->sweep_grid_full = kv.second.grid_full;
+                h->tuned_from_cache = 1;
+                break;
+            }
+    }
+    if (h->tuned_from_cache) {
+        int rc = alloc(h, &h->part, h->hesz * (size_t)h->S * h->NS * h->Npad);
+        if (rc) return rc;
+        LBVE_CUDA(cudaMemset(h->part, 0, h->hesz * (size_t)h->S * h->NS * h->Npad));
+        h->part_S = h->S;
+        return LBVE_OK;
+    }
     LBVE_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, 256, smem));
     if (per_sm < 1) per_sm = 1;
     const long long grid_full = (long long)sms * per_sm;
@@ -411,6 +449,10 @@ int sweep_autotune(lbve* h) {
     h->sweep_grid = grid_of(best_c);
     h->sweep_grid_full = (int)grid_full;
     h->part_S = (int)Sbig;
+    {
+        std::lock_guard<std::mutex> lock(g_tune_mu);
+        g_tune_cache.push_back({key, TuneVal{h->S, h->sweep_cta, h->sweep_grid, h->sweep_grid_full}});
+    }
     if (best_c.S < Sbig) {   // keep only what the chosen S needs
         dev_free(h, h->part);
         h->bytes -= h->hesz * (size_t)Sbig * h->NS * h->Npad;
@@ -580,7 +622,9 @@ int init_state(lbve* h, const double* rho_init_host) {
     return LBVE_OK;
 }
 
-int fields_impl(lbve* h, uint32_t mask, double* dst, cudaStream_t s) {
+// The field gathers of lbve_fields into device memory `dst`, raising the device flag `flag` on a non-finite
+// value (the handle's own flag, or the one kept in the fixed staging array of lbve_fields_host_fixed).
+int fields_impl(lbve* h, uint32_t mask, double* dst, int* flag, cudaStream_t s) {
     using real = double;   // node fields are kept in double
     const long long Np = h->Npad;
     const int N = h->N;
@@ -589,7 +633,7 @@ int fields_impl(lbve* h, uint32_t mask, double* dst, cudaStream_t s) {
         const long long tot = (long long)ncomp * N;
         if (tot > 0) {
             k_gather<real><<<(int)((tot + 255) / 256), 256, 0, s>>>((const real*)src, Np, ncomp, N, offset,
-                                                                      dst + off, h->flag);
+                                                                      dst + off, flag);
             LBVE_CUDA(cudaGetLastError());
         }
         off += (size_t)tot;
@@ -602,7 +646,7 @@ int fields_impl(lbve* h, uint32_t mask, double* dst, cudaStream_t s) {
     if (mask & LBVE_FIELD_KAPPA) if ((rc = gather(h->kappa, h->D * h->D, 0.0))) return rc;
     if (mask & LBVE_FIELD_N1) {
         if (N > 0) {
-            k_n1<real><<<(N + 255) / 256, 256, 0, s>>>((const real*)h->sigma, Np, N, dst + off, h->flag);
+            k_n1<real><<<(N + 255) / 256, 256, 0, s>>>((const real*)h->sigma, Np, N, dst + off, flag);
             LBVE_CUDA(cudaGetLastError());
         }
         off += N;
@@ -1156,7 +1200,7 @@ int lbve_fields(lbve_t* h, uint32_t mask, double* dst, int32_t dst_is_device, vo
         cudaFreeAsync(tmp, s);
         return rc;
     }
-    if (dst_is_device) return fields_impl(h, mask, dst, s);
+    if (dst_is_device) return fields_impl(h, mask, dst, h->flag, s);
     if (h->stage_n < cnt) {
         dev_free(h, h->stage);
         h->stage = nullptr;
@@ -1166,7 +1210,7 @@ int lbve_fields(lbve_t* h, uint32_t mask, double* dst, int32_t dst_is_device, vo
         h->stage_n = cnt;
     }
     LBVE_CUDA(cudaMemsetAsync(h->flag, 0, sizeof(int), s));
-    int rc = fields_impl(h, mask, h->stage, s);
+    int rc = fields_impl(h, mask, h->stage, h->flag, s);
     if (rc) return rc;
     int flag = 0;
     LBVE_CUDA(cudaMemcpyAsync(dst, h->stage, sizeof(double) * cnt, cudaMemcpyDeviceToHost, s));
@@ -1681,47 +1725,57 @@ namespace {
 
 constexpr int kMaxDevices = 64;
 std::mutex g_fixed_mu;
-double* g_fixed_ptr[kMaxDevices] = {nullptr};
+// Per device: the array's device address and the id of the CUDA context it was looked up in.  A context
+// that has been torn down (cudaDeviceReset) and made again gets a new id, and the address is looked up
+// again in the new context.
+struct FixedSlot { unsigned long long ctx_id; double* ptr; };
+FixedSlot g_fixed[kMaxDevices] = {};
 
-// Device address of the fixed staging array on the current device (looked up on first use).
+// Id of the calling thread's current CUDA context (0 if there is none or the driver cannot say).  The two
+// driver queries are resolved once through the runtime's entry-point lookup.
+typedef CUresult (*CtxGetCurrentFn)(CUcontext*);
+typedef CUresult (*CtxGetIdFn)(CUcontext, unsigned long long*);
+unsigned long long current_context_id() {
+    static CtxGetCurrentFn get_current = nullptr;
+    static CtxGetIdFn get_id = nullptr;
+    static bool resolved = false;
+    if (!resolved) {
+        resolved = true;
+        cudaDriverEntryPointQueryResult q1, q2;
+        void* f1 = nullptr;
+        void* f2 = nullptr;
+        if (cudaGetDriverEntryPointByVersion("cuCtxGetCurrent", &f1, 12000, cudaEnableDefault, &q1) == cudaSuccess &&
+            cudaGetDriverEntryPointByVersion("cuCtxGetId", &f2, 12000, cudaEnableDefault, &q2) == cudaSuccess &&
+            q1 == cudaDriverEntryPointSuccess && q2 == cudaDriverEntryPointSuccess) {
+            get_current = (CtxGetCurrentFn)f1;
+            get_id = (CtxGetIdFn)f2;
+        }
+        cudaGetLastError();   // a failed lookup leaves no sticky error behind
+    }
+    if (!get_current || !get_id) return 0;
+    CUcontext c = nullptr;
+    unsigned long long id = 0;
+    if (get_current(&c) != CUDA_SUCCESS || !c || get_id(c, &id) != CUDA_SUCCESS) return 0;
+    return id;
+}
+
+// Device address of the fixed staging array on the current device: looked up on the first call on a
+// device, and again when the device's context has changed since (or its id cannot be read).
 int fixed_staging_ptr(double** out) {
     int dev = -1;
     LBVE_CUDA(cudaGetDevice(&dev));
     if (dev < 0 || dev >= kMaxDevices) return LBVE_ENOSUPPORT;
     std::lock_guard<std::mutex> lock(g_fixed_mu);
-    if (!g_fixed_ptr[dev]) {
+    FixedSlot& slot = g_fixed[dev];
+    unsigned long long id = current_context_id();
+    if (!slot.ptr || id == 0 || slot.ctx_id != id) {
         double* p = nullptr;
         LBVE_CUDA(cudaGetSymbolAddress((void**)&p, g_fixed_staging));
-        g_fixed_ptr[dev] = p;
+        if (id == 0) id = current_context_id();   // the lookup makes the device's context current
+        slot.ptr = p;
+        slot.ctx_id = id;
     }
-    *out = g_fixed_ptr[dev];
-    return LBVE_OK;
-}
-
-// The gathers of lbve_fields, writing into `dst` (device) and raising `flag` on a non-finite value.
-int gather_fields_into(lbve* h, uint32_t mask, double* dst, int* flag, cudaStream_t s) {
-    const long long Np = h->Npad;
-    const int N = h->N;
-    size_t off = 0;
-    struct Part { uint32_t bit; const void* src; int ncomp; double offset; };
-    const Part parts[] = {{LBVE_FIELD_RHO, h->rho, 1, h->d.rho0},
-                          {LBVE_FIELD_U, h->u, h->D, 0.0},
-                          {LBVE_FIELD_SIGMA, h->sigma, h->NS, 0.0},
-                          {LBVE_FIELD_KAPPA, h->kappa, h->D * h->D, 0.0}};
-    for (const Part& pt : parts) {
-        if (!(mask & pt.bit)) continue;
-        const long long tot = (long long)pt.ncomp * N;
-        if (tot > 0) {
-            k_gather<double><<<(int)((tot + 255) / 256), 256, 0, s>>>((const double*)pt.src, Np, pt.ncomp, N,
-                                                                        pt.offset, dst + off, flag);
-            LBVE_CUDA(cudaGetLastError());
-        }
-        off += (size_t)tot;
-    }
-    if ((mask & LBVE_FIELD_N1) && N > 0) {
-        k_n1<double><<<(N + 255) / 256, 256, 0, s>>>((const double*)h->sigma, Np, N, dst + off, flag);
-        LBVE_CUDA(cudaGetLastError());
-    }
+    *out = slot.ptr;
     return LBVE_OK;
 }
 
@@ -1738,7 +1792,7 @@ extern "C" int lbve_fields_host_fixed(lbve_t* h, uint32_t mask, double* dst_host
     if (rc) return rc;
     int* flag = reinterpret_cast<int*>(stage + LBVE_FIXED_STAGING_DOUBLES);
     LBVE_CUDA(cudaMemsetAsync(flag, 0, sizeof(int), s));
-    if ((rc = gather_fields_into(h, mask, stage, flag, s))) return rc;
+    if ((rc = fields_impl(h, mask, stage, flag, s))) return rc;
     int flag_host = 0;
     LBVE_CUDA(cudaMemcpyAsync(dst_host, stage, sizeof(double) * cnt, cudaMemcpyDeviceToHost, s));
     LBVE_CUDA(cudaMemcpyAsync(&flag_host, flag, sizeof(int), cudaMemcpyDeviceToHost, s));

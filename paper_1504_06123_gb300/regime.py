@@ -21,6 +21,7 @@ BGK viscosity rho0 nu_N, nu_N = (tau_LB - 1/2)/3:
 from __future__ import annotations
 
 import math
+import warnings
 from dataclasses import dataclass
 
 import numpy as np
@@ -209,6 +210,14 @@ class RegimeSweep:
             if k == 0:
                 raise ValueError("no record inside the startup phase")
             ss = {key: ser[key][k - 1] for key in ("u", "sxy", "n1")}
+            # a normalising value that vanishes against its own series (a probe on the centreline, a
+            # startup too short to build stress) cannot normalise it: that curve is NaN, with a warning
+            for key in ("u", "sxy", "n1"):
+                scale = float(np.max(np.abs(ser[key]))) if len(ser[key]) else 0.0
+                if not (abs(ss[key]) > 1e-9 * scale) or scale == 0.0:
+                    warnings.warn(f"channel {c.ny} nodes wide: {key} at the end of startup is {ss[key]!r}, too "
+                                  "small to normalise its curve; returning NaN", RuntimeWarning, stacklevel=2)
+                    ss[key] = np.nan
             phases = {}
             for name, sl, t0 in (("startup", slice(0, k), 0), ("cessation", slice(k, None), n_startup)):
                 tt = (t[sl] - t0).astype(np.float64)

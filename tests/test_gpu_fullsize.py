@@ -1,0 +1,192 @@
+"""GPU parity at the workloads' stated sizes and lengths, against the FP64 oracle.
+
+The flows start from rest without density noise, so they stay invariant along the periodic flow axis x:
+every column of the GPU channel (every x-slice of the duct) must equal the oracle's one-column channel
+(one-slice duct) of the same width, history grid and parameters.  That keeps the oracle affordable at full
+history length and full run length (its node loops run on all host cores).
+
+  channel 1024 x 512, L = 1024 (B 8 x C 128): 5000 startup steps and 1000 cessation steps (force off),
+      plain FP32 form (<= 1e-5) and the 16-bit history (<= 1e-3)
+  duct 32^3 sub-run of the 128^3 duct, L = 512 (B 4 x C 128): 3000 steps, both forms, errors per field
+  64-channel batch, L = 1024: 4000 startup + 2000 cessation steps, narrowest, median and widest channel
+
+Per-field errors are normwise max-relative (max|x - x_ref| / max|x_ref|) and are printed for the record.
+"""
+import math
+
+import numpy as np
+import pytest
+
+import oracle
+from paper_1504_06123_gb300 import configs
+from paper_1504_06123_gb300 import lbve as L
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+F32, F64, S16 = L.LBVE_F32, L.LBVE_F64, L.LBVE_S16
+PLAIN, RED = (F64, F32), (F32, S16)
+TOL = {PLAIN: 1e-5, RED: 1e-3}
+NAME = {PLAIN: "plain FP32 history", RED: "16-bit history"}
+
+
+def rel(x, ref):
+    x = np.asarray(x, dtype=np.float64)
+    ref = np.asarray(ref, dtype=np.float64)
+    den = np.max(np.abs(ref))
+    num = np.max(np.abs(x - ref))
+    return (0.0 if num == 0 else math.inf) if den == 0 else float(num / den)
+
+
+def field_errors(got: dict, ref: dict, ixy: int) -> dict:
+    """u, sigma, sigma_xy, N1 (on the sigma scale), kappa and rho of one column / slice against the oracle."""
+    e = {k: rel(got[k].reshape(ref[k].shape), ref[k]) for k in ("u", "sigma", "kappa", "rho")}
+    e["sigma_xy"] = rel(got["sigma"].reshape(ref["sigma"].shape)[:, ixy], ref["sigma"][:, ixy])
+    e["n1_on_sigma_scale"] = float(np.max(np.abs(got["n1"].reshape(ref["n1"].shape) - ref["n1"])) /
+                                   max(np.max(np.abs(ref["sigma"])), 1e-300))
+    return e
+
+
+def check(errs: dict, tol: float, what: str):
+    print(what, {k: f"{v:.2e}" for k, v in errs.items()})
+    for k, v in errs.items():
+        assert v <= tol, f"{what}: {k} error {v:.3e} > {tol:.0e}"
+
+
+def columns(f: dict, nx: int, ny: int, nz: int = 1) -> dict:
+    """The fields as [slice][x][...]; all x must be bitwise equal (x-invariant flow)."""
+    out = {}
+    for k, v in f.items():
+        a = np.asarray(v).reshape(nz * ny, nx, -1)
+        assert np.array_equal(a, np.broadcast_to(a[:, :1], a.shape)), f"{k} differs along x"
+        out[k] = a[:, 0]
+    return out
+
+
+# ---------------------------------------------------------------------------------------------
+# The 1024 x 512 channel at L = 1024 through startup and cessation
+# ---------------------------------------------------------------------------------------------
+CHANNEL_CP = (40, 1000, 5000, 5400, 6000)
+
+
+@pytest.fixture(scope="module")
+def channel_oracle():
+    w = configs.plain_channel_large()
+    orc = oracle.Channel(oracle.D2Q9, 1, w.ny, tau_lb=w.tau_lb, G_inf=w.G_inf, tau=w.tau, gamma_c=w.gamma_c,
+                         g=(w.g, 0, 0), C=w.C, B=w.B)
+    out, t = {}, 0
+    for cp in CHANNEL_CP:
+        orc.step(cp - t)
+        t = cp
+        out[cp] = orc.fields()
+        if t == w.steps:
+            orc.set_force((0, 0, 0))
+    orc.close()
+    return w, out
+
+
+@pytest.mark.parametrize("prec", [PLAIN, RED])
+def test_channel_1024x512_L1024_startup_cessation_vs_oracle(channel_oracle, prec):
+    w, ref = channel_oracle
+    ch = L.Channel(w.desc(precision=prec[0], hist_storage=prec[1]))
+    t = 0
+    for cp in CHANNEL_CP:
+        ch.step(cp - t)
+        t = cp
+        got = columns(ch.fields(), w.nx, w.ny)
+        check(field_errors(got, ref[cp], 2), TOL[prec], f"channel 1024x512 L1024 {NAME[prec]} step {cp}:")
+        if t == w.steps:
+            ch.set_force((0, 0, 0))
+    ch.close()
+
+
+# ---------------------------------------------------------------------------------------------
+# The duct's 32^3 sub-run at the duct's history (L = 512) for its 3000 steps
+# ---------------------------------------------------------------------------------------------
+DUCT_CP = (40, 500, 1500, 3000)
+
+
+def duct_subrun():
+    w = configs.duct_3d()
+    n = 32
+    g = configs.force_for_peclet(30.0, n / 2, w.tau_lb, w.G_inf, w.tau, w.gamma_c)
+    return w, n, g
+
+
+@pytest.fixture(scope="module")
+def duct_oracle():
+    w, n, g = duct_subrun()
+    orc = oracle.Channel(oracle.D3Q19, 1, n, n, tau_lb=w.tau_lb, G_inf=w.G_inf, tau=w.tau, gamma_c=w.gamma_c,
+                         g=(g, 0, 0), C=w.C, B=w.B)
+    out, t = {}, 0
+    for cp in DUCT_CP:
+        orc.step(cp - t)
+        t = cp
+        out[cp] = orc.fields()
+    orc.close()
+    return out
+
+
+@pytest.mark.parametrize("prec", [PLAIN, RED])
+def test_duct_32cubed_L512_3000_steps_vs_oracle(duct_oracle, prec):
+    w, n, g = duct_subrun()
+    assert (w.C, w.B, w.steps) == (128, 4, 3000)
+    ch = L.Channel(L.make_desc(L.LBVE_D3Q19, n, n, n, tau_lb=w.tau_lb, G_inf=w.G_inf, tau=w.tau, gamma_c=w.gamma_c,
+                               g=(g, 0, 0), C=w.C, B=w.B, precision=prec[0], hist_storage=prec[1]))
+    t = 0
+    for cp in DUCT_CP:
+        ch.step(cp - t)
+        t = cp
+        got = columns(ch.fields(), n, n, n)
+        check(field_errors(got, duct_oracle[cp], 3), TOL[prec], f"duct 32^3 L512 {NAME[prec]} step {cp}:")
+    ch.close()
+
+
+# ---------------------------------------------------------------------------------------------
+# The 64-channel batch through 4000 startup and 2000 cessation steps
+# ---------------------------------------------------------------------------------------------
+BATCH_CP = (48, 1000, 4000, 4500, 6000)
+
+
+def sampled_channels(ws):
+    order = sorted(range(len(ws)), key=lambda i: ws[i].ny)
+    return order[0], order[len(order) // 2], order[-1]
+
+
+@pytest.fixture(scope="module")
+def batch_oracle():
+    ws = configs.batched_channels()
+    out = {}
+    for i in sampled_channels(ws):
+        w = ws[i]
+        o = oracle.Channel(oracle.D2Q9, 1, w.ny, tau_lb=w.tau_lb, G_inf=w.G_inf, tau=w.tau, gamma_c=w.gamma_c,
+                           g=(w.g, 0, 0), C=w.C, B=w.B)
+        t, rec = 0, {}
+        for cp in BATCH_CP:
+            o.step(cp - t)
+            t = cp
+            rec[cp] = o.fields()
+            if t == w.steps:
+                o.set_force((0, 0, 0))
+        o.close()
+        out[i] = rec
+    return ws, out
+
+
+@pytest.mark.parametrize("prec", [PLAIN, RED])
+def test_batch64_startup_cessation_vs_oracle(batch_oracle, prec):
+    ws, ref = batch_oracle
+    assert all((w.steps, w.off_steps) == (4000, 2000) for w in ws)
+    ch = L.Channel([w.desc(precision=prec[0], hist_storage=prec[1]) for w in ws])
+    t = 0
+    for cp in BATCH_CP:
+        ch.step(cp - t)
+        t = cp
+        f = ch.fields()
+        for i, r in ref.items():
+            w = ws[i]
+            got = columns(ch.channel_fields(i, f), w.nx, w.ny)
+            check(field_errors(got, r[cp], 2), TOL[prec], f"batch channel {i} (ny {w.ny}) {NAME[prec]} step {cp}:")
+        if t == ws[0].steps:
+            ch.set_force((0, 0, 0))          # cessation in every channel
+    ch.close()

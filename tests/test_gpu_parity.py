@@ -8,7 +8,7 @@ to rounding, e.g. u_y in channel flow):
                                                                velocity per step, accumulated over 3000
                                                                steps and measured against a flow that has
                                                                decayed 40x after cessation: 1.3e-5 seen)
-  FP64                                               <= 1e-11
+  FP64                                               <= 1e-12  (the stated bar of the FP64 path)
   reduced-precision form: 16-bit block-scaled history (LBVE_S16), FP32 (or FP64) populations
                                                      <= 1e-3 (the stated bar of the precision variant)
 Integer/structural results (x-invariance, history grid) are compared exactly.
@@ -28,7 +28,7 @@ pytestmark = pytest.mark.gpu
 F32, F64, S16 = L.LBVE_F32, L.LBVE_F64, L.LBVE_S16
 # (population precision, history precision) -> tolerance
 PLAIN, ALL32, ALL64, RED, RED64 = (F64, F32), (F32, F32), (F64, F64), (F32, S16), (F64, S16)
-TOL = {PLAIN: 1e-5, ALL32: 5e-5, ALL64: 1e-11, RED: 1e-3, RED64: 1e-3, F32: 1e-5, F64: 1e-11, S16: 1e-3}
+TOL = {PLAIN: 1e-5, ALL32: 5e-5, ALL64: 1e-12, RED: 1e-3, RED64: 1e-3, F32: 1e-5, F64: 1e-12, S16: 1e-3}
 
 
 def same_sweep_shape(a, *others):
@@ -54,15 +54,16 @@ def compare(gpu: dict, orc: dict, tol: float, what: str):
     order in the shear rate and, at low Peclet number, below the rounding noise of components that vanish
     by symmetry); the density field-wise, and its deviation from rho0 where that deviation (>= 1e-6) is
     resolved by the stored precision (FP32 keeps about 1e-12 absolute)."""
-    for key in ("u", "sigma", "kappa"):
-        e = rel_err(gpu[key], orc[key])
-        assert e <= tol, f"{what}: {key} normwise error {e:.3e} > {tol:.1e}"
+    errs = {key: rel_err(gpu[key], orc[key]) for key in ("u", "sigma", "kappa", "rho")}
     sig_scale = np.max(np.abs(orc["sigma"]))
     if sig_scale > 0:
-        e = np.max(np.abs(gpu["n1"] - orc["n1"])) / sig_scale
-        assert e <= tol, f"{what}: n1 error on the sigma scale {e:.3e} > {tol:.1e}"
-    e = rel_err(gpu["rho"], orc["rho"])
-    assert e <= tol, f"{what}: rho normwise error {e:.3e}"
+        errs["n1"] = np.max(np.abs(gpu["n1"] - orc["n1"])) / sig_scale
+    print(what, {k: f"{v:.2e}" for k, v in errs.items()})
+    for key in ("u", "sigma", "kappa"):
+        assert errs[key] <= tol, f"{what}: {key} normwise error {errs[key]:.3e} > {tol:.1e}"
+    if "n1" in errs:
+        assert errs["n1"] <= tol, f"{what}: n1 error on the sigma scale {errs['n1']:.3e} > {tol:.1e}"
+    assert errs["rho"] <= tol, f"{what}: rho normwise error {errs['rho']:.3e}"
     dr_ref = orc["rho"] - 1.0
     if np.max(np.abs(dr_ref)) >= 1e-6:
         # the density deviation carries the trace of sigma (second order in the shear, like N1): its

@@ -5,7 +5,7 @@
 - LBVE_MODEL_WM: the White-Metzner form of Eq. (nlmax) (Sec. II): accumulated strain in the second
   exponential, one double per history point.
 
-Tolerances (normwise max-relative per field, as in test_gpu_parity.py): FP64 1e-11; plain FP32 history
+Tolerances (normwise max-relative per field, as in test_gpu_parity.py): FP64 1e-12; plain FP32 history
 with FP64 populations 1e-5; all-FP32 5e-5.  The instantaneous model in FP32 sums its series in float
 (resolution 6e-8 of the stress), inside the FP32 bars.
 """

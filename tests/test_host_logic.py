@@ -51,6 +51,6 @@ def test_reference_arm_prints_one_contract_line(workload):
                 "scaling", "vs_baseline", "dtype", "data", "config", "cpu_baseline", "e2e", "impl"):
         assert key in d, key
     assert d["impl"] == "reference" and d["value"] > 0
-    assert d["cpu_baseline"]["kind"] == "oracle" and d["cpu_baseline"]["cores"] == 1
+    assert d["cpu_baseline"]["kind"] == "oracle" and d["cpu_baseline"]["cores"] >= 1
     assert d["e2e"]["h2d_bytes_per_step"] == 0 and d["e2e"]["d2h_bytes_per_step"] == 0
     assert "workload" in d["config"]

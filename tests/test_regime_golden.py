@@ -95,3 +95,21 @@ def test_curves_normalise_by_the_end_of_startup():
     c = sw.channels[0]
     assert st["t_over_tau0"][0] == pytest.approx(10 / c.tau0)
     assert sp["t_over_twall"][0] == pytest.approx(10 / c.t_wall)
+
+
+def test_curves_with_a_vanishing_normaliser_are_nan_with_a_warning():
+    # a probe whose shear stress is zero at the end of startup (e.g. on the centreline): its sigma_xy curve
+    # cannot be normalised and comes back NaN with a warning; the other curves are unaffected
+    sw = regime.RegimeSweep.__new__(regime.RegimeSweep)
+    sw.channels = [regime.regime_channel(1.0, 10.0, 20)]
+    sw.weights = [0.25]
+    t = np.arange(1, 11) * 10
+    vals = np.zeros((10, 2, 6))
+    vals[:, :, 1] = 1.0                             # u
+    vals[:, :, 3] = 5.0                             # sigma_xx
+    vals[:, :, 4] = 1.0                             # sigma_yy; sigma_xy stays 0
+    sw._records = [(t, vals)]
+    with pytest.warns(RuntimeWarning, match="sxy"):
+        cur = sw.curves(60)[0]
+    assert np.all(np.isnan(cur["startup"]["sxy"])) and np.all(np.isnan(cur["cessation"]["sxy"]))
+    assert np.allclose(cur["startup"]["u"], 1.0) and np.allclose(cur["cessation"]["n1"], 1.0)

@@ -711,7 +711,7 @@ static double n_eq_dev(const orc_channel* ch, int i, double drho, double rho, co
  * hydrodynamic rho and u, and tr sigma(t).
  */
 static void collide_node(const orc_channel* ch, const double* n, const double* sg, double tr_prev,
-                         double* post, double* rho_out, double* u_out, double* tr_out) {
+                         double* post, double* rho_out, double* u_out, double* tr_out, double* drho_out) {
     const int d = ch->d, Q = ch->Q;
     const double cs2 = 1.0 / 3.0;
     const double f[3] = {ch->rho0 * ch->g[0], ch->rho0 * ch->g[1], ch->rho0 * ch->g[2]};
@@ -757,6 +757,7 @@ static void collide_node(const orc_channel* ch, const double* n, const double* s
         post[i] = n[i] - (n[i] - neq) / ch->tau_lb + Fi;
     }
     *rho_out = rho;
+    *drho_out = drho;
     for (int a = 0; a < 3; ++a) u_out[a] = u[a];
     *tr_out = tr;
 }
@@ -811,8 +812,8 @@ static void channel_step(orc_channel* ch) {
         for (int y = 0; y < ch->ny; ++y)
             for (int x = 0; x < ch->nx; ++x) {
                 const int64_t k = node_id(ch, x, y, z);
-                double post[ORC_MAXQ], rho, u[3], tr;
-                collide_node(ch, &ch->n[k * Q], &ch->sigma[k * 6], ch->tr_prev[k], post, &rho, u, &tr);
+                double post[ORC_MAXQ], rho, u[3], tr, drho;
+                collide_node(ch, &ch->n[k * Q], &ch->sigma[k * 6], ch->tr_prev[k], post, &rho, u, &tr, &drho);
                 for (int i = 0; i < Q; ++i) {
                     /* stream with half-way bounce-back */
                     int xd = x + ch->c[i][0], yd = y + ch->c[i][1], zd = z + ch->c[i][2];
@@ -827,11 +828,12 @@ static void channel_step(orc_channel* ch) {
                     if (!wall && ch->xbc_pressure && (xs < 0 || xs >= ch->nx)) {
                         /* crossing the seam: the population of the ghost image (inlet ghost for +x,
                          * outlet ghost for -x) -- equilibrium at the ghost density, this node's
-                         * non-equilibrium part, both as deviations from w rho0 */
+                         * non-equilibrium part, both as deviations from w rho0 (the deviations of the
+                         * ghost and node densities from rho0 taken as such, not as rho - rho0) */
                         const double half = 0.5 * 3.0 * ch->dp * (ch->nx + 1.0) / ch->nx;
-                        const double rho_gh = ch->rho0 + ((xs >= ch->nx) ? half : -half);
-                        val = n_eq_dev(ch, i, rho_gh - ch->rho0, rho_gh, u) +
-                              (post[i] - n_eq_dev(ch, i, rho - ch->rho0, rho, u));
+                        const double drho_gh = (xs >= ch->nx) ? half : -half;
+                        val = n_eq_dev(ch, i, drho_gh, ch->rho0 + drho_gh, u) +
+                              (post[i] - n_eq_dev(ch, i, drho, rho, u));
                     }
                     if (wall) ch->n_next[k * Q + ch->opp[i]] = val;
                     else ch->n_next[node_id(ch, xd, yd, zd) * Q + i] = val;
@@ -903,8 +905,8 @@ void orc_expm(int d, const double* K, double* out) { expm_d(d, K, out); }
  * populations n in, full post-collision populations out. */
 void orc_collide(const orc_channel* ch, const double* n, const double* sigma, double tr_prev, double* post,
                  double* rho, double* u) {
-    double tr, dn[ORC_MAXQ];
+    double tr, drho, dn[ORC_MAXQ];
     for (int i = 0; i < ch->Q; ++i) dn[i] = n[i] - ch->w[i] * ch->rho0;
-    collide_node(ch, dn, sigma, tr_prev, post, rho, u, &tr);
+    collide_node(ch, dn, sigma, tr_prev, post, rho, u, &tr, &drho);
     for (int i = 0; i < ch->Q; ++i) post[i] += ch->w[i] * ch->rho0;
 }

@@ -56,6 +56,12 @@ def parse():
                          "the adjoint with checkpoints every 64 steps (a step of this line = one gradient)")
     ap.add_argument("--history", choices=["f32", "s16", "f64"], default="f32",
                     help="history storage: f32 (plain FP32 form), s16 (16-bit block-scaled precision variant), f64")
+    ap.add_argument("--form", choices=["p", "f"], default="p",
+                    help="history form: p (E - 1 advanced in place; the benchmark line) or f (the paper's factor "
+                         "storage: F - 1 and kappa + kappa^T written once, E re-formed by products every step)")
+    ap.add_argument("--no-batch", action="store_true",
+                    help="skip the 64-channel batch arms of the channel line (batched chosen form, batched FP32, "
+                         "one handle per channel)")
     ap.add_argument("--model", choices=["nlm", "wm", "inlm"], default="nlm",
                     help="constitutive model: nlm (integral nlM, the benchmark line), wm (White-Metzner form), "
                          "inlm (instantaneous nlM of Eq. inlM: no history; metric lattice node updates/s)")
@@ -141,6 +147,116 @@ class ClockSampler:
 def points_per_step(C: int, B: int, t0: int, K: int, L) -> list:
     """Retained history points (including the one created) of steps t0 .. t0+K-1 (same at every node)."""
     return [len(L.lbve_schedule(C, B, t)[0]) for t in range(t0, t0 + K)]
+
+
+def bytes_per_update(D: int, hist: int, form: int, L, wm: bool = False) -> float:
+    """Algorithmic history bytes per node-history update of the sweep (what one step must move per retained
+    point): form P reads and writes X = E - 1 and reads kappa (d*d values each; the 16-bit frame form reads
+    Q - 1 and kappa, int16 mantissas plus an exponent byte each, and rewrites Q every 32nd step); form F only
+    reads F - 1 (d*d) and kappa + kappa^T (NS)."""
+    DD, NS = D * D, (3 if D == 2 else 6)
+    if form == L.LBVE_FORM_F:
+        if hist == L.LBVE_S16:
+            return 2 * (DD + NS) + 2
+        return (DD + NS) * (4 if hist == L.LBVE_F32 else 8)
+    if hist == L.LBVE_S16:
+        return 2 * (2 * DD + 1) + (2 * DD + 1) / 32
+    b = 3 * DD * (4 if hist == L.LBVE_F32 else 8)
+    return b + (8 if wm else 0)
+
+
+FORM_NAMES = {("p", "f32"): "form P, FP32 history (E - 1 and kappa), FP64 populations",
+              ("p", "s16"): "form P, 16-bit block-scaled history (kappa, Q in a per-node frame), FP32 populations",
+              ("f", "f32"): "form F (factor storage), FP32 history (F - 1, kappa + kappa^T), FP64 populations",
+              ("f", "s16"): "form F (factor storage), 16-bit block-scaled F - 1 and kappa + kappa^T, FP32 populations"}
+FORM_BAR = {("p", "f32"): 1e-5, ("p", "s16"): 1e-3, ("f", "f32"): 1e-5, ("f", "s16"): 1e-3}
+
+
+def form_descs(descs, L, form: str, hist: str):
+    """Copies of the workload's descriptions in another history form / storage (16-bit: FP32 populations)."""
+    import copy as _copy
+    out = [_copy.copy(d) for d in descs]
+    for d in out:
+        d.hist_form = L.LBVE_FORM_F if form == "f" else L.LBVE_FORM_P
+        d.hist_storage = L.LBVE_S16 if hist == "s16" else L.LBVE_F32
+        d.pop_precision = L.LBVE_F32 if hist == "s16" else L.LBVE_F64
+    return out
+
+
+def time_steps(L, torch, descs, rho, K, W, Kp, stream, sync_ranks):
+    """Create a handle, W untimed steps, K steps timed with CUDA events on `stream` (16-step graphs replayed),
+    then Kp steps with per-launch events.  Returns (ms of the K steps, max over ranks; ms per sweep launch;
+    ms per collide launch; (slot chunks, CTAs, CTA tasks))."""
+    ch = L.Channel(descs if len(descs) > 1 else descs[0], rho)
+    try:
+        ch.step(W, stream)
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        sync_ranks()
+        e0.record(stream)
+        ch.step(K, stream)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1)
+        L.lbve_profile(ch.h, True)
+        ch.step(Kp, stream)
+        kms, launches = L.lbve_profile_read(ch.h)
+        L.lbve_profile(ch.h, False)
+        shape = L.lbve_sweep_config(ch.h)
+    finally:
+        ch.close()
+    return ms, kms[1] / max(launches[1], 1), kms[2] / max(launches[2], 1), shape
+
+
+def batch_arms(L, torch, configs, chosen: str, K: int, W: int, stream, sync_ranks, max_over_ranks, world: int,
+               peak: float) -> dict:
+    """The 64-channel batch workload (widths 8-512, L = 1024, 4000 + 2000 steps of which K are timed) in three
+    arms: the chosen reduced-precision form batched (one launch sequence for all channels, 16-step graphs
+    replayed), the plain FP32 form batched the same way, and the plain FP32 form with one handle per channel
+    stepped one launch sequence per channel per step.  Ratios: the chosen batched form against the per-channel
+    plain form (the batching variant's comparison) and against the batched plain form (equal launch mode)."""
+    ws = configs.batched_channels()
+    base = [w.desc() for w in ws]
+    N = sum(w.N for w in ws)
+    C_, B_ = ws[0].C, ws[0].B
+    out = {"workload": f"batch64_channels_L{C_ * B_}", "nodes": N, "widths": [w.ny for w in ws]}
+    fm, hs = chosen.split("_")
+    arms = {"batched_chosen": form_descs(base, L, fm, hs), "batched_plain_f32": form_descs(base, L, "p", "f32")}
+    pts = points_per_step(C_, B_, W, K, L)
+    Kp = max(8, min(K, 64))
+    pts_p = points_per_step(C_, B_, W + K, Kp, L)
+    for name, dc in arms.items():
+        ms, sweep_ms, _, shape = time_steps(L, torch, dc, None, K, W, Kp, stream, sync_ranks)
+        ms = max_over_ranks(ms)
+        bpu = bytes_per_update(2, dc[0].hist_storage, dc[0].hist_form, L)
+        out[name] = {"form": FORM_NAMES[(fm, hs) if name == "batched_chosen" else ("p", "f32")],
+                     "value": N * sum(pts) * world / (ms / 1e3), "unit": UNIT, "ms_per_step": ms / K,
+                     "sweep_ms_per_launch": sweep_ms,
+                     "roofline_frac": bpu * N * (sum(pts_p) - Kp) / Kp / (sweep_ms / 1e3) / 1e9 / peak,
+                     "launches_per_step": 3, "sweep": {"slot_chunks": shape[0], "ctas": shape[1]}}
+    # the plain form as separate channels: one handle and one launch sequence per channel per step
+    hs_ = [L.Channel(d) for d in arms["batched_plain_f32"]]
+    try:
+        Kq = max(4, K // 8)
+        for h in hs_:
+            h.step(2, stream)
+        torch.cuda.synchronize()
+        sync_ranks()
+        t0 = time.perf_counter()
+        for _ in range(Kq):
+            for h in hs_:
+                L.lbve_step(h.h, 1, stream)
+        torch.cuda.synchronize()
+        dtq = max_over_ranks(time.perf_counter() - t0)
+    finally:
+        for h in hs_:
+            h.close()
+    ptsq = points_per_step(C_, B_, 2, Kq, L)
+    out["per_channel_plain_f32"] = {"form": FORM_NAMES["p", "f32"], "value": N * sum(ptsq) * world / dtq, "unit": UNIT,
+                                    "ms_per_step": 1e3 * dtq / Kq, "launches_per_step": 3 * len(ws)}
+    out["chosen_vs_plain_per_channel"] = out["batched_chosen"]["value"] / out["per_channel_plain_f32"]["value"]
+    out["chosen_vs_plain_batched"] = out["batched_chosen"]["value"] / out["batched_plain_f32"]["value"]
+    return out
 
 
 def kernel_hash(files=("lbve_kernels.cuh", "lbve_sched.cuh")) -> str:
@@ -461,8 +577,10 @@ def run_ours(args, rank, world, local_rank):
         name += "_pressure"
         notes = dict(notes, drive="pressure-step boundary along x, dp = rho0 g nx per period")
     hist = {"f32": L.LBVE_F32, "s16": L.LBVE_S16, "f64": L.LBVE_F64}[args.history]
+    form = L.LBVE_FORM_F if args.form == "f" else L.LBVE_FORM_P
     for d in descs:
         d.hist_storage = hist
+        d.hist_form = form
         if hist == L.LBVE_S16:
             # the reduced-precision form: FP32 populations are well inside its 1e-3 budget
             d.pop_precision = L.LBVE_F32
@@ -470,19 +588,14 @@ def run_ours(args, rank, world, local_rank):
     wm = args.model == "wm"
     if wm and hist == L.LBVE_S16:
         raise SystemExit("the White-Metzner form has no 16-bit history")
+    if wm and form == L.LBVE_FORM_F:
+        raise SystemExit("the White-Metzner form has no factor-storage history")
     metric = METRIC_NODES if inst else METRIC
     d0 = descs[0]
     N = sum(d.nx * d.ny * d.nz for d in descs)
     D = 2 if d0.lattice == L.LBVE_D2Q9 else 3
     Q = d0.lattice
-    if d0.hist_storage == L.LBVE_S16:
-        # read Q and kappa (d*d int16 + 1-byte exponent each); every 32nd step also writes Q
-        bytes_per_update = 2 * (2 * D * D + 1) + (2 * D * D + 1) / 32
-    else:
-        hist_bytes = 4 if d0.hist_storage == L.LBVE_F32 else 8
-        bytes_per_update = 3 * D * D * hist_bytes     # read X, write X, read kappa
-        if wm:
-            bytes_per_update += 8                     # read the point's creation strain Gamma(t') (double)
+    bpu = bytes_per_update(D, d0.hist_storage, form, L, wm)
     # the collide kernel, per node: populations in and out, u_raw, sigma, kappa, rho, u out, tr_prev in/out
     pop_bytes = 8 if d0.pop_precision == L.LBVE_F64 else 4
     NS = 3 if D == 2 else 6
@@ -541,11 +654,14 @@ def run_ours(args, rank, world, local_rank):
         state_bytes = 2 * Q * pop_bytes * N
     else:
         pts_p = points_per_step(d0.hist_C, d0.hist_B, W + K, Kp, L)
-        alg_bytes = bytes_per_update * N * (sum(pts_p) - Kp) / Kp   # the new point is not read from memory
+        alg_bytes = bpu * N * (sum(pts_p) - Kp) / Kp   # the new point is not read from memory
         achieved = alg_bytes / (hist_ms / 1e3) / 1e9
-        roof_kernel = "k_sweep_s16" if d0.hist_storage == L.LBVE_S16 else "k_sweep"
+        roof_kernel = {(L.LBVE_FORM_P, True): "k_sweep_s16", (L.LBVE_FORM_P, False): "k_sweep",
+                       (L.LBVE_FORM_F, True): "k_sweep_f16", (L.LBVE_FORM_F, False): "k_sweep_f"}[
+                           (form, d0.hist_storage == L.LBVE_S16)]
         state_bytes = alg_bytes
-    prof = recorded_profile(args.model, args.workload) if not args.nx and args.history == "f32" else {}
+    prof = (recorded_profile(args.model, args.workload)
+            if not args.nx and args.history == "f32" and args.form == "p" else {})
     traffic = prof.get("dram_bytes_per_launch")
     roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
                 "traffic": traffic, "peak_kind": peak_kind, "kernel": roof_kernel,
@@ -564,38 +680,30 @@ def run_ours(args, rank, world, local_rank):
     ch.close()
 
     extra = {}
-    if args.workload in ("channel", "duct") and args.history == "f32" and not args.no_chosen and args.model == "nlm":
-        # the chosen (reduced-precision) form on the same workload: 16-bit block-scaled history in a
-        # per-node frame, FP32 populations (its parity bar is 1e-3)
-        import copy as _copy
-        dc = [_copy.copy(d) for d in descs]
-        for d in dc:
-            d.hist_storage = L.LBVE_S16
-            d.pop_precision = L.LBVE_F32
-        chc = L.Channel(dc if len(dc) > 1 else dc[0], rho)
-        chc.step(W, stream)
-        torch.cuda.synchronize()
-        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        barrier()
-        e0.record(stream)
-        chc.step(K, stream)
-        e1.record(stream)
-        torch.cuda.synchronize()
-        msc = max_over_ranks(e0.elapsed_time(e1))
-        L.lbve_profile(chc.h, True)
-        chc.step(Kp, stream)
-        kmc, lnc = L.lbve_profile_read(chc.h)
-        L.lbve_profile(chc.h, False)
-        chc.close()
-        sweep_c = kmc[1] / max(lnc[1], 1)
-        bytes_c = (2 * (2 * D * D + 1) + (2 * D * D + 1) / 32) * N * (sum(pts_p) - Kp) / Kp
-        chosen_value = updates_rank * world / (msc / 1e3)
-        extra = {"chosen": {"form": "16-bit block-scaled history (kappa, Q in a per-node frame), f32 populations",
-                            "value": chosen_value, "unit": UNIT, "ms_per_step": msc / K,
-                            "sweep_ms_per_launch": sweep_c,
-                            "roofline_frac": bytes_c / (sweep_c / 1e3) / 1e9 / peak,
-                            "parity_bar": 1e-3},
-                 "chosen_vs_plain": chosen_value / value}
+    if (args.workload in ("channel", "duct") and args.history == "f32" and args.form == "p" and not args.no_chosen
+            and args.model == "nlm"):
+        # every other history form on the same workload (the line's own run is form P with the FP32 history);
+        # chosen = the fastest of them that meets the reduced-precision bar (1e-3)
+        pts_f = sum(pts_p) - Kp
+        forms = {"p_f32": {"form": FORM_NAMES["p", "f32"], "value": value, "unit": UNIT, "ms_per_step": ms_max / K,
+                           "sweep_ms_per_launch": hist_ms, "bytes_per_update": bpu, "roofline_frac": achieved / peak,
+                           "parity_bar": FORM_BAR["p", "f32"]}}
+        for fm, hs in (("p", "s16"), ("f", "f32"), ("f", "s16")):
+            dc = form_descs(descs, L, fm, hs)
+            msc, sweep_c, coll_c, shape_c = time_steps(L, torch, dc, rho, K, W, Kp, stream, barrier)
+            msc = max_over_ranks(msc)
+            bpu_c = bytes_per_update(D, dc[0].hist_storage, dc[0].hist_form, L)
+            forms[f"{fm}_{hs}"] = {"form": FORM_NAMES[fm, hs], "value": updates_rank * world / (msc / 1e3),
+                                   "unit": UNIT, "ms_per_step": msc / K, "sweep_ms_per_launch": sweep_c,
+                                   "collide_ms_per_launch": coll_c, "bytes_per_update": bpu_c,
+                                   "roofline_frac": bpu_c * N * pts_f / Kp / (sweep_c / 1e3) / 1e9 / peak,
+                                   "sweep": {"slot_chunks": shape_c[0], "ctas": shape_c[1]},
+                                   "parity_bar": FORM_BAR[fm, hs]}
+        best = max((k for k in forms if k != "p_f32"), key=lambda k: forms[k]["value"])
+        extra = {"forms": forms, "chosen": dict(forms[best], key=best),
+                 "chosen_vs_plain": forms[best]["value"] / value}
+        if args.workload == "channel" and not args.no_batch and not args.nx:
+            extra["batch64"] = batch_arms(L, torch, configs, best, K, W, stream, barrier, max_over_ranks, world, peak)
     if inst and not args.no_chosen:
         # the instantaneous model with FP32 populations (the series summed in float): its collision runs on
         # the FP32 pipe instead of the FP64 one; parity bar of the all-FP32 form 5e-5

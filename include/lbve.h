@@ -49,6 +49,18 @@ extern "C" {
                             Q = E(t_b, t') in a per-node FP32 frame R = E(t, t_b) re-based every 32
                             steps; FP32 arithmetic */
 
+#define LBVE_FORM_P 0     /* history form P: every point keeps X = E(t,t') - 1, advanced in place every step by
+                             the left factor exp(kappa(t-1)) of Eq. (eeval), and its kappa (16-bit storage:
+                             the frame form described at LBVE_S16) */
+#define LBVE_FORM_F 1     /* history form F, the paper's factor storage (Sec. III): every point keeps, written
+                             once, its factor deviation F - 1 -- exp(kappa(t')) - 1, or for a merged point the
+                             product of the two merged factors, newer on the left -- and its rate of strain
+                             kappa + kappa^T (averaged on merge); every step re-forms E(t,t') as the ordered
+                             product of the factors from the newest point on (Eq. eeval).  Storage LBVE_F32,
+                             LBVE_F64 or LBVE_S16 (16-bit block-scaled F - 1 and rate of strain, FP32
+                             arithmetic); the sweep only reads the history.  Not with LBVE_MODEL_WM, nor for
+                             differentiation (LBVE_ENOSUPPORT) */
+
 #define LBVE_TRACE_FULL 0 /* Eq. (bodyforce) with the density source d_t(delta rho) as written */
 #define LBVE_TRACE_NONE 1 /* both d_t(delta rho) terms dropped, rho = sum n (channel simplification) */
 
@@ -105,6 +117,8 @@ typedef struct {
     double  dp;               /* LBVE_X_PRESSURE: pressure drop per period along x (lattice units, finite);
                                  ignored for LBVE_X_PERIODIC.  Differentiation of a channel with
                                  LBVE_X_PRESSURE returns LBVE_ENOSUPPORT */
+    int32_t hist_form;        /* LBVE_FORM_P (0) | LBVE_FORM_F: how the history stores its points (Sec. III);
+                                 the same for every channel of a batch */
 } lbve_channel_desc;
 
 typedef struct lbve lbve_t;   /* opaque; owns every device buffer of one channel or of a batch */

@@ -15,7 +15,8 @@ CSRC = os.path.join(HERE, "csrc")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(BUILD, "liblbve.so")
 SOURCES = ["lbve_api.cu"]
-HEADERS = ["lbve_kernels.cuh", "lbve_collide.cuh", "lbve_sched.cuh", "lbve_tangent.cuh", "lbve_adjoint.cuh"]
+HEADERS = ["lbve_kernels.cuh", "lbve_collide.cuh", "lbve_sched.cuh", "lbve_tangent.cuh", "lbve_adjoint.cuh",
+           "lbve_formf.cuh"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 

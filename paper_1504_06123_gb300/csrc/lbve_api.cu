@@ -22,6 +22,7 @@
 #include "lbve_collide.cuh"
 #include "lbve_tangent.cuh"
 #include "lbve_adjoint.cuh"
+#include "lbve_formf.cuh"
 
 using namespace lbk;
 
@@ -54,7 +55,9 @@ struct lbve {
     long long Npad;
     int pop_dbl;               // 1: populations stored in double
     int hist_dbl;              // 1: history stored (and advanced) in double
-    int hist_s16;              // 1: 16-bit block-scaled history in a per-node frame
+    int hist_s16;              // 1: 16-bit block-scaled history (in a per-node frame for form P)
+    int hist_formf = 0;        // 1: form F, the factor storage (per point F - 1 and kappa + kappa^T, written once)
+    int part_ns = 0;           // components per chunk record of the sweep: NS (form P), NS + d*d (form F)
     int model = LBVE_MODEL_NLM;  // constitutive model (LBVE_MODEL_*)
     size_t pesz, hesz;         // element sizes of populations and history (partial sums)
     std::vector<Chan> chan_host;
@@ -235,8 +238,10 @@ int check_desc(const lbve_channel_desc* d) {
     if (d->model != LBVE_MODEL_NLM && d->model != LBVE_MODEL_INLM && d->model != LBVE_MODEL_WM) return LBVE_EINVAL;
     if (d->x_boundary != LBVE_X_PERIODIC && d->x_boundary != LBVE_X_PRESSURE) return LBVE_EINVAL;
     if (d->x_boundary == LBVE_X_PRESSURE && !std::isfinite(d->dp)) return LBVE_EINVAL;
+    if (d->hist_form != LBVE_FORM_P && d->hist_form != LBVE_FORM_F) return LBVE_EINVAL;
     if (d->hist_storage == LBVE_BF16) return LBVE_ENOSUPPORT;
     if (d->model == LBVE_MODEL_WM && d->hist_storage == LBVE_S16) return LBVE_ENOSUPPORT;
+    if (d->model == LBVE_MODEL_WM && d->hist_form == LBVE_FORM_F) return LBVE_ENOSUPPORT;
     return LBVE_OK;
 }
 
@@ -244,7 +249,7 @@ int check_desc(const lbve_channel_desc* d) {
 bool same_batch_settings(const lbve_channel_desc& a, const lbve_channel_desc& b) {
     return a.lattice == b.lattice && a.hist_C == b.hist_C && a.hist_B == b.hist_B &&
            a.hist_storage == b.hist_storage && a.pop_precision == b.pop_precision && a.rho0 == b.rho0 &&
-           a.model == b.model;
+           a.model == b.model && a.hist_form == b.hist_form;
 }
 
 // Values per lane of the sweep (one 16-byte access): 4 floats or 2 doubles; 3D halves it (registers).
@@ -298,11 +303,58 @@ int launch_sweep_s16(lbve* h, cudaStream_t s) {
     return LBVE_OK;
 }
 
-// History storage kinds (template argument HK): 0 float, 1 double, 2 16-bit block-scaled, 3 none (the
-// instantaneous model).  Float and double also carry the White-Metzner form (chosen at run time).
+template <typename R>
+CommitF<R> commit_f(lbve* h) {
+    CommitF<R> c;
+    c.Y = (R*)h->X;
+    c.Dm = (R*)h->K;
+    c.part = (R*)h->part;
+    c.B = h->d.hist_B;
+    c.C = h->d.hist_C;
+    c.S = h->S;
+    return c;
+}
+
+CommitF16 commit_f16(lbve* h) {
+    CommitF16 c;
+    c.Ym = (unsigned short*)h->X;
+    c.Ye = (unsigned char*)h->Qe;
+    c.Dmm = (unsigned short*)h->K;
+    c.De = (unsigned char*)h->Ke;
+    c.part = (float*)h->part;
+    c.B = h->d.hist_B;
+    c.C = h->d.hist_C;
+    c.S = h->S;
+    return c;
+}
+
+template <int D, typename R> constexpr int sweep_vn_f() { return (sizeof(R) == 4 ? 4 : 2) / (D == 3 ? 2 : 1); }
+
+template <int D, typename R>
+int launch_sweep_f(lbve* h, cudaStream_t s) {
+    constexpr int VN = sweep_vn_f<D, R>();
+    k_sweep_f<D, R, VN><<<h->sweep_grid, 256, sweep_f_smem_bytes(h->L), s>>>(commit_f<R>(h), h->t_dev, geom_of(h));
+    LBVE_CUDA(cudaGetLastError());
+    return LBVE_OK;
+}
+
+template <int D>
+int launch_sweep_f16(lbve* h, cudaStream_t s) {
+    constexpr int VN = sweep_vn_s16<D>();
+    k_sweep_f16<D, VN><<<h->sweep_grid, 256, sweep_f_smem_bytes(h->L), s>>>(commit_f16(h), h->t_dev, geom_of(h));
+    LBVE_CUDA(cudaGetLastError());
+    return LBVE_OK;
+}
+
+// History kinds (template argument HK): form P in float (0), double (1), 16-bit block-scaled in a per-node
+// frame (2); 3 none (the instantaneous model); form F (the factor storage) in float (4), double (5), 16-bit
+// block-scaled (6).  Form P in float and double also carries the White-Metzner form (chosen at run time).
 template <int D, int HK>
 int launch_sweep_any(lbve* h, cudaStream_t s) {
     if (HK == 3) return LBVE_OK;
+    if (HK == 6) return launch_sweep_f16<D>(h, s);
+    if (HK == 5) return launch_sweep_f<D, double>(h, s);
+    if (HK == 4) return launch_sweep_f<D, float>(h, s);
     if (HK == 2) return launch_sweep_s16<D>(h, s);
     if (HK == 1) return launch_sweep<D, double>(h, s);
     return launch_sweep<D, float>(h, s);
@@ -320,6 +372,18 @@ template <int D> struct SweepKernel<D, 1> {
 template <int D> struct SweepKernel<D, 2> {
     static constexpr int VN = sweep_vn_s16<D>();
     static const void* fn(bool) { return (const void*)k_sweep_s16<D, VN>; }
+};
+template <int D> struct SweepKernel<D, 4> {
+    static constexpr int VN = sweep_vn_f<D, float>();
+    static const void* fn(bool) { return (const void*)k_sweep_f<D, float, VN>; }
+};
+template <int D> struct SweepKernel<D, 5> {
+    static constexpr int VN = sweep_vn_f<D, double>();
+    static const void* fn(bool) { return (const void*)k_sweep_f<D, double, VN>; }
+};
+template <int D> struct SweepKernel<D, 6> {
+    static constexpr int VN = sweep_vn_s16<D>();
+    static const void* fn(bool) { return (const void*)k_sweep_f16<D, VN>; }
 };
 
 // Autotuner of the sweep: candidate (task mode, slot-chunk count S) pairs -- warp tasks with about 2 to
@@ -347,8 +411,8 @@ template <int D, int HK>
 int sweep_autotune(lbve* h) {
     constexpr int VN = SweepKernel<D, HK>::VN;
     const void* fn = SweepKernel<D, HK>::fn(h->model == LBVE_MODEL_WM);
-    const bool has_cta = HK != 2;   // the 16-bit sweep runs warp tasks only
-    const size_t smem = has_cta ? sweep_cta_smem_bytes(h->L) : sweep_smem_bytes(h->L);
+    const bool has_cta = HK == 0 || HK == 1;   // the 16-bit and form-F sweeps run warp tasks only
+    const size_t smem = HK >= 4 ? sweep_f_smem_bytes(h->L) : has_cta ? sweep_cta_smem_bytes(h->L) : sweep_smem_bytes(h->L);
     if (smem > 48 * 1024)
         LBVE_CUDA(cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
     int dev = 0, sms = 0, per_sm = 0;
@@ -368,9 +432,9 @@ int sweep_autotune(lbve* h) {
             }
     }
     if (h->tuned_from_cache) {
-        int rc = alloc(h, &h->part, h->hesz * (size_t)h->S * h->NS * h->Npad);
+        int rc = alloc(h, &h->part, h->hesz * (size_t)h->S * h->part_ns * h->Npad);
         if (rc) return rc;
-        LBVE_CUDA(cudaMemset(h->part, 0, h->hesz * (size_t)h->S * h->NS * h->Npad));
+        LBVE_CUDA(cudaMemset(h->part, 0, h->hesz * (size_t)h->S * h->part_ns * h->Npad));
         h->part_S = h->S;
         return LBVE_OK;
     }
@@ -403,9 +467,9 @@ int sweep_autotune(lbve* h) {
         }
     long long Sbig = 1;
     for (const Cand& c : cand) Sbig = std::max(Sbig, c.S);
-    int rc = alloc(h, &h->part, h->hesz * (size_t)Sbig * h->NS * h->Npad);
+    int rc = alloc(h, &h->part, h->hesz * (size_t)Sbig * h->part_ns * h->Npad);
     if (rc) return rc;
-    LBVE_CUDA(cudaMemset(h->part, 0, h->hesz * (size_t)Sbig * h->NS * h->Npad));
+    LBVE_CUDA(cudaMemset(h->part, 0, h->hesz * (size_t)Sbig * h->part_ns * h->Npad));
     auto grid_of = [&](const Cand& c) {
         return (int)std::max(1ll, std::min(grid_full, c.cta ? tiles * c.S : (tiles * c.S + 7) / 8));
     };
@@ -418,7 +482,8 @@ int sweep_autotune(lbve* h) {
         // launches timed per candidate: one for a history of a gigabyte or more (a launch then takes
         // well over 100 us, long against the timer), three below; fixed by the size, so that the number of
         // launches at create does not depend on timings
-        const size_t hist_bytes = (size_t)h->L * h->Npad * h->D * h->D * 2 * (HK == 2 ? 2 : h->hesz);
+        const size_t hist_bytes = (size_t)h->L * h->Npad * (h->D * h->D + (h->hist_formf ? h->NS : h->D * h->D)) *
+                                  (h->hist_s16 ? 2 : h->hesz);
         const int reps = hist_bytes >= ((size_t)1 << 30) ? 1 : 3;
         for (const Cand& c : cand) {
             h->S = (int)c.S;
@@ -429,9 +494,9 @@ int sweep_autotune(lbve* h) {
             for (int r = 0; r < reps; ++r) {
                 if ((rc = launch_sweep_any<D, HK>(h, 0))) return rc;
                 if (h->hist_dbl)
-                    k_part_read<double><<<(h->N + 255) / 256, 256>>>((const double*)h->part, (int)c.S, h->NS, h->Npad, h->N, h->red);
+                    k_part_read<double><<<(h->N + 255) / 256, 256>>>((const double*)h->part, (int)c.S, h->part_ns, h->Npad, h->N, h->red);
                 else
-                    k_part_read<float><<<(h->N + 255) / 256, 256>>>((const float*)h->part, (int)c.S, h->NS, h->Npad, h->N, h->red);
+                    k_part_read<float><<<(h->N + 255) / 256, 256>>>((const float*)h->part, (int)c.S, h->part_ns, h->Npad, h->N, h->red);
                 LBVE_CUDA(cudaGetLastError());
             }
             LBVE_CUDA(cudaEventRecord(e1, 0));
@@ -455,10 +520,10 @@ int sweep_autotune(lbve* h) {
     }
     if (best_c.S < Sbig) {   // keep only what the chosen S needs
         dev_free(h, h->part);
-        h->bytes -= h->hesz * (size_t)Sbig * h->NS * h->Npad;
+        h->bytes -= h->hesz * (size_t)Sbig * h->part_ns * h->Npad;
         h->part = nullptr;
         h->part_S = 0;
-        if ((rc = alloc(h, &h->part, h->hesz * (size_t)best_c.S * h->NS * h->Npad))) return rc;
+        if ((rc = alloc(h, &h->part, h->hesz * (size_t)best_c.S * h->part_ns * h->Npad))) return rc;
         h->part_S = (int)best_c.S;
     }
     return LBVE_OK;
@@ -512,6 +577,9 @@ int one_step(lbve* h, int cur, cudaStream_t s) {
     c.t_dev = h->t_dev;
     if ((rc = prof_mark(h, s, KIND_COLLIDE, true))) return rc;
     if (HK == 3) k_collide_stream<Q, P, T, Instant<T>><<<grid, 256, 0, s>>>(c, Instant<T>{1, 4}, g);
+    else if (HK == 6) k_collide_stream<Q, P, T, CommitF16><<<grid, 256, 0, s>>>(c, commit_f16(h), g);
+    else if (HK == 5) k_collide_stream<Q, P, T, CommitF<double>><<<grid, 256, 0, s>>>(c, commit_f<double>(h), g);
+    else if (HK == 4) k_collide_stream<Q, P, T, CommitF<float>><<<grid, 256, 0, s>>>(c, commit_f<float>(h), g);
     else if (HK == 2) k_collide_stream<Q, P, T, CommitS16><<<grid, 256, 0, s>>>(c, commit_s16(h), g);
     else if (HK == 1) k_collide_stream<Q, P, T, CommitArgs<double>><<<grid, 256, 0, s>>>(c, commit_args<double>(h), g);
     else k_collide_stream<Q, P, T, CommitArgs<float>><<<grid, 256, 0, s>>>(c, commit_args<float>(h), g);
@@ -587,6 +655,20 @@ int step_impl(lbve* h, int64_t n, cudaStream_t s) {
         h->t_host += 1;
     }
     return LBVE_OK;
+}
+
+// Population storage P (collision arithmetic the same type) x history kind.
+template <int Q, typename P>
+int step_dispatch(lbve* h, int hk, int64_t n, cudaStream_t s) {
+    switch (hk) {
+        case 0: return step_impl<Q, P, 0, P>(h, n, s);
+        case 1: return step_impl<Q, P, 1, P>(h, n, s);
+        case 2: return step_impl<Q, P, 2, P>(h, n, s);
+        case 3: return step_impl<Q, P, 3, P>(h, n, s);
+        case 4: return step_impl<Q, P, 4, P>(h, n, s);
+        case 5: return step_impl<Q, P, 5, P>(h, n, s);
+        default: return step_impl<Q, P, 6, P>(h, n, s);
+    }
 }
 
 // Fluid at rest: n_q = w_q rho_init(n) (deviation w_q (rho_init - rho0)), density field rho_init - rho0.
@@ -716,9 +798,14 @@ int create_impl(const lbve_channel_desc* descs, int32_t n, const double* rho_ini
     h->pop_dbl = desc->pop_precision == LBVE_F64;
     h->hist_dbl = desc->hist_storage == LBVE_F64;
     h->hist_s16 = desc->hist_storage == LBVE_S16;
+    h->hist_formf = desc->hist_form == LBVE_FORM_F && h->L > 0;
+    h->part_ns = h->NS + (h->hist_formf ? h->D * h->D : 0);
     h->pesz = h->pop_dbl ? 8 : 4;
     h->hesz = h->hist_dbl ? 8 : 4;
     const size_t hist_elem = h->hist_s16 ? 2 : h->hesz;   // bytes of one stored history component
+    // planes per point: form P keeps X = E - 1 and kappa (d*d each); form F keeps F - 1 (d*d) and
+    // kappa + kappa^T (NS)
+    const int kplanes = h->hist_formf ? h->NS : h->D * h->D;
     h->chan_host.resize(n);
     {
         int off = 0;
@@ -741,7 +828,7 @@ int create_impl(const lbve_channel_desc* descs, int32_t n, const double* rho_ini
         (rc = alloc(h, &h->rho, fe * Np)) || (rc = alloc(h, &h->sigma, fe * h->NS * Np)) ||
         (rc = alloc(h, &h->kappa, fe * DD * Np)) || (rc = alloc(h, &h->tr_prev, fe * Np)) ||
         (h->L > 0 && (rc = alloc(h, &h->X, hist_elem * (size_t)h->L * DD * Np))) ||
-        (h->L > 0 && (rc = alloc(h, &h->K, hist_elem * (size_t)h->L * DD * Np))) ||
+        (h->L > 0 && (rc = alloc(h, &h->K, hist_elem * (size_t)h->L * kplanes * Np))) ||
         (rc = alloc(h, (void**)&h->t_dev, sizeof(long long))) || (rc = alloc(h, (void**)&h->red, 2 * sizeof(double))) ||
         (rc = alloc(h, (void**)&h->flag, sizeof(int))) ||
         (rc = alloc(h, (void**)&h->chan_dev, sizeof(Chan) * n)))
@@ -762,7 +849,7 @@ int create_impl(const lbve_channel_desc* descs, int32_t n, const double* rho_ini
     }
     if (h->hist_s16 && h->L > 0 &&
         ((rc = alloc(h, &h->Qe, (size_t)h->L * Np)) || (rc = alloc(h, &h->Ke, (size_t)h->L * Np)) ||
-         (rc = alloc(h, &h->Rm, sizeof(float) * DD * Np))))
+         (!h->hist_formf && (rc = alloc(h, &h->Rm, sizeof(float) * DD * Np)))))
         return fail(rc);
     if (h->model == LBVE_MODEL_WM &&
         ((rc = alloc(h, &h->gam_node, sizeof(double) * Np)) ||
@@ -774,7 +861,7 @@ int create_impl(const lbve_channel_desc* descs, int32_t n, const double* rho_ini
                          h->Qe, h->Ke, h->Rm, h->gam_node, h->gam_pt};
     size_t zero_sizes[] = {h->pesz * h->Q * Np, h->pesz * h->Q * Np, fe * h->D * Np, fe * h->D * Np,
                            fe * h->NS * Np, fe * DD * Np, fe * Np, hist_elem * (size_t)h->L * DD * Np,
-                           hist_elem * (size_t)h->L * DD * Np, sizeof(int), (size_t)h->L * Np, (size_t)h->L * Np,
+                           hist_elem * (size_t)h->L * kplanes * Np, sizeof(int), (size_t)h->L * Np, (size_t)h->L * Np,
                            sizeof(float) * DD * Np, sizeof(double) * Np, sizeof(double) * (size_t)h->L * Np};
     for (int i = 0; i < 15; ++i) {
         if (!zero_bufs[i]) continue;
@@ -787,7 +874,10 @@ int create_impl(const lbve_channel_desc* descs, int32_t n, const double* rho_ini
         if (e != cudaSuccess) return fail(cuda_fail(e, "cudaMemcpy"));
     }
     if (h->L == 0) rc = LBVE_OK;   // no history: no sweep
-    else if (h->D == 2) rc = h->hist_s16 ? sweep_autotune<2, 2>(h) : h->hist_dbl ? sweep_autotune<2, 1>(h) : sweep_autotune<2, 0>(h);
+    else if (h->hist_formf) {
+        if (h->D == 2) rc = h->hist_s16 ? sweep_autotune<2, 6>(h) : h->hist_dbl ? sweep_autotune<2, 5>(h) : sweep_autotune<2, 4>(h);
+        else rc = h->hist_s16 ? sweep_autotune<3, 6>(h) : h->hist_dbl ? sweep_autotune<3, 5>(h) : sweep_autotune<3, 4>(h);
+    } else if (h->D == 2) rc = h->hist_s16 ? sweep_autotune<2, 2>(h) : h->hist_dbl ? sweep_autotune<2, 1>(h) : sweep_autotune<2, 0>(h);
     else rc = h->hist_s16 ? sweep_autotune<3, 2>(h) : h->hist_dbl ? sweep_autotune<3, 1>(h) : sweep_autotune<3, 0>(h);
     if (rc) return fail(rc);
     rc = h->pop_dbl ? init_state<double>(h, rho_init) : init_state<float>(h, rho_init);
@@ -884,6 +974,7 @@ int create_tangent(const lbve_channel_desc* desc, const double* rho_init, lbve_t
     int rc = check_desc(desc);
     if (rc) return rc;
     if (desc->model != LBVE_MODEL_NLM || desc->x_boundary != LBVE_X_PERIODIC) return LBVE_ENOSUPPORT;
+    if (desc->hist_form != LBVE_FORM_P) return LBVE_ENOSUPPORT;
     const long long Ntot = (long long)desc->nx * desc->ny * desc->nz;
     if (rho_init)
         for (long long i = 0; i < Ntot; ++i)
@@ -1076,30 +1167,11 @@ int lbve_step(lbve_t* h, int64_t n_steps, void* stream) {
     if (!h || n_steps < 0) return LBVE_EINVAL;
     cudaStream_t s = (cudaStream_t)stream;
     if (h->tangent) return h->Q == 9 ? tangent_step<9>(h, n_steps, s) : tangent_step<19>(h, n_steps, s);
-    const int hk = h->model == LBVE_MODEL_INLM ? 3 : h->hist_s16 ? 2 : (h->hist_dbl ? 1 : 0);
-    const int combo = (h->pop_dbl ? 4 : 0) + hk;
-    if (h->Q == 9) {
-        switch (combo) {
-            case 0: return step_impl<9, float, 0, float>(h, n_steps, s);
-            case 1: return step_impl<9, float, 1, float>(h, n_steps, s);
-            case 2: return step_impl<9, float, 2, float>(h, n_steps, s);
-            case 3: return step_impl<9, float, 3, float>(h, n_steps, s);
-            case 4: return step_impl<9, double, 0, double>(h, n_steps, s);
-            case 5: return step_impl<9, double, 1, double>(h, n_steps, s);
-            case 6: return step_impl<9, double, 2, double>(h, n_steps, s);
-            default: return step_impl<9, double, 3, double>(h, n_steps, s);
-        }
-    }
-    switch (combo) {
-        case 0: return step_impl<19, float, 0, float>(h, n_steps, s);
-        case 1: return step_impl<19, float, 1, float>(h, n_steps, s);
-        case 2: return step_impl<19, float, 2, float>(h, n_steps, s);
-        case 3: return step_impl<19, float, 3, float>(h, n_steps, s);
-        case 4: return step_impl<19, double, 0, double>(h, n_steps, s);
-        case 5: return step_impl<19, double, 1, double>(h, n_steps, s);
-        case 6: return step_impl<19, double, 2, double>(h, n_steps, s);
-        default: return step_impl<19, double, 3, double>(h, n_steps, s);
-    }
+    const int hk = h->model == LBVE_MODEL_INLM ? 3
+                   : h->hist_formf ? (h->hist_s16 ? 6 : h->hist_dbl ? 5 : 4)
+                   : h->hist_s16 ? 2 : (h->hist_dbl ? 1 : 0);
+    if (h->Q == 9) return h->pop_dbl ? step_dispatch<9, double>(h, hk, n_steps, s) : step_dispatch<9, float>(h, hk, n_steps, s);
+    return h->pop_dbl ? step_dispatch<19, double>(h, hk, n_steps, s) : step_dispatch<19, float>(h, hk, n_steps, s);
 }
 
 int lbve_get_time(const lbve_t* h, int64_t* t) {
@@ -1236,6 +1308,33 @@ int lbve_history_apply(lbve_t* h, const double* kappa_dev, double* sigma_dev, vo
             if (h->pop_dbl) k_commit<3, Instant<double>><<<grid, 256, 0, s>>>(Instant<double>{1, 4}, kappa_dev, (double*)h->sigma, (double*)h->kappa, sigma_dev, h->t_dev, g);
             else k_commit<3, Instant<float>><<<grid, 256, 0, s>>>(Instant<float>{1, 4}, kappa_dev, (double*)h->sigma, (double*)h->kappa, sigma_dev, h->t_dev, g);
         }
+    } else if (h->hist_formf) {
+        const double* kin = kappa_dev;
+        double* sf = (double*)h->sigma;
+        double* kf = (double*)h->kappa;
+        if (h->D == 2) {
+            if (h->hist_s16) {
+                if ((rc = launch_sweep_f16<2>(h, s))) return rc;
+                k_commit<2, CommitF16><<<grid, 256, 0, s>>>(commit_f16(h), kin, sf, kf, sigma_dev, h->t_dev, g);
+            } else if (h->hist_dbl) {
+                if ((rc = launch_sweep_f<2, double>(h, s))) return rc;
+                k_commit<2, CommitF<double>><<<grid, 256, 0, s>>>(commit_f<double>(h), kin, sf, kf, sigma_dev, h->t_dev, g);
+            } else {
+                if ((rc = launch_sweep_f<2, float>(h, s))) return rc;
+                k_commit<2, CommitF<float>><<<grid, 256, 0, s>>>(commit_f<float>(h), kin, sf, kf, sigma_dev, h->t_dev, g);
+            }
+        } else {
+            if (h->hist_s16) {
+                if ((rc = launch_sweep_f16<3>(h, s))) return rc;
+                k_commit<3, CommitF16><<<grid, 256, 0, s>>>(commit_f16(h), kin, sf, kf, sigma_dev, h->t_dev, g);
+            } else if (h->hist_dbl) {
+                if ((rc = launch_sweep_f<3, double>(h, s))) return rc;
+                k_commit<3, CommitF<double>><<<grid, 256, 0, s>>>(commit_f<double>(h), kin, sf, kf, sigma_dev, h->t_dev, g);
+            } else {
+                if ((rc = launch_sweep_f<3, float>(h, s))) return rc;
+                k_commit<3, CommitF<float>><<<grid, 256, 0, s>>>(commit_f<float>(h), kin, sf, kf, sigma_dev, h->t_dev, g);
+            }
+        }
     } else if (h->hist_s16) {
         if (h->D == 2) {
             if ((rc = launch_sweep_s16<2>(h, s))) return rc;
@@ -1311,15 +1410,16 @@ std::vector<StateBuf> state_buffers(lbve* h) {
     const int DD = h->D * h->D;
     const size_t fe = h->tangent ? sizeof(Dual) : sizeof(double);
     const size_t hist_elem = h->tangent ? sizeof(Dual) : (h->hist_s16 ? 2 : h->hesz);
+    const int kplanes = h->hist_formf ? h->NS : DD;
     std::vector<StateBuf> v = {
         {h->pops[h->cur], h->pesz * h->Q * Np}, {h->u, fe * h->D * Np}, {h->rho, fe * Np},
         {h->sigma, fe * h->NS * Np}, {h->kappa, fe * DD * Np}, {h->tr_prev, fe * Np},
-        {h->X, hist_elem * (size_t)h->L * DD * Np}, {h->K, hist_elem * (size_t)h->L * DD * Np},
+        {h->X, hist_elem * (size_t)h->L * DD * Np}, {h->K, hist_elem * (size_t)h->L * kplanes * Np},
         {h->t_dev, sizeof(long long)}};
     if (h->hist_s16) {
         v.push_back({h->Qe, (size_t)h->L * Np});
         v.push_back({h->Ke, (size_t)h->L * Np});
-        v.push_back({h->Rm, sizeof(float) * DD * Np});
+        if (h->Rm) v.push_back({h->Rm, sizeof(float) * DD * Np});
     }
     if (h->gam_node) {
         v.push_back({h->gam_node, sizeof(double) * Np});
@@ -1344,6 +1444,7 @@ uint64_t config_fingerprint(const lbve* h) {
     for (const lbve_channel_desc& d : h->descs) {
         mix(d.lattice); mix(d.nx); mix(d.ny); mix(d.nz); mix(d.wall_z); mix(d.hist_C); mix(d.hist_B);
         mix(d.hist_storage); mix(d.pop_precision); mix(d.trace_coupling); mix(d.model); mix(d.x_boundary);
+        mix(d.hist_form);
     }
     return x;
 }
@@ -1592,6 +1693,7 @@ int lbve_create_adjoint(const lbve_channel_desc* desc, const double* rho_init, i
     if (!desc || !out || checkpoint_every < 1) return LBVE_EINVAL;
     if (desc->pop_precision != LBVE_F64 || desc->hist_storage != LBVE_F64) return LBVE_ENOSUPPORT;
     if (desc->model != LBVE_MODEL_NLM || desc->x_boundary != LBVE_X_PERIODIC) return LBVE_ENOSUPPORT;
+    if (desc->hist_form != LBVE_FORM_P) return LBVE_ENOSUPPORT;
     int rc = create_impl(desc, 1, rho_init, out);
     if (rc) return rc;
     (*out)->rec_K = checkpoint_every;
@@ -1647,23 +1749,23 @@ int lbve_set_sweep_config(lbve_t* h, int32_t slot_chunks, int32_t cta_tasks) {
     if (h->L == 0 || h->tangent || h->rec_K || !h->part) return LBVE_ENOSUPPORT;
     const long long Smax = h->L >= 16 ? h->L / 8 : 1;
     if (slot_chunks < 1 || slot_chunks > Smax || (cta_tasks != 0 && cta_tasks != 1)) return LBVE_EINVAL;
-    if (cta_tasks && h->hist_s16) return LBVE_EINVAL;
+    if (cta_tasks && (h->hist_s16 || h->hist_formf)) return LBVE_EINVAL;   // warp tasks only
     LBVE_CUDA(cudaDeviceSynchronize());
     if (h->graph) {
         cudaGraphExecDestroy(h->graph);
         h->graph = nullptr;
     }
     if (slot_chunks > h->part_S) {
-        const size_t old_bytes = h->hesz * (size_t)h->part_S * h->NS * h->Npad;
+        const size_t old_bytes = h->hesz * (size_t)h->part_S * h->part_ns * h->Npad;
         dev_free(h, h->part);
         h->bytes -= old_bytes;
         h->part = nullptr;
         h->part_S = 0;
-        int rc = alloc(h, &h->part, h->hesz * (size_t)slot_chunks * h->NS * h->Npad);
+        int rc = alloc(h, &h->part, h->hesz * (size_t)slot_chunks * h->part_ns * h->Npad);
         if (rc) return rc;
         h->part_S = slot_chunks;
     }
-    const int vn = h->hist_s16 ? (h->D == 2 ? 4 : 2) : (h->hist_dbl ? 2 : 4) / (h->D == 3 ? 2 : 1);
+    const int vn = h->hist_s16 ? (h->D == 2 ? 4 : 2) : (h->hist_dbl ? 2 : 4) / (h->D == 3 ? 2 : 1);   // both forms
     const long long tiles = h->Npad / (32 * vn);
     h->S = slot_chunks;
     h->sweep_cta = cta_tasks;

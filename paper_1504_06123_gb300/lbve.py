@@ -23,6 +23,7 @@ LBVE_FIXED_STAGING_DOUBLES = 1 << 21
 LBVE_D2Q9, LBVE_D3Q19 = 9, 19
 LBVE_F32, LBVE_F64, LBVE_BF16, LBVE_S16 = 0, 1, 2, 3
 LBVE_TRACE_FULL, LBVE_TRACE_NONE = 0, 1
+LBVE_FORM_P, LBVE_FORM_F = 0, 1
 LBVE_MODEL_NLM, LBVE_MODEL_INLM, LBVE_MODEL_WM = 0, 1, 2
 LBVE_X_PERIODIC, LBVE_X_PRESSURE = 0, 1
 LBVE_FIELD_RHO, LBVE_FIELD_U, LBVE_FIELD_SIGMA, LBVE_FIELD_KAPPA, LBVE_FIELD_N1 = 1, 2, 4, 8, 16
@@ -45,7 +46,7 @@ class lbve_channel_desc(C.Structure):
         ("tau_lb", C.c_double), ("rho0", C.c_double), ("G_inf", C.c_double), ("tau", C.c_double),
         ("gamma_c", C.c_double), ("g", C.c_double * 3), ("hist_C", C.c_int32), ("hist_B", C.c_int32),
         ("hist_storage", C.c_int32), ("pop_precision", C.c_int32), ("trace_coupling", C.c_int32),
-        ("model", C.c_int32), ("x_boundary", C.c_int32), ("dp", C.c_double),
+        ("model", C.c_int32), ("x_boundary", C.c_int32), ("dp", C.c_double), ("hist_form", C.c_int32),
     ]
 
 
@@ -431,8 +432,10 @@ def lbve_profile_read(h: int):
 # ---- convenience wrapper ---------------------------------------------------------------------------
 def make_desc(lattice=LBVE_D2Q9, nx=4, ny=32, nz=1, *, tau_lb=0.9, rho0=1.0, G_inf=0.01, tau=200.0,
               gamma_c=0.1, g=(0.0, 0.0, 0.0), C=128, B=1, precision=LBVE_F32, hist_storage=None,
-              trace_coupling=LBVE_TRACE_FULL, wall_z=1, model=LBVE_MODEL_NLM, dp=None) -> lbve_channel_desc:
-    """dp = None: x periodic, driven by g; a number: the pressure-step boundary with drop dp per period."""
+              trace_coupling=LBVE_TRACE_FULL, wall_z=1, model=LBVE_MODEL_NLM, dp=None,
+              hist_form=None) -> lbve_channel_desc:
+    """dp = None: x periodic, driven by g; a number: the pressure-step boundary with drop dp per period.
+    hist_form: LBVE_FORM_P (default) or LBVE_FORM_F (the factor storage of Sec. III)."""
     d = lbve_channel_desc()
     d.lattice, d.nx, d.ny, d.nz, d.wall_z = lattice, nx, ny, nz, wall_z
     d.tau_lb, d.rho0, d.G_inf, d.tau = tau_lb, rho0, G_inf, tau
@@ -445,6 +448,7 @@ def make_desc(lattice=LBVE_D2Q9, nx=4, ny=32, nz=1, *, tau_lb=0.9, rho0=1.0, G_i
     d.model = model
     d.x_boundary = LBVE_X_PERIODIC if dp is None else LBVE_X_PRESSURE
     d.dp = 0.0 if dp is None else float(dp)
+    d.hist_form = LBVE_FORM_P if hist_form is None else hist_form
     return d
 
 

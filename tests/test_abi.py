@@ -88,9 +88,10 @@ def test_pressure_boundary_arguments_are_checked_before_any_device_work():
     with pytest.raises(L.LbveError) as e:
         L.lbve_set_pressure_step(0, 1e-6)
     assert e.value.status == L.LBVE_EINVAL
-    # the C layout: dp follows x_boundary at an 8-byte boundary
+    # the C layout: dp follows x_boundary at an 8-byte boundary (the whole layout is compared with the
+    # header's struct in test_desc_layout_matches_the_header)
     assert L.lbve_channel_desc.dp.offset % 8 == 0
-    assert ctypes.sizeof(L.lbve_channel_desc) == L.lbve_channel_desc.dp.offset + 8
+    assert ctypes.sizeof(L.lbve_channel_desc) % 8 == 0
 
 
 def test_create_rejects_nonfinite_density():
@@ -128,3 +129,45 @@ def test_no_cpu_fallback_without_gpu():
     with pytest.raises(L.LbveError) as e:
         L.lbve_create(d)
     assert e.value.status in (L.LBVE_ECUDA, L.LBVE_ENOMEM)
+
+
+def test_desc_layout_matches_the_header(tmp_path):
+    """The binding's ctypes mirror of lbve_channel_desc has the C struct's size and field offsets."""
+    import subprocess
+    fields = [f[0] for f in L.lbve_channel_desc._fields_]
+    src = tmp_path / "layout.c"
+    src.write_text('#include <stdio.h>\n#include <stddef.h>\n#include "lbve.h"\nint main(void) {\n'
+                   '  printf("%zu\\n", sizeof(lbve_channel_desc));\n' +
+                   "".join(f'  printf("%zu\\n", offsetof(lbve_channel_desc, {f}));\n' for f in fields) +
+                   "  return 0;\n}\n")
+    exe = tmp_path / "layout"
+    subprocess.run(["gcc", "-std=c99", "-I", os.path.join(ROOT, "include"), "-o", str(exe), str(src)], check=True)
+    out = [int(v) for v in subprocess.run([str(exe)], capture_output=True, text=True, check=True).stdout.split()]
+    import ctypes as C
+    assert out[0] == C.sizeof(L.lbve_channel_desc)
+    for f, off in zip(fields, out[1:]):
+        assert getattr(L.lbve_channel_desc, f).offset == off, f
+
+
+def test_factor_form_arguments_are_checked_before_any_device_work():
+    """hist_form outside {P, F} is invalid; the factor form with the White-Metzner model, and differentiation
+    of a factor-form channel, are valid requests this library does not implement."""
+    bad = L.make_desc(nx=2, ny=4, C=8, B=2, hist_form=2)
+    with pytest.raises(L.LbveError) as e:
+        L.lbve_create(bad)
+    assert e.value.status == L.LBVE_EINVAL
+    wm = L.make_desc(nx=2, ny=4, C=8, B=2, model=L.LBVE_MODEL_WM, hist_form=L.LBVE_FORM_F)
+    with pytest.raises(L.LbveError) as e:
+        L.lbve_create(wm)
+    assert e.value.status == L.LBVE_ENOSUPPORT
+    f64 = L.make_desc(nx=2, ny=4, C=8, B=2, precision=L.LBVE_F64, hist_form=L.LBVE_FORM_F)
+    with pytest.raises(L.LbveError) as e:
+        L.lbve_create_tangent(f64)
+    assert e.value.status == L.LBVE_ENOSUPPORT
+    with pytest.raises(L.LbveError) as e:
+        L.lbve_create_adjoint(f64, None, 8)
+    assert e.value.status == L.LBVE_ENOSUPPORT
+    mixed = [L.make_desc(nx=2, ny=4, C=8, B=2), L.make_desc(nx=2, ny=4, C=8, B=2, hist_form=L.LBVE_FORM_F)]
+    with pytest.raises(L.LbveError) as e:
+        L.lbve_create_batch(mixed)
+    assert e.value.status == L.LBVE_EINVAL

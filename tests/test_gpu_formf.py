@@ -1,0 +1,218 @@
+"""GPU parity of history form F -- the paper's factor storage (Sec. III, Eq. eeval) -- against the FP64 oracle.
+
+Form F keeps, per retained point, its factor deviation F - 1 and its rate of strain kappa + kappa^T, written
+once, and re-forms E(t, t') every step as the ordered product of the factors (the oracle does the same with
+full matrices in FP64).  Storages: FP64 (bar 1e-12, like every FP64 path), FP32 (plain FP32 bar 1e-5) and
+16-bit block-scaled (the reduced-precision bar 1e-3).  Every case of the form-P parity tests that applies is
+repeated here: the history integral alone on prescribed gradients (ragged node counts, odd block sizes,
+3D), the small channel through startup and cessation on both history grids, edge cases, batches, launch
+shapes, graph replay and checkpoint / resume.
+"""
+import math
+
+import numpy as np
+import pytest
+
+import oracle
+from paper_1504_06123_gb300 import configs, inputs
+from paper_1504_06123_gb300 import lbve as L
+from tests.test_gpu_parity import BATCH, compare, rel_err, same_sweep_shape
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+F32, F64, S16 = L.LBVE_F32, L.LBVE_F64, L.LBVE_S16
+FF = L.LBVE_FORM_F
+# (population precision, history storage) -> bar
+ALL64, PLAIN, ALL32, RED = (F64, F64), (F64, F32), (F32, F32), (F32, S16)
+TOL = {ALL64: 1e-12, PLAIN: 1e-5, ALL32: 5e-5, RED: 1e-3, F64: 1e-12, F32: 1e-5, S16: 1e-3}
+
+
+@pytest.mark.parametrize("hist", [F64, F32, S16])
+@pytest.mark.parametrize("lattice,nx,ny,nz,C,B", [
+    (L.LBVE_D2Q9, 7, 115, 1, 16, 4),      # 805 nodes: several tiles + ragged tail
+    (L.LBVE_D2Q9, 1, 9, 1, 8, 1),         # uniform ring, tiny
+    (L.LBVE_D2Q9, 33, 64, 1, 5, 3),       # odd C
+    (L.LBVE_D3Q19, 3, 7, 11, 8, 3),       # 231 nodes, 3x3 tensors
+])
+def test_formf_history_apply_vs_oracle(hist, lattice, nx, ny, nz, C, B):
+    d = 2 if lattice == L.LBVE_D2Q9 else 3
+    N = nx * ny * nz
+    T = 150
+    G, tau, gc = 0.02, 40.0, 0.1
+    kseq = inputs.kappa_sequence(T, N, d, 2e-3, seed=11, shear=1e-3)
+    ref = oracle.history_run(kseq, C, B, G, tau, gc)
+    ch = L.Channel(L.make_desc(lattice, nx, ny, nz, G_inf=G, tau=tau, gamma_c=gc, C=C, B=B, precision=F64,
+                               hist_storage=hist, hist_form=FF))
+    ns = 3 if d == 2 else 6
+    kap_dev = torch.empty((d * d, N), dtype=torch.float64, device="cuda")
+    sig_dev = torch.empty((ns, N), dtype=torch.float64, device="cuda")
+    worst = 0.0
+    for t in range(T):
+        kap_dev.copy_(torch.from_numpy(kseq[t].reshape(N, d * d).T.copy()))
+        L.lbve_history_apply(ch.h, kap_dev, sig_dev)
+        if t % 7 == 0 or t == T - 1:
+            e = rel_err(sig_dev.cpu().numpy().T, ref[t])
+            worst = max(worst, e)
+            assert e <= TOL[hist], f"step {t}: sigma error {e:.3e}"
+    print(f"form F history-only {hist} lattice {lattice} C={C} B={B}: worst sigma error {worst:.2e}")
+    ch.close()
+
+
+@pytest.mark.parametrize("prec", [ALL64, PLAIN, ALL32, RED])
+@pytest.mark.parametrize("C,B", [(256, 1), (64, 4)])
+def test_formf_small_channel_startup_cessation(prec, C, B):
+    w = configs.plain_channel_small()
+    orc = oracle.Channel(oracle.D2Q9, w.nx, w.ny, tau_lb=w.tau_lb, G_inf=w.G_inf, tau=w.tau, gamma_c=w.gamma_c,
+                         g=(w.g, 0, 0), C=C, B=B)
+    ch = L.Channel(w.desc(C=C, B=B, precision=prec[0], hist_storage=prec[1], hist_form=FF))
+    t = 0
+    for cp in [1, 2, 10, 100, 700, w.steps, w.steps + 1, w.steps + 300, w.steps + w.off_steps]:
+        ch.step(cp - t)
+        orc.step(cp - t)
+        t = cp
+        compare(ch.fields(), orc.fields(), TOL[prec], f"form F {prec} C={C} B={B} step {t}")
+        if t == w.steps:
+            ch.set_force((0, 0, 0))
+            orc.set_force((0, 0, 0))
+    ch.close()
+
+
+@pytest.mark.parametrize("case", [
+    dict(lattice=L.LBVE_D2Q9, nx=1, ny=2, C=4, B=2, G_inf=0.01, tau=20.0, gamma_c=0.1, g=1e-5),
+    dict(lattice=L.LBVE_D2Q9, nx=3, ny=7, C=6, B=3, G_inf=0.02, tau=15.0, gamma_c=math.inf, g=2e-5),
+    dict(lattice=L.LBVE_D2Q9, nx=6, ny=10, C=8, B=2, G_inf=0.01, tau=30.0, gamma_c=0.2, g=1e-5,
+         trace_coupling=L.LBVE_TRACE_NONE),
+    dict(lattice=L.LBVE_D2Q9, nx=9, ny=13, C=8, B=3, G_inf=0.01, tau=30.0, gamma_c=0.2, g=1e-5, noise=1e-4),
+    dict(lattice=L.LBVE_D3Q19, nx=3, ny=6, nz=5, C=8, B=2, G_inf=0.01, tau=25.0, gamma_c=0.1, g=2e-5),
+    dict(lattice=L.LBVE_D3Q19, nx=2, ny=5, nz=4, C=4, B=3, G_inf=0.01, tau=25.0, gamma_c=0.1, g=2e-5,
+         wall_z=0, noise=1e-4),
+])
+@pytest.mark.parametrize("prec", [ALL64, PLAIN, RED])
+def test_formf_edge_cases_vs_oracle(case, prec):
+    c = dict(case)
+    noise = c.pop("noise", 0.0)
+    lattice = c.pop("lattice")
+    nz = c.pop("nz", 1)
+    wall_z = c.pop("wall_z", 1)
+    tc = c.pop("trace_coupling", L.LBVE_TRACE_FULL)
+    g = c.pop("g")
+    N = c["nx"] * c["ny"] * nz
+    rho = inputs.initial_density(N, noise, seed=7)
+    orc = oracle.Channel(lattice, c["nx"], c["ny"], nz, tau_lb=0.9, G_inf=c["G_inf"], tau=c["tau"],
+                         gamma_c=c["gamma_c"], g=(g, 0, 0), C=c["C"], B=c["B"], wall_z=bool(wall_z),
+                         trace_full=(tc == L.LBVE_TRACE_FULL), rho_init=rho)
+    ch = L.Channel(L.make_desc(lattice, c["nx"], c["ny"], nz, tau_lb=0.9, G_inf=c["G_inf"], tau=c["tau"],
+                               gamma_c=c["gamma_c"], g=(g, 0, 0), C=c["C"], B=c["B"], precision=prec[0],
+                               hist_storage=prec[1], trace_coupling=tc, wall_z=wall_z, hist_form=FF), rho)
+    for n in (1, 5, 60, 200):
+        ch.step(n)
+        orc.step(n)
+        if ch.t == 1 and noise and prec != ALL64:
+            continue     # the first step's noise-only gradients are below what FP32 velocities resolve
+        compare(ch.fields(), orc.fields(), TOL[prec], f"form F {case} t={ch.t}")
+    ch.close()
+
+
+@pytest.mark.parametrize("prec", [ALL64, PLAIN, RED])
+def test_formf_batched_channels_vs_oracle(prec):
+    C, B = 16, 4
+    descs = [L.make_desc(L.LBVE_D2Q9, c["nx"], c["ny"], tau_lb=c["tau_lb"], G_inf=c["G_inf"], tau=c["tau"],
+                         gamma_c=c["gamma_c"], g=(c["g"], 0, 0), C=C, B=B, precision=prec[0], hist_storage=prec[1],
+                         hist_form=FF)
+             for c in BATCH]
+    Ntot = sum(c["nx"] * c["ny"] for c in BATCH)
+    rho = inputs.initial_density(Ntot, 1e-5, seed=9)
+    ch = L.Channel(descs, rho)
+    orcs, off = [], 0
+    for c in BATCH:
+        n = c["nx"] * c["ny"]
+        orcs.append(oracle.Channel(oracle.D2Q9, c["nx"], c["ny"], tau_lb=c["tau_lb"], G_inf=c["G_inf"], tau=c["tau"],
+                                   gamma_c=c["gamma_c"], g=(c["g"], 0, 0), C=C, B=B, rho_init=rho[off:off + n]))
+        off += n
+    t = 0
+    for cp in (1, 37, 200, 260, 400):
+        ch.step(cp - t)
+        for o in orcs:
+            o.step(cp - t)
+        t = cp
+        f = ch.fields()
+        for i, o in enumerate(orcs):
+            compare(ch.channel_fields(i, f), o.fields(), TOL[prec], f"form F batch channel {i} t={t}")
+        if t == 200:
+            ch.set_force((0, 0, 0), channel=1)
+            orcs[1].set_force((0, 0, 0))
+    ch.close()
+
+
+@pytest.mark.parametrize("hist", [F64, F32, S16])
+def test_formf_launch_shapes_agree(hist):
+    """Every slot-chunk count gives the same sums up to the order of additions (the chunks' carries are
+    composed in the commit); the same shape on two handles gives the same bits; CTA tasks are refused."""
+    kw = dict(nx=6, ny=40, G_inf=0.01, tau=40.0, gamma_c=0.1, g=(1e-5, 0, 0), C=16, B=4, precision=F64,
+              hist_storage=hist, hist_form=FF)
+    Smax = 16 * 4 // 8
+    ref = None
+    for S in (1, 3, Smax):
+        ch = L.Channel(L.make_desc(**kw))
+        L.lbve_set_sweep_config(ch.h, S, 0)
+        ch.step(70)
+        f = ch.fields()
+        if ref is None:
+            ref = f
+        else:
+            for key in ("u", "sigma"):
+                assert rel_err(f[key], ref[key]) <= {F64: 1e-13, F32: 1e-6, S16: 1e-6}[hist], (S, key)
+        ch.close()
+    a = L.Channel(L.make_desc(**kw))
+    with pytest.raises(L.LbveError) as e:
+        L.lbve_set_sweep_config(a.h, 1, 1)
+    assert e.value.status == L.LBVE_EINVAL
+    b = L.Channel(L.make_desc(**kw))
+    same_sweep_shape(a, b)
+    a.step(3)
+    a.step(45)          # an odd step, then 16-step graphs, then the rest
+    for _ in range(48):
+        b.step(1)
+    fa, fb = a.fields(), b.fields()
+    for k in fa:
+        assert np.array_equal(fa[k], fb[k]), k
+    a.close()
+    b.close()
+
+
+@pytest.mark.parametrize("hist", [F32, S16])
+def test_formf_checkpoint_resume_bitwise(hist):
+    kw = dict(nx=6, ny=14, G_inf=0.01, tau=40.0, gamma_c=0.1, g=(1e-5, 0, 0), C=8, B=3, precision=F32,
+              hist_storage=hist, hist_form=FF)
+    a = L.Channel(L.make_desc(**kw))
+    a.step(37)
+    img = L.lbve_checkpoint_save(a.h)
+    a.step(50)
+    ref = a.fields()
+    b = L.Channel(L.make_desc(**kw))
+    same_sweep_shape(a, b)
+    L.lbve_checkpoint_restore(b.h, img)
+    b.step(50)
+    for k, v in ref.items():
+        assert np.array_equal(b.fields()[k], v), k
+    # a form-P handle of the same channel refuses the form-F image
+    p = L.Channel(L.make_desc(**dict(kw, hist_form=L.LBVE_FORM_P)))
+    with pytest.raises(L.LbveError) as e:
+        L.lbve_checkpoint_restore(p.h, img)
+    assert e.value.status == L.LBVE_EINVAL
+    for ch in (a, b, p):
+        ch.close()
+
+
+def test_formf_reads_less_memory_than_form_p():
+    """Form F stores d*d + NS values per point against form P's 2 d*d (2D: 7 against 8, 3D: 15 against 18)."""
+    kw = dict(nx=4, ny=64, C=32, B=4)
+    sizes = {}
+    for form in (L.LBVE_FORM_P, FF):
+        for hist in (F32, S16):
+            ch = L.Channel(L.make_desc(precision=F32, hist_storage=hist, hist_form=form, **kw))
+            sizes[form, hist] = L.lbve_memory_bytes(ch.h)
+            ch.close()
+    assert sizes[FF, F32] < sizes[L.LBVE_FORM_P, F32]
+    assert sizes[FF, S16] < sizes[L.LBVE_FORM_P, S16]

@@ -317,10 +317,7 @@ CommitF<R> commit_f(lbve* h) {
 
 CommitF16 commit_f16(lbve* h) {
     CommitF16 c;
-    c.Ym = (unsigned short*)h->X;
-    c.Ye = (unsigned char*)h->Qe;
-    c.Dmm = (unsigned short*)h->K;
-    c.De = (unsigned char*)h->Ke;
+    c.blk = (unsigned char*)h->X;
     c.part = (float*)h->part;
     c.B = h->d.hist_B;
     c.C = h->d.hist_C;
@@ -806,6 +803,12 @@ int create_impl(const lbve_channel_desc* descs, int32_t n, const double* rho_ini
     // planes per point: form P keeps X = E - 1 and kappa (d*d each); form F keeps F - 1 (d*d) and
     // kappa + kappa^T (NS)
     const int kplanes = h->hist_formf ? h->NS : h->D * h->D;
+    // history bytes: X (d*d planes) and K (kplanes); the 16-bit form F keeps both, with their exponents, in
+    // one array of 2048-byte blocks, 16 (2D) or 32 (3D) bytes per point
+    const bool f16 = h->hist_s16 && h->hist_formf;
+    const size_t x_bytes = f16 ? (size_t)h->L * h->Npad * (h->D == 2 ? 16 : 32)
+                               : hist_elem * (size_t)h->L * h->D * h->D * h->Npad;
+    const size_t k_bytes = f16 ? 0 : hist_elem * (size_t)h->L * kplanes * h->Npad;
     h->chan_host.resize(n);
     {
         int off = 0;
@@ -827,8 +830,8 @@ int create_impl(const lbve_channel_desc* descs, int32_t n, const double* rho_ini
         (rc = alloc(h, &h->u_raw, fe * h->D * Np)) || (rc = alloc(h, &h->u, fe * h->D * Np)) ||
         (rc = alloc(h, &h->rho, fe * Np)) || (rc = alloc(h, &h->sigma, fe * h->NS * Np)) ||
         (rc = alloc(h, &h->kappa, fe * DD * Np)) || (rc = alloc(h, &h->tr_prev, fe * Np)) ||
-        (h->L > 0 && (rc = alloc(h, &h->X, hist_elem * (size_t)h->L * DD * Np))) ||
-        (h->L > 0 && (rc = alloc(h, &h->K, hist_elem * (size_t)h->L * kplanes * Np))) ||
+        (h->L > 0 && (rc = alloc(h, &h->X, x_bytes))) ||
+        (h->L > 0 && k_bytes > 0 && (rc = alloc(h, &h->K, k_bytes))) ||
         (rc = alloc(h, (void**)&h->t_dev, sizeof(long long))) || (rc = alloc(h, (void**)&h->red, 2 * sizeof(double))) ||
         (rc = alloc(h, (void**)&h->flag, sizeof(int))) ||
         (rc = alloc(h, (void**)&h->chan_dev, sizeof(Chan) * n)))
@@ -847,9 +850,9 @@ int create_impl(const lbve_channel_desc* descs, int32_t n, const double* rho_ini
         cudaError_t e = cudaMemcpy(h->chan_of, co.data(), sizeof(int) * Np, cudaMemcpyHostToDevice);
         if (e != cudaSuccess) return fail(cuda_fail(e, "cudaMemcpy"));
     }
-    if (h->hist_s16 && h->L > 0 &&
+    if (h->hist_s16 && !h->hist_formf && h->L > 0 &&
         ((rc = alloc(h, &h->Qe, (size_t)h->L * Np)) || (rc = alloc(h, &h->Ke, (size_t)h->L * Np)) ||
-         (!h->hist_formf && (rc = alloc(h, &h->Rm, sizeof(float) * DD * Np)))))
+         (rc = alloc(h, &h->Rm, sizeof(float) * DD * Np))))
         return fail(rc);
     if (h->model == LBVE_MODEL_WM &&
         ((rc = alloc(h, &h->gam_node, sizeof(double) * Np)) ||
@@ -860,8 +863,8 @@ int create_impl(const lbve_channel_desc* descs, int32_t n, const double* rho_ini
     void* zero_bufs[] = {h->pops[0], h->pops[1], h->u_raw, h->u, h->sigma, h->kappa, h->tr_prev, h->X, h->K, h->flag,
                          h->Qe, h->Ke, h->Rm, h->gam_node, h->gam_pt};
     size_t zero_sizes[] = {h->pesz * h->Q * Np, h->pesz * h->Q * Np, fe * h->D * Np, fe * h->D * Np,
-                           fe * h->NS * Np, fe * DD * Np, fe * Np, hist_elem * (size_t)h->L * DD * Np,
-                           hist_elem * (size_t)h->L * kplanes * Np, sizeof(int), (size_t)h->L * Np, (size_t)h->L * Np,
+                           fe * h->NS * Np, fe * DD * Np, fe * Np, x_bytes, k_bytes, sizeof(int), (size_t)h->L * Np,
+                           (size_t)h->L * Np,
                            sizeof(float) * DD * Np, sizeof(double) * Np, sizeof(double) * (size_t)h->L * Np};
     for (int i = 0; i < 15; ++i) {
         if (!zero_bufs[i]) continue;
@@ -1411,12 +1414,14 @@ std::vector<StateBuf> state_buffers(lbve* h) {
     const size_t fe = h->tangent ? sizeof(Dual) : sizeof(double);
     const size_t hist_elem = h->tangent ? sizeof(Dual) : (h->hist_s16 ? 2 : h->hesz);
     const int kplanes = h->hist_formf ? h->NS : DD;
+    const bool f16 = h->hist_s16 && h->hist_formf;
     std::vector<StateBuf> v = {
         {h->pops[h->cur], h->pesz * h->Q * Np}, {h->u, fe * h->D * Np}, {h->rho, fe * Np},
         {h->sigma, fe * h->NS * Np}, {h->kappa, fe * DD * Np}, {h->tr_prev, fe * Np},
-        {h->X, hist_elem * (size_t)h->L * DD * Np}, {h->K, hist_elem * (size_t)h->L * kplanes * Np},
+        {h->X, f16 ? (size_t)h->L * Np * (h->D == 2 ? 16 : 32) : hist_elem * (size_t)h->L * DD * Np},
+        {h->K, f16 ? 0 : hist_elem * (size_t)h->L * kplanes * Np},
         {h->t_dev, sizeof(long long)}};
-    if (h->hist_s16) {
+    if (h->hist_s16 && !h->hist_formf) {
         v.push_back({h->Qe, (size_t)h->L * Np});
         v.push_back({h->Ke, (size_t)h->L * Np});
         if (h->Rm) v.push_back({h->Rm, sizeof(float) * DD * Np});

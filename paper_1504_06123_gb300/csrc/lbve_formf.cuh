@@ -18,8 +18,9 @@
 //
 // Commit (per node, fused into the collide kernel): sigma_struc(t) from the chunk records plus the point
 // created now (age 0, E = 1, weight 1/2), then the block merges of the quasi-logarithmic grid (older point's
-// time, factor product F_newer F_older, averaged Dm) and the new point (its factor exp(kappa(t)), formed in
-// double and rounded once to the storage).
+// time, factor product F_newer F_older, averaged Dm) and the new point (its factor exp(kappa(t))), all in the
+// history's arithmetic (float for the FP32 and 16-bit storages, double for FP64), each chunk's stress term
+// added in double.
 //
 // Storage: float or double planes, or 16-bit block-scaled (d*d int16 mantissas of Y and NS of Dm, one shared
 // power-of-two exponent byte per vector, as in the reduced-precision history of lbve_kernels.cuh).
@@ -36,11 +37,12 @@ template <int D> __host__ __device__ __forceinline__ constexpr int symi(int r, i
 }
 
 // The modulus of Eq. (nlmax) (without G_inf) times the trapezoidal weight, per point.
-// float: exp(-age (1/tau + gammadot/gamma_c)) = 2^(age (c1 + gammadot c2)) with c1 = -log2(e)/tau and
-// c2 = -log2(e)/gamma_c folded per node, on the hardware exp2 and sqrt approximations (relative error about
-// 2^-22); double: the library exp and sqrt.
+// float: w exp(-age (1/tau + gammadot/gamma_c)) = 2^(age (c1 + gammadot c2) + log2 w) with c1 = -log2(e)/tau
+// and c2 = -log2(e)/gamma_c folded per node and log2 w per rank (the argument wx), on the hardware exp2 and
+// sqrt approximations (relative error about 2^-22); double: wx = w and the library exp and sqrt.
 template <typename R> struct PtMath;
 template <> struct PtMath<float> {
+    static constexpr bool kLog2W = true;
     __device__ static __forceinline__ void consts(double inv_tau, double inv_gc, float& c1, float& c2) {
         c1 = (float)(-1.4426950408889634 * inv_tau);
         c2 = (float)(-1.4426950408889634 * inv_gc);
@@ -50,13 +52,14 @@ template <> struct PtMath<float> {
         asm("sqrt.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
         return y;
     }
-    __device__ static __forceinline__ float gw(float w, float age, float c1, float c2, float gd) {
+    __device__ static __forceinline__ float gw(float lw, float age, float c1, float c2, float gd) {
         float y;
-        asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(age * fmaf(gd, c2, c1)));
-        return w * y;
+        asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(fmaf(age, fmaf(gd, c2, c1), lw)));
+        return y;
     }
 };
 template <> struct PtMath<double> {
+    static constexpr bool kLog2W = false;
     __device__ static __forceinline__ void consts(double inv_tau, double inv_gc, double& c1, double& c2) {
         c1 = inv_tau;
         c2 = inv_gc;
@@ -119,30 +122,28 @@ __device__ __forceinline__ void dev_product(R* X, const R* Y) {
 }
 
 // ------------------------------------------------------------------------------------------------
-// Rank tables of the sweep (shared memory): the points in memory after step t-1 listed newest first --
-// the finest block from its newest point back, then each coarser block -- with their slot, age, trapezoidal
-// weight at step t and merge partner (the newer half whose Dm is averaged into the older one; -1 if none).
+// Rank table of the sweep (shared memory, one 16-byte entry per rank): the points in memory after step
+// t-1 listed newest first -- the finest block from its newest point back, then each coarser block -- with
+// their slot, merge partner (the newer half whose Dm is averaged into the older one; -1 if none), age and
+// trapezoidal weight at step t.  LOG2W: the weight is stored as log2(w) (-inf for w = 0), for the float
+// kernels that form w G as one exp2.
 // ------------------------------------------------------------------------------------------------
 __host__ __device__ inline size_t sweep_f_smem_bytes(int L) {
     return ((size_t)L * 16 + sizeof(BlockStep) * LBVE_MAXB + sizeof(int) * (LBVE_MAXB + 1) + 15) / 16 * 16;
 }
 
+struct RankEnt { int slot, partner; float age, w; };
+
 struct RankTab {
-    int* slot;
-    float* age;
-    float* w;
-    int* partner;
+    const RankEnt* e;
     int n;            // points in memory
 };
 
+template <bool LOG2W>
 __device__ __forceinline__ RankTab rank_tables(unsigned char* smem, int B, int C, long long t) {
     const int L = B * C;
-    RankTab rt;
-    rt.slot = reinterpret_cast<int*>(smem);
-    rt.age = reinterpret_cast<float*>(rt.slot + L);
-    rt.w = rt.age + L;
-    rt.partner = reinterpret_cast<int*>(rt.w + L);
-    BlockStep* s_bs = reinterpret_cast<BlockStep*>(rt.partner + L);
+    RankEnt* ent = reinterpret_cast<RankEnt*>(smem);
+    BlockStep* s_bs = reinterpret_cast<BlockStep*>(ent + L);
     int* s_off = reinterpret_cast<int*>(s_bs + LBVE_MAXB);   // first rank of each block, then the total
     if (threadIdx.x == 0) {
         sched_step(B, C, t, s_bs);
@@ -161,13 +162,16 @@ __device__ __forceinline__ RankTab rank_tables(unsigned char* smem, int B, int C
         if (k >= s_bs[bb].count_prev) continue;       // empty ring slot: not a point
         int age, part;
         const float w = sched_slot_role(s_bs, C, bb, j, &age, &part);
-        const int r = s_off[bb] + k;
-        rt.slot[r] = l;
-        rt.age[r] = (float)age;
-        rt.w[r] = w;
-        rt.partner[r] = part;
+        RankEnt e;
+        e.slot = l;
+        e.partner = part;
+        e.age = (float)age;
+        e.w = LOG2W ? (w > 0.0f ? log2f(w) : -INFINITY) : w;
+        ent[s_off[bb] + k] = e;
     }
     __syncthreads();
+    RankTab rt;
+    rt.e = ent;
     rt.n = s_off[LBVE_MAXB];
     return rt;
 }
@@ -189,7 +193,7 @@ __global__ void __launch_bounds__(256, 2) k_sweep_f(CommitF<R> a, const long lon
     using V = Vec<R, VN>;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     const long long t = *t_dev;
-    const RankTab rt = rank_tables(smem_raw, a.B, a.C, t);
+    const RankTab rt = rank_tables<PtMath<R>::kLog2W>(smem_raw, a.B, a.C, t);
     const long long Np = g.Npad;
     const int lane = threadIdx.x & 31;
     const int gwarp = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
@@ -219,7 +223,7 @@ __global__ void __launch_bounds__(256, 2) k_sweep_f(CommitF<R> a, const long lon
         const int r0 = min(rt.n, chunk * chunk_len), r1 = min(rt.n, r0 + chunk_len);
         struct Pt { V y[DD], d[NS]; };
         auto load = [&](int r, Pt& p) {
-            const long long l = rt.slot[r];
+            const long long l = rt.e[r].slot;
 #pragma unroll
             for (int c = 0; c < DD; ++c) p.y[c] = *reinterpret_cast<const V*>(a.Y + (l * DD + c) * Np + n0);
 #pragma unroll
@@ -230,6 +234,7 @@ __global__ void __launch_bounds__(256, 2) k_sweep_f(CommitF<R> a, const long lon
         for (int r = r0; r < r1; ++r) {
             const Pt cur = nxt;
             if (r + 1 < r1) load(r + 1, nxt);
+            const RankEnt e = rt.e[r];
             R Y[VN][DD], Dp[VN][NS];
 #pragma unroll
             for (int j = 0; j < VN; ++j) {
@@ -238,16 +243,15 @@ __global__ void __launch_bounds__(256, 2) k_sweep_f(CommitF<R> a, const long lon
 #pragma unroll
                 for (int c = 0; c < NS; ++c) Dp[j][c] = cur.d[c].v[j];
             }
-            const int part = rt.partner[r];
-            if (part >= 0) {   // older half of a merge: its rate of strain averaged with the newer half's
+            if (e.partner >= 0) {   // older half of a merge: its rate of strain averaged with the newer half's
 #pragma unroll
                 for (int c = 0; c < NS; ++c) {
-                    const V v = *reinterpret_cast<const V*>(a.Dm + ((long long)part * NS + c) * Np + n0);
+                    const V v = *reinterpret_cast<const V*>(a.Dm + ((long long)e.partner * NS + c) * Np + n0);
 #pragma unroll
                     for (int j = 0; j < VN; ++j) Dp[j][c] = R(0.5) * (Dp[j][c] + v.v[j]);
                 }
             }
-            const R age = (R)rt.age[r], w = (R)rt.w[r];
+            const R age = (R)e.age, w = (R)e.w;
 #pragma unroll
             for (int j = 0; j < VN; ++j) {
                 dev_product<D>(X[j], Y[j]);
@@ -272,47 +276,49 @@ __global__ void __launch_bounds__(256, 2) k_sweep_f(CommitF<R> a, const long lon
     }
 }
 
-// sigma_struc of a node from the chunk records, in double: sum_j C_j M_j C_j^T with C_1 = 1 and
-// C_{j+1} = C_j T_j, plus the point created now (E = 1, weight 1/2, G = G_inf: (1/2) Dm(t)).
-template <int D, typename R>
+// sigma_struc of a node from the chunk records: sum_j C_j M_j C_j^T with C_1 = 1 and C_{j+1} = C_j T_j (formed
+// in the history's arithmetic A, each chunk's term added in double), plus the point created now (E = 1,
+// weight 1/2, G = G_inf: (1/2) Dm(t)).
+template <int D, typename A, typename R>
 __device__ __forceinline__ void formf_sigma(const R* part, int S, long long Np, int n, const double* dnew, double G_inf,
                                             double* sig) {
     constexpr int DD = D * D;
     constexpr int NS = D == 2 ? 3 : 6;
-    double Z[DD], acc[NS];
+    A Z[DD];
+    double acc[NS];
 #pragma unroll
-    for (int i = 0; i < DD; ++i) Z[i] = 0.0;
+    for (int i = 0; i < DD; ++i) Z[i] = A(0);
 #pragma unroll
     for (int i = 0; i < NS; ++i) acc[i] = 0.0;
     for (int j = 0; j < S; ++j) {
         const R* pj = part + (long long)j * (NS + DD) * Np + n;
-        double M[DD], T[DD];
+        A M[DD], T[DD];
 #pragma unroll
         for (int i = 0; i < NS; ++i) {
-            const double v = (double)pj[i * Np];
+            const A v = (A)pj[i * Np];
             M[symr<D>(i) * D + symc<D>(i)] = v;
             M[symc<D>(i) * D + symr<D>(i)] = v;
         }
 #pragma unroll
-        for (int i = 0; i < DD; ++i) T[i] = (double)pj[(NS + i) * Np];
+        for (int i = 0; i < DD; ++i) T[i] = (A)pj[(NS + i) * Np];
         // C M C^T with C = 1 + Z: (M + Z M) (1 + Z)^T, upper triangle
-        double F[DD];
+        A F[DD];
 #pragma unroll
         for (int r = 0; r < D; ++r)
 #pragma unroll
             for (int c = 0; c < D; ++c) {
-                double s = M[r * D + c];
+                A s = M[r * D + c];
 #pragma unroll
-                for (int k = 0; k < D; ++k) s += Z[r * D + k] * M[k * D + c];
+                for (int k = 0; k < D; ++k) s = ::fma(Z[r * D + k], M[k * D + c], s);
                 F[r * D + c] = s;
             }
 #pragma unroll
         for (int i = 0; i < NS; ++i) {
             const int r = symr<D>(i), c = symc<D>(i);
-            double s = F[r * D + c];
+            A s = F[r * D + c];
 #pragma unroll
-            for (int k = 0; k < D; ++k) s += F[r * D + k] * Z[c * D + k];
-            acc[i] += s;
+            for (int k = 0; k < D; ++k) s = ::fma(F[r * D + k], Z[c * D + k], s);
+            acc[i] += (double)s;
         }
         dev_product<D>(Z, T);
     }
@@ -320,9 +326,15 @@ __device__ __forceinline__ void formf_sigma(const R* part, int S, long long Np, 
     for (int i = 0; i < NS; ++i) sig[i] = G_inf * (acc[i] + 0.5 * dnew[i]);
 }
 
-// exp(kappa) - 1 of the new point's factor, in double (Taylor to 8th order: |kappa| <= 1e-2 leaves < 1e-20).
-template <int D>
-__device__ __forceinline__ void factor_dev(const double* ktd, double* Y) { expm1_mat<D, double>(ktd, Y); }
+// exp(kappa) - 1 of the new point's factor in the arithmetic A (Taylor to 4th order in float, 8th in double:
+// |kappa| <= 1e-2 leaves below 1e-12 and 1e-20).
+template <int D, typename A>
+__device__ __forceinline__ void factor_dev(const double* ktd, A* Y) {
+    A k[D * D];
+#pragma unroll
+    for (int i = 0; i < D * D; ++i) k[i] = (A)ktd[i];
+    expm1_mat<D, A>(k, Y);
+}
 
 template <int D>
 __device__ __forceinline__ void rate_of_strain(const double* ktd, double* dp) {
@@ -341,12 +353,13 @@ __device__ __forceinline__ void hist_commit_any(const CommitF<R>& a, const Block
     constexpr int DD = D * D;
     constexpr int NS = D == 2 ? 3 : 6;
     // the new point's stored values (rounded to the storage), used for its own contribution as for any point
-    double Yn[DD], dn[NS];
-    factor_dev<D>(ktd, Yn);
+    R Yn[DD];
+    double dn[NS];
+    factor_dev<D, R>(ktd, Yn);
     rate_of_strain<D>(ktd, dn);
 #pragma unroll
     for (int i = 0; i < NS; ++i) dn[i] = (double)(R)dn[i];
-    formf_sigma<D, R>(a.part, a.S, Np, n, dn, p.G_inf, sig);
+    formf_sigma<D, R, R>(a.part, a.S, Np, n, dn, p.G_inf, sig);
     // block merges, coarsest first (every ring slot is read before it is overwritten): the older point's
     // time, the factor F_newer F_older, the average of the two rates
     for (int bb = 1; bb < a.B; ++bb) {
@@ -356,66 +369,84 @@ __device__ __forceinline__ void hist_commit_any(const CommitF<R>& a, const Block
         int o2 = b.head_prev - (a.C - 2); if (o2 < 0) o2 += a.C;
         const long long s1 = (long long)bb * a.C + o1, s2 = (long long)bb * a.C + o2;
         const long long dst = (long long)(bb - 1) * a.C + s_bs[bb - 1].head_new;
-        double Y1[DD], Y2[DD];
+        R Y1[DD], Y2[DD];
 #pragma unroll
         for (int c = 0; c < DD; ++c) {
-            Y1[c] = (double)a.Y[(s1 * DD + c) * Np + n];
-            Y2[c] = (double)a.Y[(s2 * DD + c) * Np + n];
+            Y1[c] = a.Y[(s1 * DD + c) * Np + n];
+            Y2[c] = a.Y[(s2 * DD + c) * Np + n];
         }
         dev_product<D>(Y2, Y1);   // (1 + Y2)(1 + Y1) - 1
-        double d1[NS], d2[NS];
 #pragma unroll
-        for (int c = 0; c < NS; ++c) {
-            d1[c] = (double)a.Dm[(s1 * NS + c) * Np + n];
-            d2[c] = (double)a.Dm[(s2 * NS + c) * Np + n];
-        }
+        for (int c = 0; c < NS; ++c)
+            a.Dm[(dst * NS + c) * Np + n] = R(0.5) * (a.Dm[(s1 * NS + c) * Np + n] + a.Dm[(s2 * NS + c) * Np + n]);
 #pragma unroll
-        for (int c = 0; c < DD; ++c) a.Y[(dst * DD + c) * Np + n] = (R)Y2[c];
-#pragma unroll
-        for (int c = 0; c < NS; ++c) a.Dm[(dst * NS + c) * Np + n] = (R)(0.5 * (d1[c] + d2[c]));
+        for (int c = 0; c < DD; ++c) a.Y[(dst * DD + c) * Np + n] = Y2[c];
     }
     const long long dst = (long long)(a.B - 1) * a.C + s_bs[a.B - 1].head_new;
 #pragma unroll
-    for (int c = 0; c < DD; ++c) a.Y[(dst * DD + c) * Np + n] = (R)Yn[c];
+    for (int c = 0; c < DD; ++c) a.Y[(dst * DD + c) * Np + n] = Yn[c];
 #pragma unroll
     for (int c = 0; c < NS; ++c) a.Dm[(dst * NS + c) * Np + n] = (R)dn[c];
 }
 
 // ------------------------------------------------------------------------------------------------
 // Form F, 16-bit block-scaled storage (the reduced-precision history): Y and Dm each as int16 mantissas
-// sharing one power-of-two exponent byte (s16_encode / s16_decode of lbve_kernels.cuh); FP32 arithmetic.
+// sharing one power-of-two exponent byte per vector (s16_encode / s16_decode of lbve_kernels.cuh); FP32
+// arithmetic.
+//
+// Layout: node tiles of TN = 32 VN nodes (VN = 4 in 2D, 2 in 3D: one sweep lane's nodes); each (tile, slot)
+// is one 2048-byte block, blocks ordered [tile][slot].  Inside a block, the 64 bytes of lane q (its VN
+// nodes' 7 / 15 mantissas and their exponent bytes, as 32 half-words h) lie in four 16-byte pieces, piece k
+// at byte k*512 + q*16: a warp reads one slot of its tile with four fully coalesced 16-byte loads per lane at
+// fixed offsets, and a whole slot of a tile is one contiguous block.
+//   2D: h = 4c + j  Y comp c (0..3) of node j;  h = 16 + 4c + j  Dm comp c (0..2);  h 28-29: the 4 Y exponent
+//       bytes (node j in byte j);  h 30-31: the 4 Dm exponent bytes.
+//   3D: h = 2c + j  Y comp c (0..8);  h = 18 + 2c + j  Dm comp c (0..5);  h 30: Y exponent bytes of the two
+//       nodes;  h 31: Dm exponent bytes.
 // ------------------------------------------------------------------------------------------------
+template <int D> struct F16Layout {
+    static constexpr int VN = D == 2 ? 4 : 2;       // nodes per lane
+    static constexpr int TN = 32 * VN;              // nodes per tile
+    static constexpr int DD = D * D, NS = D == 2 ? 3 : 6;
+    static constexpr int kBlock = 2048;             // bytes per (tile, slot)
+    __host__ __device__ static constexpr int y_half(int c, int j) { return c * VN + j; }
+    __host__ __device__ static constexpr int d_half(int c, int j) { return DD * VN + c * VN + j; }
+    __host__ __device__ static constexpr int ye_byte(int j) { return D == 2 ? 56 + j : 60 + j; }     // byte inside the lane's 64
+    __host__ __device__ static constexpr int de_byte(int j) { return D == 2 ? 60 + j : 62 + j; }
+    // byte offset of byte b (0..63) of lane q inside a block
+    __host__ __device__ static constexpr int lane_byte(int q, int b) { return (b >> 4) * 512 + q * 16 + (b & 15); }
+};
+
 struct CommitF16 {
-    unsigned short* __restrict__ Ym;  // [L][DD][Npad] biased mantissas of Y = F - 1
-    unsigned char* __restrict__ Ye;   // [L][Npad] biased exponents
-    unsigned short* __restrict__ Dmm; // [L][NS][Npad] biased mantissas of Dm
-    unsigned char* __restrict__ De;   // [L][Npad]
+    unsigned char* __restrict__ blk;  // [tiles][L][2048] history blocks
     float* __restrict__ part;         // [S][NS + DD][Npad]
     int B, C, S;
 };
 
 template <int D, int VN>
 __global__ void __launch_bounds__(256, 2) k_sweep_f16(CommitF16 a, const long long* __restrict__ t_dev, Geom g) {
+    using Lay = F16Layout<D>;
     constexpr int DD = D * D;
     constexpr int NS = D == 2 ? 3 : 6;
-    static_assert(VN == 2 || VN == 4, "packed decode handles 2 or 4 nodes per lane");
-    using VW = Vec<unsigned, VN / 2>;
+    static_assert(VN == Lay::VN, "one lane's nodes are one lane's bytes of a block");
     using VF = Vec<float, VN>;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     const long long t = *t_dev;
-    const RankTab rt = rank_tables(smem_raw, a.B, a.C, t);
+    const RankTab rt = rank_tables<true>(smem_raw, a.B, a.C, t);
     const long long Np = g.Npad;
+    const int L = a.B * a.C;
     const int lane = threadIdx.x & 31;
     const int gwarp = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
     const int nwarps = gridDim.x * (blockDim.x >> 5);
-    const int tiles = (int)(Np / (32 * VN));
+    const int tiles = (int)(Np / Lay::TN);
     const int tasks = tiles * a.S;
     const int chunk_len = (rt.n + a.S - 1) / a.S;
 
     for (int task = gwarp; task < tasks; task += nwarps) {
         const int tile = task % tiles;
         const int chunk = task / tiles;
-        const long long n0 = (long long)tile * 32 * VN + lane * VN;
+        const long long n0 = (long long)tile * Lay::TN + lane * VN;
+        const unsigned char* tbase = a.blk + (long long)tile * L * Lay::kBlock + lane * 16;
         float c1[VN], c2[VN];
 #pragma unroll
         for (int j = 0; j < VN; ++j) {
@@ -431,66 +462,64 @@ __global__ void __launch_bounds__(256, 2) k_sweep_f16(CommitF16 a, const long lo
             for (int i = 0; i < NS; ++i) acc[j][i] = 0.0f;
         }
         const int r0 = min(rt.n, chunk * chunk_len), r1 = min(rt.n, r0 + chunk_len);
-        struct Packed { unsigned ye, de; VW y[DD], d[NS]; };
-        auto load_exp = [&](const unsigned char* base, long long l) -> unsigned {
-            return VN == 4 ? *reinterpret_cast<const unsigned*>(base + l * Np + n0)
-                           : *reinterpret_cast<const unsigned short*>(base + l * Np + n0);
-        };
-        auto load = [&](int r, Packed& p) {
-            const long long l = rt.slot[r];
-            p.ye = load_exp(a.Ye, l);
-            p.de = load_exp(a.De, l);
+        // the lane's 64 bytes of one slot as 16 words (word q holds half-words 2q, 2q + 1)
+        auto load = [&](int r, unsigned (&wd)[16]) {
+            const uint4* p = reinterpret_cast<const uint4*>(tbase + (long long)rt.e[r].slot * Lay::kBlock);
 #pragma unroll
-            for (int c = 0; c < DD; ++c) p.y[c] = *reinterpret_cast<const VW*>(a.Ym + (l * DD + c) * Np + n0);
-#pragma unroll
-            for (int c = 0; c < NS; ++c) p.d[c] = *reinterpret_cast<const VW*>(a.Dmm + (l * NS + c) * Np + n0);
+            for (int k = 0; k < 4; ++k) {
+                const uint4 v = p[k * 32];          // + k * 512 bytes
+                wd[4 * k] = v.x; wd[4 * k + 1] = v.y; wd[4 * k + 2] = v.z; wd[4 * k + 3] = v.w;
+            }
         };
-        Packed nxt;
-        if (r0 < r1) load(r0, nxt);
-        for (int r = r0; r < r1; ++r) {
-            const Packed cur = nxt;
-            if (r + 1 < r1) load(r + 1, nxt);
+        auto half_of = [&](const unsigned (&wd)[16], int h, const S16Scale& sc) -> float {
+            return (h & 1) ? s16_hi(wd[h >> 1], sc) : s16_lo(wd[h >> 1], sc);
+        };
+        auto process = [&](int r, const unsigned (&wd)[16]) {
+            const RankEnt e = rt.e[r];
+            const unsigned ye = D == 2 ? wd[14] : (wd[15] & 0xFFFFu);
+            const unsigned de = D == 2 ? wd[15] : (wd[15] >> 16);
             float Y[VN][DD], Dp[VN][NS];
-            {
-                S16Scale sy[VN], sd[VN];
 #pragma unroll
-                for (int j = 0; j < VN; ++j) { sy[j] = S16Scale(s16_exp(cur.ye, j)); sd[j] = S16Scale(s16_exp(cur.de, j)); }
+            for (int j = 0; j < VN; ++j) {
+                const S16Scale sy(s16_exp(ye, j)), sd(s16_exp(de, j));
 #pragma unroll
-                for (int p2 = 0; p2 < VN / 2; ++p2) {
+                for (int c = 0; c < DD; ++c) Y[j][c] = half_of(wd, Lay::y_half(c, j), sy);
 #pragma unroll
-                    for (int c = 0; c < DD; ++c) {
-                        Y[2 * p2][c] = s16_lo(cur.y[c].v[p2], sy[2 * p2]);
-                        Y[2 * p2 + 1][c] = s16_hi(cur.y[c].v[p2], sy[2 * p2 + 1]);
-                    }
+                for (int c = 0; c < NS; ++c) Dp[j][c] = half_of(wd, Lay::d_half(c, j), sd);
+            }
+            if (e.partner >= 0) {   // older half of a merge: rate of strain averaged with the newer half's
+                unsigned pw[16];
+                {
+                    const uint4* p = reinterpret_cast<const uint4*>(tbase + (long long)e.partner * Lay::kBlock);
 #pragma unroll
-                    for (int c = 0; c < NS; ++c) {
-                        Dp[2 * p2][c] = s16_lo(cur.d[c].v[p2], sd[2 * p2]);
-                        Dp[2 * p2 + 1][c] = s16_hi(cur.d[c].v[p2], sd[2 * p2 + 1]);
+                    for (int k = 2; k < 4; ++k) {   // the Dm mantissas and the exponents sit in pieces 2 and 3
+                        const uint4 v = p[k * 32];
+                        pw[4 * k] = v.x; pw[4 * k + 1] = v.y; pw[4 * k + 2] = v.z; pw[4 * k + 3] = v.w;
                     }
                 }
-            }
-            const int part = rt.partner[r];
-            if (part >= 0) {   // older half of a merge: rate of strain averaged with the newer half's
-                const unsigned de2 = load_exp(a.De, part);
-                S16Scale s2[VN];
+                const unsigned de2 = D == 2 ? pw[15] : (pw[15] >> 16);
 #pragma unroll
-                for (int j = 0; j < VN; ++j) s2[j] = S16Scale(s16_exp(de2, j));
+                for (int j = 0; j < VN; ++j) {
+                    const S16Scale s2(s16_exp(de2, j));
 #pragma unroll
-                for (int c = 0; c < NS; ++c) {
-                    const VW v = *reinterpret_cast<const VW*>(a.Dmm + ((long long)part * NS + c) * Np + n0);
-#pragma unroll
-                    for (int p2 = 0; p2 < VN / 2; ++p2) {
-                        Dp[2 * p2][c] = 0.5f * (Dp[2 * p2][c] + s16_lo(v.v[p2], s2[2 * p2]));
-                        Dp[2 * p2 + 1][c] = 0.5f * (Dp[2 * p2 + 1][c] + s16_hi(v.v[p2], s2[2 * p2 + 1]));
-                    }
+                    for (int c = 0; c < NS; ++c) Dp[j][c] = 0.5f * (Dp[j][c] + half_of(pw, Lay::d_half(c, j), s2));
                 }
             }
-            const float age = rt.age[r], w = rt.w[r];
 #pragma unroll
             for (int j = 0; j < VN; ++j) {
                 dev_product<D>(X[j], Y[j]);
-                sym_integrand<D>(X[j], Dp[j], age, w, c1[j], c2[j], acc[j]);
+                sym_integrand<D>(X[j], Dp[j], e.age, e.w, c1[j], c2[j], acc[j]);
             }
+        };
+        // two slots of words alternate: the next slot's loads are in flight while a slot is processed
+        unsigned wa[16], wb[16];
+        if (r0 < r1) load(r0, wa);
+        for (int r = r0; r < r1; r += 2) {
+            if (r + 1 < r1) load(r + 1, wb);
+            process(r, wa);
+            if (r + 1 >= r1) break;
+            if (r + 2 < r1) load(r + 2, wa);
+            process(r + 1, wb);
         }
         float* out = a.part + (long long)chunk * (NS + DD) * Np + n0;
 #pragma unroll
@@ -510,29 +539,41 @@ __global__ void __launch_bounds__(256, 2) k_sweep_f16(CommitF16 a, const long lo
     }
 }
 
-// Block-scaled 16-bit encode / decode of one vector of M doubles (rounded through float).
-template <int M>
-__device__ __forceinline__ void f16_store(const double* v, unsigned short* m, unsigned char* e, long long stride, long long at) {
-    float f[M];
-    unsigned short u[M];
-    unsigned char eb;
-#pragma unroll
-    for (int i = 0; i < M; ++i) f[i] = (float)v[i];
-    s16_encode<M>(f, u, &eb);
-#pragma unroll
-    for (int i = 0; i < M; ++i) m[at + i * stride] = u[i];
-    *e = eb;
+// Byte address of byte b (0..63) of node n's lane in the block of slot l.
+template <int D>
+__device__ __forceinline__ unsigned char* f16_byte(const CommitF16& a, long long n, long long l, int b) {
+    using Lay = F16Layout<D>;
+    const long long tile = n / Lay::TN;
+    const int q = (int)((n % Lay::TN) / Lay::VN);
+    return a.blk + (tile * a.B * a.C + l) * Lay::kBlock + Lay::lane_byte(q, b);
 }
 
-template <int M>
-__device__ __forceinline__ void f16_load(const unsigned short* m, unsigned char eb, long long stride, long long at, double* v) {
+// Decode / encode the M values of one vector of node n (M = d*d for Y, NS for Dm) in the block of slot l.
+template <int D, bool IS_Y>
+__device__ __forceinline__ void f16_get(const CommitF16& a, long long n, long long l, float* v) {
+    using Lay = F16Layout<D>;
+    constexpr int M = IS_Y ? Lay::DD : Lay::NS;
+    const int j = (int)(n % Lay::VN);
     unsigned short u[M];
-    float f[M];
 #pragma unroll
-    for (int i = 0; i < M; ++i) u[i] = m[at + i * stride];
-    s16_decode<M>(u, eb, f);
+    for (int c = 0; c < M; ++c)
+        u[c] = *reinterpret_cast<const unsigned short*>(f16_byte<D>(a, n, l, 2 * (IS_Y ? Lay::y_half(c, j) : Lay::d_half(c, j))));
+    const unsigned char eb = *f16_byte<D>(a, n, l, IS_Y ? Lay::ye_byte(j) : Lay::de_byte(j));
+    s16_decode<M>(u, eb, v);
+}
+
+template <int D, bool IS_Y>
+__device__ __forceinline__ void f16_put(const CommitF16& a, long long n, long long l, const float* v) {
+    using Lay = F16Layout<D>;
+    constexpr int M = IS_Y ? Lay::DD : Lay::NS;
+    const int j = (int)(n % Lay::VN);
+    unsigned short u[M];
+    unsigned char eb;
+    s16_encode<M>(v, u, &eb);
 #pragma unroll
-    for (int i = 0; i < M; ++i) v[i] = (double)f[i];
+    for (int c = 0; c < M; ++c)
+        *reinterpret_cast<unsigned short*>(f16_byte<D>(a, n, l, 2 * (IS_Y ? Lay::y_half(c, j) : Lay::d_half(c, j)))) = u[c];
+    *f16_byte<D>(a, n, l, IS_Y ? Lay::ye_byte(j) : Lay::de_byte(j)) = eb;
 }
 
 template <int D>
@@ -541,23 +582,27 @@ __device__ __forceinline__ void hist_commit_any(const CommitF16& a, const BlockS
                                                 double* sig, long long /*t*/) {
     constexpr int DD = D * D;
     constexpr int NS = D == 2 ? 3 : 6;
-    double Yn[DD], dn[NS];
-    factor_dev<D>(ktd, Yn);
-    rate_of_strain<D>(ktd, dn);
-    // the new point as stored: encoded once, its own contribution from the stored (rounded) rate
-    const long long dst_new = (long long)(a.B - 1) * a.C + s_bs[a.B - 1].head_new;
-    unsigned short um[NS];
-    unsigned char ue;
+    float Yn[DD], dn[NS];
+    factor_dev<D, float>(ktd, Yn);
     {
-        float f[NS];
+        double dd[NS];
+        rate_of_strain<D>(ktd, dd);
 #pragma unroll
-        for (int i = 0; i < NS; ++i) f[i] = (float)dn[i];
-        s16_encode<NS>(f, um, &ue);
+        for (int i = 0; i < NS; ++i) dn[i] = (float)dd[i];
+    }
+    // the new point as stored (encoded once): its own contribution from the stored, rounded rate
+    const long long dst_new = (long long)(a.B - 1) * a.C + s_bs[a.B - 1].head_new;
+    double dstored[NS];
+    {
+        unsigned short um[NS];
+        unsigned char ue;
+        float f[NS];
+        s16_encode<NS>(dn, um, &ue);
         s16_decode<NS>(um, ue, f);
 #pragma unroll
-        for (int i = 0; i < NS; ++i) dn[i] = (double)f[i];
+        for (int i = 0; i < NS; ++i) dstored[i] = (double)f[i];
     }
-    formf_sigma<D, float>(a.part, a.S, Np, n, dn, p.G_inf, sig);
+    formf_sigma<D, float, float>(a.part, a.S, Np, n, dstored, p.G_inf, sig);
     for (int bb = 1; bb < a.B; ++bb) {
         const BlockStep& b = s_bs[bb];
         if (!b.evict) continue;
@@ -565,21 +610,19 @@ __device__ __forceinline__ void hist_commit_any(const CommitF16& a, const BlockS
         int o2 = b.head_prev - (a.C - 2); if (o2 < 0) o2 += a.C;
         const long long s1 = (long long)bb * a.C + o1, s2 = (long long)bb * a.C + o2;
         const long long dst = (long long)(bb - 1) * a.C + s_bs[bb - 1].head_new;
-        double Y1[DD], Y2[DD], d1[NS], d2[NS];
-        f16_load<DD>(a.Ym, a.Ye[s1 * Np + n], Np, s1 * DD * Np + n, Y1);
-        f16_load<DD>(a.Ym, a.Ye[s2 * Np + n], Np, s2 * DD * Np + n, Y2);
-        f16_load<NS>(a.Dmm, a.De[s1 * Np + n], Np, s1 * NS * Np + n, d1);
-        f16_load<NS>(a.Dmm, a.De[s2 * Np + n], Np, s2 * NS * Np + n, d2);
+        float Y1[DD], Y2[DD], d1[NS], d2[NS];
+        f16_get<D, true>(a, n, s1, Y1);
+        f16_get<D, true>(a, n, s2, Y2);
+        f16_get<D, false>(a, n, s1, d1);
+        f16_get<D, false>(a, n, s2, d2);
         dev_product<D>(Y2, Y1);
 #pragma unroll
-        for (int c = 0; c < NS; ++c) d1[c] = 0.5 * (d1[c] + d2[c]);
-        f16_store<DD>(Y2, a.Ym, a.Ye + dst * Np + n, Np, dst * DD * Np + n);
-        f16_store<NS>(d1, a.Dmm, a.De + dst * Np + n, Np, dst * NS * Np + n);
+        for (int c = 0; c < NS; ++c) d1[c] = 0.5f * (d1[c] + d2[c]);
+        f16_put<D, true>(a, n, dst, Y2);
+        f16_put<D, false>(a, n, dst, d1);
     }
-    f16_store<DD>(Yn, a.Ym, a.Ye + dst_new * Np + n, Np, dst_new * DD * Np + n);
-#pragma unroll
-    for (int i = 0; i < NS; ++i) a.Dmm[(dst_new * NS + i) * Np + n] = um[i];
-    a.De[dst_new * Np + n] = ue;
+    f16_put<D, true>(a, n, dst_new, Yn);
+    f16_put<D, false>(a, n, dst_new, dn);
 }
 
 }  // namespace lbk

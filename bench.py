@@ -59,6 +59,9 @@ def parse():
     ap.add_argument("--form", choices=["p", "f"], default="p",
                     help="history form: p (E - 1 advanced in place; the benchmark line) or f (the paper's factor "
                          "storage: F - 1 and kappa + kappa^T written once, E re-formed by products every step)")
+    ap.add_argument("--lb-steps", type=int, default=None,
+                    help="gradient workload: LB steps per gradient (default the workload's 4000); fewer only for "
+                         "profiler captures, not a bench line")
     ap.add_argument("--no-batch", action="store_true",
                     help="skip the 64-channel batch arms of the channel line (batched chosen form, batched FP32, "
                          "one handle per channel)")
@@ -485,16 +488,22 @@ def run_gradient(args, rank, world, local_rank):
     from paper_1504_06123_gb300.autograd import run_profiles
     torch.cuda.set_device(local_rank)
     w = configs.gradient_channel()
-    desc = w.desc(precision=L.LBVE_F64, hist_storage=L.LBVE_F64)
+    if args.lb_steps:
+        w.steps = args.lb_steps
+    # the workload's precision is FP32: the plain FP32 form (FP32 history, FP64 populations, as in every FP32
+    # workload here: FP32 populations drift by their rounding over 4000 steps); --history f64: the FP64 model
+    prec = L.LBVE_F64 if args.history == "f64" else L.LBVE_F32
+    desc = w.desc(precision=L.LBVE_F64, hist_storage=prec)
+    desc64 = w.desc(precision=L.LBVE_F64, hist_storage=L.LBVE_F64)
     theta = np.array([w.G_inf, w.tau, w.gamma_c, w.g])
-    ut, st = run_profiles(desc, inputs.perturbed(theta, seed=w.seed), w.steps)
+    ut, st = run_profiles(desc64, inputs.perturbed(theta, seed=w.seed), w.steps)
     N = w.nx * w.ny
     K = args.steps if args.steps != 300 else 3
     W = args.warmup if args.warmup != 5 else 1
     stream = torch.cuda.current_stream()
     su, ss = float(np.max(np.abs(ut))) ** 2, float(np.max(np.abs(st))) ** 2
 
-    def gradient():
+    def gradient(desc=desc):
         h = L.lbve_create_adjoint(desc, None, 64)
         try:
             L.lbve_step(h, w.steps, stream)
@@ -517,12 +526,20 @@ def run_gradient(args, rank, world, local_rank):
             g = gradient()
         torch.cuda.synchronize()
         dt = time.perf_counter() - t0
-    # the tangent-linear model on the same workload (forward mode: all four derivatives in one run)
+    # the other precision's gradient (one evaluation), the tangent-linear model (FP64, forward mode: all four
+    # derivatives in one run) and the plain forward of the same precision, for the ratio backward / forward
+    other = desc64 if prec == L.LBVE_F32 else w.desc(precision=L.LBVE_F64, hist_storage=L.LBVE_F32)
     torch.cuda.synchronize()
+    t3 = time.perf_counter()
+    g_other = gradient(other)
+    torch.cuda.synchronize()
+    dt_other = time.perf_counter() - t3
     t1 = time.perf_counter()
-    run_profiles(desc, theta, w.steps, with_tangents=True)
+    run_profiles(desc64, theta, w.steps, with_tangents=True)
     torch.cuda.synchronize()
     dt_tan = time.perf_counter() - t1
+    run_profiles(desc, theta, w.steps)
+    torch.cuda.synchronize()
     t2 = time.perf_counter()
     run_profiles(desc, theta, w.steps)
     torch.cuda.synchronize()
@@ -534,12 +551,16 @@ def run_gradient(args, rank, world, local_rank):
         line = {
             "metric": "gradient evaluations/s", "value": value, "unit": "gradient evaluations/s", "n_gpus": world,
             "steps": K, "warmup": W, "ms_per_step": 1e3 * dt / K, "higher_is_better": True, "scaling": "weak",
-            "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "config": {"workload": "gradient_channel_4x128_L512_4000steps", "nodes": N,
+            "vs_baseline": None, "dtype": "f64" if prec == L.LBVE_F64 else "f32", "data": "synthetic",
+            "config": {"workload": f"gradient_channel_4x128_L512_{w.steps}steps", "nodes": N,
+                       "precision": ("FP64 history" if prec == L.LBVE_F64 else "FP32 history") +
+                                    ", FP64 populations (the adjoint itself in FP64)",
                        "history_points": desc.hist_B * desc.hist_C, "lb_steps": w.steps, "checkpoint_every": 64,
                        "loss": "mean((u_x - u*)^2)/max|u*|^2 + mean((sigma_xy - s*)^2)/max|s*|^2, final step",
                        "parallelism": f"replicas{world}", "l2": "state fits in L2 (latency-bound size)"},
             "gradient": [float(x) for x in g],
+            "other_precision": {"precision": "FP64" if prec == L.LBVE_F32 else "FP32",
+                                "gradient": [float(x) for x in g_other], "gradient_s": dt_other},
             "forward_updates_per_s": upd * K / dt,
             "plain_forward_s": dt_fwd, "gradient_s": dt / K, "gradient_over_forward": (dt / K) / dt_fwd,
             "tangent_s": dt_tan,

@@ -287,9 +287,11 @@ int lbve_checkpoint_save(lbve_t* h, void* dst, int32_t dst_is_device, void* stre
 int lbve_checkpoint_restore(lbve_t* h, const void* src, int32_t src_is_device, void* stream);
 
 /*
- * Reverse mode (adjoint).  lbve_create_adjoint makes an FP64 channel (pop_precision and hist_storage must
- * be LBVE_F64; ENOSUPPORT otherwise) that records a state image every checkpoint_every steps while it is
- * stepped from t = 0.  lbve_backward then returns grad_out = dL/d(G_inf, tau, gamma_c, g_x) for a loss L
+ * Reverse mode (adjoint).  lbve_create_adjoint makes a channel (form P history; pop_precision and
+ * hist_storage LBVE_F64 or LBVE_F32, ENOSUPPORT otherwise) that records a state image every checkpoint_every
+ * steps while it is stepped from t = 0.  The replayed states are kept in the channel's own storage; the
+ * adjoint itself, and dL/dtheta, are computed in FP64 (with FP32 storage the gradient is that of the FP32
+ * trajectory).  lbve_backward then returns grad_out = dL/d(G_inf, tau, gamma_c, g_x) for a loss L
  * of the fields of the last completed step, given dL_du ([d][N], host) and dL_dsigma ([nsig][N], host):
  * it replays every segment from its image, keeps the per-step states of that segment, and runs the
  * adjoint of the hybrid step (collision and streaming, history commit and sweep, finite differences,

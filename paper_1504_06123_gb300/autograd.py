@@ -106,17 +106,18 @@ class AdjointRun:
 class LBVEChannelAdjoint(torch.autograd.Function):
     """theta (float64 tensor [4]) -> (u_x [N], sigma_xy [N]); gradients by the adjoint with checkpoints.
 
-    The adjoint runs the FP64 hybrid step (lbve_create_adjoint accepts FP64 populations and history only),
-    so `desc` must ask for LBVE_F64 populations and history: the gradient is that of the FP64 model, and a
-    description of another precision is refused rather than silently changed.  One backward pass per
-    forward: the recorded states are freed by the first."""
+    The forward runs in the precision `desc` asks for -- populations and history LBVE_F64 or LBVE_F32, history
+    form P -- and the gradient is that of that model (of its FP32 trajectory for FP32 storage; the adjoint
+    itself runs in FP64).  Other storages (the 16-bit history, the factor form) are refused rather than
+    silently changed.  One backward pass per forward: the recorded states are freed by the first."""
 
     @staticmethod
     def forward(ctx, theta: torch.Tensor, desc: L.lbve_channel_desc, steps: int, checkpoint_every: int = 64,
                 rho_init=None):
-        if desc.pop_precision != L.LBVE_F64 or desc.hist_storage != L.LBVE_F64:
-            raise ValueError("LBVEChannelAdjoint differentiates the FP64 model: desc.pop_precision and "
-                             "desc.hist_storage must be LBVE_F64")
+        if (desc.pop_precision not in (L.LBVE_F64, L.LBVE_F32) or desc.hist_storage not in (L.LBVE_F64, L.LBVE_F32)
+                or desc.hist_form != L.LBVE_FORM_P):
+            raise ValueError("LBVEChannelAdjoint differentiates the FP64 or FP32 model with the form-P history: "
+                             "desc.pop_precision and desc.hist_storage must be LBVE_F64 or LBVE_F32")
         d = _with_params(desc, theta.detach().cpu().numpy())
         dim = 2 if d.lattice == L.LBVE_D2Q9 else 3
         N = d.nx * d.ny * d.nz

@@ -1,4 +1,6 @@
-// lbve_adjoint.cuh -- reverse-mode (adjoint) model of the hybrid step, FP64, form "P" history.
+// lbve_adjoint.cuh -- reverse-mode (adjoint) model of the hybrid step, form "P" history.  The tape (the
+// per-step states the forward recorded: populations TP, history TH) is read in its storage precision, FP64
+// or FP32; every adjoint quantity and every partial of dL/dtheta is carried in FP64.
 //
 // For a loss of the fields of the last step, the adjoint runs the steps backwards: lambda of the state
 // after step t (populations after streaming, history slots after the commit, tr sigma of step t) gives
@@ -147,10 +149,10 @@ __device__ inline void integrand_adjoint(const double* X, const double* kap, dou
     }
 }
 
-struct AdjArgs {
-    const double* n;        // [Q][Npad] populations of step t (before collision)
-    const double* X;        // [L][DD][Npad] history before the step
-    const double* K;        // [L][DD][Npad]
+template <typename TP, typename TH> struct AdjArgs {
+    const TP* n;            // [Q][Npad] populations of step t (before collision)
+    const TH* X;            // [L][DD][Npad] history before the step
+    const TH* K;            // [L][DD][Npad]
     const double* trp;      // [Npad] tr sigma(t-1)
     const double* u_raw;    // [D][Npad] raw velocity of step t (recomputed by k_moments)
     const double* lam_n1;   // [Q][Npad] lambda of the populations after step t
@@ -177,7 +179,8 @@ __device__ inline void adj_chunk(int Ls, int S, int chunk, int* l0, int* l1) {
 }
 
 // The per-CTA table of slot roles at step t (ages, weights, merge partners; same as the sweep's).
-__device__ inline void adj_table(const AdjArgs& a, float* s_age, float* s_w, int* s_part, BlockStep* s_bs) {
+template <class A>
+__device__ inline void adj_table(const A& a, float* s_age, float* s_w, int* s_part, BlockStep* s_bs) {
     const int Ls = a.B * a.C;
     if (threadIdx.x == 0) sched_step(a.B, a.C, a.t, s_bs);
     __syncthreads();
@@ -193,8 +196,8 @@ __device__ inline void adj_table(const AdjArgs& a, float* s_age, float* s_w, int
 
 // Forward recompute of the history sweep of step t on the taped history: per (node, chunk) thread the
 // partial sum of the integrand over the chunk's slots (point_update on a copy; the tape is read only).
-template <int D>
-__global__ void __launch_bounds__(128) k_adj_sig(AdjArgs a, Geom g, AdjPar p) {
+template <int D, typename TP, typename TH>
+__global__ void __launch_bounds__(128) k_adj_sig(AdjArgs<TP, TH> a, Geom g, AdjPar p) {
     constexpr int DD = D * D;
     constexpr int NS = D == 2 ? 3 : 6;
     const int Ls = a.B * a.C;
@@ -232,8 +235,8 @@ __global__ void __launch_bounds__(128) k_adj_sig(AdjArgs a, Geom g, AdjPar p) {
     for (int i = 0; i < NS; ++i) a.part_sig[((long long)chunk * NS + i) * Np + n] = acc[i];
 }
 
-template <int Q>
-__global__ void __launch_bounds__(64) k_adj_node(AdjArgs a, Geom g, AdjPar p) {
+template <int Q, typename TP, typename TH>
+__global__ void __launch_bounds__(64) k_adj_node(AdjArgs<TP, TH> a, Geom g, AdjPar p) {
     using L = Lattice<Q>;
     constexpr int D = L::D;
     constexpr int DD = D * D;
@@ -446,8 +449,8 @@ __global__ void __launch_bounds__(64) k_adj_node(AdjArgs a, Geom g, AdjPar p) {
 // Adjoint of the history sweep of step t, per (node, chunk) thread over the chunk's slots: lambda of each
 // point's X and kappa (in place; the newer half of a merge has weight 0 and is not visited, so every lamK
 // entry has a single writer), and the chunk's partial lambda(A), lambda(1/tau), lambda(1/gamma_c).
-template <int D>
-__global__ void __launch_bounds__(128) k_adj_hist(AdjArgs a, Geom g, AdjPar p) {
+template <int D, typename TP, typename TH>
+__global__ void __launch_bounds__(128) k_adj_hist(AdjArgs<TP, TH> a, Geom g, AdjPar p) {
     constexpr int DD = D * D;
     const int Ls = a.B * a.C;
     extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -523,8 +526,8 @@ __global__ void __launch_bounds__(128) k_adj_hist(AdjArgs a, Geom g, AdjPar p) {
 
 // The chunk sums of k_adj_hist (chunk order), the adjoint of A = exp(kappa(t-1)) - 1 (kappa(t-1) is the kappa
 // of the newest stored point) and the rate parts of dL/dtheta.
-template <int D>
-__global__ void __launch_bounds__(128) k_adj_fin(AdjArgs a, Geom g, AdjPar p) {
+template <int D, typename TP, typename TH>
+__global__ void __launch_bounds__(128) k_adj_fin(AdjArgs<TP, TH> a, Geom g, AdjPar p) {
     constexpr int DD = D * D;
     const int n = blockIdx.x * blockDim.x + threadIdx.x;
     if (n >= g.N) return;
@@ -587,8 +590,8 @@ __device__ inline double fd_weight(const Chan& c, int axis, int xn, int yn) {
 }
 
 // Transpose of the finite differences and adjoint of the raw moments at node n.
-template <int Q>
-__global__ void __launch_bounds__(128) k_adj_fd(const double* __restrict__ pops, const double* __restrict__ lam_kt,
+template <int Q, typename TP>
+__global__ void __launch_bounds__(128) k_adj_fd(const TP* __restrict__ pops, const double* __restrict__ lam_kt,
                                                 double* __restrict__ lam_n0, double* __restrict__ lam_theta, Geom g,
                                                 AdjPar p) {
     using L = Lattice<Q>;
@@ -628,7 +631,7 @@ __global__ void __launch_bounds__(128) k_adj_fd(const double* __restrict__ pops,
     // u_raw = (J + f/2) / (rho0 + dr)
     double dr = 0.0, J[3] = {0, 0, 0};
     for (int q = 0; q < Q; ++q) {
-        const double v = pops[q * Np + n];
+        const double v = (double)pops[q * Np + n];
         dr += v;
         J[0] += L::cx(q) * v;
         J[1] += L::cy(q) * v;

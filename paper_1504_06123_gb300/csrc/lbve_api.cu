@@ -1561,17 +1561,22 @@ struct DevBuf {
     ~DevBuf() { if (h) dev_free(h, p); }
 };
 
-template <int Q>
+// TP: population storage of the handle (and of the tape), TH: history storage (form P); the adjoint
+// arithmetic and its buffers are double throughout.
+template <int Q, typename TP, typename TH>
 int backward_impl(lbve* h, const double* dL_du, const double* dL_ds, double* grad, cudaStream_t s) {
     constexpr int D = Lattice<Q>::D;
     constexpr int DD = D * D;
+    constexpr int HK = sizeof(TH) == 8 ? 1 : 0;
     const int NS = h->NS;
     const long long Np = h->Npad;
     const int64_t T = h->t_host;
     const int K = h->rec_K;
     if (T < 1) return LBVE_ESTATE;
-    const size_t hist_b = sizeof(double) * (size_t)h->L * DD * Np;
-    const size_t pop_b = sizeof(double) * h->Q * Np;
+    const size_t hist_b = sizeof(TH) * (size_t)h->L * DD * Np;
+    const size_t lhist_b = sizeof(double) * (size_t)h->L * DD * Np;
+    const size_t pop_b = sizeof(TP) * h->Q * Np;
+    const size_t lpop_b = sizeof(double) * h->Q * Np;
     // work buffers
     DevBuf lam_n, lamX, lamK, lam_trp, lam_kt, lam_th, seeds, tape, ur, cnt, fin, psig, plt, padj;
     // slot chunks of the split history kernels: about 64k (node, chunk) threads, at most 32 chunks
@@ -1580,7 +1585,7 @@ int backward_impl(lbve* h, const double* dL_du, const double* dL_ds, double* gra
     size_t img = 0;
     lbve_checkpoint_size(h, &img);
     int rc;
-    if ((rc = lam_n.get(h, 2 * pop_b)) || (rc = lamX.get(h, hist_b)) || (rc = lamK.get(h, hist_b)) ||
+    if ((rc = lam_n.get(h, 2 * lpop_b)) || (rc = lamX.get(h, lhist_b)) || (rc = lamK.get(h, lhist_b)) ||
         (rc = lam_trp.get(h, sizeof(double) * Np)) || (rc = lam_kt.get(h, sizeof(double) * DD * Np)) ||
         (rc = lam_th.get(h, sizeof(double) * 4 * Np)) || (rc = seeds.get(h, sizeof(double) * (D + NS) * Np)) ||
         (rc = tape.get(h, step_b * (size_t)K)) || (rc = ur.get(h, sizeof(double) * D * Np)) ||
@@ -1590,9 +1595,9 @@ int backward_impl(lbve* h, const double* dL_du, const double* dL_ds, double* gra
         return rc;
     rc = lbve_checkpoint_save(h, fin.p, 1, s);   // the final state, restored at the end
     if (rc) return rc;
-    LBVE_CUDA(cudaMemsetAsync(lam_n.p, 0, 2 * pop_b, s));
-    LBVE_CUDA(cudaMemsetAsync(lamX.p, 0, hist_b, s));
-    LBVE_CUDA(cudaMemsetAsync(lamK.p, 0, hist_b, s));
+    LBVE_CUDA(cudaMemsetAsync(lam_n.p, 0, 2 * lpop_b, s));
+    LBVE_CUDA(cudaMemsetAsync(lamX.p, 0, lhist_b, s));
+    LBVE_CUDA(cudaMemsetAsync(lamK.p, 0, lhist_b, s));
     LBVE_CUDA(cudaMemsetAsync(lam_trp.p, 0, sizeof(double) * Np, s));
     LBVE_CUDA(cudaMemsetAsync(lam_th.p, 0, sizeof(double) * 4 * Np, s));
     LBVE_CUDA(cudaMemsetAsync(seeds.p, 0, sizeof(double) * (D + NS) * Np, s));
@@ -1609,9 +1614,9 @@ int backward_impl(lbve* h, const double* dL_du, const double* dL_ds, double* gra
     const int grid64 = (h->N + 63) / 64, grid128 = (h->N + 127) / 128;
     const size_t smem = sweep_smem_bytes(h->L);
     if (smem > 48 * 1024) {
-        LBVE_CUDA(cudaFuncSetAttribute(k_adj_node<Q>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-        LBVE_CUDA(cudaFuncSetAttribute(k_adj_sig<D>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-        LBVE_CUDA(cudaFuncSetAttribute(k_adj_hist<D>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+        LBVE_CUDA(cudaFuncSetAttribute(k_adj_node<Q, TP, TH>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+        LBVE_CUDA(cudaFuncSetAttribute(k_adj_sig<D, TP, TH>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+        LBVE_CUDA(cudaFuncSetAttribute(k_adj_hist<D, TP, TH>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
     }
     const int grid_chunks = (int)(((long long)S * Np + 127) / 128);
     const int rec = h->rec_K;
@@ -1629,19 +1634,19 @@ int backward_impl(lbve* h, const double* dL_du, const double* dL_ds, double* gra
             LBVE_CUDA(cudaMemcpyAsync(slot + pop_b + hist_b, h->K, hist_b, cudaMemcpyDeviceToDevice, s));
             LBVE_CUDA(cudaMemcpyAsync(slot + pop_b + 2 * hist_b, h->tr_prev, sizeof(double) * Np,
                                       cudaMemcpyDeviceToDevice, s));
-            rc = one_step<Q, double, 1, double>(h, h->cur, s);
+            rc = one_step<Q, TP, HK, TP>(h, h->cur, s);
             h->cur ^= 1;
             h->t_host += 1;
         }
         for (int64_t t = t1 - 1; t >= t0 && rc == LBVE_OK; --t) {
             const char* slot = (const char*)tape.p + step_b * (size_t)(t - t0);
-            const double* pops_t = (const double*)slot;
-            k_moments<Q, double><<<(h->N + 255) / 256, 256, 0, s>>>(pops_t, (double*)ur.p, g, (long long*)cnt.p);
+            const TP* pops_t = (const TP*)slot;
+            k_moments<Q, TP><<<(h->N + 255) / 256, 256, 0, s>>>(pops_t, (double*)ur.p, g, (long long*)cnt.p);
             LBVE_CUDA(cudaGetLastError());
-            AdjArgs a;
+            AdjArgs<TP, TH> a;
             a.n = pops_t;
-            a.X = (const double*)(slot + pop_b);
-            a.K = (const double*)(slot + pop_b + hist_b);
+            a.X = (const TH*)(slot + pop_b);
+            a.K = (const TH*)(slot + pop_b + hist_b);
             a.trp = (const double*)(slot + pop_b + 2 * hist_b);
             a.u_raw = (const double*)ur.p;
             a.lam_n1 = (const double*)lam_n.p + (size_t)cur_lam * h->Q * Np;
@@ -1660,15 +1665,15 @@ int backward_impl(lbve* h, const double* dL_du, const double* dL_ds, double* gra
             a.B = h->d.hist_B;
             a.C = h->d.hist_C;
             a.S = S;
-            k_adj_sig<D><<<grid_chunks, 128, smem, s>>>(a, g, p);
+            k_adj_sig<D, TP, TH><<<grid_chunks, 128, smem, s>>>(a, g, p);
             LBVE_CUDA(cudaGetLastError());
-            k_adj_node<Q><<<grid64, 64, smem, s>>>(a, g, p);
+            k_adj_node<Q, TP, TH><<<grid64, 64, smem, s>>>(a, g, p);
             LBVE_CUDA(cudaGetLastError());
-            k_adj_hist<D><<<grid_chunks, 128, smem, s>>>(a, g, p);
+            k_adj_hist<D, TP, TH><<<grid_chunks, 128, smem, s>>>(a, g, p);
             LBVE_CUDA(cudaGetLastError());
-            k_adj_fin<D><<<grid128, 128, 0, s>>>(a, g, p);
+            k_adj_fin<D, TP, TH><<<grid128, 128, 0, s>>>(a, g, p);
             LBVE_CUDA(cudaGetLastError());
-            k_adj_fd<Q><<<grid128, 128, 0, s>>>(pops_t, (const double*)lam_kt.p, a.lam_n0, (double*)lam_th.p, g, p);
+            k_adj_fd<Q, TP><<<grid128, 128, 0, s>>>(pops_t, (const double*)lam_kt.p, a.lam_n0, (double*)lam_th.p, g, p);
             LBVE_CUDA(cudaGetLastError());
             cur_lam ^= 1;
         }
@@ -1696,7 +1701,9 @@ extern "C" {
 int lbve_create_adjoint(const lbve_channel_desc* desc, const double* rho_init, int32_t checkpoint_every,
                         lbve_t** out) {
     if (!desc || !out || checkpoint_every < 1) return LBVE_EINVAL;
-    if (desc->pop_precision != LBVE_F64 || desc->hist_storage != LBVE_F64) return LBVE_ENOSUPPORT;
+    if ((desc->pop_precision != LBVE_F64 && desc->pop_precision != LBVE_F32) ||
+        (desc->hist_storage != LBVE_F64 && desc->hist_storage != LBVE_F32))
+        return LBVE_ENOSUPPORT;
     if (desc->model != LBVE_MODEL_NLM || desc->x_boundary != LBVE_X_PERIODIC) return LBVE_ENOSUPPORT;
     if (desc->hist_form != LBVE_FORM_P) return LBVE_ENOSUPPORT;
     int rc = create_impl(desc, 1, rho_init, out);
@@ -1709,8 +1716,21 @@ int lbve_backward(lbve_t* h, const double* dL_du, const double* dL_dsigma, doubl
     if (!h || !dL_du || !dL_dsigma || !grad_out) return LBVE_EINVAL;
     if (!h->rec_K) return LBVE_ESTATE;
     cudaStream_t s = (cudaStream_t)stream;
-    return h->Q == 9 ? backward_impl<9>(h, dL_du, dL_dsigma, grad_out, s)
-                     : backward_impl<19>(h, dL_du, dL_dsigma, grad_out, s);
+    const int combo = (h->pop_dbl ? 2 : 0) + (h->hist_dbl ? 1 : 0);
+    if (h->Q == 9) {
+        switch (combo) {
+            case 0: return backward_impl<9, float, float>(h, dL_du, dL_dsigma, grad_out, s);
+            case 1: return backward_impl<9, float, double>(h, dL_du, dL_dsigma, grad_out, s);
+            case 2: return backward_impl<9, double, float>(h, dL_du, dL_dsigma, grad_out, s);
+            default: return backward_impl<9, double, double>(h, dL_du, dL_dsigma, grad_out, s);
+        }
+    }
+    switch (combo) {
+        case 0: return backward_impl<19, float, float>(h, dL_du, dL_dsigma, grad_out, s);
+        case 1: return backward_impl<19, float, double>(h, dL_du, dL_dsigma, grad_out, s);
+        case 2: return backward_impl<19, double, float>(h, dL_du, dL_dsigma, grad_out, s);
+        default: return backward_impl<19, double, double>(h, dL_du, dL_dsigma, grad_out, s);
+    }
 }
 
 int lbve_create_tangent(const lbve_channel_desc* desc, const double* rho_init, lbve_t** out) {

@@ -50,7 +50,7 @@ def fake(monkeypatch):
 
 
 def desc(prec=L.LBVE_F64):
-    return L.make_desc(nx=2, ny=4, C=8, B=2, precision=prec, hist_storage=prec)
+    return L.make_desc(nx=2, ny=4, C=8, B=2, precision=L.LBVE_F32 if prec == L.LBVE_S16 else prec, hist_storage=prec)
 
 
 def theta(requires_grad=True):
@@ -96,7 +96,13 @@ def test_second_backward_is_refused(fake):
     assert fake.backwards == 1 and fake.destroyed == 1
 
 
-def test_other_precision_is_refused(fake):
-    with pytest.raises(ValueError, match="FP64"):
-        AG.LBVEChannelAdjoint.apply(theta(), desc(L.LBVE_F32), 10)
+def test_other_storage_is_refused(fake):
+    with pytest.raises(ValueError, match="FP64 or FP32"):
+        AG.LBVEChannelAdjoint.apply(theta(), desc(L.LBVE_S16), 10)
+    f = desc()
+    f.hist_form = L.LBVE_FORM_F
+    with pytest.raises(ValueError, match="form-P"):
+        AG.LBVEChannelAdjoint.apply(theta(), f, 10)
     assert fake.made == 0
+    AG.LBVEChannelAdjoint.apply(theta(), desc(L.LBVE_F32), 10)     # FP32 storage is differentiated
+    assert fake.made == 1

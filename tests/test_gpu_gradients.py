@@ -171,3 +171,73 @@ def test_adjoint_workload_channel():
     g_tan, _ = tangent_grad(desc, theta, w.steps, ut, st)
     print("adjoint gradient (G_inf, tau, gamma_c, g):", g_adj)
     np.testing.assert_allclose(g_adj, g_tan, rtol=1e-8)
+
+
+# ---------------------------------------------------------------------------------------------
+# The differentiation workload against the oracle's own gradient (central differences of the FP64 oracle
+# over the full 4000 steps, written by tests/golden/make_gradient_golden.py), and the FP32 adjoint
+# ---------------------------------------------------------------------------------------------
+import json  # noqa: E402
+import os  # noqa: E402
+
+GOLDEN = os.path.join(os.path.dirname(os.path.abspath(__file__)), "golden", "gradient_channel_4x128_L512.json")
+
+
+@pytest.fixture(scope="module")
+def golden():
+    with open(GOLDEN) as f:
+        return json.load(f)
+
+
+def workload_desc(gold, pops, hist):
+    w = configs.gradient_channel()
+    wl = gold["workload"]
+    assert (w.nx, w.ny, w.tau_lb, w.C, w.B, w.steps) == (wl["nx"], wl["ny"], wl["tau_lb"], wl["C"], wl["B"], wl["steps"])
+    np.testing.assert_array_equal([w.G_inf, w.tau, w.gamma_c, w.g], gold["theta"])
+    return w, w.desc(precision=pops, hist_storage=hist)
+
+
+def workload_adjoint(golden, pops, hist):
+    w, desc = workload_desc(golden, pops, hist)
+    theta = np.array(golden["theta"])
+    ut, st = np.array(golden["u_target"]), np.array(golden["sigma_xy_target"])
+    g_adj = adjoint_grad(desc, theta, w.steps, ut, st, 64)
+    g_orc = np.array(golden["gradient"])
+    return g_adj, g_orc, np.abs(g_adj - g_orc) / np.abs(g_orc)
+
+
+@pytest.mark.parametrize("pops,hist", [(L.LBVE_F64, L.LBVE_F64), (L.LBVE_F64, L.LBVE_F32)])
+def test_adjoint_workload_vs_oracle_gradient(golden, pops, hist):
+    """The 4 x 128, L = 512, 4000-step workload (checkpoints every 64 steps) with the oracle's targets, in the
+    FP64 model and in the plain FP32 form (FP32 history, FP64 populations), against the oracle's
+    central-difference gradient: <= 1e-4 per component."""
+    g_adj, g_orc, rel = workload_adjoint(golden, pops, hist)
+    print(f"adjoint (populations {pops}, history {hist}) {g_adj} oracle {g_orc} relative {rel}")
+    check(g_adj, g_orc, f"adjoint (populations {pops}, history {hist}) vs the oracle's gradient, 4000 steps")
+
+
+def test_all_fp32_adjoint_error_on_the_workload(golden):
+    """With FP32 populations as well, the model's own trajectory drifts from the FP64 one by the populations'
+    rounding (about 6e-8 of the velocity per step, accumulated over 4000 steps), and its gradient -- computed
+    exactly for that trajectory -- differs from the FP64 model's by about 1e-3 (1e-2 in the force component,
+    the smallest relative effect on the profiles).  Stated, and bounded here at 3e-2."""
+    g_adj, g_orc, rel = workload_adjoint(golden, L.LBVE_F32, L.LBVE_F32)
+    print(f"adjoint (all FP32) {g_adj} oracle {g_orc} relative {rel}")
+    assert np.all(rel <= 3e-2), rel
+
+
+def test_fp32_adjoint_against_fp64_adjoint():
+    """The FP32 model's gradient (FP32 populations and history, adjoint in FP64) against the FP64 model's, on a
+    small channel through two history grids: they differ by the FP32 trajectory's rounding only."""
+    for C, B in [(32, 2), (8, 4)]:
+        kw = dict(nx=4, ny=16, tau_lb=0.9, G_inf=0.01, tau=60.0, gamma_c=0.1, g=(2e-5, 0, 0), C=C, B=B)
+        d64 = L.make_desc(precision=L.LBVE_F64, hist_storage=L.LBVE_F64, **kw)
+        d32 = L.make_desc(precision=L.LBVE_F32, hist_storage=L.LBVE_F32, **kw)
+        steps = 300
+        theta = np.array([d64.G_inf, d64.tau, d64.gamma_c, d64.g[0]])
+        ut, st = run_profiles(d64, inputs.perturbed(theta, seed=5), steps)
+        g64 = adjoint_grad(d64, theta, steps, ut, st, 32)
+        g32 = adjoint_grad(d32, theta, steps, ut, st, 32)
+        rel = np.abs(g32 - g64) / np.abs(g64)
+        print(f"C={C} B={B}: FP32 adjoint {g32}, FP64 adjoint {g64}, relative {rel}")
+        check(g32, g64, f"FP32 vs FP64 adjoint C={C} B={B}")

@@ -113,3 +113,4 @@ def test_curves_with_a_vanishing_normaliser_are_nan_with_a_warning():
         cur = sw.curves(60)[0]
     assert np.all(np.isnan(cur["startup"]["sxy"])) and np.all(np.isnan(cur["cessation"]["sxy"]))
     assert np.allclose(cur["startup"]["u"], 1.0) and np.allclose(cur["cessation"]["n1"], 1.0)
+

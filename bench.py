@@ -276,11 +276,16 @@ PROFILE_OF = {("channel", "nlm"): "sweep_channel_1024x512_L1024.md",
               ("regime", "nlm"): "sweep_regime_10_channels_L1920.md"}
 
 
-def recorded_profile(model: str = "nlm", workload: str = "channel") -> dict:
+# the channel line's other history forms (bench.py's forms entries)
+FORM_PROFILE = {"f_s16": "sweep_f16_channel_1024x512_L1024.md", "f_f32": "sweep_f_channel_1024x512_L1024.md",
+                "p_s16": "sweep_s16_channel_1024x512_L1024.md"}
+
+
+def recorded_profile(model: str = "nlm", workload: str = "channel", name: str | None = None) -> dict:
     """Figures of the committed ncu summary of the dominant kernel (dram_bytes_per_launch, and for an
     ALU-bound kernel fp64_thread_inst_per_node), if it was taken on the current source of that kernel (the
     summary names the source files its hash covers); {} otherwise."""
-    name = PROFILE_OF.get((workload, model))
+    name = name or PROFILE_OF.get((workload, model))
     p = os.path.join(ROOT, "profiles", name) if name else ""
     if not name or not os.path.exists(p):
         return {}
@@ -714,7 +719,10 @@ def run_ours(args, rank, world, local_rank):
             msc, sweep_c, coll_c, shape_c = time_steps(L, torch, dc, rho, K, W, Kp, stream, barrier)
             msc = max_over_ranks(msc)
             bpu_c = bytes_per_update(D, dc[0].hist_storage, dc[0].hist_form, L)
+            traffic_c = (recorded_profile(name=FORM_PROFILE.get(f"{fm}_{hs}")).get("dram_bytes_per_launch")
+                         if args.workload == "channel" and not args.nx else None)
             forms[f"{fm}_{hs}"] = {"form": FORM_NAMES[fm, hs], "value": updates_rank * world / (msc / 1e3),
+                                   "traffic": traffic_c,
                                    "unit": UNIT, "ms_per_step": msc / K, "sweep_ms_per_launch": sweep_c,
                                    "collide_ms_per_launch": coll_c, "bytes_per_update": bpu_c,
                                    "roofline_frac": bpu_c * N * pts_f / Kp / (sweep_c / 1e3) / 1e9 / peak,

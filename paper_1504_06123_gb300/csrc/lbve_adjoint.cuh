@@ -33,44 +33,51 @@ struct AdjPar {
     int trace_full;
 };
 
-// Adjoint of A = exp(K) - 1 (Taylor series of the forward, order 8): lambda_K += sum_m 1/m! sum_j
-// (K^j)^T lamA (K^(m-1-j))^T.
-template <int D>
+// Adjoint of A = exp(K) - 1 as the forward forms it (expm1_mat: Horner's scheme of the Taylor polynomial of
+// order ORDER, 4 for a float history, 8 for double): P_ORDER = K/ORDER, P_m = (K + K P_{m+1})/m for
+// m = ORDER-1 .. 1, A = P_1.  Reversed: lambda_K += lambda_{P_m} (1 + P_{m+1})^T / m and
+// lambda_{P_{m+1}} = K^T lambda_{P_m} / m, then lambda_K += lambda_{P_ORDER} / ORDER.  In double.
+template <int D, int ORDER>
 __device__ inline void expm1_adjoint(const double* K, const double* lamA, double* lamK) {
     constexpr int DD = D * D;
-    constexpr int ORDER = 8;
-    double P[ORDER][DD];   // P[j] = K^j
+    double P[ORDER + 1][DD];   // P[m], m = 1 .. ORDER
 #pragma unroll
-    for (int i = 0; i < DD; ++i) P[0][i] = (i % (D + 1) == 0) ? 1.0 : 0.0;
-    for (int j = 1; j < ORDER; ++j)
+    for (int i = 0; i < DD; ++i) P[ORDER][i] = K[i] * (1.0 / ORDER);
+#pragma unroll
+    for (int m = ORDER - 1; m >= 1; --m)
+#pragma unroll
         for (int r = 0; r < D; ++r)
+#pragma unroll
             for (int c = 0; c < D; ++c) {
-                double s = 0.0;
-                for (int k = 0; k < D; ++k) s += P[j - 1][r * D + k] * K[k * D + c];
-                P[j][r * D + c] = s;
+                double s = K[r * D + c];
+#pragma unroll
+                for (int k = 0; k < D; ++k) s += K[r * D + k] * P[m + 1][k * D + c];
+                P[m][r * D + c] = s * (1.0 / m);
             }
-    double fact = 1.0;
-    for (int m = 1; m <= ORDER; ++m) {
-        fact *= m;
-        for (int j = 0; j < m; ++j) {
-            // (K^j)^T lamA (K^(m-1-j))^T
-            const double* Pa = P[j];
-            const double* Pb = P[m - 1 - j];
-            double T[DD];
-            for (int r = 0; r < D; ++r)
-                for (int c = 0; c < D; ++c) {
-                    double s = 0.0;
-                    for (int k = 0; k < D; ++k) s += Pa[k * D + r] * lamA[k * D + c];
-                    T[r * D + c] = s;
+    double lp[DD];
+#pragma unroll
+    for (int i = 0; i < DD; ++i) lp[i] = lamA[i];
+#pragma unroll
+    for (int m = 1; m <= ORDER - 1; ++m) {
+        double nx[DD];
+#pragma unroll
+        for (int r = 0; r < D; ++r)
+#pragma unroll
+            for (int c = 0; c < D; ++c) {
+                double s = lp[r * D + c], t = 0.0;
+#pragma unroll
+                for (int k = 0; k < D; ++k) {
+                    s += lp[r * D + k] * P[m + 1][c * D + k];   // lambda_{P_m} (1 + P_{m+1})^T
+                    t += K[k * D + r] * lp[k * D + c];          // K^T lambda_{P_m}
                 }
-            for (int r = 0; r < D; ++r)
-                for (int c = 0; c < D; ++c) {
-                    double s = 0.0;
-                    for (int k = 0; k < D; ++k) s += T[r * D + k] * Pb[c * D + k];
-                    lamK[r * D + c] += s / fact;
-                }
-        }
+                lamK[r * D + c] += s * (1.0 / m);
+                nx[r * D + c] = t * (1.0 / m);
+            }
+#pragma unroll
+        for (int i = 0; i < DD; ++i) lp[i] = nx[i];
     }
+#pragma unroll
+    for (int i = 0; i < DD; ++i) lamK[i] += lp[i] * (1.0 / ORDER);
 }
 
 // Packed symmetric (NS components) -> full matrix of the adjoint pairing: sum_p lam_p S_p = tr(Lt S)
@@ -87,51 +94,69 @@ __device__ inline void packed_to_pairing(const double* lam, double* Lt) {
 
 // Forward integrand (same arithmetic as point_integrand) returning S packed, g and gammadot; and its
 // adjoint for a pairing matrix Lt: lamE (dL/dE), lamk (dL/dkappa), and the scalar parts for the rates.
-template <int D>
-__device__ inline void integrand_adjoint(const double* X, const double* kap, double age, double w, double inv_tau,
-                                         double inv_gc, const double* Lt, double* lamX, double* lamk,
-                                         double* lam_inv_tau, double* lam_inv_gc) {
+// R: the arithmetic of the history (the forward's exp and sqrt of that type, FastMath); the rate parts are
+// accumulated in double.
+template <int D, typename R>
+__device__ inline void integrand_adjoint(const R* X, const R* kap, R age, R w, R inv_tau, R inv_gc, const R* Lt,
+                                         R* lamX, R* lamk, double* lam_inv_tau, double* lam_inv_gc) {
     constexpr int DD = D * D;
-    double E[DD];
-    for (int i = 0; i < DD; ++i) E[i] = X[i] + ((i % (D + 1) == 0) ? 1.0 : 0.0);
+    R E[DD];
+#pragma unroll
+    for (int i = 0; i < DD; ++i) E[i] = X[i] + ((i % (D + 1) == 0) ? R(1) : R(0));
     // M = E kap E^T
-    double EK[DD], M[DD];
+    R EK[DD], M[DD];
+#pragma unroll
     for (int r = 0; r < D; ++r)
+#pragma unroll
         for (int c = 0; c < D; ++c) {
-            double s = 0.0;
+            R s = 0;
+#pragma unroll
             for (int k = 0; k < D; ++k) s += E[r * D + k] * kap[k * D + c];
             EK[r * D + c] = s;
         }
+#pragma unroll
     for (int r = 0; r < D; ++r)
+#pragma unroll
         for (int c = 0; c < D; ++c) {
-            double s = 0.0;
+            R s = 0;
+#pragma unroll
             for (int k = 0; k < D; ++k) s += EK[r * D + k] * E[c * D + k];
             M[r * D + c] = s;
         }
-    double trD2 = 0.0, Dm[DD];
+    R trD2 = 0, Dm[DD];
+#pragma unroll
     for (int r = 0; r < D; ++r)
+#pragma unroll
         for (int c = 0; c < D; ++c) {
             Dm[r * D + c] = kap[r * D + c] + kap[c * D + r];
             trD2 += Dm[r * D + c] * Dm[r * D + c];
         }
-    const double gd = ::sqrt(0.5 * trD2);
-    const double g = ::exp(-age * (inv_tau + gd * inv_gc));
+    const R gd = FastMath<R>::sqrt_pos(R(0.5) * trD2);
+    const R g = FastMath<R>::exp_neg(age * (inv_tau + gd * inv_gc));
     // sS = tr(Lt S), S = M + M^T
-    double sS = 0.0;
+    R sS = 0;
+#pragma unroll
     for (int r = 0; r < D; ++r)
+#pragma unroll
         for (int c = 0; c < D; ++c) sS += Lt[r * D + c] * (M[c * D + r] + M[r * D + c]);
     // dS: lamE = 2 w g Lt E (kap + kap^T); lamkap = 2 w g E^T Lt E
-    double LE[DD];
+    R LE[DD];
+#pragma unroll
     for (int r = 0; r < D; ++r)
+#pragma unroll
         for (int c = 0; c < D; ++c) {
-            double s = 0.0;
+            R s = 0;
+#pragma unroll
             for (int k = 0; k < D; ++k) s += Lt[r * D + k] * E[k * D + c];
             LE[r * D + c] = s;
         }
-    const double wg2 = 2.0 * w * g;
+    const R wg2 = R(2) * w * g;
+#pragma unroll
     for (int r = 0; r < D; ++r)
+#pragma unroll
         for (int c = 0; c < D; ++c) {
-            double s = 0.0, s2 = 0.0;
+            R s = 0, s2 = 0;
+#pragma unroll
             for (int k = 0; k < D; ++k) {
                 s += LE[r * D + k] * Dm[k * D + c];          // Lt E (kap + kap^T)
                 s2 += E[k * D + r] * LE[k * D + c];          // E^T Lt E
@@ -140,11 +165,12 @@ __device__ inline void integrand_adjoint(const double* X, const double* kap, dou
             lamk[r * D + c] += wg2 * s2;
         }
     // dg: g = exp(-age (inv_tau + gd inv_gc))
-    const double dl_dg = w * sS;
-    *lam_inv_tau += dl_dg * (-age * g);
-    *lam_inv_gc += dl_dg * (-age * gd * g);
-    if (gd > 0.0) {
-        const double dl_dgd = dl_dg * (-age * inv_gc * g);
+    const R dl_dg = w * sS;
+    *lam_inv_tau += (double)(dl_dg * (-age * g));
+    *lam_inv_gc += (double)(dl_dg * (-age * gd * g));
+    if (gd > R(0)) {
+        const R dl_dgd = dl_dg * (-age * inv_gc * g);
+#pragma unroll
         for (int i = 0; i < DD; ++i) lamk[i] += dl_dgd * Dm[i] / gd;
     }
 }
@@ -157,8 +183,8 @@ template <typename TP, typename TH> struct AdjArgs {
     const double* u_raw;    // [D][Npad] raw velocity of step t (recomputed by k_moments)
     const double* lam_n1;   // [Q][Npad] lambda of the populations after step t
     double* lam_n0;         // [Q][Npad] lambda of the populations before step t (this kernel's part)
-    double* lamX;           // [L][DD][Npad] in: after step t; out: before step t
-    double* lamK;           // [L][DD][Npad]
+    TH* lamX;               // [L][DD][Npad] in: after step t; out: before step t (history type)
+    TH* lamK;               // [L][DD][Npad]
     double* lam_trp;        // [Npad] in: lambda of tr sigma(t); out: of tr sigma(t-1)
     double* lam_kt;         // [DD][Npad] out: lambda of kappa(t)
     double* lam_theta;      // [4][Npad] += per-node parts of dL/dtheta
@@ -167,7 +193,8 @@ template <typename TP, typename TH> struct AdjArgs {
     double* part_sig;       // [S][NS][Npad] k_adj_sig: partial sums of the forward integrand
     double* lt;             // [DD][Npad] pairing matrix of lambda(sigma_struc) / G_inf-scaled (k_adj_node)
     double* part_adj;       // [S][DD + 2][Npad] k_adj_hist: partial lambda(A), lambda(1/tau), lambda(1/gamma_c)
-    long long t;
+    long long t_off;        // step t = *t0 + t_off (the segment's first step lives in device memory, so that
+    const long long* t0;    // one captured graph serves every segment)
     int B, C, S;            // history grid; S slot chunks of the split kernels
 };
 
@@ -180,9 +207,12 @@ __device__ inline void adj_chunk(int Ls, int S, int chunk, int* l0, int* l1) {
 
 // The per-CTA table of slot roles at step t (ages, weights, merge partners; same as the sweep's).
 template <class A>
+__device__ inline long long adj_t(const A& a) { return *a.t0 + a.t_off; }
+
+template <class A>
 __device__ inline void adj_table(const A& a, float* s_age, float* s_w, int* s_part, BlockStep* s_bs) {
     const int Ls = a.B * a.C;
-    if (threadIdx.x == 0) sched_step(a.B, a.C, a.t, s_bs);
+    if (threadIdx.x == 0) sched_step(a.B, a.C, adj_t(a), s_bs);
     __syncthreads();
     for (int l = threadIdx.x; l < Ls; l += blockDim.x) {
         int age, part;
@@ -211,43 +241,41 @@ __global__ void __launch_bounds__(128) k_adj_sig(AdjArgs<TP, TH> a, Geom g, AdjP
     const int n = (int)(idx % g.Npad), chunk = (int)(idx / g.Npad);
     if (chunk >= a.S || n >= g.N) return;
     const long long Np = g.Npad;
+    using R = TH;   // the forward sweep's arithmetic
     const long long s_last = (long long)(a.B - 1) * a.C + s_bs[a.B - 1].head_prev;
-    double kl[DD], A[DD];
+    R kl[DD], A[DD];
     for (int c = 0; c < DD; ++c) kl[c] = a.K[(s_last * DD + c) * Np + n];
-    expm1_mat<D>(kl, A);
-    double acc[NS];
-    for (int i = 0; i < NS; ++i) acc[i] = 0.0;
+    expm1_mat<D, R>(kl, A);
+    R acc[NS];
+    for (int i = 0; i < NS; ++i) acc[i] = 0;
     int l0, l1;
     adj_chunk(Ls, a.S, chunk, &l0, &l1);
     for (int l = l0; l < l1; ++l) {
         const float w = s_w[l];
         if (w == 0.0f) continue;
-        double Xl[DD], kap[DD];
+        R Xl[DD], kap[DD];
         for (int c = 0; c < DD; ++c) {
             Xl[c] = a.X[((long long)l * DD + c) * Np + n];
             kap[c] = a.K[((long long)l * DD + c) * Np + n];
         }
         const int part = s_part[l];
         if (part >= 0)
-            for (int c = 0; c < DD; ++c) kap[c] = 0.5 * (kap[c] + a.K[((long long)part * DD + c) * Np + n]);
-        point_update<D>(Xl, A, kap, (double)s_age[l], (double)w, p.inv_tau, p.inv_gc, acc);
+            for (int c = 0; c < DD; ++c) kap[c] = R(0.5) * (kap[c] + a.K[((long long)part * DD + c) * Np + n]);
+        point_update<D, R>(Xl, A, kap, (R)s_age[l], (R)w, (R)p.inv_tau, (R)p.inv_gc, acc);
     }
-    for (int i = 0; i < NS; ++i) a.part_sig[((long long)chunk * NS + i) * Np + n] = acc[i];
+    for (int i = 0; i < NS; ++i) a.part_sig[((long long)chunk * NS + i) * Np + n] = (double)acc[i];
 }
 
 template <int Q, typename TP, typename TH>
-__global__ void __launch_bounds__(64) k_adj_node(AdjArgs<TP, TH> a, Geom g, AdjPar p) {
+__global__ void __launch_bounds__(32) k_adj_node(AdjArgs<TP, TH> a, Geom g, AdjPar p) {
     using L = Lattice<Q>;
     constexpr int D = L::D;
     constexpr int DD = D * D;
     constexpr int NS = D == 2 ? 3 : 6;
-    const int Ls = a.B * a.C;
-    extern __shared__ __align__(16) unsigned char smem_raw[];
-    float* s_age = reinterpret_cast<float*>(smem_raw);
-    float* s_w = s_age + Ls;
-    int* s_part = reinterpret_cast<int*>(s_w + Ls);
-    BlockStep* s_bs = reinterpret_cast<BlockStep*>(s_part + Ls);
-    adj_table(a, s_age, s_w, s_part, s_bs);
+    // only the block transitions of step t are needed here (the merges of the commit)
+    __shared__ BlockStep s_bs[LBVE_MAXB];
+    if (threadIdx.x == 0) sched_step(a.B, a.C, adj_t(a), s_bs);
+    __syncthreads();
     const int n = blockIdx.x * blockDim.x + threadIdx.x;
     if (n >= g.N) return;
     const long long Np = g.Npad;
@@ -266,7 +294,9 @@ __global__ void __launch_bounds__(64) k_adj_node(AdjArgs<TP, TH> a, Geom g, AdjP
     kappa_fd<D>(a.u_raw, Np, ch, n, kt);
     double acc[NS];   // the history sum of step t (k_adj_sig's chunks, in chunk order)
     for (int i = 0; i < NS; ++i) acc[i] = 0.0;
+#pragma unroll 16   // the chunks' loads in flight together (the additions keep their order)
     for (int c = 0; c < a.S; ++c)
+#pragma unroll
         for (int i = 0; i < NS; ++i) acc[i] += a.part_sig[((long long)c * NS + i) * Np + n];
     double newp[NS];   // the point created now: (kappa + kappa^T)/2 packed
     if (D == 2) {
@@ -404,9 +434,9 @@ __global__ void __launch_bounds__(64) k_adj_node(AdjArgs<TP, TH> a, Geom g, AdjP
     {
         const long long dst = (long long)(a.B - 1) * a.C + s_bs[a.B - 1].head_new;
         for (int c = 0; c < DD; ++c) {
-            lam_kt[c] += a.lamK[(dst * DD + c) * Np + n];
-            a.lamK[(dst * DD + c) * Np + n] = 0.0;
-            a.lamX[(dst * DD + c) * Np + n] = 0.0;
+            lam_kt[c] += (double)a.lamK[(dst * DD + c) * Np + n];
+            a.lamK[(dst * DD + c) * Np + n] = TH(0);
+            a.lamX[(dst * DD + c) * Np + n] = TH(0);
         }
     }
     // merges in reverse order (finest first): X_dst = X'_o1, K_dst = (K_o1 + K_o2)/2
@@ -419,11 +449,11 @@ __global__ void __launch_bounds__(64) k_adj_node(AdjArgs<TP, TH> a, Geom g, AdjP
         const long long dst = (long long)(bb - 1) * a.C + s_bs[bb - 1].head_new;
         for (int c = 0; c < DD; ++c) {
             const double lx = a.lamX[(dst * DD + c) * Np + n], lk = a.lamK[(dst * DD + c) * Np + n];
-            a.lamX[(dst * DD + c) * Np + n] = 0.0;
-            a.lamK[(dst * DD + c) * Np + n] = 0.0;
-            a.lamX[(src1 * DD + c) * Np + n] += lx;
-            a.lamK[(src1 * DD + c) * Np + n] += 0.5 * lk;
-            a.lamK[(src2 * DD + c) * Np + n] += 0.5 * lk;
+            a.lamX[(dst * DD + c) * Np + n] = TH(0);
+            a.lamK[(dst * DD + c) * Np + n] = TH(0);
+            a.lamX[(src1 * DD + c) * Np + n] = (TH)((double)a.lamX[(src1 * DD + c) * Np + n] + lx);
+            a.lamK[(src1 * DD + c) * Np + n] = (TH)((double)a.lamK[(src1 * DD + c) * Np + n] + 0.5 * lk);
+            a.lamK[(src2 * DD + c) * Np + n] = (TH)((double)a.lamK[(src2 * DD + c) * Np + n] + 0.5 * lk);
         }
     }
 
@@ -463,63 +493,64 @@ __global__ void __launch_bounds__(128) k_adj_hist(AdjArgs<TP, TH> a, Geom g, Adj
     const int n = (int)(idx % g.Npad), chunk = (int)(idx / g.Npad);
     if (chunk >= a.S || n >= g.N) return;
     const long long Np = g.Npad;
+    using R = TH;   // the forward sweep's arithmetic; the chunk's rate parts in double
     const long long s_last = (long long)(a.B - 1) * a.C + s_bs[a.B - 1].head_prev;
-    double kl[DD], A[DD], Lt[DD], lamA[DD];
+    R kl[DD], A[DD], Lt[DD], lamA[DD];
     for (int c = 0; c < DD; ++c) {
         kl[c] = a.K[(s_last * DD + c) * Np + n];
-        Lt[c] = a.lt[c * Np + n];
-        lamA[c] = 0.0;
+        Lt[c] = (R)a.lt[c * Np + n];
+        lamA[c] = 0;
     }
-    expm1_mat<D>(kl, A);
+    expm1_mat<D, R>(kl, A);
     double lam_it = 0.0, lam_ig = 0.0;
     int l0, l1;
     adj_chunk(Ls, a.S, chunk, &l0, &l1);
     for (int l = l0; l < l1; ++l) {
         const float w = s_w[l];
         if (w == 0.0f) continue;
-        double Xl[DD], Xn[DD], kap[DD], lX[DD], lk[DD];
+        R Xl[DD], Xn[DD], kap[DD], lX[DD], lk[DD];
         for (int c = 0; c < DD; ++c) {
             Xl[c] = a.X[((long long)l * DD + c) * Np + n];
             kap[c] = a.K[((long long)l * DD + c) * Np + n];
             lX[c] = a.lamX[((long long)l * DD + c) * Np + n];   // lambda of X' (after the sweep)
-            lk[c] = 0.0;
+            lk[c] = 0;
         }
         const int part = s_part[l];
         if (part >= 0)
-            for (int c = 0; c < DD; ++c) kap[c] = 0.5 * (kap[c] + a.K[((long long)part * DD + c) * Np + n]);
+            for (int c = 0; c < DD; ++c) kap[c] = R(0.5) * (kap[c] + a.K[((long long)part * DD + c) * Np + n]);
         // X' = X + A + A X
         for (int r = 0; r < D; ++r)
             for (int c = 0; c < D; ++c) {
-                double s = Xl[r * D + c] + A[r * D + c];
+                R s = Xl[r * D + c] + A[r * D + c];
                 for (int k = 0; k < D; ++k) s += A[r * D + k] * Xl[k * D + c];
                 Xn[r * D + c] = s;
             }
-        integrand_adjoint<D>(Xn, kap, (double)s_age[l], (double)w, p.inv_tau, p.inv_gc, Lt, lX, lk, &lam_it, &lam_ig);
+        integrand_adjoint<D, R>(Xn, kap, (R)s_age[l], (R)w, (R)p.inv_tau, (R)p.inv_gc, Lt, lX, lk, &lam_it, &lam_ig);
         // lambda A += lX (1 + X)^T ; lambda X = (1 + A)^T lX
         for (int r = 0; r < D; ++r)
             for (int c = 0; c < D; ++c) {
-                double s = lX[r * D + c];
+                R s = lX[r * D + c];
                 for (int k = 0; k < D; ++k) s += lX[r * D + k] * Xl[c * D + k];
                 lamA[r * D + c] += s;
             }
         for (int r = 0; r < D; ++r)
             for (int c = 0; c < D; ++c) {
-                double s = lX[r * D + c];
+                R s = lX[r * D + c];
                 for (int k = 0; k < D; ++k) s += A[k * D + r] * lX[k * D + c];
                 Xn[r * D + c] = s;   // reuse as lambda X (before the sweep)
             }
         for (int c = 0; c < DD; ++c) a.lamX[((long long)l * DD + c) * Np + n] = Xn[c];
         if (part >= 0) {
             for (int c = 0; c < DD; ++c) {
-                a.lamK[((long long)l * DD + c) * Np + n] += 0.5 * lk[c];
-                a.lamK[((long long)part * DD + c) * Np + n] += 0.5 * lk[c];
+                a.lamK[((long long)l * DD + c) * Np + n] += R(0.5) * lk[c];
+                a.lamK[((long long)part * DD + c) * Np + n] += R(0.5) * lk[c];
             }
         } else {
             for (int c = 0; c < DD; ++c) a.lamK[((long long)l * DD + c) * Np + n] += lk[c];
         }
     }
     double* out = a.part_adj + (long long)chunk * (DD + 2) * Np + n;
-    for (int c = 0; c < DD; ++c) out[c * Np] = lamA[c];
+    for (int c = 0; c < DD; ++c) out[c * Np] = (double)lamA[c];
     out[DD * Np] = lam_it;
     out[(DD + 1) * Np] = lam_ig;
 }
@@ -527,29 +558,31 @@ __global__ void __launch_bounds__(128) k_adj_hist(AdjArgs<TP, TH> a, Geom g, Adj
 // The chunk sums of k_adj_hist (chunk order), the adjoint of A = exp(kappa(t-1)) - 1 (kappa(t-1) is the kappa
 // of the newest stored point) and the rate parts of dL/dtheta.
 template <int D, typename TP, typename TH>
-__global__ void __launch_bounds__(128) k_adj_fin(AdjArgs<TP, TH> a, Geom g, AdjPar p) {
+__global__ void __launch_bounds__(32) k_adj_fin(AdjArgs<TP, TH> a, Geom g, AdjPar p) {
     constexpr int DD = D * D;
+    __shared__ BlockStep bs[LBVE_MAXB];
+    if (threadIdx.x == 0) sched_step(a.B, a.C, adj_t(a), bs);
+    __syncthreads();
     const int n = blockIdx.x * blockDim.x + threadIdx.x;
     if (n >= g.N) return;
     const long long Np = g.Npad;
     double lamA[DD], lam_it = 0.0, lam_ig = 0.0;
     for (int c = 0; c < DD; ++c) lamA[c] = 0.0;
+#pragma unroll 16   // the chunks' loads in flight together (the additions keep their order)
     for (int ch = 0; ch < a.S; ++ch) {
         const double* in = a.part_adj + (long long)ch * (DD + 2) * Np + n;
         for (int c = 0; c < DD; ++c) lamA[c] += in[c * Np];
         lam_it += in[DD * Np];
         lam_ig += in[(DD + 1) * Np];
     }
-    BlockStep bs[LBVE_MAXB];
-    sched_step(a.B, a.C, a.t, bs);
     const long long s_last = (long long)(a.B - 1) * a.C + bs[a.B - 1].head_prev;
     double kl[DD], lk[DD];
     for (int c = 0; c < DD; ++c) {
         kl[c] = a.K[(s_last * DD + c) * Np + n];
         lk[c] = 0.0;
     }
-    expm1_adjoint<D>(kl, lamA, lk);
-    for (int c = 0; c < DD; ++c) a.lamK[(s_last * DD + c) * Np + n] += lk[c];
+    expm1_adjoint<D, sizeof(TH) == 4 ? 4 : 8>(kl, lamA, lk);   // the order the forward's history type used
+    for (int c = 0; c < DD; ++c) a.lamK[(s_last * DD + c) * Np + n] = (TH)((double)a.lamK[(s_last * DD + c) * Np + n] + lk[c]);
     a.lam_theta[1 * Np + n] += lam_it * (-1.0 / (p.tau * p.tau));                // d(1/tau)/dtau
     a.lam_theta[2 * Np + n] += isinf(p.gamma_c) ? 0.0 : lam_ig * (-1.0 / (p.gamma_c * p.gamma_c));
 }

@@ -541,6 +541,7 @@ CommitArgs<R> commit_args(lbve* h) {
 }
 
 __global__ void k_advance_t(long long* t) { *t += 1; }
+__global__ void k_set_ll(long long* p, long long v) { *p = v; }
 
 // One hybrid step: moments -> history sweep -> commit + collide + stream.  pops[cur] -> pops[cur ^ 1].
 // P: population storage type, HK: history kind (0 float, 1 double, 2 16-bit, 3 none: the instantaneous
@@ -615,21 +616,12 @@ int capture_graph(lbve* h) {
 
 int record_checkpoint(lbve* h, cudaStream_t s);
 
+// n steps as launch sequences: whole graphs of kGraphSteps steps (an even count, so populations end where
+// they started; the graph is recorded for cur == 0, so a pending odd step is run first), the rest one by one.
+// Profiling records per-launch events and therefore launches step by step.
 template <int Q, typename P, int HK, typename T>
-int step_impl(lbve* h, int64_t n, cudaStream_t s) {
+int advance(lbve* h, int64_t n, cudaStream_t s) {
     int rc;
-    if (h->rec_K) {   // recording for the adjoint: an image every rec_K steps, no graphs
-        for (int64_t i = 0; i < n; ++i) {
-            if (h->t_host % h->rec_K == 0 && (rc = record_checkpoint(h, s))) return rc;
-            if ((rc = one_step<Q, P, HK, T>(h, h->cur, s))) return rc;
-            h->cur ^= 1;
-            h->t_host += 1;
-        }
-        return LBVE_OK;
-    }
-    // whole graphs of kGraphSteps steps (an even count, so populations end where they started); the
-    // graph is recorded for cur == 0, so a pending odd step is run first.  Profiling records per-launch
-    // events and therefore launches step by step.
     if (!h->profiling && n >= kGraphSteps) {
         if (h->cur == 1) {
             if ((rc = one_step<Q, P, HK, T>(h, 1, s))) return rc;
@@ -650,6 +642,20 @@ int step_impl(lbve* h, int64_t n, cudaStream_t s) {
         if ((rc = one_step<Q, P, HK, T>(h, h->cur, s))) return rc;
         h->cur ^= 1;
         h->t_host += 1;
+    }
+    return LBVE_OK;
+}
+
+template <int Q, typename P, int HK, typename T>
+int step_impl(lbve* h, int64_t n, cudaStream_t s) {
+    if (!h->rec_K) return advance<Q, P, HK, T>(h, n, s);
+    // recording for the adjoint: a state image at every multiple of rec_K steps, the steps in between as usual
+    int rc;
+    while (n > 0) {
+        if (h->t_host % h->rec_K == 0 && (rc = record_checkpoint(h, s))) return rc;
+        const int64_t seg = std::min<int64_t>(n, h->rec_K - h->t_host % h->rec_K);
+        if ((rc = advance<Q, P, HK, T>(h, seg, s))) return rc;
+        n -= seg;
     }
     return LBVE_OK;
 }
@@ -1574,13 +1580,15 @@ int backward_impl(lbve* h, const double* dL_du, const double* dL_ds, double* gra
     const int K = h->rec_K;
     if (T < 1) return LBVE_ESTATE;
     const size_t hist_b = sizeof(TH) * (size_t)h->L * DD * Np;
-    const size_t lhist_b = sizeof(double) * (size_t)h->L * DD * Np;
+    const size_t lhist_b = sizeof(TH) * (size_t)h->L * DD * Np;   // lambda of the history: the history's type
     const size_t pop_b = sizeof(TP) * h->Q * Np;
     const size_t lpop_b = sizeof(double) * h->Q * Np;
     // work buffers
     DevBuf lam_n, lamX, lamK, lam_trp, lam_kt, lam_th, seeds, tape, ur, cnt, fin, psig, plt, padj;
-    // slot chunks of the split history kernels: about 64k (node, chunk) threads, at most 32 chunks
-    const int S = (int)std::max(1ll, std::min<long long>({32ll, (long long)h->L, (65536ll + h->N - 1) / h->N}));
+    // slot chunks of the split history kernels: about 32k (node, chunk) threads, at least 8 slots a chunk (the
+    // per-node kernels add the chunks' partial sums in order, a chain as long as the chunk count)
+    const int S = (int)std::max(1ll, std::min<long long>({64ll, (long long)std::max(1, h->L / 8),
+                                                         (32768ll + h->N - 1) / h->N}));
     const size_t step_b = pop_b + 2 * hist_b + sizeof(double) * Np;   // pops, X, K, tr_prev
     size_t img = 0;
     lbve_checkpoint_size(h, &img);
@@ -1611,48 +1619,63 @@ int backward_impl(lbve* h, const double* dL_du, const double* dL_ds, double* gra
                                   cudaMemcpyHostToDevice, s));
     const Geom g = geom_of(h);
     const AdjPar p = adj_par(h);
-    const int grid64 = (h->N + 63) / 64, grid128 = (h->N + 127) / 128;
+    // The per-node adjoint kernels are FP64 chains, and an SM's FP64 pipe completes a warp instruction in
+    // (active lanes / 2) cycles: with few nodes, blocks of fewer threads spread them over more SMs, each
+    // warp instruction taking fewer cycles (tpb threads a block, enough blocks to cover the SMs).
+    int dev = 0, sms = 1;
+    LBVE_CUDA(cudaGetDevice(&dev));
+    LBVE_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+    int tpb = 1;
+    while (tpb < 32 && (h->N + tpb - 1) / tpb > sms) tpb *= 2;
+    const int gridn = (h->N + tpb - 1) / tpb;
     const size_t smem = sweep_smem_bytes(h->L);
     if (smem > 48 * 1024) {
-        LBVE_CUDA(cudaFuncSetAttribute(k_adj_node<Q, TP, TH>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
         LBVE_CUDA(cudaFuncSetAttribute(k_adj_sig<D, TP, TH>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
         LBVE_CUDA(cudaFuncSetAttribute(k_adj_hist<D, TP, TH>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
     }
     const int grid_chunks = (int)(((long long)S * Np + 127) / 128);
-    const int rec = h->rec_K;
-    h->rec_K = 0;   // the replay below must not record
-    int cur_lam = 0;
-    const int64_t nseg = (T + K - 1) / K;
-    for (int64_t sg = nseg - 1; sg >= 0 && rc == LBVE_OK; --sg) {
-        if ((size_t)sg >= h->ckpts.size() || !h->ckpts[sg]) { rc = LBVE_ESTATE; break; }
-        if ((rc = lbve_checkpoint_restore(h, h->ckpts[sg], 1, s))) break;
-        const int64_t t0 = sg * K, t1 = std::min<int64_t>(T, t0 + K);
-        for (int64_t t = t0; t < t1 && rc == LBVE_OK; ++t) {   // replay with a tape of each step's state
+    DevBuf t0buf;   // the first step of the segment being processed (read by the adjoint kernels)
+    if ((rc = t0buf.get(h, sizeof(long long)))) return rc;
+    long long* t0dev = (long long*)t0buf.p;
+#define LBVE_SEG(call)                                        \
+    do {                                                      \
+        cudaError_t e_ = (call);                              \
+        if (e_ != cudaSuccess) return cuda_fail(e_, #call);   \
+    } while (0)
+    // replay steps t0 .. t1-1 from the restored image, keeping each step's state on the tape
+    auto replay = [&](int64_t t0, int64_t t1, cudaStream_t st) -> int {
+        for (int64_t t = t0; t < t1; ++t) {
             char* slot = (char*)tape.p + step_b * (size_t)(t - t0);
-            LBVE_CUDA(cudaMemcpyAsync(slot, h->pops[h->cur], pop_b, cudaMemcpyDeviceToDevice, s));
-            LBVE_CUDA(cudaMemcpyAsync(slot + pop_b, h->X, hist_b, cudaMemcpyDeviceToDevice, s));
-            LBVE_CUDA(cudaMemcpyAsync(slot + pop_b + hist_b, h->K, hist_b, cudaMemcpyDeviceToDevice, s));
-            LBVE_CUDA(cudaMemcpyAsync(slot + pop_b + 2 * hist_b, h->tr_prev, sizeof(double) * Np,
-                                      cudaMemcpyDeviceToDevice, s));
-            rc = one_step<Q, TP, HK, TP>(h, h->cur, s);
+            LBVE_SEG(cudaMemcpyAsync(slot, h->pops[h->cur], pop_b, cudaMemcpyDeviceToDevice, st));
+            LBVE_SEG(cudaMemcpyAsync(slot + pop_b, h->X, hist_b, cudaMemcpyDeviceToDevice, st));
+            LBVE_SEG(cudaMemcpyAsync(slot + pop_b + hist_b, h->K, hist_b, cudaMemcpyDeviceToDevice, st));
+            LBVE_SEG(cudaMemcpyAsync(slot + pop_b + 2 * hist_b, h->tr_prev, sizeof(double) * Np,
+                                     cudaMemcpyDeviceToDevice, st));
+            const int r = one_step<Q, TP, HK, TP>(h, h->cur, st);
+            if (r) return r;
             h->cur ^= 1;
             h->t_host += 1;
         }
-        for (int64_t t = t1 - 1; t >= t0 && rc == LBVE_OK; --t) {
+        return LBVE_OK;
+    };
+    // the adjoint of steps t1-1 down to t0 (lambda buffers alternate from parity lam0)
+    auto adjoint = [&](int64_t t0, int64_t t1, int lam0, cudaStream_t st) -> int {
+        int cl = lam0;
+        for (int64_t t = t1 - 1; t >= t0; --t) {
             const char* slot = (const char*)tape.p + step_b * (size_t)(t - t0);
             const TP* pops_t = (const TP*)slot;
-            k_moments<Q, TP><<<(h->N + 255) / 256, 256, 0, s>>>(pops_t, (double*)ur.p, g, (long long*)cnt.p);
-            LBVE_CUDA(cudaGetLastError());
+            k_moments<Q, TP><<<(h->N + 255) / 256, 256, 0, st>>>(pops_t, (double*)ur.p, g, (long long*)cnt.p);
+            LBVE_SEG(cudaGetLastError());
             AdjArgs<TP, TH> a;
             a.n = pops_t;
             a.X = (const TH*)(slot + pop_b);
             a.K = (const TH*)(slot + pop_b + hist_b);
             a.trp = (const double*)(slot + pop_b + 2 * hist_b);
             a.u_raw = (const double*)ur.p;
-            a.lam_n1 = (const double*)lam_n.p + (size_t)cur_lam * h->Q * Np;
-            a.lam_n0 = (double*)lam_n.p + (size_t)(cur_lam ^ 1) * h->Q * Np;
-            a.lamX = (double*)lamX.p;
-            a.lamK = (double*)lamK.p;
+            a.lam_n1 = (const double*)lam_n.p + (size_t)cl * h->Q * Np;
+            a.lam_n0 = (double*)lam_n.p + (size_t)(cl ^ 1) * h->Q * Np;
+            a.lamX = (TH*)lamX.p;
+            a.lamK = (TH*)lamK.p;
             a.lam_trp = (double*)lam_trp.p;
             a.lam_kt = (double*)lam_kt.p;
             a.lam_theta = (double*)lam_th.p;
@@ -1661,23 +1684,71 @@ int backward_impl(lbve* h, const double* dL_du, const double* dL_ds, double* gra
             a.part_sig = (double*)psig.p;
             a.lt = (double*)plt.p;
             a.part_adj = (double*)padj.p;
-            a.t = t;
+            a.t_off = t - t0;
+            a.t0 = t0dev;
             a.B = h->d.hist_B;
             a.C = h->d.hist_C;
             a.S = S;
-            k_adj_sig<D, TP, TH><<<grid_chunks, 128, smem, s>>>(a, g, p);
-            LBVE_CUDA(cudaGetLastError());
-            k_adj_node<Q, TP, TH><<<grid64, 64, smem, s>>>(a, g, p);
-            LBVE_CUDA(cudaGetLastError());
-            k_adj_hist<D, TP, TH><<<grid_chunks, 128, smem, s>>>(a, g, p);
-            LBVE_CUDA(cudaGetLastError());
-            k_adj_fin<D, TP, TH><<<grid128, 128, 0, s>>>(a, g, p);
-            LBVE_CUDA(cudaGetLastError());
-            k_adj_fd<Q, TP><<<grid128, 128, 0, s>>>(pops_t, (const double*)lam_kt.p, a.lam_n0, (double*)lam_th.p, g, p);
-            LBVE_CUDA(cudaGetLastError());
-            cur_lam ^= 1;
+            k_adj_sig<D, TP, TH><<<grid_chunks, 128, smem, st>>>(a, g, p);
+            LBVE_SEG(cudaGetLastError());
+            k_adj_node<Q, TP, TH><<<gridn, tpb, 0, st>>>(a, g, p);
+            LBVE_SEG(cudaGetLastError());
+            k_adj_hist<D, TP, TH><<<grid_chunks, 128, smem, st>>>(a, g, p);
+            LBVE_SEG(cudaGetLastError());
+            k_adj_fin<D, TP, TH><<<gridn, tpb, 0, st>>>(a, g, p);
+            LBVE_SEG(cudaGetLastError());
+            k_adj_fd<Q, TP><<<gridn, tpb, 0, st>>>(pops_t, (const double*)lam_kt.p, a.lam_n0, (double*)lam_th.p, g, p);
+            LBVE_SEG(cudaGetLastError());
+            cl ^= 1;
         }
+        return LBVE_OK;
+    };
+#undef LBVE_SEG
+    // A full segment (K steps, not containing the last step, whose adjoint takes the loss seeds) is the same
+    // sequence of launches for every segment: it is captured once per parity of the lambda buffers and
+    // replayed; the segment's first step is written to device memory before each replay.
+    cudaGraphExec_t seg_graph[2] = {nullptr, nullptr};
+    auto free_graphs = [&]() {
+        for (cudaGraphExec_t& ge : seg_graph)
+            if (ge) { cudaGraphExecDestroy(ge); ge = nullptr; }
+    };
+    if (!h->graph_stream) LBVE_CUDA(cudaStreamCreateWithFlags(&h->graph_stream, cudaStreamNonBlocking));
+    const int rec = h->rec_K;
+    h->rec_K = 0;   // the replay below must not record
+    int cur_lam = 0;
+    const int64_t nseg = (T + K - 1) / K;
+    for (int64_t sg = nseg - 1; sg >= 0 && rc == LBVE_OK; --sg) {
+        if ((size_t)sg >= h->ckpts.size() || !h->ckpts[sg]) { rc = LBVE_ESTATE; break; }
+        if ((rc = lbve_checkpoint_restore(h, h->ckpts[sg], 1, s))) break;
+        const int64_t t0 = sg * K, t1 = std::min<int64_t>(T, t0 + K);
+        k_set_ll<<<1, 1, 0, s>>>(t0dev, (long long)t0);
+        if (cudaGetLastError() != cudaSuccess) { rc = cuda_fail(cudaErrorLaunchFailure, "k_set_ll"); break; }
+        const bool graphable = t1 - t0 == K && t1 < T && !h->profiling;
+        if (!graphable) {
+            if ((rc = replay(t0, t1, s)) || (rc = adjoint(t0, t1, cur_lam, s))) break;
+        } else {
+            if (!seg_graph[cur_lam]) {
+                cudaGraph_t gr = nullptr;
+                cudaError_t e = cudaStreamBeginCapture(h->graph_stream, cudaStreamCaptureModeThreadLocal);
+                if (e != cudaSuccess) { rc = cuda_fail(e, "cudaStreamBeginCapture"); break; }
+                int rc2 = replay(t0, t1, h->graph_stream);
+                if (rc2 == LBVE_OK) rc2 = adjoint(t0, t1, cur_lam, h->graph_stream);
+                e = cudaStreamEndCapture(h->graph_stream, &gr);
+                if (rc2 == LBVE_OK && e == cudaSuccess) e = cudaGraphInstantiate(&seg_graph[cur_lam], gr, 0);
+                if (gr) cudaGraphDestroy(gr);
+                if (rc2) { rc = rc2; break; }
+                if (e != cudaSuccess) { rc = cuda_fail(e, "segment graph"); seg_graph[cur_lam] = nullptr; break; }
+            }
+            cudaError_t e = cudaGraphLaunch(seg_graph[cur_lam], s);
+            if (e != cudaSuccess) { rc = cuda_fail(e, "cudaGraphLaunch"); break; }
+        }
+        cur_lam ^= (int)((t1 - t0) & 1);
     }
+    if (rc == LBVE_OK) {
+        cudaError_t e = cudaStreamSynchronize(s);
+        if (e != cudaSuccess) rc = cuda_fail(e, "backward");
+    }
+    free_graphs();
     h->rec_K = rec;
     if (rc) return rc;
     // dL/dtheta = sum over nodes of the per-node parts

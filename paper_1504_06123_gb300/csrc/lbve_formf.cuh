@@ -290,6 +290,7 @@ __device__ __forceinline__ void formf_sigma(const R* part, int S, long long Np, 
     for (int i = 0; i < DD; ++i) Z[i] = A(0);
 #pragma unroll
     for (int i = 0; i < NS; ++i) acc[i] = 0.0;
+#pragma unroll 4
     for (int j = 0; j < S; ++j) {
         const R* pj = part + (long long)j * (NS + DD) * Np + n;
         A M[DD], T[DD];

@@ -212,6 +212,19 @@ int lbve_get_time(const lbve_t* h, int64_t* t);
  */
 int lbve_fields(lbve_t* h, uint32_t field_mask, double* dst, int32_t dst_is_device, void* stream);
 
+/*
+ * lbve_fields for one channel of a batch and in a chosen precision: the fields selected by field_mask of the
+ * nodes of `channel` (-1: all nodes, as lbve_fields), one block per field in increasing bit order, each block
+ * component-major ([comp][nodes of the channel], node order of lbve_channel_nodes), written as dst_dtype values
+ * (LBVE_F64: double; LBVE_F32: float, each value rounded once from the double field).  dst holds
+ * (components of the selected fields) x (nodes of the channel) values; device or host memory as in
+ * lbve_fields, with the same synchronisation and the same ENONFINITE report for host destinations.
+ * Errors: EINVAL (channel outside -1 .. n_channels-1, another dst_dtype, bad mask), ENOSUPPORT for tangent
+ * handles (lbve_tangent_fields).
+ */
+int lbve_fields_ex(lbve_t* h, int32_t channel, uint32_t field_mask, void* dst, int32_t dst_is_device,
+                   int32_t dst_dtype, void* stream);
+
 /* Number of doubles lbve_fields writes for field_mask. */
 int lbve_fields_count(const lbve_t* h, uint32_t field_mask, size_t* count);
 

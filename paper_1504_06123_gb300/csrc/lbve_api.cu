@@ -739,6 +739,42 @@ int fields_impl(lbve* h, uint32_t mask, double* dst, int* flag, cudaStream_t s) 
     return LBVE_OK;
 }
 
+// Fields of the node range [n0, n0 + cnt) into dst (device) as values of type O, one block per field in
+// increasing bit order, each block component-major; N1 = sigma_xx - sigma_yy.  Node fields are double.
+template <typename O>
+__global__ void k_gather_range(const double* __restrict__ src, long long Npad, int ncomp, long long n0, int cnt,
+                               double offset, int n1, O* __restrict__ dst, int* nonfinite) {
+    const long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    if (i >= (long long)ncomp * cnt) return;
+    const int c = (int)(i / cnt);
+    const long long n = n0 + (i - (long long)c * cnt);
+    const double v = n1 ? src[n] - src[Npad + n] : src[c * Npad + n] + offset;
+    dst[i] = (O)v;
+    if (!isfinite(v)) atomicOr(nonfinite, 1);
+}
+
+template <typename O>
+int fields_range_impl(lbve* h, uint32_t mask, long long n0, int cnt, O* dst, int* flag, cudaStream_t s) {
+    struct Part { uint32_t bit; const void* src; int ncomp; double offset; int n1; };
+    const Part parts[] = {{LBVE_FIELD_RHO, h->rho, 1, h->d.rho0, 0},      // stored as rho - rho0
+                          {LBVE_FIELD_U, h->u, h->D, 0.0, 0},
+                          {LBVE_FIELD_SIGMA, h->sigma, h->NS, 0.0, 0},
+                          {LBVE_FIELD_KAPPA, h->kappa, h->D * h->D, 0.0, 0},
+                          {LBVE_FIELD_N1, h->sigma, 1, 0.0, 1}};
+    size_t off = 0;
+    for (const Part& pt : parts) {
+        if (!(mask & pt.bit)) continue;
+        const long long tot = (long long)pt.ncomp * cnt;
+        if (tot > 0) {
+            k_gather_range<O><<<(int)((tot + 255) / 256), 256, 0, s>>>((const double*)pt.src, h->Npad, pt.ncomp, n0,
+                                                                       cnt, pt.offset, pt.n1, dst + off, flag);
+            LBVE_CUDA(cudaGetLastError());
+        }
+        off += (size_t)tot;
+    }
+    return LBVE_OK;
+}
+
 size_t fields_count(const lbve* h, uint32_t mask) {
     size_t c = 0;
     if (mask & LBVE_FIELD_RHO) c += 1;
@@ -1295,6 +1331,41 @@ int lbve_fields(lbve_t* h, uint32_t mask, double* dst, int32_t dst_is_device, vo
     if (rc) return rc;
     int flag = 0;
     LBVE_CUDA(cudaMemcpyAsync(dst, h->stage, sizeof(double) * cnt, cudaMemcpyDeviceToHost, s));
+    LBVE_CUDA(cudaMemcpyAsync(&flag, h->flag, sizeof(int), cudaMemcpyDeviceToHost, s));
+    LBVE_CUDA(cudaStreamSynchronize(s));
+    return flag ? LBVE_ENONFINITE : LBVE_OK;
+}
+
+int lbve_fields_ex(lbve_t* h, int32_t channel, uint32_t mask, void* dst, int32_t dst_is_device, int32_t dst_dtype,
+                   void* stream) {
+    if (!h || !dst || (mask & ~31u)) return LBVE_EINVAL;
+    if (channel < -1 || channel >= h->nchan) return LBVE_EINVAL;
+    if (dst_dtype != LBVE_F64 && dst_dtype != LBVE_F32) return LBVE_EINVAL;
+    if (h->tangent) return LBVE_ENOSUPPORT;
+    cudaStream_t s = (cudaStream_t)stream;
+    const long long n0 = channel < 0 ? 0 : h->chan_host[channel].off;
+    const int cnt = channel < 0 ? h->N : h->descs[channel].nx * h->descs[channel].ny * h->descs[channel].nz;
+    const size_t vals = h->N > 0 ? fields_count(h, mask) / (size_t)h->N * (size_t)cnt : 0;
+    const size_t esz = dst_dtype == LBVE_F64 ? sizeof(double) : sizeof(float);
+    auto run = [&](void* d, int* flag) {
+        return dst_dtype == LBVE_F64 ? fields_range_impl<double>(h, mask, n0, cnt, (double*)d, flag, s)
+                                     : fields_range_impl<float>(h, mask, n0, cnt, (float*)d, flag, s);
+    };
+    if (dst_is_device) return run(dst, h->flag);
+    const size_t need = (vals * esz + sizeof(double) - 1) / sizeof(double);   // staging, in doubles
+    if (h->stage_n < need) {
+        dev_free(h, h->stage);
+        h->stage = nullptr;
+        h->stage_n = 0;
+        int rc = dev_alloc(h, (void**)&h->stage, sizeof(double) * (need > 0 ? need : 1));
+        if (rc) return rc;
+        h->stage_n = need;
+    }
+    LBVE_CUDA(cudaMemsetAsync(h->flag, 0, sizeof(int), s));
+    int rc = run(h->stage, h->flag);
+    if (rc) return rc;
+    int flag = 0;
+    LBVE_CUDA(cudaMemcpyAsync(dst, h->stage, vals * esz, cudaMemcpyDeviceToHost, s));
     LBVE_CUDA(cudaMemcpyAsync(&flag, h->flag, sizeof(int), cudaMemcpyDeviceToHost, s));
     LBVE_CUDA(cudaStreamSynchronize(s));
     return flag ? LBVE_ENONFINITE : LBVE_OK;

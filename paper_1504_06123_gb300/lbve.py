@@ -36,7 +36,7 @@ EXPORTS = [
     "lbve_fields_host_fixed", "lbve_create_batch", "lbve_channel_nodes", "lbve_sweep_config",
     "lbve_create_tangent", "lbve_tangent_fields", "lbve_checkpoint_size", "lbve_checkpoint_save",
     "lbve_checkpoint_restore", "lbve_create_adjoint", "lbve_backward", "lbve_set_pressure_step",
-    "lbve_set_probes", "lbve_probe_read", "lbve_set_sweep_config", "lbve_create_ex",
+    "lbve_set_probes", "lbve_probe_read", "lbve_set_sweep_config", "lbve_create_ex", "lbve_fields_ex",
 ]
 
 
@@ -131,6 +131,7 @@ def load(path: str | None = None):
         lib.lbve_get_time.argtypes = [vp, C.POINTER(i64)]
         lib.lbve_fields.argtypes = [vp, C.c_uint32, vp, i32, vp]
         lib.lbve_fields_count.argtypes = [vp, C.c_uint32, C.POINTER(C.c_size_t)]
+        lib.lbve_fields_ex.argtypes = [vp, i32, C.c_uint32, vp, i32, i32, vp]
         lib.lbve_history_apply.argtypes = [vp, vp, vp, vp]
         lib.lbve_mass.argtypes = [vp, dp, dp, vp]
         lib.lbve_schedule.argtypes = [i32, i32, i64, C.POINTER(i64), dp, C.POINTER(i32)]
@@ -345,6 +346,26 @@ def lbve_fields_count(h: int, mask: int) -> int:
     n = C.c_size_t()
     _check(load().lbve_fields_count(h, mask, C.byref(n)), "lbve_fields_count")
     return n.value
+
+
+def lbve_fields_ex(h: int, channel: int, mask: int, dtype: int = LBVE_F64, dst=None, stream=None):
+    """Fields of one channel (-1: all nodes) as float64 (LBVE_F64) or float32 (LBVE_F32), one block per field,
+    component-major.  dst None: a new numpy array (host copy, synchronising); dst a device tensor / pointer:
+    asynchronous device write, returns dst."""
+    lib = load()
+    if dst is None:
+        total = lbve_fields_count(h, mask)
+        count = total if channel < 0 else total // _nodes(h) * lbve_channel_nodes(h, channel)[1]
+        out = np.empty(count, dtype=np.float64 if dtype == LBVE_F64 else np.float32)
+        _check(lib.lbve_fields_ex(h, channel, mask, out.ctypes.data, 0, dtype, _stream(stream)), "lbve_fields_ex")
+        return out
+    _check(lib.lbve_fields_ex(h, channel, mask, _ptr(dst), 1, dtype, _stream(stream)), "lbve_fields_ex")
+    return dst
+
+
+def _nodes(h: int) -> int:
+    """All nodes of the handle (the field count of the density alone)."""
+    return lbve_fields_count(h, LBVE_FIELD_RHO)
 
 
 def lbve_fields(h: int, mask: int, dst=None, stream=None):

@@ -482,3 +482,37 @@ def test_nonfinite_state_is_reported():
         ch.fields()
     assert e.value.status == L.LBVE_ENONFINITE
     ch.close()
+
+
+def test_fields_ex_per_channel_and_precision():
+    """lbve_fields_ex: one channel's nodes of every field, in FP64 (the same bits as lbve_fields) and FP32 (each
+    value rounded once), to host and to device memory; a channel outside the batch and another dtype refused."""
+    descs = [L.make_desc(L.LBVE_D2Q9, c["nx"], c["ny"], tau_lb=c["tau_lb"], G_inf=c["G_inf"], tau=c["tau"],
+                         gamma_c=c["gamma_c"], g=(c["g"], 0, 0), C=16, B=4, precision=F64, hist_storage=F32)
+             for c in BATCH]
+    ch = L.Channel(descs, inputs.initial_density(sum(c["nx"] * c["ny"] for c in BATCH), 1e-5, seed=9))
+    ch.step(40)
+    mask = L.LBVE_FIELD_RHO | L.LBVE_FIELD_U | L.LBVE_FIELD_SIGMA | L.LBVE_FIELD_KAPPA | L.LBVE_FIELD_N1
+    full = L.lbve_fields(ch.h, mask)
+    N = ch.N
+    rows = full.reshape(-1, N)                         # 1 + 2 + 3 + 4 + 1 component rows
+    assert rows.shape[0] == 11
+    for c in range(len(descs)):
+        off, cnt = L.lbve_channel_nodes(ch.h, c)
+        want = rows[:, off:off + cnt].ravel()
+        assert np.array_equal(L.lbve_fields_ex(ch.h, c, mask, L.LBVE_F64), want)
+        got32 = L.lbve_fields_ex(ch.h, c, mask, L.LBVE_F32)
+        assert got32.dtype == np.float32 and np.array_equal(got32, want.astype(np.float32))
+        dev = torch.empty(want.size, dtype=torch.float32, device="cuda")
+        L.lbve_fields_ex(ch.h, c, mask, L.LBVE_F32, dst=dev)
+        torch.cuda.synchronize()
+        assert np.array_equal(dev.cpu().numpy(), want.astype(np.float32))
+    assert np.array_equal(L.lbve_fields_ex(ch.h, -1, mask), full)
+    sig = L.lbve_fields_ex(ch.h, 2, L.LBVE_FIELD_SIGMA)
+    off, cnt = L.lbve_channel_nodes(ch.h, 2)
+    assert np.array_equal(sig, rows[3:6, off:off + cnt].ravel())
+    for bad in [(len(descs), L.LBVE_F64), (-2, L.LBVE_F64), (0, L.LBVE_S16)]:
+        with pytest.raises(L.LbveError) as e:
+            L.lbve_fields_ex(ch.h, bad[0], mask, bad[1], dst=torch.empty(4, device="cuda"))
+        assert e.value.status == L.LBVE_EINVAL
+    ch.close()

@@ -211,6 +211,11 @@ void fill_chan(const lbve_channel_desc& d, int off, Chan* c) {
     c->inv_gc = std::isinf(d.gamma_c) ? 0.0 : 1.0 / d.gamma_c;
     c->xbc = d.x_boundary == LBVE_X_PRESSURE;
     c->drho_gh = c->xbc ? 3.0 * d.dp * (d.nx + 1.0) / (2.0 * d.nx) : 0.0;   // (dp / c_s^2)(nx + 1)/(2 nx)
+    c->rho0_f = (float)c->rho0;
+    c->omega_f = (float)c->omega;
+    for (int a = 0; a < 3; ++a) c->f_f[a] = (float)c->f[a];
+    c->G_inf_f = (float)c->G_inf;
+    c->drho_gh_f = (float)c->drho_gh;
 }
 
 int check_desc(const lbve_channel_desc* d) {
@@ -555,7 +560,8 @@ int one_step(lbve* h, int cur, cudaStream_t s) {
     P* dout = (P*)h->pops[cur ^ 1];
     int rc;
     if ((rc = prof_mark(h, s, KIND_MOMENTS, true))) return rc;
-    k_moments<Q, P><<<grid, 256, 0, s>>>(din, (double*)h->u_raw, g, h->t_dev);
+    using M = typename std::conditional<sizeof(P) == 4 && (HK == 2 || HK == 6), float, double>::type;
+    k_moments<Q, P, M><<<grid, 256, 0, s>>>(din, (double*)h->u_raw, g, h->t_dev);
     LBVE_CUDA(cudaGetLastError());
     if ((rc = prof_mark(h, s, KIND_MOMENTS, false))) return rc;
     if (HK != 3) {
@@ -1157,10 +1163,8 @@ int lbve_set_force(lbve_t* h, int32_t channel, const double g[3], void* stream) 
     }
     const int c0 = channel < 0 ? 0 : channel, c1 = channel < 0 ? h->nchan : channel + 1;
     for (int c = c0; c < c1; ++c) {
-        for (int a = 0; a < 3; ++a) {
-            h->descs[c].g[a] = g[a];
-            h->chan_host[c].f[a] = h->descs[c].rho0 * g[a];
-        }
+        for (int a = 0; a < 3; ++a) h->descs[c].g[a] = g[a];
+        fill_chan(h->descs[c], h->chan_host[c].off, &h->chan_host[c]);
         int rc = push_chan(h, c, (cudaStream_t)stream);
         if (rc) return rc;
     }
@@ -1735,7 +1739,7 @@ int backward_impl(lbve* h, const double* dL_du, const double* dL_ds, double* gra
         for (int64_t t = t1 - 1; t >= t0; --t) {
             const char* slot = (const char*)tape.p + step_b * (size_t)(t - t0);
             const TP* pops_t = (const TP*)slot;
-            k_moments<Q, TP><<<(h->N + 255) / 256, 256, 0, st>>>(pops_t, (double*)ur.p, g, (long long*)cnt.p);
+            k_moments<Q, TP, double><<<(h->N + 255) / 256, 256, 0, st>>>(pops_t, (double*)ur.p, g, (long long*)cnt.p);
             LBVE_SEG(cudaGetLastError());
             AdjArgs<TP, TH> a;
             a.n = pops_t;

@@ -28,8 +28,8 @@ constexpr double kInlmEps = 1e-18;
 template <int D> __device__ __forceinline__ constexpr int sym_r(int i) { return D == 2 ? (i == 1 ? 1 : 0) : (i < 3 ? i : (i == 5 ? 1 : 0)); }
 template <int D> __device__ __forceinline__ constexpr int sym_c(int i) { return D == 2 ? (i == 0 ? 0 : 1) : (i < 3 ? i : (i == 3 ? 1 : 2)); }
 
-template <int D, typename T>
-__device__ __forceinline__ void inlm_stress(const double* ktd, const Chan& p, double* sig) {
+template <int D, typename T, typename N>
+__device__ __forceinline__ void inlm_stress(const double* ktd, const Chan& p, N* sig) {
     constexpr int DD = D * D;
     constexpr int NS = D == 2 ? 3 : 6;
     const double tMd = 1.0 / (p.inv_tau + shear_rate_d<D>(ktd) * p.inv_gc);
@@ -77,14 +77,14 @@ __device__ __forceinline__ void inlm_stress(const double* ktd, const Chan& p, do
     }
     const double nan = __longlong_as_double(0x7ff8000000000000ll);
 #pragma unroll
-    for (int i = 0; i < NS; ++i) sig[i] = ok ? p.G_inf * (double)Z[i] : nan;
+    for (int i = 0; i < NS; ++i) sig[i] = (N)(ok ? p.G_inf * (double)Z[i] : nan);
 }
 
-template <int D, typename T>
-__device__ __forceinline__ void hist_commit_any(const Instant<T>&, const BlockStep*, long long, int,
+template <int D, typename T, typename N>
+__device__ __forceinline__ void hist_commit_any(Arith<N>, const Instant<T>&, const BlockStep*, long long, int,
                                                 const double* /*kprev*/, const double* ktd, const Chan& p,
-                                                double* sig, long long /*t*/) {
-    inlm_stress<D, T>(ktd, p, sig);
+                                                N* sig, long long /*t*/) {
+    inlm_stress<D, T, N>(ktd, p, sig);
 }
 
 // ------------------------------------------------------------------------------------------------
@@ -104,7 +104,8 @@ template <typename P> struct CollArgs {
 
 // One node per thread: history commit (sigma_struc(t), merges, new point), then the collision with
 // that stress and push streaming.  T: arithmetic type of the collision (double for double populations;
-// float for float).
+// float for float).  The finite-difference gradient and the node scalars run in double, the node fields
+// are stored in double.
 template <int Q, typename P, typename T, class H>
 __global__ void __launch_bounds__(256) k_collide_stream(CollArgs<P> a, H h, Geom g) {
     using L = Lattice<Q>;
@@ -119,61 +120,58 @@ __global__ void __launch_bounds__(256) k_collide_stream(CollArgs<P> a, H h, Geom
     if (n >= g.N) return;
     const long long Np = g.Npad;
     const Chan& p = g.ch[chan_index(g, n)];
-    double sg[NS];
+    // sums of the commit and the moments in N (float only with float populations and the 16-bit history,
+    // whose storage rounding is far coarser); the node scalars (trace, density source, rho, u) in double
+    using N = typename std::conditional<sizeof(P) == 4 && Hist16<H>::value, float, double>::type;
+    N sg[NS];
     {
         double ktd[DD], kprev[DD];
         kappa_fd<D>(a.u_raw, Np, p, n, ktd);
 #pragma unroll
         for (int c = 0; c < DD; ++c) kprev[c] = a.kappa[c * Np + n];
-        hist_commit_any<D>(h, s_bs, Np, n, kprev, ktd, p, sg, t);
+        hist_commit_any<D>(Arith<N>(), h, s_bs, Np, n, kprev, ktd, p, sg, t);
 #pragma unroll
-        for (int i = 0; i < NS; ++i) a.sigma[i * Np + n] = sg[i];
+        for (int i = 0; i < NS; ++i) a.sigma[i * Np + n] = (double)sg[i];
 #pragma unroll
         for (int c = 0; c < DD; ++c) a.kappa[c * Np + n] = ktd[c];
     }
     T dn[Q];
-    double drho_raw = 0, jd[3] = {0, 0, 0};
+    N dm[Q], drho_m, jd_m[3];
 #pragma unroll
-    for (int q = 0; q < Q; ++q) {
-        const P v = a.dn_in[q * Np + n];
-        dn[q] = (T)v;
-        drho_raw += (double)v;
-        if (L::cx(q)) jd[0] += L::cx(q) * (double)v;
-        if (L::cy(q)) jd[1] += L::cy(q) * (double)v;
-        if (D == 3 && L::cz(q)) jd[2] += L::cz(q) * (double)v;
-    }
+    for (int q = 0; q < Q; ++q) { dn[q] = (T)a.dn_in[q * Np + n]; dm[q] = (N)a.dn_in[q * Np + n]; }
+    node_moments<Q, N>(dm, drho_m, jd_m);
     // stress: traceless part and density source (Sec. III, trace split)
     T S[3][3];
     double trd = 0;
     if (D == 2) {
         S[0][0] = (T)sg[0]; S[1][1] = (T)sg[1];
         S[0][1] = S[1][0] = (T)sg[2];
-        trd = sg[0] + sg[1];
+        trd = (double)sg[0] + (double)sg[1];
     } else {
         S[0][0] = (T)sg[0]; S[1][1] = (T)sg[1]; S[2][2] = (T)sg[2];
         S[0][1] = S[1][0] = (T)sg[3];
         S[0][2] = S[2][0] = (T)sg[4];
         S[1][2] = S[2][1] = (T)sg[5];
-        trd = sg[0] + sg[1] + sg[2];
+        trd = (double)sg[0] + (double)sg[1] + (double)sg[2];
     }
     double ddr_d = 0;
     if (p.trace_full) ddr_d = -(trd - a.tr_prev[n]) * (3.0 / D);   // -(tr - tr_prev)/(d cs^2)
-    const double drho_d = drho_raw + 0.5 * ddr_d;                  // rho - rho0
+    const double drho_d = (double)drho_m + 0.5 * ddr_d;            // rho - rho0
     const double rho_d = p.rho0 + drho_d;
     const double inv_rho = 1.0 / rho_d;
     double ud[3] = {0, 0, 0};
 #pragma unroll
-    for (int c = 0; c < D; ++c) ud[c] = (jd[c] + 0.5 * p.f[c]) * inv_rho;
+    for (int c = 0; c < D; ++c) ud[c] = ((double)jd_m[c] + 0.5 * p.f[c]) * inv_rho;
     const T tr = (T)trd, ddr = (T)ddr_d, drho = (T)drho_d, rho = (T)rho_d;
     T u[3], f[3];
 #pragma unroll
-    for (int c = 0; c < 3; ++c) { u[c] = (T)ud[c]; f[c] = (T)p.f[c]; }
+    for (int c = 0; c < 3; ++c) { u[c] = (T)ud[c]; f[c] = chan_val<T>(p.f[c], p.f_f[c]); }
 #pragma unroll
     for (int c = 0; c < D; ++c) S[c][c] -= tr * T(1.0 / D);
     T uu = 0;
 #pragma unroll
     for (int c = 0; c < D; ++c) uu += u[c] * u[c];
-    const T omega = (T)p.omega;
+    const T omega = chan_val<T>(p.omega, p.omega_f);
     const T fpre = T(1) - T(0.5) * omega;
     // BGK relaxation to the second-order equilibrium plus the forcing of Eq. (bodyforce), regrouped per
     // node.  With X_ab = -ddr u_a u_b + u_b f_a + u_a f_b (its second-order forcing term), S traceless,
@@ -208,7 +206,7 @@ __global__ void __launch_bounds__(256) k_collide_stream(CollArgs<P> a, H h, Geom
     // as the compiler can tell, which would reload every field after each store
     const int cnx = p.nx, cny = p.ny, cnz = p.nz, coff = p.off;
     const bool cwz = p.wall_z != 0, cxbc = p.xbc != 0;
-    const T cdgh = (T)p.drho_gh;
+    const T cdgh = chan_val<T>(p.drho_gh, p.drho_gh_f);
 #pragma unroll
     for (int q = 0; q < Q; ++q) {
         const int cq[3] = {L::cx(q), L::cy(q), L::cz(q)};

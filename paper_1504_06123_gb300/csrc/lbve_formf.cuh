@@ -277,19 +277,19 @@ __global__ void __launch_bounds__(256, 2) k_sweep_f(CommitF<R> a, const long lon
 }
 
 // sigma_struc of a node from the chunk records: sum_j C_j M_j C_j^T with C_1 = 1 and C_{j+1} = C_j T_j (formed
-// in the history's arithmetic A, each chunk's term added in double), plus the point created now (E = 1,
-// weight 1/2, G = G_inf: (1/2) Dm(t)).
-template <int D, typename A, typename R>
-__device__ __forceinline__ void formf_sigma(const R* part, int S, long long Np, int n, const double* dnew, double G_inf,
-                                            double* sig) {
+// in the history's arithmetic A, each chunk's term added in the node arithmetic N), plus the point created
+// now (E = 1, weight 1/2, G = G_inf: (1/2) Dm(t)).
+template <int D, typename A, typename R, typename N>
+__device__ __forceinline__ void formf_sigma(const R* part, int S, long long Np, int n, const N* dnew, N G_inf,
+                                            N* sig) {
     constexpr int DD = D * D;
     constexpr int NS = D == 2 ? 3 : 6;
     A Z[DD];
-    double acc[NS];
+    N acc[NS];
 #pragma unroll
     for (int i = 0; i < DD; ++i) Z[i] = A(0);
 #pragma unroll
-    for (int i = 0; i < NS; ++i) acc[i] = 0.0;
+    for (int i = 0; i < NS; ++i) acc[i] = N(0);
 #pragma unroll 4
     for (int j = 0; j < S; ++j) {
         const R* pj = part + (long long)j * (NS + DD) * Np + n;
@@ -319,12 +319,12 @@ __device__ __forceinline__ void formf_sigma(const R* part, int S, long long Np, 
             A s = F[r * D + c];
 #pragma unroll
             for (int k = 0; k < D; ++k) s = ::fma(F[r * D + k], Z[c * D + k], s);
-            acc[i] += (double)s;
+            acc[i] += (N)s;
         }
         dev_product<D>(Z, T);
     }
 #pragma unroll
-    for (int i = 0; i < NS; ++i) sig[i] = G_inf * (acc[i] + 0.5 * dnew[i]);
+    for (int i = 0; i < NS; ++i) sig[i] = G_inf * (acc[i] + N(0.5) * dnew[i]);
 }
 
 // exp(kappa) - 1 of the new point's factor in the arithmetic A (Taylor to 4th order in float, 8th in double:
@@ -347,20 +347,21 @@ __device__ __forceinline__ void rate_of_strain(const double* ktd, double* dp) {
     }
 }
 
-template <int D, typename R>
-__device__ __forceinline__ void hist_commit_any(const CommitF<R>& a, const BlockStep* s_bs, long long Np, int n,
-                                                const double* /*kprev*/, const double* ktd, const Chan& p,
-                                                double* sig, long long /*t*/) {
+template <int D, typename R, typename N>
+__device__ __forceinline__ void hist_commit_any(Arith<N>, const CommitF<R>& a, const BlockStep* s_bs, long long Np,
+                                                int n, const double* /*kprev*/, const double* ktd, const Chan& p,
+                                                N* sig, long long /*t*/) {
     constexpr int DD = D * D;
     constexpr int NS = D == 2 ? 3 : 6;
     // the new point's stored values (rounded to the storage), used for its own contribution as for any point
     R Yn[DD];
-    double dn[NS];
+    double dd[NS];
+    N dn[NS];
     factor_dev<D, R>(ktd, Yn);
-    rate_of_strain<D>(ktd, dn);
+    rate_of_strain<D>(ktd, dd);
 #pragma unroll
-    for (int i = 0; i < NS; ++i) dn[i] = (double)(R)dn[i];
-    formf_sigma<D, R, R>(a.part, a.S, Np, n, dn, p.G_inf, sig);
+    for (int i = 0; i < NS; ++i) dn[i] = (N)(R)dd[i];
+    formf_sigma<D, R, R, N>(a.part, a.S, Np, n, dn, chan_val<N>(p.G_inf, p.G_inf_f), sig);
     // block merges, coarsest first (every ring slot is read before it is overwritten): the older point's
     // time, the factor F_newer F_older, the average of the two rates
     for (int bb = 1; bb < a.B; ++bb) {
@@ -387,7 +388,7 @@ __device__ __forceinline__ void hist_commit_any(const CommitF<R>& a, const Block
 #pragma unroll
     for (int c = 0; c < DD; ++c) a.Y[(dst * DD + c) * Np + n] = Yn[c];
 #pragma unroll
-    for (int c = 0; c < NS; ++c) a.Dm[(dst * NS + c) * Np + n] = (R)dn[c];
+    for (int c = 0; c < NS; ++c) a.Dm[(dst * NS + c) * Np + n] = (R)dd[c];
 }
 
 // ------------------------------------------------------------------------------------------------
@@ -423,6 +424,19 @@ struct CommitF16 {
     float* __restrict__ part;         // [S][NS + DD][Npad]
     int B, C, S;
 };
+template <> struct Hist16<CommitF16> { static constexpr bool value = true; };
+
+// Ranks ahead of the one in process whose blocks a warp asks the L2 to fetch (one bulk prefetch of 2048 bytes
+// per slot, issued by lane 0): the loads of those slots then hit the L2, and the DRAM requests in flight per
+// warp are not bounded by the two register buffers.
+#ifndef LBVE_F16_PREFETCH
+#define LBVE_F16_PREFETCH 4
+#endif
+
+// Bulk prefetch of [p, p + bytes) into the L2 (p and bytes multiples of 16; no completion to wait for).
+__device__ __forceinline__ void prefetch_l2_bulk(const void* p, unsigned bytes) {
+    asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(p), "r"(bytes) : "memory");
+}
 
 template <int D, int VN>
 __global__ void __launch_bounds__(256, 2) k_sweep_f16(CommitF16 a, const long long* __restrict__ t_dev, Geom g) {
@@ -512,14 +526,22 @@ __global__ void __launch_bounds__(256, 2) k_sweep_f16(CommitF16 a, const long lo
                 sym_integrand<D>(X[j], Dp[j], e.age, e.w, c1[j], c2[j], acc[j]);
             }
         };
-        // two slots of words alternate: the next slot's loads are in flight while a slot is processed
+        // two slots of words alternate: the next slot's loads are in flight while a slot is processed; the
+        // blocks of the ranks LBVE_F16_PREFETCH ahead are on their way to the L2
+        constexpr int PF = LBVE_F16_PREFETCH;
+        auto prefetch = [&](int r) {
+            if (PF > 0 && lane == 0 && r < r1) prefetch_l2_bulk(tbase + (long long)rt.e[r].slot * Lay::kBlock, Lay::kBlock);
+        };
+        for (int k = 2; k < PF; ++k) prefetch(r0 + k);
         unsigned wa[16], wb[16];
         if (r0 < r1) load(r0, wa);
         for (int r = r0; r < r1; r += 2) {
             if (r + 1 < r1) load(r + 1, wb);
+            prefetch(r + PF);
             process(r, wa);
             if (r + 1 >= r1) break;
             if (r + 2 < r1) load(r + 2, wa);
+            prefetch(r + 1 + PF);
             process(r + 1, wb);
         }
         float* out = a.part + (long long)chunk * (NS + DD) * Np + n0;
@@ -577,10 +599,10 @@ __device__ __forceinline__ void f16_put(const CommitF16& a, long long n, long lo
     *f16_byte<D>(a, n, l, IS_Y ? Lay::ye_byte(j) : Lay::de_byte(j)) = eb;
 }
 
-template <int D>
-__device__ __forceinline__ void hist_commit_any(const CommitF16& a, const BlockStep* s_bs, long long Np, int n,
-                                                const double* /*kprev*/, const double* ktd, const Chan& p,
-                                                double* sig, long long /*t*/) {
+template <int D, typename N>
+__device__ __forceinline__ void hist_commit_any(Arith<N>, const CommitF16& a, const BlockStep* s_bs, long long Np,
+                                                int n, const double* /*kprev*/, const double* ktd, const Chan& p,
+                                                N* sig, long long /*t*/) {
     constexpr int DD = D * D;
     constexpr int NS = D == 2 ? 3 : 6;
     float Yn[DD], dn[NS];
@@ -593,7 +615,7 @@ __device__ __forceinline__ void hist_commit_any(const CommitF16& a, const BlockS
     }
     // the new point as stored (encoded once): its own contribution from the stored, rounded rate
     const long long dst_new = (long long)(a.B - 1) * a.C + s_bs[a.B - 1].head_new;
-    double dstored[NS];
+    N dstored[NS];
     {
         unsigned short um[NS];
         unsigned char ue;
@@ -601,9 +623,9 @@ __device__ __forceinline__ void hist_commit_any(const CommitF16& a, const BlockS
         s16_encode<NS>(dn, um, &ue);
         s16_decode<NS>(um, ue, f);
 #pragma unroll
-        for (int i = 0; i < NS; ++i) dstored[i] = (double)f[i];
+        for (int i = 0; i < NS; ++i) dstored[i] = (N)f[i];
     }
-    formf_sigma<D, float, float>(a.part, a.S, Np, n, dstored, p.G_inf, sig);
+    formf_sigma<D, float, float, N>(a.part, a.S, Np, n, dstored, chan_val<N>(p.G_inf, p.G_inf_f), sig);
     for (int bb = 1; bb < a.B; ++bb) {
         const BlockStep& b = s_bs[bb];
         if (!b.evict) continue;

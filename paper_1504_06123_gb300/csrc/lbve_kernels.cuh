@@ -30,6 +30,8 @@
 #include <math.h>
 #include <stdint.h>
 
+#include <type_traits>
+
 #include "lbve_sched.cuh"
 
 namespace lbk {
@@ -89,7 +91,18 @@ struct Chan {
     double G_inf, inv_tau, inv_gc;
     int xbc;          // 1: pressure-step boundary along x
     double drho_gh;   // its ghost densities rho0 +- drho_gh (the linear profile of the pressure drop)
+    // the same values rounded to float, for the node arithmetic of float populations
+    float rho0_f, omega_f, f_f[3], G_inf_f, drho_gh_f;
 };
+
+// Node arithmetic type of the per-node kernels: the channel parameters in that type.
+template <typename T> __device__ __forceinline__ T chan_val(double d, float f);
+template <> __device__ __forceinline__ double chan_val<double>(double d, float) { return d; }
+template <> __device__ __forceinline__ float chan_val<float>(double, float f) { return f; }
+
+// Tag of the node arithmetic a history commit sums and returns sigma_struc in (double with double
+// populations, float with float populations).
+template <typename N> struct Arith {};
 
 struct Geom {
     int N;                 // all nodes of all channels
@@ -113,10 +126,50 @@ __device__ __forceinline__ void node_xyz(const Chan& c, int n, int& x, int& y, i
 // ------------------------------------------------------------------------------------------------
 // K1: raw moments -> u_raw
 // ------------------------------------------------------------------------------------------------
-// Moments are summed in double: exact for float populations up to the last bit of the result.
+// Zeroth and first moments of the (deviation-form) populations of one node in the type T.  In double the
+// sums run in q order.  In float the terms can be far larger than the sums (the even, stress-carrying parts
+// of opposite populations cancel in j, and their isotropic parts largely cancel in the mass), so the float
+// sums are formed without cancellation error: j from differences of opposite populations (exact when the two
+// are within a factor of two, i.e. when the even part dominates), the mass by compensated summation (each
+// addition's rounding error recovered exactly by the two-sum identity and carried along).
+template <int Q, typename T>
+__device__ __forceinline__ void node_moments(const T* v, T& drho, T* j) {
+    using L = Lattice<Q>;
+    constexpr int D = L::D;
+    drho = T(0);
+    j[0] = j[1] = j[2] = T(0);
+    if constexpr (sizeof(T) == 8) {
+#pragma unroll
+        for (int q = 0; q < Q; ++q) {
+            drho += v[q];
+            if (L::cx(q)) j[0] += L::cx(q) * v[q];
+            if (L::cy(q)) j[1] += L::cy(q) * v[q];
+            if (D == 3 && L::cz(q)) j[2] += L::cz(q) * v[q];
+        }
+    } else {
+        T c = T(0);
+#pragma unroll
+        for (int q = 0; q < Q; ++q) {
+            const T t = drho + v[q];
+            const T z = t - drho;
+            c += (drho - (t - z)) + (v[q] - z);
+            drho = t;
+        }
+        drho += c;
+#pragma unroll
+        for (int q = 0; q < Q; ++q) {   // each pair (q, opposite of q) once, from its member with c_a = +1
+            const T d = v[q] - v[L::opp(q)];
+            if (L::cx(q) > 0) j[0] += d;
+            if (L::cy(q) > 0) j[1] += d;
+            if (D == 3 && L::cz(q) > 0) j[2] += d;
+        }
+    }
+}
+
 // The first kernel of a step also advances the device step counter (it starts at -1), so that the later
 // kernels of the step all read the same t.
-template <int Q, typename P>
+// M: arithmetic of the moments (float only for float populations with the 16-bit history).
+template <int Q, typename P, typename M>
 __global__ void __launch_bounds__(256) k_moments(const P* __restrict__ dn, double* __restrict__ u_raw, Geom g,
                                                  long long* t_dev) {
     using L = Lattice<Q>;
@@ -125,18 +178,13 @@ __global__ void __launch_bounds__(256) k_moments(const P* __restrict__ dn, doubl
     if (n == 0) *t_dev += 1;
     if (n >= g.N) return;
     const Chan& p = g.ch[chan_index(g, n)];
-    double drho = 0, j[3] = {0, 0, 0};
+    M v[Q], drho, j[3];
 #pragma unroll
-    for (int q = 0; q < Q; ++q) {
-        const double v = (double)dn[(long long)q * g.Npad + n];
-        drho += v;
-        if (L::cx(q)) j[0] += L::cx(q) * v;
-        if (L::cy(q)) j[1] += L::cy(q) * v;
-        if (D == 3 && L::cz(q)) j[2] += L::cz(q) * v;
-    }
-    const double inv = 1.0 / (p.rho0 + drho);
+    for (int q = 0; q < Q; ++q) v[q] = (M)dn[(long long)q * g.Npad + n];
+    node_moments<Q, M>(v, drho, j);
+    const M inv = M(1) / (chan_val<M>(p.rho0, p.rho0_f) + drho);
 #pragma unroll
-    for (int a = 0; a < D; ++a) u_raw[(long long)a * g.Npad + n] = (j[a] + 0.5 * p.f[a]) * inv;
+    for (int a = 0; a < D; ++a) u_raw[(long long)a * g.Npad + n] = (double)((j[a] + M(0.5) * chan_val<M>(p.f[a], p.f_f[a])) * inv);
 }
 
 // ------------------------------------------------------------------------------------------------
@@ -548,33 +596,33 @@ __device__ __forceinline__ double shear_rate_d(const double* k) {
     return sqrt(0.5 * trD2);
 }
 
-template <int D, typename R>
+template <int D, typename R, typename N>
 __device__ __forceinline__ void hist_commit(const CommitArgs<R>& a, const BlockStep* s_bs, long long Np, int n,
-                                            const double* ktd, double G_inf, double* sig /* [NS] out */) {
+                                            const double* ktd, N G_inf, N* sig /* [NS] out */) {
     constexpr int DD = D * D;
     constexpr int NS = D == 2 ? 3 : 6;
-    double acc[NS];
+    N acc[NS];
 #pragma unroll
-    for (int i = 0; i < NS; ++i) acc[i] = 0.0;
+    for (int i = 0; i < NS; ++i) acc[i] = N(0);
 #pragma unroll 4
     for (int c = 0; c < a.S; ++c)
 #pragma unroll
-        for (int i = 0; i < NS; ++i) acc[i] += (double)a.part[((long long)c * NS + i) * Np + n];
+        for (int i = 0; i < NS; ++i) acc[i] += (N)a.part[((long long)c * NS + i) * Np + n];
     // the new point, summed in the history's precision like every other point
     R kt[DD];
 #pragma unroll
     for (int c = 0; c < DD; ++c) kt[c] = (R)ktd[c];
     if (D == 2) {
-        acc[0] += (double)(R(0.5) * (kt[0] + kt[0]));
-        acc[1] += (double)(R(0.5) * (kt[3] + kt[3]));
-        acc[2] += (double)(R(0.5) * (kt[1] + kt[2]));
+        acc[0] += (N)(R(0.5) * (kt[0] + kt[0]));
+        acc[1] += (N)(R(0.5) * (kt[3] + kt[3]));
+        acc[2] += (N)(R(0.5) * (kt[1] + kt[2]));
     } else {
-        acc[0] += (double)(R(0.5) * (kt[0] + kt[0]));
-        acc[1] += (double)(R(0.5) * (kt[4] + kt[4]));
-        acc[2] += (double)(R(0.5) * (kt[8] + kt[8]));
-        acc[3] += (double)(R(0.5) * (kt[1] + kt[3]));
-        acc[4] += (double)(R(0.5) * (kt[2] + kt[6]));
-        acc[5] += (double)(R(0.5) * (kt[5] + kt[7]));
+        acc[0] += (N)(R(0.5) * (kt[0] + kt[0]));
+        acc[1] += (N)(R(0.5) * (kt[4] + kt[4]));
+        acc[2] += (N)(R(0.5) * (kt[8] + kt[8]));
+        acc[3] += (N)(R(0.5) * (kt[1] + kt[3]));
+        acc[4] += (N)(R(0.5) * (kt[2] + kt[6]));
+        acc[5] += (N)(R(0.5) * (kt[5] + kt[7]));
     }
 #pragma unroll
     for (int i = 0; i < NS; ++i) sig[i] = G_inf * acc[i];
@@ -607,12 +655,13 @@ __device__ __forceinline__ void hist_commit(const CommitArgs<R>& a, const BlockS
 }
 
 // Uniform entry for every history storage: kprev = kappa(t-1) of the node (the node kappa field before
-// this step overwrites it), used by storages that keep a per-node frame.
-template <int D, typename R>
-__device__ __forceinline__ void hist_commit_any(const CommitArgs<R>& a, const BlockStep* s_bs, long long Np, int n,
-                                                const double* /*kprev*/, const double* ktd, const Chan& p,
-                                                double* sig, long long /*t*/) {
-    hist_commit<D, R>(a, s_bs, Np, n, ktd, p.G_inf, sig);
+// this step overwrites it), used by storages that keep a per-node frame; sigma_struc(t) summed and returned
+// in the node arithmetic N.
+template <int D, typename R, typename N>
+__device__ __forceinline__ void hist_commit_any(Arith<N>, const CommitArgs<R>& a, const BlockStep* s_bs, long long Np,
+                                                int n, const double* /*kprev*/, const double* ktd, const Chan& p,
+                                                N* sig, long long /*t*/) {
+    hist_commit<D, R, N>(a, s_bs, Np, n, ktd, chan_val<N>(p.G_inf, p.G_inf_f), sig);
 }
 
 // ------------------------------------------------------------------------------------------------
@@ -688,6 +737,10 @@ struct CommitS16 {
     int B, C, S, TB;
 };
 
+// History storages whose node sums may run in float with float populations (the 16-bit forms).
+template <class H> struct Hist16 { static constexpr bool value = false; };
+template <> struct Hist16<CommitS16> { static constexpr bool value = true; };
+
 // R - 1 of the frame after step t: exp(kappa(t-1)) R(t-1) - 1 = A + Rm + A Rm.
 template <int D>
 __device__ __forceinline__ void frame_advance(const double* kprev, const float* Rm, float* Rn) {
@@ -741,9 +794,9 @@ __device__ __forceinline__ void frame_inverse_dev(const float* M, float* X) {
 // sigma of a node from the frame-free sum: the sweep accumulates P = sum w G (Q kappa Q^T + (.)^T) (packed
 // symmetric, NS components); since every point of the node sees the same frame, the sum with
 // E = R Q is R P R^T.
-template <int D>
-__device__ __forceinline__ void frame_apply(const float* Rm, const double* p, double* out) {
-    double P[D][D], R[D][D], RP[D][D];
+template <int D, typename N>
+__device__ __forceinline__ void frame_apply(const float* Rm, const N* p, N* out) {
+    N P[D][D], R[D][D], RP[D][D];
     if (D == 2) {
         P[0][0] = p[0]; P[1][1] = p[1]; P[0][1] = P[1][0] = p[2];
     } else {
@@ -753,22 +806,22 @@ __device__ __forceinline__ void frame_apply(const float* Rm, const double* p, do
 #pragma unroll
     for (int r = 0; r < D; ++r)
 #pragma unroll
-        for (int c = 0; c < D; ++c) R[r][c] = (double)Rm[r * D + c] + (r == c ? 1.0 : 0.0);
+        for (int c = 0; c < D; ++c) R[r][c] = (N)Rm[r * D + c] + (r == c ? N(1) : N(0));
 #pragma unroll
     for (int r = 0; r < D; ++r)
 #pragma unroll
         for (int c = 0; c < D; ++c) {
-            double acc = 0.0;
+            N acc = N(0);
 #pragma unroll
             for (int k = 0; k < D; ++k) acc += R[r][k] * P[k][c];
             RP[r][c] = acc;
         }
-    double S[D][D];
+    N S[D][D];
 #pragma unroll
     for (int r = 0; r < D; ++r)
 #pragma unroll
         for (int c = 0; c < D; ++c) {
-            double acc = 0.0;
+            N acc = N(0);
 #pragma unroll
             for (int k = 0; k < D; ++k) acc += RP[r][k] * R[c][k];
             S[r][c] = acc;
@@ -781,11 +834,11 @@ __device__ __forceinline__ void frame_apply(const float* Rm, const double* p, do
     }
 }
 
-template <int D>
-__device__ __forceinline__ void hist_commit_any(const CommitS16& a, const BlockStep* s_bs, long long Np, int n,
-                                                const double* kprev, const double* ktd, const Chan& p,
-                                                double* sig, long long t) {
-    const double G_inf = p.G_inf;
+template <int D, typename N>
+__device__ __forceinline__ void hist_commit_any(Arith<N>, const CommitS16& a, const BlockStep* s_bs, long long Np,
+                                                int n, const double* kprev, const double* ktd, const Chan& p,
+                                                N* sig, long long t) {
+    const N G_inf = chan_val<N>(p.G_inf, p.G_inf_f);
     constexpr int DD = D * D;
     constexpr int NS = D == 2 ? 3 : 6;
     // the frame of this step (identical arithmetic to the sweep's rebase path), then the rebase
@@ -796,14 +849,14 @@ __device__ __forceinline__ void hist_commit_any(const CommitS16& a, const BlockS
     const bool rebase = (t % a.TB) == 0;
     // sigma: R (sum of chunk partials) R^T + the point created now (its stored, rounded kappa; E = 1,
     // weight 1/2)
-    double acc[NS], P[NS];
+    N acc[NS], P[NS];
 #pragma unroll
-    for (int i = 0; i < NS; ++i) P[i] = 0.0;
+    for (int i = 0; i < NS; ++i) P[i] = N(0);
 #pragma unroll 4
     for (int c = 0; c < a.S; ++c)
 #pragma unroll
-        for (int i = 0; i < NS; ++i) P[i] += (double)a.part[((long long)c * NS + i) * Np + n];
-    frame_apply<D>(Rn, P, acc);
+        for (int i = 0; i < NS; ++i) P[i] += (N)a.part[((long long)c * NS + i) * Np + n];
+    frame_apply<D, N>(Rn, P, acc);
     float kt[DD];
     unsigned short km[DD];
     unsigned char ke;
@@ -812,16 +865,16 @@ __device__ __forceinline__ void hist_commit_any(const CommitS16& a, const BlockS
     s16_encode<DD>(kt, km, &ke);
     s16_decode<DD>(km, ke, kt);
     if (D == 2) {
-        acc[0] += (double)(0.5f * (kt[0] + kt[0]));
-        acc[1] += (double)(0.5f * (kt[3] + kt[3]));
-        acc[2] += (double)(0.5f * (kt[1] + kt[2]));
+        acc[0] += (N)(0.5f * (kt[0] + kt[0]));
+        acc[1] += (N)(0.5f * (kt[3] + kt[3]));
+        acc[2] += (N)(0.5f * (kt[1] + kt[2]));
     } else {
-        acc[0] += (double)(0.5f * (kt[0] + kt[0]));
-        acc[1] += (double)(0.5f * (kt[4] + kt[4]));
-        acc[2] += (double)(0.5f * (kt[8] + kt[8]));
-        acc[3] += (double)(0.5f * (kt[1] + kt[3]));
-        acc[4] += (double)(0.5f * (kt[2] + kt[6]));
-        acc[5] += (double)(0.5f * (kt[5] + kt[7]));
+        acc[0] += (N)(0.5f * (kt[0] + kt[0]));
+        acc[1] += (N)(0.5f * (kt[4] + kt[4]));
+        acc[2] += (N)(0.5f * (kt[8] + kt[8]));
+        acc[3] += (N)(0.5f * (kt[1] + kt[3]));
+        acc[4] += (N)(0.5f * (kt[2] + kt[6]));
+        acc[5] += (N)(0.5f * (kt[5] + kt[7]));
     }
 #pragma unroll
     for (int i = 0; i < NS; ++i) sig[i] = G_inf * acc[i];
@@ -1066,7 +1119,7 @@ __global__ void __launch_bounds__(256) k_commit(H a, const double* __restrict__ 
         ktd[c] = kappa_in[(long long)c * g.N + n];
         kprev[c] = kappa_f[c * g.Npad + n];
     }
-    hist_commit_any<D>(a, s_bs, g.Npad, n, kprev, ktd, g.ch[chan_index(g, n)], sig, t);
+    hist_commit_any<D>(Arith<double>(), a, s_bs, g.Npad, n, kprev, ktd, g.ch[chan_index(g, n)], sig, t);
 #pragma unroll
     for (int i = 0; i < NS; ++i) {
         sigma_f[i * g.Npad + n] = sig[i];

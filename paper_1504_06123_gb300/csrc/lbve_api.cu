@@ -85,6 +85,7 @@ struct lbve {
     int sweep_grid_full = 0;   // resident CTAs of the sweep on this device (SMs x CTAs per SM)
     int tuned_from_cache = 0;  // 1: the launch shape came from an earlier handle of the same shape
     int part_S = 0;            // slot chunks the partial-sum buffer holds
+    int node_tpb = 256;        // threads per block of the per-node kernels (moments, commit + collide)
     long long* t_dev = nullptr;
     double* red = nullptr;     // reduction scratch (2 doubles)
     double* stage = nullptr;   // lbve_fields staging for host destinations
@@ -455,7 +456,7 @@ int sweep_autotune(lbve* h) {
         cand.push_back({cta, S});
     };
     // task counts just above and just below k waves of the resident warps (CTAs)
-    for (long long k : {2, 4, 8, 16, 32}) {
+    for (long long k : {1, 2, 4, 8, 16, 32}) {
         add(0, (k * warps + tiles - 1) / tiles);
         add(0, k * warps / tiles);
     }
@@ -496,9 +497,9 @@ int sweep_autotune(lbve* h) {
             for (int r = 0; r < reps; ++r) {
                 if ((rc = launch_sweep_any<D, HK>(h, 0))) return rc;
                 if (h->hist_dbl)
-                    k_part_read<double><<<(h->N + 255) / 256, 256>>>((const double*)h->part, (int)c.S, h->part_ns, h->Npad, h->N, h->red);
+                    k_part_read<double><<<(h->N + h->node_tpb - 1) / h->node_tpb, h->node_tpb>>>((const double*)h->part, (int)c.S, h->part_ns, h->Npad, h->N, h->red);
                 else
-                    k_part_read<float><<<(h->N + 255) / 256, 256>>>((const float*)h->part, (int)c.S, h->part_ns, h->Npad, h->N, h->red);
+                    k_part_read<float><<<(h->N + h->node_tpb - 1) / h->node_tpb, h->node_tpb>>>((const float*)h->part, (int)c.S, h->part_ns, h->Npad, h->N, h->red);
                 LBVE_CUDA(cudaGetLastError());
             }
             LBVE_CUDA(cudaEventRecord(e1, 0));
@@ -555,13 +556,14 @@ template <int Q, typename P, int HK, typename T>
 int one_step(lbve* h, int cur, cudaStream_t s) {
     constexpr int D = Lattice<Q>::D;
     const Geom g = geom_of(h);
-    const int grid = (h->N + 255) / 256;
+    const int tpb = h->node_tpb;
+    const int grid = (h->N + tpb - 1) / tpb;
     const P* din = (const P*)h->pops[cur];
     P* dout = (P*)h->pops[cur ^ 1];
     int rc;
     if ((rc = prof_mark(h, s, KIND_MOMENTS, true))) return rc;
     using M = typename std::conditional<sizeof(P) == 4 && (HK == 2 || HK == 6), float, double>::type;
-    k_moments<Q, P, M><<<grid, 256, 0, s>>>(din, (double*)h->u_raw, g, h->t_dev);
+    k_moments<Q, P, M><<<grid, tpb, 0, s>>>(din, (double*)h->u_raw, g, h->t_dev);
     LBVE_CUDA(cudaGetLastError());
     if ((rc = prof_mark(h, s, KIND_MOMENTS, false))) return rc;
     if (HK != 3) {
@@ -580,13 +582,13 @@ int one_step(lbve* h, int cur, cudaStream_t s) {
     c.u = (double*)h->u;
     c.t_dev = h->t_dev;
     if ((rc = prof_mark(h, s, KIND_COLLIDE, true))) return rc;
-    if (HK == 3) k_collide_stream<Q, P, T, Instant<T>><<<grid, 256, 0, s>>>(c, Instant<T>{1, 4}, g);
-    else if (HK == 6) k_collide_stream<Q, P, T, CommitF16><<<grid, 256, 0, s>>>(c, commit_f16(h), g);
-    else if (HK == 5) k_collide_stream<Q, P, T, CommitF<double>><<<grid, 256, 0, s>>>(c, commit_f<double>(h), g);
-    else if (HK == 4) k_collide_stream<Q, P, T, CommitF<float>><<<grid, 256, 0, s>>>(c, commit_f<float>(h), g);
-    else if (HK == 2) k_collide_stream<Q, P, T, CommitS16><<<grid, 256, 0, s>>>(c, commit_s16(h), g);
-    else if (HK == 1) k_collide_stream<Q, P, T, CommitArgs<double>><<<grid, 256, 0, s>>>(c, commit_args<double>(h), g);
-    else k_collide_stream<Q, P, T, CommitArgs<float>><<<grid, 256, 0, s>>>(c, commit_args<float>(h), g);
+    if (HK == 3) k_collide_stream<Q, P, T, Instant<T>><<<grid, tpb, 0, s>>>(c, Instant<T>{1, 4}, g);
+    else if (HK == 6) k_collide_stream<Q, P, T, CommitF16><<<grid, tpb, 0, s>>>(c, commit_f16(h), g);
+    else if (HK == 5) k_collide_stream<Q, P, T, CommitF<double>><<<grid, tpb, 0, s>>>(c, commit_f<double>(h), g);
+    else if (HK == 4) k_collide_stream<Q, P, T, CommitF<float>><<<grid, tpb, 0, s>>>(c, commit_f<float>(h), g);
+    else if (HK == 2) k_collide_stream<Q, P, T, CommitS16><<<grid, tpb, 0, s>>>(c, commit_s16(h), g);
+    else if (HK == 1) k_collide_stream<Q, P, T, CommitArgs<double>><<<grid, tpb, 0, s>>>(c, commit_args<double>(h), g);
+    else k_collide_stream<Q, P, T, CommitArgs<float>><<<grid, tpb, 0, s>>>(c, commit_args<float>(h), g);
     LBVE_CUDA(cudaGetLastError());
     if ((rc = prof_mark(h, s, KIND_COLLIDE, false))) return rc;
     if (h->probe_n > 0) {
@@ -837,6 +839,24 @@ int create_impl(const lbve_channel_desc* descs, int32_t n, const double* rho_ini
     h->Q = desc->lattice;
     h->NS = h->D == 2 ? 3 : 6;
     h->N = (int)Ntot;
+    {   // Block size of the per-node kernels.  Few nodes: blocks of fewer threads spread them over more SMs
+        // (their FP64 work completes a warp instruction in active lanes / 2 cycles).  More nodes: the
+        // largest block (<= 256) whose last wave of blocks over the SMs is at least 90 % full, so that no
+        // SM holds twice the work of another.  A failed query keeps 256 (the allocations below report a
+        // broken device).
+        int dev = 0, sms = 0;
+        if (cudaGetDevice(&dev) == cudaSuccess &&
+            cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) == cudaSuccess && sms > 0) {
+            int tpb = 1;
+            while (tpb < 32 && (h->N + tpb - 1) / tpb > sms) tpb *= 2;
+            if (tpb == 32 && (h->N + 31) / 32 > sms)
+                for (int b = 256; b >= 32; b /= 2) {
+                    const double waves = (double)((h->N + b - 1) / b) / sms;
+                    if (b == 32 || std::ceil(waves) <= 1.1 * waves) { tpb = b; break; }
+                }
+            h->node_tpb = tpb;
+        }
+    }
     h->model = desc->model;
     h->L = desc->model == LBVE_MODEL_INLM ? 0 : desc->hist_C * desc->hist_B;   // the instantaneous model keeps no history
     h->Npad = ((long long)h->N + 127) / 128 * 128;
@@ -1739,7 +1759,7 @@ int backward_impl(lbve* h, const double* dL_du, const double* dL_ds, double* gra
         for (int64_t t = t1 - 1; t >= t0; --t) {
             const char* slot = (const char*)tape.p + step_b * (size_t)(t - t0);
             const TP* pops_t = (const TP*)slot;
-            k_moments<Q, TP, double><<<(h->N + 255) / 256, 256, 0, st>>>(pops_t, (double*)ur.p, g, (long long*)cnt.p);
+            k_moments<Q, TP, double><<<(h->N + h->node_tpb - 1) / h->node_tpb, h->node_tpb, 0, st>>>(pops_t, (double*)ur.p, g, (long long*)cnt.p);
             LBVE_SEG(cudaGetLastError());
             AdjArgs<TP, TH> a;
             a.n = pops_t;

@@ -190,13 +190,49 @@ template <typename TP, typename TH> struct AdjArgs {
     double* lam_theta;      // [4][Npad] += per-node parts of dL/dtheta
     const double* seed_u;   // [D][Npad] dL/du of this step's velocity (last step), or nullptr
     const double* seed_s;   // [NS][Npad] dL/dsigma of this step (last step), or nullptr
-    double* part_sig;       // [S][NS][Npad] k_adj_sig: partial sums of the forward integrand
+    double* part_sig;       // [SG][NS][Npad] k_adj_sig: partial sums of the forward integrand per chunk group
     double* lt;             // [DD][Npad] pairing matrix of lambda(sigma_struc) / G_inf-scaled (k_adj_node)
-    double* part_adj;       // [S][DD + 2][Npad] k_adj_hist: partial lambda(A), lambda(1/tau), lambda(1/gamma_c)
+    double* part_adj;       // [SG][DD + 2][Npad] k_adj_hist: partial lambda(A), lambda(1/tau), lambda(1/gamma_c)
     long long t_off;        // step t = *t0 + t_off (the segment's first step lives in device memory, so that
     const long long* t0;    // one captured graph serves every segment)
     int B, C, S;            // history grid; S slot chunks of the split kernels
+    int cpb, SG;            // chunks per block of the split kernels (a power of two <= 16) and chunk groups
 };
+
+// Thread -> (node, chunk) of the split kernels: a block of 128 threads holds G = 128 / cpb nodes x cpb
+// chunks, consecutive threads on consecutive nodes of one chunk; block b covers node group b % (Npad / G)
+// and chunk group b / (Npad / G).  The block adds its cpb chunks of every node itself (chunk_group_sum), so
+// that the per-node FP64 kernels add SG = S / cpb group sums instead of S chunk sums.
+struct SplitIdx { int n, chunk, nl, cl, G, group; };
+__device__ inline SplitIdx split_idx(int cpb, long long Npad) {
+    SplitIdx x;
+    x.G = blockDim.x / cpb;
+    x.nl = threadIdx.x % x.G;
+    x.cl = threadIdx.x / x.G;
+    const int ngroups = (int)(Npad / x.G);
+    x.group = blockIdx.x / ngroups;
+    x.n = (blockIdx.x % ngroups) * x.G + x.nl;
+    x.chunk = x.group * cpb + x.cl;
+    return x;
+}
+
+// Sum of the M values v of the block's cpb chunks of each node, by a fixed pairwise tree in shared memory
+// (s_red: blockDim.x * M doubles); every thread of the block calls it; the sums are valid in the threads of
+// chunk cl = 0 (returned in v).
+template <int M>
+__device__ inline void chunk_group_sum(double* s_red, const SplitIdx& x, int cpb, double* v) {
+#pragma unroll
+    for (int i = 0; i < M; ++i) s_red[threadIdx.x * M + i] = v[i];
+    __syncthreads();
+    for (int st = cpb / 2; st >= 1; st /= 2) {
+        if (x.cl < st)
+#pragma unroll
+            for (int i = 0; i < M; ++i) s_red[threadIdx.x * M + i] += s_red[(threadIdx.x + st * x.G) * M + i];
+        __syncthreads();
+    }
+#pragma unroll
+    for (int i = 0; i < M; ++i) v[i] = s_red[threadIdx.x * M + i];
+}
 
 // Slot range [l0, l1) of chunk `chunk` of S over Ls slots.
 __device__ inline void adj_chunk(int Ls, int S, int chunk, int* l0, int* l1) {
@@ -237,19 +273,20 @@ __global__ void __launch_bounds__(128) k_adj_sig(AdjArgs<TP, TH> a, Geom g, AdjP
     int* s_part = reinterpret_cast<int*>(s_w + Ls);
     BlockStep* s_bs = reinterpret_cast<BlockStep*>(s_part + Ls);
     adj_table(a, s_age, s_w, s_part, s_bs);
-    const long long idx = blockIdx.x * (long long)blockDim.x + threadIdx.x;
-    const int n = (int)(idx % g.Npad), chunk = (int)(idx / g.Npad);
-    if (chunk >= a.S || n >= g.N) return;
+    __shared__ double s_red[128 * NS];
+    const SplitIdx x = split_idx(a.cpb, g.Npad);
+    const int n = x.n, chunk = x.chunk;
+    const bool active = chunk < a.S && n < g.N;
     const long long Np = g.Npad;
     using R = TH;   // the forward sweep's arithmetic
     const long long s_last = (long long)(a.B - 1) * a.C + s_bs[a.B - 1].head_prev;
     R kl[DD], A[DD];
-    for (int c = 0; c < DD; ++c) kl[c] = a.K[(s_last * DD + c) * Np + n];
+    for (int c = 0; c < DD; ++c) kl[c] = active ? a.K[(s_last * DD + c) * Np + n] : R(0);
     expm1_mat<D, R>(kl, A);
     R acc[NS];
     for (int i = 0; i < NS; ++i) acc[i] = 0;
-    int l0, l1;
-    adj_chunk(Ls, a.S, chunk, &l0, &l1);
+    int l0 = 0, l1 = 0;
+    if (active) adj_chunk(Ls, a.S, chunk, &l0, &l1);
     for (int l = l0; l < l1; ++l) {
         const float w = s_w[l];
         if (w == 0.0f) continue;
@@ -263,7 +300,11 @@ __global__ void __launch_bounds__(128) k_adj_sig(AdjArgs<TP, TH> a, Geom g, AdjP
             for (int c = 0; c < DD; ++c) kap[c] = R(0.5) * (kap[c] + a.K[((long long)part * DD + c) * Np + n]);
         point_update<D, R>(Xl, A, kap, (R)s_age[l], (R)w, (R)p.inv_tau, (R)p.inv_gc, acc);
     }
-    for (int i = 0; i < NS; ++i) a.part_sig[((long long)chunk * NS + i) * Np + n] = (double)acc[i];
+    double v[NS];
+    for (int i = 0; i < NS; ++i) v[i] = (double)acc[i];
+    chunk_group_sum<NS>(s_red, x, a.cpb, v);
+    if (x.cl == 0 && n < g.N)
+        for (int i = 0; i < NS; ++i) a.part_sig[((long long)x.group * NS + i) * Np + n] = v[i];
 }
 
 template <int Q, typename TP, typename TH>
@@ -294,8 +335,8 @@ __global__ void __launch_bounds__(32) k_adj_node(AdjArgs<TP, TH> a, Geom g, AdjP
     kappa_fd<D>(a.u_raw, Np, ch, n, kt);
     double acc[NS];   // the history sum of step t (k_adj_sig's chunks, in chunk order)
     for (int i = 0; i < NS; ++i) acc[i] = 0.0;
-#pragma unroll 16   // the chunks' loads in flight together (the additions keep their order)
-    for (int c = 0; c < a.S; ++c)
+#pragma unroll 16   // the groups' loads in flight together (the additions keep their order)
+    for (int c = 0; c < a.SG; ++c)
 #pragma unroll
         for (int i = 0; i < NS; ++i) acc[i] += a.part_sig[((long long)c * NS + i) * Np + n];
     double newp[NS];   // the point created now: (kappa + kappa^T)/2 packed
@@ -489,22 +530,23 @@ __global__ void __launch_bounds__(128) k_adj_hist(AdjArgs<TP, TH> a, Geom g, Adj
     int* s_part = reinterpret_cast<int*>(s_w + Ls);
     BlockStep* s_bs = reinterpret_cast<BlockStep*>(s_part + Ls);
     adj_table(a, s_age, s_w, s_part, s_bs);
-    const long long idx = blockIdx.x * (long long)blockDim.x + threadIdx.x;
-    const int n = (int)(idx % g.Npad), chunk = (int)(idx / g.Npad);
-    if (chunk >= a.S || n >= g.N) return;
+    __shared__ double s_red[128 * (DD + 2)];
+    const SplitIdx x = split_idx(a.cpb, g.Npad);
+    const int n = x.n, chunk = x.chunk;
+    const bool active = chunk < a.S && n < g.N;
     const long long Np = g.Npad;
     using R = TH;   // the forward sweep's arithmetic; the chunk's rate parts in double
     const long long s_last = (long long)(a.B - 1) * a.C + s_bs[a.B - 1].head_prev;
     R kl[DD], A[DD], Lt[DD], lamA[DD];
     for (int c = 0; c < DD; ++c) {
-        kl[c] = a.K[(s_last * DD + c) * Np + n];
-        Lt[c] = (R)a.lt[c * Np + n];
+        kl[c] = active ? a.K[(s_last * DD + c) * Np + n] : R(0);
+        Lt[c] = active ? (R)a.lt[c * Np + n] : R(0);
         lamA[c] = 0;
     }
     expm1_mat<D, R>(kl, A);
     double lam_it = 0.0, lam_ig = 0.0;
-    int l0, l1;
-    adj_chunk(Ls, a.S, chunk, &l0, &l1);
+    int l0 = 0, l1 = 0;
+    if (active) adj_chunk(Ls, a.S, chunk, &l0, &l1);
     for (int l = l0; l < l1; ++l) {
         const float w = s_w[l];
         if (w == 0.0f) continue;
@@ -549,10 +591,15 @@ __global__ void __launch_bounds__(128) k_adj_hist(AdjArgs<TP, TH> a, Geom g, Adj
             for (int c = 0; c < DD; ++c) a.lamK[((long long)l * DD + c) * Np + n] += lk[c];
         }
     }
-    double* out = a.part_adj + (long long)chunk * (DD + 2) * Np + n;
-    for (int c = 0; c < DD; ++c) out[c * Np] = (double)lamA[c];
-    out[DD * Np] = lam_it;
-    out[(DD + 1) * Np] = lam_ig;
+    double v[DD + 2];
+    for (int c = 0; c < DD; ++c) v[c] = (double)lamA[c];
+    v[DD] = lam_it;
+    v[DD + 1] = lam_ig;
+    chunk_group_sum<DD + 2>(s_red, x, a.cpb, v);
+    if (x.cl == 0 && n < g.N) {
+        double* out = a.part_adj + (long long)x.group * (DD + 2) * Np + n;
+        for (int c = 0; c < DD + 2; ++c) out[c * Np] = v[c];
+    }
 }
 
 // The chunk sums of k_adj_hist (chunk order), the adjoint of A = exp(kappa(t-1)) - 1 (kappa(t-1) is the kappa
@@ -568,8 +615,8 @@ __global__ void __launch_bounds__(32) k_adj_fin(AdjArgs<TP, TH> a, Geom g, AdjPa
     const long long Np = g.Npad;
     double lamA[DD], lam_it = 0.0, lam_ig = 0.0;
     for (int c = 0; c < DD; ++c) lamA[c] = 0.0;
-#pragma unroll 16   // the chunks' loads in flight together (the additions keep their order)
-    for (int ch = 0; ch < a.S; ++ch) {
+#pragma unroll 16   // the groups' loads in flight together (the additions keep their order)
+    for (int ch = 0; ch < a.SG; ++ch) {
         const double* in = a.part_adj + (long long)ch * (DD + 2) * Np + n;
         for (int c = 0; c < DD; ++c) lamA[c] += in[c * Np];
         lam_it += in[DD * Np];

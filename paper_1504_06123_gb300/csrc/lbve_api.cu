@@ -1724,11 +1724,14 @@ int backward_impl(lbve* h, const double* dL_du, const double* dL_ds, double* gra
     while (tpb < 32 && (h->N + tpb - 1) / tpb > sms) tpb *= 2;
     const int gridn = (h->N + tpb - 1) / tpb;
     const size_t smem = sweep_smem_bytes(h->L);
-    if (smem > 48 * 1024) {
+    if (smem > 32 * 1024) {   // the split kernels also hold up to 11 KB of static shared memory (their chunk sums)
         LBVE_CUDA(cudaFuncSetAttribute(k_adj_sig<D, TP, TH>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
         LBVE_CUDA(cudaFuncSetAttribute(k_adj_hist<D, TP, TH>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
     }
-    const int grid_chunks = (int)(((long long)S * Np + 127) / 128);
+    int cpb = 1;   // chunks a block of the split kernels adds itself (a power of two <= 16, <= S)
+    while (cpb * 2 <= std::min(16, S)) cpb *= 2;
+    const int SG = (S + cpb - 1) / cpb;
+    const int grid_chunks = (int)((long long)SG * (Np / (128 / cpb)));
     DevBuf t0buf;   // the first step of the segment being processed (read by the adjoint kernels)
     if ((rc = t0buf.get(h, sizeof(long long)))) return rc;
     long long* t0dev = (long long*)t0buf.p;
@@ -1784,6 +1787,8 @@ int backward_impl(lbve* h, const double* dL_du, const double* dL_ds, double* gra
             a.B = h->d.hist_B;
             a.C = h->d.hist_C;
             a.S = S;
+            a.cpb = cpb;
+            a.SG = SG;
             k_adj_sig<D, TP, TH><<<grid_chunks, 128, smem, st>>>(a, g, p);
             LBVE_SEG(cudaGetLastError());
             k_adj_node<Q, TP, TH><<<gridn, tpb, 0, st>>>(a, g, p);

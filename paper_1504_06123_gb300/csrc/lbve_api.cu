@@ -496,10 +496,13 @@ int sweep_autotune(lbve* h) {
             LBVE_CUDA(cudaEventRecord(e0, 0));
             for (int r = 0; r < reps; ++r) {
                 if ((rc = launch_sweep_any<D, HK>(h, 0))) return rc;
+                const int pg = (h->N + h->node_tpb - 1) / h->node_tpb;
                 if (h->hist_dbl)
-                    k_part_read<double><<<(h->N + h->node_tpb - 1) / h->node_tpb, h->node_tpb>>>((const double*)h->part, (int)c.S, h->part_ns, h->Npad, h->N, h->red);
+                    k_part_read<double, double><<<pg, h->node_tpb>>>((const double*)h->part, (int)c.S, h->part_ns, h->Npad, h->N, h->red);
+                else if (h->hist_s16 && !h->pop_dbl)   // the commit's float sums of the 16-bit forms
+                    k_part_read<float, float><<<pg, h->node_tpb>>>((const float*)h->part, (int)c.S, h->part_ns, h->Npad, h->N, h->red);
                 else
-                    k_part_read<float><<<(h->N + h->node_tpb - 1) / h->node_tpb, h->node_tpb>>>((const float*)h->part, (int)c.S, h->part_ns, h->Npad, h->N, h->red);
+                    k_part_read<float, double><<<pg, h->node_tpb>>>((const float*)h->part, (int)c.S, h->part_ns, h->Npad, h->N, h->red);
                 LBVE_CUDA(cudaGetLastError());
             }
             LBVE_CUDA(cudaEventRecord(e1, 0));

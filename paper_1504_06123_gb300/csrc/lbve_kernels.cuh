@@ -556,16 +556,17 @@ __global__ void __launch_bounds__(256, 2) k_sweep(SweepArgs<R> a, Geom g) {
 }
 
 // Autotuning aid: the commit's read of the chunk partials (one thread per node, chunks in order), so
-// that the tuner weighs a slot-chunk count S by the sweep plus the reduction it causes in the commit.
-template <typename R>
+// that the tuner weighs a slot-chunk count S by the sweep plus the reduction it causes in the commit (A: the
+// commit's summation type).
+template <typename R, typename A>
 __global__ void k_part_read(const R* __restrict__ part, int S, int NS, long long Np, int N, double* sink) {
     const int n = blockIdx.x * blockDim.x + threadIdx.x;
     if (n >= N) return;
-    double acc = 0.0;
+    A acc = A(0);
 #pragma unroll 4
     for (int c = 0; c < S; ++c)
-        for (int i = 0; i < NS; ++i) acc += (double)part[((long long)c * NS + i) * Np + n];
-    if (acc == 1.2345e300) *sink = acc;   // keeps the loads; the all-rest history sums to 0
+        for (int i = 0; i < NS; ++i) acc += (A)part[((long long)c * NS + i) * Np + n];
+    if (acc == A(1.2345e30)) *sink = (double)acc;   // keeps the loads; the all-rest history sums to 0
 }
 
 // ------------------------------------------------------------------------------------------------

@@ -74,8 +74,9 @@ def parse():
     ap.add_argument("--nx", type=int, default=None,
                     help="narrower channel (same rows, same history) for profiler captures; not a bench line")
     ap.add_argument("--sweep-shape", default=None,
-                    help="S,cta: pin the history sweep's launch shape (slot chunks, 1 = CTA tasks) after the "
-                         "autotuner, e.g. to profile the shape a timed run chose")
+                    help="S,mode: pin the history sweep's launch shape after the autotuner (slot chunks; mode 0 "
+                         "warp tasks, 1 CTA tasks, 2 balanced ranges of the 16-bit form F), e.g. to profile the "
+                         "shape a timed run chose")
     return ap.parse_args()
 
 
@@ -236,7 +237,8 @@ def batch_arms(L, torch, configs, chosen: str, K: int, W: int, stream, sync_rank
                      "value": N * sum(pts) * world / (ms / 1e3), "unit": UNIT, "ms_per_step": ms / K,
                      "sweep_ms_per_launch": sweep_ms,
                      "roofline_frac": bpu * N * (sum(pts_p) - Kp) / Kp / (sweep_ms / 1e3) / 1e9 / peak,
-                     "launches_per_step": 3, "sweep": {"slot_chunks": shape[0], "ctas": shape[1]}}
+                     "launches_per_step": 3, "sweep": {"slot_chunks": shape[0], "ctas": shape[1],
+                                                         "tasks": ("warp", "cta", "balanced")[shape[2]]}}
     # the plain form as separate channels: one handle and one launch sequence per channel per step
     hs_ = [L.Channel(d) for d in arms["batched_plain_f32"]]
     try:
@@ -726,7 +728,8 @@ def run_ours(args, rank, world, local_rank):
                                    "unit": UNIT, "ms_per_step": msc / K, "sweep_ms_per_launch": sweep_c,
                                    "collide_ms_per_launch": coll_c, "bytes_per_update": bpu_c,
                                    "roofline_frac": bpu_c * N * pts_f / Kp / (sweep_c / 1e3) / 1e9 / peak,
-                                   "sweep": {"slot_chunks": shape_c[0], "ctas": shape_c[1]},
+                                   "sweep": {"slot_chunks": shape_c[0], "ctas": shape_c[1],
+                                             "tasks": ("warp", "cta", "balanced")[shape_c[2]]},
                                    "parity_bar": FORM_BAR[fm, hs]}
         best = max((k for k in forms if k != "p_f32"), key=lambda k: forms[k]["value"])
         extra = {"forms": forms, "chosen": dict(forms[best], key=best),
@@ -842,7 +845,7 @@ def run_ours(args, rank, world, local_rank):
                             "l2": ("no flush: per-step state (" + ("populations" if inst else "history") +
                                    f", {state_bytes / 1e6:.0f} MB) larger than the 129 MB L2")
                                   if state_bytes > 2.5e8 else "state fits in L2 (latency-bound size)",
-                            "sweep": {"slot_chunks": S, "ctas": ctas, "tasks": "cta" if cta_tasks else "warp"}},
+                            "sweep": {"slot_chunks": S, "ctas": ctas, "tasks": ("warp", "cta", "balanced")[cta_tasks]}},
                            **notes),
             "mlups": mlups,
             "kernel_ms_per_launch": {"moments": kms[0] / max(launches[0], 1), "history": hist_ms,

@@ -321,7 +321,9 @@ int lbve_memory_bytes(const lbve_t* h, size_t* bytes);
 /*
  * Launch shape of the history sweep chosen at create by the autotuner: the number of slot chunks each
  * node's points are split into (tasks = node tiles x chunks), the number of persistent CTAs, and the task
- * mode (*cta_tasks = 0: a task is one warp's; 1: a task is one CTA's, its warps splitting the chunk).
+ * mode (*cta_tasks = 0: a task is one warp's; 1: a task is one CTA's, its warps splitting the chunk;
+ * 2, 16-bit form F only: balanced ranges -- every warp of the resident grid takes an equal run of the
+ * tile-major sequence of (node tile, point), a tile being cut into at most *slot_chunks pieces).
  * The tuner times candidate shapes once per process for each (device, lattice, history storage and model,
  * history grid, padded node count); later handles of the same kind take the shape found then.
  * The shape fixes the order in which the trapezoidal sum of Eq. (gitt) is added up: results are bitwise
@@ -331,8 +333,9 @@ int lbve_sweep_config(const lbve_t* h, int32_t* slot_chunks, int32_t* ctas, int3
 
 /*
  * Replace the autotuned launch shape (for bitwise-reproducible runs across handles, whose autotuner may
- * choose differently): slot_chunks in 1 .. max(1, B*C/8), cta_tasks 0 or 1 (1 only with an FP32 or FP64
- * history).  Synchronises the device; the step graphs are re-captured.  EINVAL outside those ranges,
+ * choose differently): slot_chunks in 1 .. max(1, B*C/8), cta_tasks 0, 1 (only with an FP32 or FP64
+ * history) or 2 (only with the 16-bit form F; slot_chunks is then set from the grid, and EINVAL if that
+ * exceeds B*C/8).  Synchronises the device; the step graphs are re-captured.  EINVAL outside those ranges,
  * ENOSUPPORT for a handle without a history sweep (instantaneous model, tangent and adjoint handles).
  */
 int lbve_set_sweep_config(lbve_t* h, int32_t slot_chunks, int32_t cta_tasks);

@@ -328,6 +328,7 @@ CommitF16 commit_f16(lbve* h) {
     c.B = h->d.hist_B;
     c.C = h->d.hist_C;
     c.S = h->S;
+    c.bal_nw = h->sweep_cta == 2 ? h->sweep_grid * 8 : 0;   // balanced ranges: one warp per 32 threads of the grid
     return c;
 }
 
@@ -468,12 +469,15 @@ int sweep_autotune(lbve* h) {
             add(1, (k * grid_full + tiles - 1) / tiles);
             add(1, k * grid_full / tiles);
         }
+    // 16-bit form F: balanced ranges over all resident warps (S = the most pieces a tile can be cut into)
+    if (HK == 6 && f16_bal_max_pieces(tiles, (int)warps) <= Smax) add(2, f16_bal_max_pieces(tiles, (int)warps));
     long long Sbig = 1;
     for (const Cand& c : cand) Sbig = std::max(Sbig, c.S);
     int rc = alloc(h, &h->part, h->hesz * (size_t)Sbig * h->part_ns * h->Npad);
     if (rc) return rc;
     LBVE_CUDA(cudaMemset(h->part, 0, h->hesz * (size_t)Sbig * h->part_ns * h->Npad));
     auto grid_of = [&](const Cand& c) {
+        if (c.cta == 2) return (int)grid_full;
         return (int)std::max(1ll, std::min(grid_full, c.cta ? tiles * c.S : (tiles * c.S + 7) / 8));
     };
     Cand best_c = cand[0];
@@ -1947,8 +1951,15 @@ int lbve_set_sweep_config(lbve_t* h, int32_t slot_chunks, int32_t cta_tasks) {
     if (!h) return LBVE_EINVAL;
     if (h->L == 0 || h->tangent || h->rec_K || !h->part) return LBVE_ENOSUPPORT;
     const long long Smax = h->L >= 16 ? h->L / 8 : 1;
-    if (slot_chunks < 1 || slot_chunks > Smax || (cta_tasks != 0 && cta_tasks != 1)) return LBVE_EINVAL;
-    if (cta_tasks && (h->hist_s16 || h->hist_formf)) return LBVE_EINVAL;   // warp tasks only
+    if (slot_chunks < 1 || slot_chunks > Smax || cta_tasks < 0 || cta_tasks > 2) return LBVE_EINVAL;
+    if (cta_tasks == 1 && (h->hist_s16 || h->hist_formf)) return LBVE_EINVAL;   // warp tasks only
+    const bool f16 = h->hist_s16 && h->hist_formf;
+    if (cta_tasks == 2) {   // balanced ranges (16-bit form F only): the chunk count follows from the grid
+        if (!f16) return LBVE_EINVAL;
+        const long long tiles16 = h->Npad / (32 * (h->D == 2 ? 4 : 2));
+        slot_chunks = f16_bal_max_pieces(tiles16, h->sweep_grid_full * 8);
+        if (slot_chunks > Smax) return LBVE_EINVAL;
+    }
     LBVE_CUDA(cudaDeviceSynchronize());
     if (h->graph) {
         cudaGraphExecDestroy(h->graph);
@@ -1968,8 +1979,9 @@ int lbve_set_sweep_config(lbve_t* h, int32_t slot_chunks, int32_t cta_tasks) {
     const long long tiles = h->Npad / (32 * vn);
     h->S = slot_chunks;
     h->sweep_cta = cta_tasks;
-    h->sweep_grid = (int)std::max(1ll, std::min((long long)h->sweep_grid_full,
-                                                cta_tasks ? tiles * slot_chunks : (tiles * slot_chunks + 7) / 8));
+    h->sweep_grid = cta_tasks == 2 ? h->sweep_grid_full
+                                   : (int)std::max(1ll, std::min((long long)h->sweep_grid_full,
+                                                                 cta_tasks ? tiles * slot_chunks : (tiles * slot_chunks + 7) / 8));
     return LBVE_OK;
 }
 

@@ -14,7 +14,10 @@
 // sums w G(t, t') (1 + X) Dm (1 + X)^T.  The chunk before it contributes the carry C_j = T_1 ... T_{j-1} of
 // the chunks' total products T, so that E = C_j (1 + X): the chunk writes its local sum M_j and its product
 // deviation T_j - 1, and the commit adds C_j M_j C_j^T over the chunks in order (the carry leaves the point
-// sum like a frame: every point of the chunk sees the same C_j).  One read-only pass over the history.
+// sum like a frame: every point of the chunk sees the same C_j).  One read-only pass over the history.  The
+// chunk holding the oldest point needs no T (nothing follows it); the 16-bit sweep sums that chunk in
+// Horner form from its oldest point to its newest, H <- F (H + w G Dm) F^T, one congruence per point in
+// place of the running product and the sandwich (the same sum, the additions in another order).
 //
 // Commit (per node, fused into the collide kernel): sigma_struc(t) from the chunk records plus the point
 // created now (age 0, E = 1, weight 1/2), then the block merges of the quasi-logarithmic grid (older point's
@@ -25,6 +28,8 @@
 // Storage: float or double planes, or 16-bit block-scaled (d*d int16 mantissas of Y and NS of Dm, one shared
 // power-of-two exponent byte per vector, as in the reduced-precision history of lbve_kernels.cuh).
 #pragma once
+#include <type_traits>
+
 #include "lbve_kernels.cuh"
 
 namespace lbk {
@@ -70,6 +75,16 @@ template <> struct PtMath<double> {
     }
 };
 
+// w G of one point: gammadot^2 = (1/2) tr Dm^2 from the packed Dm, then the modulus and weight as one exp.
+template <int D, typename R>
+__device__ __forceinline__ R point_weight(const R* Dp, R age, R w, R c1, R c2) {
+    constexpr int NS = D == 2 ? 3 : 6;
+    R h = 0;
+#pragma unroll
+    for (int i = 0; i < NS; ++i) h = ::fma(Dp[i], (i < D ? R(0.5) : R(1)) * Dp[i], h);
+    return PtMath<R>::gw(w, age, c1, c2, PtMath<R>::sqrt_pos(h));
+}
+
 // w G (1 + X) Dm (1 + X)^T added to acc (packed symmetric), Dm packed symmetric:
 // F = Dm + X Dm, then the upper triangle of F (1 + X)^T = F + F X^T; gammadot^2 = (1/2) tr Dm^2.
 template <int D, typename R>
@@ -90,10 +105,7 @@ __device__ __forceinline__ void sym_integrand(const R* X, const R* Dp, R age, R 
             for (int k = 0; k < D; ++k) s = ::fma(X[r * D + k], Dm[k * D + c], s);
             F[r * D + c] = s;
         }
-    R h = 0;
-#pragma unroll
-    for (int i = 0; i < NS; ++i) h = ::fma(Dp[i], (i < D ? R(0.5) : R(1)) * Dp[i], h);
-    const R g = PtMath<R>::gw(w, age, c1, c2, PtMath<R>::sqrt_pos(h));
+    const R g = point_weight<D>(Dp, age, w, c1, c2);
 #pragma unroll
     for (int i = 0; i < NS; ++i) {
         const int r = symr<D>(i), c = symc<D>(i);
@@ -101,6 +113,38 @@ __device__ __forceinline__ void sym_integrand(const R* X, const R* Dp, R age, R 
 #pragma unroll
         for (int k = 0; k < D; ++k) s = ::fma(F[r * D + k], X[c * D + k], s);
         acc[i] = ::fma(g, s, acc[i]);
+    }
+}
+
+// H <- (1 + Y) H (1 + Y)^T, H packed symmetric: G = H + Y H, then the upper triangle of G (1 + Y)^T = G + G Y^T.
+// One step of the Horner form of a chunk's sum, taken from its oldest rank k = K to its newest k = 1:
+// H_K = F_K (w_K G_K Dm_K) F_K^T, H_k = F_k (w_k G_k Dm_k + H_{k+1}) F_k^T, so that H_1 is the sum over k of
+// w_k G_k P_k Dm_k P_k^T with P_k = F_1 ... F_k -- the chunk's M without forming P_k itself.
+template <int D, typename R>
+__device__ __forceinline__ void sym_congruence(R* H, const R* Y) {
+    constexpr int NS = D == 2 ? 3 : 6;
+    R Hm[D * D];
+#pragma unroll
+    for (int r = 0; r < D; ++r)
+#pragma unroll
+        for (int c = 0; c < D; ++c) Hm[r * D + c] = H[symi<D>(r, c)];
+    R G[D * D];
+#pragma unroll
+    for (int r = 0; r < D; ++r)
+#pragma unroll
+        for (int c = 0; c < D; ++c) {
+            R s = Hm[r * D + c];
+#pragma unroll
+            for (int k = 0; k < D; ++k) s = ::fma(Y[r * D + k], Hm[k * D + c], s);
+            G[r * D + c] = s;
+        }
+#pragma unroll
+    for (int i = 0; i < NS; ++i) {
+        const int r = symr<D>(i), c = symc<D>(i);
+        R s = G[r * D + c];
+#pragma unroll
+        for (int k = 0; k < D; ++k) s = ::fma(G[r * D + k], Y[c * D + k], s);
+        H[i] = s;
     }
 }
 
@@ -300,8 +344,11 @@ __device__ __forceinline__ void formf_sigma(const R* part, int S, long long Np, 
             M[symr<D>(i) * D + symc<D>(i)] = v;
             M[symc<D>(i) * D + symr<D>(i)] = v;
         }
+        // the last chunk's product is composed into nothing: not read (the 16-bit sweep does not write it)
+        if (j + 1 < S) {
 #pragma unroll
-        for (int i = 0; i < DD; ++i) T[i] = (A)pj[(NS + i) * Np];
+            for (int i = 0; i < DD; ++i) T[i] = (A)pj[(NS + i) * Np];
+        }
         // C M C^T with C = 1 + Z: (M + Z M) (1 + Z)^T, upper triangle
         A F[DD];
 #pragma unroll
@@ -321,7 +368,7 @@ __device__ __forceinline__ void formf_sigma(const R* part, int S, long long Np, 
             for (int k = 0; k < D; ++k) s = ::fma(F[r * D + k], Z[c * D + k], s);
             acc[i] += (N)s;
         }
-        dev_product<D>(Z, T);
+        if (j + 1 < S) dev_product<D>(Z, T);
     }
 #pragma unroll
     for (int i = 0; i < NS; ++i) sig[i] = G_inf * (acc[i] + N(0.5) * dnew[i]);
@@ -423,8 +470,20 @@ struct CommitF16 {
     unsigned char* __restrict__ blk;  // [tiles][L][2048] history blocks
     float* __restrict__ part;         // [S][NS + DD][Npad]
     int B, C, S;
+    int bal_nw;                       // 0: chunk tasks (S chunks per tile); > 0: balanced ranges over bal_nw warps
 };
 template <> struct Hist16<CommitF16> { static constexpr bool value = true; };
+
+// Balanced ranges of the 16-bit form-F sweep: with n points per node and `tiles` node tiles, warp w of nw
+// takes the ranks [w Wp, (w + 1) Wp) of the tile-major sequence of (tile, rank), Wp = ceil(tiles n / nw), so
+// every warp streams the same number of blocks.  A tile is cut at the multiples of Wp inside it; its
+// pieces, in rank order, are owned by warps floor(t n / Wp) ... floor(((t + 1) n - 1) / Wp), and piece j
+// writes chunk record j.  At most ceil(nw / tiles) + 1 pieces per tile.
+__host__ __device__ inline long long f16_bal_wp(long long tiles, int n, int nw) { return (tiles * n + nw - 1) / nw; }
+__host__ __device__ inline int f16_bal_pieces(long long tile, int n, long long wp) {
+    return (int)(((tile + 1) * n - 1) / wp - (tile * n) / wp + 1);
+}
+__host__ __device__ inline int f16_bal_max_pieces(long long tiles, int nw) { return (int)((nw + tiles - 1) / tiles) + 1; }
 
 // Ranks ahead of the one in process whose blocks a warp asks the L2 to fetch (one bulk prefetch of 2048 bytes
 // per slot, issued by lane 0): the loads of those slots then hit the L2, and the DRAM requests in flight per
@@ -438,120 +497,124 @@ __device__ __forceinline__ void prefetch_l2_bulk(const void* p, unsigned bytes) 
     asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(p), "r"(bytes) : "memory");
 }
 
-template <int D, int VN>
-__global__ void __launch_bounds__(256, 2) k_sweep_f16(CommitF16 a, const long long* __restrict__ t_dev, Geom g) {
+// One piece of work of the 16-bit form-F sweep: ranks [r0, r1) of tile `tile`, its sums (and product
+// deviation) into chunk record `chunk`.  HZ: the tile's oldest piece (r1 = n), whose product the commit never
+// composes -- summed in Horner form from its oldest rank to its newest (sym_congruence), one congruence per
+// point instead of the running product plus the sandwich; other pieces run newest first with the running
+// product.  The kernel calls each path from a loop of its own: one loop holding both spills registers.
+template <int D, int VN, bool HZ>
+__device__ __forceinline__ void f16_piece(const CommitF16 a, const RankEnt* __restrict__ ent, const int n_pts,
+                                       const Geom g, const int tile, const int r0, const int r1, const int chunk) {
     using Lay = F16Layout<D>;
     constexpr int DD = D * D;
     constexpr int NS = D == 2 ? 3 : 6;
-    static_assert(VN == Lay::VN, "one lane's nodes are one lane's bytes of a block");
     using VF = Vec<float, VN>;
-    extern __shared__ __align__(16) unsigned char smem_raw[];
-    const long long t = *t_dev;
-    const RankTab rt = rank_tables<true>(smem_raw, a.B, a.C, t);
+    const RankTab rt{ent, n_pts};
     const long long Np = g.Npad;
     const int L = a.B * a.C;
     const int lane = threadIdx.x & 31;
-    const int gwarp = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
-    const int nwarps = gridDim.x * (blockDim.x >> 5);
-    const int tiles = (int)(Np / Lay::TN);
-    const int tasks = tiles * a.S;
-    const int chunk_len = (rt.n + a.S - 1) / a.S;
-
-    for (int task = gwarp; task < tasks; task += nwarps) {
-        const int tile = task % tiles;
-        const int chunk = task / tiles;
-        const long long n0 = (long long)tile * Lay::TN + lane * VN;
-        const unsigned char* tbase = a.blk + (long long)tile * L * Lay::kBlock + lane * 16;
-        float c1[VN], c2[VN];
+    const long long n0 = (long long)tile * Lay::TN + lane * VN;
+    const unsigned char* tbase = a.blk + (long long)tile * L * Lay::kBlock + lane * 16;
+    float c1[VN], c2[VN];
+#pragma unroll
+    for (int j = 0; j < VN; ++j) {
+        const Chan& c = g.ch[chan_index(g, n0 + j)];
+        PtMath<float>::consts(c.inv_tau, c.inv_gc, c1[j], c2[j]);
+    }
+    float X[VN][DD], acc[VN][NS];
+#pragma unroll
+    for (int j = 0; j < VN; ++j) {
+#pragma unroll
+        for (int i = 0; i < DD; ++i) X[j][i] = 0.0f;
+#pragma unroll
+        for (int i = 0; i < NS; ++i) acc[j][i] = 0.0f;
+    }
+    const int m = r1 - r0;
+    // rank of the q-th point visited
+    auto rank_at = [&](int q) { return HZ ? r1 - 1 - q : r0 + q; };
+    // the lane's 64 bytes of one slot as 16 words (word q holds half-words 2q, 2q + 1)
+    auto load = [&](int q, unsigned (&wd)[16]) {
+        const uint4* p = reinterpret_cast<const uint4*>(tbase + (long long)rt.e[rank_at(q)].slot * Lay::kBlock);
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+            const uint4 v = p[k * 32];          // + k * 512 bytes
+            wd[4 * k] = v.x; wd[4 * k + 1] = v.y; wd[4 * k + 2] = v.z; wd[4 * k + 3] = v.w;
+        }
+    };
+    auto half_of = [&](const unsigned (&wd)[16], int h, const S16Scale& sc) -> float {
+        return (h & 1) ? s16_hi(wd[h >> 1], sc) : s16_lo(wd[h >> 1], sc);
+    };
+    auto process = [&](int q, const unsigned (&wd)[16]) {
+        const RankEnt e = rt.e[rank_at(q)];
+        const unsigned ye = D == 2 ? wd[14] : (wd[15] & 0xFFFFu);
+        const unsigned de = D == 2 ? wd[15] : (wd[15] >> 16);
+        float Y[VN][DD], Dp[VN][NS];
 #pragma unroll
         for (int j = 0; j < VN; ++j) {
-            const Chan& c = g.ch[chan_index(g, n0 + j)];
-            PtMath<float>::consts(c.inv_tau, c.inv_gc, c1[j], c2[j]);
+            const S16Scale sy(s16_exp(ye, j)), sd(s16_exp(de, j));
+#pragma unroll
+            for (int c = 0; c < DD; ++c) Y[j][c] = half_of(wd, Lay::y_half(c, j), sy);
+#pragma unroll
+            for (int c = 0; c < NS; ++c) Dp[j][c] = half_of(wd, Lay::d_half(c, j), sd);
         }
-        float X[VN][DD], acc[VN][NS];
+        if (e.partner >= 0) {   // older half of a merge: rate of strain averaged with the newer half's
+            unsigned pw[16];
+            {
+                const uint4* p = reinterpret_cast<const uint4*>(tbase + (long long)e.partner * Lay::kBlock);
+#pragma unroll
+                for (int k = 2; k < 4; ++k) {   // the Dm mantissas and the exponents sit in pieces 2 and 3
+                    const uint4 v = p[k * 32];
+                    pw[4 * k] = v.x; pw[4 * k + 1] = v.y; pw[4 * k + 2] = v.z; pw[4 * k + 3] = v.w;
+                }
+            }
+            const unsigned de2 = D == 2 ? pw[15] : (pw[15] >> 16);
+#pragma unroll
+            for (int j = 0; j < VN; ++j) {
+                const S16Scale s2(s16_exp(de2, j));
+#pragma unroll
+                for (int c = 0; c < NS; ++c) Dp[j][c] = 0.5f * (Dp[j][c] + half_of(pw, Lay::d_half(c, j), s2));
+            }
+        }
 #pragma unroll
         for (int j = 0; j < VN; ++j) {
+            if (HZ) {
+                const float wg = point_weight<D>(Dp[j], e.age, e.w, c1[j], c2[j]);
 #pragma unroll
-            for (int i = 0; i < DD; ++i) X[j][i] = 0.0f;
-#pragma unroll
-            for (int i = 0; i < NS; ++i) acc[j][i] = 0.0f;
-        }
-        const int r0 = min(rt.n, chunk * chunk_len), r1 = min(rt.n, r0 + chunk_len);
-        // the lane's 64 bytes of one slot as 16 words (word q holds half-words 2q, 2q + 1)
-        auto load = [&](int r, unsigned (&wd)[16]) {
-            const uint4* p = reinterpret_cast<const uint4*>(tbase + (long long)rt.e[r].slot * Lay::kBlock);
-#pragma unroll
-            for (int k = 0; k < 4; ++k) {
-                const uint4 v = p[k * 32];          // + k * 512 bytes
-                wd[4 * k] = v.x; wd[4 * k + 1] = v.y; wd[4 * k + 2] = v.z; wd[4 * k + 3] = v.w;
-            }
-        };
-        auto half_of = [&](const unsigned (&wd)[16], int h, const S16Scale& sc) -> float {
-            return (h & 1) ? s16_hi(wd[h >> 1], sc) : s16_lo(wd[h >> 1], sc);
-        };
-        auto process = [&](int r, const unsigned (&wd)[16]) {
-            const RankEnt e = rt.e[r];
-            const unsigned ye = D == 2 ? wd[14] : (wd[15] & 0xFFFFu);
-            const unsigned de = D == 2 ? wd[15] : (wd[15] >> 16);
-            float Y[VN][DD], Dp[VN][NS];
-#pragma unroll
-            for (int j = 0; j < VN; ++j) {
-                const S16Scale sy(s16_exp(ye, j)), sd(s16_exp(de, j));
-#pragma unroll
-                for (int c = 0; c < DD; ++c) Y[j][c] = half_of(wd, Lay::y_half(c, j), sy);
-#pragma unroll
-                for (int c = 0; c < NS; ++c) Dp[j][c] = half_of(wd, Lay::d_half(c, j), sd);
-            }
-            if (e.partner >= 0) {   // older half of a merge: rate of strain averaged with the newer half's
-                unsigned pw[16];
-                {
-                    const uint4* p = reinterpret_cast<const uint4*>(tbase + (long long)e.partner * Lay::kBlock);
-#pragma unroll
-                    for (int k = 2; k < 4; ++k) {   // the Dm mantissas and the exponents sit in pieces 2 and 3
-                        const uint4 v = p[k * 32];
-                        pw[4 * k] = v.x; pw[4 * k + 1] = v.y; pw[4 * k + 2] = v.z; pw[4 * k + 3] = v.w;
-                    }
-                }
-                const unsigned de2 = D == 2 ? pw[15] : (pw[15] >> 16);
-#pragma unroll
-                for (int j = 0; j < VN; ++j) {
-                    const S16Scale s2(s16_exp(de2, j));
-#pragma unroll
-                    for (int c = 0; c < NS; ++c) Dp[j][c] = 0.5f * (Dp[j][c] + half_of(pw, Lay::d_half(c, j), s2));
-                }
-            }
-#pragma unroll
-            for (int j = 0; j < VN; ++j) {
+                for (int i = 0; i < NS; ++i) acc[j][i] = fmaf(wg, Dp[j][i], acc[j][i]);
+                sym_congruence<D>(acc[j], Y[j]);
+            } else {
                 dev_product<D>(X[j], Y[j]);
                 sym_integrand<D>(X[j], Dp[j], e.age, e.w, c1[j], c2[j], acc[j]);
             }
-        };
-        // two slots of words alternate: the next slot's loads are in flight while a slot is processed; the
-        // blocks of the ranks LBVE_F16_PREFETCH ahead are on their way to the L2
-        constexpr int PF = LBVE_F16_PREFETCH;
-        auto prefetch = [&](int r) {
-            if (PF > 0 && lane == 0 && r < r1) prefetch_l2_bulk(tbase + (long long)rt.e[r].slot * Lay::kBlock, Lay::kBlock);
-        };
-        for (int k = 2; k < PF; ++k) prefetch(r0 + k);
-        unsigned wa[16], wb[16];
-        if (r0 < r1) load(r0, wa);
-        for (int r = r0; r < r1; r += 2) {
-            if (r + 1 < r1) load(r + 1, wb);
-            prefetch(r + PF);
-            process(r, wa);
-            if (r + 1 >= r1) break;
-            if (r + 2 < r1) load(r + 2, wa);
-            prefetch(r + 1 + PF);
-            process(r + 1, wb);
         }
-        float* out = a.part + (long long)chunk * (NS + DD) * Np + n0;
+    };
+    // two slots of words alternate: the next slot's loads are in flight while a slot is processed; the
+    // blocks of the points LBVE_F16_PREFETCH ahead in the visiting order are on their way to the L2
+    constexpr int PF = LBVE_F16_PREFETCH;
+    auto prefetch = [&](int q) {
+        if (PF > 0 && lane == 0 && q < m) prefetch_l2_bulk(tbase + (long long)rt.e[rank_at(q)].slot * Lay::kBlock, Lay::kBlock);
+    };
+    for (int k = 2; k < PF; ++k) prefetch(k);
+    unsigned wa[16], wb[16];
+    if (m > 0) load(0, wa);
+    for (int q = 0; q < m; q += 2) {
+        if (q + 1 < m) load(q + 1, wb);
+        prefetch(q + PF);
+        process(q, wa);
+        if (q + 1 >= m) break;
+        if (q + 2 < m) load(q + 2, wa);
+        prefetch(q + 1 + PF);
+        process(q + 1, wb);
+    }
+    float* out = a.part + (long long)chunk * (NS + DD) * Np + n0;
 #pragma unroll
-        for (int i = 0; i < NS; ++i) {
-            VF v;
+    for (int i = 0; i < NS; ++i) {
+        VF v;
 #pragma unroll
-            for (int j = 0; j < VN; ++j) v.v[j] = acc[j][i];
-            *reinterpret_cast<VF*>(out + i * Np) = v;
-        }
+        for (int j = 0; j < VN; ++j) v.v[j] = acc[j][i];
+        *reinterpret_cast<VF*>(out + i * Np) = v;
+    }
+    if (!HZ) {
 #pragma unroll
         for (int i = 0; i < DD; ++i) {
             VF v;
@@ -559,6 +622,50 @@ __global__ void __launch_bounds__(256, 2) k_sweep_f16(CommitF16 a, const long lo
             for (int j = 0; j < VN; ++j) v.v[j] = X[j][i];
             *reinterpret_cast<VF*>(out + (NS + i) * Np) = v;
         }
+    }
+}
+
+template <int D, int VN>
+__global__ void __launch_bounds__(256, 2) k_sweep_f16(CommitF16 a, const long long* __restrict__ t_dev, Geom g) {
+    using Lay = F16Layout<D>;
+    static_assert(VN == Lay::VN, "one lane's nodes are one lane's bytes of a block");
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    const long long t = *t_dev;
+    const RankTab rt = rank_tables<true>(smem_raw, a.B, a.C, t);
+    const int gwarp = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+    const int nwarps = gridDim.x * (blockDim.x >> 5);
+    const int tiles = (int)(g.Npad / Lay::TN);
+
+    const int n = rt.n;
+    if (a.bal_nw > 0) {
+        // balanced ranges: this warp's span of (tile, rank) is the tail of one tile, whole tiles, and the head
+        // of one more -- the pieces that reach their tile's oldest point (Horner form), then at most one that
+        // ends before it
+        const long long wp = f16_bal_wp(tiles, n, a.bal_nw);
+        const long long lo = (long long)gwarp * wp, hi = min((long long)tiles * n, lo + wp);
+        long long tt = lo / n;
+        for (; (tt + 1) * n <= hi; ++tt) {
+            const long long base = tt * n;
+            f16_piece<D, VN, true>(a, rt.e, n, g, (int)tt, (int)max(0ll, lo - base), n, (int)(gwarp - base / wp));
+        }
+        if (tt * n < hi) {
+            const long long base = tt * n;
+            f16_piece<D, VN, false>(a, rt.e, n, g, (int)tt, (int)max(0ll, lo - base), (int)(hi - base),
+                                    (int)(gwarp - base / wp));
+        }
+    } else {
+        // chunk tasks: tiles x S tasks, chunk-major, warps striding over them -- the chunks before the one that
+        // holds the oldest point (running product), then that one (Horner form); chunks past it are empty and
+        // the commit does not read them
+        const int len = (n + a.S - 1) / a.S;
+        const int S_eff = (n + len - 1) / len;
+        int task = gwarp;
+        for (; task < tiles * (S_eff - 1); task += nwarps) {
+            const int chunk = task / tiles;
+            f16_piece<D, VN, false>(a, rt.e, n, g, task % tiles, chunk * len, (chunk + 1) * len, chunk);
+        }
+        for (; task < tiles * S_eff; task += nwarps)
+            f16_piece<D, VN, true>(a, rt.e, n, g, task % tiles, (S_eff - 1) * len, n, S_eff - 1);
     }
 }
 
@@ -625,7 +732,20 @@ __device__ __forceinline__ void hist_commit_any(Arith<N>, const CommitF16& a, co
 #pragma unroll
         for (int i = 0; i < NS; ++i) dstored[i] = (N)f[i];
     }
-    formf_sigma<D, float, float, N>(a.part, a.S, Np, n, dstored, chan_val<N>(p.G_inf, p.G_inf_f), sig);
+    // the chunk records the sweep wrote for this node's tile, the last one the tile's oldest piece (its product
+    // not written): balanced ranges cut the tile into pieces; chunk tasks leave the chunks past the oldest
+    // point empty
+    int npts = 0;
+    for (int bb = 0; bb < a.B; ++bb) npts += s_bs[bb].count_prev;
+    int S;
+    if (a.bal_nw > 0) {
+        const long long tiles = Np / F16Layout<D>::TN;
+        S = f16_bal_pieces(n / F16Layout<D>::TN, npts, f16_bal_wp(tiles, npts, a.bal_nw));
+    } else {
+        const int len = (npts + a.S - 1) / a.S;
+        S = (npts + len - 1) / len;
+    }
+    formf_sigma<D, float, float, N>(a.part, S, Np, n, dstored, chan_val<N>(p.G_inf, p.G_inf_f), sig);
     for (int bb = 1; bb < a.B; ++bb) {
         const BlockStep& b = s_bs[bb];
         if (!b.evict) continue;

@@ -181,6 +181,69 @@ def test_formf_launch_shapes_agree(hist):
     b.close()
 
 
+def test_formf16_balanced_ranges():
+    """Task mode 2 of the 16-bit form F (balanced ranges): every warp of the resident grid streams an equal
+    run of the tile-major (tile, rank) sequence, a tile is cut into pieces whose chunk records the commit
+    composes in rank order.  Against the FP64 oracle at the reduced-precision bar; against chunk tasks to a
+    few units of the 16-bit storage's rounding (2^-15 of a vector's scale: a different order of the FP32
+    additions can move a stored value across a rounding boundary, and the runs then differ at that level);
+    bitwise equal on two handles; refused for another storage and where the pieces of a tile would exceed
+    B*C/8."""
+    kw = dict(nx=8, ny=320, tau_lb=0.8, G_inf=0.01, tau=200.0, gamma_c=0.1, g=(2e-6, 0, 0), C=128, B=8)
+    gkw = dict(kw, precision=F32, hist_storage=S16, hist_form=FF)
+    ref = L.Channel(L.make_desc(**gkw))
+    L.lbve_set_sweep_config(ref.h, 4, 0)
+    bal = [L.Channel(L.make_desc(**gkw)) for _ in range(2)]
+    for b in bal:
+        L.lbve_set_sweep_config(b.h, 1, 2)
+        S, ctas, mode = L.lbve_sweep_config(b.h)
+        assert mode == 2 and 1 < S <= 128, (S, ctas, mode)
+    ref.step(300)
+    bal[0].step(300)
+    bal[1].step(7)      # odd steps, then 16-step graphs
+    bal[1].step(293)
+    fr, f0, f1 = ref.fields(), bal[0].fields(), bal[1].fields()
+    orc = oracle.Channel(oracle.D2Q9, kw["nx"], kw["ny"], tau_lb=kw["tau_lb"], G_inf=kw["G_inf"], tau=kw["tau"],
+                         gamma_c=kw["gamma_c"], g=kw["g"], C=kw["C"], B=kw["B"])
+    orc.step(300)
+    compare(f0, orc.fields(), TOL[RED], "balanced ranges, 8 x 320, L = 1024, 300 steps")
+    orc.close()
+    for key in ("u", "sigma", "kappa"):
+        assert rel_err(f0[key], fr[key]) <= 1e-4, key
+    for k in f0:
+        assert np.array_equal(f0[k], f1[k]), k
+    for c in [ref] + bal:
+        c.close()
+    other = L.Channel(L.make_desc(**dict(gkw, hist_storage=F32)))
+    small = L.Channel(L.make_desc(**dict(gkw, ny=40, C=16, B=4)))
+    for c in (other, small):
+        with pytest.raises(L.LbveError) as e:
+            L.lbve_set_sweep_config(c.h, 1, 2)
+        assert e.value.status == L.LBVE_EINVAL
+        c.close()
+
+
+@pytest.mark.parametrize("hist", [F32, S16])
+def test_formf_empty_trailing_chunks(hist):
+    """A history grid where chunk tasks leave the last chunk empty at some steps (B = 3, C = 27: 79 to 81
+    points, S = 10 chunks of 9 ranks hold 81 points in nine): the commit composes the chunks up to the one
+    that holds the oldest point and reads no product of that one (the 16-bit sweep sums a tile's oldest
+    chunk in Horner form and writes none).  Every shape against the FP64 oracle at the storage's bar."""
+    kw = dict(nx=4, ny=40, tau_lb=0.8, G_inf=0.01, tau=30.0, gamma_c=0.1, g=(1e-5, 0, 0), C=27, B=3)
+    orc = oracle.Channel(oracle.D2Q9, kw["nx"], kw["ny"], tau_lb=kw["tau_lb"], G_inf=kw["G_inf"], tau=kw["tau"],
+                         gamma_c=kw["gamma_c"], g=kw["g"], C=kw["C"], B=kw["B"])
+    orc.step(90)
+    ref = orc.fields()
+    orc.close()
+    for S in (1, 9, 10):
+        ch = L.Channel(L.make_desc(**dict(kw, precision=F32 if hist == S16 else F64, hist_storage=hist,
+                                          hist_form=FF)))
+        L.lbve_set_sweep_config(ch.h, S, 0)
+        ch.step(90)
+        compare(ch.fields(), ref, TOL[hist], f"form F {hist} S = {S}")
+        ch.close()
+
+
 @pytest.mark.parametrize("hist", [F32, S16])
 def test_formf_checkpoint_resume_bitwise(hist):
     kw = dict(nx=6, ny=14, G_inf=0.01, tau=40.0, gamma_c=0.1, g=(1e-5, 0, 0), C=8, B=3, precision=F32,

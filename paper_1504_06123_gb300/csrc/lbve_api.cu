@@ -391,10 +391,10 @@ template <int D> struct SweepKernel<D, 6> {
 };
 
 // Autotuner of the sweep: candidate (task mode, slot-chunk count S) pairs -- warp tasks with about 2 to
-// 32 tasks per resident warp, and (k_sweep) CTA tasks with 1 to 8 tasks per resident CTA -- each timed
-// over a few launches on the freshly created, all-rest history (which the sweep leaves unchanged:
-// exp(0) - 1 = 0), together with the commit's reduction of the S partial sums (k_part_read); the fastest
-// is kept.  The partial-sum buffer is sized for the largest candidate and then trimmed by reallocation.
+// 32 tasks per resident warp, (k_sweep) CTA tasks with 1 to 8 tasks per resident CTA, and (16-bit form F)
+// balanced ranges over all resident warps -- each timed on a few single launches on the freshly created,
+// all-rest history (which the sweep leaves unchanged: exp(0) - 1 = 0), together with the commit's reduction
+// of the S partial sums (k_part_read); the candidate with the fastest launch is kept.  The partial-sum buffer is sized for the largest candidate and then trimmed by reallocation.
 // Launch shapes the autotuner has chosen in this process, keyed by everything the sweep's speed depends on
 // (device and its SM count, lattice, history storage and model, history grid, padded node count), so that
 // a second handle of the same shape -- a user re-creating a channel, a batch of equal size -- is not timed
@@ -486,21 +486,24 @@ int sweep_autotune(lbve* h) {
         cudaEvent_t e0, e1;
         LBVE_CUDA(cudaEventCreate(&e0));
         LBVE_CUDA(cudaEventCreate(&e1));
-        // launches timed per candidate: one for a history of a gigabyte or more (a launch then takes
-        // well over 100 us, long against the timer), three below; fixed by the size, so that the number of
-        // launches at create does not depend on timings
+        // rounds over all candidates: one untimed (first launches), then two timed for a history of a gigabyte
+        // or more (a launch then takes well over 100 us, long against the timer), three below; each launch
+        // timed on its own and a candidate's fastest kept, so that neither a one-off stall of the memory
+        // system nor the clocks settling while the tuner runs decides the shape.  The number of launches is
+        // fixed by the size, so the launches at create do not depend on timings.
         const size_t hist_bytes = (size_t)h->L * h->Npad * (h->D * h->D + (h->hist_formf ? h->NS : h->D * h->D)) *
                                   (h->hist_s16 ? 2 : h->hesz);
-        const int reps = hist_bytes >= ((size_t)1 << 30) ? 1 : 3;
-        for (const Cand& c : cand) {
-            h->S = (int)c.S;
-            h->sweep_cta = c.cta;
-            h->sweep_grid = grid_of(c);
-            if ((rc = launch_sweep_any<D, HK>(h, 0))) return rc;   // warm-up
-            LBVE_CUDA(cudaEventRecord(e0, 0));
-            for (int r = 0; r < reps; ++r) {
+        const int reps = hist_bytes >= ((size_t)1 << 30) ? 2 : 3;
+        std::vector<float> fastest(cand.size(), 1e30f);
+        const int pg = (h->N + h->node_tpb - 1) / h->node_tpb;
+        for (int r = 0; r <= reps; ++r)
+            for (size_t ci = 0; ci < cand.size(); ++ci) {
+                const Cand& c = cand[ci];
+                h->S = (int)c.S;
+                h->sweep_cta = c.cta;
+                h->sweep_grid = grid_of(c);
+                LBVE_CUDA(cudaEventRecord(e0, 0));
                 if ((rc = launch_sweep_any<D, HK>(h, 0))) return rc;
-                const int pg = (h->N + h->node_tpb - 1) / h->node_tpb;
                 if (h->hist_dbl)
                     k_part_read<double, double><<<pg, h->node_tpb>>>((const double*)h->part, (int)c.S, h->part_ns, h->Npad, h->N, h->red);
                 else if (h->hist_s16 && !h->pop_dbl)   // the commit's float sums of the 16-bit forms
@@ -508,14 +511,14 @@ int sweep_autotune(lbve* h) {
                 else
                     k_part_read<float, double><<<pg, h->node_tpb>>>((const float*)h->part, (int)c.S, h->part_ns, h->Npad, h->N, h->red);
                 LBVE_CUDA(cudaGetLastError());
+                LBVE_CUDA(cudaEventRecord(e1, 0));
+                LBVE_CUDA(cudaEventSynchronize(e1));
+                float one = 0.f;
+                LBVE_CUDA(cudaEventElapsedTime(&one, e0, e1));
+                if (r > 0) fastest[ci] = std::min(fastest[ci], one);
             }
-            LBVE_CUDA(cudaEventRecord(e1, 0));
-            LBVE_CUDA(cudaEventSynchronize(e1));
-            float ms = 0.f;
-            LBVE_CUDA(cudaEventElapsedTime(&ms, e0, e1));
-            ms /= (float)reps;
-            if (ms < best) { best = ms; best_c = c; }
-        }
+        for (size_t ci = 0; ci < cand.size(); ++ci)
+            if (fastest[ci] < best) { best = fastest[ci]; best_c = cand[ci]; }
         cudaEventDestroy(e0);
         cudaEventDestroy(e1);
     }

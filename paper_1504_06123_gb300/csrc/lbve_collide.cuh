@@ -120,20 +120,23 @@ __global__ void __launch_bounds__(256) k_collide_stream(CollArgs<P> a, H h, Geom
     if (n >= g.N) return;
     const long long Np = g.Npad;
     const Chan& p = g.ch[chan_index(g, n)];
-    // sums of the commit and the moments in N (float only with float populations and the 16-bit history,
-    // whose storage rounding is far coarser); the node scalars (trace, density source, rho, u) in double
+    // N: arithmetic of the gradient, the commit's sums, the moments and the node scalars (trace, density
+    // source, rho, u) -- float only with float populations and the 16-bit history, whose storage rounding
+    // (2^-15 of a vector's scale) is far coarser, else double.  With float, k_moments stored u_raw in float
+    // too.  The node fields are stored in double either way.
     using N = typename std::conditional<sizeof(P) == 4 && Hist16<H>::value, float, double>::type;
     N sg[NS];
     {
-        double ktd[DD], kprev[DD];
-        kappa_fd<D>(a.u_raw, Np, p, n, ktd);
+        N ktd[DD];
+        double kprev[DD];
+        kappa_fd<D>(reinterpret_cast<const N*>(a.u_raw), Np, p, n, ktd);
 #pragma unroll
         for (int c = 0; c < DD; ++c) kprev[c] = a.kappa[c * Np + n];
         hist_commit_any<D>(Arith<N>(), h, s_bs, Np, n, kprev, ktd, p, sg, t);
 #pragma unroll
         for (int i = 0; i < NS; ++i) a.sigma[i * Np + n] = (double)sg[i];
 #pragma unroll
-        for (int c = 0; c < DD; ++c) a.kappa[c * Np + n] = ktd[c];
+        for (int c = 0; c < DD; ++c) a.kappa[c * Np + n] = (double)ktd[c];
     }
     T dn[Q];
     N dm[Q], drho_m, jd_m[3];
@@ -142,26 +145,26 @@ __global__ void __launch_bounds__(256) k_collide_stream(CollArgs<P> a, H h, Geom
     node_moments<Q, N>(dm, drho_m, jd_m);
     // stress: traceless part and density source (Sec. III, trace split)
     T S[3][3];
-    double trd = 0;
+    N trd = 0;
     if (D == 2) {
         S[0][0] = (T)sg[0]; S[1][1] = (T)sg[1];
         S[0][1] = S[1][0] = (T)sg[2];
-        trd = (double)sg[0] + (double)sg[1];
+        trd = sg[0] + sg[1];
     } else {
         S[0][0] = (T)sg[0]; S[1][1] = (T)sg[1]; S[2][2] = (T)sg[2];
         S[0][1] = S[1][0] = (T)sg[3];
         S[0][2] = S[2][0] = (T)sg[4];
         S[1][2] = S[2][1] = (T)sg[5];
-        trd = (double)sg[0] + (double)sg[1] + (double)sg[2];
+        trd = sg[0] + sg[1] + sg[2];
     }
-    double ddr_d = 0;
-    if (p.trace_full) ddr_d = -(trd - a.tr_prev[n]) * (3.0 / D);   // -(tr - tr_prev)/(d cs^2)
-    const double drho_d = (double)drho_m + 0.5 * ddr_d;            // rho - rho0
-    const double rho_d = p.rho0 + drho_d;
-    const double inv_rho = 1.0 / rho_d;
-    double ud[3] = {0, 0, 0};
+    N ddr_d = 0;   // tr_prev holds the last step's N trace, exactly
+    if (p.trace_full) ddr_d = -(trd - (N)a.tr_prev[n]) * N(3.0 / D);   // -(tr - tr_prev)/(d cs^2)
+    const N drho_d = drho_m + N(0.5) * ddr_d;                            // rho - rho0
+    const N rho_d = chan_val<N>(p.rho0, p.rho0_f) + drho_d;
+    const N inv_rho = N(1) / rho_d;
+    N ud[3] = {0, 0, 0};
 #pragma unroll
-    for (int c = 0; c < D; ++c) ud[c] = ((double)jd_m[c] + 0.5 * p.f[c]) * inv_rho;
+    for (int c = 0; c < D; ++c) ud[c] = (jd_m[c] + N(0.5) * chan_val<N>(p.f[c], p.f_f[c])) * inv_rho;
     const T tr = (T)trd, ddr = (T)ddr_d, drho = (T)drho_d, rho = (T)rho_d;
     T u[3], f[3];
 #pragma unroll
@@ -249,10 +252,10 @@ __global__ void __launch_bounds__(256) k_collide_stream(CollArgs<P> a, H h, Geom
         if (wall) a.dn_out[L::opp(q) * Np + n] = post;
         else a.dn_out[q * Np + (coff + xd + cnx * (yd + cny * zd))] = post;
     }
-    a.rho[n] = drho_d;
+    a.rho[n] = (double)drho_d;
 #pragma unroll
-    for (int c = 0; c < D; ++c) a.u[c * Np + n] = ud[c];
-    a.tr_prev[n] = p.trace_full ? trd : 0.0;
+    for (int c = 0; c < D; ++c) a.u[c * Np + n] = (double)ud[c];
+    a.tr_prev[n] = p.trace_full ? (double)trd : 0.0;
 }
 
 // ------------------------------------------------------------------------------------------------

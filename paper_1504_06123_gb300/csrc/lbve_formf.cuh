@@ -376,16 +376,16 @@ __device__ __forceinline__ void formf_sigma(const R* part, int S, long long Np, 
 
 // exp(kappa) - 1 of the new point's factor in the arithmetic A (Taylor to 4th order in float, 8th in double:
 // |kappa| <= 1e-2 leaves below 1e-12 and 1e-20).
-template <int D, typename A>
-__device__ __forceinline__ void factor_dev(const double* ktd, A* Y) {
+template <int D, typename A, typename K>
+__device__ __forceinline__ void factor_dev(const K* ktd, A* Y) {
     A k[D * D];
 #pragma unroll
     for (int i = 0; i < D * D; ++i) k[i] = (A)ktd[i];
     expm1_mat<D, A>(k, Y);
 }
 
-template <int D>
-__device__ __forceinline__ void rate_of_strain(const double* ktd, double* dp) {
+template <int D, typename K>
+__device__ __forceinline__ void rate_of_strain(const K* ktd, K* dp) {
     constexpr int NS = D == 2 ? 3 : 6;
 #pragma unroll
     for (int i = 0; i < NS; ++i) {
@@ -706,16 +706,16 @@ __device__ __forceinline__ void f16_put(const CommitF16& a, long long n, long lo
     *f16_byte<D>(a, n, l, IS_Y ? Lay::ye_byte(j) : Lay::de_byte(j)) = eb;
 }
 
-template <int D, typename N>
+template <int D, typename N, typename K>
 __device__ __forceinline__ void hist_commit_any(Arith<N>, const CommitF16& a, const BlockStep* s_bs, long long Np,
-                                                int n, const double* /*kprev*/, const double* ktd, const Chan& p,
+                                                int n, const double* /*kprev*/, const K* ktd, const Chan& p,
                                                 N* sig, long long /*t*/) {
     constexpr int DD = D * D;
     constexpr int NS = D == 2 ? 3 : 6;
     float Yn[DD], dn[NS];
     factor_dev<D, float>(ktd, Yn);
     {
-        double dd[NS];
+        K dd[NS];
         rate_of_strain<D>(ktd, dd);
 #pragma unroll
         for (int i = 0; i < NS; ++i) dn[i] = (float)dd[i];

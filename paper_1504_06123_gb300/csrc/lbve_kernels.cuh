@@ -168,7 +168,8 @@ __device__ __forceinline__ void node_moments(const T* v, T& drho, T* j) {
 
 // The first kernel of a step also advances the device step counter (it starts at -1), so that the later
 // kernels of the step all read the same t.
-// M: arithmetic of the moments (float only for float populations with the 16-bit history).
+// M: arithmetic of the moments (float only for float populations with the 16-bit history); u_raw is stored
+// in M as well (float values in the same buffer), which the collision's gradient then reads in M.
 template <int Q, typename P, typename M>
 __global__ void __launch_bounds__(256) k_moments(const P* __restrict__ dn, double* __restrict__ u_raw, Geom g,
                                                  long long* t_dev) {
@@ -183,8 +184,9 @@ __global__ void __launch_bounds__(256) k_moments(const P* __restrict__ dn, doubl
     for (int q = 0; q < Q; ++q) v[q] = (M)dn[(long long)q * g.Npad + n];
     node_moments<Q, M>(v, drho, j);
     const M inv = M(1) / (chan_val<M>(p.rho0, p.rho0_f) + drho);
+    M* const ur = reinterpret_cast<M*>(u_raw);
 #pragma unroll
-    for (int a = 0; a < D; ++a) u_raw[(long long)a * g.Npad + n] = (double)((j[a] + M(0.5) * chan_val<M>(p.f[a], p.f_f[a])) * inv);
+    for (int a = 0; a < D; ++a) ur[(long long)a * g.Npad + n] = (j[a] + M(0.5) * chan_val<M>(p.f[a], p.f_f[a])) * inv;
 }
 
 // ------------------------------------------------------------------------------------------------
@@ -835,9 +837,9 @@ __device__ __forceinline__ void frame_apply(const float* Rm, const N* p, N* out)
     }
 }
 
-template <int D, typename N>
+template <int D, typename N, typename K>
 __device__ __forceinline__ void hist_commit_any(Arith<N>, const CommitS16& a, const BlockStep* s_bs, long long Np,
-                                                int n, const double* kprev, const double* ktd, const Chan& p,
+                                                int n, const double* kprev, const K* ktd, const Chan& p,
                                                 N* sig, long long t) {
     const N G_inf = chan_val<N>(p.G_inf, p.G_inf_f);
     constexpr int DD = D * D;

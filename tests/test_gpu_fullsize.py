@@ -1,9 +1,12 @@
 """GPU parity at the workloads' stated sizes and lengths, against the FP64 oracle.
 
 The flows start from rest without density noise, so they stay invariant along the periodic flow axis x:
-every column of the GPU channel (every x-slice of the duct) must equal the oracle's one-column channel
-(one-slice duct) of the same width, history grid and parameters.  That keeps the oracle affordable at full
-history length and full run length (its node loops run on all host cores).
+every column of the GPU channel (every x-slice of the duct) must match the oracle's one-column channel
+(one-slice duct) of the same width, history grid and parameters, and each comparison below takes the worst
+column.  That keeps the oracle affordable at full history length and full run length (its node loops run on
+all host cores).  The GPU's columns agree bitwise when every node tile sums its history in the same order;
+the balanced ranges of the 16-bit form F cut the tiles at different points, and the columns then differ by
+rounding.
 
   channel 1024 x 512, L = 1024 (B 8 x C 128): 5000 startup steps and 1000 cessation steps (force off),
       plain FP32 history (<= 1e-5) and the 16-bit history (<= 1e-3), each in form P (E - 1 advanced in
@@ -55,21 +58,27 @@ def run_peaks(refs: list) -> dict:
 
 
 def field_errors(got: dict, ref: dict, ixy: int, peaks: dict | None = None) -> dict:
-    """u, sigma, sigma_xy, N1 (on the sigma scale), kappa and rho of one column / slice against the oracle;
-    with `peaks`, a denominator below 1e-2 of the field's peak is held there (decayed flow after cessation)."""
+    """u, sigma, sigma_xy, N1 (on the sigma scale), kappa and rho of every column / slice against the oracle's
+    one (the worst column); with `peaks`, a denominator below 1e-2 of the field's peak is held there (decayed
+    flow after cessation)."""
+    def cols(key, r):   # got[key] as [slice][x][...] against r as [slice][1][...]
+        x = np.asarray(got[key], dtype=np.float64)
+        return x.reshape(x.shape[0], x.shape[1], -1), np.asarray(r, dtype=np.float64).reshape(x.shape[0], 1, -1)
+
     def err(key, x, r):
         den = np.max(np.abs(r))
         if peaks is not None:
             den = max(den, 1e-2 * peaks[key])
-        num = np.max(np.abs(np.asarray(x, dtype=np.float64) - r))
+        num = np.max(np.abs(x - r))
         return (0.0 if num == 0 else math.inf) if den == 0 else float(num / den)
-    e = {k: err(k, got[k].reshape(ref[k].shape), ref[k]) for k in ("u", "sigma", "kappa", "rho")}
-    e["sigma_xy"] = err("sigma_xy", got["sigma"].reshape(ref["sigma"].shape)[:, ixy], ref["sigma"][:, ixy])
+    e = {k: err(k, *cols(k, ref[k])) for k in ("u", "sigma", "kappa", "rho")}
+    gs, rs = cols("sigma", ref["sigma"])
+    e["sigma_xy"] = err("sigma_xy", gs[..., ixy], rs[..., ixy])
     sig_den = np.max(np.abs(ref["sigma"]))
     if peaks is not None:
         sig_den = max(sig_den, 1e-2 * peaks["sigma"])
-    e["n1_on_sigma_scale"] = float(np.max(np.abs(got["n1"].reshape(ref["n1"].shape) - ref["n1"])) /
-                                   max(sig_den, 1e-300))
+    gn, rn = cols("n1", ref["n1"])
+    e["n1_on_sigma_scale"] = float(np.max(np.abs(gn - rn)) / max(sig_den, 1e-300))
     return e
 
 
@@ -80,13 +89,8 @@ def check(errs: dict, tol: float, what: str):
 
 
 def columns(f: dict, nx: int, ny: int, nz: int = 1) -> dict:
-    """The fields as [slice][x][...]; all x must be bitwise equal (x-invariant flow)."""
-    out = {}
-    for k, v in f.items():
-        a = np.asarray(v).reshape(nz * ny, nx, -1)
-        assert np.array_equal(a, np.broadcast_to(a[:, :1], a.shape)), f"{k} differs along x"
-        out[k] = a[:, 0]
-    return out
+    """The fields as [slice][x][...] (node n = x + nx (y + ny z)); field_errors compares every x."""
+    return {k: np.asarray(v).reshape(nz * ny, nx, -1) for k, v in f.items()}
 
 
 # ---------------------------------------------------------------------------------------------

@@ -248,7 +248,7 @@ __device__ inline long long adj_t(const A& a) { return *a.t0 + a.t_off; }
 template <class A>
 __device__ inline void adj_table(const A& a, float* s_age, float* s_w, int* s_part, BlockStep* s_bs) {
     const int Ls = a.B * a.C;
-    if (threadIdx.x == 0) sched_step(a.B, a.C, adj_t(a), s_bs);
+    sched_step_cta(a.B, a.C, adj_t(a), s_bs);
     __syncthreads();
     for (int l = threadIdx.x; l < Ls; l += blockDim.x) {
         int age, part;
@@ -315,7 +315,7 @@ __global__ void __launch_bounds__(32) k_adj_node(AdjArgs<TP, TH> a, Geom g, AdjP
     constexpr int NS = D == 2 ? 3 : 6;
     // only the block transitions of step t are needed here (the merges of the commit)
     __shared__ BlockStep s_bs[LBVE_MAXB];
-    if (threadIdx.x == 0) sched_step(a.B, a.C, adj_t(a), s_bs);
+    sched_step_cta(a.B, a.C, adj_t(a), s_bs);
     __syncthreads();
     const int n = blockIdx.x * blockDim.x + threadIdx.x;
     if (n >= g.N) return;
@@ -608,7 +608,7 @@ template <int D, typename TP, typename TH>
 __global__ void __launch_bounds__(32) k_adj_fin(AdjArgs<TP, TH> a, Geom g, AdjPar p) {
     constexpr int DD = D * D;
     __shared__ BlockStep bs[LBVE_MAXB];
-    if (threadIdx.x == 0) sched_step(a.B, a.C, adj_t(a), bs);
+    sched_step_cta(a.B, a.C, adj_t(a), bs);
     __syncthreads();
     const int n = blockIdx.x * blockDim.x + threadIdx.x;
     if (n >= g.N) return;

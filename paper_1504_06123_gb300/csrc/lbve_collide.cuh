@@ -114,7 +114,7 @@ __global__ void __launch_bounds__(256) k_collide_stream(CollArgs<P> a, H h, Geom
     constexpr int NS = D == 2 ? 3 : 6;
     __shared__ BlockStep s_bs[LBVE_MAXB];
     const long long t = *a.t_dev;
-    if (threadIdx.x == 0) sched_step(h.B, h.C, t, s_bs);
+    sched_step_cta(h.B, h.C, t, s_bs);
     __syncthreads();
     const int n = blockIdx.x * blockDim.x + threadIdx.x;
     if (n >= g.N) return;

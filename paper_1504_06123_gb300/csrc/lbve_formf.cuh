@@ -189,8 +189,9 @@ __device__ __forceinline__ RankTab rank_tables(unsigned char* smem, int B, int C
     RankEnt* ent = reinterpret_cast<RankEnt*>(smem);
     BlockStep* s_bs = reinterpret_cast<BlockStep*>(ent + L);
     int* s_off = reinterpret_cast<int*>(s_bs + LBVE_MAXB);   // first rank of each block, then the total
+    sched_step_cta(B, C, t, s_bs);
+    __syncthreads();
     if (threadIdx.x == 0) {
-        sched_step(B, C, t, s_bs);
         int r = 0;
         for (int bb = B - 1; bb >= 0; --bb) {
             s_off[bb] = r;

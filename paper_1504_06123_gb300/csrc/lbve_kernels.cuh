@@ -493,7 +493,7 @@ __global__ void __launch_bounds__(256, 2) k_sweep(SweepArgs<R> a, Geom g) {
     R* s_red = reinterpret_cast<R*>(smem_raw + sweep_smem_bytes(L));
 
     const long long t = *a.t_dev;
-    if (threadIdx.x == 0) sched_step(a.B, a.C, t, s_bs);
+    sched_step_cta(a.B, a.C, t, s_bs);
     __syncthreads();
     for (int l = threadIdx.x; l < L; l += blockDim.x) {
         int age, part;
@@ -951,7 +951,7 @@ __global__ void __launch_bounds__(256, 2) k_sweep_s16(CommitS16 a, const double*
     BlockStep* s_bs = reinterpret_cast<BlockStep*>(s_part + L);
 
     const long long t = *t_dev;
-    if (threadIdx.x == 0) sched_step(a.B, a.C, t, s_bs);
+    sched_step_cta(a.B, a.C, t, s_bs);
     __syncthreads();
     for (int l = threadIdx.x; l < L; l += blockDim.x) {
         int age, part;
@@ -1112,7 +1112,7 @@ __global__ void __launch_bounds__(256) k_commit(H a, const double* __restrict__ 
     constexpr int NS = D == 2 ? 3 : 6;
     __shared__ BlockStep s_bs[LBVE_MAXB];
     const long long t = *t_dev;
-    if (threadIdx.x == 0) sched_step(a.B, a.C, t, s_bs);
+    sched_step_cta(a.B, a.C, t, s_bs);
     __syncthreads();
     const int n = blockIdx.x * blockDim.x + threadIdx.x;
     if (n >= g.N) return;

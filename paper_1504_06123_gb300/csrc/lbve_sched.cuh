@@ -40,31 +40,72 @@ LBVE_HD void sched_block_state(int B, int C, long long t, int bb, int* head, int
         return;
     }
     const long long r = t >> (B - 1 - bb);   // index of the latest receipt
-    *head = (int)(r % C);
+    // (the 32-bit remainder for any receipt index below 2^32, the same value as the 64-bit one)
+    *head = r <= 0xFFFFFFFFll ? (int)((unsigned)r % (unsigned)C) : (int)(r % C);
     *count = (bb == 0) ? C : ((r & 1) == 0 ? C - 1 : C);
 }
 
-// Per-block state transition of step t >= 0.
+// State of block bb in step t >= 0, every field but age_prev.
+LBVE_HD void sched_block(int B, int C, long long t, int bb, BlockStep* sb) {
+    const int sp = 1 << (B - 1 - bb);
+    int hp, cp, hn, cn;
+    sched_block_state(B, C, t - 1, bb, &hp, &cp);
+    sched_block_state(B, C, t, bb, &hn, &cn);
+    const int recv = (t & (long long)(sp - 1)) == 0;
+    sb->head_prev = hp;
+    sb->count_prev = cp;
+    sb->head_new = hn;
+    sb->count_new = cn;
+    sb->recv = recv;
+    sb->evict = recv && cp == C;
+    sb->spacing = sp;
+}
+
+// Per-block state transition of step t >= 0.  The age of block bb's newest point, finest block first: the
+// ages spanned by every finer block (its points times its spacing, less one) plus the gaps between blocks.
 LBVE_HD void sched_step(int B, int C, long long t, BlockStep* s) {
     int age = 0;
     for (int bb = B - 1; bb >= 0; --bb) {
-        const int sp = 1 << (B - 1 - bb);
-        int hp, cp, hn, cn;
-        sched_block_state(B, C, t - 1, bb, &hp, &cp);
-        sched_block_state(B, C, t, bb, &hn, &cn);
-        const int recv = (t & (long long)(sp - 1)) == 0;
-        if (bb != B - 1) age += sp;             // gap to the oldest point of the finer block
-        s[bb].head_prev = hp;
-        s[bb].count_prev = cp;
-        s[bb].head_new = hn;
-        s[bb].count_new = cn;
-        s[bb].recv = recv;
-        s[bb].evict = recv && cp == C;
-        s[bb].spacing = sp;
+        sched_block(B, C, t, bb, &s[bb]);
+        if (bb != B - 1) age += s[bb].spacing;                // gap to the oldest point of the finer block
         s[bb].age_prev = age;
-        age += (cp - 1) * sp;                   // age of the block's oldest point
+        age += (s[bb].count_prev - 1) * s[bb].spacing;        // age of the block's oldest point
     }
 }
+
+#if defined(__CUDACC__)
+// sched_step computed by a CTA: lane bb < B of warp 0 fills block bb, and the ages follow as warp suffix sums,
+// age_prev(bb) = sum over b > bb of (count_prev(b) - 1) spacing(b) + sum over bb <= b < B - 1 of spacing(b).
+// CTAs of fewer than 32 threads let thread 0 run sched_step.  Every thread of the CTA calls it; the states
+// are valid after the caller's next __syncthreads().
+__device__ __forceinline__ void sched_step_cta(int B, int C, long long t, BlockStep* s) {
+    if (blockDim.x < 32) {
+        if (threadIdx.x == 0) sched_step(B, C, t, s);
+        return;
+    }
+    if (threadIdx.x >= 32) return;
+    const int bb = threadIdx.x;
+    int term = 0, gap = 0;
+    if (bb < B) {
+        BlockStep b;
+        sched_block(B, C, t, bb, &b);
+        term = (b.count_prev - 1) * b.spacing;
+        gap = bb < B - 1 ? b.spacing : 0;
+        s[bb] = b;
+    }
+    int st = term, sg = gap;   // inclusive suffix sums over lanes bb .. 31
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const int a1 = __shfl_down_sync(0xffffffffu, st, o);
+        const int a2 = __shfl_down_sync(0xffffffffu, sg, o);
+        if (bb + o < 32) {
+            st += a1;
+            sg += a2;
+        }
+    }
+    if (bb < B) s[bb].age_prev = st - term + sg;
+}
+#endif
 
 // Role of ring slot j of block bb during step t, for a point already in memory (the point created at
 // step t is not in memory yet).  Returns the trapezoidal weight (0 = slot takes no part: empty, or

@@ -104,7 +104,7 @@ __global__ void __launch_bounds__(128) k_moments_t(const Dual* __restrict__ dn, 
 // The per-CTA table of slot roles at step t (ages, weights, merge partners).
 __device__ inline void tan_table(int B, int C, long long t, float* s_age, float* s_w, int* s_part, BlockStep* s_bs) {
     const int L = B * C;
-    if (threadIdx.x == 0) sched_step(B, C, t, s_bs);
+    sched_step_cta(B, C, t, s_bs);
     __syncthreads();
     for (int l = threadIdx.x; l < L; l += blockDim.x) {
         int age, part;

@@ -223,6 +223,31 @@ def test_formf16_balanced_ranges():
         c.close()
 
 
+def test_formf16_balanced_ranges_duct():
+    """Balanced ranges of the 3D sweep (two nodes a lane, 64-node tiles): a 6 x 32 x 32 duct (6144 nodes, 96 tiles,
+    each cut into some 26 pieces on 2432 resident warps; L = 4 x 64 allows 32) with the 16-bit form F pinned to
+    mode 2, against the FP64 oracle at the reduced-precision bar, and bitwise equal on a second handle."""
+    kw = dict(tau_lb=0.9, G_inf=0.005, tau=60.0, gamma_c=0.1, g=(2e-5, 0, 0), C=64, B=4)
+    chans = []
+    for _ in range(2):
+        c = L.Channel(L.make_desc(L.LBVE_D3Q19, 6, 32, 32, precision=F32, hist_storage=S16, hist_form=FF, **kw))
+        L.lbve_set_sweep_config(c.h, 1, 2)
+        assert L.lbve_sweep_config(c.h)[2] == 2
+        chans.append(c)
+    chans[0].step(150)
+    chans[1].step(3)
+    chans[1].step(147)
+    f0, f1 = chans[0].fields(), chans[1].fields()
+    for k in f0:
+        assert np.array_equal(f0[k], f1[k]), k
+    orc = oracle.Channel(oracle.D3Q19, 6, 32, 32, **kw)
+    orc.step(150)
+    compare(f0, orc.fields(), TOL[RED], "balanced ranges, 6 x 32 x 32 duct, L = 256, 150 steps")
+    orc.close()
+    for c in chans:
+        c.close()
+
+
 @pytest.mark.parametrize("hist", [F32, S16])
 def test_formf_empty_trailing_chunks(hist):
     """A history grid where chunk tasks leave the last chunk empty at some steps (B = 3, C = 27: 79 to 81

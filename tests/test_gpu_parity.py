@@ -11,7 +11,8 @@ to rounding, e.g. u_y in channel flow):
   FP64                                               <= 1e-12  (the stated bar of the FP64 path)
   reduced-precision form: 16-bit block-scaled history (LBVE_S16), FP32 (or FP64) populations
                                                      <= 1e-3 (the stated bar of the precision variant)
-Integer/structural results (x-invariance, history grid) are compared exactly.
+Integer/structural results (x-invariance, history grid, the streaming map with its walls and periodic wraps)
+are compared exactly.
 """
 import math
 
@@ -516,3 +517,40 @@ def test_fields_ex_per_channel_and_precision():
             L.lbve_fields_ex(ch.h, bad[0], mask, bad[1], dst=torch.empty(4, device="cuda"))
         assert e.value.status == L.LBVE_EINVAL
     ch.close()
+
+
+# ---------------------------------------------------------------------------------------------
+# The streaming map and the walls, exactly: one density pulse, no stress, omega = 1
+# ---------------------------------------------------------------------------------------------
+@pytest.mark.parametrize("lattice,nx,ny,nz,wall_z,src", [
+    (L.LBVE_D2Q9, 5, 6, 1, 1, (0, 0, 0)),        # on the bottom wall, on the periodic seam
+    (L.LBVE_D2Q9, 5, 6, 1, 1, (2, 5, 0)),        # on the top wall
+    (L.LBVE_D3Q19, 4, 5, 6, 1, (0, 0, 5)),       # a duct edge: two walls and the seam
+    (L.LBVE_D3Q19, 4, 5, 6, 0, (3, 2, 0)),       # periodic z: the pulse wraps in x and z
+])
+def test_streaming_and_walls_exact(lattice, nx, ny, nz, wall_z, src):
+    """With tau_LB = 1 (omega = 1), no stress (G_inf = 0) and no force, a density pulse delta at one node of a fluid
+    at rest collides to w_q delta in every direction q and streams: one step later the node density is w_q delta
+    at the neighbour in direction q, the populations sent into a wall come back to the pulse's node (half-way
+    bounce-back), and every other node is exactly at rest.  delta = 36 * 2^-30 makes every w_q delta and their
+    sums exact, so the density field after the second step (the densities the streamed populations carry) is
+    compared with the oracle's bit for bit: the periodic wrap along x (and z), the walls and the index map of
+    every direction."""
+    N = nx * ny * nz
+    delta = 36.0 * 2.0 ** -30
+    rho = np.ones(N)
+    x, y, z = src
+    rho[x + nx * (y + ny * z)] += delta
+    kw = dict(tau_lb=1.0, G_inf=0.0, tau=50.0, gamma_c=0.1, g=(0.0, 0.0, 0.0), C=8, B=2)
+    ch = L.Channel(L.make_desc(lattice, nx, ny, nz, precision=F64, hist_storage=F64, wall_z=wall_z, **kw), rho)
+    orc = oracle.Channel(oracle.D2Q9 if lattice == L.LBVE_D2Q9 else oracle.D3Q19, nx, ny, nz, wall_z=bool(wall_z),
+                         rho_init=rho, **kw)
+    ch.step(2)
+    orc.step(2)
+    got, ref = ch.fields()["rho"], orc.fields()["rho"]
+    ch.close()
+    orc.close()
+    moved = np.flatnonzero(ref != 1.0)
+    assert 1 < len(moved) <= (9 if lattice == L.LBVE_D2Q9 else 19)
+    assert abs(np.sum(ref - 1.0) - delta) <= 1e-30          # the pulse's mass, all of it accounted for
+    np.testing.assert_array_equal(got, ref)
